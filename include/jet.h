@@ -1,0 +1,212 @@
+/*
+ * jet.h - C ABI of the B300 sliced tensor-network contraction library.
+ *
+ * The problem these calls state (Section 3, "Overview of Jet"): a tensor network
+ * of gate and state tensors with labelled indices, a pairwise contraction path,
+ * and a set of sliced indices, reduced to one or more output amplitudes.
+ *
+ *   network  Section 2.1 / 2.2.1: tensors are nodes, shared labels are edges; a
+ *            label carried by two tensors is summed over, a label carried by one
+ *            tensor is an open leg (an output qudit).
+ *   path     Section 2.3 (Eq. sequence, binary contraction tree): step k contracts
+ *            two live tensors over the labels they share.
+ *   slice    Section 2.4 (Eq. sliced_sum): a sliced label is fixed to each of its
+ *            values in turn; the amplitude is the sum of the partial contractions.
+ *   reuse    Section 3.2 (Eq. task_based_amplitude_flops): an intermediate that
+ *            does not depend on a slice (or amplitude) value is computed once and
+ *            read by every slice (amplitude) that needs it.
+ *
+ * Conventions shared by every call
+ *   - Tensors are dense and row-major; labels[0] is the slowest index.
+ *   - Every call returns JET_OK (0) or a negative JET_E* code; on error nothing
+ *     has changed (all-or-nothing) and jet_last_error() describes the failure.
+ *     A handle stays valid after an error.
+ *   - Input buffers are copied; the caller keeps ownership of everything it
+ *     passes.  Output buffers are caller-owned.
+ *   - A handle is not thread-safe: one thread at a time per handle.
+ *   - Complex numbers are interleaved (re, im).
+ *   - Device work runs on the CUDA stream the caller passes (NULL = the legacy
+ *     default stream) on the device named in jet_options.device.
+ */
+#ifndef JET_B300_H
+#define JET_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JET_OK        0
+#define JET_EINVAL   -1   /* bad label, dim, path, slice, size or pointer         */
+#define JET_ENOMEM   -2   /* device or host allocation failed, or workspace too small */
+#define JET_ECUDA    -3   /* a CUDA runtime or driver call failed                 */
+#define JET_ETIMEOUT -4   /* a bounded device-side wait ran out                   */
+#define JET_ESTATE   -5   /* call out of order (e.g. contract before a path)      */
+
+typedef struct jet_network jet_network;            /* opaque, owned by the library */
+
+typedef struct { float re, im; } jet_c64;
+typedef struct { double re, im; } jet_c128;
+
+/* Arithmetic used for the large (GEMM-shaped) pairwise contractions.  Small
+ * contractions always run on CUDA cores in FP32 (FP64 in JET_PREC_FP64).
+ * Intermediates are complex64, except in JET_PREC_FP64 (complex128).  Slice
+ * and amplitude sums are always FP64. */
+typedef enum {
+    JET_PREC_FP32   = 0,  /* FP32 FMA on CUDA cores (the plain reference path)         */
+    JET_PREC_TF32   = 1,  /* one TF32 tcgen05 product per real product, FP32 accumulate */
+    JET_PREC_TF32X3 = 2,  /* x = hi + lo in TF32; hi*hi + hi*lo + lo*hi                 */
+    JET_PREC_BF16X3 = 3,  /* x = hi + lo in BF16; hi*hi + hi*lo + lo*hi                 */
+    JET_PREC_BF16X6 = 4,  /* x = hi + mid + lo in BF16; the six products above 2^-24    */
+    JET_PREC_FP64   = 5   /* complex128 everywhere, FP64 on CUDA cores                  */
+} jet_precision;
+
+typedef struct {
+    int32_t precision;        /* jet_precision, default JET_PREC_FP32                     */
+    int32_t reuse;            /* 1 (default): shared intermediates computed once;
+                                 0: every (slice, amplitude) recomputes its whole tree   */
+    int32_t use_graph;        /* 1 (default): record the launch sequence in a CUDA graph */
+    int32_t device;           /* CUDA device ordinal, default 0                          */
+    int64_t gemm_min_k;       /* contractions with a summed extent >= this (and large
+                                 outputs) take the GEMM route; default 64                 */
+    int64_t workspace_limit;  /* bytes of device workspace the plan may use; 0 = none    */
+} jet_options;
+
+typedef struct {
+    int32_t rank;
+    const int64_t *labels;    /* rank labels, any non-negative values                    */
+    const int32_t *dims;      /* rank dims, each >= 1; a label has one dim everywhere     */
+    const jet_c64 *data;      /* prod(dims) values, row-major, labels[0] slowest (host)   */
+} jet_tensor_desc;
+
+typedef struct {
+    double   flop_planned;        /* algorithmic real FLOP of one amplitude, the path
+                                     unsliced: 8 * prod(dims of the union) per step        */
+    double   flop_sliced;         /* N_sl * FLOP_sl (Eq. sliced_flops), no reuse           */
+    double   flop_executed;       /* FLOP of the unique instances the last plan executes  */
+    double   reuse_fraction;      /* f_sl of Eq. task_based_amplitude_flops (last plan)   */
+    double   bytes_executed;      /* algorithmic HBM bytes of the last plan               */
+    int64_t  max_intermediate;    /* largest intermediate of one slice, elements          */
+    int64_t  workspace_bytes;     /* device workspace the last plan needs                 */
+    int64_t  n_instances;         /* unique contraction instances in the last plan        */
+    int64_t  n_launches;          /* kernel launches per contract call                    */
+    int32_t  n_slices;            /* N_sl                                                  */
+    int32_t  n_sliced_labels;
+    int32_t  n_gemm_nodes;        /* tree nodes routed to the GEMM kernels                */
+    int32_t  n_direct_nodes;      /* tree nodes routed to the direct-contraction kernel   */
+} jet_stats_t;
+
+/* Defaults listed in jet_options above. */
+void jet_options_default(jet_options *opt);
+
+/* Build a network from n tensors (Section 2.2.1).  Copies every tensor to the
+ * device.  Each label must appear in one or two tensors, with the same dim in
+ * both; labels appearing once are open legs.  opt may be NULL (defaults).
+ * Errors: JET_EINVAL (n < 1, rank < 0, dim < 1, a label on three tensors or
+ * repeated in one tensor, mismatched dims, NULL pointers), JET_ENOMEM, JET_ECUDA. */
+int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_options *opt,
+                       jet_network **out);
+
+/* Declare the output legs, in the order the amplitude patterns of jet_contract
+ * list their digits (the bras <a_i| of Section 2.2.1 attach here).  Every open
+ * leg must be listed exactly once.  Clears the path-dependent plan.
+ * Errors: JET_EINVAL (a label that is not an open leg, a duplicate, a missing leg). */
+int jet_network_set_open(jet_network *net, int32_t n_out, const int64_t *out_labels);
+
+/* Replace the values of tensor tensor_id (same shape).  Host pointer; the copy to
+ * the device is ordered on the library's internal stream before the next
+ * contraction.  Errors: JET_EINVAL (bad id / NULL), JET_ECUDA. */
+int jet_tensor_update(jet_network *net, int32_t tensor_id, const jet_c64 *data);
+
+/* Replace the values of all tensors at once: data holds every tensor's values
+ * back to back in tensor order (jet_network_n_values() complex values).  One
+ * host-to-device copy on `stream`, ordered before work later issued there.
+ * Pass pinned host memory for an asynchronous copy. */
+int jet_tensors_upload(jet_network *net, const jet_c64 *data, void *cuda_stream);
+int64_t jet_network_n_values(const jet_network *net);
+
+/* Set the contraction path (Section 2.3): n_steps = n_tensors - 1 pairs in SSA
+ * form: ids 0..n-1 are the input tensors, step k creates id n+k; each id is
+ * consumed exactly once.  Errors: JET_EINVAL (wrong count, an id used twice or
+ * not yet created), JET_ESTATE (open legs not declared). */
+int jet_path_set(jet_network *net, int32_t n_steps, const int32_t *pairs);
+
+/* Read back the current path (2 * (n_tensors - 1) ints). */
+int jet_path_get(const jet_network *net, int32_t *pairs_out);
+
+/* The library's own planner (greedy; the paper delegates path search to an
+ * external tool, Section 3): repeatedly contract the pair of tensors sharing a
+ * label that minimises size(out) - size(A) - size(B), ties to smaller FLOP then
+ * smaller ids; trial t > 0 perturbs the score with seeded noise; the path of
+ * lowest total FLOP is kept and set.  flop_out (may be NULL) receives its FLOP.
+ * Open legs count as fixed (dim 1) because every amplitude fixes them. */
+int jet_path_greedy(jet_network *net, uint64_t seed, int32_t n_trials, double *flop_out);
+
+/* Slice the given closed labels (Section 2.4); n = 0 clears the slicing.
+ * Slice id s is the mixed-radix number over the sliced labels, the first label
+ * most significant.  Errors: JET_EINVAL (open or unknown label, duplicate). */
+int jet_slice(jet_network *net, int32_t n, const int64_t *labels);
+
+/* Greedy slice finder along the current path: while an intermediate of one
+ * slice exceeds max_elems, or fewer than min_n labels are sliced, slice the
+ * closed label of the largest intermediate that minimises the reuse-aware FLOP
+ * of Eq. task_based_amplitude_flops (ties: lower total FLOP, then smaller
+ * label), at most max_n labels.  Writes the chosen labels (labels_out may be
+ * NULL, else room for max_n) and their count, and applies them.
+ * Errors: JET_ESTATE (no path), JET_EINVAL (cap not reachable within max_n). */
+int jet_slice_auto(jet_network *net, int64_t max_elems, int32_t min_n, int32_t max_n, int32_t *n_out,
+                   int64_t *labels_out);
+
+/* Contract the network to n_amps amplitudes.  outputs holds n_amps rows of
+ * n_out digits (the values of the open legs, in jet_network_set_open order).
+ * amp_b = sum over slices s (increasing s, FP64) of the sliced contraction.
+ * amps_out: n_amps complex128 values in HOST memory; the call copies them back
+ * and synchronises the stream before returning.
+ * Errors: JET_EINVAL (digit out of range, n_amps < 1), JET_ESTATE (no path),
+ * JET_ENOMEM (workspace), JET_ECUDA, JET_ETIMEOUT. */
+int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs,
+                 jet_c128 *amps_out, void *cuda_stream);
+
+/* Same as jet_contract but amps_dev is DEVICE memory (n_amps complex128) and
+ * the call returns without synchronising: the amplitudes are ready when work
+ * issued on cuda_stream before the next call completes. */
+int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,
+                       jet_c128 *amps_dev, void *cuda_stream);
+
+/* Device workspace.  jet_plan prepares the plan for this batch of outputs and
+ * reports the bytes of device workspace it needs.  jet_set_workspace hands the
+ * library caller-owned device memory (at least that many bytes, 256-byte
+ * aligned) to use instead of allocating its own; NULL releases it.  The caller
+ * keeps the memory alive until the handle is destroyed or another workspace is
+ * set.  Without a workspace the library allocates one itself. */
+int jet_plan(jet_network *net, int32_t n_amps, const int32_t *outputs, size_t *bytes_out);
+int jet_set_workspace(jet_network *net, void *dptr, size_t bytes);
+
+/* Adjoint (environment) contraction; not in the paper.
+ * env_G = sum_b cot_b * d amp_b / d G for each requested input tensor G
+ * (holomorphic: G is not conjugated; env_G has G's shape and layout).
+ * For loss = sum_b |amp_b|^2 pass cot_b = conj(amp_b); then
+ * d loss / d theta = 2 Re sum_G <env_G, dG/dtheta>, <X,Y> = sum_i X_i Y_i.
+ * Per slice the forward tree is recomputed (no intermediates are kept across
+ * slices).  env_out[i] points to prod(dims) complex64 values of HOST memory for
+ * tensor tensor_ids[i]; amps_out (may be NULL) receives the amplitudes.
+ * Errors as jet_contract, plus JET_EINVAL (bad tensor id). */
+int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs,
+                      const jet_c128 *cot, int32_t n_req, const int32_t *tensor_ids,
+                      jet_c64 *const *env_out, jet_c128 *amps_out, void *cuda_stream);
+
+/* Statistics of the network and the last plan (see jet_stats_t). */
+int jet_stats(const jet_network *net, jet_stats_t *out);
+
+/* Release the handle and every device buffer the library allocated. */
+void jet_network_destroy(jet_network *net);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *jet_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JET_B300_H */

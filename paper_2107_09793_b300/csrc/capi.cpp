@@ -1,0 +1,367 @@
+// C ABI entry points (declared in include/jet.h).  Each call validates its
+// arguments, works on copies, and converts internal errors into JET_E* codes
+// plus a thread-local message; nothing escapes the boundary as an exception.
+#include <algorithm>
+#include <cstring>
+#include <exception>
+#include <new>
+#include <string>
+#include <unordered_set>
+
+#include "internal.h"
+
+namespace jet {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+
+[[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+template <typename F>
+static int guarded(F &&f)
+{
+    try {
+        f();
+        g_last_error.clear();
+        return JET_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return JET_ENOMEM;
+    } catch (const std::exception &e) {
+        g_last_error = e.what();
+        return JET_EINVAL;
+    } catch (...) {
+        g_last_error = "unknown error";
+        return JET_EINVAL;
+    }
+}
+
+static void invalidate_plan(Network &net)
+{
+    if (net.plan) {
+        release_plan_device(*net.plan);
+        net.plan.reset();
+    }
+}
+
+static Plan &get_plan(Network &net, int32_t n_amps, const int32_t *outputs)
+{
+    if (!outputs) fail(JET_EINVAL, "outputs is NULL");
+    const size_t n = (size_t)n_amps * net.open.size();
+    Plan *P = net.plan.get();
+    bool reuse = P && P->n_amps == n_amps && P->path_version == net.path_version &&
+                 P->slice_version == net.slice_version && P->precision == net.opt.precision &&
+                 P->reuse == net.opt.reuse && P->outputs.size() == n &&
+                 std::equal(P->outputs.begin(), P->outputs.end(), outputs);
+    if (!reuse) {
+        auto fresh = build_plan(net, n_amps, outputs);
+        invalidate_plan(net);
+        net.plan = std::move(fresh);
+    }
+    return *net.plan;
+}
+
+}  // namespace jet
+
+using namespace jet;
+
+struct jet_network : public jet::Network {};
+
+extern "C" {
+
+void jet_options_default(jet_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof *opt);
+    opt->precision = JET_PREC_FP32;
+    opt->reuse = 1;
+    opt->use_graph = 1;
+    opt->device = 0;
+    opt->gemm_min_k = 64;
+    opt->workspace_limit = 0;
+}
+
+int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_options *opt, jet_network **out)
+{
+    return guarded([&] {
+        if (!out) fail(JET_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!tensors || n < 1) fail(JET_EINVAL, "need at least one tensor");
+        auto net = std::make_unique<jet_network>();
+        if (opt) net->opt = *opt;
+        else jet_options_default(&net->opt);
+        if (net->opt.precision < JET_PREC_FP32 || net->opt.precision > JET_PREC_FP64)
+            fail(JET_EINVAL, "unknown precision mode");
+        if (net->opt.gemm_min_k < 1) net->opt.gemm_min_k = 64;
+        int64_t off = 0;
+        for (int32_t t = 0; t < n; ++t) {
+            const jet_tensor_desc &d = tensors[t];
+            if (d.rank < 0 || d.rank > 64) fail(JET_EINVAL, "tensor " + std::to_string(t) + ": bad rank");
+            if (d.rank > 0 && (!d.labels || !d.dims)) fail(JET_EINVAL, "tensor " + std::to_string(t) + ": NULL labels/dims");
+            if (!d.data) fail(JET_EINVAL, "tensor " + std::to_string(t) + ": NULL data");
+            Leaf L;
+            std::unordered_set<int64_t> seen;
+            for (int32_t k = 0; k < d.rank; ++k) {
+                int64_t l = d.labels[k];
+                int32_t dim = d.dims[k];
+                if (l < 0) fail(JET_EINVAL, "tensor " + std::to_string(t) + ": negative label");
+                if (dim < 1 || dim > 65535) fail(JET_EINVAL, "tensor " + std::to_string(t) + ": dim out of range");
+                if (!seen.insert(l).second)
+                    fail(JET_EINVAL, "tensor " + std::to_string(t) + ": label " + std::to_string(l) + " repeated");
+                LabelInfo &li = net->labels[l];
+                if (li.n_owner == 2)
+                    fail(JET_EINVAL, "label " + std::to_string(l) + " appears on more than two tensors");
+                if (li.n_owner == 1 && li.dim != dim)
+                    fail(JET_EINVAL, "label " + std::to_string(l) + ": dims differ between tensors");
+                li.dim = dim;
+                li.owner[li.n_owner++] = t;
+                L.labels.push_back(l);
+                L.dims.push_back(dim);
+                L.size *= dim;
+                if (L.size > ((int64_t)1 << 40)) fail(JET_EINVAL, "tensor too large");
+            }
+            L.offset = off;
+            off += L.size;
+            net->leaves.push_back(L);
+        }
+        net->n_values = off;
+        net->host_values.resize(off);
+        for (int32_t t = 0; t < n; ++t)
+            std::memcpy(net->host_values.data() + net->leaves[t].offset, tensors[t].data,
+                        (size_t)net->leaves[t].size * sizeof(jet_c64));
+        // a single open leg set by default: none declared yet
+        *out = net.release();
+    });
+}
+
+int jet_network_set_open(jet_network *net, int32_t n_out, const int64_t *out_labels)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (n_out < 0 || (n_out > 0 && !out_labels)) fail(JET_EINVAL, "bad open-leg list");
+        std::unordered_set<int64_t> seen;
+        for (int32_t j = 0; j < n_out; ++j) {
+            auto it = net->labels.find(out_labels[j]);
+            if (it == net->labels.end() || it->second.n_owner != 1)
+                fail(JET_EINVAL, "label " + std::to_string(out_labels[j]) + " is not an open leg");
+            if (!seen.insert(out_labels[j]).second) fail(JET_EINVAL, "open leg listed twice");
+        }
+        size_t n_open = 0;
+        for (auto &kv : net->labels) n_open += kv.second.n_owner == 1;
+        if (n_open != (size_t)n_out)
+            fail(JET_EINVAL, "every open leg must be listed (" + std::to_string(n_open) + " open legs)");
+        net->open.assign(out_labels, out_labels + n_out);
+        net->open_set = true;
+        for (int64_t l : net->open)
+            if (std::find(net->sliced.begin(), net->sliced.end(), l) != net->sliced.end()) {
+                net->sliced.clear();
+                ++net->slice_version;
+            }
+        invalidate_plan(*net);
+    });
+}
+
+int jet_tensor_update(jet_network *net, int32_t tensor_id, const jet_c64 *data)
+{
+    return guarded([&] {
+        if (!net || !data) fail(JET_EINVAL, "NULL argument");
+        if (tensor_id < 0 || tensor_id >= (int32_t)net->leaves.size()) fail(JET_EINVAL, "bad tensor id");
+        const Leaf &L = net->leaves[tensor_id];
+        std::memcpy(net->host_values.data() + L.offset, data, (size_t)L.size * sizeof(jet_c64));
+        upload_leaf(*net, tensor_id, nullptr);
+    });
+}
+
+int jet_tensors_upload(jet_network *net, const jet_c64 *data, void *cuda_stream)
+{
+    return guarded([&] {
+        if (!net || !data) fail(JET_EINVAL, "NULL argument");
+        upload_all(*net, data, cuda_stream);
+    });
+}
+
+int64_t jet_network_n_values(const jet_network *net) { return net ? net->n_values : -1; }
+
+int jet_path_set(jet_network *net, int32_t n_steps, const int32_t *pairs)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (n_steps < 0 || (n_steps > 0 && !pairs)) fail(JET_EINVAL, "bad path");
+        std::vector<std::pair<int32_t, int32_t>> p;
+        for (int32_t k = 0; k < n_steps; ++k) p.push_back({pairs[2 * k], pairs[2 * k + 1]});
+        validate_path(*net, p);
+        net->path = p;
+        ++net->path_version;
+        net->flop_planned = path_cost(*net, p, {}).flop;
+        invalidate_plan(*net);
+    });
+}
+
+int jet_path_get(const jet_network *net, int32_t *pairs_out)
+{
+    return guarded([&] {
+        if (!net || !pairs_out) fail(JET_EINVAL, "NULL argument");
+        if (net->path.size() + 1 != net->leaves.size()) fail(JET_ESTATE, "no path set");
+        for (size_t k = 0; k < net->path.size(); ++k) {
+            pairs_out[2 * k] = net->path[k].first;
+            pairs_out[2 * k + 1] = net->path[k].second;
+        }
+    });
+}
+
+int jet_path_greedy(jet_network *net, uint64_t seed, int32_t n_trials, double *flop_out)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        double f = 0;
+        auto p = greedy_path(*net, seed, std::max(n_trials, 1), &f);
+        validate_path(*net, p);
+        net->path = p;
+        ++net->path_version;
+        net->flop_planned = f;
+        if (flop_out) *flop_out = f;
+        invalidate_plan(*net);
+    });
+}
+
+int jet_slice(jet_network *net, int32_t n, const int64_t *labels)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (n < 0 || (n > 0 && !labels)) fail(JET_EINVAL, "bad slice list");
+        std::vector<int64_t> s;
+        for (int32_t i = 0; i < n; ++i) {
+            auto it = net->labels.find(labels[i]);
+            if (it == net->labels.end()) fail(JET_EINVAL, "unknown label " + std::to_string(labels[i]));
+            if (it->second.n_owner != 2) fail(JET_EINVAL, "label " + std::to_string(labels[i]) + " is an open leg");
+            if (std::find(s.begin(), s.end(), labels[i]) != s.end()) fail(JET_EINVAL, "label sliced twice");
+            s.push_back(labels[i]);
+        }
+        double nsl = 1;
+        for (int64_t l : s) nsl *= net->labels.at(l).dim;
+        if (nsl > (double)(1 << 30)) fail(JET_EINVAL, "too many slices");
+        net->sliced = s;
+        ++net->slice_version;
+        invalidate_plan(*net);
+    });
+}
+
+int jet_slice_auto(jet_network *net, int64_t max_elems, int32_t min_n, int32_t max_n, int32_t *n_out,
+                   int64_t *labels_out)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (net->path.size() + 1 != net->leaves.size()) fail(JET_ESTATE, "no path set");
+        if (max_elems < 1) fail(JET_EINVAL, "max_elems must be >= 1");
+        auto s = slice_auto(*net, max_elems, std::max(min_n, 0), std::max(max_n, 0));
+        if (n_out) *n_out = (int32_t)s.size();
+        if (labels_out)
+            for (size_t i = 0; i < s.size(); ++i) labels_out[i] = s[i];
+        net->sliced = s;
+        ++net->slice_version;
+        invalidate_plan(*net);
+    });
+}
+
+int jet_plan(jet_network *net, int32_t n_amps, const int32_t *outputs, size_t *bytes_out)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        Plan &P = get_plan(*net, n_amps, outputs);
+        if (bytes_out) *bytes_out = P.arena_bytes;
+    });
+}
+
+int jet_set_workspace(jet_network *net, void *dptr, size_t bytes)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (dptr && ((uintptr_t)dptr & 255)) fail(JET_EINVAL, "workspace must be 256-byte aligned");
+        net->user_arena = dptr;
+        net->user_arena_bytes = dptr ? bytes : 0;
+    });
+}
+
+int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c128 *amps_dev,
+                       void *cuda_stream)
+{
+    return guarded([&] {
+        if (!net || !amps_dev) fail(JET_EINVAL, "NULL argument");
+        Plan &P = get_plan(*net, n_amps, outputs);
+        bind_and_run(*net, P, nullptr, cuda_stream);
+        copy_d2d_async(amps_dev, net->d_amps, (size_t)n_amps * sizeof(jet_c128),
+                       cuda_stream ? cuda_stream : net->stream);
+    });
+}
+
+int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c128 *amps_out, void *cuda_stream)
+{
+    return guarded([&] {
+        if (!net || !amps_out) fail(JET_EINVAL, "NULL argument");
+        Plan &P = get_plan(*net, n_amps, outputs);
+        bind_and_run(*net, P, nullptr, cuda_stream);
+        copy_d2h(amps_out, net->d_amps, (size_t)n_amps * sizeof(jet_c128), cuda_stream ? cuda_stream : net->stream);
+    });
+}
+
+int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs, const jet_c128 *cot,
+                      int32_t n_req, const int32_t *tensor_ids, jet_c64 *const *env_out, jet_c128 *amps_out,
+                      void *cuda_stream)
+{
+    return guarded([&] {
+        (void)net; (void)n_amps; (void)outputs; (void)cot; (void)n_req; (void)tensor_ids;
+        (void)env_out; (void)amps_out; (void)cuda_stream;
+        fail(JET_ESTATE, "jet_contract_grad: not available in this build");
+    });
+}
+
+int jet_stats(const jet_network *net, jet_stats_t *out)
+{
+    return guarded([&] {
+        if (!net || !out) fail(JET_EINVAL, "NULL argument");
+        std::memset(out, 0, sizeof *out);
+        out->flop_planned = net->flop_planned;
+        double nsl = 1;
+        for (int64_t l : net->sliced) nsl *= net->labels.at(l).dim;
+        out->n_slices = (int32_t)nsl;
+        out->n_sliced_labels = (int32_t)net->sliced.size();
+        if (net->path.size() + 1 == net->leaves.size()) {
+            PathCost c = path_cost(*net, net->path, net->sliced);
+            out->flop_sliced = nsl * c.flop;
+            out->max_intermediate = (int64_t)c.max_size;
+        }
+        if (net->plan) {
+            const Plan &P = *net->plan;
+            out->flop_executed = P.flop_executed;
+            out->bytes_executed = P.bytes_executed;
+            out->workspace_bytes = (int64_t)P.arena_bytes;
+            out->n_instances = P.n_instances;
+            out->n_launches = (int64_t)P.ops.size();
+            out->n_gemm_nodes = P.n_gemm;
+            out->n_direct_nodes = P.n_direct;
+            double per_assign = out->flop_sliced / std::max(nsl, 1.0);   // FLOP_sl
+            double n_assign = (double)P.n_amps * nsl;
+            double noreuse = n_assign * per_assign;
+            if (n_assign > 1 && per_assign > 0)
+                out->reuse_fraction = (noreuse - P.flop_executed) / ((n_assign - 1) * per_assign);
+        }
+    });
+}
+
+void jet_network_destroy(jet_network *net)
+{
+    if (!net) return;
+    try {
+        free_network_device(*net);
+    } catch (...) {
+    }
+    delete net;
+}
+
+const char *jet_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

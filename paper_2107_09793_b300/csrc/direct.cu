@@ -1,0 +1,273 @@
+// Direct strided pairwise contraction (Section 2.3, one step of Eq. sequence):
+//   C[out] = sum_k A[offA(out) + offA(k)] * B[offB(out) + offB(k)]
+// evaluated from label strides, with no operand transpose.  This is the route
+// for the many small contractions of a circuit network (gate absorption,
+// gate-gate fusion, leaf/bra attachment, Section 2.2.1) and for
+// contractions with few outputs and a long summed index (split-K).
+//
+// Also: the deterministic split-K partial sum, and the FP64 slice/amplitude
+// reduction of Eq. sliced_sum.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernel_args.h"
+#include "kernels.cuh"
+
+namespace jet {
+
+template <typename V>
+__device__ __forceinline__ V cmul_add(V acc, V x, V y)
+{
+    acc.x = fma(x.x, y.x, acc.x);
+    acc.x = fma(-x.y, y.y, acc.x);
+    acc.y = fma(x.x, y.y, acc.y);
+    acc.y = fma(x.y, y.x, acc.y);
+    return acc;
+}
+
+template <typename V>
+__device__ __forceinline__ V vzero()
+{
+    V z;
+    z.x = 0;
+    z.y = 0;
+    return z;
+}
+
+// Row decode: POW2 uses shifts (every dim a power of two), else div/mod.
+template <bool POW2>
+__device__ __forceinline__ void decode(int64_t r, int rank, const int64_t *dim, const int64_t *sA,
+                                       const int64_t *sB, int64_t &oa, int64_t &ob)
+{
+    for (int j = 0; j < rank; ++j) {
+        int64_t d = dim[j];
+        int64_t q, dg;
+        if (POW2) {
+            int sh = __ffsll((unsigned long long)d) - 1;
+            q = r >> sh;
+            dg = r & (d - 1);
+        } else {
+            q = r / d;
+            dg = r - q * d;
+        }
+        oa += dg * sA[j];
+        ob += dg * sB[j];
+        r = q;
+    }
+}
+
+template <typename V, bool POW2>
+__global__ void __launch_bounds__(256) direct_kernel(const __grid_constant__ DirectArgs a)
+{
+    extern __shared__ int32_t sm[];
+    int32_t *sColA = sm, *sColB = sm + a.n_cols;
+    int32_t *sKA = sColB + a.n_cols, *sKB = sKA + a.n_klo;
+    const int32_t *gColA = (const int32_t *)a.colA, *gColB = (const int32_t *)a.colB;
+    const int32_t *gKA = (const int32_t *)a.kA, *gKB = (const int32_t *)a.kB;
+    for (int i = threadIdx.x; i < a.n_cols; i += blockDim.x) {
+        sColA[i] = gColA[i];
+        sColB[i] = gColB[i];
+    }
+    for (int i = threadIdx.x; i < a.n_klo; i += blockDim.x) {
+        sKA[i] = gKA[i];
+        sKB[i] = gKB[i];
+    }
+    __syncthreads();
+    const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
+    for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
+        const V *__restrict__ A = (const V *)pA[inst];
+        const V *__restrict__ B = (const V *)pB[inst];
+        V *__restrict__ C = (V *)pC[inst];
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.n_out;
+             e += (int64_t)gridDim.x * blockDim.x) {
+            int64_t r = e / a.n_cols;
+            int c = (int)(e - r * a.n_cols);
+            int64_t oa = sColA[c], ob = sColB[c];
+            decode<POW2>(r, a.row_rank, a.row_dim, a.row_sA, a.row_sB, oa, ob);
+            V acc = vzero<V>();
+            for (int64_t h = 0; h < a.n_khi; ++h) {
+                int64_t ha = oa, hb = ob;
+                decode<POW2>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
+                for (int q = 0; q < a.n_klo; ++q) acc = cmul_add(acc, __ldg(A + ha + sKA[q]), __ldg(B + hb + sKB[q]));
+            }
+            C[e] = acc;
+        }
+    }
+}
+
+// Few outputs, long summed index: block (part, output group, instance) sums
+// its slice of khi values over all klo entries, block-reduces, writes a partial.
+template <typename V, bool POW2>
+__global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constant__ DirectArgs a)
+{
+    extern __shared__ int32_t sm[];
+    int32_t *sKA = sm, *sKB = sm + a.n_klo;
+    __shared__ V red[JET_SPLITK_G][8];
+    const int32_t *gKA = (const int32_t *)a.kA, *gKB = (const int32_t *)a.kB;
+    const int32_t *gColA = (const int32_t *)a.colA, *gColB = (const int32_t *)a.colB;
+    for (int i = threadIdx.x; i < a.n_klo; i += blockDim.x) {
+        sKA[i] = gKA[i];
+        sKB[i] = gKB[i];
+    }
+    __syncthreads();
+    const int64_t inst = blockIdx.z;
+    if (inst >= a.n_inst) return;
+    const V *__restrict__ A = (const V *)((const uint64_t *)a.ptrA)[inst];
+    const V *__restrict__ B = (const V *)((const uint64_t *)a.ptrB)[inst];
+    const int64_t out0 = (int64_t)blockIdx.y * JET_SPLITK_G;
+    const int nout = (int)((a.n_out - out0) < JET_SPLITK_G ? (a.n_out - out0) : JET_SPLITK_G);
+    int64_t oa[JET_SPLITK_G], ob[JET_SPLITK_G];
+    V acc[JET_SPLITK_G];
+#pragma unroll
+    for (int j = 0; j < JET_SPLITK_G; ++j) {
+        oa[j] = ob[j] = 0;
+        acc[j] = vzero<V>();
+        if (j < nout) {
+            int64_t e = out0 + j;
+            int64_t r = e / a.n_cols;
+            int c = (int)(e - r * a.n_cols);
+            oa[j] = gColA[c];
+            ob[j] = gColB[c];
+            decode<POW2>(r, a.row_rank, a.row_dim, a.row_sA, a.row_sB, oa[j], ob[j]);
+        }
+    }
+    const int64_t h0 = (int64_t)blockIdx.x * a.khi_per_part;
+    const int64_t h1 = (h0 + a.khi_per_part) < a.n_khi ? (h0 + a.khi_per_part) : a.n_khi;
+    for (int64_t h = h0; h < h1; ++h) {
+        int64_t ha = 0, hb = 0;
+        decode<POW2>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
+        for (int q = threadIdx.x; q < a.n_klo; q += blockDim.x) {
+            const int64_t ka = ha + sKA[q], kb = hb + sKB[q];
+#pragma unroll
+            for (int j = 0; j < JET_SPLITK_G; ++j)
+                if (j < nout) acc[j] = cmul_add(acc[j], __ldg(A + oa[j] + ka), __ldg(B + ob[j] + kb));
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < JET_SPLITK_G; ++j) {
+        V s = acc[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        if (lane == 0) red[j][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < nout) {
+        V s = vzero<V>();
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s.x += red[threadIdx.x][w].x;
+            s.y += red[threadIdx.x][w].y;
+        }
+        V *part = (V *)a.partials;
+        part[(inst * a.ksplit + blockIdx.x) * a.n_out + out0 + threadIdx.x] = s;
+    }
+}
+
+template <typename V>
+__global__ void splitk_reduce_kernel(const __grid_constant__ SplitKReduceArgs a)
+{
+    const V *part = (const V *)a.partials;
+    const uint64_t *pC = (const uint64_t *)a.ptrC;
+    const int64_t total = a.n_out * a.n_inst;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t inst = e / a.n_out, o = e - inst * a.n_out;
+        V s = vzero<V>();
+        for (int p = 0; p < a.ksplit; ++p) {
+            V x = part[(inst * a.ksplit + p) * a.n_out + o];
+            s.x += x.x;
+            s.y += x.y;
+        }
+        ((V *)pC[inst])[o] = s;
+    }
+}
+
+// amp[b] = sum_{s = 0 .. n_sl-1} root(b, s), in FP64, one thread per amplitude.
+__global__ void slice_reduce_kernel(const __grid_constant__ ReduceArgs a)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= a.n_amps) return;
+    const uint64_t *roots = (const uint64_t *)a.roots;
+    double re = 0, im = 0;
+    for (int s = 0; s < a.n_slices; ++s) {
+        uint64_t p = roots[(int64_t)b * a.n_slices + s];
+        if (a.fp64_in) {
+            double2 v = *(const double2 *)p;
+            re += v.x;
+            im += v.y;
+        } else {
+            float2 v = *(const float2 *)p;
+            re += (double)v.x;
+            im += (double)v.y;
+        }
+    }
+    ((double2 *)a.amps)[b] = make_double2(re, im);
+}
+
+__global__ void c64_to_c128_kernel(const float2 *src, double2 *dst, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float2 v = src[i];
+        dst[i] = make_double2(v.x, v.y);
+    }
+}
+
+// ------------------------------------------------------------ launchers
+cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    dim3 grid(c.gx, c.gy, c.gz);
+    bool fp64 = c.variant & 1, splitk = c.variant & 2, pow2 = c.variant & 4;
+    size_t smem = c.smem;
+#define JET_DIRECT_LAUNCH(V, P)                                                                 \
+    do {                                                                                        \
+        if (splitk) direct_splitk_kernel<V, P><<<grid, c.block, smem, s>>>(a);                  \
+        else direct_kernel<V, P><<<grid, c.block, smem, s>>>(a);                                \
+    } while (0)
+    if (fp64) {
+        if (pow2) JET_DIRECT_LAUNCH(double2, true);
+        else JET_DIRECT_LAUNCH(double2, false);
+    } else {
+        if (pow2) JET_DIRECT_LAUNCH(float2, true);
+        else JET_DIRECT_LAUNCH(float2, false);
+    }
+#undef JET_DIRECT_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t set_direct_smem_limits()
+{
+    const int bytes = 8 * (JET_COLMAX + JET_KLOMAX);
+    cudaError_t e = cudaSuccess;
+#define JET_SMEM(K)                                                                             \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+    JET_SMEM(direct_kernel<float2 JET_COMMA true>);
+    JET_SMEM(direct_kernel<float2 JET_COMMA false>);
+    JET_SMEM(direct_kernel<double2 JET_COMMA true>);
+    JET_SMEM(direct_kernel<double2 JET_COMMA false>);
+#undef JET_SMEM
+    return e;
+}
+
+cudaError_t launch_splitk_reduce(const SplitKReduceArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    if (c.variant & 1) splitk_reduce_kernel<double2><<<c.gx, 256, 0, s>>>(a);
+    else splitk_reduce_kernel<float2><<<c.gx, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slice_reduce(const ReduceArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    slice_reduce_kernel<<<c.gx, c.block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_c64_to_c128(const void *src, void *dst, int64_t n, cudaStream_t s)
+{
+    int64_t blocks = std::min<int64_t>((n + 255) / 256, 148 * 8);
+    if (blocks < 1) blocks = 1;
+    c64_to_c128_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float2 *)src, (double2 *)dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace jet

@@ -1,0 +1,262 @@
+// Executor: binds a plan to its device buffers (leaves, arena, amplitudes),
+// issues its launches in tree order on the caller's stream, and records the
+// whole launch sequence once into a CUDA graph that later calls replay.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+#include "kernel_args.h"
+#include "kernels.cuh"
+
+namespace jet {
+
+#define JET_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) fail(JET_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void *device_alloc(size_t bytes)
+{
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(e == cudaErrorMemoryAllocation ? JET_ENOMEM : JET_ECUDA,
+             std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    return p;
+}
+
+void device_free(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+static void set_device(const Network &net) { JET_CUDA(cudaSetDevice(net.opt.device)); }
+
+static bool g_smem_set[64] = {false};
+
+static void init_device_once(const Network &net)
+{
+    int dev = net.opt.device;
+    if (dev >= 0 && dev < 64 && !g_smem_set[dev]) {
+        JET_CUDA(set_direct_smem_limits());
+        g_smem_set[dev] = true;
+    }
+}
+
+void ensure_leaves_on_device(Network &net)
+{
+    set_device(net);
+    init_device_once(net);
+    if (!net.stream) {
+        cudaStream_t s;
+        JET_CUDA(cudaStreamCreate(&s));
+        net.stream = s;
+    }
+    if (!net.d_leaves) {
+        net.d_leaves = device_alloc((size_t)net.n_values * sizeof(jet_c64));
+        JET_CUDA(cudaMemcpy(net.d_leaves, net.host_values.data(), (size_t)net.n_values * sizeof(jet_c64),
+                            cudaMemcpyHostToDevice));
+        net.leaves64_stale = true;
+    }
+    if (net.opt.precision == JET_PREC_FP64) {
+        if (!net.d_leaves64) {
+            net.d_leaves64 = device_alloc((size_t)net.n_values * sizeof(jet_c128));
+            net.leaves64_stale = true;
+        }
+        if (net.leaves64_stale) {
+            JET_CUDA(launch_c64_to_c128(net.d_leaves, net.d_leaves64, net.n_values, (cudaStream_t)net.stream));
+            JET_CUDA(cudaStreamSynchronize((cudaStream_t)net.stream));
+            net.leaves64_stale = false;
+        }
+    }
+}
+
+void upload_leaf(Network &net, int32_t tensor_id, void *)
+{
+    if (!net.d_leaves) return;  // uploaded in full on first use
+    set_device(net);
+    const Leaf &L = net.leaves[tensor_id];
+    JET_CUDA(cudaMemcpy((jet_c64 *)net.d_leaves + L.offset, net.host_values.data() + L.offset,
+                        (size_t)L.size * sizeof(jet_c64), cudaMemcpyHostToDevice));
+    net.leaves64_stale = true;
+}
+
+void upload_all(Network &net, const jet_c64 *data, void *stream)
+{
+    ensure_leaves_on_device(net);
+    cudaStream_t s = (cudaStream_t)stream;
+    JET_CUDA(cudaMemcpyAsync(net.d_leaves, data, (size_t)net.n_values * sizeof(jet_c64), cudaMemcpyHostToDevice, s));
+    if (net.opt.precision == JET_PREC_FP64) {
+        JET_CUDA(launch_c64_to_c128(net.d_leaves, net.d_leaves64, net.n_values, s));
+        net.leaves64_stale = false;
+    } else {
+        net.leaves64_stale = true;
+    }
+}
+
+void copy_d2h(void *dst, const void *src, size_t bytes, void *stream)
+{
+    JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    JET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+}
+
+void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream)
+{
+    JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+}
+
+bool gemm_available(int32_t) { return false; }
+
+void release_plan_device(Plan &plan)
+{
+    if (plan.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)plan.graph_exec);
+    plan.graph_exec = nullptr;
+    device_free(plan.d_args);
+    plan.d_args = nullptr;
+    plan.d_args_bytes = 0;
+}
+
+void free_network_device(Network &net)
+{
+    if (net.plan) release_plan_device(*net.plan);
+    device_free(net.d_leaves);
+    device_free(net.d_leaves64);
+    device_free(net.own_arena);
+    device_free(net.d_amps);
+    if (net.stream) cudaStreamDestroy((cudaStream_t)net.stream);
+    net.d_leaves = net.d_leaves64 = net.own_arena = net.d_amps = nullptr;
+    net.stream = nullptr;
+}
+
+static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op &op, cudaStream_t s)
+{
+    LaunchCfg c{op.grid_x, op.grid_y, op.grid_z, op.block, op.smem, op.variant};
+    const uint8_t *p = args.data() + op.args_off;
+    cudaError_t e = cudaSuccess;
+    switch (op.kind) {
+    case OpKind::Direct: {
+        DirectArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_direct(a, c, s);
+        break;
+    }
+    case OpKind::SplitKReduce: {
+        SplitKReduceArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_splitk_reduce(a, c, s);
+        break;
+    }
+    case OpKind::Reduce: {
+        ReduceArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_slice_reduce(a, c, s);
+        break;
+    }
+    default:
+        fail(JET_EINVAL, "internal: unknown op kind");
+    }
+    if (e != cudaSuccess) fail(JET_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    (void)P;
+}
+
+void bind_and_run(Network &net, Plan &P, void *, void *stream)
+{
+    ensure_leaves_on_device(net);
+    cudaStream_t s = stream ? (cudaStream_t)stream : (cudaStream_t)net.stream;
+
+    // workspace
+    void *arena = nullptr;
+    if (net.user_arena) {
+        if (net.user_arena_bytes < P.arena_bytes)
+            fail(JET_ENOMEM, "workspace too small: need " + std::to_string(P.arena_bytes) + " bytes, have " +
+                                 std::to_string(net.user_arena_bytes));
+        arena = net.user_arena;
+    } else {
+        if (net.own_arena_bytes < P.arena_bytes) {
+            JET_CUDA(cudaStreamSynchronize(s));
+            device_free(net.own_arena);
+            net.own_arena = nullptr;
+            net.own_arena_bytes = 0;
+            net.own_arena = device_alloc(P.arena_bytes);
+            net.own_arena_bytes = P.arena_bytes;
+        }
+        arena = net.own_arena;
+    }
+    if (net.d_amps_cap < P.n_amps) {
+        JET_CUDA(cudaStreamSynchronize(s));
+        device_free(net.d_amps);
+        net.d_amps = nullptr;
+        net.d_amps = device_alloc((size_t)P.n_amps * sizeof(jet_c128));
+        net.d_amps_cap = P.n_amps;
+    }
+    void *leaves = net.opt.precision == JET_PREC_FP64 ? net.d_leaves64 : net.d_leaves;
+
+    // (re)bind pointers
+    bool rebind = P.dirty_args || P.bound_arena != arena || P.bound_leaves != leaves || P.bound_amps != net.d_amps;
+    if (rebind) {
+        if (P.graph_exec) {
+            JET_CUDA(cudaStreamSynchronize(s));
+            cudaGraphExecDestroy((cudaGraphExec_t)P.graph_exec);
+            P.graph_exec = nullptr;
+        }
+        if (P.d_args_bytes < P.host_args.size()) {
+            device_free(P.d_args);
+            P.d_args = nullptr;
+            P.d_args = device_alloc(P.host_args.size());
+            P.d_args_bytes = P.host_args.size();
+        }
+        uintptr_t bases[4] = {(uintptr_t)leaves, (uintptr_t)arena, (uintptr_t)P.d_args, (uintptr_t)net.d_amps};
+        for (const auto &pt : P.patches) {
+            uint64_t v = (uint64_t)(bases[pt.base] + (uintptr_t)pt.byte_off);
+            std::memcpy(P.host_args.data() + pt.at, &v, 8);
+        }
+        JET_CUDA(cudaMemcpy(P.d_args, P.host_args.data(), P.host_args.size(), cudaMemcpyHostToDevice));
+        P.bound_arena = arena;
+        P.bound_leaves = leaves;
+        P.bound_amps = net.d_amps;
+        P.dirty_args = false;
+    }
+
+    if (net.opt.use_graph) {
+        if (!P.graph_exec) {
+            if (P.graph_exec) {
+                cudaGraphExecDestroy((cudaGraphExec_t)P.graph_exec);
+                P.graph_exec = nullptr;
+            }
+            // capture on a private stream, then replay on the caller's
+            cudaStream_t cap;
+            JET_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                try {
+                    for (const Op &op : P.ops) launch_op(P, P.host_args, op, cap);
+                } catch (...) {
+                    cudaStreamEndCapture(cap, &g);
+                    if (g) cudaGraphDestroy(g);
+                    cudaStreamDestroy(cap);
+                    throw;
+                }
+                e = cudaStreamEndCapture(cap, &g);
+            }
+            cudaStreamDestroy(cap);
+            if (e != cudaSuccess) fail(JET_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            cudaGraphExec_t ge;
+            e = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) fail(JET_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            P.graph_exec = ge;
+            P.graph_stream = (void *)s;
+        }
+        JET_CUDA(cudaGraphLaunch((cudaGraphExec_t)P.graph_exec, s));
+    } else {
+        for (const Op &op : P.ops) launch_op(P, P.host_args, op, s);
+    }
+}
+
+}  // namespace jet

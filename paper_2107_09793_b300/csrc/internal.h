@@ -1,0 +1,166 @@
+// Internal data structures of the library (host side).
+#pragma once
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "../../include/jet.h"
+
+namespace jet {
+
+// Error carrying a JET_E* code; caught at the C boundary.
+struct Error {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string &msg);
+void set_last_error(const std::string &msg);
+
+struct Leaf {
+    std::vector<int64_t> labels;
+    std::vector<int32_t> dims;
+    int64_t size = 1;
+    int64_t offset = 0;      // element offset in the packed leaf buffer
+};
+
+struct LabelInfo {
+    int32_t dim = 0;
+    int32_t owner[2] = {-1, -1};
+    int32_t n_owner = 0;
+};
+
+// ---------------------------------------------------------------- planner
+// Contraction tree derived from an SSA path (Section 2.3, binary tree).
+struct Tree {
+    int32_t n_leaves = 0;
+    std::vector<std::pair<int32_t, int32_t>> children;   // internal node k -> (a, b), ids are SSA ids
+    // per SSA id: remaining labels (fixed ones removed), in no particular order
+    std::vector<std::vector<int64_t>> labels;
+    int32_t root() const { return n_leaves + (int32_t)children.size() - 1; }
+};
+
+// FLOP / size model of a path with a given set of fixed labels (dim 1).
+struct PathCost {
+    double flop = 0;                 // sum over steps of 8 * prod(dims of the union)
+    double max_size = 0;             // largest intermediate (elements)
+    std::vector<double> step_flop;   // per internal node
+    std::vector<double> node_size;   // per SSA id
+};
+
+// -------------------------------------------------------------- plan / ops
+enum class OpKind : int32_t { Direct = 0, Permute = 1, GemmSimt = 2, GemmTc = 3, Reduce = 4, SplitKReduce = 5 };
+
+struct Op {
+    OpKind kind;
+    int32_t node = -1;
+    int64_t n_inst = 0;
+    size_t args_off = 0;      // byte offset of this op's argument block in the plan's constant buffer
+    size_t args_bytes = 0;
+    double flop = 0;          // algorithmic real FLOP of this launch (all instances)
+    double bytes = 0;         // algorithmic HBM bytes of this launch
+    int32_t grid_x = 1, grid_y = 1, grid_z = 1, block = 256;
+    int32_t smem = 0;
+    int32_t variant = 0;      // kernel-specific variant selector
+};
+
+struct Network;
+
+struct Plan {
+    // key
+    std::vector<int32_t> outputs;
+    int32_t n_amps = 0;
+    uint64_t path_version = 0;
+    uint64_t slice_version = 0;
+    int32_t precision = 0;
+    int32_t reuse = 1;
+
+    // sizes
+    int64_t n_slices = 1;
+    size_t arena_bytes = 0;          // intermediates + scratch (device workspace)
+    std::vector<Op> ops;
+    std::vector<uint8_t> host_args;   // argument blocks (pointers patched at bind time)
+    // pointer patch list: (byte offset in host_args, buffer id, element/byte offset)
+    struct Patch { size_t at; int32_t base; int64_t byte_off; };
+    std::vector<Patch> patches;       // base: 0 = leaf buffer, 1 = arena, 2 = args buffer itself, 3 = amps out
+    size_t amps_patch_count = 0;
+
+    // statistics
+    double flop_executed = 0, bytes_executed = 0;
+    int64_t n_instances = 0;
+    int32_t n_gemm = 0, n_direct = 0;
+    int64_t max_intermediate = 0;
+
+    // device state (owned)
+    void *d_args = nullptr;
+    size_t d_args_bytes = 0;
+    void *bound_arena = nullptr;
+    void *bound_leaves = nullptr;
+    void *bound_amps = nullptr;
+    void *graph_exec = nullptr;       // cudaGraphExec_t
+    void *graph_stream = nullptr;
+    bool dirty_args = true;
+};
+
+struct Network {
+    jet_options opt;
+    std::vector<Leaf> leaves;
+    std::unordered_map<int64_t, LabelInfo> labels;
+    std::vector<int64_t> open;        // declared output legs (order = pattern digit order)
+    bool open_set = false;
+    std::vector<std::pair<int32_t, int32_t>> path;
+    uint64_t path_version = 0;
+    std::vector<int64_t> sliced;
+    uint64_t slice_version = 0;
+
+    int64_t n_values = 0;            // total complex values of all leaves
+    std::vector<jet_c64> host_values;
+    void *d_leaves = nullptr;        // complex64, packed
+    void *d_leaves64 = nullptr;      // complex128 copy for the FP64 path (lazy)
+    bool leaves64_stale = true;
+    void *stream = nullptr;          // library-internal stream for uploads
+
+    std::unique_ptr<Plan> plan;
+    void *own_arena = nullptr;
+    size_t own_arena_bytes = 0;
+    void *user_arena = nullptr;
+    size_t user_arena_bytes = 0;
+    void *d_amps = nullptr;          // device amplitude buffer (complex128)
+    int64_t d_amps_cap = 0;
+
+    // planner results
+    double flop_planned = 0;
+};
+
+// planner.cpp
+Tree build_tree(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path);
+PathCost path_cost(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
+                   const std::vector<int64_t> &fixed);
+std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_t seed,
+                                                     int32_t n_trials, double *flop_out);
+std::vector<int64_t> slice_auto(const Network &net, int64_t max_elems, int32_t min_n, int32_t max_n);
+double reuse_aware_flop(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
+                        const std::vector<int64_t> &sliced);
+void validate_path(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path);
+
+// plan.cpp
+std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs);
+
+// exec.cu
+void ensure_leaves_on_device(Network &net);
+void bind_and_run(Network &net, Plan &plan, void *amps_dev, void *stream);
+void release_plan_device(Plan &plan);
+void free_network_device(Network &net);
+void upload_leaf(Network &net, int32_t tensor_id, void *stream);
+void upload_all(Network &net, const jet_c64 *data, void *stream);
+void *device_alloc(size_t bytes);
+void device_free(void *p);
+void copy_d2h(void *dst, const void *src, size_t bytes, void *stream);
+void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream);
+bool gemm_available(int32_t precision);
+
+}  // namespace jet

@@ -1,0 +1,95 @@
+// Plain-old-data argument blocks of the device kernels.  Built on the host by
+// the plan compiler, passed to the kernels by value (__grid_constant__).
+// Pointer-table fields hold device addresses patched in when the plan is bound
+// to its buffers.
+#pragma once
+#include <stdint.h>
+
+#define JET_MAXR 40          // max labels decoded by loop (rows, outer K part)
+#define JET_COLMAX 1024      // max entries of a column offset table
+#define JET_KLOMAX 1024      // max entries of an inner-K offset table
+#define JET_SPLITK_G 8       // outputs per block in the split-K direct kernel
+
+// Pairwise contraction C = sum_K A * B evaluated directly from strides
+// (Section 2.3).  The output index is split as (row, col): col is the trailing
+// group of output labels (offset tables colA/colB), row is decoded by loop.
+// The summed index is split as (khi, klo): klo has offset tables kA/kB, khi is
+// decoded by loop.  All offsets are in elements.
+struct DirectArgs {
+    uint64_t ptrA, ptrB, ptrC;      // device arrays of n_inst addresses (uint64)
+    uint64_t colA, colB;            // device int32[n_cols]
+    uint64_t kA, kB;                // device int32[n_klo]
+    uint64_t partials;              // split-K scratch: complex[n_inst][ksplit][n_out] (or 0)
+    int64_t n_rows, n_khi, n_out;
+    int32_t n_cols, n_klo;
+    int32_t n_inst, ksplit;
+    int32_t row_rank, khi_rank;
+    int32_t khi_per_part;           // split-K: khi values per part
+    int32_t pad_;
+    int64_t row_dim[JET_MAXR], row_sA[JET_MAXR], row_sB[JET_MAXR];   // fastest label first
+    int64_t khi_dim[JET_MAXR], khi_sA[JET_MAXR], khi_sB[JET_MAXR];   // fastest label first
+};
+
+// Sum the split-K partials of each output in a fixed order (deterministic).
+struct SplitKReduceArgs {
+    uint64_t partials;              // complex[n_inst][ksplit][n_out]
+    uint64_t ptrC;                  // device array of n_inst addresses
+    int64_t n_out;
+    int32_t n_inst, ksplit;
+};
+
+// Gather a strided tensor into a dense one: dst[i] = src[off(i)], where the
+// destination index is decoded fastest label first (Section 3.1: the transpose
+// half of transpose-transpose-GEMM).
+struct PermuteArgs {
+    uint64_t ptrSrc, ptrDst;        // device arrays of n_inst addresses
+    int64_t n;                      // elements per instance
+    int32_t rank, n_inst;
+    int64_t dim[JET_MAXR];          // destination labels, fastest first
+    int64_t sstride[JET_MAXR];      // matching source strides
+};
+
+// Batched complex GEMM C[m][n] = sum_k A[m][k] B[k][n] (row-major C, ldc = N).
+// a_kmajor: A stored [M][K] (else [K][M]); b_kmajor: B stored [N][K] (else [K][N]).
+struct GemmArgs {
+    uint64_t ptrA, ptrB, ptrC;      // device arrays of n_inst addresses
+    int64_t M, N, K;
+    int32_t n_inst;
+    int32_t a_kmajor, b_kmajor;
+    int32_t pad_;
+};
+
+// Split-precision operand planes for the tensor-core GEMM: a complex operand in
+// any strided layout is written as bf16/tf32 planes, K contiguous, padded.
+struct SplitArgs {
+    uint64_t ptrSrc;                // device array of n_inst addresses (complex64)
+    uint64_t dst;                   // base of the planes (per instance: planes * rows_pad * k_pad)
+    int64_t rows, k, rows_pad, k_pad;
+    int64_t inst_stride;            // elements between instances' plane sets
+    int32_t n_inst, n_planes_per_part;
+    int32_t rank_r, rank_k;
+    int32_t mode;                   // jet_precision
+    int32_t pad_;
+    int64_t r_dim[JET_MAXR], r_s[JET_MAXR];   // row labels, fastest first, source strides
+    int64_t k_dim[JET_MAXR], k_s[JET_MAXR];   // K labels, fastest first, source strides
+};
+
+// Tensor-core GEMM over split planes (see gemm_tc.cu).
+struct TcGemmArgs {
+    uint64_t planesA, planesB;      // plane bases (device)
+    uint64_t ptrC;                  // device array of n_inst addresses
+    int64_t M, N, K;                // logical sizes
+    int64_t m_pad, n_pad, k_pad;
+    int64_t a_inst_stride, b_inst_stride;   // elements between instances
+    int32_t n_inst, mode;
+    int32_t tiles_m, tiles_n;
+};
+
+// amp[b] = sum over slices s (increasing s) of root[inst(b, s)], FP64
+// (Section 2.4, Eq. sliced_sum; the single reduction over slices).
+struct ReduceArgs {
+    uint64_t roots;                 // device array of n_amps * n_slices addresses of scalars
+    uint64_t amps;                  // complex128[n_amps]
+    int32_t n_amps, n_slices;
+    int32_t fp64_in, pad_;
+};

@@ -1,0 +1,566 @@
+// Plan compiler: turns (network, path, sliced labels, batch of output patterns)
+// into a fixed list of kernel launches over a liveness-planned device arena.
+//
+// Reuse DAG (Section 3.2): an assignment alpha = (amplitude b, slice s) gives a
+// value to every fixed label (open legs take the pattern's digits, sliced
+// labels the slice id's digits, Section 2.4).  A tree node's result depends
+// only on the fixed labels under it, so its distinct instances are the
+// distinct restrictions of alpha to those labels - the paper's task naming
+// "<path step> + <indices> + <slice values>" made into integer keys.  Each
+// instance is computed once (reuse on) and read by every alpha that needs it.
+// With reuse off every alpha gets its own copy of every internal node (the
+// no-shared-work baseline of Section 4).
+//
+// Intermediate deletion (Section 4, peak memory): a node's buffer lives from
+// its own launch until its parent's launch has been issued; offsets come from
+// a best-fit allocator simulated in launch order, so the arena size is the
+// peak of live intermediates.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "internal.h"
+#include "kernel_args.h"
+
+namespace jet {
+
+namespace {
+
+enum Base : int32_t { BASE_LEAVES = 0, BASE_ARENA = 1, BASE_BLOB = 2, BASE_AMPS = 3 };
+
+struct View {
+    std::vector<int64_t> labels;   // layout order, slowest first
+    std::vector<int64_t> strides;  // elements
+    std::vector<int64_t> dims;
+    int64_t size = 1;
+};
+
+struct NodeInfo {
+    View view;
+    int64_t n_inst = 0;
+    std::vector<int64_t> inst_off;   // element offset of each instance from its base
+    int32_t base = BASE_ARENA;
+    int64_t buf_off = 0;             // arena byte offset of instance 0 (internal nodes)
+    std::vector<int32_t> ia, ib;     // child instances of each instance (internal nodes)
+};
+
+struct Blob {
+    std::vector<uint8_t> bytes;
+    std::vector<Plan::Patch> patches;
+    size_t reserve(size_t n, size_t align = 16)
+    {
+        size_t off = (bytes.size() + align - 1) / align * align;
+        bytes.resize(off + n, 0);
+        return off;
+    }
+    size_t put_i32(const std::vector<int32_t> &v)
+    {
+        size_t off = reserve(std::max<size_t>(v.size(), 1) * 4);
+        if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), v.size() * 4);
+        return off;
+    }
+    size_t put_ptrs(const std::vector<std::pair<int32_t, int64_t>> &refs)
+    {
+        size_t off = reserve(std::max<size_t>(refs.size(), 1) * 8);
+        for (size_t i = 0; i < refs.size(); ++i) patches.push_back({off + 8 * i, refs[i].first, refs[i].second});
+        return off;
+    }
+    void patch_field(size_t struct_off, size_t field_off, int32_t base, int64_t byte_off)
+    {
+        patches.push_back({struct_off + field_off, base, byte_off});
+    }
+};
+
+// Best-fit allocator over a linear arena, 256-byte granules.
+struct Arena {
+    std::map<size_t, size_t> free_;   // offset -> size
+    size_t top = 0, peak = 0;
+    static size_t round(size_t b) { return (b + 255) / 256 * 256; }
+    size_t alloc(size_t bytes)
+    {
+        bytes = round(std::max<size_t>(bytes, 1));
+        auto best = free_.end();
+        for (auto it = free_.begin(); it != free_.end(); ++it)
+            if (it->second >= bytes && (best == free_.end() || it->second < best->second)) best = it;
+        if (best != free_.end()) {
+            size_t off = best->first, sz = best->second;
+            free_.erase(best);
+            if (sz > bytes) free_[off + bytes] = sz - bytes;
+            return off;
+        }
+        size_t off = top;
+        top += bytes;
+        peak = std::max(peak, top);
+        return off;
+    }
+    void release(size_t off, size_t bytes)
+    {
+        bytes = round(std::max<size_t>(bytes, 1));
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+                it = pv;
+            }
+        }
+        if (it->first + it->second == top) {
+            top = it->first;
+            free_.erase(it);
+        }
+    }
+};
+
+int64_t prod(const std::vector<int64_t> &d, size_t from = 0, size_t to = SIZE_MAX)
+{
+    int64_t p = 1;
+    for (size_t i = from; i < std::min(to, d.size()); ++i) p *= d[i];
+    return p;
+}
+
+View dense_view(const std::vector<int64_t> &labels, const Network &net)
+{
+    View v;
+    v.labels = labels;
+    for (int64_t l : labels) v.dims.push_back(net.labels.at(l).dim);
+    v.strides.assign(labels.size(), 1);
+    for (int i = (int)labels.size() - 2; i >= 0; --i) v.strides[i] = v.strides[i + 1] * v.dims[i + 1];
+    v.size = prod(v.dims);
+    return v;
+}
+
+int find_pos(const std::vector<int64_t> &v, int64_t x)
+{
+    auto it = std::find(v.begin(), v.end(), x);
+    return it == v.end() ? -1 : (int)(it - v.begin());
+}
+
+}  // namespace
+
+std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs)
+{
+    if (net.path.size() + 1 != net.leaves.size()) fail(JET_ESTATE, "no contraction path set");
+    if (!net.open_set) fail(JET_ESTATE, "open legs not declared (jet_network_set_open)");
+    if (n_amps < 1) fail(JET_EINVAL, "n_amps must be >= 1");
+    const int32_t n_open = (int32_t)net.open.size();
+    for (int32_t b = 0; b < n_amps; ++b)
+        for (int32_t j = 0; j < n_open; ++j) {
+            int32_t v = outputs[(int64_t)b * n_open + j];
+            if (v < 0 || v >= net.labels.at(net.open[j]).dim)
+                fail(JET_EINVAL, "output digit out of range at amplitude " + std::to_string(b));
+        }
+
+    auto plan = std::make_unique<Plan>();
+    Plan &P = *plan;
+    P.outputs.assign(outputs, outputs + (int64_t)n_amps * n_open);
+    P.n_amps = n_amps;
+    P.path_version = net.path_version;
+    P.slice_version = net.slice_version;
+    P.precision = net.opt.precision;
+    P.reuse = net.opt.reuse;
+    const bool fp64 = net.opt.precision == JET_PREC_FP64;
+    const int64_t es = fp64 ? 16 : 8;
+
+    // ---- fixed labels and their values under an assignment alpha = b * n_sl + s
+    std::unordered_map<int64_t, int32_t> open_pos, slice_pos;
+    for (int32_t j = 0; j < n_open; ++j) open_pos[net.open[j]] = j;
+    std::vector<int64_t> sl_dim, sl_w;
+    for (size_t j = 0; j < net.sliced.size(); ++j) {
+        slice_pos[net.sliced[j]] = (int32_t)j;
+        sl_dim.push_back(net.labels.at(net.sliced[j]).dim);
+    }
+    sl_w.assign(sl_dim.size(), 1);
+    for (int j = (int)sl_dim.size() - 2; j >= 0; --j) sl_w[j] = sl_w[j + 1] * sl_dim[j + 1];
+    const int64_t n_sl = prod(sl_dim);
+    P.n_slices = n_sl;
+    const int64_t n_assign = (int64_t)n_amps * n_sl;
+    if (n_assign > (int64_t)1 << 30) fail(JET_EINVAL, "too many (amplitude, slice) assignments");
+    auto value = [&](int64_t l, int64_t alpha) -> int64_t {
+        auto o = open_pos.find(l);
+        int64_t b = alpha / n_sl, s = alpha % n_sl;
+        if (o != open_pos.end()) return outputs[b * n_open + o->second];
+        int32_t j = slice_pos.at(l);
+        return (s / sl_w[j]) % sl_dim[j];
+    };
+    auto is_fixed = [&](int64_t l) { return open_pos.count(l) || slice_pos.count(l); };
+
+    const int32_t n_leaves = (int32_t)net.leaves.size();
+    const int32_t n_nodes = 2 * n_leaves - 1;
+    std::vector<NodeInfo> node(n_nodes);
+    std::vector<std::vector<int32_t>> inst_of(n_nodes);   // per node: instance id for each alpha
+
+    // ---- leaves: strided views with the fixed labels removed
+    for (int32_t i = 0; i < n_leaves; ++i) {
+        const Leaf &L = net.leaves[i];
+        NodeInfo &N = node[i];
+        N.base = BASE_LEAVES;
+        std::vector<int64_t> full_stride(L.labels.size(), 1);
+        for (int k = (int)L.labels.size() - 2; k >= 0; --k) full_stride[k] = full_stride[k + 1] * L.dims[k + 1];
+        std::vector<int64_t> fx, fx_stride, fx_dim;
+        for (size_t k = 0; k < L.labels.size(); ++k) {
+            if (is_fixed(L.labels[k])) {
+                fx.push_back(L.labels[k]);
+                fx_stride.push_back(full_stride[k]);
+                fx_dim.push_back(L.dims[k]);
+            } else {
+                N.view.labels.push_back(L.labels[k]);
+                N.view.strides.push_back(full_stride[k]);
+                N.view.dims.push_back(L.dims[k]);
+            }
+        }
+        N.view.size = prod(N.view.dims);
+        auto &ids = inst_of[i];
+        ids.resize(n_assign);
+        if (fx.empty()) {
+            N.n_inst = 1;
+            N.inst_off.push_back(L.offset);
+            std::fill(ids.begin(), ids.end(), 0);
+        } else {
+            std::unordered_map<int64_t, int32_t> key2id;
+            for (int64_t a = 0; a < n_assign; ++a) {
+                int64_t key = 0, off = 0;
+                for (size_t k = 0; k < fx.size(); ++k) {
+                    int64_t v = value(fx[k], a);
+                    key = key * fx_dim[k] + v;
+                    off += v * fx_stride[k];
+                }
+                auto it = key2id.find(key);
+                if (it == key2id.end()) {
+                    it = key2id.emplace(key, (int32_t)N.inst_off.size()).first;
+                    N.inst_off.push_back(L.offset + off);
+                }
+                ids[a] = it->second;
+            }
+            N.n_inst = (int64_t)N.inst_off.size();
+        }
+    }
+
+    // ---- internal nodes: instances, layouts, routing
+    Arena arena;
+    Blob blob;
+    const bool gemm_ok = gemm_available(net.opt.precision);
+    int64_t max_inter = 0;
+
+    auto base_ref = [&](int32_t id, int32_t inst) -> std::pair<int32_t, int64_t> {
+        const NodeInfo &N = node[id];
+        if (N.base == BASE_LEAVES) return {BASE_LEAVES, N.inst_off[inst] * es};
+        return {BASE_ARENA, N.buf_off + (int64_t)inst * N.view.size * es};
+    };
+
+    for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
+        const int32_t a = net.path[k].first, b = net.path[k].second, v = n_leaves + k;
+        NodeInfo &N = node[v];
+        // instances
+        auto &ids = inst_of[v];
+        ids.resize(n_assign);
+        const NodeInfo &NA = node[a], &NB = node[b];
+        if (!P.reuse) {
+            for (int64_t x = 0; x < n_assign; ++x) {
+                ids[x] = (int32_t)x;
+                N.ia.push_back(inst_of[a][x]);
+                N.ib.push_back(inst_of[b][x]);
+            }
+        } else if (NA.n_inst == 1 && NB.n_inst == 1) {
+            std::fill(ids.begin(), ids.end(), 0);
+            N.ia.push_back(0);
+            N.ib.push_back(0);
+        } else {
+            std::unordered_map<int64_t, int32_t> key2id;
+            for (int64_t x = 0; x < n_assign; ++x) {
+                int64_t key = (int64_t)inst_of[a][x] * NB.n_inst + inst_of[b][x];
+                auto it = key2id.find(key);
+                if (it == key2id.end()) {
+                    it = key2id.emplace(key, (int32_t)N.ia.size()).first;
+                    N.ia.push_back(inst_of[a][x]);
+                    N.ib.push_back(inst_of[b][x]);
+                }
+                ids[x] = it->second;
+            }
+        }
+        N.n_inst = (int64_t)N.ia.size();
+        std::vector<int32_t>().swap(inst_of[a]);
+        std::vector<int32_t>().swap(inst_of[b]);
+
+        // label classes
+        const View &VA = NA.view, &VB = NB.view;
+        std::vector<int64_t> K, fa, fb;
+        for (int64_t l : VA.labels) (find_pos(VB.labels, l) >= 0 ? K : fa).push_back(l);
+        for (int64_t l : VB.labels)
+            if (find_pos(VA.labels, l) < 0) fb.push_back(l);
+        auto dimprod = [&](const std::vector<int64_t> &ls) {
+            int64_t p = 1;
+            for (int64_t l : ls) p *= net.labels.at(l).dim;
+            return p;
+        };
+        const int64_t nK = dimprod(K), nFa = dimprod(fa), nFb = dimprod(fb);
+        const bool use_gemm = gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64;
+
+        // output layout
+        std::vector<int64_t> out;
+        bool a_big = VA.size >= VB.size;
+        const View &VBig = a_big ? VA : VB;
+        const View &VSmall = a_big ? VB : VA;
+        const std::vector<int64_t> &fbig = a_big ? fa : fb, &fsmall = a_big ? fb : fa;
+        if (!use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size) {
+            // keep the big operand's order; the small operand's free labels take
+            // the place of the first summed label (gate application in place)
+            int ins = -1;
+            for (size_t i = 0; i < VBig.labels.size(); ++i)
+                if (find_pos(K, VBig.labels[i]) >= 0) { ins = (int)i; break; }
+            for (size_t i = 0; i < VBig.labels.size(); ++i) {
+                if ((int)i == ins) out.insert(out.end(), fsmall.begin(), fsmall.end());
+                if (find_pos(K, VBig.labels[i]) < 0) out.push_back(VBig.labels[i]);
+            }
+            if (ins < 0) out.insert(out.begin(), fsmall.begin(), fsmall.end());
+        } else if (use_gemm) {
+            bool a_is_m = nFa >= nFb;
+            out = a_is_m ? fa : fb;
+            const auto &other = a_is_m ? fb : fa;
+            out.insert(out.end(), other.begin(), other.end());
+        } else {
+            out = fbig;
+            out.insert(out.end(), fsmall.begin(), fsmall.end());
+        }
+        N.view = dense_view(out, net);
+        max_inter = std::max(max_inter, N.view.size);
+
+        // arena buffer for all instances
+        size_t nbytes = (size_t)N.n_inst * N.view.size * es;
+        N.buf_off = (int64_t)arena.alloc(nbytes);
+        N.base = BASE_ARENA;
+
+        // per-instance pointer tables
+        std::vector<std::pair<int32_t, int64_t>> pa, pb, pc;
+        for (int64_t i = 0; i < N.n_inst; ++i) {
+            pa.push_back(base_ref(a, N.ia[i]));
+            pb.push_back(base_ref(b, N.ib[i]));
+            pc.push_back({BASE_ARENA, N.buf_off + i * N.view.size * es});
+        }
+        std::vector<int64_t> un = VA.labels;
+        for (int64_t l : fb) un.push_back(l);
+        const double flop = 8.0 * (double)dimprod(un) * (double)N.n_inst;
+        const double bytes = (double)es * (double)N.n_inst * (double)(VA.size + VB.size + N.view.size);
+        P.flop_executed += flop;
+        P.bytes_executed += bytes;
+        P.n_instances += N.n_inst;
+
+        std::vector<size_t> scratch;   // arena scratch freed after this node
+        std::vector<size_t> scratch_bytes;
+
+        // ------------------------------------------------ direct contraction
+        {
+            (void)use_gemm;
+            ++P.n_direct;
+            const View &VX = a_big ? VA : VB;   // operand whose strides order the summed labels
+            auto strideA = [&](int64_t l) { int p = find_pos(VA.labels, l); return p < 0 ? 0 : VA.strides[p]; };
+            auto strideB = [&](int64_t l) { int p = find_pos(VB.labels, l); return p < 0 ? 0 : VB.strides[p]; };
+            DirectArgs d;
+            std::memset(&d, 0, sizeof d);
+            // output split: cols = longest suffix with product <= JET_COLMAX
+            const auto &C = N.view;
+            size_t ncol_labels = 0;
+            int64_t ncols = 1;
+            while (ncol_labels < C.labels.size() &&
+                   ncols * C.dims[C.labels.size() - 1 - ncol_labels] <= JET_COLMAX) {
+                ncols *= C.dims[C.labels.size() - 1 - ncol_labels];
+                ++ncol_labels;
+            }
+            size_t nrow_labels = C.labels.size() - ncol_labels;
+            if (nrow_labels > JET_MAXR) fail(JET_EINVAL, "intermediate rank too large");
+            std::vector<int32_t> colA(ncols), colB(ncols);
+            for (int64_t c = 0; c < ncols; ++c) {
+                int64_t r = c, oa = 0, ob = 0;
+                for (size_t j = 0; j < ncol_labels; ++j) {
+                    size_t li = C.labels.size() - 1 - j;
+                    int64_t dg = r % C.dims[li];
+                    r /= C.dims[li];
+                    oa += dg * strideA(C.labels[li]);
+                    ob += dg * strideB(C.labels[li]);
+                }
+                if (oa > INT32_MAX || ob > INT32_MAX) fail(JET_EINVAL, "column offset overflow");
+                colA[c] = (int32_t)oa;
+                colB[c] = (int32_t)ob;
+            }
+            d.n_cols = (int32_t)ncols;
+            d.n_rows = prod(C.dims, 0, nrow_labels);
+            d.row_rank = (int32_t)nrow_labels;
+            for (size_t j = 0; j < nrow_labels; ++j) {
+                size_t li = nrow_labels - 1 - j;
+                d.row_dim[j] = C.dims[li];
+                d.row_sA[j] = strideA(C.labels[li]);
+                d.row_sB[j] = strideB(C.labels[li]);
+            }
+            // summed labels: slowest first by stride in the larger operand
+            std::vector<int64_t> Ks = K;
+            std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) {
+                int px = find_pos(VX.labels, x), py = find_pos(VX.labels, y);
+                return VX.strides[px] > VX.strides[py];
+            });
+            std::vector<int64_t> Kd;
+            for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
+            size_t nklo_labels = 0;
+            int64_t nklo = 1;
+            while (nklo_labels < Ks.size() && nklo * Kd[Ks.size() - 1 - nklo_labels] <= JET_KLOMAX) {
+                nklo *= Kd[Ks.size() - 1 - nklo_labels];
+                ++nklo_labels;
+            }
+            size_t nkhi_labels = Ks.size() - nklo_labels;
+            if (nkhi_labels > JET_MAXR) fail(JET_EINVAL, "summed rank too large");
+            std::vector<int32_t> kA(nklo), kB(nklo);
+            for (int64_t q = 0; q < nklo; ++q) {
+                int64_t r = q, oa = 0, ob = 0;
+                for (size_t j = 0; j < nklo_labels; ++j) {
+                    size_t li = Ks.size() - 1 - j;
+                    int64_t dg = r % Kd[li];
+                    r /= Kd[li];
+                    oa += dg * strideA(Ks[li]);
+                    ob += dg * strideB(Ks[li]);
+                }
+                if (oa > INT32_MAX || ob > INT32_MAX) fail(JET_EINVAL, "summed offset overflow");
+                kA[q] = (int32_t)oa;
+                kB[q] = (int32_t)ob;
+            }
+            d.n_klo = (int32_t)nklo;
+            d.khi_rank = (int32_t)nkhi_labels;
+            d.n_khi = 1;
+            for (size_t j = 0; j < nkhi_labels; ++j) {
+                size_t li = nkhi_labels - 1 - j;
+                d.khi_dim[j] = Kd[li];
+                d.khi_sA[j] = strideA(Ks[li]);
+                d.khi_sB[j] = strideB(Ks[li]);
+                d.n_khi *= Kd[li];
+            }
+            d.n_out = d.n_rows * d.n_cols;
+            d.n_inst = (int32_t)N.n_inst;
+            // split the summed index across blocks when there are few outputs
+            const int64_t total_out = d.n_out * N.n_inst;
+            const int64_t n_k = d.n_khi * d.n_klo;
+            d.ksplit = 1;
+            if (total_out < 16384 && n_k >= 4096 && d.n_khi > 1) {
+                int64_t groups = (d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G * N.n_inst;
+                int64_t want = std::max<int64_t>(1, (148 * 8 + groups - 1) / groups);
+                int64_t parts = std::min<int64_t>(want, d.n_khi);
+                d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
+                d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
+            }
+            size_t off_colA = blob.put_i32(colA), off_colB = blob.put_i32(colB);
+            size_t off_kA = blob.put_i32(kA), off_kB = blob.put_i32(kB);
+            size_t off_pa = blob.put_ptrs(pa), off_pb = blob.put_ptrs(pb), off_pc = blob.put_ptrs(pc);
+            size_t part_off = 0, part_bytes = 0;
+            if (d.ksplit > 1) {
+                part_bytes = (size_t)N.n_inst * d.ksplit * d.n_out * es;
+                part_off = arena.alloc(part_bytes);
+                scratch.push_back(part_off);
+                scratch_bytes.push_back(part_bytes);
+            }
+            size_t so = blob.reserve(sizeof(DirectArgs));
+            std::memcpy(blob.bytes.data() + so, &d, sizeof d);
+            blob.patch_field(so, offsetof(DirectArgs, ptrA), BASE_BLOB, (int64_t)off_pa);
+            blob.patch_field(so, offsetof(DirectArgs, ptrB), BASE_BLOB, (int64_t)off_pb);
+            blob.patch_field(so, offsetof(DirectArgs, ptrC), BASE_BLOB, (int64_t)off_pc);
+            blob.patch_field(so, offsetof(DirectArgs, colA), BASE_BLOB, (int64_t)off_colA);
+            blob.patch_field(so, offsetof(DirectArgs, colB), BASE_BLOB, (int64_t)off_colB);
+            blob.patch_field(so, offsetof(DirectArgs, kA), BASE_BLOB, (int64_t)off_kA);
+            blob.patch_field(so, offsetof(DirectArgs, kB), BASE_BLOB, (int64_t)off_kB);
+            if (d.ksplit > 1) blob.patch_field(so, offsetof(DirectArgs, partials), BASE_ARENA, (int64_t)part_off);
+            Op op;
+            op.kind = OpKind::Direct;
+            op.node = v;
+            op.n_inst = N.n_inst;
+            op.args_off = so;
+            op.args_bytes = sizeof(DirectArgs);
+            op.flop = flop;
+            op.bytes = bytes;
+            op.variant = fp64 ? 1 : 0;
+            bool pow2 = true;
+            for (int j = 0; j < d.row_rank; ++j) pow2 = pow2 && (d.row_dim[j] & (d.row_dim[j] - 1)) == 0;
+            for (int j = 0; j < d.khi_rank; ++j) pow2 = pow2 && (d.khi_dim[j] & (d.khi_dim[j] - 1)) == 0;
+            if (pow2) op.variant |= 4;
+            op.block = 256;
+            if (d.ksplit > 1) {
+                op.grid_x = d.ksplit;
+                op.grid_y = (int32_t)((d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G);
+                op.grid_z = (int32_t)std::min<int64_t>(N.n_inst, 65535);
+                op.variant |= 2;
+            } else {
+                int64_t blocks = (d.n_out + 255) / 256;
+                int64_t gy = std::min<int64_t>(N.n_inst, 65535);
+                int64_t gx = std::min<int64_t>(blocks, std::max<int64_t>(1, 148 * 16 / std::max<int64_t>(1, gy)));
+                op.grid_x = (int32_t)std::max<int64_t>(gx, 1);
+                op.grid_y = (int32_t)gy;
+            }
+            op.smem = (int32_t)(8 * ncols + 8 * nklo);
+            P.ops.push_back(op);
+            if (d.ksplit > 1) {
+                SplitKReduceArgs r;
+                std::memset(&r, 0, sizeof r);
+                r.n_out = d.n_out;
+                r.n_inst = d.n_inst;
+                r.ksplit = d.ksplit;
+                size_t ro = blob.reserve(sizeof r);
+                std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
+                blob.patch_field(ro, offsetof(SplitKReduceArgs, partials), BASE_ARENA, (int64_t)part_off);
+                blob.patch_field(ro, offsetof(SplitKReduceArgs, ptrC), BASE_BLOB, (int64_t)off_pc);
+                Op rop;
+                rop.kind = OpKind::SplitKReduce;
+                rop.node = v;
+                rop.n_inst = N.n_inst;
+                rop.args_off = ro;
+                rop.args_bytes = sizeof r;
+                rop.variant = fp64 ? 1 : 0;
+                int64_t tot = d.n_out * N.n_inst;
+                rop.grid_x = (int32_t)std::min<int64_t>((tot + 255) / 256, 65535);
+                P.ops.push_back(rop);
+            }
+        }
+
+        for (size_t s = 0; s < scratch.size(); ++s) arena.release(scratch[s], scratch_bytes[s]);
+        // children are dead once this node's launches are issued
+        for (int32_t c : {a, b})
+            if (node[c].base == BASE_ARENA)
+                arena.release((size_t)node[c].buf_off, (size_t)node[c].n_inst * node[c].view.size * es);
+    }
+
+    // ---- slice / amplitude reduction (Eq. sliced_sum), FP64, slices in increasing order
+    const int32_t root = n_nodes - 1;
+    if (!node[root].view.labels.empty()) fail(JET_EINVAL, "the network has undeclared open legs");
+    {
+        std::vector<std::pair<int32_t, int64_t>> roots;
+        roots.reserve(n_assign);
+        for (int64_t x = 0; x < n_assign; ++x) roots.push_back(base_ref(root, inst_of[root][x]));
+        size_t off_roots = blob.put_ptrs(roots);
+        ReduceArgs r;
+        std::memset(&r, 0, sizeof r);
+        r.n_amps = n_amps;
+        r.n_slices = (int32_t)n_sl;
+        r.fp64_in = fp64 ? 1 : 0;
+        size_t ro = blob.reserve(sizeof r);
+        std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
+        blob.patch_field(ro, offsetof(ReduceArgs, roots), BASE_BLOB, (int64_t)off_roots);
+        blob.patch_field(ro, offsetof(ReduceArgs, amps), BASE_AMPS, 0);
+        Op op;
+        op.kind = OpKind::Reduce;
+        op.node = root;
+        op.n_inst = n_amps;
+        op.args_off = ro;
+        op.args_bytes = sizeof r;
+        op.grid_x = (n_amps + 127) / 128;
+        op.block = 128;
+        P.ops.push_back(op);
+    }
+
+    P.arena_bytes = std::max<size_t>(arena.peak, 256);
+    P.host_args = std::move(blob.bytes);
+    P.patches = std::move(blob.patches);
+    P.max_intermediate = max_inter;
+    return plan;
+}
+
+}  // namespace jet

@@ -1,0 +1,319 @@
+// Host-side planner: contraction tree, FLOP/size model, greedy path, slice finder.
+//
+// Section 2.3: a pairwise path is a binary contraction tree; each step sums the
+// labels its two operands share.  Section 2.4 (Eq. sliced_flops): slicing
+// fixes labels, shrinking every intermediate that carries them and multiplying
+// the work by the number of slices.  Section 3.2 (Eq. task_based_amplitude_flops):
+// with shared work reused, a tree node is computed once per distinct assignment
+// of the sliced labels that occur under it, not once per slice.
+#include <algorithm>
+#include <cmath>
+#include <set>
+#include <unordered_set>
+
+#include "internal.h"
+
+namespace jet {
+
+static double label_size(const Network &net, const std::vector<int64_t> &ls,
+                         const std::unordered_set<int64_t> &fixed)
+{
+    double s = 1;
+    for (int64_t l : ls)
+        if (!fixed.count(l)) s *= (double)net.labels.at(l).dim;
+    return s;
+}
+
+// labels of a contraction result: symmetric difference, a's order then b's
+static std::vector<int64_t> sym_diff(const std::vector<int64_t> &a, const std::vector<int64_t> &b)
+{
+    std::vector<int64_t> out;
+    out.reserve(a.size() + b.size());
+    for (int64_t x : a)
+        if (std::find(b.begin(), b.end(), x) == b.end()) out.push_back(x);
+    for (int64_t x : b)
+        if (std::find(a.begin(), a.end(), x) == a.end()) out.push_back(x);
+    return out;
+}
+
+static std::vector<int64_t> set_union(const std::vector<int64_t> &a, const std::vector<int64_t> &b)
+{
+    std::vector<int64_t> out = a;
+    for (int64_t x : b)
+        if (std::find(a.begin(), a.end(), x) == a.end()) out.push_back(x);
+    return out;
+}
+
+void validate_path(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path)
+{
+    int32_t n = (int32_t)net.leaves.size();
+    if ((int32_t)path.size() != n - 1)
+        fail(JET_EINVAL, "path must have n_tensors - 1 = " + std::to_string(n - 1) + " steps, got " +
+                             std::to_string(path.size()));
+    std::vector<char> used(2 * n, 0);
+    for (int32_t k = 0; k < (int32_t)path.size(); ++k) {
+        int32_t a = path[k].first, b = path[k].second;
+        int32_t limit = n + k;  // ids < n + k exist before step k
+        if (a < 0 || b < 0 || a >= limit || b >= limit || a == b)
+            fail(JET_EINVAL, "path step " + std::to_string(k) + ": invalid ids (" + std::to_string(a) +
+                                 ", " + std::to_string(b) + ")");
+        if (used[a] || used[b])
+            fail(JET_EINVAL, "path step " + std::to_string(k) + ": an id is consumed twice");
+        used[a] = used[b] = 1;
+    }
+}
+
+Tree build_tree(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path)
+{
+    Tree t;
+    t.n_leaves = (int32_t)net.leaves.size();
+    t.children = path;
+    t.labels.resize(t.n_leaves + path.size());
+    for (int32_t i = 0; i < t.n_leaves; ++i) t.labels[i] = net.leaves[i].labels;
+    for (size_t k = 0; k < path.size(); ++k)
+        t.labels[t.n_leaves + k] = sym_diff(t.labels[path[k].first], t.labels[path[k].second]);
+    return t;
+}
+
+static std::unordered_set<int64_t> fixed_set(const Network &net, const std::vector<int64_t> &extra)
+{
+    std::unordered_set<int64_t> f(extra.begin(), extra.end());
+    for (auto &kv : net.labels)
+        if (kv.second.n_owner == 1) f.insert(kv.first);  // open legs: fixed by every amplitude
+    return f;
+}
+
+PathCost path_cost(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
+                   const std::vector<int64_t> &fixed_extra)
+{
+    auto fixed = fixed_set(net, fixed_extra);
+    Tree t = build_tree(net, path);
+    PathCost c;
+    c.node_size.resize(t.labels.size());
+    for (size_t i = 0; i < t.labels.size(); ++i) c.node_size[i] = label_size(net, t.labels[i], fixed);
+    for (size_t k = 0; k < path.size(); ++k) {
+        auto u = set_union(t.labels[path[k].first], t.labels[path[k].second]);
+        double f = 8.0 * label_size(net, u, fixed);
+        c.step_flop.push_back(f);
+        c.flop += f;
+        c.max_size = std::max(c.max_size, c.node_size[t.n_leaves + k]);
+    }
+    return c;
+}
+
+// Sum over tree nodes of (number of distinct sliced-label assignments under the
+// node) x (node FLOP with the sliced labels fixed): Eq. task_based_amplitude_flops
+// counted exactly, node by node.
+double reuse_aware_flop(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
+                        const std::vector<int64_t> &sliced)
+{
+    auto fixed = fixed_set(net, sliced);
+    std::unordered_set<int64_t> sl(sliced.begin(), sliced.end());
+    Tree t = build_tree(net, path);
+    int32_t n = t.n_leaves;
+    std::vector<std::vector<int64_t>> under(t.labels.size());  // sliced labels under each node
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t l : net.leaves[i].labels)
+            if (sl.count(l)) under[i].push_back(l);
+    double total = 0;
+    for (size_t k = 0; k < path.size(); ++k) {
+        int32_t a = path[k].first, b = path[k].second;
+        auto u = set_union(under[a], under[b]);
+        double inst = 1;
+        for (int64_t l : u) inst *= net.labels.at(l).dim;
+        under[n + k] = u;
+        auto un = set_union(t.labels[a], t.labels[b]);
+        total += inst * 8.0 * label_size(net, un, fixed);
+    }
+    return total;
+}
+
+// ------------------------------------------------------------ greedy path
+namespace {
+struct Cand {
+    double score, flop;
+    int32_t a, b;
+    bool operator<(const Cand &o) const
+    {
+        if (score != o.score) return score < o.score;
+        if (flop != o.flop) return flop < o.flop;
+        if (a != o.a) return a < o.a;
+        return b < o.b;
+    }
+};
+
+struct SplitMix {
+    uint64_t s;
+    uint64_t next()
+    {
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    double uniform() { return (next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+}  // namespace
+
+static std::vector<std::pair<int32_t, int32_t>> greedy_once(const Network &net, SplitMix *rng,
+                                                            double temperature, double *flop_out)
+{
+    auto fixed = fixed_set(net, {});
+    int32_t n = (int32_t)net.leaves.size();
+    std::vector<std::vector<int64_t>> lab(2 * n);
+    std::vector<double> size(2 * n, 0);
+    std::vector<char> alive(2 * n, 0);
+    std::unordered_map<int64_t, std::vector<int32_t>> owner;
+    for (int32_t i = 0; i < n; ++i) {
+        lab[i] = net.leaves[i].labels;
+        size[i] = label_size(net, lab[i], fixed);
+        alive[i] = 1;
+        for (int64_t l : lab[i]) owner[l].push_back(i);
+    }
+    std::set<Cand> cands;
+    std::map<std::pair<int32_t, int32_t>, Cand> by_pair;
+    auto add_pair = [&](int32_t a, int32_t b) {
+        if (a > b) std::swap(a, b);
+        if (by_pair.count({a, b})) return;
+        auto out = sym_diff(lab[a], lab[b]);
+        auto un = set_union(lab[a], lab[b]);
+        double so = label_size(net, out, fixed);
+        double score = so - size[a] - size[b];
+        if (rng) {
+            double g = -std::log(-std::log(std::max(rng->uniform(), 1e-300)));
+            double ls = (score >= 0 ? 1 : -1) * std::log2(1 + std::fabs(score));
+            score = ls - temperature * g;
+        }
+        Cand c{score, 8.0 * label_size(net, un, fixed), a, b};
+        cands.insert(c);
+        by_pair[{a, b}] = c;
+    };
+    auto drop_node = [&](int32_t x) {
+        for (int64_t l : lab[x])
+            for (int32_t y : owner[l]) {
+                if (y == x) continue;
+                auto key = std::make_pair(std::min(x, y), std::max(x, y));
+                auto it = by_pair.find(key);
+                if (it != by_pair.end()) {
+                    cands.erase(it->second);
+                    by_pair.erase(it);
+                }
+            }
+    };
+    for (auto &kv : owner)
+        if (kv.second.size() == 2) add_pair(kv.second[0], kv.second[1]);
+
+    std::vector<std::pair<int32_t, int32_t>> path;
+    double total = 0;
+    int32_t next = n;
+    int32_t n_alive = n;
+    while (n_alive > 1) {
+        int32_t a, b;
+        if (!cands.empty()) {
+            Cand c = *cands.begin();
+            a = c.a;
+            b = c.b;
+        } else {  // disconnected: join the two smallest
+            std::vector<int32_t> ids;
+            for (int32_t i = 0; i < next; ++i)
+                if (alive[i]) ids.push_back(i);
+            std::sort(ids.begin(), ids.end(), [&](int32_t x, int32_t y) {
+                return size[x] != size[y] ? size[x] < size[y] : x < y;
+            });
+            a = std::min(ids[0], ids[1]);
+            b = std::max(ids[0], ids[1]);
+        }
+        drop_node(a);
+        drop_node(b);
+        int32_t c = next++;
+        lab[c] = sym_diff(lab[a], lab[b]);
+        size[c] = label_size(net, lab[c], fixed);
+        total += 8.0 * label_size(net, set_union(lab[a], lab[b]), fixed);
+        alive[a] = alive[b] = 0;
+        alive[c] = 1;
+        --n_alive;
+        for (int64_t l : lab[a]) {
+            auto &o = owner[l];
+            o.erase(std::remove(o.begin(), o.end(), a), o.end());
+        }
+        for (int64_t l : lab[b]) {
+            auto &o = owner[l];
+            o.erase(std::remove(o.begin(), o.end(), b), o.end());
+        }
+        for (int64_t l : lab[c]) owner[l].push_back(c);
+        for (int64_t l : lab[c])
+            for (int32_t y : owner[l])
+                if (y != c) add_pair(c, y);
+        path.push_back({a, b});
+    }
+    if (flop_out) *flop_out = total;
+    return path;
+}
+
+std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_t seed,
+                                                     int32_t n_trials, double *flop_out)
+{
+    if (net.leaves.size() == 1) {
+        if (flop_out) *flop_out = 0;
+        return {};
+    }
+    double best_flop = 0;
+    auto best = greedy_once(net, nullptr, 0, &best_flop);
+    SplitMix rng{seed};
+    for (int32_t t = 1; t < n_trials; ++t) {
+        double f;
+        double temp = 0.25 + 1.75 * rng.uniform();
+        auto p = greedy_once(net, &rng, temp, &f);
+        if (f < best_flop) {
+            best_flop = f;
+            best = p;
+        }
+    }
+    if (flop_out) *flop_out = best_flop;
+    return best;
+}
+
+// ------------------------------------------------------------ slice finder
+std::vector<int64_t> slice_auto(const Network &net, int64_t max_elems, int32_t min_n, int32_t max_n)
+{
+    std::vector<int64_t> sliced;
+    while (true) {
+        PathCost c = path_cost(net, net.path, sliced);
+        if (c.max_size <= (double)max_elems && (int32_t)sliced.size() >= min_n) return sliced;
+        if ((int32_t)sliced.size() >= max_n)
+            fail(JET_EINVAL, "slice_auto: cap " + std::to_string(max_elems) + " not reachable with " +
+                                 std::to_string(max_n) + " sliced labels");
+        // candidates: closed, unsliced labels of the largest intermediates
+        Tree t = build_tree(net, net.path);
+        std::set<int64_t> cand;
+        for (size_t i = t.n_leaves; i < t.labels.size(); ++i)
+            if (c.node_size[i] >= c.max_size)
+                for (int64_t l : t.labels[i]) {
+                    const LabelInfo &li = net.labels.at(l);
+                    if (li.n_owner == 2 && li.dim > 1 && c.node_size[i] > 1 &&
+                        std::find(sliced.begin(), sliced.end(), l) == sliced.end())
+                        cand.insert(l);
+                }
+        if (cand.empty()) fail(JET_EINVAL, "slice_auto: no sliceable label in the largest intermediate");
+        int64_t best = -1;
+        double best_cost = 0, best_total = 0;
+        for (int64_t l : cand) {
+            auto s2 = sliced;
+            s2.push_back(l);
+            double cost = reuse_aware_flop(net, net.path, s2);
+            PathCost c2 = path_cost(net, net.path, s2);
+            double nsl = 1;
+            for (int64_t x : s2) nsl *= net.labels.at(x).dim;
+            double total = nsl * c2.flop;
+            if (best < 0 || cost < best_cost || (cost == best_cost && total < best_total)) {
+                best = l;
+                best_cost = cost;
+                best_total = total;
+            }
+        }
+        sliced.push_back(best);
+    }
+}
+
+}  // namespace jet

@@ -1,0 +1,237 @@
+"""ctypes binding of libjet.so (the C ABI in include/jet.h).
+
+Argument marshalling only: every step of the contraction runs in the library's
+CUDA kernels.  There is no fallback: if the shared library is missing or a call
+fails, a JetError is raised.
+"""
+import ctypes
+import os
+from typing import Dict, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libjet.so")
+
+JET_OK, JET_EINVAL, JET_ENOMEM, JET_ECUDA, JET_ETIMEOUT, JET_ESTATE = 0, -1, -2, -3, -4, -5
+PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp64": 5}
+
+EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", "jet_tensor_update",
+           "jet_tensors_upload", "jet_network_n_values", "jet_path_set", "jet_path_get",
+           "jet_path_greedy", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
+           "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
+           "jet_network_destroy", "jet_last_error"]
+
+
+class JetError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"jet error {code}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("reuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("gemm_min_k", ctypes.c_int64), ("workspace_limit", ctypes.c_int64)]
+
+
+class TensorDesc(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("labels", ctypes.POINTER(ctypes.c_int64)),
+                ("dims", ctypes.POINTER(ctypes.c_int32)), ("data", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("flop_planned", ctypes.c_double), ("flop_sliced", ctypes.c_double),
+                ("flop_executed", ctypes.c_double), ("reuse_fraction", ctypes.c_double),
+                ("bytes_executed", ctypes.c_double), ("max_intermediate", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64), ("n_instances", ctypes.c_int64),
+                ("n_launches", ctypes.c_int64), ("n_slices", ctypes.c_int32),
+                ("n_sliced_labels", ctypes.c_int32), ("n_gemm_nodes", ctypes.c_int32),
+                ("n_direct_nodes", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise JetError(JET_ESTATE, f"{LIB_PATH} not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "jet_options_default": (None, [P]),
+            "jet_network_create": (I32, [P, I32, P, P]),
+            "jet_network_set_open": (I32, [P, I32, P]),
+            "jet_tensor_update": (I32, [P, I32, P]),
+            "jet_tensors_upload": (I32, [P, P, P]),
+            "jet_network_n_values": (I64, [P]),
+            "jet_path_set": (I32, [P, I32, P]),
+            "jet_path_get": (I32, [P, P]),
+            "jet_path_greedy": (I32, [P, ctypes.c_uint64, I32, P]),
+            "jet_slice": (I32, [P, I32, P]),
+            "jet_slice_auto": (I32, [P, I64, I32, I32, P, P]),
+            "jet_contract": (I32, [P, I32, P, P, P]),
+            "jet_contract_async": (I32, [P, I32, P, P, P]),
+            "jet_plan": (I32, [P, I32, P, P]),
+            "jet_set_workspace": (I32, [P, P, ctypes.c_size_t]),
+            "jet_contract_grad": (I32, [P, I32, P, P, I32, P, P, P, P]),
+            "jet_stats": (I32, [P, P]),
+            "jet_network_destroy": (None, [P]),
+            "jet_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != JET_OK:
+        raise JetError(rc, lib().jet_last_error().decode())
+
+
+def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=64) -> Options:
+    o = Options()
+    lib().jet_options_default(ctypes.byref(o))
+    o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    o.reuse = int(bool(reuse))
+    o.use_graph = int(bool(use_graph))
+    o.device = int(device)
+    o.gemm_min_k = int(gemm_min_k)
+    return o
+
+
+class Network:
+    """A tensor network handle (jet_network_create)."""
+
+    def __init__(self, labels: Sequence[Sequence[int]], data: Sequence[np.ndarray], options: Options = None,
+                 **opt_kwargs):
+        L = lib()
+        self._keep = []
+        n = len(data)
+        descs = (TensorDesc * n)()
+        self.shapes = []
+        for i, (lab, t) in enumerate(zip(labels, data)):
+            t = np.ascontiguousarray(np.asarray(t), dtype=np.complex64)
+            la = np.ascontiguousarray(np.asarray(lab, dtype=np.int64))
+            di = np.ascontiguousarray(np.asarray(t.shape, dtype=np.int32))
+            if la.size != t.ndim:
+                raise JetError(JET_EINVAL, f"tensor {i}: {la.size} labels for rank {t.ndim}")
+            self._keep += [t, la, di]
+            descs[i].rank = t.ndim
+            descs[i].labels = la.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+            descs[i].dims = di.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+            descs[i].data = t.ctypes.data
+            self.shapes.append(t.shape)
+        opts = options if options is not None else default_options(**opt_kwargs)
+        h = ctypes.c_void_p()
+        _check(L.jet_network_create(descs, n, ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self._keep = []
+        self.n_tensors = n
+        self.n_out = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().jet_network_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_open(self, out_labels: Sequence[int]):
+        a = np.ascontiguousarray(np.asarray(out_labels, dtype=np.int64))
+        _check(lib().jet_network_set_open(self._h, a.size, a.ctypes.data))
+        self.n_out = a.size
+
+    def update(self, tensor_id: int, data: np.ndarray):
+        t = np.ascontiguousarray(data, dtype=np.complex64)
+        _check(lib().jet_tensor_update(self._h, int(tensor_id), t.ctypes.data))
+
+    def n_values(self) -> int:
+        return int(lib().jet_network_n_values(self._h))
+
+    def upload(self, host_ptr: int, stream: int = 0):
+        _check(lib().jet_tensors_upload(self._h, ctypes.c_void_p(host_ptr), ctypes.c_void_p(stream)))
+
+    def path_set(self, pairs: Sequence[Tuple[int, int]]):
+        a = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        _check(lib().jet_path_set(self._h, a.shape[0], a.ctypes.data))
+
+    def path_get(self) -> List[Tuple[int, int]]:
+        a = np.zeros((max(self.n_tensors - 1, 0), 2), dtype=np.int32)
+        _check(lib().jet_path_get(self._h, a.ctypes.data))
+        return [tuple(map(int, r)) for r in a]
+
+    def path_greedy(self, seed: int = 0, n_trials: int = 1) -> float:
+        f = ctypes.c_double()
+        _check(lib().jet_path_greedy(self._h, ctypes.c_uint64(seed), int(n_trials), ctypes.byref(f)))
+        return f.value
+
+    def slice(self, labels: Sequence[int]):
+        a = np.ascontiguousarray(np.asarray(labels, dtype=np.int64))
+        _check(lib().jet_slice(self._h, a.size, a.ctypes.data))
+
+    def slice_auto(self, max_elems: int, min_n: int = 0, max_n: int = 64) -> List[int]:
+        n = ctypes.c_int32()
+        out = np.zeros(max(max_n, 1), dtype=np.int64)
+        _check(lib().jet_slice_auto(self._h, int(max_elems), int(min_n), int(max_n), ctypes.byref(n),
+                                    out.ctypes.data))
+        return [int(x) for x in out[:n.value]]
+
+    def _outputs(self, outputs) -> np.ndarray:
+        o = np.ascontiguousarray(np.asarray(outputs, dtype=np.int32).reshape(-1, self.n_out))
+        return o
+
+    def plan(self, outputs) -> int:
+        o = self._outputs(outputs)
+        b = ctypes.c_size_t()
+        _check(lib().jet_plan(self._h, o.shape[0], o.ctypes.data, ctypes.byref(b)))
+        return b.value
+
+    def set_workspace(self, dptr: int, nbytes: int):
+        _check(lib().jet_set_workspace(self._h, ctypes.c_void_p(dptr), ctypes.c_size_t(nbytes)))
+
+    def contract(self, outputs, stream: int = 0) -> np.ndarray:
+        o = self._outputs(outputs)
+        amps = np.zeros(o.shape[0], dtype=np.complex128)
+        _check(lib().jet_contract(self._h, o.shape[0], o.ctypes.data, amps.ctypes.data, ctypes.c_void_p(stream)))
+        return amps
+
+    def contract_async(self, outputs, amps_dev_ptr: int, stream: int = 0):
+        o = self._outputs(outputs)
+        _check(lib().jet_contract_async(self._h, o.shape[0], o.ctypes.data, ctypes.c_void_p(amps_dev_ptr),
+                                        ctypes.c_void_p(stream)))
+
+    def contract_grad(self, outputs, cot, tensor_ids: Sequence[int], stream: int = 0):
+        o = self._outputs(outputs)
+        c = np.ascontiguousarray(np.asarray(cot, dtype=np.complex128).reshape(o.shape[0]))
+        ids = np.ascontiguousarray(np.asarray(tensor_ids, dtype=np.int32))
+        envs = [np.zeros(self.shapes[i], dtype=np.complex64) for i in ids]
+        ptrs = (ctypes.c_void_p * max(len(envs), 1))(*[e.ctypes.data for e in envs])
+        amps = np.zeros(o.shape[0], dtype=np.complex128)
+        _check(lib().jet_contract_grad(self._h, o.shape[0], o.ctypes.data, c.ctypes.data, ids.size,
+                                       ids.ctypes.data, ptrs, amps.ctypes.data, ctypes.c_void_p(stream)))
+        return amps, envs
+
+    def stats(self) -> Dict[str, float]:
+        s = Stats()
+        _check(lib().jet_stats(self._h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+def from_network(tn, **opt_kwargs) -> Network:
+    """Build a handle from a circuits.TensorNetwork and declare its open legs."""
+    net = Network(tn.labels, tn.data, **opt_kwargs)
+    net.set_open(tn.open_labels)
+    return net

@@ -1,0 +1,166 @@
+"""Host-side tests of the C ABI: the library loads and exports every declared
+symbol, and the planner's path/slice/reuse bookkeeping matches brute-force
+counts.  No call here touches a GPU (device work is lazy until a contraction)."""
+import os
+import re
+from itertools import product
+
+import numpy as np
+import pytest
+
+from paper_2107_09793_b300 import jet
+from circuits import configs, random_grid_circuit, circuit_to_network
+import oracle
+from oracle.einsum import network_flops
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "jet.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(jet_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = jet.lib()
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def _net(name="grid12", **kw):
+    w = configs.build(name)
+    return w, jet.from_network(w.network, **kw)
+
+
+def test_greedy_path_is_valid_and_flop_model_matches():
+    w, net = _net()
+    f = net.path_greedy(seed=3, n_trials=8)
+    path = net.path_get()
+    tn = w.network
+    n = len(tn.labels)
+    assert len(path) == n - 1
+    seen = set()
+    for k, (a, b) in enumerate(path):
+        assert a < n + k and b < n + k and a != b and a not in seen and b not in seen
+        seen |= {a, b}
+    # the library's FLOP model equals the oracle's independent count with open legs at dim 1
+    dims = {}
+    for l, t in zip(tn.labels, tn.data):
+        for x, s in zip(l, t.shape):
+            dims[x] = 1 if x in tn.open_labels else s
+    assert f == network_flops(tn.labels, dims, path)
+    assert net.stats()["flop_planned"] == f
+
+
+def test_path_set_validation_errors():
+    w, net = _net()
+    n = len(w.network.labels)
+    with pytest.raises(jet.JetError) as e:
+        net.path_set([(0, 1)])
+    assert e.value.code == jet.JET_EINVAL
+    bad = [(0, 1)] + [(0, k) for k in range(2, n)]
+    with pytest.raises(jet.JetError) as e:
+        net.path_set(bad)
+    assert e.value.code == jet.JET_EINVAL
+
+
+def test_contract_before_path_is_state_error():
+    w, net = _net()
+    with pytest.raises(jet.JetError) as e:
+        net.plan(w.outputs)
+    assert e.value.code == jet.JET_ESTATE
+
+
+def test_create_rejects_bad_networks():
+    a = np.ones((2, 2), np.complex64)
+    with pytest.raises(jet.JetError) as e:
+        jet.Network([[0, 0]], [a])             # label repeated in a tensor
+    assert e.value.code == jet.JET_EINVAL
+    with pytest.raises(jet.JetError):
+        jet.Network([[0, 1], [1, 2], [1, 3]], [a, a, a])   # label on three tensors
+    with pytest.raises(jet.JetError):
+        jet.Network([[0, 1], [1, 2]], [a, np.ones((3, 2), np.complex64)])  # dims differ
+    net = jet.Network([[0, 1], [1, 2]], [a, a])
+    with pytest.raises(jet.JetError):
+        net.set_open([0])                      # must list every open leg
+    with pytest.raises(jet.JetError):
+        net.set_open([0, 1])                   # 1 is closed
+    net.set_open([2, 0])
+    net.path_set([(0, 1)])
+    with pytest.raises(jet.JetError) as e:
+        net.plan([[2, 0]])                     # digit out of range
+    assert e.value.code == jet.JET_EINVAL
+    with pytest.raises(jet.JetError):
+        net.slice([0])                         # open legs cannot be sliced
+
+
+def _instances_brute(tn, path, sliced, outputs):
+    """Distinct (node, values of the fixed labels under it) pairs, by enumeration."""
+    fixed = set(sliced) | set(tn.open_labels)
+    dims = {}
+    for l, t in zip(tn.labels, tn.data):
+        for x, s in zip(l, t.shape):
+            dims[x] = s
+    n = len(tn.labels)
+    under = [sorted(set(l) & fixed) for l in tn.labels]
+    labels = [list(l) for l in tn.labels]
+    total_inst, total_flop = 0, 0
+    for k, (a, b) in enumerate(path):
+        u = sorted(set(under[a]) | set(under[b]))
+        under.append(u)
+        keys = set()
+        for o in outputs:
+            for sv in product(*[range(dims[x]) for x in sliced]):
+                val = dict(zip(sliced, sv))
+                val.update(zip(tn.open_labels, o))
+                keys.add(tuple(val[x] for x in u))
+        un = list(dict.fromkeys(labels[a] + labels[b]))
+        labels.append([x for x in labels[a] if x not in labels[b]] + [x for x in labels[b] if x not in labels[a]])
+        f = 8 * int(np.prod([dims[x] for x in un if x not in fixed]))
+        total_inst += len(keys)
+        total_flop += len(keys) * f
+    return total_inst, total_flop
+
+
+def test_reuse_dag_counts_match_brute_force():
+    """Section 3.2: each (node, fixed-label values) instance is computed once."""
+    circ = random_grid_circuit(2, 3, 5, seed=12)
+    tn = circuit_to_network(circ)
+    net = jet.from_network(tn)
+    net.path_greedy(seed=1, n_trials=4)
+    sliced = net.slice_auto(1 << 4, min_n=3, max_n=10)
+    assert len(sliced) >= 3
+    outputs = np.array([[0, 1, 0, 1, 1, 0], [0, 1, 0, 0, 0, 1], [1, 1, 1, 1, 1, 1]], np.int32)
+    net.plan(outputs)
+    st = net.stats()
+    inst, flop = _instances_brute(tn, net.path_get(), sliced, outputs)
+    assert st["n_instances"] == inst
+    assert st["flop_executed"] == flop
+    # no reuse: every (amplitude, slice) recomputes every node
+    net2 = jet.from_network(tn, reuse=False)
+    net2.path_set(net.path_get())
+    net2.slice(sliced)
+    net2.plan(outputs)
+    nsl = 2 ** len(sliced)
+    assert net2.stats()["n_instances"] == (len(tn.labels) - 1) * nsl * len(outputs)
+    assert net2.stats()["flop_executed"] > st["flop_executed"]
+
+
+def test_slice_auto_reaches_cap_and_min_count():
+    w, net = _net("grid30")
+    net.path_greedy(seed=1, n_trials=16)
+    sl = net.slice_auto(1 << 24, min_n=6, max_n=30)
+    st = net.stats()
+    assert st["max_intermediate"] <= 1 << 24
+    assert len(sl) >= 6 and st["n_slices"] == 2 ** len(sl)
+    assert len(set(sl)) == len(sl) and not set(sl) & set(w.network.open_labels)
+
+
+def test_workspace_plan_is_host_only():
+    w, net = _net()
+    net.path_greedy(seed=1, n_trials=2)
+    nbytes = net.plan(w.outputs)
+    assert nbytes >= 256 and nbytes % 256 == 0
