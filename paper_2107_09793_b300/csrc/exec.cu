@@ -110,7 +110,7 @@ void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream)
     JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
 }
 
-bool gemm_available(int32_t) { return false; }
+bool gemm_available(int32_t) { return true; }
 
 void release_plan_device(Plan &plan)
 {
@@ -149,6 +149,18 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
         SplitKReduceArgs a;
         std::memcpy(&a, p, sizeof a);
         e = launch_splitk_reduce(a, c, s);
+        break;
+    }
+    case OpKind::Permute: {
+        PermuteArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_permute(a, c, s);
+        break;
+    }
+    case OpKind::GemmSimt: {
+        GemmArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_gemm_simt(a, c, s);
         break;
     }
     case OpKind::Reduce: {

@@ -19,6 +19,8 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
 cudaError_t set_direct_smem_limits();
 cudaError_t launch_splitk_reduce(const SplitKReduceArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_slice_reduce(const ReduceArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_permute(const PermuteArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_gemm_simt(const GemmArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_c64_to_c128(const void *src, void *dst, int64_t n, cudaStream_t s);
 
 }  // namespace jet

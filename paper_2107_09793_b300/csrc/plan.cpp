@@ -354,9 +354,143 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         std::vector<size_t> scratch;   // arena scratch freed after this node
         std::vector<size_t> scratch_bytes;
 
+        // ------------------------------------------------ GEMM route (Section 3.1)
+        if (use_gemm) {
+            ++P.n_gemm;
+            const bool a_is_m = nFa >= nFb;     // same choice as the output layout above
+            const int32_t idM = a_is_m ? a : b, idN = a_is_m ? b : a;
+            const View &VM = node[idM].view, &VN = node[idN].view;
+            const std::vector<int64_t> &fM = a_is_m ? fa : fb, &fN = a_is_m ? fb : fa;
+            const std::vector<int32_t> &instM = a_is_m ? N.ia : N.ib, &instN = a_is_m ? N.ib : N.ia;
+            auto is_dense = [](const View &V) {
+                int64_t s = 1;
+                for (int i = (int)V.labels.size() - 1; i >= 0; --i) {
+                    if (V.strides[i] != s) return false;
+                    s *= V.dims[i];
+                }
+                return true;
+            };
+            auto cat = [](std::vector<int64_t> x, const std::vector<int64_t> &y) {
+                x.insert(x.end(), y.begin(), y.end());
+                return x;
+            };
+            // summed-label order: take it from an operand that is already [free, K] or [K, free]
+            auto split_order = [&](const View &V, const std::vector<int64_t> &f, bool k_last) {
+                std::vector<int64_t> kap;
+                if (!is_dense(V) || V.labels.size() != f.size() + K.size()) return kap;
+                size_t nf = f.size();
+                std::vector<int64_t> head(V.labels.begin(), V.labels.begin() + (k_last ? nf : K.size()));
+                std::vector<int64_t> tail(V.labels.begin() + (k_last ? nf : K.size()), V.labels.end());
+                if ((k_last ? head : tail) != f) return kap;
+                return k_last ? tail : head;
+            };
+            std::vector<int64_t> kappa = split_order(VM, fM, true);
+            if (kappa.empty()) kappa = split_order(VM, fM, false);
+            if (kappa.empty()) kappa = split_order(VN, fN, true);
+            if (kappa.empty()) kappa = split_order(VN, fN, false);
+            if (kappa.empty())
+                for (int64_t l : VM.labels)
+                    if (find_pos(K, l) >= 0) kappa.push_back(l);
+            auto form = [&](const View &V, const std::vector<int64_t> &f) {
+                if (!is_dense(V)) return -1;
+                if (V.labels == cat(f, kappa)) return 1;   // [free][K]: K-major
+                if (V.labels == cat(kappa, f)) return 0;   // [K][free]
+                return -1;
+            };
+            int formM = form(VM, fM), formN = form(VN, fN);
+            // operands that are neither: gather each child instance into [free, K] once
+            auto permute_child = [&](int32_t id, const View &V, const std::vector<int64_t> &f) {
+                std::vector<int64_t> tgt = cat(f, kappa);
+                const int64_t ninst = node[id].n_inst;
+                const size_t bytes_p = (size_t)ninst * V.size * es;
+                size_t off = arena.alloc(bytes_p);
+                scratch.push_back(off);
+                scratch_bytes.push_back(bytes_p);
+                PermuteArgs pr;
+                std::memset(&pr, 0, sizeof pr);
+                pr.n = V.size;
+                pr.rank = (int32_t)tgt.size();
+                pr.n_inst = (int32_t)ninst;
+                if (pr.rank > JET_MAXR) fail(JET_EINVAL, "permute rank too large");
+                for (int j = 0; j < pr.rank; ++j) {
+                    int64_t l = tgt[tgt.size() - 1 - j];
+                    int p = find_pos(V.labels, l);
+                    pr.dim[j] = V.dims[p];
+                    pr.sstride[j] = V.strides[p];
+                }
+                std::vector<std::pair<int32_t, int64_t>> ps, pd;
+                for (int64_t j = 0; j < ninst; ++j) {
+                    ps.push_back(base_ref(id, (int32_t)j));
+                    pd.push_back({BASE_ARENA, (int64_t)off + j * V.size * es});
+                }
+                size_t o_ps = blob.put_ptrs(ps), o_pd = blob.put_ptrs(pd);
+                size_t so = blob.reserve(sizeof pr);
+                std::memcpy(blob.bytes.data() + so, &pr, sizeof pr);
+                blob.patch_field(so, offsetof(PermuteArgs, ptrSrc), BASE_BLOB, (int64_t)o_ps);
+                blob.patch_field(so, offsetof(PermuteArgs, ptrDst), BASE_BLOB, (int64_t)o_pd);
+                Op op;
+                op.kind = OpKind::Permute;
+                op.node = v;
+                op.n_inst = ninst;
+                op.args_off = so;
+                op.args_bytes = sizeof pr;
+                op.bytes = 2.0 * (double)es * (double)V.size * (double)ninst;
+                op.variant = fp64 ? 1 : 0;
+                int64_t gy = std::min<int64_t>(ninst, 65535);
+                op.grid_y = (int32_t)gy;
+                op.grid_x = (int32_t)std::max<int64_t>(
+                    1, std::min<int64_t>((V.size + 255) / 256, std::max<int64_t>(1, 148 * 16 / gy)));
+                P.ops.push_back(op);
+                P.bytes_executed += op.bytes;
+                return off;
+            };
+            std::vector<std::pair<int32_t, int64_t>> gA, gB;
+            if (formM < 0) {
+                size_t off = permute_child(idM, VM, fM);
+                for (int64_t i = 0; i < N.n_inst; ++i) gA.push_back({BASE_ARENA, (int64_t)off + instM[i] * VM.size * es});
+                formM = 1;
+            } else {
+                for (int64_t i = 0; i < N.n_inst; ++i) gA.push_back(base_ref(idM, instM[i]));
+            }
+            if (formN < 0) {
+                size_t off = permute_child(idN, VN, fN);
+                for (int64_t i = 0; i < N.n_inst; ++i) gB.push_back({BASE_ARENA, (int64_t)off + instN[i] * VN.size * es});
+                formN = 1;
+            } else {
+                for (int64_t i = 0; i < N.n_inst; ++i) gB.push_back(base_ref(idN, instN[i]));
+            }
+            if (N.n_inst > 65535) fail(JET_EINVAL, "too many instances of one GEMM node");
+            GemmArgs g;
+            std::memset(&g, 0, sizeof g);
+            g.M = dimprod(fM);
+            g.N = dimprod(fN);
+            g.K = nK;
+            g.n_inst = (int32_t)N.n_inst;
+            g.a_kmajor = formM == 1;
+            g.b_kmajor = formN == 1;
+            size_t o_a = blob.put_ptrs(gA), o_b = blob.put_ptrs(gB), o_c = blob.put_ptrs(pc);
+            size_t so = blob.reserve(sizeof g);
+            std::memcpy(blob.bytes.data() + so, &g, sizeof g);
+            blob.patch_field(so, offsetof(GemmArgs, ptrA), BASE_BLOB, (int64_t)o_a);
+            blob.patch_field(so, offsetof(GemmArgs, ptrB), BASE_BLOB, (int64_t)o_b);
+            blob.patch_field(so, offsetof(GemmArgs, ptrC), BASE_BLOB, (int64_t)o_c);
+            Op op;
+            op.kind = OpKind::GemmSimt;
+            op.node = v;
+            op.n_inst = N.n_inst;
+            op.args_off = so;
+            op.args_bytes = sizeof g;
+            op.flop = flop;
+            op.bytes = bytes;
+            op.variant = fp64 ? 1 : 0;
+            op.grid_x = (int32_t)((g.N + 63) / 64);
+            op.grid_y = (int32_t)((g.M + 63) / 64);
+            op.grid_z = (int32_t)N.n_inst;
+            if (op.grid_y > 65535) fail(JET_EINVAL, "GEMM M too large");
+            P.ops.push_back(op);
+        }
         // ------------------------------------------------ direct contraction
-        {
-            (void)use_gemm;
+        else {
             ++P.n_direct;
             const View &VX = a_big ? VA : VB;   // operand whose strides order the summed labels
             auto strideA = [&](int64_t l) { int p = find_pos(VA.labels, l); return p < 0 ? 0 : VA.strides[p]; };

@@ -115,7 +115,7 @@ class Network:
         descs = (TensorDesc * n)()
         self.shapes = []
         for i, (lab, t) in enumerate(zip(labels, data)):
-            t = np.ascontiguousarray(np.asarray(t), dtype=np.complex64)
+            t = np.array(t, dtype=np.complex64, order="C")
             la = np.ascontiguousarray(np.asarray(lab, dtype=np.int64))
             di = np.ascontiguousarray(np.asarray(t.shape, dtype=np.int32))
             if la.size != t.ndim:
