@@ -305,6 +305,8 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c
         Plan &P = get_plan(*net, n_amps, outputs);
         bind_and_run(*net, P, nullptr, cuda_stream);
         copy_d2h(amps_out, net->d_amps, (size_t)n_amps * sizeof(jet_c128), cuda_stream ? cuda_stream : net->stream);
+        if (read_clear_status(*net, cuda_stream))
+            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
     });
 }
 

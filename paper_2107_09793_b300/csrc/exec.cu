@@ -44,6 +44,7 @@ static void init_device_once(const Network &net)
     int dev = net.opt.device;
     if (dev >= 0 && dev < 64 && !g_smem_set[dev]) {
         JET_CUDA(set_direct_smem_limits());
+        JET_CUDA(set_tc_smem_limits());
         g_smem_set[dev] = true;
     }
 }
@@ -56,6 +57,10 @@ void ensure_leaves_on_device(Network &net)
         cudaStream_t s;
         JET_CUDA(cudaStreamCreate(&s));
         net.stream = s;
+    }
+    if (!net.d_status) {
+        net.d_status = device_alloc(256);
+        JET_CUDA(cudaMemset(net.d_status, 0, 256));
     }
     if (!net.d_leaves) {
         net.d_leaves = device_alloc((size_t)net.n_values * sizeof(jet_c64));
@@ -112,6 +117,17 @@ void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream)
 
 bool gemm_available(int32_t) { return true; }
 
+int read_clear_status(Network &net, void *stream)
+{
+    if (!net.d_status) return 0;
+    uint32_t st = 0;
+    cudaStream_t s = stream ? (cudaStream_t)stream : (cudaStream_t)net.stream;
+    JET_CUDA(cudaMemcpyAsync(&st, net.d_status, 4, cudaMemcpyDeviceToHost, s));
+    JET_CUDA(cudaStreamSynchronize(s));
+    if (st) JET_CUDA(cudaMemsetAsync(net.d_status, 0, 4, s));
+    return (int)st;
+}
+
 void release_plan_device(Plan &plan)
 {
     if (plan.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)plan.graph_exec);
@@ -128,6 +144,8 @@ void free_network_device(Network &net)
     device_free(net.d_leaves64);
     device_free(net.own_arena);
     device_free(net.d_amps);
+    device_free(net.d_status);
+    net.d_status = nullptr;
     if (net.stream) cudaStreamDestroy((cudaStream_t)net.stream);
     net.d_leaves = net.d_leaves64 = net.own_arena = net.d_amps = nullptr;
     net.stream = nullptr;
@@ -161,6 +179,18 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
         GemmArgs a;
         std::memcpy(&a, p, sizeof a);
         e = launch_gemm_simt(a, c, s);
+        break;
+    }
+    case OpKind::TcSplit: {
+        TcSplitArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_tc_split(a, c, s);
+        break;
+    }
+    case OpKind::GemmTc: {
+        TcGemmArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_tc_gemm(a, c, s);
         break;
     }
     case OpKind::Reduce: {
@@ -222,11 +252,21 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream)
             P.d_args = device_alloc(P.host_args.size());
             P.d_args_bytes = P.host_args.size();
         }
-        uintptr_t bases[4] = {(uintptr_t)leaves, (uintptr_t)arena, (uintptr_t)P.d_args, (uintptr_t)net.d_amps};
+        uintptr_t bases[5] = {(uintptr_t)leaves, (uintptr_t)arena, (uintptr_t)P.d_args, (uintptr_t)net.d_amps,
+                              (uintptr_t)net.d_status};
         for (const auto &pt : P.patches) {
             uint64_t v = (uint64_t)(bases[pt.base] + (uintptr_t)pt.byte_off);
             std::memcpy(P.host_args.data() + pt.at, &v, 8);
         }
+        // tensor maps of the tensor-core GEMMs point into the (re)bound arena
+        for (const Op &op : P.ops)
+            if (op.kind == OpKind::GemmTc) {
+                TcGemmArgs g;
+                std::memcpy(&g, P.host_args.data() + op.args_off, sizeof g);
+                int rc = encode_tc_maps(g);
+                if (rc != 0) fail(JET_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string(rc) + ")");
+                std::memcpy(P.host_args.data() + op.args_off, &g, sizeof g);
+            }
         JET_CUDA(cudaMemcpy(P.d_args, P.host_args.data(), P.host_args.size(), cudaMemcpyHostToDevice));
         P.bound_arena = arena;
         P.bound_leaves = leaves;

@@ -1,0 +1,477 @@
+// Tensor-core route of a pairwise contraction (Section 3.1's matrix multiply),
+// written for the 5th-generation tensor cores of sm_103a.
+//
+// Complex product in the 4M real form with split precision:
+//   x = x_hi + x_lo (+ x_mid) in BF16 or TF32;  a*b ~ sum of the split terms
+//   whose magnitude is above the working precision (3 terms for a 2-way split,
+//   6 for BF16 3-way), accumulated in FP32.
+//   P = Ar.Br, Q = Ai.Bi, I = Ar.Bi + Ai.Br,  C = (P - Q) + i I.
+//
+// tc_split_kernel gathers a complex64 operand from any strides into K-major
+// padded planes (the transpose of Section 3.1 fused with the split).
+// tc_gemm_kernel: one 128x128 output tile per CTA; warp 0 issues TMA loads of
+// all planes of a K-block into a SWIZZLE_64B stage ring, warp 1 allocates TMEM
+// and one thread issues tcgen05.mma into three FP32 accumulators (3 x 128
+// TMEM columns), warps 2-5 read TMEM back and write complex64 C.  Every
+// mbarrier wait is bounded: on time-out the CTA records a status bit, frees
+// its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "tc_args.h"
+
+namespace jet {
+
+constexpr int TC_BM = 128;          // tile rows (M) and tile columns (N)
+constexpr int TC_BN = 128;
+constexpr int TC_ROWB = 64;         // bytes of K per stage row (SWIZZLE_64B span)
+constexpr int TC_PLANE_TILE = TC_BM * TC_ROWB;   // 8 KiB per plane tile
+constexpr uint32_t TC_TMEM_COLS = 512;
+
+template <int MODE>
+struct TcCfg;
+template <>
+struct TcCfg<JET_PREC_TF32> {
+    static constexpr int NP = 2, NT = 1, EB = 4, KIND = 1, STAGES = 4;
+    __device__ static void term(int t, int &p, int &q) { p = 0; q = 0; }
+};
+template <>
+struct TcCfg<JET_PREC_TF32X3> {
+    static constexpr int NP = 4, NT = 3, EB = 4, KIND = 1, STAGES = 3;
+    __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }   // lo.lo dropped
+};
+template <>
+struct TcCfg<JET_PREC_BF16X3> {
+    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 3;
+    __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }
+};
+template <>
+struct TcCfg<JET_PREC_BF16X6> {
+    static constexpr int NP = 6, NT = 6, EB = 2, KIND = 0, STAGES = 2;
+    // hi=0, mid=1, lo=2: hh, hm, mh, hl, lh, mm
+    __device__ static void term(int t, int &p, int &q)
+    {
+        const int P[6] = {0, 0, 1, 0, 2, 1}, Q[6] = {0, 1, 0, 2, 0, 1};
+        p = P[t];
+        q = Q[t];
+    }
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2 s of wall time (or when another role of the
+// CTA has already given up) and returns false.
+__device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > 2000000000ull) return false;
+        }
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1,
+                                            int c2)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, SWIZZLE_64B, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)4 << 61;                   // SWIZZLE_64B
+    return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    if (KIND == 0)
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+#define JET_TMEM_LD32(taddr, r)                                                                                      \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"   \
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                          \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),   \
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),          \
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),        \
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),        \
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                             \
+                 : "r"(taddr))
+
+// ------------------------------------------------------------------ split kernel
+__device__ __forceinline__ float tf32_rna(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int MODE>
+__device__ __forceinline__ void split_store(float x, uint8_t *base, int64_t plane_elems, int first_plane, int64_t e)
+{
+    if (MODE == JET_PREC_TF32) {
+        ((float *)base)[(int64_t)first_plane * plane_elems + e] = tf32_rna(x);
+    } else if (MODE == JET_PREC_TF32X3) {
+        float hi = tf32_rna(x);
+        float lo = tf32_rna(x - hi);
+        ((float *)base)[(int64_t)first_plane * plane_elems + e] = hi;
+        ((float *)base)[(int64_t)(first_plane + 1) * plane_elems + e] = lo;
+    } else if (MODE == JET_PREC_BF16X3) {
+        __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+        ((__nv_bfloat16 *)base)[(int64_t)first_plane * plane_elems + e] = hi;
+        ((__nv_bfloat16 *)base)[(int64_t)(first_plane + 1) * plane_elems + e] = lo;
+    } else {
+        __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        float r = x - __bfloat162float(hi);
+        __nv_bfloat16 mid = __float2bfloat16_rn(r);
+        __nv_bfloat16 lo = __float2bfloat16_rn(r - __bfloat162float(mid));
+        ((__nv_bfloat16 *)base)[(int64_t)first_plane * plane_elems + e] = hi;
+        ((__nv_bfloat16 *)base)[(int64_t)(first_plane + 1) * plane_elems + e] = mid;
+        ((__nv_bfloat16 *)base)[(int64_t)(first_plane + 2) * plane_elems + e] = lo;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256) tc_split_kernel(const __grid_constant__ TcSplitArgs a)
+{
+    constexpr int NP = TcCfg<MODE>::NP, EB = TcCfg<MODE>::EB;
+    const int64_t plane_elems = a.rows_pad * a.k_pad;
+    const int64_t total = plane_elems;
+    for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
+        const float2 *__restrict__ S = (const float2 *)((const uint64_t *)a.ptrSrc)[inst];
+        uint8_t *base = (uint8_t *)a.planes + (int64_t)inst * NP * plane_elems * EB;
+        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t row = e / a.k_pad, k = e - row * a.k_pad;
+            float2 v = make_float2(0.f, 0.f);
+            if (row < a.rows && k < a.k) {
+                int64_t off = 0, r = row;
+                for (int j = 0; j < a.rank_r; ++j) {
+                    int64_t q = r / a.r_dim[j];
+                    off += (r - q * a.r_dim[j]) * a.r_s[j];
+                    r = q;
+                }
+                r = k;
+                for (int j = 0; j < a.rank_k; ++j) {
+                    int64_t q = r / a.k_dim[j];
+                    off += (r - q * a.k_dim[j]) * a.k_s[j];
+                    r = q;
+                }
+                v = __ldg(S + off);
+            }
+            split_store<MODE>(v.x, base, plane_elems, 0, e);
+            split_store<MODE>(v.y, base, plane_elems, NP / 2, e);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ GEMM kernel
+template <int MODE>
+__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__ TcGemmArgs a)
+{
+    using Cfg = TcCfg<MODE>;
+    constexpr int NP = Cfg::NP, NPH = NP / 2, S = Cfg::STAGES;
+    constexpr int STAGE_BYTES = 2 * NP * TC_PLANE_TILE;
+    constexpr int KE = TC_ROWB / Cfg::EB;               // K elements per stage
+    constexpr int KSUB = TC_ROWB / 32;                   // MMAs of 32 bytes of K per stage
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2 * S + 1];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int abort_flag;
+
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile_n = blockIdx.x, tile_m = blockIdx.y, inst = blockIdx.z;
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]), accb = smem_u32(&bars[2 * S]);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+    const int n_kb = a.n_kb;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const int zA = ((const int32_t *)a.zA)[inst], zB = ((const int32_t *)a.zB)[inst];
+            int issued = 0;
+            for (int kb = 0; kb < n_kb; ++kb) {
+                const int s = kb % S;
+                if (kb >= S && !mbar_wait_bounded(empty0 + 8 * s, ((kb / S) - 1) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+                for (int p = 0; p < NP; ++p)
+                    tma_load_3d(st + p * TC_PLANE_TILE, &a.tmA, full0 + 8 * s, kb * KE, tile_m * TC_BM, zA + p);
+                for (int p = 0; p < NP; ++p)
+                    tma_load_3d(st + (NP + p) * TC_PLANE_TILE, &a.tmB, full0 + 8 * s, kb * KE, tile_n * TC_BN, zB + p);
+                issued = kb + 1;
+            }
+            if (abort_flag) {   // let copies already in flight land before the CTA exits
+                for (int kb = issued - S > 0 ? issued - S : 0; kb < issued; ++kb)
+                    mbar_wait_bounded(full0 + 8 * (kb % S), (kb / S) & 1, &abort_flag);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // kind::f16 / kind::tf32 instruction descriptor: FP32 D, K-major A and B, M=128, N=128
+            const uint32_t fmt = Cfg::KIND == 0 ? 1u : 2u;
+            const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                                   ((uint32_t)(TC_BM >> 4) << 24);
+            const uint32_t dP = tmem, dQ = tmem + TC_BN, dI = tmem + 2 * TC_BN;
+            for (int kb = 0; kb < n_kb; ++kb) {
+                const int s = kb % S;
+                if (!mbar_wait_bounded(full0 + 8 * s, (kb / S) & 1, &abort_flag)) {
+                    abort_flag = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
+#pragma unroll
+                for (int sub = 0; sub < KSUB; ++sub) {
+#pragma unroll
+                    for (int t = 0; t < Cfg::NT; ++t) {
+                        int p, q;
+                        Cfg::term(t, p, q);
+                        const uint64_t aRe = sdesc(st + p * TC_PLANE_TILE + sub * 32);
+                        const uint64_t aIm = sdesc(st + (NPH + p) * TC_PLANE_TILE + sub * 32);
+                        const uint64_t bRe = sdesc(st + (NP + q) * TC_PLANE_TILE + sub * 32);
+                        const uint64_t bIm = sdesc(st + (NP + NPH + q) * TC_PLANE_TILE + sub * 32);
+                        const uint32_t acc = (kb | sub | t) ? 1u : 0u;
+                        umma<Cfg::KIND>(dP, aRe, bRe, idesc, acc);
+                        umma<Cfg::KIND>(dQ, aIm, bIm, idesc, acc);
+                        umma<Cfg::KIND>(dI, aRe, bIm, idesc, acc);
+                        umma<Cfg::KIND>(dI, aIm, bRe, idesc, 1u);
+                    }
+                }
+                umma_commit(empty0 + 8 * s);
+            }
+            umma_commit(accb);
+        }
+    } else {
+        // epilogue warps 2..5: warp w reads TMEM lanes 32*(w%4) .. +31
+        const bool ok = mbar_wait_bounded(accb, 0, &abort_flag);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) abort_flag = 1;
+        const int quarter = warp & 3;
+        const int64_t row = (int64_t)tile_m * TC_BM + quarter * 32 + lane;
+        float2 *C = (float2 *)((const uint64_t *)a.ptrC)[inst];
+        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+        for (int chunk = 0; chunk < TC_BN / 32; ++chunk) {
+            uint32_t P[32], Q[32], I[32];
+            JET_TMEM_LD32(lane_addr + chunk * 32, P);
+            JET_TMEM_LD32(lane_addr + TC_BN + chunk * 32, Q);
+            JET_TMEM_LD32(lane_addr + 2 * TC_BN + chunk * 32, I);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (ok && row < a.M) {
+                const int64_t col0 = (int64_t)tile_n * TC_BN + chunk * 32;
+                float2 *dst = C + row * a.N + col0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (col0 + j < a.N)
+                        dst[j] = make_float2(__uint_as_float(P[j]) - __uint_as_float(Q[j]), __uint_as_float(I[j]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS));
+    }
+    if (threadIdx.x == 0 && abort_flag) atomicOr((unsigned int *)a.status, 1u);
+}
+
+// ------------------------------------------------------------------ host side
+template <int MODE>
+static int tc_smem_bytes()
+{
+    return TcCfg<MODE>::STAGES * 2 * TcCfg<MODE>::NP * TC_PLANE_TILE + 1024;
+}
+
+int tc_planes(int mode)
+{
+    switch (mode) {
+    case JET_PREC_TF32: return TcCfg<JET_PREC_TF32>::NP;
+    case JET_PREC_TF32X3: return TcCfg<JET_PREC_TF32X3>::NP;
+    case JET_PREC_BF16X3: return TcCfg<JET_PREC_BF16X3>::NP;
+    case JET_PREC_BF16X6: return TcCfg<JET_PREC_BF16X6>::NP;
+    default: return 0;
+    }
+}
+
+int tc_elem_bytes(int mode) { return (mode == JET_PREC_TF32 || mode == JET_PREC_TF32X3) ? 4 : 2; }
+int tc_k_block(int mode) { return TC_ROWB / tc_elem_bytes(mode); }
+int tc_tile() { return TC_BM; }
+
+cudaError_t set_tc_smem_limits()
+{
+    cudaError_t e = cudaSuccess;
+#define JET_TCSM(M)                                                                                        \
+    if (e == cudaSuccess)                                                                                  \
+        e = cudaFuncSetAttribute(tc_gemm_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<M>())
+    JET_TCSM(JET_PREC_TF32);
+    JET_TCSM(JET_PREC_TF32X3);
+    JET_TCSM(JET_PREC_BF16X3);
+    JET_TCSM(JET_PREC_BF16X6);
+#undef JET_TCSM
+    return e;
+}
+
+cudaError_t launch_tc_split(const TcSplitArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    dim3 grid(c.gx, c.gy, 1);
+    switch (a.mode) {
+    case JET_PREC_TF32: tc_split_kernel<JET_PREC_TF32><<<grid, 256, 0, s>>>(a); break;
+    case JET_PREC_TF32X3: tc_split_kernel<JET_PREC_TF32X3><<<grid, 256, 0, s>>>(a); break;
+    case JET_PREC_BF16X3: tc_split_kernel<JET_PREC_BF16X3><<<grid, 256, 0, s>>>(a); break;
+    case JET_PREC_BF16X6: tc_split_kernel<JET_PREC_BF16X6><<<grid, 256, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    dim3 grid(c.gx, c.gy, c.gz);
+    switch (a.mode) {
+    case JET_PREC_TF32:
+        tc_gemm_kernel<JET_PREC_TF32><<<grid, 192, tc_smem_bytes<JET_PREC_TF32>(), s>>>(a);
+        break;
+    case JET_PREC_TF32X3:
+        tc_gemm_kernel<JET_PREC_TF32X3><<<grid, 192, tc_smem_bytes<JET_PREC_TF32X3>(), s>>>(a);
+        break;
+    case JET_PREC_BF16X3:
+        tc_gemm_kernel<JET_PREC_BF16X3><<<grid, 192, tc_smem_bytes<JET_PREC_BF16X3>(), s>>>(a);
+        break;
+    case JET_PREC_BF16X6:
+        tc_gemm_kernel<JET_PREC_BF16X6><<<grid, 192, tc_smem_bytes<JET_PREC_BF16X6>(), s>>>(a);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+int encode_tc_maps(TcGemmArgs &a)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return -1;
+    const int eb = tc_elem_bytes(a.mode);
+    const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    cuuint32_t box[3] = {(cuuint32_t)(TC_ROWB / eb), (cuuint32_t)TC_BM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)a.k_pad, (cuuint64_t)a.m_pad, (cuuint64_t)a.planesA_total};
+        cuuint64_t strides[2] = {(cuuint64_t)(a.k_pad * eb), (cuuint64_t)(a.m_pad * a.k_pad * eb)};
+        if (fn(&a.tmA, dt, 3, (void *)a.planesA, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -2;
+    }
+    {
+        cuuint64_t dims[3] = {(cuuint64_t)a.k_pad, (cuuint64_t)a.n_pad, (cuuint64_t)a.planesB_total};
+        cuuint64_t strides[2] = {(cuuint64_t)(a.k_pad * eb), (cuuint64_t)(a.n_pad * a.k_pad * eb)};
+        if (fn(&a.tmB, dt, 3, (void *)a.planesB, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -3;
+    }
+    return 0;
+}
+
+}  // namespace jet

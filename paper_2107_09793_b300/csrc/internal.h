@@ -53,7 +53,7 @@ struct PathCost {
 };
 
 // -------------------------------------------------------------- plan / ops
-enum class OpKind : int32_t { Direct = 0, Permute = 1, GemmSimt = 2, GemmTc = 3, Reduce = 4, SplitKReduce = 5 };
+enum class OpKind : int32_t { Direct = 0, Permute = 1, GemmSimt = 2, GemmTc = 3, Reduce = 4, SplitKReduce = 5, TcSplit = 6 };
 
 struct Op {
     OpKind kind;
@@ -130,6 +130,7 @@ struct Network {
     void *user_arena = nullptr;
     size_t user_arena_bytes = 0;
     void *d_amps = nullptr;          // device amplitude buffer (complex128)
+    void *d_status = nullptr;        // device status word (bounded-wait time-outs)
     int64_t d_amps_cap = 0;
 
     // planner results
@@ -162,5 +163,6 @@ void device_free(void *p);
 void copy_d2h(void *dst, const void *src, size_t bytes, void *stream);
 void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream);
 bool gemm_available(int32_t precision);
+int read_clear_status(Network &net, void *stream);
 
 }  // namespace jet

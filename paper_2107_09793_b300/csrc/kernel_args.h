@@ -59,32 +59,6 @@ struct GemmArgs {
     int32_t pad_;
 };
 
-// Split-precision operand planes for the tensor-core GEMM: a complex operand in
-// any strided layout is written as bf16/tf32 planes, K contiguous, padded.
-struct SplitArgs {
-    uint64_t ptrSrc;                // device array of n_inst addresses (complex64)
-    uint64_t dst;                   // base of the planes (per instance: planes * rows_pad * k_pad)
-    int64_t rows, k, rows_pad, k_pad;
-    int64_t inst_stride;            // elements between instances' plane sets
-    int32_t n_inst, n_planes_per_part;
-    int32_t rank_r, rank_k;
-    int32_t mode;                   // jet_precision
-    int32_t pad_;
-    int64_t r_dim[JET_MAXR], r_s[JET_MAXR];   // row labels, fastest first, source strides
-    int64_t k_dim[JET_MAXR], k_s[JET_MAXR];   // K labels, fastest first, source strides
-};
-
-// Tensor-core GEMM over split planes (see gemm_tc.cu).
-struct TcGemmArgs {
-    uint64_t planesA, planesB;      // plane bases (device)
-    uint64_t ptrC;                  // device array of n_inst addresses
-    int64_t M, N, K;                // logical sizes
-    int64_t m_pad, n_pad, k_pad;
-    int64_t a_inst_stride, b_inst_stride;   // elements between instances
-    int32_t n_inst, mode;
-    int32_t tiles_m, tiles_n;
-};
-
 // amp[b] = sum over slices s (increasing s) of root[inst(b, s)], FP64
 // (Section 2.4, Eq. sliced_sum; the single reduction over slices).
 struct ReduceArgs {

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "kernel_args.h"
+#include "tc_args.h"
 
 #define JET_COMMA ,
 
@@ -21,6 +22,10 @@ cudaError_t launch_splitk_reduce(const SplitKReduceArgs &a, const LaunchCfg &c, 
 cudaError_t launch_slice_reduce(const ReduceArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_permute(const PermuteArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_gemm_simt(const GemmArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_tc_split(const TcSplitArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_tc_gemm(const TcGemmArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t set_tc_smem_limits();
+int encode_tc_maps(TcGemmArgs &a);
 cudaError_t launch_c64_to_c128(const void *src, void *dst, int64_t n, cudaStream_t s);
 
 }  // namespace jet

@@ -22,12 +22,13 @@
 
 #include "internal.h"
 #include "kernel_args.h"
+#include "tc_args.h"
 
 namespace jet {
 
 namespace {
 
-enum Base : int32_t { BASE_LEAVES = 0, BASE_ARENA = 1, BASE_BLOB = 2, BASE_AMPS = 3 };
+enum Base : int32_t { BASE_LEAVES = 0, BASE_ARENA = 1, BASE_BLOB = 2, BASE_AMPS = 3, BASE_STATUS = 4 };
 
 struct View {
     std::vector<int64_t> labels;   // layout order, slowest first
@@ -144,6 +145,12 @@ int find_pos(const std::vector<int64_t> &v, int64_t x)
 
 }  // namespace
 
+// tensor-core route geometry (gemm_tc.cu)
+int tc_planes(int mode);
+int tc_elem_bytes(int mode);
+int tc_k_block(int mode);
+int tc_tile();
+
 std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs)
 {
     if (net.path.size() + 1 != net.leaves.size()) fail(JET_ESTATE, "no contraction path set");
@@ -246,6 +253,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     Arena arena;
     Blob blob;
     const bool gemm_ok = gemm_available(net.opt.precision);
+    const bool tc_mode = tc_planes(net.opt.precision) > 0;
     int64_t max_inter = 0;
 
     auto base_ref = [&](int32_t id, int32_t inst) -> std::pair<int32_t, int64_t> {
@@ -397,6 +405,107 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 if (V.labels == cat(kappa, f)) return 0;   // [K][free]
                 return -1;
             };
+            if (tc_mode) {
+                // tensor cores: gather + split each child instance once into K-major planes
+                const int NP = tc_planes(net.opt.precision), eb = tc_elem_bytes(net.opt.precision);
+                const int64_t kblk = tc_k_block(net.opt.precision), T = tc_tile();
+                const int64_t Mv = dimprod(fM), Nv = dimprod(fN);
+                const int64_t m_pad = (Mv + T - 1) / T * T, n_pad = (Nv + T - 1) / T * T;
+                const int64_t k_pad = (nK + kblk - 1) / kblk * kblk;
+                auto split_child = [&](int32_t id, const View &V, const std::vector<int64_t> &f, int64_t rows_pad) {
+                    const int64_t ninst = node[id].n_inst;
+                    const size_t nbytes_p = (size_t)ninst * NP * rows_pad * k_pad * eb;
+                    size_t off = arena.alloc(nbytes_p);
+                    scratch.push_back(off);
+                    scratch_bytes.push_back(nbytes_p);
+                    TcSplitArgs sa;
+                    std::memset(&sa, 0, sizeof sa);
+                    sa.rows = dimprod(f);
+                    sa.k = nK;
+                    sa.rows_pad = rows_pad;
+                    sa.k_pad = k_pad;
+                    sa.n_inst = (int32_t)ninst;
+                    sa.n_planes = NP;
+                    sa.mode = net.opt.precision;
+                    sa.rank_r = (int32_t)f.size();
+                    sa.rank_k = (int32_t)kappa.size();
+                    if (sa.rank_r > JET_MAXR || sa.rank_k > JET_MAXR) fail(JET_EINVAL, "operand rank too large");
+                    for (int j = 0; j < sa.rank_r; ++j) {
+                        int p = find_pos(V.labels, f[f.size() - 1 - j]);
+                        sa.r_dim[j] = V.dims[p];
+                        sa.r_s[j] = V.strides[p];
+                    }
+                    for (int j = 0; j < sa.rank_k; ++j) {
+                        int p = find_pos(V.labels, kappa[kappa.size() - 1 - j]);
+                        sa.k_dim[j] = V.dims[p];
+                        sa.k_s[j] = V.strides[p];
+                    }
+                    std::vector<std::pair<int32_t, int64_t>> ps;
+                    for (int64_t j = 0; j < ninst; ++j) ps.push_back(base_ref(id, (int32_t)j));
+                    size_t o_ps = blob.put_ptrs(ps);
+                    size_t so = blob.reserve(sizeof sa);
+                    std::memcpy(blob.bytes.data() + so, &sa, sizeof sa);
+                    blob.patch_field(so, offsetof(TcSplitArgs, ptrSrc), BASE_BLOB, (int64_t)o_ps);
+                    blob.patch_field(so, offsetof(TcSplitArgs, planes), BASE_ARENA, (int64_t)off);
+                    Op op;
+                    op.kind = OpKind::TcSplit;
+                    op.node = v;
+                    op.n_inst = ninst;
+                    op.args_off = so;
+                    op.args_bytes = sizeof sa;
+                    op.bytes = (double)ninst * ((double)V.size * 8.0 + (double)NP * rows_pad * k_pad * eb);
+                    int64_t gy = std::min<int64_t>(ninst, 65535);
+                    op.grid_y = (int32_t)gy;
+                    op.grid_x = (int32_t)std::max<int64_t>(
+                        1, std::min<int64_t>((rows_pad * k_pad + 255) / 256, std::max<int64_t>(1, 148 * 16 / gy)));
+                    P.ops.push_back(op);
+                    P.bytes_executed += op.bytes;
+                    return off;
+                };
+                size_t offA = split_child(idM, VM, fM, m_pad);
+                size_t offB = split_child(idN, VN, fN, n_pad);
+                std::vector<int32_t> zA, zB;
+                for (int64_t i = 0; i < N.n_inst; ++i) {
+                    zA.push_back(instM[i] * NP);
+                    zB.push_back(instN[i] * NP);
+                }
+                if (N.n_inst > 65535) fail(JET_EINVAL, "too many instances of one GEMM node");
+                TcGemmArgs g;
+                std::memset(&g, 0, sizeof g);
+                g.M = Mv;
+                g.N = Nv;
+                g.K = nK;
+                g.m_pad = m_pad;
+                g.n_pad = n_pad;
+                g.k_pad = k_pad;
+                g.planesA_total = node[idM].n_inst * NP;
+                g.planesB_total = node[idN].n_inst * NP;
+                g.n_inst = (int32_t)N.n_inst;
+                g.mode = net.opt.precision;
+                g.n_kb = (int32_t)(k_pad / kblk);
+                size_t o_za = blob.put_i32(zA), o_zb = blob.put_i32(zB), o_c = blob.put_ptrs(pc);
+                size_t so = blob.reserve(sizeof g, 128);
+                std::memcpy(blob.bytes.data() + so, &g, sizeof g);
+                blob.patch_field(so, offsetof(TcGemmArgs, planesA), BASE_ARENA, (int64_t)offA);
+                blob.patch_field(so, offsetof(TcGemmArgs, planesB), BASE_ARENA, (int64_t)offB);
+                blob.patch_field(so, offsetof(TcGemmArgs, zA), BASE_BLOB, (int64_t)o_za);
+                blob.patch_field(so, offsetof(TcGemmArgs, zB), BASE_BLOB, (int64_t)o_zb);
+                blob.patch_field(so, offsetof(TcGemmArgs, ptrC), BASE_BLOB, (int64_t)o_c);
+                blob.patch_field(so, offsetof(TcGemmArgs, status), BASE_STATUS, 0);
+                Op op;
+                op.kind = OpKind::GemmTc;
+                op.node = v;
+                op.n_inst = N.n_inst;
+                op.args_off = so;
+                op.args_bytes = sizeof g;
+                op.flop = flop;
+                op.bytes = bytes;
+                op.grid_x = (int32_t)(n_pad / T);
+                op.grid_y = (int32_t)(m_pad / T);
+                op.grid_z = (int32_t)N.n_inst;
+                if (op.grid_y > 65535) fail(JET_EINVAL, "GEMM M too large");
+                P.ops.push_back(op);
+            } else {
             int formM = form(VM, fM), formN = form(VN, fN);
             // operands that are neither: gather each child instance into [free, K] once
             auto permute_child = [&](int32_t id, const View &V, const std::vector<int64_t> &f) {
@@ -488,6 +597,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             op.grid_z = (int32_t)N.n_inst;
             if (op.grid_y > 65535) fail(JET_EINVAL, "GEMM M too large");
             P.ops.push_back(op);
+            }
         }
         // ------------------------------------------------ direct contraction
         else {

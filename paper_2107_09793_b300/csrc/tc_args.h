@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "kernel_args.h"
+#include "../../include/jet.h"
 
 // Operand split: a complex64 operand, gathered from any strides into
 // [rows_pad][k_pad] K-contiguous planes.  Plane order per instance:
@@ -25,7 +26,7 @@ struct TcSplitArgs {
 // C[m][n] = sum_k A[m][k] B[n][k] over split planes, complex 4M form with three
 // FP32 accumulators in TMEM: P = Ar.Br, Q = Ai.Bi, I = Ar.Bi + Ai.Br;
 // C = (P - Q) + i I.  Each real product expands into the split terms of the mode.
-struct alignas(64) TcGemmArgs {
+struct TcGemmArgs {
     CUtensorMap tmA;                 // 3-D map over A planes: (k_pad, m_pad, planes)
     CUtensorMap tmB;                 // 3-D map over B planes: (k_pad, n_pad, planes)
     uint64_t planesA, planesB;       // plane bases (device), used to encode the maps

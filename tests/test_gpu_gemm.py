@@ -57,10 +57,12 @@ CASES = [
     # ragged: dims 3 and 5 (M, N, K not multiples of the tiles)
     ([0, 1, 2, 3, 10, 11, 12], [10, 11, 12, 20, 21, 22], {0: 3, 1: 5, 2: 3, 3: 3, 10: 5, 11: 3, 12: 5,
                                                         20: 5, 21: 3, 22: 5}),
+    # several 128x128 tiles and 16+ K-blocks (wraps the tensor-core stage ring)
+    (list(range(0, 8)) + list(range(10, 19)), list(range(10, 19)) + list(range(20, 28)), {}),
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32", "tf32x3", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_gemm_layouts(prec, case):
     la, lb, dd = CASES[case]
