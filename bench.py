@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark: sliced pairwise contraction of the 30-qubit 5x6 grid circuit
+(14 cycles, 6 sliced indices = 64 slices, largest intermediate <= 2^24 complex64)
+down to one amplitude, on one B300, through the library's C ABI.
+
+A step = one full contraction (all slices, shared intermediates computed once,
+FP64 slice sum), replayed from the captured CUDA graph.  `value` is whole-job
+amplitudes/s with the inputs resident in HBM; `e2e` is the same metric through
+jet_tensors_upload + jet_contract with pinned host buffers (host<->device
+copies inside the timed region).  The FP32 CUDA-core path runs the same plan
+for comparison.  `--impl reference` times the FP64 CPU oracle instead.
+
+Multi-GPU (torchrun): every rank contracts its own seeded bitstring (weak
+scaling, no collective on the data path); time = max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contraction TFLOP/s & amplitudes/s, split-prec vs plain FP32 at ≤1e-5 rel err"
+WORKLOAD = ("grid30: 30-qubit 5x6 grid random circuit, 14 cycles, sqrt(X|Y|W) + fSim(pi/2,pi/6) ABCDCDAB, "
+            "6 sliced indices (64 slices), largest intermediate <= 2^24 complex64, one amplitude")
+PATH_TRIALS, PATH_SEED, CAP, N_SLICED = 1024, 1, 1 << 24, 6
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def rank_outputs(base, rank, n_qubits, seed=2):
+    """Rank r contracts the workload bitstring (r = 0) or its own seeded one."""
+    from circuits import random_bitstrings
+    if rank == 0:
+        return np.asarray(base, np.int32)
+    return random_bitstrings(n_qubits, 1, 7000 + seed * 131 + rank)
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def build_network(w, precision, profile=0, path=None, sliced=None, device=0):
+    from paper_2107_09793_b300 import jet
+    net = jet.from_network(w.network, precision=precision, profile=profile, device=device)
+    if path is None:
+        net.path_greedy(seed=PATH_SEED, n_trials=PATH_TRIALS)
+        sliced = net.slice_auto(CAP, min_n=N_SLICED, max_n=max(N_SLICED, 24))
+    else:
+        net.path_set(path)
+        net.slice(sliced)
+    return net, net.path_get(), sliced
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the timed region runs."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device, self.lines, self.proc = device, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((ts, parts))
+        inwin = [r for r in rows if t0 - 0.15 <= r[0] <= t1 + 0.15] or rows
+        if not inwin:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(p[1]) for _, p in inwin if p[1].replace(".", "").isdigit()]
+        mx = [float(p[2]) for _, p in inwin if p[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, p in inwin for i in range(4) if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(inwin),
+                "power_w_max": max((float(p[3]) for _, p in inwin if p[3].replace(".", "").isdigit()),
+                                   default=None)}
+
+
+def golden_amplitude():
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "grid30.json")) as f:
+            g = json.load(f)
+        a = g["amplitudes"][0]
+        return complex(a[0], a[1]), g["outputs"][0]
+    except (OSError, ValueError, KeyError):
+        return None, None
+
+
+def oracle_slice_sample(w, sliced, n_slices, outputs):
+    """FP64 oracle (pairwise numpy.tensordot) on slice 0 only: a bounded sample."""
+    import oracle
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max((i.get("num_threads", 0) for i in threadpool_info()), default=0) or len(os.sched_getaffinity(0))
+    except Exception:
+        cores = len(os.sched_getaffinity(0))
+    t0 = time.perf_counter()
+    part = oracle.sliced_partials(w.network.as_complex64(), outputs[0], sliced, [0])
+    dt = time.perf_counter() - t0
+    return {"value": (1.0 / n_slices) / dt, "unit": "amplitudes/s", "cores": int(cores), "kind": "oracle",
+            "sample": f"1 of {n_slices} slices of the grid30 amplitude (FP64 pairwise tensordot, own greedy path), "
+                      f"{dt:.1f} s"}, part
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from circuits import configs
+    w = configs.build("grid30")
+    from paper_2107_09793_b300 import jet  # planner only (host), to pick the same sliced labels
+    net = jet.from_network(w.network)
+    net.path_greedy(seed=PATH_SEED, n_trials=PATH_TRIALS)
+    sliced = net.slice_auto(CAP, min_n=N_SLICED, max_n=max(N_SLICED, 24))
+    n_sl = 2 ** len(sliced)
+    steps = max(1, min(args.steps, 3))
+    warm = min(args.warmup, 1)
+    times = []
+    base = None
+    for i in range(warm + steps):
+        b, _ = oracle_slice_sample(w, sliced, n_sl, w.outputs)
+        if i >= warm:
+            times.append(1.0 / b["value"] / n_sl)
+        base = b
+    t = sum(times)
+    value = steps * (1.0 / n_sl) / t
+    line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": 1000 * t / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one slice of the 64 (bounded sample)"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_impl(args):
+    import torch
+    from circuits import configs
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    peaks, peak_src = load_peaks()
+    w = configs.build("grid30")
+    outs = rank_outputs(w.outputs, rank, w.circuit.n)
+
+    net, path, sliced = build_network(w, args.precision, profile=1, device=dev)
+    from paper_2107_09793_b300 import jet
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    amps_dev = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        net.contract_async(outs, amps_dev.data_ptr(), sh)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    step_ms, gemm_ms = [], {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()                      # evict L2 between timed steps (256 MiB > 126 MB L2)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for i, r in enumerate(net.profile()):
+            if r["ms"] >= 0:
+                gemm_ms.setdefault(i, []).append(r["ms"])
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall1 = time.time()
+    time.sleep(0.25)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    amp = complex(amps_dev[0].item())
+    local_s = sum(step_ms) / 1000.0
+    total_s = max_over_ranks(local_s, world)
+    value = world * args.steps / total_s
+    st = net.stats()
+    recs = net.profile()
+
+    # roofline of the dominant (tensor-core GEMM) launches, timed live above
+    gl = [(i, recs[i]) for i in gemm_ms]
+    roof = None
+    if gl:
+        tot_ms = {i: statistics.mean(v) for i, v in gemm_ms.items()}
+        big = max(gl, key=lambda x: tot_ms[x[0]])[0]
+        ms = tot_ms[big]
+        achieved = recs[big]["flop"] / (ms * 1e-3) / 1e12
+        tc = args.precision not in ("fp32", "fp64")
+        issue = {"bf16x3": 3, "tf32x3": 3, "bf16x6": 6, "tf32": 1}.get(args.precision, 1)
+        peak = peaks["bf16_tflops_sustained"] * (0.5 if args.precision.startswith("tf32") else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"tc_gemm_kernel<{args.precision}>" if tc else "gemm_simt_kernel",
+                "per_launch_ms": ms, "flop_per_launch": recs[big]["flop"],
+                "issued_tensor_tflops": achieved * issue if tc else None,
+                "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)"
+                                                                         if args.precision.startswith("tf32") else ""),
+                "gemm_share_of_step": sum(tot_ms.values()) / (sum(step_ms) / len(step_ms))}
+
+    # where the step's time goes: one extra profiled step with every launch timed
+    breakdown = {}
+    nprof = jet.from_network(w.network, precision=args.precision, profile=2, device=dev)
+    nprof.path_set(path)
+    nprof.slice(sliced)
+    aprof = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+    for _ in range(2):
+        flush.zero_()
+        nprof.contract_async(outs, aprof.data_ptr(), sh)
+        torch.cuda.synchronize()
+    for r in nprof.profile():
+        if r["ms"] < 0:
+            continue
+        b = breakdown.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "bytes": 0.0, "flop": 0.0})
+        b["ms"] += r["ms"]
+        b["launches"] += 1
+        b["bytes"] += r["bytes"]
+        b["flop"] += r["flop"]
+    tot_b = sum(b["ms"] for b in breakdown.values()) or 1.0
+    for b in breakdown.values():
+        b["share"] = b["ms"] / tot_b
+        b["gb_s"] = b["bytes"] / (b["ms"] * 1e-3) / 1e9 if b["ms"] > 0 else None
+    nprof.close()
+
+    # same plan on CUDA cores (FP32), the comparison path
+    fp32 = None
+    if not args.skip_fp32 and args.precision != "fp32":
+        n32 = jet.from_network(w.network, precision="fp32", device=dev)
+        n32.path_set(path)
+        n32.slice(sliced)
+        a32 = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+        for _ in range(2):
+            n32.contract_async(outs, a32.data_ptr(), sh)
+        torch.cuda.synchronize()
+        k32 = max(2, min(args.steps, 5))
+        ms32 = []
+        for _ in range(k32):
+            flush.zero_()
+            ev0.record(stream)
+            n32.contract_async(outs, a32.data_ptr(), sh)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms32.append(ev0.elapsed_time(ev1))
+        fp32 = {"value": 1000.0 / statistics.mean(ms32), "unit": "amplitudes/s", "ms_per_step": statistics.mean(ms32),
+                "tflops": st["flop_executed"] / (statistics.mean(ms32) * 1e-3) / 1e12,
+                "amp": [complex(a32[0].item()).real, complex(a32[0].item()).imag]}
+        n32.close()
+
+    # end to end through the C ABI: pinned host inputs -> device, contract, amplitude back to host
+    nv = net.n_values()
+    host_vals = torch.empty(nv, dtype=torch.complex64, pin_memory=True)
+    host_vals.numpy()[:] = np.concatenate([np.asarray(t, np.complex64).ravel() for t in w.network.data])
+    e2e_s = []
+    for i in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.upload(host_vals.data_ptr(), sh)
+        a = net.contract(outs, stream=sh)
+        dt = time.perf_counter() - t0
+        if i:
+            e2e_s.append(dt)
+    e2e_total = max_over_ranks(sum(e2e_s), world)
+    e2e = {"value": world * len(e2e_s) / e2e_total, "unit": "amplitudes/s", "h2d_bytes_per_step": int(nv * 8),
+           "d2h_bytes_per_step": int(len(outs) * 16 + 4)}
+
+    if rank != 0:
+        return 0
+    g_amp, g_out = golden_amplitude()
+    err = None
+    if g_amp is not None and list(g_out) == list(map(int, outs[0])):
+        err = {"split": abs(amp - g_amp) / abs(g_amp)}
+        if fp32:
+            a32 = complex(*fp32["amp"])
+            err["fp32"] = abs(a32 - g_amp) / abs(g_amp)
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        cpu, _ = oracle_slice_sample(w, sliced, st["n_slices"], outs)
+    kinds = {}
+    line = {
+        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_slices": st["n_slices"], "sliced_labels": sliced,
+                   "path": f"library greedy, {PATH_TRIALS} trials, seed {PATH_SEED}",
+                   "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
+                   "launch": "one CUDA graph per step"},
+        "tflops": st["flop_executed"] / (total_s / args.steps) / 1e12 * world,
+        "flop_per_step": st["flop_executed"], "flop_no_reuse": st["flop_sliced"],
+        "reuse_fraction": st["reuse_fraction"], "workspace_gb": st["workspace_bytes"] / 1e9,
+        "amplitude": [amp.real, amp.imag], "rel_err_vs_oracle": err,
+        "fp32_simt": fp32, "roofline": roof, "breakdown": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": int(st["n_launches"]) * args.steps,
+        "wall_s_timed": t_wall1 - t_wall0,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="jet", choices=["jet", "reference"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp32", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_impl(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -72,6 +72,9 @@ typedef struct {
     int64_t gemm_min_k;       /* contractions with a summed extent >= this (and large
                                  outputs) take the GEMM route; default 64                 */
     int64_t workspace_limit;  /* bytes of device workspace the plan may use; 0 = none    */
+    int32_t profile;          /* 0 (default): off; 1: CUDA events around every GEMM-route
+                                 launch; 2: around every launch (read with jet_profile)  */
+    int32_t pad_;
 } jet_options;
 
 typedef struct {
@@ -97,6 +100,20 @@ typedef struct {
     int32_t  n_gemm_nodes;        /* tree nodes routed to the GEMM kernels                */
     int32_t  n_direct_nodes;      /* tree nodes routed to the direct-contraction kernel   */
 } jet_stats_t;
+
+/* One launch of the current plan, for jet_profile. */
+typedef struct {
+    int32_t kind;             /* 0 direct, 1 permute, 2 SIMT GEMM, 3 tensor-core GEMM,
+                                 4 slice reduction, 5 split-K reduction, 6 operand split */
+    int32_t node;             /* tree node (SSA id) the launch belongs to               */
+    int64_t n_inst;           /* instances the launch processes                         */
+    double  flop;             /* algorithmic real FLOP of the launch                    */
+    double  bytes;            /* algorithmic HBM bytes of the launch                    */
+    float   ms;               /* device time of the last run, -1 if not timed           */
+    int32_t block;            /* threads per block                                      */
+    int32_t grid[3];          /* launch grid                                            */
+    int32_t smem;             /* dynamic shared memory bytes (0 = kernel default)       */
+} jet_op_record;
 
 /* Defaults listed in jet_options above. */
 void jet_options_default(jet_options *opt);
@@ -196,6 +213,12 @@ int jet_set_workspace(jet_network *net, void *dptr, size_t bytes);
 int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs,
                       const jet_c128 *cot, int32_t n_req, const int32_t *tensor_ids,
                       jet_c64 *const *env_out, jet_c128 *amps_out, void *cuda_stream);
+
+/* The launches of the current plan in issue order, with the device time of
+ * each timed launch in the last contraction (jet_options.profile).  Waits for
+ * that contraction to finish.  Writes min(cap, count) records and the count.
+ * Errors: JET_ESTATE (no plan yet). */
+int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t *n_out);
 
 /* Statistics of the network and the last plan (see jet_stats_t). */
 int jet_stats(const jet_network *net, jet_stats_t *out);

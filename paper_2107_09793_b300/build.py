@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return SO
     tmp = SO + f".tmp{os.getpid()}"
     cmd = [os.path.join(CUDA, "bin", "nvcc"), "-shared", *ARCH, "-Xcompiler", "-fPIC",
-           "--cudart", "static", "-o", tmp, *objs]
+           "--cudart", "static", "-Xlinker", "--exclude-libs,ALL", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

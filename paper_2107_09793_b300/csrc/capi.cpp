@@ -83,6 +83,7 @@ void jet_options_default(jet_options *opt)
     opt->device = 0;
     opt->gemm_min_k = 64;
     opt->workspace_limit = 0;
+    opt->profile = 0;
 }
 
 int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_options *opt, jet_network **out)
@@ -318,6 +319,30 @@ int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs, 
         (void)net; (void)n_amps; (void)outputs; (void)cot; (void)n_req; (void)tensor_ids;
         (void)env_out; (void)amps_out; (void)cuda_stream;
         fail(JET_ESTATE, "jet_contract_grad: not available in this build");
+    });
+}
+
+int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t *n_out)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (!net->plan) fail(JET_ESTATE, "no plan yet");
+        const Plan &P = *net->plan;
+        if (n_out) *n_out = (int32_t)P.ops.size();
+        for (size_t i = 0; out && i < P.ops.size() && (int32_t)i < cap; ++i) {
+            const Op &op = P.ops[i];
+            out[i].kind = (int32_t)op.kind;
+            out[i].node = op.node;
+            out[i].n_inst = op.n_inst;
+            out[i].flop = op.flop;
+            out[i].bytes = op.bytes;
+            out[i].ms = op_elapsed_ms(P, i);
+            out[i].block = op.block;
+            out[i].grid[0] = op.grid_x;
+            out[i].grid[1] = op.grid_y;
+            out[i].grid[2] = op.grid_z;
+            out[i].smem = op.smem;
+        }
     });
 }
 

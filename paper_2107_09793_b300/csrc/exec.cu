@@ -128,8 +128,32 @@ int read_clear_status(Network &net, void *stream)
     return (int)st;
 }
 
+static void destroy_events(Plan &plan)
+{
+    for (void *e : plan.ev_begin)
+        if (e) cudaEventDestroy((cudaEvent_t)e);
+    for (void *e : plan.ev_end)
+        if (e) cudaEventDestroy((cudaEvent_t)e);
+    plan.ev_begin.clear();
+    plan.ev_end.clear();
+    plan.profile_level = 0;
+}
+
+float op_elapsed_ms(const Plan &plan, size_t i)
+{
+    if (i >= plan.ev_begin.size() || !plan.ev_begin[i]) return -1.f;
+    if (cudaEventSynchronize((cudaEvent_t)plan.ev_end[i]) != cudaSuccess) return -1.f;
+    float ms = -1.f;
+    if (cudaEventElapsedTime(&ms, (cudaEvent_t)plan.ev_begin[i], (cudaEvent_t)plan.ev_end[i]) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+    }
+    return ms;
+}
+
 void release_plan_device(Plan &plan)
 {
+    destroy_events(plan);
     if (plan.graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)plan.graph_exec);
     plan.graph_exec = nullptr;
     device_free(plan.d_args);
@@ -155,6 +179,7 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
 {
     LaunchCfg c{op.grid_x, op.grid_y, op.grid_z, op.block, op.smem, op.variant};
     const uint8_t *p = args.data() + op.args_off;
+    cudaGetLastError();   // drop any stale error so the check below sees this launch only
     cudaError_t e = cudaSuccess;
     switch (op.kind) {
     case OpKind::Direct: {
@@ -202,7 +227,12 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
     default:
         fail(JET_EINVAL, "internal: unknown op kind");
     }
-    if (e != cudaSuccess) fail(JET_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        fail(JET_ECUDA, std::string("kernel launch (op kind ") + std::to_string((int)op.kind) + ", node " +
+                            std::to_string(op.node) + ", grid " + std::to_string(op.grid_x) + "x" +
+                            std::to_string(op.grid_y) + "x" + std::to_string(op.grid_z) + ", smem " +
+                            std::to_string(op.smem) + ", variant " + std::to_string(op.variant) +
+                            "): " + cudaGetErrorString(e));
     (void)P;
 }
 
@@ -274,6 +304,40 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream)
         P.dirty_args = false;
     }
 
+    // optional per-launch timing: event records become nodes of the captured graph
+    if (P.profile_level != net.opt.profile) {
+        if (P.graph_exec) {
+            JET_CUDA(cudaStreamSynchronize(s));
+            cudaGraphExecDestroy((cudaGraphExec_t)P.graph_exec);
+            P.graph_exec = nullptr;
+        }
+        destroy_events(P);
+        if (net.opt.profile > 0) {
+            P.ev_begin.assign(P.ops.size(), nullptr);
+            P.ev_end.assign(P.ops.size(), nullptr);
+            for (size_t i = 0; i < P.ops.size(); ++i) {
+                OpKind k = P.ops[i].kind;
+                bool want = net.opt.profile >= 2 || k == OpKind::GemmTc || k == OpKind::GemmSimt;
+                if (!want) continue;
+                cudaEvent_t a, b;
+                JET_CUDA(cudaEventCreate(&a));
+                JET_CUDA(cudaEventCreate(&b));
+                P.ev_begin[i] = a;
+                P.ev_end[i] = b;
+            }
+        }
+        P.profile_level = net.opt.profile;
+    }
+    auto issue_all = [&](cudaStream_t st) {
+        for (size_t i = 0; i < P.ops.size(); ++i) {
+            const bool timed = i < P.ev_begin.size() && P.ev_begin[i];
+            // external event records: real timestamp nodes when the stream is being captured
+            if (timed) JET_CUDA(cudaEventRecordWithFlags((cudaEvent_t)P.ev_begin[i], st, cudaEventRecordExternal));
+            launch_op(P, P.host_args, P.ops[i], st);
+            if (timed) JET_CUDA(cudaEventRecordWithFlags((cudaEvent_t)P.ev_end[i], st, cudaEventRecordExternal));
+        }
+    };
+
     if (net.opt.use_graph) {
         if (!P.graph_exec) {
             if (P.graph_exec) {
@@ -287,7 +351,7 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream)
             cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 try {
-                    for (const Op &op : P.ops) launch_op(P, P.host_args, op, cap);
+                    issue_all(cap);
                 } catch (...) {
                     cudaStreamEndCapture(cap, &g);
                     if (g) cudaGraphDestroy(g);
@@ -307,7 +371,7 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream)
         }
         JET_CUDA(cudaGraphLaunch((cudaGraphExec_t)P.graph_exec, s));
     } else {
-        for (const Op &op : P.ops) launch_op(P, P.host_args, op, s);
+        issue_all(s);
     }
 }
 

@@ -101,6 +101,8 @@ struct Plan {
     void *bound_arena = nullptr;
     void *bound_leaves = nullptr;
     void *bound_amps = nullptr;
+    std::vector<void *> ev_begin, ev_end;   // per op: cudaEvent_t pair when profiled
+    int32_t profile_level = 0;
     void *graph_exec = nullptr;       // cudaGraphExec_t
     void *graph_stream = nullptr;
     bool dirty_args = true;
@@ -164,5 +166,6 @@ void copy_d2h(void *dst, const void *src, size_t bytes, void *stream);
 void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream);
 bool gemm_available(int32_t precision);
 int read_clear_status(Network &net, void *stream);
+float op_elapsed_ms(const Plan &plan, size_t i);
 
 }  // namespace jet

@@ -20,7 +20,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_tensors_upload", "jet_network_n_values", "jet_path_set", "jet_path_get",
            "jet_path_greedy", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
-           "jet_network_destroy", "jet_last_error"]
+           "jet_network_destroy", "jet_last_error", "jet_profile"]
 
 
 class JetError(RuntimeError):
@@ -31,7 +31,18 @@ class JetError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("gemm_min_k", ctypes.c_int64), ("workspace_limit", ctypes.c_int64)]
+                ("device", ctypes.c_int32), ("gemm_min_k", ctypes.c_int64), ("workspace_limit", ctypes.c_int64),
+                ("profile", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class OpRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("node", ctypes.c_int32), ("n_inst", ctypes.c_int64),
+                ("flop", ctypes.c_double), ("bytes", ctypes.c_double), ("ms", ctypes.c_float),
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("smem", ctypes.c_int32)]
+
+
+OP_KINDS = {0: "direct", 1: "permute", 2: "gemm_simt", 3: "gemm_tc", 4: "slice_reduce", 5: "splitk_reduce",
+            6: "tc_split"}
 
 
 class TensorDesc(ctypes.Structure):
@@ -77,6 +88,7 @@ def lib():
             "jet_set_workspace": (I32, [P, P, ctypes.c_size_t]),
             "jet_contract_grad": (I32, [P, I32, P, P, I32, P, P, P, P]),
             "jet_stats": (I32, [P, P]),
+            "jet_profile": (I32, [P, P, I32, P]),
             "jet_network_destroy": (None, [P]),
             "jet_last_error": (ctypes.c_char_p, []),
         }
@@ -93,7 +105,7 @@ def _check(rc: int):
         raise JetError(rc, lib().jet_last_error().decode())
 
 
-def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=64) -> Options:
+def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=64, profile=0) -> Options:
     o = Options()
     lib().jet_options_default(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -101,6 +113,7 @@ def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm
     o.use_graph = int(bool(use_graph))
     o.device = int(device)
     o.gemm_min_k = int(gemm_min_k)
+    o.profile = int(profile)
     return o
 
 
@@ -223,6 +236,15 @@ class Network:
         _check(lib().jet_contract_grad(self._h, o.shape[0], o.ctypes.data, c.ctypes.data, ids.size,
                                        ids.ctypes.data, ptrs, amps.ctypes.data, ctypes.c_void_p(stream)))
         return amps, envs
+
+    def profile(self) -> List[Dict[str, float]]:
+        n = ctypes.c_int32()
+        _check(lib().jet_profile(self._h, None, 0, ctypes.byref(n)))
+        recs = (OpRecord * max(n.value, 1))()
+        _check(lib().jet_profile(self._h, recs, n.value, ctypes.byref(n)))
+        return [{"kind": OP_KINDS.get(r.kind, str(r.kind)), "node": r.node, "n_inst": r.n_inst, "flop": r.flop,
+                 "bytes": r.bytes, "ms": r.ms, "block": r.block, "grid": tuple(r.grid), "smem": r.smem}
+                for r in recs[:n.value]]
 
     def stats(self) -> Dict[str, float]:
         s = Stats()

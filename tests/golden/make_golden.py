@@ -1,0 +1,81 @@
+"""Writes the stored expected values under tests/golden/ for the large workloads.
+
+Calls only the FP64 oracle (`oracle`) and the seeded input generators
+(`circuits`): every tensor is rounded to complex64 first, exactly as the CUDA
+path receives it, then upcast to complex128.
+
+  grid30.json : 30-qubit 5x6 grid circuit, 14 cycles (seed 2)
+     * amplitudes of the workload's bitstring and 7 more seeded bitstrings, from the
+       dense 2^30 state vector (O1, 16 GiB);
+     * 4 slice partials of the workload bitstring (Eq. sliced_sum) by pairwise
+       contraction (O2) for a fixed, rule-chosen set of 6 sliced labels: the wire
+       label of qubits 12..17 (grid row 2) just after their 8th single-qubit gate.
+
+Usage: python tests/golden/make_golden.py grid30
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from circuits import configs, random_bitstrings, Circuit, Gate  # noqa: E402
+
+
+def rounded(circ):
+    return Circuit(n=circ.n, d=circ.d,
+                   gates=[Gate(np.asarray(g.matrix, np.complex64).astype(np.complex128), g.qubits, g.params, g.kind)
+                          for g in circ.gates],
+                   initial=[np.asarray(v, np.complex64).astype(np.complex128) for v in circ.initial])
+
+
+def rule_sliced_labels(w, qubits, nth):
+    """Label on each listed qubit's wire right after its nth (0-based) 1-qubit gate."""
+    tn = w.network
+    count = {q: 0 for q in qubits}
+    out = {}
+    for gi, g in enumerate(w.circuit.gates):
+        if len(g.qubits) == 1 and g.qubits[0] in count:
+            q = g.qubits[0]
+            if count[q] == nth:
+                out[q] = tn.labels[tn.gate_tensor[gi]][0]
+            count[q] += 1
+    return [out[q] for q in qubits]
+
+
+def grid30():
+    w = configs.build("grid30")
+    circ = rounded(w.circuit)
+    outs = np.concatenate([w.outputs, random_bitstrings(w.circuit.n, 7, 2024)])
+    t0 = time.time()
+    amps = oracle.sv_amplitudes(circ, outs)
+    t_sv = time.time() - t0
+    sliced = rule_sliced_labels(w, list(range(12, 18)), 7)
+    slice_ids = [0, 17, 42, 63]
+    t0 = time.time()
+    parts = oracle.sliced_partials(w.network.as_complex64(), w.outputs[0], sliced, slice_ids)
+    t_o2 = time.time() - t0
+    rec = {
+        "workload": "grid30", "source": "oracle O1 (2^30 state vector) and O2 (pairwise numpy.tensordot)",
+        "outputs": outs.tolist(),
+        "amplitudes": [[a.real, a.imag] for a in amps],
+        "sliced_labels": [int(x) for x in sliced],
+        "slice_ids": slice_ids,
+        "slice_partials": [[p.real, p.imag] for p in parts],
+        "seconds": {"statevector": round(t_sv, 1), "four_slices": round(t_o2, 1)},
+    }
+    with open(os.path.join(HERE, "grid30.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec["seconds"]))
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["grid30"]
+    for name in which:
+        {"grid30": grid30}[name]()
