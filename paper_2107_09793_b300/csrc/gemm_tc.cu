@@ -166,61 +166,114 @@ __device__ __forceinline__ float tf32_rna(float x)
     return __uint_as_float(r);
 }
 
+// The mode's parts of one value, largest first (x = p0 + p1 + p2 up to rounding).
 template <int MODE>
-__device__ __forceinline__ void split_store(float x, uint8_t *base, int64_t plane_elems, int first_plane, int64_t e)
+__device__ __forceinline__ void split_parts(float x, float (&p)[3])
 {
     if (MODE == JET_PREC_TF32) {
-        ((float *)base)[(int64_t)first_plane * plane_elems + e] = tf32_rna(x);
+        p[0] = tf32_rna(x);
     } else if (MODE == JET_PREC_TF32X3) {
-        float hi = tf32_rna(x);
-        float lo = tf32_rna(x - hi);
-        ((float *)base)[(int64_t)first_plane * plane_elems + e] = hi;
-        ((float *)base)[(int64_t)(first_plane + 1) * plane_elems + e] = lo;
+        p[0] = tf32_rna(x);
+        p[1] = tf32_rna(x - p[0]);
     } else if (MODE == JET_PREC_BF16X3) {
-        __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        __nv_bfloat16 lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-        ((__nv_bfloat16 *)base)[(int64_t)first_plane * plane_elems + e] = hi;
-        ((__nv_bfloat16 *)base)[(int64_t)(first_plane + 1) * plane_elems + e] = lo;
+        p[0] = __bfloat162float(__float2bfloat16_rn(x));
+        p[1] = __bfloat162float(__float2bfloat16_rn(x - p[0]));
     } else {
-        __nv_bfloat16 hi = __float2bfloat16_rn(x);
-        float r = x - __bfloat162float(hi);
-        __nv_bfloat16 mid = __float2bfloat16_rn(r);
-        __nv_bfloat16 lo = __float2bfloat16_rn(r - __bfloat162float(mid));
-        ((__nv_bfloat16 *)base)[(int64_t)first_plane * plane_elems + e] = hi;
-        ((__nv_bfloat16 *)base)[(int64_t)(first_plane + 1) * plane_elems + e] = mid;
-        ((__nv_bfloat16 *)base)[(int64_t)(first_plane + 2) * plane_elems + e] = lo;
+        p[0] = __bfloat162float(__float2bfloat16_rn(x));
+        const float r = x - p[0];
+        p[1] = __bfloat162float(__float2bfloat16_rn(r));
+        p[2] = __bfloat162float(__float2bfloat16_rn(r - p[1]));
     }
 }
 
+constexpr int SPLIT_TR = 32, SPLIT_TK = 64;
+
+// Tiled gather + split: a block owns a 32-row x 64-column tile of the planes.
+// The source offsets of its rows and columns are decoded once into shared
+// memory; the tile is read with threads running along the source's fastest
+// label (rows or K, fast_k) and written along K, two values per thread.
 template <int MODE>
 __global__ void __launch_bounds__(256) tc_split_kernel(const __grid_constant__ TcSplitArgs a)
 {
-    constexpr int NP = TcCfg<MODE>::NP, EB = TcCfg<MODE>::EB;
+    constexpr int NP = TcCfg<MODE>::NP, EB = TcCfg<MODE>::EB, NPH = NP / 2;
+    __shared__ float2 tile[SPLIT_TR][SPLIT_TK + 1];
+    __shared__ int64_t rowOff[SPLIT_TR], kOff[SPLIT_TK];
+    const int tid = threadIdx.x;
+    const int64_t k_tiles = (a.k_pad + SPLIT_TK - 1) / SPLIT_TK;
+    const int64_t tiles = (a.rows_pad / SPLIT_TR) * k_tiles;
     const int64_t plane_elems = a.rows_pad * a.k_pad;
-    const int64_t total = plane_elems;
     for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
         const float2 *__restrict__ S = (const float2 *)((const uint64_t *)a.ptrSrc)[inst];
         uint8_t *base = (uint8_t *)a.planes + (int64_t)inst * NP * plane_elems * EB;
-        for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t row = e / a.k_pad, k = e - row * a.k_pad;
-            float2 v = make_float2(0.f, 0.f);
-            if (row < a.rows && k < a.k) {
-                int64_t off = 0, r = row;
-                for (int j = 0; j < a.rank_r; ++j) {
-                    int64_t q = r / a.r_dim[j];
-                    off += (r - q * a.r_dim[j]) * a.r_s[j];
-                    r = q;
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+            const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
+            const int64_t row0 = rt * SPLIT_TR, k0 = kt * SPLIT_TK;
+            __syncthreads();
+            if (tid < SPLIT_TR) {
+                int64_t row = row0 + tid, off = -1;
+                if (row < a.rows) {
+                    off = 0;
+                    for (int j = 0; j < a.rank_r; ++j) {
+                        int64_t q = row / a.r_dim[j];
+                        off += (row - q * a.r_dim[j]) * a.r_s[j];
+                        row = q;
+                    }
                 }
-                r = k;
-                for (int j = 0; j < a.rank_k; ++j) {
-                    int64_t q = r / a.k_dim[j];
-                    off += (r - q * a.k_dim[j]) * a.k_s[j];
-                    r = q;
+                rowOff[tid] = off;
+            } else if (tid < SPLIT_TR + SPLIT_TK) {
+                int64_t k = k0 + (tid - SPLIT_TR), off = -1;
+                if (k < a.k) {
+                    off = 0;
+                    for (int j = 0; j < a.rank_k; ++j) {
+                        int64_t q = k / a.k_dim[j];
+                        off += (k - q * a.k_dim[j]) * a.k_s[j];
+                        k = q;
+                    }
                 }
-                v = __ldg(S + off);
+                kOff[tid - SPLIT_TR] = off;
             }
-            split_store<MODE>(v.x, base, plane_elems, 0, e);
-            split_store<MODE>(v.y, base, plane_elems, NP / 2, e);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < (SPLIT_TR * SPLIT_TK) / 256; ++i) {
+                int r, kk;
+                if (a.fast_k) {
+                    kk = tid & (SPLIT_TK - 1);
+                    r = (tid >> 6) + 4 * i;
+                } else {
+                    r = tid & (SPLIT_TR - 1);
+                    kk = (tid >> 5) + 8 * i;
+                }
+                const int64_t ro = rowOff[r], ko = kOff[kk];
+                tile[r][kk] = (ro >= 0 && ko >= 0) ? __ldg(S + ro + ko) : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < (SPLIT_TR * SPLIT_TK / 2) / 256; ++i) {
+                const int idx = tid + 256 * i;
+                const int r = idx / (SPLIT_TK / 2), kp = 2 * (idx % (SPLIT_TK / 2));
+                const int64_t k = k0 + kp;
+                if (k >= a.k_pad) continue;
+                const int64_t e = (row0 + r) * a.k_pad + k;
+                const float2 v0 = tile[r][kp], v1 = tile[r][kp + 1];
+                float re0[3], re1[3], im0[3], im1[3];
+                split_parts<MODE>(v0.x, re0);
+                split_parts<MODE>(v1.x, re1);
+                split_parts<MODE>(v0.y, im0);
+                split_parts<MODE>(v1.y, im1);
+#pragma unroll
+                for (int p = 0; p < NPH; ++p) {
+                    if (EB == 2) {
+                        __nv_bfloat162 *pr = (__nv_bfloat162 *)((__nv_bfloat16 *)base + (int64_t)p * plane_elems + e);
+                        __nv_bfloat162 *pi =
+                            (__nv_bfloat162 *)((__nv_bfloat16 *)base + (int64_t)(NPH + p) * plane_elems + e);
+                        *pr = __floats2bfloat162_rn(re0[p], re1[p]);
+                        *pi = __floats2bfloat162_rn(im0[p], im1[p]);
+                    } else {
+                        *(float2 *)((float *)base + (int64_t)p * plane_elems + e) = make_float2(re0[p], re1[p]);
+                        *(float2 *)((float *)base + (int64_t)(NPH + p) * plane_elems + e) = make_float2(im0[p], im1[p]);
+                    }
+                }
+            }
         }
     }
 }

@@ -440,6 +440,15 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                         sa.k_dim[j] = V.dims[p];
                         sa.k_s[j] = V.strides[p];
                     }
+                    {
+                        int64_t best = -1, bl = -1;
+                        for (size_t q = 0; q < V.labels.size(); ++q)
+                            if (best < 0 || V.strides[q] < best) {
+                                best = V.strides[q];
+                                bl = V.labels[q];
+                            }
+                        sa.fast_k = find_pos(kappa, bl) >= 0 ? 1 : 0;
+                    }
                     std::vector<std::pair<int32_t, int64_t>> ps;
                     for (int64_t j = 0; j < ninst; ++j) ps.push_back(base_ref(id, (int32_t)j));
                     size_t o_ps = blob.put_ptrs(ps);
@@ -456,8 +465,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     op.bytes = (double)ninst * ((double)V.size * 8.0 + (double)NP * rows_pad * k_pad * eb);
                     int64_t gy = std::min<int64_t>(ninst, 65535);
                     op.grid_y = (int32_t)gy;
+                    const int64_t tiles = (rows_pad / 32) * ((k_pad + 63) / 64);
                     op.grid_x = (int32_t)std::max<int64_t>(
-                        1, std::min<int64_t>((rows_pad * k_pad + 255) / 256, std::max<int64_t>(1, 148 * 16 / gy)));
+                        1, std::min<int64_t>(tiles, std::max<int64_t>(1, 148 * 16 / gy)));
                     P.ops.push_back(op);
                     P.bytes_executed += op.bytes;
                     return off;

@@ -18,7 +18,7 @@ struct TcSplitArgs {
     int64_t rows, k, rows_pad, k_pad;
     int32_t n_inst, n_planes;
     int32_t rank_r, rank_k;
-    int32_t mode, pad_;
+    int32_t mode, fast_k;           // fast_k: the source's stride-1 label is a summed label
     int64_t r_dim[JET_MAXR], r_s[JET_MAXR];   // row labels, fastest first, source strides
     int64_t k_dim[JET_MAXR], k_s[JET_MAXR];   // summed labels, fastest first, source strides
 };
