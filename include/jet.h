@@ -223,6 +223,31 @@ int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t
 /* Statistics of the network and the last plan (see jet_stats_t). */
 int jet_stats(const jet_network *net, jet_stats_t *out);
 
+/* Pairwise contraction of two dense tensors that allocates no device memory.
+ * The paper has no counterpart; it serves callers that cannot call cudaMalloc:
+ * a process whose GPU memory is pre-reserved by its own allocator (an
+ * allocation behind that allocator's back can fail or fragment its pool), or a
+ * latency-critical loop where cudaMalloc / cudaFree would add implicit device
+ * synchronisation.  a_dev and b_dev are row-major complex64 tensors in DEVICE
+ * memory (labels[0] slowest); labels shared by the two tensors are summed;
+ * c_dev (DEVICE, caller-allocated) receives the result with A's unshared labels
+ * in A's order followed by B's unshared labels in B's order, row-major.
+ * Scratch (split-K partial sums and offset tables) lives in one fixed 16 MiB
+ * device array inside the library, held by every GPU that loads the library
+ * until the process exits; the output may have at most 524280 elements
+ * (larger outputs are rejected with JET_EINVAL), each tensor fewer than 2^31
+ * elements, at most 40 labels each.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture on the device.  Every call shares the array: calls that
+ * overlap on the GPU (different streams, or different host threads) race, so
+ * order them on one stream.  Runs asynchronously on cuda_stream on `device`.
+ * Errors: JET_EINVAL (NULL pointer, bad rank/dim, repeated label, size limit),
+ * JET_ECUDA. */
+int jet_pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_t *dims_a,
+                              const jet_c64 *a_dev, int32_t rank_b, const int64_t *labels_b,
+                              const int32_t *dims_b, const jet_c64 *b_dev, jet_c64 *c_dev,
+                              int32_t device, void *cuda_stream);
+
 /* Release the handle and every device buffer the library allocated. */
 void jet_network_destroy(jet_network *net);
 

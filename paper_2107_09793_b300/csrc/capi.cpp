@@ -379,6 +379,16 @@ int jet_stats(const jet_network *net, jet_stats_t *out)
     });
 }
 
+int jet_pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_t *dims_a, const jet_c64 *a_dev,
+                              int32_t rank_b, const int64_t *labels_b, const int32_t *dims_b, const jet_c64 *b_dev,
+                              jet_c64 *c_dev, int32_t device, void *cuda_stream)
+{
+    return guarded([&] {
+        pair_contract_noalloc(rank_a, labels_a, dims_a, a_dev, rank_b, labels_b, dims_b, b_dev, c_dev, device,
+                              cuda_stream);
+    });
+}
+
 void jet_network_destroy(jet_network *net)
 {
     if (!net) return;

@@ -168,4 +168,9 @@ bool gemm_available(int32_t precision);
 int read_clear_status(Network &net, void *stream);
 float op_elapsed_ms(const Plan &plan, size_t i);
 
+// noalloc.cu
+void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_t *dims_a, const void *a_dev,
+                           int32_t rank_b, const int64_t *labels_b, const int32_t *dims_b, const void *b_dev,
+                           void *c_dev, int32_t device, void *stream);
+
 }  // namespace jet

@@ -20,7 +20,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_tensors_upload", "jet_network_n_values", "jet_path_set", "jet_path_get",
            "jet_path_greedy", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
-           "jet_network_destroy", "jet_last_error", "jet_profile"]
+           "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc"]
 
 
 class JetError(RuntimeError):
@@ -89,6 +89,7 @@ def lib():
             "jet_contract_grad": (I32, [P, I32, P, P, I32, P, P, P, P]),
             "jet_stats": (I32, [P, P]),
             "jet_profile": (I32, [P, P, I32, P]),
+            "jet_pair_contract_noalloc": (I32, [I32, P, P, P, I32, P, P, P, P, I32, P]),
             "jet_network_destroy": (None, [P]),
             "jet_last_error": (ctypes.c_char_p, []),
         }
@@ -250,6 +251,19 @@ class Network:
         s = Stats()
         _check(lib().jet_stats(self._h, ctypes.byref(s)))
         return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+
+def pair_contract_noalloc(labels_a, shape_a, a_dev_ptr: int, labels_b, shape_b, b_dev_ptr: int, c_dev_ptr: int,
+                          device: int = 0, stream: int = 0):
+    """jet_pair_contract_noalloc: contract two complex64 device tensors into a
+    caller-allocated device output without any device allocation."""
+    la = np.ascontiguousarray(np.asarray(labels_a, dtype=np.int64))
+    lb = np.ascontiguousarray(np.asarray(labels_b, dtype=np.int64))
+    da = np.ascontiguousarray(np.asarray(shape_a, dtype=np.int32))
+    db = np.ascontiguousarray(np.asarray(shape_b, dtype=np.int32))
+    _check(lib().jet_pair_contract_noalloc(la.size, la.ctypes.data, da.ctypes.data, ctypes.c_void_p(a_dev_ptr),
+                                           lb.size, lb.ctypes.data, db.ctypes.data, ctypes.c_void_p(b_dev_ptr),
+                                           ctypes.c_void_p(c_dev_ptr), int(device), ctypes.c_void_p(stream)))
 
 
 def from_network(tn, **opt_kwargs) -> Network:
