@@ -374,6 +374,46 @@ def run_impl(args):
     return 0
 
 
+def run_gemm_case(args):
+    """One pairwise contraction shaped like the workload's dominant node, large
+    enough to exceed L2 but small enough for an ncu capture: C[8192 x 8192] =
+    A[8192 x 2048] B[2048 x 8192], complex64, in the chosen precision."""
+    import torch
+    from circuits import SplitMix64
+    from paper_2107_09793_b300 import jet
+    torch.cuda.set_device(0)
+    rm, rk, rn = 13, 11, 13
+    la = list(range(rm)) + list(range(100, 100 + rk))
+    lb = list(range(100, 100 + rk)) + list(range(200, 200 + rn))
+    rng = np.random.default_rng(SplitMix64(9).next_u64() % (1 << 32))
+    A = (rng.random([2] * len(la)) - 0.5 + 1j * (rng.random([2] * len(la)) - 0.5)).astype(np.complex64)
+    B = (rng.random([2] * len(lb)) - 0.5 + 1j * (rng.random([2] * len(lb)) - 0.5)).astype(np.complex64)
+    # the pair is one GEMM node; a rank-1 selector on each free leg closes the network
+    sel = [np.ones(2, np.complex64)] * (rm + rn)
+    labels = [la, lb] + [[l] for l in list(range(rm)) + list(range(200, 200 + rn))]
+    net = jet.Network(labels, [A, B] + sel, precision=args.precision, profile=1)
+    net.set_open([])
+    path, cur = [(0, 1)], len(labels)
+    for i in range(2, len(labels)):
+        path.append((cur, i))
+        cur += 1
+    net.path_set(path)
+    outs = np.zeros((1, 0), np.int32)
+    amps = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    sh = torch.cuda.current_stream().cuda_stream
+    ms = []
+    for i in range(args.warmup + args.steps):
+        net.contract_async(outs, amps.data_ptr(), sh)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            ms += [r["ms"] for r in net.profile() if r["kind"] in ("gemm_tc", "gemm_simt")]
+    flop = 8.0 * 2 ** (rm + rk + rn)
+    t = statistics.mean(ms) * 1e-3
+    print(json.dumps({"case": "gemm M=N=8192 K=2048 complex", "precision": args.precision, "gemm_ms": t * 1e3,
+                      "algorithmic_tflops": flop / t / 1e12}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,7 +423,11 @@ def main():
     ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--case", default="workload", choices=["workload", "gemm"],
+                    help="gemm: a single complex GEMM node sized for ncu captures")
     args = ap.parse_args()
+    if args.case == "gemm":
+        return run_gemm_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_impl(args)

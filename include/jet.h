@@ -69,8 +69,8 @@ typedef struct {
                                  0: every (slice, amplitude) recomputes its whole tree   */
     int32_t use_graph;        /* 1 (default): record the launch sequence in a CUDA graph */
     int32_t device;           /* CUDA device ordinal, default 0                          */
-    int64_t gemm_min_k;       /* contractions with a summed extent >= this (and large
-                                 outputs) take the GEMM route; default 64                 */
+    int64_t gemm_min_k;       /* contractions with a summed extent >= this (and both free
+                                 extents >= 64) take the GEMM route; default 16           */
     int64_t workspace_limit;  /* bytes of device workspace the plan may use; 0 = none    */
     int32_t profile;          /* 0 (default): off; 1: CUDA events around every GEMM-route
                                  launch; 2: around every launch (read with jet_profile)  */
@@ -104,7 +104,8 @@ typedef struct {
 /* One launch of the current plan, for jet_profile. */
 typedef struct {
     int32_t kind;             /* 0 direct, 1 permute, 2 SIMT GEMM, 3 tensor-core GEMM,
-                                 4 slice reduction, 5 split-K reduction, 6 operand split */
+                                 4 slice reduction, 5 split-K reduction, 6 operand split,
+                                 7 batched small contractions of one tree level          */
     int32_t node;             /* tree node (SSA id) the launch belongs to               */
     int64_t n_inst;           /* instances the launch processes                         */
     double  flop;             /* algorithmic real FLOP of the launch                    */

@@ -81,7 +81,7 @@ void jet_options_default(jet_options *opt)
     opt->reuse = 1;
     opt->use_graph = 1;
     opt->device = 0;
-    opt->gemm_min_k = 64;
+    opt->gemm_min_k = 16;
     opt->workspace_limit = 0;
     opt->profile = 0;
 }
@@ -97,7 +97,7 @@ int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_opti
         else jet_options_default(&net->opt);
         if (net->opt.precision < JET_PREC_FP32 || net->opt.precision > JET_PREC_FP64)
             fail(JET_EINVAL, "unknown precision mode");
-        if (net->opt.gemm_min_k < 1) net->opt.gemm_min_k = 64;
+        if (net->opt.gemm_min_k < 1) net->opt.gemm_min_k = 16;
         int64_t off = 0;
         for (int32_t t = 0; t < n; ++t) {
             const jet_tensor_desc &d = tensors[t];

@@ -183,6 +183,44 @@ __global__ void splitk_reduce_kernel(const __grid_constant__ SplitKReduceArgs a)
     }
 }
 
+// Many small contractions of one tree level in one launch.  Task t owns blocks
+// [block0_t, block0_{t+1}); a block finds its task by binary search and walks
+// the task's (instance, output) items with full offset tables.
+template <typename V>
+__global__ void __launch_bounds__(256) small_batch_kernel(const __grid_constant__ SmallBatchArgs a)
+{
+    const SmallTask *T = (const SmallTask *)a.tasks;
+    int lo = 0, hi = a.n_tasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T[mid].block0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const SmallTask t = T[lo];
+    const int nb = (lo + 1 < a.n_tasks ? T[lo + 1].block0 : a.n_blocks) - t.block0;
+    const int32_t *__restrict__ oA = (const int32_t *)t.offA, *__restrict__ oB = (const int32_t *)t.offB;
+    const int32_t *__restrict__ kA = (const int32_t *)t.kA, *__restrict__ kB = (const int32_t *)t.kB;
+    const int64_t total = (int64_t)t.n_inst * t.n_out;
+    for (int64_t i = (int64_t)(blockIdx.x - t.block0) * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)nb * blockDim.x) {
+        const int inst = (int)(i / t.n_out), o = (int)(i - (int64_t)inst * t.n_out);
+        const V *__restrict__ A = (const V *)((const uint64_t *)t.ptrA)[inst];
+        const V *__restrict__ B = (const V *)((const uint64_t *)t.ptrB)[inst];
+        V *__restrict__ C = (V *)((const uint64_t *)t.ptrC)[inst];
+        const int32_t xa = oA[o], xb = oB[o];
+        V acc = vzero<V>();
+        for (int q = 0; q < t.n_k; ++q) acc = cmul_add(acc, A[xa + kA[q]], B[xb + kB[q]]);
+        C[o] = acc;
+    }
+}
+
+cudaError_t launch_small_batch(const SmallBatchArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    if (c.variant & 1) small_batch_kernel<double2><<<c.gx, 256, 0, s>>>(a);
+    else small_batch_kernel<float2><<<c.gx, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // amp[b] = sum_{s = 0 .. n_sl-1} root(b, s), in FP64, one thread per amplitude.
 __global__ void slice_reduce_kernel(const __grid_constant__ ReduceArgs a)
 {

@@ -194,6 +194,12 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
         e = launch_splitk_reduce(a, c, s);
         break;
     }
+    case OpKind::SmallBatch: {
+        SmallBatchArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_small_batch(a, c, s);
+        break;
+    }
     case OpKind::Permute: {
         PermuteArgs a;
         std::memcpy(&a, p, sizeof a);

@@ -59,6 +59,22 @@ struct GemmArgs {
     int32_t pad_;
 };
 
+// A small pairwise contraction inside a batched launch: full offset tables
+// (output -> A/B offsets, summed index -> A/B offsets), no index decoding.
+struct SmallTask {
+    uint64_t ptrA, ptrB, ptrC;      // device arrays of n_inst addresses
+    uint64_t offA, offB;            // device int32[n_out]
+    uint64_t kA, kB;                // device int32[n_k]
+    int32_t n_out, n_k, n_inst;
+    int32_t block0;                 // first block of this task within the launch
+};
+
+// One launch over many independent small contractions of one tree level.
+struct SmallBatchArgs {
+    uint64_t tasks;                 // device SmallTask[n_tasks], ordered by block0
+    int32_t n_tasks, n_blocks;
+};
+
 // amp[b] = sum over slices s (increasing s) of root[inst(b, s)], FP64
 // (Section 2.4, Eq. sliced_sum; the single reduction over slices).
 struct ReduceArgs {

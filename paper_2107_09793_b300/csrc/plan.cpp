@@ -44,6 +44,10 @@ struct NodeInfo {
     int32_t base = BASE_ARENA;
     int64_t buf_off = 0;             // arena byte offset of instance 0 (internal nodes)
     std::vector<int32_t> ia, ib;     // child instances of each instance (internal nodes)
+    int32_t a = -1, b = -1;          // children (internal nodes)
+    std::vector<int64_t> K, fa, fb;  // summed labels, free labels of a, free labels of b
+    bool use_gemm = false, a_big = false, small = false;
+    int32_t depth = 0;               // tree level (leaves 0)
 };
 
 struct Blob {
@@ -262,10 +266,18 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         return {BASE_ARENA, N.buf_off + (int64_t)inst * N.view.size * es};
     };
 
+    auto dimprod = [&](const std::vector<int64_t> &ls) {
+        int64_t p = 1;
+        for (int64_t l : ls) p *= net.labels.at(l).dim;
+        return p;
+    };
+
+    // ---- pass 1, tree order: instances (reuse DAG), label classes, route, layout, depth
     for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
         const int32_t a = net.path[k].first, b = net.path[k].second, v = n_leaves + k;
         NodeInfo &N = node[v];
-        // instances
+        N.a = a;
+        N.b = b;
         auto &ids = inst_of[v];
         ids.resize(n_assign);
         const NodeInfo &NA = node[a], &NB = node[b];
@@ -296,41 +308,34 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         std::vector<int32_t>().swap(inst_of[a]);
         std::vector<int32_t>().swap(inst_of[b]);
 
-        // label classes
         const View &VA = NA.view, &VB = NB.view;
-        std::vector<int64_t> K, fa, fb;
-        for (int64_t l : VA.labels) (find_pos(VB.labels, l) >= 0 ? K : fa).push_back(l);
+        for (int64_t l : VA.labels) (find_pos(VB.labels, l) >= 0 ? N.K : N.fa).push_back(l);
         for (int64_t l : VB.labels)
-            if (find_pos(VA.labels, l) < 0) fb.push_back(l);
-        auto dimprod = [&](const std::vector<int64_t> &ls) {
-            int64_t p = 1;
-            for (int64_t l : ls) p *= net.labels.at(l).dim;
-            return p;
-        };
-        const int64_t nK = dimprod(K), nFa = dimprod(fa), nFb = dimprod(fb);
-        const bool use_gemm = gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64;
+            if (find_pos(VA.labels, l) < 0) N.fb.push_back(l);
+        const int64_t nK = dimprod(N.K), nFa = dimprod(N.fa), nFb = dimprod(N.fb);
+        N.use_gemm = gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64;
 
         // output layout
         std::vector<int64_t> out;
-        bool a_big = VA.size >= VB.size;
-        const View &VBig = a_big ? VA : VB;
-        const View &VSmall = a_big ? VB : VA;
-        const std::vector<int64_t> &fbig = a_big ? fa : fb, &fsmall = a_big ? fb : fa;
-        if (!use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size) {
+        N.a_big = VA.size >= VB.size;
+        const View &VBig = N.a_big ? VA : VB;
+        const View &VSmall = N.a_big ? VB : VA;
+        const std::vector<int64_t> &fbig = N.a_big ? N.fa : N.fb, &fsmall = N.a_big ? N.fb : N.fa;
+        if (!N.use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size) {
             // keep the big operand's order; the small operand's free labels take
             // the place of the first summed label (gate application in place)
             int ins = -1;
             for (size_t i = 0; i < VBig.labels.size(); ++i)
-                if (find_pos(K, VBig.labels[i]) >= 0) { ins = (int)i; break; }
+                if (find_pos(N.K, VBig.labels[i]) >= 0) { ins = (int)i; break; }
             for (size_t i = 0; i < VBig.labels.size(); ++i) {
                 if ((int)i == ins) out.insert(out.end(), fsmall.begin(), fsmall.end());
-                if (find_pos(K, VBig.labels[i]) < 0) out.push_back(VBig.labels[i]);
+                if (find_pos(N.K, VBig.labels[i]) < 0) out.push_back(VBig.labels[i]);
             }
             if (ins < 0) out.insert(out.begin(), fsmall.begin(), fsmall.end());
-        } else if (use_gemm) {
+        } else if (N.use_gemm) {
             bool a_is_m = nFa >= nFb;
-            out = a_is_m ? fa : fb;
-            const auto &other = a_is_m ? fb : fa;
+            out = a_is_m ? N.fa : N.fb;
+            const auto &other = a_is_m ? N.fb : N.fa;
             out.insert(out.end(), other.begin(), other.end());
         } else {
             out = fbig;
@@ -338,6 +343,79 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         }
         N.view = dense_view(out, net);
         max_inter = std::max(max_inter, N.view.size);
+        // small direct contractions are batched per tree level into one launch
+        N.small = !N.use_gemm && N.view.size <= 4096 && nK <= 2048 &&
+                  (double)N.n_inst * (double)N.view.size * (double)nK <= (double)(1 << 24);
+        N.depth = 1 + std::max(node[a].depth, node[b].depth);
+    }
+
+    // ---- launch order: by tree level, a level's small contractions first (one
+    // batched launch), then its large ones in tree order
+    std::vector<int32_t> order;
+    for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) order.push_back(n_leaves + k);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        if (node[x].depth != node[y].depth) return node[x].depth < node[y].depth;
+        return (int)node[x].small > (int)node[y].small;
+    });
+
+    // pending batch of small contractions (one tree level)
+    std::vector<Plan::Patch> batch_patches;   // offsets relative to the batch's task array
+    std::vector<SmallTask> batch;
+    std::vector<int32_t> batch_nodes;
+    double batch_flop = 0, batch_bytes = 0;
+    auto release_children = [&](int32_t v) {
+        for (int32_t c : {node[v].a, node[v].b})
+            if (node[c].base == BASE_ARENA)
+                arena.release((size_t)node[c].buf_off, (size_t)node[c].n_inst * node[c].view.size * es);
+    };
+    auto flush_batch = [&]() {
+        if (batch.empty()) return;
+        int32_t blocks = 0;
+        for (auto &t : batch) {
+            t.block0 = blocks;
+            int64_t items = (int64_t)t.n_inst * t.n_out;
+            blocks += (int32_t)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 256));
+        }
+        // task records (their table pointers are patched like every other pointer)
+        size_t o_tasks = blob.reserve(sizeof(SmallTask) * batch.size(), 64);
+        for (size_t i = 0; i < batch.size(); ++i)
+            std::memcpy(blob.bytes.data() + o_tasks + i * sizeof(SmallTask), &batch[i], sizeof(SmallTask));
+        for (auto &pt : batch_patches) blob.patches.push_back({o_tasks + pt.at, pt.base, pt.byte_off});
+        SmallBatchArgs sb;
+        std::memset(&sb, 0, sizeof sb);
+        sb.n_tasks = (int32_t)batch.size();
+        sb.n_blocks = blocks;
+        size_t so = blob.reserve(sizeof sb);
+        std::memcpy(blob.bytes.data() + so, &sb, sizeof sb);
+        blob.patch_field(so, offsetof(SmallBatchArgs, tasks), BASE_BLOB, (int64_t)o_tasks);
+        Op op;
+        op.kind = OpKind::SmallBatch;
+        op.node = batch_nodes.front();
+        op.n_inst = (int64_t)batch.size();
+        op.args_off = so;
+        op.args_bytes = sizeof sb;
+        op.flop = batch_flop;
+        op.bytes = batch_bytes;
+        op.variant = fp64 ? 1 : 0;
+        op.grid_x = blocks;
+        P.ops.push_back(op);
+        for (int32_t v : batch_nodes) release_children(v);
+        batch.clear();
+        batch_nodes.clear();
+        batch_patches.clear();
+        batch_flop = batch_bytes = 0;
+    };
+
+    // ---- pass 2, launch order: arena offsets, pointer tables, launches
+    for (int32_t v : order) {
+        NodeInfo &N = node[v];
+        const int32_t a = N.a, b = N.b;
+        const NodeInfo &NA = node[a], &NB = node[b];
+        const View &VA = NA.view, &VB = NB.view;
+        const std::vector<int64_t> &K = N.K, &fa = N.fa, &fb = N.fb;
+        const int64_t nK = dimprod(K), nFa = dimprod(fa), nFb = dimprod(fb);
+        const bool use_gemm = N.use_gemm, a_big = N.a_big;
+        if (!N.small || (!batch_nodes.empty() && node[batch_nodes.front()].depth != N.depth)) flush_batch();
 
         // arena buffer for all instances
         size_t nbytes = (size_t)N.n_inst * N.view.size * es;
@@ -358,6 +436,68 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         P.flop_executed += flop;
         P.bytes_executed += bytes;
         P.n_instances += N.n_inst;
+
+        if (N.small) {
+            // full offset tables: out -> (offA, offB), summed -> (kA, kB)
+            ++P.n_direct;
+            auto strideOf = [&](const View &V, int64_t l) {
+                int p = find_pos(V.labels, l);
+                return p < 0 ? (int64_t)0 : V.strides[p];
+            };
+            const auto &C = N.view;
+            std::vector<int32_t> oA(C.size), oB(C.size), kA(nK), kB(nK);
+            for (int64_t o = 0; o < C.size; ++o) {
+                int64_t r = o, x = 0, y = 0;
+                for (int j = (int)C.labels.size() - 1; j >= 0; --j) {
+                    int64_t dg = r % C.dims[j];
+                    r /= C.dims[j];
+                    x += dg * strideOf(VA, C.labels[j]);
+                    y += dg * strideOf(VB, C.labels[j]);
+                }
+                oA[o] = (int32_t)x;
+                oB[o] = (int32_t)y;
+            }
+            // summed labels in the direct kernel's order (slowest first by stride in the
+            // larger operand), so both kernels add the terms in the same sequence
+            const View &VX = a_big ? VA : VB;
+            std::vector<int64_t> Ks = K;
+            std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) {
+                return strideOf(VX, x) > strideOf(VX, y);
+            });
+            std::vector<int64_t> Kd;
+            for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
+            for (int64_t q = 0; q < nK; ++q) {
+                int64_t r = q, x = 0, y = 0;
+                for (int j = (int)Ks.size() - 1; j >= 0; --j) {
+                    int64_t dg = r % Kd[j];
+                    r /= Kd[j];
+                    x += dg * strideOf(VA, Ks[j]);
+                    y += dg * strideOf(VB, Ks[j]);
+                }
+                kA[q] = (int32_t)x;
+                kB[q] = (int32_t)y;
+            }
+            SmallTask t;
+            std::memset(&t, 0, sizeof t);
+            t.n_out = (int32_t)C.size;
+            t.n_k = (int32_t)nK;
+            t.n_inst = (int32_t)N.n_inst;
+            const size_t i0 = batch.size() * sizeof(SmallTask);
+            size_t o_pa = blob.put_ptrs(pa), o_pb = blob.put_ptrs(pb), o_pc = blob.put_ptrs(pc);
+            size_t o_oa = blob.put_i32(oA), o_ob = blob.put_i32(oB), o_ka = blob.put_i32(kA), o_kb = blob.put_i32(kB);
+            batch_patches.push_back({i0 + offsetof(SmallTask, ptrA), BASE_BLOB, (int64_t)o_pa});
+            batch_patches.push_back({i0 + offsetof(SmallTask, ptrB), BASE_BLOB, (int64_t)o_pb});
+            batch_patches.push_back({i0 + offsetof(SmallTask, ptrC), BASE_BLOB, (int64_t)o_pc});
+            batch_patches.push_back({i0 + offsetof(SmallTask, offA), BASE_BLOB, (int64_t)o_oa});
+            batch_patches.push_back({i0 + offsetof(SmallTask, offB), BASE_BLOB, (int64_t)o_ob});
+            batch_patches.push_back({i0 + offsetof(SmallTask, kA), BASE_BLOB, (int64_t)o_ka});
+            batch_patches.push_back({i0 + offsetof(SmallTask, kB), BASE_BLOB, (int64_t)o_kb});
+            batch.push_back(t);
+            batch_nodes.push_back(v);
+            batch_flop += flop;
+            batch_bytes += bytes;
+            continue;   // children are released when the batch is issued
+        }
 
         std::vector<size_t> scratch;   // arena scratch freed after this node
         std::vector<size_t> scratch_bytes;
@@ -777,10 +917,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
 
         for (size_t s = 0; s < scratch.size(); ++s) arena.release(scratch[s], scratch_bytes[s]);
         // children are dead once this node's launches are issued
-        for (int32_t c : {a, b})
-            if (node[c].base == BASE_ARENA)
-                arena.release((size_t)node[c].buf_off, (size_t)node[c].n_inst * node[c].view.size * es);
+        release_children(v);
     }
+    flush_batch();
 
     // ---- slice / amplitude reduction (Eq. sliced_sum), FP64, slices in increasing order
     const int32_t root = n_nodes - 1;

@@ -42,7 +42,7 @@ class OpRecord(ctypes.Structure):
 
 
 OP_KINDS = {0: "direct", 1: "permute", 2: "gemm_simt", 3: "gemm_tc", 4: "slice_reduce", 5: "splitk_reduce",
-            6: "tc_split"}
+            6: "tc_split", 7: "small_batch"}
 
 
 class TensorDesc(ctypes.Structure):
@@ -106,7 +106,7 @@ def _check(rc: int):
         raise JetError(rc, lib().jet_last_error().decode())
 
 
-def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=64, profile=0) -> Options:
+def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=16, profile=0) -> Options:
     o = Options()
     lib().jet_options_default(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -204,8 +204,10 @@ class Network:
         return [int(x) for x in out[:n.value]]
 
     def _outputs(self, outputs) -> np.ndarray:
-        o = np.ascontiguousarray(np.asarray(outputs, dtype=np.int32).reshape(-1, self.n_out))
-        return o
+        o = np.asarray(outputs, dtype=np.int32)
+        if self.n_out == 0:   # closed network: one (empty) pattern per amplitude row
+            return np.zeros((o.shape[0] if o.ndim == 2 else 1, 0), np.int32)
+        return np.ascontiguousarray(o.reshape(-1, self.n_out))
 
     def plan(self, outputs) -> int:
         o = self._outputs(outputs)
