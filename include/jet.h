@@ -187,6 +187,19 @@ int jet_slice_auto(jet_network *net, int64_t max_elems, int32_t min_n, int32_t m
 int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs,
                  jet_c128 *amps_out, void *cuda_stream);
 
+/* Contract only the listed slices and return each one's partial contraction
+ * (the s_i of Eq. sliced_sum): partials_out[b * n_ids + j] is amplitude b's
+ * network with the sliced labels fixed to the digits of slice id slice_ids[j]
+ * (mixed radix, first sliced label most significant).  Intermediates shared by
+ * the listed slices are computed once.  Summing the partials of every slice in
+ * increasing id order gives jet_contract's amplitude; disjoint id ranges are
+ * how independent processes (one per GPU) split one amplitude's work.
+ * partials_out: n_amps * n_ids complex128 values of HOST memory; the call
+ * synchronises the stream.  Errors as jet_contract, plus JET_EINVAL (empty list
+ * or an id outside [0, number of slices)). */
+int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs, int32_t n_ids,
+                        const int64_t *slice_ids, jet_c128 *partials_out, void *cuda_stream);
+
 /* Same as jet_contract but amps_dev is DEVICE memory (n_amps complex128) and
  * the call returns without synchronising: the amplitudes are ready when work
  * issued on cuda_stream before the next call completes. */

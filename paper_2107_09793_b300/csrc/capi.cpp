@@ -48,17 +48,19 @@ static void invalidate_plan(Network &net)
     }
 }
 
-static Plan &get_plan(Network &net, int32_t n_amps, const int32_t *outputs)
+static Plan &get_plan(Network &net, int32_t n_amps, const int32_t *outputs,
+                      const std::vector<int64_t> *slice_ids = nullptr)
 {
-    if (!outputs) fail(JET_EINVAL, "outputs is NULL");
+    if (!outputs && !net.open.empty()) fail(JET_EINVAL, "outputs is NULL");
     const size_t n = (size_t)n_amps * net.open.size();
     Plan *P = net.plan.get();
     bool reuse = P && P->n_amps == n_amps && P->path_version == net.path_version &&
                  P->slice_version == net.slice_version && P->precision == net.opt.precision &&
                  P->reuse == net.opt.reuse && P->outputs.size() == n &&
-                 std::equal(P->outputs.begin(), P->outputs.end(), outputs);
+                 std::equal(P->outputs.begin(), P->outputs.end(), outputs) &&
+                 P->partials == (slice_ids != nullptr) && (!slice_ids || P->slice_ids == *slice_ids);
     if (!reuse) {
-        auto fresh = build_plan(net, n_amps, outputs);
+        auto fresh = build_plan(net, n_amps, outputs, slice_ids);
         invalidate_plan(net);
         net.plan = std::move(fresh);
     }
@@ -306,6 +308,21 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c
         Plan &P = get_plan(*net, n_amps, outputs);
         bind_and_run(*net, P, nullptr, cuda_stream);
         copy_d2h(amps_out, net->d_amps, (size_t)n_amps * sizeof(jet_c128), cuda_stream ? cuda_stream : net->stream);
+        if (read_clear_status(*net, cuda_stream))
+            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+    });
+}
+
+int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs, int32_t n_ids,
+                        const int64_t *slice_ids, jet_c128 *partials_out, void *cuda_stream)
+{
+    return guarded([&] {
+        if (!net || !partials_out || !slice_ids || n_ids < 1) fail(JET_EINVAL, "bad arguments");
+        std::vector<int64_t> ids(slice_ids, slice_ids + n_ids);
+        Plan &P = get_plan(*net, n_amps, outputs, &ids);
+        bind_and_run(*net, P, nullptr, cuda_stream);
+        copy_d2h(partials_out, net->d_amps, (size_t)n_amps * n_ids * sizeof(jet_c128),
+                 cuda_stream ? cuda_stream : net->stream);
         if (read_clear_status(*net, cuda_stream))
             fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
     });

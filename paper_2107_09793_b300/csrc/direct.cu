@@ -224,9 +224,22 @@ cudaError_t launch_small_batch(const SmallBatchArgs &a, const LaunchCfg &c, cuda
 // amp[b] = sum_{s = 0 .. n_sl-1} root(b, s), in FP64, one thread per amplitude.
 __global__ void slice_reduce_kernel(const __grid_constant__ ReduceArgs a)
 {
+    const uint64_t *roots = (const uint64_t *)a.roots;
+    if (a.partials) {   // per-slice partials, no summation
+        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= (int64_t)a.n_amps * a.n_slices) return;
+        const uint64_t p = roots[i];
+        double2 v;
+        if (a.fp64_in) v = *(const double2 *)p;
+        else {
+            const float2 f = *(const float2 *)p;
+            v = make_double2(f.x, f.y);
+        }
+        ((double2 *)a.amps)[i] = v;
+        return;
+    }
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.n_amps) return;
-    const uint64_t *roots = (const uint64_t *)a.roots;
     double re = 0, im = 0;
     for (int s = 0; s < a.n_slices; ++s) {
         uint64_t p = roots[(int64_t)b * a.n_slices + s];

@@ -265,12 +265,13 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream)
         }
         arena = net.own_arena;
     }
-    if (net.d_amps_cap < P.n_amps) {
+    const int64_t n_out_vals = P.partials ? (int64_t)P.n_amps * P.n_slices : P.n_amps;
+    if (net.d_amps_cap < n_out_vals) {
         JET_CUDA(cudaStreamSynchronize(s));
         device_free(net.d_amps);
         net.d_amps = nullptr;
-        net.d_amps = device_alloc((size_t)P.n_amps * sizeof(jet_c128));
-        net.d_amps_cap = P.n_amps;
+        net.d_amps = device_alloc((size_t)n_out_vals * sizeof(jet_c128));
+        net.d_amps_cap = n_out_vals;
     }
     void *leaves = net.opt.precision == JET_PREC_FP64 ? net.d_leaves64 : net.d_leaves;
 

@@ -5,16 +5,18 @@
 //   x = x_hi + x_lo (+ x_mid) in BF16 or TF32;  a*b ~ sum of the split terms
 //   whose magnitude is above the working precision (3 terms for a 2-way split,
 //   6 for BF16 3-way), accumulated in FP32.
-//   P = Ar.Br, Q = Ai.Bi, I = Ar.Bi + Ai.Br,  C = (P - Q) + i I.
+//   Re C = sum Ar.Br + (-Ai).Bi,  Im C = sum Ar.Bi + Ai.Br, each in one FP32
+//   accumulator, term by term (the negated product uses the instruction
+//   descriptor's negate-A bit).
 //
 // tc_split_kernel gathers a complex64 operand from any strides into K-major
 // padded planes (the transpose of Section 3.1 fused with the split).
-// tc_gemm_kernel: one 128x128 output tile per CTA; warp 0 issues TMA loads of
-// all planes of a K-block into a SWIZZLE_64B stage ring, warp 1 allocates TMEM
-// and one thread issues tcgen05.mma into three FP32 accumulators (3 x 128
-// TMEM columns), warps 2-5 read TMEM back and write complex64 C.  Every
-// mbarrier wait is bounded: on time-out the CTA records a status bit, frees
-// its TMEM and returns.
+// tc_gemm_kernel: persistent over 128x128 output tiles; warp 0 issues TMA
+// loads of all planes of a K-block into a SWIZZLE_64B stage ring, warp 1
+// allocates TMEM and one thread issues tcgen05.mma into 32-wide K chunks of
+// double-buffered TMEM accumulators, warps 2-9 add each chunk into FP32
+// registers and write complex64 C.  Every mbarrier wait is bounded: on
+// time-out the CTA records a status bit, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -29,7 +31,7 @@ constexpr int TC_BM = 128;          // tile rows (M) and tile columns (N)
 constexpr int TC_BN = 128;
 constexpr int TC_ROWB = 64;         // bytes of K per stage row (SWIZZLE_64B span)
 constexpr int TC_PLANE_TILE = TC_BM * TC_ROWB;   // 8 KiB per plane tile
-constexpr uint32_t TC_TMEM_COLS = 512;
+constexpr uint32_t TC_TMEM_COLS = 512;   // two chunk buffers x (Re 128 + Im 128 columns)
 
 template <int MODE>
 struct TcCfg;
@@ -279,30 +281,70 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const __grid_constant__ T
 }
 
 // ------------------------------------------------------------------ GEMM kernel
+// Persistent: CTA c handles tiles c, c + gridDim.x, ...  Roles (10 warps):
+//   warp 0     TMA producer (one thread): all planes of each K-block into the stage ring
+//   warp 1     TMEM owner; one thread issues the MMAs
+//   warps 2-9  promotion/epilogue: warp w owns TMEM lanes 32*(w%4).. and half the columns
+// The K range of a tile is cut into chunks of 32; each chunk accumulates into a
+// fresh TMEM buffer (two buffers alternate, 256 columns each: Re 128 + Im 128).
+// The epilogue warps add every finished chunk into FP32 registers (round to
+// nearest) and release the buffer; after the tile's last chunk they write C.
+// Restarting the tensor-core accumulator every 32 of K keeps the long sums as
+// accurate as an FP32 FMA chain.
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr int TC_GROUP_M = 8;   // tile rasterisation: groups of 8 M-tiles walk the N-tiles together
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tile_coords(int64_t t, int tiles_m, int tiles_n, int &inst, int &tm, int &tn)
+{
+    const int64_t per = (int64_t)tiles_m * tiles_n;
+    inst = (int)(t / per);
+    const int r = (int)(t - (int64_t)inst * per);
+    const int group = r / (TC_GROUP_M * tiles_n);
+    const int first_m = group * TC_GROUP_M;
+    const int gm = min(TC_GROUP_M, tiles_m - first_m);
+    const int idx = r - group * TC_GROUP_M * tiles_n;
+    tm = first_m + idx % gm;
+    tn = idx / gm;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__ TcGemmArgs a)
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcGemmArgs a)
 {
     using Cfg = TcCfg<MODE>;
     constexpr int NP = Cfg::NP, NPH = NP / 2, S = Cfg::STAGES;
     constexpr int STAGE_BYTES = 2 * NP * TC_PLANE_TILE;
     constexpr int KE = TC_ROWB / Cfg::EB;               // K elements per stage
     constexpr int KSUB = TC_ROWB / 32;                   // MMAs of 32 bytes of K per stage
+    constexpr int CHUNK_KB = 32 / KE > 0 ? 32 / KE : 1;  // stages per 32-wide K chunk
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2 * S + 1];
+    __shared__ __align__(8) uint64_t bars[2 * S + 4];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile_n = blockIdx.x, tile_m = blockIdx.y, inst = blockIdx.z;
-    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]), accb = smem_u32(&bars[2 * S]);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]);
+    const uint32_t tfull0 = smem_u32(&bars[2 * S]), tempty0 = smem_u32(&bars[2 * S + 2]);
+    const int tiles_m = (int)(a.m_pad / TC_BM), tiles_n = (int)(a.n_pad / TC_BN);
+    const int64_t total_tiles = (int64_t)a.n_inst * tiles_m * tiles_n;
+    const int n_kb = a.n_kb;
+    const int n_chunks = (n_kb + CHUNK_KB - 1) / CHUNK_KB;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, TC_EPI_WARPS);
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -315,90 +357,136 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
-    const int n_kb = a.n_kb;
 
     if (warp == 0) {
         if (lane == 0) {
-            const int zA = ((const int32_t *)a.zA)[inst], zB = ((const int32_t *)a.zB)[inst];
-            int issued = 0;
-            for (int kb = 0; kb < n_kb; ++kb) {
-                const int s = kb % S;
-                if (kb >= S && !mbar_wait_bounded(empty0 + 8 * s, ((kb / S) - 1) & 1, &abort_flag)) {
-                    abort_flag = 1;
-                    break;
+            int64_t kg = 0, issued = 0;
+            for (int64_t t = blockIdx.x; t < total_tiles && !abort_flag; t += gridDim.x) {
+                int inst, tm, tn;
+                tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
+                const int zA = ((const int32_t *)a.zA)[inst], zB = ((const int32_t *)a.zB)[inst];
+                for (int kb = 0; kb < n_kb; ++kb, ++kg) {
+                    const int s = (int)(kg % S);
+                    if (kg >= S && !mbar_wait_bounded(empty0 + 8 * s, (uint32_t)(((kg / S) - 1) & 1), &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                    mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+                    for (int p = 0; p < NP; ++p)
+                        tma_load_3d(st + p * TC_PLANE_TILE, &a.tmA, full0 + 8 * s, kb * KE, tm * TC_BM, zA + p);
+                    for (int p = 0; p < NP; ++p)
+                        tma_load_3d(st + (NP + p) * TC_PLANE_TILE, &a.tmB, full0 + 8 * s, kb * KE, tn * TC_BN, zB + p);
+                    issued = kg + 1;
                 }
-                const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
-                mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-                for (int p = 0; p < NP; ++p)
-                    tma_load_3d(st + p * TC_PLANE_TILE, &a.tmA, full0 + 8 * s, kb * KE, tile_m * TC_BM, zA + p);
-                for (int p = 0; p < NP; ++p)
-                    tma_load_3d(st + (NP + p) * TC_PLANE_TILE, &a.tmB, full0 + 8 * s, kb * KE, tile_n * TC_BN, zB + p);
-                issued = kb + 1;
             }
             if (abort_flag) {   // let copies already in flight land before the CTA exits
-                for (int kb = issued - S > 0 ? issued - S : 0; kb < issued; ++kb)
-                    mbar_wait_bounded(full0 + 8 * (kb % S), (kb / S) & 1, &abort_flag);
+                for (int64_t k = issued - S > 0 ? issued - S : 0; k < issued; ++k)
+                    mbar_wait_bounded(full0 + 8 * (int)(k % S), (uint32_t)((k / S) & 1), &abort_flag);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // kind::f16 / kind::tf32 instruction descriptor: FP32 D, K-major A and B, M=128, N=128
+            // kind::f16 / kind::tf32 instruction descriptor: FP32 D, K-major A and B, M=128, N=128;
+            // the negate-A variant accumulates (-Ai).Bi into the real part
             const uint32_t fmt = Cfg::KIND == 0 ? 1u : 2u;
             const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
-            const uint32_t dP = tmem, dQ = tmem + TC_BN, dI = tmem + 2 * TC_BN;
-            for (int kb = 0; kb < n_kb; ++kb) {
-                const int s = kb % S;
-                if (!mbar_wait_bounded(full0 + 8 * s, (kb / S) & 1, &abort_flag)) {
+            const uint32_t idesc_neg = idesc | (1u << 13);
+            int64_t kg = 0, cg = 0;
+            for (int64_t t = blockIdx.x; t < total_tiles && !abort_flag; t += gridDim.x) {
+                for (int c = 0; c < n_chunks && !abort_flag; ++c, ++cg) {
+                    const int buf = (int)(cg & 1);
+                    if (cg >= 2 && !mbar_wait_bounded(tempty0 + 8 * buf, (uint32_t)(((cg >> 1) - 1) & 1), &abort_flag)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t dR = tmem + buf * 2 * TC_BN, dI = dR + TC_BN;
+                    const int kb_end = min(n_kb, (c + 1) * CHUNK_KB);
+                    for (int kb = c * CHUNK_KB; kb < kb_end; ++kb, ++kg) {
+                        const int s = (int)(kg % S);
+                        if (!mbar_wait_bounded(full0 + 8 * s, (uint32_t)((kg / S) & 1), &abort_flag)) {
+                            abort_flag = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                        const bool first_kb = kb == c * CHUNK_KB;
+#pragma unroll
+                        for (int sub = 0; sub < KSUB; ++sub) {
+#pragma unroll
+                            for (int tt = 0; tt < Cfg::NT; ++tt) {
+                                int p, q;
+                                Cfg::term(tt, p, q);
+                                const uint64_t aRe = sdesc(st + p * TC_PLANE_TILE + sub * 32);
+                                const uint64_t aIm = sdesc(st + (NPH + p) * TC_PLANE_TILE + sub * 32);
+                                const uint64_t bRe = sdesc(st + (NP + q) * TC_PLANE_TILE + sub * 32);
+                                const uint64_t bIm = sdesc(st + (NP + NPH + q) * TC_PLANE_TILE + sub * 32);
+                                const uint32_t acc = (!first_kb || sub || tt) ? 1u : 0u;
+                                umma<Cfg::KIND>(dR, aRe, bRe, idesc, acc);
+                                umma<Cfg::KIND>(dR, aIm, bIm, idesc_neg, 1u);
+                                umma<Cfg::KIND>(dI, aRe, bIm, idesc, acc);
+                                umma<Cfg::KIND>(dI, aIm, bRe, idesc, 1u);
+                            }
+                        }
+                        umma_commit(empty0 + 8 * s);
+                    }
+                    umma_commit(tfull0 + 8 * buf);
+                }
+            }
+        }
+    } else {
+        // promotion + epilogue: rows 32*(warp%4) + lane, columns half*64 .. +63 of the tile
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        int64_t cg = 0;
+        for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+            int inst, tm, tn;
+            tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
+            float racc[64], iacc[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) racc[j] = iacc[j] = 0.f;
+            bool ok = !abort_flag;
+            for (int c = 0; c < n_chunks && ok; ++c, ++cg) {
+                const int buf = (int)(cg & 1);
+                if (!mbar_wait_bounded(tfull0 + 8 * buf, (uint32_t)((cg >> 1) & 1), &abort_flag)) {
                     abort_flag = 1;
+                    ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
+                const uint32_t base = tmem + buf * 2 * TC_BN + ((uint32_t)(quarter * 32) << 16) + half * 64;
 #pragma unroll
-                for (int sub = 0; sub < KSUB; ++sub) {
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t R[32], I[32];
+                    JET_TMEM_LD32(base + h * 32, R);
+                    JET_TMEM_LD32(base + TC_BN + h * 32, I);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int t = 0; t < Cfg::NT; ++t) {
-                        int p, q;
-                        Cfg::term(t, p, q);
-                        const uint64_t aRe = sdesc(st + p * TC_PLANE_TILE + sub * 32);
-                        const uint64_t aIm = sdesc(st + (NPH + p) * TC_PLANE_TILE + sub * 32);
-                        const uint64_t bRe = sdesc(st + (NP + q) * TC_PLANE_TILE + sub * 32);
-                        const uint64_t bIm = sdesc(st + (NP + NPH + q) * TC_PLANE_TILE + sub * 32);
-                        const uint32_t acc = (kb | sub | t) ? 1u : 0u;
-                        umma<Cfg::KIND>(dP, aRe, bRe, idesc, acc);
-                        umma<Cfg::KIND>(dQ, aIm, bIm, idesc, acc);
-                        umma<Cfg::KIND>(dI, aRe, bIm, idesc, acc);
-                        umma<Cfg::KIND>(dI, aIm, bRe, idesc, 1u);
+                    for (int j = 0; j < 32; ++j) {
+                        racc[h * 32 + j] += __uint_as_float(R[j]);
+                        iacc[h * 32 + j] += __uint_as_float(I[j]);
                     }
                 }
-                umma_commit(empty0 + 8 * s);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
             }
-            umma_commit(accb);
-        }
-    } else {
-        // epilogue warps 2..5: warp w reads TMEM lanes 32*(w%4) .. +31
-        const bool ok = mbar_wait_bounded(accb, 0, &abort_flag);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok) abort_flag = 1;
-        const int quarter = warp & 3;
-        const int64_t row = (int64_t)tile_m * TC_BM + quarter * 32 + lane;
-        float2 *C = (float2 *)((const uint64_t *)a.ptrC)[inst];
-        const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16);
-#pragma unroll 1
-        for (int chunk = 0; chunk < TC_BN / 32; ++chunk) {
-            uint32_t P[32], Q[32], I[32];
-            JET_TMEM_LD32(lane_addr + chunk * 32, P);
-            JET_TMEM_LD32(lane_addr + TC_BN + chunk * 32, Q);
-            JET_TMEM_LD32(lane_addr + 2 * TC_BN + chunk * 32, I);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (ok && row < a.M) {
-                const int64_t col0 = (int64_t)tile_n * TC_BN + chunk * 32;
+            if (!ok) break;
+            const int64_t row = (int64_t)tm * TC_BM + quarter * 32 + lane;
+            if (row < a.M) {
+                float2 *C = (float2 *)((const uint64_t *)a.ptrC)[inst];
+                const int64_t col0 = (int64_t)tn * TC_BN + half * 64;
                 float2 *dst = C + row * a.N + col0;
+                if ((a.N & 1) == 0 && col0 + 64 <= a.N) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (col0 + j < a.N)
-                        dst[j] = make_float2(__uint_as_float(P[j]) - __uint_as_float(Q[j]), __uint_as_float(I[j]));
+                    for (int j = 0; j < 64; j += 2)
+                        *(float4 *)(dst + j) = make_float4(racc[j], iacc[j], racc[j + 1], iacc[j + 1]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 64; ++j)
+                        if (col0 + j < a.N) dst[j] = make_float2(racc[j], iacc[j]);
+                }
             }
         }
     }
@@ -460,21 +548,33 @@ cudaError_t launch_tc_split(const TcSplitArgs &a, const LaunchCfg &c, cudaStream
     return cudaGetLastError();
 }
 
+static int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            n = 148;
+    }
+    return n;
+}
+
 cudaError_t launch_tc_gemm(const TcGemmArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    dim3 grid(c.gx, c.gy, c.gz);
+    const int64_t tiles = (int64_t)c.gx * c.gy * c.gz;   // persistent: one CTA per SM at most
+    dim3 grid((unsigned)std::min<int64_t>(tiles, sm_count()), 1, 1);
     switch (a.mode) {
     case JET_PREC_TF32:
-        tc_gemm_kernel<JET_PREC_TF32><<<grid, 192, tc_smem_bytes<JET_PREC_TF32>(), s>>>(a);
+        tc_gemm_kernel<JET_PREC_TF32><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_TF32>(), s>>>(a);
         break;
     case JET_PREC_TF32X3:
-        tc_gemm_kernel<JET_PREC_TF32X3><<<grid, 192, tc_smem_bytes<JET_PREC_TF32X3>(), s>>>(a);
+        tc_gemm_kernel<JET_PREC_TF32X3><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_TF32X3>(), s>>>(a);
         break;
     case JET_PREC_BF16X3:
-        tc_gemm_kernel<JET_PREC_BF16X3><<<grid, 192, tc_smem_bytes<JET_PREC_BF16X3>(), s>>>(a);
+        tc_gemm_kernel<JET_PREC_BF16X3><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_BF16X3>(), s>>>(a);
         break;
     case JET_PREC_BF16X6:
-        tc_gemm_kernel<JET_PREC_BF16X6><<<grid, 192, tc_smem_bytes<JET_PREC_BF16X6>(), s>>>(a);
+        tc_gemm_kernel<JET_PREC_BF16X6><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_BF16X6>(), s>>>(a);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -78,6 +78,8 @@ struct Plan {
     uint64_t slice_version = 0;
     int32_t precision = 0;
     int32_t reuse = 1;
+    std::vector<int64_t> slice_ids;  // listed slices only (partials mode), else all
+    bool partials = false;
 
     // sizes
     int64_t n_slices = 1;
@@ -151,7 +153,8 @@ double reuse_aware_flop(const Network &net, const std::vector<std::pair<int32_t,
 void validate_path(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path);
 
 // plan.cpp
-std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs);
+std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs,
+                                 const std::vector<int64_t> *slice_ids = nullptr);
 
 // exec.cu
 void ensure_leaves_on_device(Network &net);

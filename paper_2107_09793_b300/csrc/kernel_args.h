@@ -79,7 +79,8 @@ struct SmallBatchArgs {
 // (Section 2.4, Eq. sliced_sum; the single reduction over slices).
 struct ReduceArgs {
     uint64_t roots;                 // device array of n_amps * n_slices addresses of scalars
-    uint64_t amps;                  // complex128[n_amps]
+    uint64_t amps;                  // complex128[n_amps] (or [n_amps][n_slices] partials)
     int32_t n_amps, n_slices;
-    int32_t fp64_in, pad_;
+    int32_t fp64_in;
+    int32_t partials;               // 1: write every root value instead of the sums
 };

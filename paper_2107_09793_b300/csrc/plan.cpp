@@ -155,7 +155,8 @@ int tc_elem_bytes(int mode);
 int tc_k_block(int mode);
 int tc_tile();
 
-std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs)
+std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs,
+                                 const std::vector<int64_t> *slice_ids)
 {
     if (net.path.size() + 1 != net.leaves.size()) fail(JET_ESTATE, "no contraction path set");
     if (!net.open_set) fail(JET_ESTATE, "open legs not declared (jet_network_set_open)");
@@ -189,7 +190,17 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     }
     sl_w.assign(sl_dim.size(), 1);
     for (int j = (int)sl_dim.size() - 2; j >= 0; --j) sl_w[j] = sl_w[j + 1] * sl_dim[j + 1];
-    const int64_t n_sl = prod(sl_dim);
+    // all slices, or only the listed slice ids (per-slice partials, Eq. sliced_sum's s_i)
+    const int64_t n_sl_all = prod(sl_dim);
+    if (slice_ids) {
+        if (slice_ids->empty()) fail(JET_EINVAL, "empty slice-id list");
+        for (int64_t sid : *slice_ids)
+            if (sid < 0 || sid >= n_sl_all)
+                fail(JET_EINVAL, "slice id " + std::to_string(sid) + " out of range [0, " + std::to_string(n_sl_all) + ")");
+        P.slice_ids = *slice_ids;
+        P.partials = true;
+    }
+    const int64_t n_sl = slice_ids ? (int64_t)slice_ids->size() : n_sl_all;
     P.n_slices = n_sl;
     const int64_t n_assign = (int64_t)n_amps * n_sl;
     if (n_assign > (int64_t)1 << 30) fail(JET_EINVAL, "too many (amplitude, slice) assignments");
@@ -197,6 +208,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         auto o = open_pos.find(l);
         int64_t b = alpha / n_sl, s = alpha % n_sl;
         if (o != open_pos.end()) return outputs[b * n_open + o->second];
+        if (slice_ids) s = (*slice_ids)[s];
         int32_t j = slice_pos.at(l);
         return (s / sl_w[j]) % sl_dim[j];
     };
@@ -933,6 +945,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         std::memset(&r, 0, sizeof r);
         r.n_amps = n_amps;
         r.n_slices = (int32_t)n_sl;
+        r.partials = P.partials ? 1 : 0;
         r.fp64_in = fp64 ? 1 : 0;
         size_t ro = blob.reserve(sizeof r);
         std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
@@ -944,7 +957,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         op.n_inst = n_amps;
         op.args_off = ro;
         op.args_bytes = sizeof r;
-        op.grid_x = (n_amps + 127) / 128;
+        op.grid_x = (int32_t)(((P.partials ? n_assign : n_amps) + 127) / 128);
         op.block = 128;
         P.ops.push_back(op);
     }

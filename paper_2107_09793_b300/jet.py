@@ -20,7 +20,8 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_tensors_upload", "jet_network_n_values", "jet_path_set", "jet_path_get",
            "jet_path_greedy", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
-           "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc"]
+           "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
+           "jet_contract_slices"]
 
 
 class JetError(RuntimeError):
@@ -84,6 +85,7 @@ def lib():
             "jet_slice_auto": (I32, [P, I64, I32, I32, P, P]),
             "jet_contract": (I32, [P, I32, P, P, P]),
             "jet_contract_async": (I32, [P, I32, P, P, P]),
+            "jet_contract_slices": (I32, [P, I32, P, I32, P, P, P]),
             "jet_plan": (I32, [P, I32, P, P]),
             "jet_set_workspace": (I32, [P, P, ctypes.c_size_t]),
             "jet_contract_grad": (I32, [P, I32, P, P, I32, P, P, P, P]),
@@ -223,6 +225,15 @@ class Network:
         amps = np.zeros(o.shape[0], dtype=np.complex128)
         _check(lib().jet_contract(self._h, o.shape[0], o.ctypes.data, amps.ctypes.data, ctypes.c_void_p(stream)))
         return amps
+
+    def contract_slices(self, outputs, slice_ids, stream: int = 0) -> np.ndarray:
+        """Per-slice partials, shape (n_amps, len(slice_ids))."""
+        o = self._outputs(outputs)
+        ids = np.ascontiguousarray(np.asarray(slice_ids, dtype=np.int64))
+        out = np.zeros((o.shape[0], ids.size), dtype=np.complex128)
+        _check(lib().jet_contract_slices(self._h, o.shape[0], o.ctypes.data, ids.size, ids.ctypes.data,
+                                         out.ctypes.data, ctypes.c_void_p(stream)))
+        return out
 
     def contract_async(self, outputs, amps_dev_ptr: int, stream: int = 0):
         o = self._outputs(outputs)

@@ -164,3 +164,14 @@ def test_workspace_plan_is_host_only():
     net.path_greedy(seed=1, n_trials=2)
     nbytes = net.plan(w.outputs)
     assert nbytes >= 256 and nbytes % 256 == 0
+
+
+def test_contract_slices_rejects_bad_ids_before_any_device_work():
+    w, net = _net()
+    net.path_greedy(seed=1, n_trials=2)
+    net.slice_auto(1 << 8, min_n=2, max_n=12)
+    nsl = net.stats()["n_slices"]
+    for bad in ([nsl], [-1], []):
+        with pytest.raises(jet.JetError) as e:
+            net.contract_slices(w.outputs, bad)
+        assert e.value.code == jet.JET_EINVAL
