@@ -296,29 +296,33 @@ def run_impl(args):
         b["gb_s"] = b["bytes"] / (b["ms"] * 1e-3) / 1e9 if b["ms"] > 0 else None
     nprof.close()
 
-    # same plan on CUDA cores (FP32), the comparison path
-    fp32 = None
-    if not args.skip_fp32 and args.precision != "fp32":
-        n32 = jet.from_network(w.network, precision="fp32", device=dev)
-        n32.path_set(path)
-        n32.slice(sliced)
-        a32 = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
-        for _ in range(2):
-            n32.contract_async(outs, a32.data_ptr(), sh)
-        torch.cuda.synchronize()
-        k32 = max(2, min(args.steps, 5))
-        ms32 = []
-        for _ in range(k32):
-            flush.zero_()
-            ev0.record(stream)
-            n32.contract_async(outs, a32.data_ptr(), sh)
-            ev1.record(stream)
-            ev1.synchronize()
-            ms32.append(ev0.elapsed_time(ev1))
-        fp32 = {"value": 1000.0 / statistics.mean(ms32), "unit": "amplitudes/s", "ms_per_step": statistics.mean(ms32),
-                "tflops": st["flop_executed"] / (statistics.mean(ms32) * 1e-3) / 1e12,
-                "amp": [complex(a32[0].item()).real, complex(a32[0].item()).imag]}
-        n32.close()
+    # the same plan in the other arithmetic modes: FP32 CUDA cores (the plain
+    # reference path) and the other tensor-core splits, each with its error
+    modes = {}
+    if not args.skip_fp32:
+        for prec in [m for m in ("fp32", "bf16x3", "tf32x3", "bf16x6") if m != args.precision]:
+            nm = jet.from_network(w.network, precision=prec, device=dev)
+            nm.path_set(path)
+            nm.slice(sliced)
+            am = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+            for _ in range(2):
+                nm.contract_async(outs, am.data_ptr(), sh)
+            torch.cuda.synchronize()
+            km = max(2, min(args.steps, 5))
+            msm = []
+            for _ in range(km):
+                flush.zero_()
+                ev0.record(stream)
+                nm.contract_async(outs, am.data_ptr(), sh)
+                ev1.record(stream)
+                ev1.synchronize()
+                msm.append(ev0.elapsed_time(ev1))
+            amp_m = complex(am[0].item())
+            modes[prec] = {"value": 1000.0 / statistics.mean(msm), "unit": "amplitudes/s",
+                           "ms_per_step": statistics.mean(msm),
+                           "tflops": st["flop_executed"] / (statistics.mean(msm) * 1e-3) / 1e12,
+                           "amp": [amp_m.real, amp_m.imag]}
+            nm.close()
 
     # end to end through the C ABI: pinned host inputs -> device, contract, amplitude back to host
     nv = net.n_values()
@@ -343,10 +347,10 @@ def run_impl(args):
     g_amp, g_out = golden_amplitude()
     err = None
     if g_amp is not None and list(g_out) == list(map(int, outs[0])):
-        err = {"split": abs(amp - g_amp) / abs(g_amp)}
-        if fp32:
-            a32 = complex(*fp32["amp"])
-            err["fp32"] = abs(a32 - g_amp) / abs(g_amp)
+        err = {args.precision: abs(amp - g_amp) / abs(g_amp)}
+        for prec, m in modes.items():
+            m["rel_err_vs_oracle"] = abs(complex(*m["amp"]) - g_amp) / abs(g_amp)
+            err[prec] = m["rel_err_vs_oracle"]
     cpu = None
     if world == 1 and not args.skip_cpu:
         cpu, _ = oracle_slice_sample(w, sliced, st["n_slices"], outs)
@@ -363,7 +367,7 @@ def run_impl(args):
         "flop_per_step": st["flop_executed"], "flop_no_reuse": st["flop_sliced"],
         "reuse_fraction": st["reuse_fraction"], "workspace_gb": st["workspace_bytes"] / 1e9,
         "amplitude": [amp.real, amp.imag], "rel_err_vs_oracle": err,
-        "fp32_simt": fp32, "roofline": roof, "breakdown": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "fp32_simt": modes.get("fp32"), "modes": modes, "roofline": roof, "breakdown": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(st["n_launches"]) * args.steps,
         "wall_s_timed": t_wall1 - t_wall0,
     }
@@ -420,9 +424,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jet", choices=["jet", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--precision", default="bf16x6", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
-    ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
     ap.add_argument("--case", default="workload", choices=["workload", "gemm"],
                     help="gemm: a single complex GEMM node sized for ncu captures")
     args = ap.parse_args()
