@@ -220,10 +220,15 @@ int jet_set_workspace(jet_network *net, void *dptr, size_t bytes);
  * (holomorphic: G is not conjugated; env_G has G's shape and layout).
  * For loss = sum_b |amp_b|^2 pass cot_b = conj(amp_b); then
  * d loss / d theta = 2 Re sum_G <env_G, dG/dtheta>, <X,Y> = sum_i X_i Y_i.
- * Per slice the forward tree is recomputed (no intermediates are kept across
- * slices).  env_out[i] points to prod(dims) complex64 values of HOST memory for
- * tensor tensor_ids[i]; amps_out (may be NULL) receives the amplitudes.
- * Errors as jet_contract, plus JET_EINVAL (bad tensor id). */
+ * Slice by slice the forward tree is recomputed (intermediates shared by the
+ * amplitudes of the batch are computed once; nothing is kept across slices),
+ * then swept backwards: for C = sum_K A B, env(A) = env(C) contracted with B
+ * over B's free labels.  Environments accumulate over slices in FP64.
+ * env_out[i] points to prod(dims) complex64 values of HOST memory for tensor
+ * tensor_ids[i]; amps_out (may be NULL) receives the amplitudes.  Runs the
+ * launches eagerly on cuda_stream and synchronises it.
+ * Errors as jet_contract, plus JET_EINVAL (bad or repeated tensor id,
+ * a network of one tensor). */
 int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs,
                       const jet_c128 *cot, int32_t n_req, const int32_t *tensor_ids,
                       jet_c64 *const *env_out, jet_c128 *amps_out, void *cuda_stream);

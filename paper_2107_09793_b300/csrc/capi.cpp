@@ -333,9 +333,71 @@ int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs, 
                       void *cuda_stream)
 {
     return guarded([&] {
-        (void)net; (void)n_amps; (void)outputs; (void)cot; (void)n_req; (void)tensor_ids;
-        (void)env_out; (void)amps_out; (void)cuda_stream;
-        fail(JET_ESTATE, "jet_contract_grad: not available in this build");
+        if (!net || !cot || n_amps < 1 || n_req < 0 || (n_req > 0 && (!tensor_ids || !env_out)))
+            fail(JET_EINVAL, "bad arguments");
+        if (net->path.size() + 1 != net->leaves.size()) fail(JET_ESTATE, "no contraction path set");
+        GradRequest g;
+        g.cot.resize(2 * (size_t)n_amps);
+        for (int32_t b = 0; b < n_amps; ++b) {
+            g.cot[2 * b] = cot[b].re;
+            g.cot[2 * b + 1] = cot[b].im;
+        }
+        g.env_off.assign(net->leaves.size(), -1);
+        int64_t total = 0;
+        for (int32_t i = 0; i < n_req; ++i) {
+            const int32_t id = tensor_ids[i];
+            if (id < 0 || id >= (int32_t)net->leaves.size()) fail(JET_EINVAL, "bad tensor id " + std::to_string(id));
+            if (g.env_off[id] >= 0) fail(JET_EINVAL, "tensor id requested twice");
+            if (!env_out[i]) fail(JET_EINVAL, "NULL environment buffer");
+            g.env_off[id] = total;
+            total += net->leaves[id].size;
+            g.leaves.push_back(id);
+        }
+        {   // plan the first slice on the host before any device work (argument errors surface here)
+            std::vector<int64_t> first{0};
+            build_plan(*net, n_amps, outputs, &first, &g);
+        }
+        ensure_leaves_on_device(*net);
+        void *s = cuda_stream ? cuda_stream : net->stream;
+        if (net->d_env_cap < std::max<int64_t>(total, 1)) {
+            device_free(net->d_env);
+            net->d_env = nullptr;
+            net->d_env = device_alloc((size_t)std::max<int64_t>(total, 1) * sizeof(jet_c128));
+            net->d_env_cap = std::max<int64_t>(total, 1);
+        }
+        device_memset_async(net->d_env, (size_t)std::max<int64_t>(total, 1) * sizeof(jet_c128), s);
+        int64_t n_sl = 1;
+        for (int64_t l : net->sliced) n_sl *= net->labels.at(l).dim;
+        // per slice: recompute the forward tree (shared work reused across the
+        // amplitudes, not across slices), sweep it backwards, accumulate in FP64
+        std::vector<double> amps(2 * (size_t)n_amps, 0.0);
+        std::vector<jet_c128> part(n_amps);
+        for (int64_t sl = 0; sl < n_sl; ++sl) {
+            std::vector<int64_t> ids{sl};
+            auto P = build_plan(*net, n_amps, outputs, &ids, &g);
+            try {
+                bind_and_run(*net, *P, nullptr, cuda_stream, false);
+                copy_d2h(part.data(), net->d_amps, (size_t)n_amps * sizeof(jet_c128), s);
+            } catch (...) {
+                release_plan_device(*P);
+                throw;
+            }
+            release_plan_device(*P);
+            for (int32_t b = 0; b < n_amps; ++b) {
+                amps[2 * b] += part[b].re;
+                amps[2 * b + 1] += part[b].im;
+            }
+            if (read_clear_status(*net, cuda_stream))
+                fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+        }
+        std::vector<jet_c128> env((size_t)std::max<int64_t>(total, 1));
+        copy_d2h(env.data(), net->d_env, (size_t)std::max<int64_t>(total, 1) * sizeof(jet_c128), s);
+        for (int32_t i = 0; i < n_req; ++i) {
+            const int64_t off = g.env_off[tensor_ids[i]], n = net->leaves[tensor_ids[i]].size;
+            for (int64_t e = 0; e < n; ++e) env_out[i][e] = {(float)env[off + e].re, (float)env[off + e].im};
+        }
+        if (amps_out)
+            for (int32_t b = 0; b < n_amps; ++b) amps_out[b] = {amps[2 * b], amps[2 * b + 1]};
     });
 }
 

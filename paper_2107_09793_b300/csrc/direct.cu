@@ -221,6 +221,43 @@ cudaError_t launch_small_batch(const SmallBatchArgs &a, const LaunchCfg &c, cuda
     return cudaGetLastError();
 }
 
+template <typename VS, typename VT>
+__global__ void __launch_bounds__(256) accum_kernel(const __grid_constant__ AccumArgs a)
+{
+    const int32_t *ptr = (const int32_t *)a.csr_ptr, *src = (const int32_t *)a.csr_src;
+    const uint64_t *tgt = (const uint64_t *)a.tgt;
+    const VS *S = (const VS *)a.src;
+    const int64_t total = (int64_t)a.n_tgt * a.n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = idx / a.n, e = idx - t * a.n;
+        int64_t r = e, off = 0;
+        for (int j = 0; j < a.rank; ++j) {
+            const int64_t q = r / a.dim[j];
+            off += (r - q * a.dim[j]) * a.tstride[j];
+            r = q;
+        }
+        VT acc = vzero<VT>();
+        for (int p = ptr[t]; p < ptr[t + 1]; ++p) {
+            const VS v = S[(int64_t)src[p] * a.n + e];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        VT *d = (VT *)tgt[t] + off;
+        VT cur = *d;
+        cur.x += acc.x;
+        cur.y += acc.y;
+        *d = cur;
+    }
+}
+
+cudaError_t launch_accum(const AccumArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    if (a.src_fp64 && a.tgt_fp64) accum_kernel<double2, double2><<<c.gx, 256, 0, s>>>(a);
+    else if (a.tgt_fp64) accum_kernel<float2, double2><<<c.gx, 256, 0, s>>>(a);
+    else accum_kernel<float2, float2><<<c.gx, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // amp[b] = sum_{s = 0 .. n_sl-1} root(b, s), in FP64, one thread per amplitude.
 __global__ void slice_reduce_kernel(const __grid_constant__ ReduceArgs a)
 {

@@ -110,6 +110,11 @@ void copy_d2h(void *dst, const void *src, size_t bytes, void *stream)
     JET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
 }
 
+void device_memset_async(void *dst, size_t bytes, void *stream)
+{
+    JET_CUDA(cudaMemsetAsync(dst, 0, bytes, (cudaStream_t)stream));
+}
+
 void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream)
 {
     JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
@@ -170,6 +175,9 @@ void free_network_device(Network &net)
     device_free(net.d_amps);
     device_free(net.d_status);
     net.d_status = nullptr;
+    device_free(net.d_env);
+    net.d_env = nullptr;
+    net.d_env_cap = 0;
     if (net.stream) cudaStreamDestroy((cudaStream_t)net.stream);
     net.d_leaves = net.d_leaves64 = net.own_arena = net.d_amps = nullptr;
     net.stream = nullptr;
@@ -198,6 +206,18 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
         SmallBatchArgs a;
         std::memcpy(&a, p, sizeof a);
         e = launch_small_batch(a, c, s);
+        break;
+    }
+    case OpKind::Accum: {
+        AccumArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_accum(a, c, s);
+        break;
+    }
+    case OpKind::Memset: {
+        MemsetArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = cudaMemsetAsync((void *)a.ptr, 0, (size_t)a.bytes, s);
         break;
     }
     case OpKind::Permute: {
@@ -242,7 +262,7 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
     (void)P;
 }
 
-void bind_and_run(Network &net, Plan &P, void *, void *stream)
+void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
 {
     ensure_leaves_on_device(net);
     cudaStream_t s = stream ? (cudaStream_t)stream : (cudaStream_t)net.stream;
@@ -289,8 +309,8 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream)
             P.d_args = device_alloc(P.host_args.size());
             P.d_args_bytes = P.host_args.size();
         }
-        uintptr_t bases[5] = {(uintptr_t)leaves, (uintptr_t)arena, (uintptr_t)P.d_args, (uintptr_t)net.d_amps,
-                              (uintptr_t)net.d_status};
+        uintptr_t bases[6] = {(uintptr_t)leaves, (uintptr_t)arena, (uintptr_t)P.d_args, (uintptr_t)net.d_amps,
+                              (uintptr_t)net.d_status, (uintptr_t)net.d_env};
         for (const auto &pt : P.patches) {
             uint64_t v = (uint64_t)(bases[pt.base] + (uintptr_t)pt.byte_off);
             std::memcpy(P.host_args.data() + pt.at, &v, 8);
@@ -345,7 +365,7 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream)
         }
     };
 
-    if (net.opt.use_graph) {
+    if (net.opt.use_graph && allow_graph) {
         if (!P.graph_exec) {
             if (P.graph_exec) {
                 cudaGraphExecDestroy((cudaGraphExec_t)P.graph_exec);

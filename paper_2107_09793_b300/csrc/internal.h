@@ -53,7 +53,7 @@ struct PathCost {
 };
 
 // -------------------------------------------------------------- plan / ops
-enum class OpKind : int32_t { Direct = 0, Permute = 1, GemmSimt = 2, GemmTc = 3, Reduce = 4, SplitKReduce = 5, TcSplit = 6, SmallBatch = 7 };
+enum class OpKind : int32_t { Direct = 0, Permute = 1, GemmSimt = 2, GemmTc = 3, Reduce = 4, SplitKReduce = 5, TcSplit = 6, SmallBatch = 7, Accum = 8, Memset = 9 };
 
 struct Op {
     OpKind kind;
@@ -69,6 +69,15 @@ struct Op {
 };
 
 struct Network;
+
+// What an adjoint plan needs besides the forward plan: the cotangent of every
+// amplitude and, per input tensor, where its FP64 environment accumulates
+// (complex128 element offset in the environment buffer, -1 = not requested).
+struct GradRequest {
+    std::vector<double> cot;          // 2 * n_amps (re, im)
+    std::vector<int64_t> env_off;     // per tensor id
+    std::vector<int32_t> leaves;      // requested tensor ids
+};
 
 struct Plan {
     // key
@@ -135,6 +144,8 @@ struct Network {
     size_t user_arena_bytes = 0;
     void *d_amps = nullptr;          // device amplitude buffer (complex128)
     void *d_status = nullptr;        // device status word (bounded-wait time-outs)
+    void *d_env = nullptr;           // complex128 environments of requested tensors (adjoint)
+    int64_t d_env_cap = 0;
     int64_t d_amps_cap = 0;
 
     // planner results
@@ -154,11 +165,12 @@ void validate_path(const Network &net, const std::vector<std::pair<int32_t, int3
 
 // plan.cpp
 std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs,
-                                 const std::vector<int64_t> *slice_ids = nullptr);
+                                 const std::vector<int64_t> *slice_ids = nullptr,
+                                 const GradRequest *grad = nullptr);
 
 // exec.cu
 void ensure_leaves_on_device(Network &net);
-void bind_and_run(Network &net, Plan &plan, void *amps_dev, void *stream);
+void bind_and_run(Network &net, Plan &plan, void *amps_dev, void *stream, bool allow_graph = true);
 void release_plan_device(Plan &plan);
 void free_network_device(Network &net);
 void upload_leaf(Network &net, int32_t tensor_id, void *stream);
@@ -167,6 +179,7 @@ void *device_alloc(size_t bytes);
 void device_free(void *p);
 void copy_d2h(void *dst, const void *src, size_t bytes, void *stream);
 void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream);
+void device_memset_async(void *dst, size_t bytes, void *stream);
 bool gemm_available(int32_t precision);
 int read_clear_status(Network &net, void *stream);
 float op_elapsed_ms(const Plan &plan, size_t i);

@@ -75,6 +75,26 @@ struct SmallBatchArgs {
     int32_t n_tasks, n_blocks;
 };
 
+// Adjoint accumulation: for each target instance t, env_t[off(e)] += sum over the
+// source instances i mapped to t (ascending i) of src_i[e]; e runs over the
+// dense source layout, off(e) decodes it with the target's strides.
+struct AccumArgs {
+    uint64_t src;                   // source base; instance i at src + i * n elements
+    uint64_t tgt;                   // device array of n_tgt target addresses
+    uint64_t csr_ptr, csr_src;      // int32[n_tgt + 1], int32[n_src]
+    int64_t n;                      // elements per source instance
+    int32_t n_tgt, rank;
+    int32_t src_fp64, tgt_fp64;
+    int64_t dim[JET_MAXR];          // source labels, fastest first
+    int64_t tstride[JET_MAXR];      // matching target strides
+};
+
+// cudaMemsetAsync(ptr, 0, bytes) as a plan step.
+struct MemsetArgs {
+    uint64_t ptr;
+    int64_t bytes;
+};
+
 // amp[b] = sum over slices s (increasing s) of root[inst(b, s)], FP64
 // (Section 2.4, Eq. sliced_sum; the single reduction over slices).
 struct ReduceArgs {

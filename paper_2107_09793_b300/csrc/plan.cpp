@@ -28,7 +28,7 @@ namespace jet {
 
 namespace {
 
-enum Base : int32_t { BASE_LEAVES = 0, BASE_ARENA = 1, BASE_BLOB = 2, BASE_AMPS = 3, BASE_STATUS = 4 };
+enum Base : int32_t { BASE_LEAVES = 0, BASE_ARENA = 1, BASE_BLOB = 2, BASE_AMPS = 3, BASE_STATUS = 4, BASE_ENV = 5 };
 
 struct View {
     std::vector<int64_t> labels;   // layout order, slowest first
@@ -156,7 +156,7 @@ int tc_k_block(int mode);
 int tc_tile();
 
 std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs,
-                                 const std::vector<int64_t> *slice_ids)
+                                 const std::vector<int64_t> *slice_ids, const GradRequest *grad)
 {
     if (net.path.size() + 1 != net.leaves.size()) fail(JET_ESTATE, "no contraction path set");
     if (!net.open_set) fail(JET_ESTATE, "open legs not declared (jet_network_set_open)");
@@ -376,6 +376,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     std::vector<int32_t> batch_nodes;
     double batch_flop = 0, batch_bytes = 0;
     auto release_children = [&](int32_t v) {
+        if (grad) return;   // the adjoint sweep reads every forward intermediate
         for (int32_t c : {node[v].a, node[v].b})
             if (node[c].base == BASE_ARENA)
                 arena.release((size_t)node[c].buf_off, (size_t)node[c].n_inst * node[c].view.size * es);
@@ -416,6 +417,176 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         batch_nodes.clear();
         batch_patches.clear();
         batch_flop = batch_bytes = 0;
+    };
+
+    // Direct strided contraction of every instance: C (dense, layout Cv) = sum over
+    // K of A (view VA) * B (view VB); pa/pb/pc: per-instance addresses.
+    auto emit_direct = [&](int32_t v, const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K,
+                           bool a_big, int64_t n_inst, const std::vector<std::pair<int32_t, int64_t>> &pa,
+                           const std::vector<std::pair<int32_t, int64_t>> &pb,
+                           const std::vector<std::pair<int32_t, int64_t>> &pc, double flop, double bytes,
+                           std::vector<size_t> &scratch, std::vector<size_t> &scratch_bytes) {
+            const View &VX = a_big ? VA : VB;   // operand whose strides order the summed labels
+            auto strideA = [&](int64_t l) { int p = find_pos(VA.labels, l); return p < 0 ? 0 : VA.strides[p]; };
+            auto strideB = [&](int64_t l) { int p = find_pos(VB.labels, l); return p < 0 ? 0 : VB.strides[p]; };
+            DirectArgs d;
+            std::memset(&d, 0, sizeof d);
+            // output split: cols = longest suffix with product <= JET_COLMAX
+            const auto &C = Cv;
+            size_t ncol_labels = 0;
+            int64_t ncols = 1;
+            while (ncol_labels < C.labels.size() &&
+                   ncols * C.dims[C.labels.size() - 1 - ncol_labels] <= JET_COLMAX) {
+                ncols *= C.dims[C.labels.size() - 1 - ncol_labels];
+                ++ncol_labels;
+            }
+            size_t nrow_labels = C.labels.size() - ncol_labels;
+            if (nrow_labels > JET_MAXR) fail(JET_EINVAL, "intermediate rank too large");
+            std::vector<int32_t> colA(ncols), colB(ncols);
+            for (int64_t c = 0; c < ncols; ++c) {
+                int64_t r = c, oa = 0, ob = 0;
+                for (size_t j = 0; j < ncol_labels; ++j) {
+                    size_t li = C.labels.size() - 1 - j;
+                    int64_t dg = r % C.dims[li];
+                    r /= C.dims[li];
+                    oa += dg * strideA(C.labels[li]);
+                    ob += dg * strideB(C.labels[li]);
+                }
+                if (oa > INT32_MAX || ob > INT32_MAX) fail(JET_EINVAL, "column offset overflow");
+                colA[c] = (int32_t)oa;
+                colB[c] = (int32_t)ob;
+            }
+            d.n_cols = (int32_t)ncols;
+            d.n_rows = prod(C.dims, 0, nrow_labels);
+            d.row_rank = (int32_t)nrow_labels;
+            for (size_t j = 0; j < nrow_labels; ++j) {
+                size_t li = nrow_labels - 1 - j;
+                d.row_dim[j] = C.dims[li];
+                d.row_sA[j] = strideA(C.labels[li]);
+                d.row_sB[j] = strideB(C.labels[li]);
+            }
+            // summed labels: slowest first by stride in the larger operand
+            std::vector<int64_t> Ks = K;
+            std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) {
+                int px = find_pos(VX.labels, x), py = find_pos(VX.labels, y);
+                return VX.strides[px] > VX.strides[py];
+            });
+            std::vector<int64_t> Kd;
+            for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
+            size_t nklo_labels = 0;
+            int64_t nklo = 1;
+            while (nklo_labels < Ks.size() && nklo * Kd[Ks.size() - 1 - nklo_labels] <= JET_KLOMAX) {
+                nklo *= Kd[Ks.size() - 1 - nklo_labels];
+                ++nklo_labels;
+            }
+            size_t nkhi_labels = Ks.size() - nklo_labels;
+            if (nkhi_labels > JET_MAXR) fail(JET_EINVAL, "summed rank too large");
+            std::vector<int32_t> kA(nklo), kB(nklo);
+            for (int64_t q = 0; q < nklo; ++q) {
+                int64_t r = q, oa = 0, ob = 0;
+                for (size_t j = 0; j < nklo_labels; ++j) {
+                    size_t li = Ks.size() - 1 - j;
+                    int64_t dg = r % Kd[li];
+                    r /= Kd[li];
+                    oa += dg * strideA(Ks[li]);
+                    ob += dg * strideB(Ks[li]);
+                }
+                if (oa > INT32_MAX || ob > INT32_MAX) fail(JET_EINVAL, "summed offset overflow");
+                kA[q] = (int32_t)oa;
+                kB[q] = (int32_t)ob;
+            }
+            d.n_klo = (int32_t)nklo;
+            d.khi_rank = (int32_t)nkhi_labels;
+            d.n_khi = 1;
+            for (size_t j = 0; j < nkhi_labels; ++j) {
+                size_t li = nkhi_labels - 1 - j;
+                d.khi_dim[j] = Kd[li];
+                d.khi_sA[j] = strideA(Ks[li]);
+                d.khi_sB[j] = strideB(Ks[li]);
+                d.n_khi *= Kd[li];
+            }
+            d.n_out = d.n_rows * d.n_cols;
+            d.n_inst = (int32_t)n_inst;
+            // split the summed index across blocks when there are few outputs
+            const int64_t total_out = d.n_out * n_inst;
+            const int64_t n_k = d.n_khi * d.n_klo;
+            d.ksplit = 1;
+            if (total_out < 16384 && n_k >= 4096 && d.n_khi > 1) {
+                int64_t groups = (d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G * n_inst;
+                int64_t want = std::max<int64_t>(1, (148 * 8 + groups - 1) / groups);
+                int64_t parts = std::min<int64_t>(want, d.n_khi);
+                d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
+                d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
+            }
+            size_t off_colA = blob.put_i32(colA), off_colB = blob.put_i32(colB);
+            size_t off_kA = blob.put_i32(kA), off_kB = blob.put_i32(kB);
+            size_t off_pa = blob.put_ptrs(pa), off_pb = blob.put_ptrs(pb), off_pc = blob.put_ptrs(pc);
+            size_t part_off = 0, part_bytes = 0;
+            if (d.ksplit > 1) {
+                part_bytes = (size_t)n_inst * d.ksplit * d.n_out * es;
+                part_off = arena.alloc(part_bytes);
+                scratch.push_back(part_off);
+                scratch_bytes.push_back(part_bytes);
+            }
+            size_t so = blob.reserve(sizeof(DirectArgs));
+            std::memcpy(blob.bytes.data() + so, &d, sizeof d);
+            blob.patch_field(so, offsetof(DirectArgs, ptrA), BASE_BLOB, (int64_t)off_pa);
+            blob.patch_field(so, offsetof(DirectArgs, ptrB), BASE_BLOB, (int64_t)off_pb);
+            blob.patch_field(so, offsetof(DirectArgs, ptrC), BASE_BLOB, (int64_t)off_pc);
+            blob.patch_field(so, offsetof(DirectArgs, colA), BASE_BLOB, (int64_t)off_colA);
+            blob.patch_field(so, offsetof(DirectArgs, colB), BASE_BLOB, (int64_t)off_colB);
+            blob.patch_field(so, offsetof(DirectArgs, kA), BASE_BLOB, (int64_t)off_kA);
+            blob.patch_field(so, offsetof(DirectArgs, kB), BASE_BLOB, (int64_t)off_kB);
+            if (d.ksplit > 1) blob.patch_field(so, offsetof(DirectArgs, partials), BASE_ARENA, (int64_t)part_off);
+            Op op;
+            op.kind = OpKind::Direct;
+            op.node = v;
+            op.n_inst = n_inst;
+            op.args_off = so;
+            op.args_bytes = sizeof(DirectArgs);
+            op.flop = flop;
+            op.bytes = bytes;
+            op.variant = fp64 ? 1 : 0;
+            bool pow2 = true;
+            for (int j = 0; j < d.row_rank; ++j) pow2 = pow2 && (d.row_dim[j] & (d.row_dim[j] - 1)) == 0;
+            for (int j = 0; j < d.khi_rank; ++j) pow2 = pow2 && (d.khi_dim[j] & (d.khi_dim[j] - 1)) == 0;
+            if (pow2) op.variant |= 4;
+            op.block = 256;
+            if (d.ksplit > 1) {
+                op.grid_x = d.ksplit;
+                op.grid_y = (int32_t)((d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G);
+                op.grid_z = (int32_t)std::min<int64_t>(n_inst, 65535);
+                op.variant |= 2;
+            } else {
+                int64_t blocks = (d.n_out + 255) / 256;
+                int64_t gy = std::min<int64_t>(n_inst, 65535);
+                int64_t gx = std::min<int64_t>(blocks, std::max<int64_t>(1, 148 * 16 / std::max<int64_t>(1, gy)));
+                op.grid_x = (int32_t)std::max<int64_t>(gx, 1);
+                op.grid_y = (int32_t)gy;
+            }
+            op.smem = (int32_t)(8 * ncols + 8 * nklo);
+            P.ops.push_back(op);
+            if (d.ksplit > 1) {
+                SplitKReduceArgs r;
+                std::memset(&r, 0, sizeof r);
+                r.n_out = d.n_out;
+                r.n_inst = d.n_inst;
+                r.ksplit = d.ksplit;
+                size_t ro = blob.reserve(sizeof r);
+                std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
+                blob.patch_field(ro, offsetof(SplitKReduceArgs, partials), BASE_ARENA, (int64_t)part_off);
+                blob.patch_field(ro, offsetof(SplitKReduceArgs, ptrC), BASE_BLOB, (int64_t)off_pc);
+                Op rop;
+                rop.kind = OpKind::SplitKReduce;
+                rop.node = v;
+                rop.n_inst = n_inst;
+                rop.args_off = ro;
+                rop.args_bytes = sizeof r;
+                rop.variant = fp64 ? 1 : 0;
+                int64_t tot = d.n_out * n_inst;
+                rop.grid_x = (int32_t)std::min<int64_t>((tot + 255) / 256, 65535);
+                P.ops.push_back(rop);
+            }
     };
 
     // ---- pass 2, launch order: arena offsets, pointer tables, launches
@@ -764,167 +935,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         // ------------------------------------------------ direct contraction
         else {
             ++P.n_direct;
-            const View &VX = a_big ? VA : VB;   // operand whose strides order the summed labels
-            auto strideA = [&](int64_t l) { int p = find_pos(VA.labels, l); return p < 0 ? 0 : VA.strides[p]; };
-            auto strideB = [&](int64_t l) { int p = find_pos(VB.labels, l); return p < 0 ? 0 : VB.strides[p]; };
-            DirectArgs d;
-            std::memset(&d, 0, sizeof d);
-            // output split: cols = longest suffix with product <= JET_COLMAX
-            const auto &C = N.view;
-            size_t ncol_labels = 0;
-            int64_t ncols = 1;
-            while (ncol_labels < C.labels.size() &&
-                   ncols * C.dims[C.labels.size() - 1 - ncol_labels] <= JET_COLMAX) {
-                ncols *= C.dims[C.labels.size() - 1 - ncol_labels];
-                ++ncol_labels;
-            }
-            size_t nrow_labels = C.labels.size() - ncol_labels;
-            if (nrow_labels > JET_MAXR) fail(JET_EINVAL, "intermediate rank too large");
-            std::vector<int32_t> colA(ncols), colB(ncols);
-            for (int64_t c = 0; c < ncols; ++c) {
-                int64_t r = c, oa = 0, ob = 0;
-                for (size_t j = 0; j < ncol_labels; ++j) {
-                    size_t li = C.labels.size() - 1 - j;
-                    int64_t dg = r % C.dims[li];
-                    r /= C.dims[li];
-                    oa += dg * strideA(C.labels[li]);
-                    ob += dg * strideB(C.labels[li]);
-                }
-                if (oa > INT32_MAX || ob > INT32_MAX) fail(JET_EINVAL, "column offset overflow");
-                colA[c] = (int32_t)oa;
-                colB[c] = (int32_t)ob;
-            }
-            d.n_cols = (int32_t)ncols;
-            d.n_rows = prod(C.dims, 0, nrow_labels);
-            d.row_rank = (int32_t)nrow_labels;
-            for (size_t j = 0; j < nrow_labels; ++j) {
-                size_t li = nrow_labels - 1 - j;
-                d.row_dim[j] = C.dims[li];
-                d.row_sA[j] = strideA(C.labels[li]);
-                d.row_sB[j] = strideB(C.labels[li]);
-            }
-            // summed labels: slowest first by stride in the larger operand
-            std::vector<int64_t> Ks = K;
-            std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) {
-                int px = find_pos(VX.labels, x), py = find_pos(VX.labels, y);
-                return VX.strides[px] > VX.strides[py];
-            });
-            std::vector<int64_t> Kd;
-            for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
-            size_t nklo_labels = 0;
-            int64_t nklo = 1;
-            while (nklo_labels < Ks.size() && nklo * Kd[Ks.size() - 1 - nklo_labels] <= JET_KLOMAX) {
-                nklo *= Kd[Ks.size() - 1 - nklo_labels];
-                ++nklo_labels;
-            }
-            size_t nkhi_labels = Ks.size() - nklo_labels;
-            if (nkhi_labels > JET_MAXR) fail(JET_EINVAL, "summed rank too large");
-            std::vector<int32_t> kA(nklo), kB(nklo);
-            for (int64_t q = 0; q < nklo; ++q) {
-                int64_t r = q, oa = 0, ob = 0;
-                for (size_t j = 0; j < nklo_labels; ++j) {
-                    size_t li = Ks.size() - 1 - j;
-                    int64_t dg = r % Kd[li];
-                    r /= Kd[li];
-                    oa += dg * strideA(Ks[li]);
-                    ob += dg * strideB(Ks[li]);
-                }
-                if (oa > INT32_MAX || ob > INT32_MAX) fail(JET_EINVAL, "summed offset overflow");
-                kA[q] = (int32_t)oa;
-                kB[q] = (int32_t)ob;
-            }
-            d.n_klo = (int32_t)nklo;
-            d.khi_rank = (int32_t)nkhi_labels;
-            d.n_khi = 1;
-            for (size_t j = 0; j < nkhi_labels; ++j) {
-                size_t li = nkhi_labels - 1 - j;
-                d.khi_dim[j] = Kd[li];
-                d.khi_sA[j] = strideA(Ks[li]);
-                d.khi_sB[j] = strideB(Ks[li]);
-                d.n_khi *= Kd[li];
-            }
-            d.n_out = d.n_rows * d.n_cols;
-            d.n_inst = (int32_t)N.n_inst;
-            // split the summed index across blocks when there are few outputs
-            const int64_t total_out = d.n_out * N.n_inst;
-            const int64_t n_k = d.n_khi * d.n_klo;
-            d.ksplit = 1;
-            if (total_out < 16384 && n_k >= 4096 && d.n_khi > 1) {
-                int64_t groups = (d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G * N.n_inst;
-                int64_t want = std::max<int64_t>(1, (148 * 8 + groups - 1) / groups);
-                int64_t parts = std::min<int64_t>(want, d.n_khi);
-                d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
-                d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
-            }
-            size_t off_colA = blob.put_i32(colA), off_colB = blob.put_i32(colB);
-            size_t off_kA = blob.put_i32(kA), off_kB = blob.put_i32(kB);
-            size_t off_pa = blob.put_ptrs(pa), off_pb = blob.put_ptrs(pb), off_pc = blob.put_ptrs(pc);
-            size_t part_off = 0, part_bytes = 0;
-            if (d.ksplit > 1) {
-                part_bytes = (size_t)N.n_inst * d.ksplit * d.n_out * es;
-                part_off = arena.alloc(part_bytes);
-                scratch.push_back(part_off);
-                scratch_bytes.push_back(part_bytes);
-            }
-            size_t so = blob.reserve(sizeof(DirectArgs));
-            std::memcpy(blob.bytes.data() + so, &d, sizeof d);
-            blob.patch_field(so, offsetof(DirectArgs, ptrA), BASE_BLOB, (int64_t)off_pa);
-            blob.patch_field(so, offsetof(DirectArgs, ptrB), BASE_BLOB, (int64_t)off_pb);
-            blob.patch_field(so, offsetof(DirectArgs, ptrC), BASE_BLOB, (int64_t)off_pc);
-            blob.patch_field(so, offsetof(DirectArgs, colA), BASE_BLOB, (int64_t)off_colA);
-            blob.patch_field(so, offsetof(DirectArgs, colB), BASE_BLOB, (int64_t)off_colB);
-            blob.patch_field(so, offsetof(DirectArgs, kA), BASE_BLOB, (int64_t)off_kA);
-            blob.patch_field(so, offsetof(DirectArgs, kB), BASE_BLOB, (int64_t)off_kB);
-            if (d.ksplit > 1) blob.patch_field(so, offsetof(DirectArgs, partials), BASE_ARENA, (int64_t)part_off);
-            Op op;
-            op.kind = OpKind::Direct;
-            op.node = v;
-            op.n_inst = N.n_inst;
-            op.args_off = so;
-            op.args_bytes = sizeof(DirectArgs);
-            op.flop = flop;
-            op.bytes = bytes;
-            op.variant = fp64 ? 1 : 0;
-            bool pow2 = true;
-            for (int j = 0; j < d.row_rank; ++j) pow2 = pow2 && (d.row_dim[j] & (d.row_dim[j] - 1)) == 0;
-            for (int j = 0; j < d.khi_rank; ++j) pow2 = pow2 && (d.khi_dim[j] & (d.khi_dim[j] - 1)) == 0;
-            if (pow2) op.variant |= 4;
-            op.block = 256;
-            if (d.ksplit > 1) {
-                op.grid_x = d.ksplit;
-                op.grid_y = (int32_t)((d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G);
-                op.grid_z = (int32_t)std::min<int64_t>(N.n_inst, 65535);
-                op.variant |= 2;
-            } else {
-                int64_t blocks = (d.n_out + 255) / 256;
-                int64_t gy = std::min<int64_t>(N.n_inst, 65535);
-                int64_t gx = std::min<int64_t>(blocks, std::max<int64_t>(1, 148 * 16 / std::max<int64_t>(1, gy)));
-                op.grid_x = (int32_t)std::max<int64_t>(gx, 1);
-                op.grid_y = (int32_t)gy;
-            }
-            op.smem = (int32_t)(8 * ncols + 8 * nklo);
-            P.ops.push_back(op);
-            if (d.ksplit > 1) {
-                SplitKReduceArgs r;
-                std::memset(&r, 0, sizeof r);
-                r.n_out = d.n_out;
-                r.n_inst = d.n_inst;
-                r.ksplit = d.ksplit;
-                size_t ro = blob.reserve(sizeof r);
-                std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
-                blob.patch_field(ro, offsetof(SplitKReduceArgs, partials), BASE_ARENA, (int64_t)part_off);
-                blob.patch_field(ro, offsetof(SplitKReduceArgs, ptrC), BASE_BLOB, (int64_t)off_pc);
-                Op rop;
-                rop.kind = OpKind::SplitKReduce;
-                rop.node = v;
-                rop.n_inst = N.n_inst;
-                rop.args_off = ro;
-                rop.args_bytes = sizeof r;
-                rop.variant = fp64 ? 1 : 0;
-                int64_t tot = d.n_out * N.n_inst;
-                rop.grid_x = (int32_t)std::min<int64_t>((tot + 255) / 256, 65535);
-                P.ops.push_back(rop);
-            }
+            emit_direct(v, VA, VB, N.view, K, a_big, N.n_inst, pa, pb, pc, flop, bytes, scratch, scratch_bytes);
         }
 
         for (size_t s = 0; s < scratch.size(); ++s) arena.release(scratch[s], scratch_bytes[s]);
@@ -932,6 +943,141 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         release_children(v);
     }
     flush_batch();
+
+    // ---- adjoint sweep (environment contraction), reverse launch order.
+    // For C = sum_K A B: env(A) = env(C) contracted with B over B's free labels,
+    // laid out like A; env(B) likewise.  Several instances of C that read the
+    // same child instance add their contributions in increasing instance order.
+    if (grad) {
+        const int32_t rootv = n_nodes - 1;
+        if (rootv < n_leaves) fail(JET_EINVAL, "the adjoint needs at least two tensors");
+        std::vector<char> need(n_nodes, 0);
+        for (int32_t id : grad->leaves) need[id] = 1;
+        for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
+            const int32_t v = n_leaves + k;
+            need[v] = need[node[v].a] || need[node[v].b];
+        }
+        std::vector<std::pair<int32_t, int64_t>> env_base(n_nodes, {-1, 0});
+        {   // seed: env(root instance) = sum of cot_b over the amplitudes mapped to it
+            const NodeInfo &R = node[rootv];
+            std::vector<double> seed(2 * R.n_inst, 0.0);
+            for (int64_t x = 0; x < n_assign; ++x) {
+                const int32_t i = inst_of[rootv][x];
+                const int64_t b = x / n_sl;
+                seed[2 * i] += grad->cot[2 * b];
+                seed[2 * i + 1] += grad->cot[2 * b + 1];
+            }
+            const size_t off = blob.reserve((size_t)R.n_inst * es, 16);
+            for (int64_t i = 0; i < R.n_inst; ++i) {
+                if (fp64) {
+                    std::memcpy(blob.bytes.data() + off + i * 16, &seed[2 * i], 16);
+                } else {
+                    const float f[2] = {(float)seed[2 * i], (float)seed[2 * i + 1]};
+                    std::memcpy(blob.bytes.data() + off + i * 8, f, 8);
+                }
+            }
+            env_base[rootv] = {BASE_BLOB, (int64_t)off};
+        }
+        auto emit_memset = [&](size_t off, size_t nbytes) {
+            MemsetArgs m;
+            m.ptr = 0;
+            m.bytes = (int64_t)nbytes;
+            const size_t so = blob.reserve(sizeof m);
+            std::memcpy(blob.bytes.data() + so, &m, sizeof m);
+            blob.patch_field(so, offsetof(MemsetArgs, ptr), BASE_ARENA, (int64_t)off);
+            Op op;
+            op.kind = OpKind::Memset;
+            op.args_off = so;
+            op.args_bytes = sizeof m;
+            P.ops.push_back(op);
+        };
+        for (int32_t v : order)
+            if (need[v] && v != rootv) {
+                const size_t nb = (size_t)node[v].n_inst * node[v].view.size * es;
+                const size_t off = arena.alloc(nb);
+                env_base[v] = {BASE_ARENA, (int64_t)off};
+                emit_memset(off, nb);
+            }
+        for (auto it = order.rbegin(); it != order.rend(); ++it) {
+            const int32_t v = *it;
+            if (!need[v]) continue;
+            const NodeInfo &N = node[v];
+            for (int side = 0; side < 2; ++side) {
+                const int32_t c = side == 0 ? N.a : N.b, o = side == 0 ? N.b : N.a;
+                if (!need[c]) continue;
+                const std::vector<int32_t> &ic = side == 0 ? N.ia : N.ib, &io = side == 0 ? N.ib : N.ia;
+                const NodeInfo &NC = node[c], &NO = node[o];
+                const View Tv = dense_view(NC.view.labels, net);
+                std::vector<int64_t> Kb;   // summed: labels of C that come from the other child
+                for (int64_t l : N.view.labels)
+                    if (find_pos(NO.view.labels, l) >= 0) Kb.push_back(l);
+                const size_t tbytes = (size_t)N.n_inst * Tv.size * es;
+                const size_t toff = arena.alloc(tbytes);
+                std::vector<std::pair<int32_t, int64_t>> pe, po, pt;
+                for (int64_t i = 0; i < N.n_inst; ++i) {
+                    pe.push_back({env_base[v].first, env_base[v].second + i * N.view.size * es});
+                    po.push_back(base_ref(o, io[i]));
+                    pt.push_back({BASE_ARENA, (int64_t)toff + i * Tv.size * es});
+                }
+                std::vector<int64_t> un = N.view.labels;
+                for (int64_t l : NO.view.labels)
+                    if (find_pos(un, l) < 0) un.push_back(l);
+                const double flop = 8.0 * (double)dimprod(un) * (double)N.n_inst;
+                const double bytes = (double)es * (double)N.n_inst * (double)(N.view.size + NO.view.size + Tv.size);
+                std::vector<size_t> scr, scrb;
+                emit_direct(v, N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, N.n_inst, pe, po, pt, flop,
+                            bytes, scr, scrb);
+                for (size_t q = 0; q < scr.size(); ++q) arena.release(scr[q], scrb[q]);
+                P.flop_executed += flop;
+                // sum the contributions into env(c)
+                AccumArgs ac;
+                std::memset(&ac, 0, sizeof ac);
+                ac.n = Tv.size;
+                ac.n_tgt = (int32_t)NC.n_inst;
+                ac.rank = (int32_t)Tv.labels.size();
+                ac.src_fp64 = fp64 ? 1 : 0;
+                const bool leaf = c < n_leaves;
+                ac.tgt_fp64 = (leaf || fp64) ? 1 : 0;
+                for (int j = 0; j < ac.rank; ++j) {
+                    const size_t li = Tv.labels.size() - 1 - j;
+                    ac.dim[j] = Tv.dims[li];
+                    ac.tstride[j] = leaf ? NC.view.strides[li] : Tv.strides[li];
+                }
+                std::vector<int32_t> cptr(NC.n_inst + 1, 0), csrc(N.n_inst);
+                for (int64_t i = 0; i < N.n_inst; ++i) ++cptr[ic[i] + 1];
+                for (int64_t j = 0; j < NC.n_inst; ++j) cptr[j + 1] += cptr[j];
+                {
+                    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+                    for (int64_t i = 0; i < N.n_inst; ++i) csrc[fill[ic[i]]++] = (int32_t)i;
+                }
+                std::vector<std::pair<int32_t, int64_t>> tg;
+                for (int64_t j = 0; j < NC.n_inst; ++j) {
+                    if (leaf)
+                        tg.push_back({BASE_ENV, (grad->env_off[c] + (NC.inst_off[j] - net.leaves[c].offset)) * 16});
+                    else
+                        tg.push_back({env_base[c].first, env_base[c].second + j * NC.view.size * es});
+                }
+                const size_t o_p = blob.put_i32(cptr), o_s = blob.put_i32(csrc), o_t = blob.put_ptrs(tg);
+                const size_t so = blob.reserve(sizeof ac);
+                std::memcpy(blob.bytes.data() + so, &ac, sizeof ac);
+                blob.patch_field(so, offsetof(AccumArgs, src), BASE_ARENA, (int64_t)toff);
+                blob.patch_field(so, offsetof(AccumArgs, tgt), BASE_BLOB, (int64_t)o_t);
+                blob.patch_field(so, offsetof(AccumArgs, csr_ptr), BASE_BLOB, (int64_t)o_p);
+                blob.patch_field(so, offsetof(AccumArgs, csr_src), BASE_BLOB, (int64_t)o_s);
+                Op op;
+                op.kind = OpKind::Accum;
+                op.node = c;
+                op.n_inst = NC.n_inst;
+                op.args_off = so;
+                op.args_bytes = sizeof ac;
+                op.bytes = (double)es * (double)N.n_inst * (double)Tv.size * 2.0;
+                op.grid_x = (int32_t)std::max<int64_t>(
+                    1, std::min<int64_t>(((int64_t)NC.n_inst * Tv.size + 255) / 256, 148 * 16));
+                P.ops.push_back(op);
+                arena.release(toff, tbytes);
+            }
+        }
+    }
 
     // ---- slice / amplitude reduction (Eq. sliced_sum), FP64, slices in increasing order
     const int32_t root = n_nodes - 1;

@@ -244,7 +244,8 @@ class Network:
         o = self._outputs(outputs)
         c = np.ascontiguousarray(np.asarray(cot, dtype=np.complex128).reshape(o.shape[0]))
         ids = np.ascontiguousarray(np.asarray(tensor_ids, dtype=np.int32))
-        envs = [np.zeros(self.shapes[i], dtype=np.complex64) for i in ids]
+        # out-of-range ids get a placeholder buffer; the library rejects them
+        envs = [np.zeros(self.shapes[i] if 0 <= i < len(self.shapes) else (1,), dtype=np.complex64) for i in ids]
         ptrs = (ctypes.c_void_p * max(len(envs), 1))(*[e.ctypes.data for e in envs])
         amps = np.zeros(o.shape[0], dtype=np.complex128)
         _check(lib().jet_contract_grad(self._h, o.shape[0], o.ctypes.data, c.ctypes.data, ids.size,

@@ -175,3 +175,19 @@ def test_contract_slices_rejects_bad_ids_before_any_device_work():
         with pytest.raises(jet.JetError) as e:
             net.contract_slices(w.outputs, bad)
         assert e.value.code == jet.JET_EINVAL
+
+
+def test_contract_grad_argument_errors_before_device_work():
+    w, net = _net()
+    net.path_greedy(seed=1, n_trials=2)
+    cot = np.ones(1, np.complex128)
+    for ids in ([-1], [len(w.network.data)], [3, 3]):
+        with pytest.raises(jet.JetError) as e:
+            net.contract_grad(w.outputs, cot, ids)
+        assert e.value.code == jet.JET_EINVAL
+    one = jet.Network([[7]], [np.array([1, 2], np.complex64)])
+    one.set_open([7])
+    one.path_set([])
+    with pytest.raises(jet.JetError) as e:
+        one.contract_grad([[0]], cot, [0])
+    assert e.value.code == jet.JET_EINVAL
