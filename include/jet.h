@@ -114,6 +114,8 @@ typedef struct {
     int32_t block;            /* threads per block                                      */
     int32_t grid[3];          /* launch grid                                            */
     int32_t smem;             /* dynamic shared memory bytes (0 = kernel default)       */
+    int32_t variant;          /* kernel variant selector (kind specific)                */
+    int32_t pad_;
 } jet_op_record;
 
 /* Defaults listed in jet_options above. */

@@ -421,6 +421,8 @@ int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t
             out[i].grid[1] = op.grid_y;
             out[i].grid[2] = op.grid_z;
             out[i].smem = op.smem;
+            out[i].variant = op.variant;
+            out[i].pad_ = 0;
         }
     });
 }

@@ -194,8 +194,8 @@ constexpr int SPLIT_TR = 32, SPLIT_TK = 64;
 // The source offsets of its rows and columns are decoded once into shared
 // memory; the tile is read with threads running along the source's fastest
 // label (rows or K, fast_k) and written along K, two values per thread.
-template <int MODE>
-__global__ void __launch_bounds__(256) tc_split_kernel(const __grid_constant__ TcSplitArgs a)
+template <int MODE, bool POW2>
+__global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant__ TcSplitArgs a)
 {
     constexpr int NP = TcCfg<MODE>::NP, EB = TcCfg<MODE>::EB, NPH = NP / 2;
     __shared__ float2 tile[SPLIT_TR][SPLIT_TK + 1];
@@ -211,28 +211,30 @@ __global__ void __launch_bounds__(256) tc_split_kernel(const __grid_constant__ T
             const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
             const int64_t row0 = rt * SPLIT_TR, k0 = kt * SPLIT_TK;
             __syncthreads();
-            if (tid < SPLIT_TR) {
-                int64_t row = row0 + tid, off = -1;
-                if (row < a.rows) {
+            if (tid < SPLIT_TR + SPLIT_TK) {
+                const bool is_row = tid < SPLIT_TR;
+                int64_t x = is_row ? row0 + tid : k0 + (tid - SPLIT_TR), off = -1;
+                if (x < (is_row ? a.rows : a.k)) {
                     off = 0;
-                    for (int j = 0; j < a.rank_r; ++j) {
-                        int64_t q = row / a.r_dim[j];
-                        off += (row - q * a.r_dim[j]) * a.r_s[j];
-                        row = q;
+                    const int rank = is_row ? a.rank_r : a.rank_k;
+                    const int64_t *dim = is_row ? a.r_dim : a.k_dim, *str = is_row ? a.r_s : a.k_s;
+                    for (int j = 0; j < rank; ++j) {
+                        const int64_t d = dim[j];
+                        int64_t q, r;
+                        if (POW2) {
+                            const int sh = __ffsll((unsigned long long)d) - 1;
+                            q = x >> sh;
+                            r = x & (d - 1);
+                        } else {
+                            q = x / d;
+                            r = x - q * d;
+                        }
+                        off += r * str[j];
+                        x = q;
                     }
                 }
-                rowOff[tid] = off;
-            } else if (tid < SPLIT_TR + SPLIT_TK) {
-                int64_t k = k0 + (tid - SPLIT_TR), off = -1;
-                if (k < a.k) {
-                    off = 0;
-                    for (int j = 0; j < a.rank_k; ++j) {
-                        int64_t q = k / a.k_dim[j];
-                        off += (k - q * a.k_dim[j]) * a.k_s[j];
-                        k = q;
-                    }
-                }
-                kOff[tid - SPLIT_TR] = off;
+                if (is_row) rowOff[tid] = off;
+                else kOff[tid - SPLIT_TR] = off;
             }
             __syncthreads();
 #pragma unroll
@@ -538,13 +540,20 @@ cudaError_t set_tc_smem_limits()
 cudaError_t launch_tc_split(const TcSplitArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
     dim3 grid(c.gx, c.gy, 1);
+    const bool pow2 = c.variant & 2;
+#define JET_SPLIT(M)                                                                         \
+    do {                                                                                     \
+        if (pow2) tc_split_kernel<M, true><<<grid, 256, 0, s>>>(a);                          \
+        else tc_split_kernel<M, false><<<grid, 256, 0, s>>>(a);                              \
+    } while (0)
     switch (a.mode) {
-    case JET_PREC_TF32: tc_split_kernel<JET_PREC_TF32><<<grid, 256, 0, s>>>(a); break;
-    case JET_PREC_TF32X3: tc_split_kernel<JET_PREC_TF32X3><<<grid, 256, 0, s>>>(a); break;
-    case JET_PREC_BF16X3: tc_split_kernel<JET_PREC_BF16X3><<<grid, 256, 0, s>>>(a); break;
-    case JET_PREC_BF16X6: tc_split_kernel<JET_PREC_BF16X6><<<grid, 256, 0, s>>>(a); break;
+    case JET_PREC_TF32: JET_SPLIT(JET_PREC_TF32); break;
+    case JET_PREC_TF32X3: JET_SPLIT(JET_PREC_TF32X3); break;
+    case JET_PREC_BF16X3: JET_SPLIT(JET_PREC_BF16X3); break;
+    case JET_PREC_BF16X6: JET_SPLIT(JET_PREC_BF16X6); break;
     default: return cudaErrorInvalidValue;
     }
+#undef JET_SPLIT
     return cudaGetLastError();
 }
 

@@ -47,6 +47,8 @@ struct NodeInfo {
     int32_t a = -1, b = -1;          // children (internal nodes)
     std::vector<int64_t> K, fa, fb;  // summed labels, free labels of a, free labels of b
     bool use_gemm = false, a_big = false, small = false;
+    bool a_is_m = true;              // GEMM route: child a is the M operand
+    std::vector<int64_t> fM, fN;     // GEMM route: output = fM ++ fN, in these orders
     int32_t depth = 0;               // tree level (leaves 0)
 };
 
@@ -284,6 +286,22 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         return p;
     };
 
+    // label sets of every tree node (fixed labels removed) and each node's parent
+    // and sibling: a GEMM node shapes its output for the contraction that reads it
+    std::vector<std::vector<int64_t>> labset(n_nodes);
+    std::vector<int32_t> parent(n_nodes, -1), sibling(n_nodes, -1);
+    for (int32_t i = 0; i < n_leaves; ++i) labset[i] = node[i].view.labels;
+    for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
+        const int32_t a = net.path[k].first, b = net.path[k].second, v = n_leaves + k;
+        for (int64_t l : labset[a])
+            if (find_pos(labset[b], l) < 0) labset[v].push_back(l);
+        for (int64_t l : labset[b])
+            if (find_pos(labset[a], l) < 0) labset[v].push_back(l);
+        parent[a] = parent[b] = v;
+        sibling[a] = b;
+        sibling[b] = a;
+    }
+
     // ---- pass 1, tree order: instances (reuse DAG), label classes, route, layout, depth
     for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
         const int32_t a = net.path[k].first, b = net.path[k].second, v = n_leaves + k;
@@ -345,10 +363,40 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             }
             if (ins < 0) out.insert(out.begin(), fsmall.begin(), fsmall.end());
         } else if (N.use_gemm) {
-            bool a_is_m = nFa >= nFb;
-            out = a_is_m ? N.fa : N.fb;
-            const auto &other = a_is_m ? N.fb : N.fa;
-            out.insert(out.end(), other.begin(), other.end());
+            N.a_is_m = nFa >= nFb;
+            N.fM = N.a_is_m ? N.fa : N.fb;
+            N.fN = N.a_is_m ? N.fb : N.fa;
+            // for a tensor-core parent, lay the output out as [parent-free, parent-summed]
+            // when the parent's summed labels all come from one side: the parent's
+            // operand split is then a plain format conversion
+            const int32_t pp = parent[v];
+            if (tc_mode && pp >= 0) {
+                const auto &ls = labset[sibling[v]];
+                std::vector<int64_t> Kp, Fp, Fs;
+                for (int64_t l : labset[v]) (find_pos(ls, l) >= 0 ? Kp : Fp).push_back(l);
+                for (int64_t l : ls)
+                    if (find_pos(labset[v], l) < 0) Fs.push_back(l);
+                const bool p_gemm = !Kp.empty() && dimprod(Kp) >= net.opt.gemm_min_k && dimprod(Fp) >= 64 &&
+                                    dimprod(Fs) >= 64;
+                auto holds_all = [&](const std::vector<int64_t> &X) {
+                    for (int64_t l : Kp)
+                        if (find_pos(X, l) < 0) return false;
+                    return true;
+                };
+                const int side = !p_gemm ? -1 : holds_all(N.fb) ? 1 : holds_all(N.fa) ? 0 : -1;
+                if (side >= 0) {
+                    N.a_is_m = side == 1;
+                    N.fM = N.a_is_m ? N.fa : N.fb;
+                    const auto &fNs = N.a_is_m ? N.fb : N.fa;
+                    N.fN.clear();
+                    for (int64_t l : fNs)
+                        if (find_pos(Kp, l) < 0) N.fN.push_back(l);
+                    for (int64_t l : fNs)
+                        if (find_pos(Kp, l) >= 0) N.fN.push_back(l);
+                }
+            }
+            out = N.fM;
+            out.insert(out.end(), N.fN.begin(), N.fN.end());
         } else {
             out = fbig;
             out.insert(out.end(), fsmall.begin(), fsmall.end());
@@ -688,10 +736,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         // ------------------------------------------------ GEMM route (Section 3.1)
         if (use_gemm) {
             ++P.n_gemm;
-            const bool a_is_m = nFa >= nFb;     // same choice as the output layout above
+            const bool a_is_m = N.a_is_m;       // the output layout's choice (pass 1)
             const int32_t idM = a_is_m ? a : b, idN = a_is_m ? b : a;
             const View &VM = node[idM].view, &VN = node[idN].view;
-            const std::vector<int64_t> &fM = a_is_m ? fa : fb, &fN = a_is_m ? fb : fa;
+            const std::vector<int64_t> &fM = N.fM, &fN = N.fN;
             const std::vector<int32_t> &instM = a_is_m ? N.ia : N.ib, &instN = a_is_m ? N.ib : N.ia;
             auto is_dense = [](const View &V) {
                 int64_t s = 1;
@@ -715,10 +763,12 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 if ((k_last ? head : tail) != f) return kap;
                 return k_last ? tail : head;
             };
-            std::vector<int64_t> kappa = split_order(VM, fM, true);
-            if (kappa.empty()) kappa = split_order(VM, fM, false);
-            if (kappa.empty()) kappa = split_order(VN, fN, true);
-            if (kappa.empty()) kappa = split_order(VN, fN, false);
+            // the larger operand decides the summed-label order (its split is the costly one)
+            const bool m_big = VM.size >= VN.size;
+            std::vector<int64_t> kappa = m_big ? split_order(VM, fM, true) : split_order(VN, fN, true);
+            if (kappa.empty()) kappa = m_big ? split_order(VM, fM, false) : split_order(VN, fN, false);
+            if (kappa.empty()) kappa = m_big ? split_order(VN, fN, true) : split_order(VM, fM, true);
+            if (kappa.empty()) kappa = m_big ? split_order(VN, fN, false) : split_order(VM, fM, false);
             if (kappa.empty())
                 for (int64_t l : VM.labels)
                     if (find_pos(K, l) >= 0) kappa.push_back(l);
@@ -772,6 +822,17 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                             }
                         sa.fast_k = find_pos(kappa, bl) >= 0 ? 1 : 0;
                     }
+                    // already [rows][K] in this order, dense, K unpadded: a pure format conversion
+                    bool conv = nK == k_pad && nK % 4 == 0 && V.labels.size() == f.size() + kappa.size();
+                    for (size_t q = 0; conv && q < V.labels.size(); ++q)
+                        conv = V.labels[q] == (q < f.size() ? f[q] : kappa[q - f.size()]);
+                    if (conv) {
+                        int64_t st = 1;
+                        for (int q = (int)V.labels.size() - 1; conv && q >= 0; --q) {
+                            conv = V.strides[q] == st;
+                            st *= V.dims[q];
+                        }
+                    }
                     std::vector<std::pair<int32_t, int64_t>> ps;
                     for (int64_t j = 0; j < ninst; ++j) ps.push_back(base_ref(id, (int32_t)j));
                     size_t o_ps = blob.put_ptrs(ps);
@@ -791,6 +852,17 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     const int64_t tiles = (rows_pad / 32) * ((k_pad + 63) / 64);
                     op.grid_x = (int32_t)std::max<int64_t>(
                         1, std::min<int64_t>(tiles, std::max<int64_t>(1, 148 * 16 / gy)));
+                    {
+                        bool pow2 = true;
+                        for (int j = 0; j < sa.rank_r; ++j) pow2 = pow2 && (sa.r_dim[j] & (sa.r_dim[j] - 1)) == 0;
+                        for (int j = 0; j < sa.rank_k; ++j) pow2 = pow2 && (sa.k_dim[j] & (sa.k_dim[j] - 1)) == 0;
+                        if (pow2) op.variant |= 2;
+                    }
+                    if (conv) {
+                        op.variant |= 1;
+                        op.grid_x = (int32_t)std::max<int64_t>(
+                            1, std::min<int64_t>((rows_pad * k_pad / 4 + 255) / 256, std::max<int64_t>(1, 148 * 16 / gy)));
+                    }
                     P.ops.push_back(op);
                     P.bytes_executed += op.bytes;
                     return off;

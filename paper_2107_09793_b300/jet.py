@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
 class OpRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("node", ctypes.c_int32), ("n_inst", ctypes.c_int64),
                 ("flop", ctypes.c_double), ("bytes", ctypes.c_double), ("ms", ctypes.c_float),
-                ("block", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("smem", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("grid", ctypes.c_int32 * 3), ("smem", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 OP_KINDS = {0: "direct", 1: "permute", 2: "gemm_simt", 3: "gemm_tc", 4: "slice_reduce", 5: "splitk_reduce",
@@ -258,7 +259,8 @@ class Network:
         recs = (OpRecord * max(n.value, 1))()
         _check(lib().jet_profile(self._h, recs, n.value, ctypes.byref(n)))
         return [{"kind": OP_KINDS.get(r.kind, str(r.kind)), "node": r.node, "n_inst": r.n_inst, "flop": r.flop,
-                 "bytes": r.bytes, "ms": r.ms, "block": r.block, "grid": tuple(r.grid), "smem": r.smem}
+                 "bytes": r.bytes, "ms": r.ms, "block": r.block, "grid": tuple(r.grid), "smem": r.smem,
+                 "variant": r.variant}
                 for r in recs[:n.value]]
 
     def stats(self) -> Dict[str, float]:
