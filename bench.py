@@ -261,7 +261,7 @@ def run_impl(args):
         ms = tot_ms[big]
         achieved = recs[big]["flop"] / (ms * 1e-3) / 1e12
         tc = args.precision not in ("fp32", "fp64")
-        issue = {"bf16x3": 3, "tf32x3": 3, "bf16x6": 6, "tf32": 1}.get(args.precision, 1)
+        issue = {"bf16x3": 3, "tf32x3": 3, "bf16x6": 6, "fp16x3": 3, "tf32": 1}.get(args.precision, 1)
         peak = peaks["bf16_tflops_sustained"] * (0.5 if args.precision.startswith("tf32") else 1.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
@@ -300,7 +300,7 @@ def run_impl(args):
     # reference path) and the other tensor-core splits, each with its error
     modes = {}
     if not args.skip_fp32:
-        for prec in [m for m in ("fp32", "bf16x3", "tf32x3", "bf16x6") if m != args.precision]:
+        for prec in [m for m in ("fp32", "bf16x3", "tf32x3", "bf16x6", "fp16x3") if m != args.precision]:
             nm = jet.from_network(w.network, precision=prec, device=dev)
             nm.path_set(path)
             nm.slice(sliced)
@@ -424,7 +424,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jet", choices=["jet", "reference"])
-    ap.add_argument("--precision", default="bf16x6", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
     ap.add_argument("--case", default="workload", choices=["workload", "gemm"],

@@ -60,7 +60,10 @@ typedef enum {
     JET_PREC_TF32X3 = 2,  /* x = hi + lo in TF32; hi*hi + hi*lo + lo*hi                 */
     JET_PREC_BF16X3 = 3,  /* x = hi + lo in BF16; hi*hi + hi*lo + lo*hi                 */
     JET_PREC_BF16X6 = 4,  /* x = hi + mid + lo in BF16; the six products above 2^-24    */
-    JET_PREC_FP64   = 5   /* complex128 everywhere, FP64 on CUDA cores                  */
+    JET_PREC_FP64   = 5,  /* complex128 everywhere, FP64 on CUDA cores                  */
+    JET_PREC_FP16X3 = 6   /* x * 2^s = hi + lo in FP16, one power-of-two scale s per
+                             operand row and 32-wide K chunk (undone exactly when the
+                             chunk is added up); hi*hi + hi*lo + lo*hi                   */
 } jet_precision;
 
 typedef struct {

@@ -97,7 +97,7 @@ int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_opti
         auto net = std::make_unique<jet_network>();
         if (opt) net->opt = *opt;
         else jet_options_default(&net->opt);
-        if (net->opt.precision < JET_PREC_FP32 || net->opt.precision > JET_PREC_FP64)
+        if (net->opt.precision < JET_PREC_FP32 || net->opt.precision > JET_PREC_FP16X3)
             fail(JET_EINVAL, "unknown precision mode");
         if (net->opt.gemm_min_k < 1) net->opt.gemm_min_k = 16;
         int64_t off = 0;

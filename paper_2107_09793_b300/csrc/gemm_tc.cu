@@ -19,6 +19,7 @@
 // time-out the CTA records a status bit, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -35,24 +36,36 @@ constexpr uint32_t TC_TMEM_COLS = 512;   // two chunk buffers x (Re 128 + Im 128
 
 template <int MODE>
 struct TcCfg;
+// FMT: operand format code of the instruction descriptor (F16 0, BF16 1, TF32 2).
+// SCALED: operand rows carry a power-of-two scale per 32-wide K chunk.
 template <>
 struct TcCfg<JET_PREC_TF32> {
-    static constexpr int NP = 2, NT = 1, EB = 4, KIND = 1, STAGES = 4;
+    static constexpr int NP = 2, NT = 1, EB = 4, KIND = 1, STAGES = 4, FMT = 2, CHUNK_K = 64;
+    static constexpr bool SCALED = false;
     __device__ static void term(int t, int &p, int &q) { p = 0; q = 0; }
 };
 template <>
 struct TcCfg<JET_PREC_TF32X3> {
-    static constexpr int NP = 4, NT = 3, EB = 4, KIND = 1, STAGES = 3;
+    static constexpr int NP = 4, NT = 3, EB = 4, KIND = 1, STAGES = 3, FMT = 2, CHUNK_K = 32;
+    static constexpr bool SCALED = false;
     __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }   // lo.lo dropped
 };
 template <>
 struct TcCfg<JET_PREC_BF16X3> {
-    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 3;
+    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 3, FMT = 1, CHUNK_K = 64;
+    static constexpr bool SCALED = false;
+    __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }
+};
+template <>
+struct TcCfg<JET_PREC_FP16X3> {
+    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 3, FMT = 0, CHUNK_K = 64;
+    static constexpr bool SCALED = true;
     __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }
 };
 template <>
 struct TcCfg<JET_PREC_BF16X6> {
-    static constexpr int NP = 6, NT = 6, EB = 2, KIND = 0, STAGES = 2;
+    static constexpr int NP = 6, NT = 6, EB = 2, KIND = 0, STAGES = 2, FMT = 1, CHUNK_K = 32;
+    static constexpr bool SCALED = false;
     // hi=0, mid=1, lo=2: hh, hm, mh, hl, lh, mm
     __device__ static void term(int t, int &p, int &q)
     {
@@ -150,6 +163,18 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
                  : "memory");
 }
 
+#define JET_TMEM_LD8(taddr, r)                                                                                       \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                              \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])    \
+                 : "r"(taddr))
+
+#define JET_TMEM_LD16(taddr, r)                                                                                      \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),   \
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),          \
+                   "=r"(r[15])                                                                                       \
+                 : "r"(taddr))
+
 #define JET_TMEM_LD32(taddr, r)                                                                                      \
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"   \
                  "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                          \
@@ -180,6 +205,9 @@ __device__ __forceinline__ void split_parts(float x, float (&p)[3])
     } else if (MODE == JET_PREC_BF16X3) {
         p[0] = __bfloat162float(__float2bfloat16_rn(x));
         p[1] = __bfloat162float(__float2bfloat16_rn(x - p[0]));
+    } else if (MODE == JET_PREC_FP16X3) {   // x already scaled into FP16 range
+        p[0] = __half2float(__float2half_rn(x));
+        p[1] = __half2float(__float2half_rn(x - p[0]));
     } else {
         p[0] = __bfloat162float(__float2bfloat16_rn(x));
         const float r = x - p[0];
@@ -200,6 +228,7 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
     constexpr int NP = TcCfg<MODE>::NP, EB = TcCfg<MODE>::EB, NPH = NP / 2;
     __shared__ float2 tile[SPLIT_TR][SPLIT_TK + 1];
     __shared__ int64_t rowOff[SPLIT_TR], kOff[SPLIT_TK];
+    __shared__ float mul[SPLIT_TR];   // SCALED: 2^s of each row of this 64-wide chunk
     const int tid = threadIdx.x;
     const int64_t k_tiles = (a.k_pad + SPLIT_TK - 1) / SPLIT_TK;
     const int64_t tiles = (a.rows_pad / SPLIT_TR) * k_tiles;
@@ -251,6 +280,31 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
                 tile[r][kk] = (ro >= 0 && ko >= 0) ? __ldg(S + ro + ko) : make_float2(0.f, 0.f);
             }
             __syncthreads();
+            if (TcCfg<MODE>::SCALED) {
+                // one power-of-two scale per (row, 64-wide K chunk = this tile's columns):
+                // the chunk's largest |re| or |im| lands in [2^14, 2^15), inside FP16's range
+                const int r = tid >> 3, sub = tid & 7;
+                float m = 0.f;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float2 v = tile[r][sub * 8 + q];
+                    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+                }
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
+                int e = 0;
+                if (m > 0.f) {
+                    frexpf(m, &e);                     // m = f * 2^e, f in [0.5, 1)
+                    e = max(-100, min(100, 15 - e));   // m * 2^e in [2^14, 2^15)
+                }
+                if (sub == 0) {
+                    mul[r] = ldexpf(1.f, e);
+                    const int64_t n_ch = (a.k_pad + 63) >> 6;
+                    ((float *)a.scales)[(inst * n_ch + kt) * a.rows_pad + row0 + r] = ldexpf(1.f, -e);
+                }
+                __syncthreads();
+            }
 #pragma unroll
             for (int i = 0; i < (SPLIT_TR * SPLIT_TK / 2) / 256; ++i) {
                 const int idx = tid + 256 * i;
@@ -258,7 +312,14 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
                 const int64_t k = k0 + kp;
                 if (k >= a.k_pad) continue;
                 const int64_t e = (row0 + r) * a.k_pad + k;
-                const float2 v0 = tile[r][kp], v1 = tile[r][kp + 1];
+                float2 v0 = tile[r][kp], v1 = tile[r][kp + 1];
+                if (TcCfg<MODE>::SCALED) {
+                    const float f = mul[r];
+                    v0.x *= f;
+                    v0.y *= f;
+                    v1.x *= f;
+                    v1.y *= f;
+                }
                 float re0[3], re1[3], im0[3], im1[3];
                 split_parts<MODE>(v0.x, re0);
                 split_parts<MODE>(v1.x, re1);
@@ -266,7 +327,12 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
                 split_parts<MODE>(v1.y, im1);
 #pragma unroll
                 for (int p = 0; p < NPH; ++p) {
-                    if (EB == 2) {
+                    if (EB == 2 && TcCfg<MODE>::FMT == 0) {
+                        __half2 *pr = (__half2 *)((__half *)base + (int64_t)p * plane_elems + e);
+                        __half2 *pi = (__half2 *)((__half *)base + (int64_t)(NPH + p) * plane_elems + e);
+                        *pr = __floats2half2_rn(re0[p], re1[p]);
+                        *pi = __floats2half2_rn(im0[p], im1[p]);
+                    } else if (EB == 2) {
                         __nv_bfloat162 *pr = (__nv_bfloat162 *)((__nv_bfloat16 *)base + (int64_t)p * plane_elems + e);
                         __nv_bfloat162 *pi =
                             (__nv_bfloat162 *)((__nv_bfloat16 *)base + (int64_t)(NPH + p) * plane_elems + e);
@@ -323,7 +389,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     constexpr int STAGE_BYTES = 2 * NP * TC_PLANE_TILE;
     constexpr int KE = TC_ROWB / Cfg::EB;               // K elements per stage
     constexpr int KSUB = TC_ROWB / 32;                   // MMAs of 32 bytes of K per stage
-    constexpr int CHUNK_KB = 32 / KE > 0 ? 32 / KE : 1;  // stages per 32-wide K chunk
+    constexpr int CHUNK_KB = Cfg::CHUNK_K / KE > 0 ? Cfg::CHUNK_K / KE : 1;   // stages per K chunk
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2 * S + 4];
     __shared__ uint32_t tmem_holder;
@@ -391,7 +457,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         if (lane == 0) {
             // kind::f16 / kind::tf32 instruction descriptor: FP32 D, K-major A and B, M=128, N=128;
             // the negate-A variant accumulates (-Ai).Bi into the real part
-            const uint32_t fmt = Cfg::KIND == 0 ? 1u : 2u;
+            const uint32_t fmt = (uint32_t)Cfg::FMT;
             const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
                                    ((uint32_t)(TC_BM >> 4) << 24);
             const uint32_t idesc_neg = idesc | (1u << 13);
@@ -458,16 +524,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t base = tmem + buf * 2 * TC_BN + ((uint32_t)(quarter * 32) << 16) + half * 64;
+                // SCALED: undo the operands' power-of-two chunk scales (exact)
+                float fm = 1.f;
+                const float *fn = nullptr;
+                if (Cfg::SCALED) {
+                    const int64_t instA = ((const int32_t *)a.zA)[inst] / NP, instB = ((const int32_t *)a.zB)[inst] / NP;
+                    const int64_t row = (int64_t)tm * TC_BM + quarter * 32 + lane;
+                    fm = ((const float *)a.scaleA)[(instA * n_chunks + c) * a.m_pad + row];
+                    fn = (const float *)a.scaleB + (instB * n_chunks + c) * a.n_pad + (int64_t)tn * TC_BN + half * 64;
+                }
+                // 16 columns per TMEM load (8 in the scaled mode, whose scales need registers too)
+                constexpr int LW = Cfg::SCALED ? 8 : 16;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t R[32], I[32];
-                    JET_TMEM_LD32(base + h * 32, R);
-                    JET_TMEM_LD32(base + TC_BN + h * 32, I);
+                for (int h = 0; h < 64 / LW; ++h) {
+                    uint32_t R[LW], I[LW];
+                    if (LW == 8) {
+                        JET_TMEM_LD8(base + h * LW, R);
+                        JET_TMEM_LD8(base + TC_BN + h * LW, I);
+                    } else {
+                        JET_TMEM_LD16(base + h * LW, R);
+                        JET_TMEM_LD16(base + TC_BN + h * LW, I);
+                    }
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        racc[h * 32 + j] += __uint_as_float(R[j]);
-                        iacc[h * 32 + j] += __uint_as_float(I[j]);
+                    for (int j = 0; j < LW; ++j) {
+                        if (Cfg::SCALED) {
+                            const float f = fm * __ldg(fn + h * LW + j);
+                            racc[h * LW + j] = fmaf(__uint_as_float(R[j]), f, racc[h * LW + j]);
+                            iacc[h * LW + j] = fmaf(__uint_as_float(I[j]), f, iacc[h * LW + j]);
+                        } else {
+                            racc[h * LW + j] += __uint_as_float(R[j]);
+                            iacc[h * LW + j] += __uint_as_float(I[j]);
+                        }
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -515,6 +603,7 @@ int tc_planes(int mode)
     case JET_PREC_TF32X3: return TcCfg<JET_PREC_TF32X3>::NP;
     case JET_PREC_BF16X3: return TcCfg<JET_PREC_BF16X3>::NP;
     case JET_PREC_BF16X6: return TcCfg<JET_PREC_BF16X6>::NP;
+    case JET_PREC_FP16X3: return TcCfg<JET_PREC_FP16X3>::NP;
     default: return 0;
     }
 }
@@ -533,6 +622,7 @@ cudaError_t set_tc_smem_limits()
     JET_TCSM(JET_PREC_TF32X3);
     JET_TCSM(JET_PREC_BF16X3);
     JET_TCSM(JET_PREC_BF16X6);
+    JET_TCSM(JET_PREC_FP16X3);
 #undef JET_TCSM
     return e;
 }
@@ -551,6 +641,7 @@ cudaError_t launch_tc_split(const TcSplitArgs &a, const LaunchCfg &c, cudaStream
     case JET_PREC_TF32X3: JET_SPLIT(JET_PREC_TF32X3); break;
     case JET_PREC_BF16X3: JET_SPLIT(JET_PREC_BF16X3); break;
     case JET_PREC_BF16X6: JET_SPLIT(JET_PREC_BF16X6); break;
+    case JET_PREC_FP16X3: JET_SPLIT(JET_PREC_FP16X3); break;
     default: return cudaErrorInvalidValue;
     }
 #undef JET_SPLIT
@@ -585,6 +676,9 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, const LaunchCfg &c, cudaStream_t
     case JET_PREC_BF16X6:
         tc_gemm_kernel<JET_PREC_BF16X6><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_BF16X6>(), s>>>(a);
         break;
+    case JET_PREC_FP16X3:
+        tc_gemm_kernel<JET_PREC_FP16X3><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_FP16X3>(), s>>>(a);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -614,7 +708,9 @@ int encode_tc_maps(TcGemmArgs &a)
     EncodeTiledFn fn = encode_fn();
     if (!fn) return -1;
     const int eb = tc_elem_bytes(a.mode);
-    const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = eb == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : a.mode == JET_PREC_FP16X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint32_t box[3] = {(cuuint32_t)(TC_ROWB / eb), (cuuint32_t)TC_BM, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     {

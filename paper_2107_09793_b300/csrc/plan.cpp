@@ -785,12 +785,21 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 const int64_t Mv = dimprod(fM), Nv = dimprod(fN);
                 const int64_t m_pad = (Mv + T - 1) / T * T, n_pad = (Nv + T - 1) / T * T;
                 const int64_t k_pad = (nK + kblk - 1) / kblk * kblk;
-                auto split_child = [&](int32_t id, const View &V, const std::vector<int64_t> &f, int64_t rows_pad) {
+                const bool scaled = net.opt.precision == JET_PREC_FP16X3;
+                auto split_child = [&](int32_t id, const View &V, const std::vector<int64_t> &f, int64_t rows_pad,
+                                       size_t &scale_off) {
                     const int64_t ninst = node[id].n_inst;
                     const size_t nbytes_p = (size_t)ninst * NP * rows_pad * k_pad * eb;
                     size_t off = arena.alloc(nbytes_p);
                     scratch.push_back(off);
                     scratch_bytes.push_back(nbytes_p);
+                    scale_off = 0;
+                    if (scaled) {   // one float per (instance, 64-wide K chunk, row)
+                        const size_t sb = (size_t)ninst * ((k_pad + 63) / 64) * rows_pad * 4;
+                        scale_off = arena.alloc(sb);
+                        scratch.push_back(scale_off);
+                        scratch_bytes.push_back(sb);
+                    }
                     TcSplitArgs sa;
                     std::memset(&sa, 0, sizeof sa);
                     sa.rows = dimprod(f);
@@ -840,6 +849,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     std::memcpy(blob.bytes.data() + so, &sa, sizeof sa);
                     blob.patch_field(so, offsetof(TcSplitArgs, ptrSrc), BASE_BLOB, (int64_t)o_ps);
                     blob.patch_field(so, offsetof(TcSplitArgs, planes), BASE_ARENA, (int64_t)off);
+                    if (scaled) blob.patch_field(so, offsetof(TcSplitArgs, scales), BASE_ARENA, (int64_t)scale_off);
                     Op op;
                     op.kind = OpKind::TcSplit;
                     op.node = v;
@@ -867,8 +877,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     P.bytes_executed += op.bytes;
                     return off;
                 };
-                size_t offA = split_child(idM, VM, fM, m_pad);
-                size_t offB = split_child(idN, VN, fN, n_pad);
+                size_t sclA = 0, sclB = 0;
+                size_t offA = split_child(idM, VM, fM, m_pad, sclA);
+                size_t offB = split_child(idN, VN, fN, n_pad, sclB);
                 std::vector<int32_t> zA, zB;
                 for (int64_t i = 0; i < N.n_inst; ++i) {
                     zA.push_back(instM[i] * NP);
@@ -897,6 +908,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 blob.patch_field(so, offsetof(TcGemmArgs, zB), BASE_BLOB, (int64_t)o_zb);
                 blob.patch_field(so, offsetof(TcGemmArgs, ptrC), BASE_BLOB, (int64_t)o_c);
                 blob.patch_field(so, offsetof(TcGemmArgs, status), BASE_STATUS, 0);
+                if (scaled) {
+                    blob.patch_field(so, offsetof(TcGemmArgs, scaleA), BASE_ARENA, (int64_t)sclA);
+                    blob.patch_field(so, offsetof(TcGemmArgs, scaleB), BASE_ARENA, (int64_t)sclB);
+                }
                 Op op;
                 op.kind = OpKind::GemmTc;
                 op.node = v;

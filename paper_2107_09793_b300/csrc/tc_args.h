@@ -15,6 +15,7 @@
 struct TcSplitArgs {
     uint64_t ptrSrc;                 // device array of n_inst source addresses (complex64)
     uint64_t planes;                 // plane base (device)
+    uint64_t scales;                 // FP16X3: float 2^-s per [instance][K chunk][row] (else 0)
     int64_t rows, k, rows_pad, k_pad;
     int32_t n_inst, n_planes;
     int32_t rank_r, rank_k;
@@ -33,6 +34,7 @@ struct TcGemmArgs {
     uint64_t zA, zB;                 // device int32[n_inst]: first plane index of each instance
     uint64_t ptrC;                   // device array of n_inst output addresses (complex64)
     uint64_t status;                 // device uint32 error word (bounded-wait time-outs)
+    uint64_t scaleA, scaleB;         // FP16X3: 2^-s per [instance][K chunk][row] of each operand
     int64_t M, N, K;
     int64_t m_pad, n_pad, k_pad;
     int64_t planesA_total, planesB_total;   // plane count along the maps' third dimension

@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libjet.so")
 
 JET_OK, JET_EINVAL, JET_ENOMEM, JET_ECUDA, JET_ETIMEOUT, JET_ESTATE = 0, -1, -2, -3, -4, -5
-PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp64": 5}
+PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp64": 5, "fp16x3": 6}
 
 EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", "jet_tensor_update",
            "jet_tensors_upload", "jet_network_n_values", "jet_path_set", "jet_path_get",

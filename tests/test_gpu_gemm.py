@@ -11,7 +11,7 @@ from paper_2107_09793_b300 import jet
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "fp64": 1e-12, "tf32x3": 1e-5, "bf16x3": 1e-5, "bf16x6": 1e-5, "tf32": 3e-3}
+TOL = {"fp32": 1e-5, "fp64": 1e-12, "tf32x3": 1e-5, "bf16x3": 1e-5, "bf16x6": 1e-5, "fp16x3": 1e-5, "tf32": 3e-3}
 
 
 def _rand(rng, shape):
@@ -62,7 +62,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32", "tf32x3", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3"])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_gemm_layouts(prec, case):
     la, lb, dd = CASES[case]
