@@ -167,6 +167,29 @@ int jet_path_get(const jet_network *net, int32_t *pairs_out);
  * Open legs count as fixed (dim 1) because every amplitude fixes them. */
 int jet_path_greedy(jet_network *net, uint64_t seed, int32_t n_trials, double *flop_out);
 
+/* Batch-aware form of jet_path_greedy for a batch of amplitudes contracted
+ * together with shared work reused (Sections 3.2 and 4: several amplitudes
+ * with one path, only the bras differ).  A tree node holding open legs L is
+ * computed once per distinct restriction of the batch's output digits to L, so
+ * every size and FLOP in the greedy score is weighted by that count: subtrees
+ * without bras are shared by the whole batch and the planner keeps the bras
+ * late when that is cheaper.  Besides the pairwise passes of jet_path_greedy it
+ * runs linear passes (one tensor grows by absorbing the neighbouring leaf with
+ * the smallest weighted result), from leaf 0 and, on odd trials, from a seeded
+ * random leaf, and two leaf-order linear paths: leaves absorbed strictly in
+ * index order (for a circuit listed initial states first, then gates in time
+ * order: the state-vector order), and the lowest-index leaf sharing a label
+ * with the growing tensor (initial states join when first touched).  Steps whose weighted result (instances x elements) exceeds
+ * max_elems are taken only when no other step is left, and the kept path is
+ * the one of lowest FLOP among those whose largest weighted intermediate fits
+ * max_elems (none fits: the smallest such peak).  max_elems <= 0: no cap.
+ * outputs: n_amps x n_out digits, HOST memory, the jet_contract layout (only
+ * read during the call).  flop_out receives the batch's total FLOP (instances
+ * x node FLOP, summed).  Errors: JET_EINVAL (NULL, n_amps < 1, digit out of
+ * range), JET_ESTATE (open legs not declared). */
+int jet_path_greedy_batch(jet_network *net, int32_t n_amps, const int32_t *outputs, int64_t max_elems,
+                          uint64_t seed, int32_t n_trials, double *flop_out);
+
 /* Slice the given closed labels (Section 2.4); n = 0 clears the slicing.
  * Slice id s is the mixed-radix number over the sliced labels, the first label
  * most significant.  Errors: JET_EINVAL (open or unknown label, duplicate). */

@@ -11,6 +11,9 @@ Three independent routes to the same numbers:
                         Eq. sequence) with numpy.tensordot as the pairwise step;
                         slicing by fixing index values (Section 2.4, Eq. sliced_sum);
                         bras attached as literal rank-1 tensors (Section 2.2.1).
+  * sector       (O1 for bosonic networks): the same state vector restricted to
+                        one total-photon sector (beamsplitters conserve the photon
+                        number), so 16-mode, d = 4 lattices fit a host.
   * naive        (A3): the literal sum over every index assignment of the product
                         of all tensor entries (Eq. naive_summation), tiny cases only.
 Every function here is pinned by tests against closed forms, brute force and
@@ -20,7 +23,8 @@ from .statevector import sv_state, sv_amplitudes, sv_env, gate_arrays
 from .einsum import (contract_network, greedy_path, attach_bras, slice_network,
                      amplitude, sliced_partials, network_flops)
 from .naive import naive_sum
+from .sector import sector_amplitudes, sector_dim
 
 __all__ = ["sv_state", "sv_amplitudes", "sv_env", "gate_arrays", "contract_network",
            "greedy_path", "attach_bras", "slice_network", "amplitude", "sliced_partials",
-           "network_flops", "naive_sum"]
+           "network_flops", "naive_sum", "sector_amplitudes", "sector_dim"]

@@ -6,7 +6,7 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SO = os.path.join(HERE, "liboracle.so")
-SRC = [os.path.join(HERE, "sv.c")]
+SRC = [os.path.join(HERE, "sv.c"), os.path.join(HERE, "sector.c")]
 
 
 def build(force: bool = False) -> str:

@@ -231,6 +231,31 @@ int jet_path_greedy(jet_network *net, uint64_t seed, int32_t n_trials, double *f
     });
 }
 
+int jet_path_greedy_batch(jet_network *net, int32_t n_amps, const int32_t *outputs, int64_t max_elems,
+                          uint64_t seed, int32_t n_trials, double *flop_out)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (!net->open_set) fail(JET_ESTATE, "open legs not declared (jet_network_set_open)");
+        if (n_amps < 1 || !outputs) fail(JET_EINVAL, "need n_amps >= 1 and an outputs array");
+        const int32_t n_open = (int32_t)net->open.size();
+        for (int32_t b = 0; b < n_amps; ++b)
+            for (int32_t j = 0; j < n_open; ++j) {
+                const int32_t v = outputs[(int64_t)b * n_open + j];
+                if (v < 0 || v >= net->labels.at(net->open[j]).dim)
+                    fail(JET_EINVAL, "output digit out of range at amplitude " + std::to_string(b));
+            }
+        double f = 0;
+        auto p = greedy_path(*net, seed, std::max(n_trials, 1), &f, n_amps, outputs, (double)max_elems);
+        validate_path(*net, p);
+        net->path = p;
+        ++net->path_version;
+        net->flop_planned = f;
+        if (flop_out) *flop_out = f;
+        invalidate_plan(*net);
+    });
+}
+
 int jet_slice(jet_network *net, int32_t n, const int64_t *labels)
 {
     return guarded([&] {

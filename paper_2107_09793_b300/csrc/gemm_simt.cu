@@ -50,12 +50,15 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ 
     __shared__ V As[SB_K][SB_M + 1];
     __shared__ V Bs[SB_K][SB_N + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t m0 = (int64_t)blockIdx.y * SB_M, n0 = (int64_t)blockIdx.x * SB_N;
-    const int64_t inst = blockIdx.z;
+    const int64_t M = a.M, N = a.N, K = a.K;
+    const int64_t n0 = (int64_t)blockIdx.x * SB_N, tiles_m = (M + SB_M - 1) / SB_M;
+    // row tiles and instances beyond the grid's y/z extent are walked by stride
+    for (int64_t inst = blockIdx.z; inst < a.n_inst; inst += gridDim.z)
+    for (int64_t mt = blockIdx.y; mt < tiles_m; mt += gridDim.y) {
+    const int64_t m0 = mt * SB_M;
     const V *__restrict__ A = (const V *)((const uint64_t *)a.ptrA)[inst];
     const V *__restrict__ B = (const V *)((const uint64_t *)a.ptrB)[inst];
     V *__restrict__ C = (V *)((const uint64_t *)a.ptrC)[inst];
-    const int64_t M = a.M, N = a.N, K = a.K;
     V acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -110,6 +113,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const __grid_constant__ 
             int64_t gn = n0 + tx + 16 * j;
             if (gn < N) C[gm * N + gn] = acc[i][j];
         }
+    }
     }
 }
 

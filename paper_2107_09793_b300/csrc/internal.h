@@ -156,8 +156,13 @@ struct Network {
 Tree build_tree(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path);
 PathCost path_cost(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
                    const std::vector<int64_t> &fixed);
-std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_t seed,
-                                                     int32_t n_trials, double *flop_out);
+// outputs != NULL selects the batch planner: every node is costed once per
+// distinct restriction of the outputs (n_amps x n_open digits) to the open legs
+// under it, linear passes join the pairwise ones, and paths whose largest
+// instance-weighted intermediate exceeds max_elems (> 0) lose to those under it.
+std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_t seed, int32_t n_trials,
+                                                     double *flop_out, int32_t n_amps = 1,
+                                                     const int32_t *outputs = nullptr, double max_elems = 0);
 std::vector<int64_t> slice_auto(const Network &net, int64_t max_elems, int32_t min_n, int32_t max_n);
 double reuse_aware_flop(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
                         const std::vector<int64_t> &sliced);

@@ -404,8 +404,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         N.view = dense_view(out, net);
         max_inter = std::max(max_inter, N.view.size);
         // small direct contractions are batched per tree level into one launch
+        // (their full offset tables are int32: operands below 2^31 elements)
         N.small = !N.use_gemm && N.view.size <= 4096 && nK <= 2048 &&
-                  (double)N.n_inst * (double)N.view.size * (double)nK <= (double)(1 << 24);
+                  (double)N.n_inst * (double)N.view.size * (double)nK <= (double)(1 << 24) &&
+                  VA.size <= INT32_MAX && VB.size <= INT32_MAX;
         N.depth = 1 + std::max(node[a].depth, node[b].depth);
     }
 
@@ -479,13 +481,20 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             auto strideB = [&](int64_t l) { int p = find_pos(VB.labels, l); return p < 0 ? 0 : VB.strides[p]; };
             DirectArgs d;
             std::memset(&d, 0, sizeof d);
-            // output split: cols = longest suffix with product <= JET_COLMAX
+            // output split: cols = longest suffix with product <= JET_COLMAX whose
+            // offsets fit the int32 tables (labels with larger strides are decoded)
             const auto &C = Cv;
             size_t ncol_labels = 0;
-            int64_t ncols = 1;
-            while (ncol_labels < C.labels.size() &&
-                   ncols * C.dims[C.labels.size() - 1 - ncol_labels] <= JET_COLMAX) {
-                ncols *= C.dims[C.labels.size() - 1 - ncol_labels];
+            int64_t ncols = 1, col_maxA = 0, col_maxB = 0;
+            while (ncol_labels < C.labels.size()) {
+                const size_t li = C.labels.size() - 1 - ncol_labels;
+                const int64_t dm = C.dims[li] - 1;
+                if (ncols * C.dims[li] > JET_COLMAX || col_maxA + dm * strideA(C.labels[li]) > INT32_MAX ||
+                    col_maxB + dm * strideB(C.labels[li]) > INT32_MAX)
+                    break;
+                ncols *= C.dims[li];
+                col_maxA += dm * strideA(C.labels[li]);
+                col_maxB += dm * strideB(C.labels[li]);
                 ++ncol_labels;
             }
             size_t nrow_labels = C.labels.size() - ncol_labels;
@@ -522,9 +531,16 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             std::vector<int64_t> Kd;
             for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
             size_t nklo_labels = 0;
-            int64_t nklo = 1;
-            while (nklo_labels < Ks.size() && nklo * Kd[Ks.size() - 1 - nklo_labels] <= JET_KLOMAX) {
-                nklo *= Kd[Ks.size() - 1 - nklo_labels];
+            int64_t nklo = 1, klo_maxA = 0, klo_maxB = 0;
+            while (nklo_labels < Ks.size()) {
+                const size_t li = Ks.size() - 1 - nklo_labels;
+                const int64_t dm = Kd[li] - 1;
+                if (nklo * Kd[li] > JET_KLOMAX || klo_maxA + dm * strideA(Ks[li]) > INT32_MAX ||
+                    klo_maxB + dm * strideB(Ks[li]) > INT32_MAX)
+                    break;
+                nklo *= Kd[li];
+                klo_maxA += dm * strideA(Ks[li]);
+                klo_maxB += dm * strideB(Ks[li]);
                 ++nklo_labels;
             }
             size_t nkhi_labels = Ks.size() - nklo_labels;
@@ -885,7 +901,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     zA.push_back(instM[i] * NP);
                     zB.push_back(instN[i] * NP);
                 }
-                if (N.n_inst > 65535) fail(JET_EINVAL, "too many instances of one GEMM node");
+                if (N.n_inst * NP > INT32_MAX) fail(JET_EINVAL, "too many instances of one GEMM node");
                 TcGemmArgs g;
                 std::memset(&g, 0, sizeof g);
                 g.M = Mv;
@@ -922,8 +938,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 op.bytes = bytes;
                 op.grid_x = (int32_t)(n_pad / T);
                 op.grid_y = (int32_t)(m_pad / T);
-                op.grid_z = (int32_t)N.n_inst;
-                if (op.grid_y > 65535) fail(JET_EINVAL, "GEMM M too large");
+                op.grid_z = (int32_t)N.n_inst;   // persistent launch: the tile count only
                 P.ops.push_back(op);
             } else {
             int formM = form(VM, fM), formN = form(VN, fN);
@@ -988,7 +1003,6 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             } else {
                 for (int64_t i = 0; i < N.n_inst; ++i) gB.push_back(base_ref(idN, instN[i]));
             }
-            if (N.n_inst > 65535) fail(JET_EINVAL, "too many instances of one GEMM node");
             GemmArgs g;
             std::memset(&g, 0, sizeof g);
             g.M = dimprod(fM);
@@ -1012,10 +1026,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             op.flop = flop;
             op.bytes = bytes;
             op.variant = fp64 ? 1 : 0;
+            if ((g.N + 63) / 64 > INT32_MAX) fail(JET_EINVAL, "GEMM N too large");
             op.grid_x = (int32_t)((g.N + 63) / 64);
-            op.grid_y = (int32_t)((g.M + 63) / 64);
-            op.grid_z = (int32_t)N.n_inst;
-            if (op.grid_y > 65535) fail(JET_EINVAL, "GEMM M too large");
+            op.grid_y = (int32_t)std::min<int64_t>((g.M + 63) / 64, 65535);
+            op.grid_z = (int32_t)std::min<int64_t>(N.n_inst, 65535);
             P.ops.push_back(op);
             }
         }

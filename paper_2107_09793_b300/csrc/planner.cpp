@@ -8,6 +8,8 @@
 // of the sliced labels that occur under it, not once per slice.
 #include <algorithm>
 #include <cmath>
+#include <iterator>
+#include <map>
 #include <set>
 #include <unordered_set>
 
@@ -131,10 +133,12 @@ double reuse_aware_flop(const Network &net, const std::vector<std::pair<int32_t,
 // ------------------------------------------------------------ greedy path
 namespace {
 struct Cand {
+    int over;              // result above the memory cap: taken only when nothing else is left
     double score, flop;
     int32_t a, b;
     bool operator<(const Cand &o) const
     {
+        if (over != o.over) return over < o.over;
         if (score != o.score) return score < o.score;
         if (flop != o.flop) return flop < o.flop;
         if (a != o.a) return a < o.a;
@@ -156,13 +160,58 @@ struct SplitMix {
 };
 }  // namespace
 
+// Number of distinct restrictions of a batch of output patterns to a set of
+// open legs: how many instances a tree node holding those legs has when the
+// batch is contracted with shared work reused (Section 3.2; the legs are fixed
+// by the amplitudes' bras).  Memoised per leg set.
+struct BatchInstances {
+    int32_t n_amps = 0, n_out = 0;
+    const int32_t *outputs = nullptr;                 // n_amps x n_out digits
+    std::unordered_map<int64_t, int32_t> digit;       // open label -> digit position
+    std::map<std::vector<int32_t>, double> memo;
+
+    double count(const std::vector<int32_t> &pos)
+    {
+        if (pos.empty() || n_amps <= 1) return 1;
+        auto it = memo.find(pos);
+        if (it != memo.end()) return it->second;
+        std::vector<int32_t> rows(n_amps);
+        for (int32_t i = 0; i < n_amps; ++i) rows[i] = i;
+        auto less = [&](int32_t x, int32_t y) {
+            for (int32_t p : pos) {
+                const int32_t dx = outputs[(size_t)x * n_out + p], dy = outputs[(size_t)y * n_out + p];
+                if (dx != dy) return dx < dy;
+            }
+            return false;
+        };
+        std::sort(rows.begin(), rows.end(), less);
+        double distinct = 1;
+        for (int32_t i = 1; i < n_amps; ++i)
+            if (less(rows[i - 1], rows[i])) distinct += 1;
+        memo[pos] = distinct;
+        return distinct;
+    }
+};
+
+static std::vector<int32_t> merge_pos(const std::vector<int32_t> &a, const std::vector<int32_t> &b)
+{
+    std::vector<int32_t> out;
+    std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(out));
+    return out;
+}
+
+// One greedy pass.  Score of a candidate pair = (elements written) - (elements
+// freed), each tensor counted once per instance it has under the batch `bt`
+// (one instance each when bt is null: a single amplitude).
 static std::vector<std::pair<int32_t, int32_t>> greedy_once(const Network &net, SplitMix *rng,
-                                                            double temperature, double *flop_out)
+                                                            double temperature, double *flop_out,
+                                                            BatchInstances *bt, double cap, double *peak_out)
 {
     auto fixed = fixed_set(net, {});
     int32_t n = (int32_t)net.leaves.size();
     std::vector<std::vector<int64_t>> lab(2 * n);
-    std::vector<double> size(2 * n, 0);
+    std::vector<double> size(2 * n, 0), inst(2 * n, 1);
+    std::vector<std::vector<int32_t>> opos(2 * n);    // open-leg digit positions under each node
     std::vector<char> alive(2 * n, 0);
     std::unordered_map<int64_t, std::vector<int32_t>> owner;
     for (int32_t i = 0; i < n; ++i) {
@@ -170,6 +219,14 @@ static std::vector<std::pair<int32_t, int32_t>> greedy_once(const Network &net, 
         size[i] = label_size(net, lab[i], fixed);
         alive[i] = 1;
         for (int64_t l : lab[i]) owner[l].push_back(i);
+        if (bt) {
+            for (int64_t l : lab[i]) {
+                auto it = bt->digit.find(l);
+                if (it != bt->digit.end()) opos[i].push_back(it->second);
+            }
+            std::sort(opos[i].begin(), opos[i].end());
+            inst[i] = bt->count(opos[i]);
+        }
     }
     std::set<Cand> cands;
     std::map<std::pair<int32_t, int32_t>, Cand> by_pair;
@@ -178,14 +235,15 @@ static std::vector<std::pair<int32_t, int32_t>> greedy_once(const Network &net, 
         if (by_pair.count({a, b})) return;
         auto out = sym_diff(lab[a], lab[b]);
         auto un = set_union(lab[a], lab[b]);
+        const double io = bt ? bt->count(merge_pos(opos[a], opos[b])) : 1.0;
         double so = label_size(net, out, fixed);
-        double score = so - size[a] - size[b];
+        double score = io * so - inst[a] * size[a] - inst[b] * size[b];
         if (rng) {
             double g = -std::log(-std::log(std::max(rng->uniform(), 1e-300)));
             double ls = (score >= 0 ? 1 : -1) * std::log2(1 + std::fabs(score));
             score = ls - temperature * g;
         }
-        Cand c{score, 8.0 * label_size(net, un, fixed), a, b};
+        Cand c{io * so > cap ? 1 : 0, score, io * 8.0 * label_size(net, un, fixed), a, b};
         cands.insert(c);
         by_pair[{a, b}] = c;
     };
@@ -205,7 +263,7 @@ static std::vector<std::pair<int32_t, int32_t>> greedy_once(const Network &net, 
         if (kv.second.size() == 2) add_pair(kv.second[0], kv.second[1]);
 
     std::vector<std::pair<int32_t, int32_t>> path;
-    double total = 0;
+    double total = 0, peak = 0;
     int32_t next = n;
     int32_t n_alive = n;
     while (n_alive > 1) {
@@ -229,7 +287,10 @@ static std::vector<std::pair<int32_t, int32_t>> greedy_once(const Network &net, 
         int32_t c = next++;
         lab[c] = sym_diff(lab[a], lab[b]);
         size[c] = label_size(net, lab[c], fixed);
-        total += 8.0 * label_size(net, set_union(lab[a], lab[b]), fixed);
+        opos[c] = merge_pos(opos[a], opos[b]);
+        inst[c] = bt ? bt->count(opos[c]) : 1.0;
+        total += inst[c] * 8.0 * label_size(net, set_union(lab[a], lab[b]), fixed);
+        peak = std::max(peak, inst[c] * size[c]);
         alive[a] = alive[b] = 0;
         alive[c] = 1;
         --n_alive;
@@ -248,25 +309,195 @@ static std::vector<std::pair<int32_t, int32_t>> greedy_once(const Network &net, 
         path.push_back({a, b});
     }
     if (flop_out) *flop_out = total;
+    if (peak_out) *peak_out = peak;
     return path;
 }
 
-std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_t seed,
-                                                     int32_t n_trials, double *flop_out)
+// One linear (sequential) greedy pass: a single tensor grows from leaf
+// `start`, each step absorbing the leaf that shares a label with it and leaves
+// the smallest instance-weighted result (ties: smaller step FLOP, smaller id).
+// For a circuit this includes the state-vector (Schroedinger) order and its
+// light-cone variants, which pairwise greedy rarely finds.
+static std::vector<std::pair<int32_t, int32_t>> greedy_linear(const Network &net, int32_t start, SplitMix *rng,
+                                                              double temperature, double *flop_out,
+                                                              BatchInstances *bt, double cap, double *peak_out)
+{
+    auto fixed = fixed_set(net, {});
+    const int32_t n = (int32_t)net.leaves.size();
+    std::vector<std::vector<int32_t>> lpos(n);
+    if (bt)
+        for (int32_t i = 0; i < n; ++i) {
+            for (int64_t l : net.leaves[i].labels) {
+                auto it = bt->digit.find(l);
+                if (it != bt->digit.end()) lpos[i].push_back(it->second);
+            }
+            std::sort(lpos[i].begin(), lpos[i].end());
+        }
+    std::vector<char> used(n, 0);
+    std::vector<int64_t> T = net.leaves[start].labels;
+    std::vector<int32_t> tpos = lpos[start];
+    used[start] = 1;
+    int32_t tid = start;
+    std::vector<std::pair<int32_t, int32_t>> path;
+    double total = 0, peak = 0;
+    for (int32_t k = 0; k + 1 < n; ++k) {
+        std::set<int32_t> nb;
+        for (int64_t l : T) {
+            const LabelInfo &li = net.labels.at(l);
+            for (int q = 0; q < li.n_owner; ++q)
+                if (li.owner[q] >= 0 && !used[li.owner[q]]) nb.insert(li.owner[q]);
+        }
+        if (nb.empty())   // disconnected remainder: take the smallest leaf
+            for (int32_t i = 0; i < n; ++i)
+                if (!used[i]) {
+                    if (nb.empty() || net.leaves[i].size < net.leaves[*nb.begin()].size) nb = {i};
+                }
+        double best_s = 0, best_f = 0, best_w = 0;
+        int best_over = 0;
+        int32_t best = -1;
+        for (int32_t x : nb) {
+            auto out = sym_diff(T, net.leaves[x].labels);
+            const double io = bt ? bt->count(merge_pos(tpos, lpos[x])) : 1.0;
+            const double w = io * label_size(net, out, fixed);
+            const int over = w > cap ? 1 : 0;
+            double sc = w;
+            const double f = io * 8.0 * label_size(net, set_union(T, net.leaves[x].labels), fixed);
+            if (rng) {
+                const double g = -std::log(-std::log(std::max(rng->uniform(), 1e-300)));
+                sc = std::log2(1 + sc) - temperature * g;
+            }
+            if (best < 0 || over < best_over || (over == best_over && (sc < best_s || (sc == best_s && f < best_f)))) {
+                best = x;
+                best_s = sc;
+                best_f = f;
+                best_w = w;
+                best_over = over;
+            }
+        }
+        total += best_f;
+        peak = std::max(peak, best_w);
+        T = sym_diff(T, net.leaves[best].labels);
+        tpos = merge_pos(tpos, lpos[best]);
+        used[best] = 1;
+        path.push_back({std::min(tid, best), std::max(tid, best)});
+        tid = n + k;
+    }
+    if (flop_out) *flop_out = total;
+    if (peak_out) *peak_out = peak;
+    return path;
+}
+
+// Linear path in leaf order.  strict: absorb leaves 1, 2, ... in turn (for a
+// circuit whose leaves are listed in time order with the initial states first,
+// the state-vector order); else: absorb the lowest-index leaf that shares a
+// label with the growing tensor (initial states join when first touched).
+// Weighted FLOP and peak as in the greedy passes.
+static std::vector<std::pair<int32_t, int32_t>> leaf_order_linear(const Network &net, bool strict, double *flop_out,
+                                                                  BatchInstances *bt, double *peak_out)
+{
+    auto fixed = fixed_set(net, {});
+    const int32_t n = (int32_t)net.leaves.size();
+    auto pos_of = [&](int32_t i) {
+        std::vector<int32_t> p;
+        if (bt)
+            for (int64_t l : net.leaves[i].labels) {
+                auto it = bt->digit.find(l);
+                if (it != bt->digit.end()) p.push_back(it->second);
+            }
+        std::sort(p.begin(), p.end());
+        return p;
+    };
+    std::vector<char> used(n, 0);
+    std::vector<int64_t> T = net.leaves[0].labels;
+    std::vector<int32_t> tpos = pos_of(0);
+    used[0] = 1;
+    int32_t tid = 0;
+    std::vector<std::pair<int32_t, int32_t>> path;
+    double total = 0, peak = 0;
+    for (int32_t k = 0; k + 1 < n; ++k) {
+        int32_t x = -1;
+        if (!strict)
+            for (int32_t i = 1; i < n && x < 0; ++i) {
+                if (used[i]) continue;
+                for (int64_t l : net.leaves[i].labels)
+                    if (std::find(T.begin(), T.end(), l) != T.end()) {
+                        x = i;
+                        break;
+                    }
+            }
+        if (x < 0)
+            for (int32_t i = 1; i < n; ++i)
+                if (!used[i]) {
+                    x = i;
+                    break;
+                }
+        tpos = merge_pos(tpos, pos_of(x));
+        const double io = bt ? bt->count(tpos) : 1.0;
+        total += io * 8.0 * label_size(net, set_union(T, net.leaves[x].labels), fixed);
+        T = sym_diff(T, net.leaves[x].labels);
+        peak = std::max(peak, io * label_size(net, T, fixed));
+        used[x] = 1;
+        path.push_back({std::min(tid, x), std::max(tid, x)});
+        tid = n + k;
+    }
+    if (flop_out) *flop_out = total;
+    if (peak_out) *peak_out = peak;
+    return path;
+}
+
+std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_t seed, int32_t n_trials,
+                                                     double *flop_out, int32_t n_amps, const int32_t *outputs,
+                                                     double max_elems)
 {
     if (net.leaves.size() == 1) {
         if (flop_out) *flop_out = 0;
         return {};
     }
-    double best_flop = 0;
-    auto best = greedy_once(net, nullptr, 0, &best_flop);
+    const bool batch_mode = outputs != nullptr;
+    BatchInstances batch, *bt = nullptr;
+    if (batch_mode && n_amps > 1) {
+        batch.n_amps = n_amps;
+        batch.n_out = (int32_t)net.open.size();
+        batch.outputs = outputs;
+        for (int32_t j = 0; j < batch.n_out; ++j) batch.digit[net.open[j]] = j;
+        bt = &batch;
+    }
+    const double cap = max_elems > 0 ? max_elems : INFINITY;
+    // keep the path of lowest FLOP among those whose largest (instance-weighted)
+    // intermediate fits the cap; above the cap, the smaller peak wins
+    double best_flop = 0, best_peak = 0;
+    auto better = [&](double f, double pk) {
+        const bool in = pk <= cap, best_in = best_peak <= cap;
+        if (in != best_in) return in;
+        return in ? f < best_flop : (pk < best_peak || (pk == best_peak && f < best_flop));
+    };
+    auto best = greedy_once(net, nullptr, 0, &best_flop, bt, cap, &best_peak);
+    if (batch_mode) {   // the batch planner adds linear passes: leaf order, then greedy ones
+        for (int v = 0; v < 3; ++v) {
+            double f, pk;
+            auto p = v < 2 ? leaf_order_linear(net, v == 0, &f, bt, &pk)
+                           : greedy_linear(net, 0, nullptr, 0, &f, bt, cap, &pk);
+            if (better(f, pk)) {
+                best_flop = f;
+                best_peak = pk;
+                best = p;
+            }
+        }
+    }
     SplitMix rng{seed};
     for (int32_t t = 1; t < n_trials; ++t) {
-        double f;
+        double f, pk;
         double temp = 0.25 + 1.75 * rng.uniform();
-        auto p = greedy_once(net, &rng, temp, &f);
-        if (f < best_flop) {
+        std::vector<std::pair<int32_t, int32_t>> p;
+        if (batch_mode && (t & 1)) {
+            const int32_t start = (int32_t)(rng.next() % net.leaves.size());
+            p = greedy_linear(net, start, &rng, temp, &f, bt, cap, &pk);
+        } else {
+            p = greedy_once(net, &rng, temp, &f, bt, cap, &pk);
+        }
+        if (better(f, pk)) {
             best_flop = f;
+            best_peak = pk;
             best = p;
         }
     }

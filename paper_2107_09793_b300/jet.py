@@ -18,7 +18,7 @@ PREC = {"fp32": 0, "tf32": 1, "tf32x3": 2, "bf16x3": 3, "bf16x6": 4, "fp64": 5, 
 
 EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", "jet_tensor_update",
            "jet_tensors_upload", "jet_network_n_values", "jet_path_set", "jet_path_get",
-           "jet_path_greedy", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
+           "jet_path_greedy", "jet_path_greedy_batch", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
            "jet_contract_slices"]
@@ -82,6 +82,7 @@ def lib():
             "jet_path_set": (I32, [P, I32, P]),
             "jet_path_get": (I32, [P, P]),
             "jet_path_greedy": (I32, [P, ctypes.c_uint64, I32, P]),
+            "jet_path_greedy_batch": (I32, [P, I32, P, ctypes.c_int64, ctypes.c_uint64, I32, P]),
             "jet_slice": (I32, [P, I32, P]),
             "jet_slice_auto": (I32, [P, I64, I32, I32, P, P]),
             "jet_contract": (I32, [P, I32, P, P, P]),
@@ -193,6 +194,17 @@ class Network:
     def path_greedy(self, seed: int = 0, n_trials: int = 1) -> float:
         f = ctypes.c_double()
         _check(lib().jet_path_greedy(self._h, ctypes.c_uint64(seed), int(n_trials), ctypes.byref(f)))
+        return f.value
+
+    def path_greedy_batch(self, outputs, seed: int = 0, n_trials: int = 1, max_elems: int = 0) -> float:
+        """Greedy path for contracting the batch `outputs` together (every node
+        weighted by its number of distinct bra restrictions; pairwise and linear
+        passes; intermediates capped at max_elems weighted elements when > 0).
+        Returns the batch FLOP of the kept path."""
+        o = self._outputs(outputs)
+        f = ctypes.c_double()
+        _check(lib().jet_path_greedy_batch(self._h, o.shape[0], o.ctypes.data, ctypes.c_int64(int(max_elems)),
+                                           ctypes.c_uint64(seed), int(n_trials), ctypes.byref(f)))
         return f.value
 
     def slice(self, labels: Sequence[int]):

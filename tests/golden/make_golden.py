@@ -11,7 +11,14 @@ path receives it, then upcast to complex128.
        contraction (O2) for a fixed, rule-chosen set of 6 sliced labels: the wire
        label of qubits 12..17 (grid row 2) just after their 8th single-qubit gate.
 
-Usage: python tests/golden/make_golden.py grid30
+  gbs16.json  : 16-mode 4x4 bosonic lattice, Fock cutoff 4, 4 beamsplitter layers
+     (seed 5), the workload's 256 seeded photon patterns: the amplitudes of the 8
+     even-total patterns of the batch with the smallest totals (N <= 16), each
+     from the FP64 state vector of its own total-photon sector (beamsplitters
+     conserve the photon number; Section 4, Algorithm 1).  Odd totals are exactly
+     zero and need no stored value.
+
+Usage: python tests/golden/make_golden.py grid30 gbs16
 """
 import json
 import os
@@ -75,7 +82,29 @@ def grid30():
     print(json.dumps(rec["seconds"]))
 
 
+def gbs16():
+    w = configs.build("gbs16")
+    circ = rounded(w.circuit)
+    tot = w.outputs.sum(axis=1)
+    even = [int(i) for i in np.argsort(tot, kind="stable") if tot[i] % 2 == 0]
+    pick = [i for i in even if tot[i] <= 16][:8]
+    t0 = time.time()
+    amps = oracle.sector_amplitudes(circ, w.outputs[pick])
+    t_sec = time.time() - t0
+    rec = {
+        "workload": "gbs16", "source": "oracle O1, per total-photon sector (sector.c)",
+        "batch_index": pick,
+        "outputs": w.outputs[pick].tolist(),
+        "totals": [int(tot[i]) for i in pick],
+        "amplitudes": [[a.real, a.imag] for a in amps],
+        "seconds": {"sectors": round(t_sec, 1)},
+    }
+    with open(os.path.join(HERE, "gbs16.json"), "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec["seconds"]))
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["grid30"]
     for name in which:
-        {"grid30": grid30}[name]()
+        {"grid30": grid30, "gbs16": gbs16}[name]()

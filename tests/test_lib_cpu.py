@@ -191,3 +191,52 @@ def test_contract_grad_argument_errors_before_device_work():
     with pytest.raises(jet.JetError) as e:
         one.contract_grad([[0]], cot, [0])
     assert e.value.code == jet.JET_EINVAL
+
+
+def test_batch_greedy_flop_matches_reuse_dag_brute_force():
+    """The batch planner's FLOP = sum over nodes of (distinct bra restrictions
+    under the node) x (node FLOP), the same count the reuse DAG executes."""
+    from circuits import gbs_lattice_circuit, random_patterns
+    for circ, outs in [(gbs_lattice_circuit(2, 3, 4, 2, seed=17), random_patterns(6, 24, 5, 4)),
+                       (random_grid_circuit(2, 3, 5, seed=12), np.array(list(product([0, 1], repeat=6))[::5], np.int32))]:
+        tn = circuit_to_network(circ)
+        net = jet.from_network(tn)
+        f = net.path_greedy_batch(outs, seed=2, n_trials=8)
+        net.plan(outs)
+        inst, flop = _instances_brute(tn, net.path_get(), [], outs)
+        assert net.stats()["flop_executed"] == flop == f
+        assert net.stats()["n_instances"] == inst
+        # a single-amplitude batch is costed like the plain greedy's open-legs-fixed model
+        net1 = jet.from_network(tn)
+        f1 = net1.path_greedy_batch(outs[:1], seed=2, n_trials=1)
+        net1.plan(outs[:1])
+        assert net1.stats()["flop_executed"] == f1
+
+
+def test_batch_greedy_keeps_bras_late_on_the_bosonic_lattice():
+    """16 modes, d = 4, 256 patterns: with the weighted cap at 2^32 the planner
+    keeps the state-vector order (every tensor shared by the batch until the
+    last layer), far below the per-amplitude greedy path run for the batch."""
+    w = configs.build("gbs16")
+    tn = w.network
+    n = len(tn.labels)
+    net = jet.from_network(tn)
+    f = net.path_greedy_batch(w.outputs, seed=1, n_trials=8, max_elems=1 << 32)
+    assert net.path_get() == [(0, 1)] + [(k + 2, n + k) for k in range(n - 2)]
+    net.plan(w.outputs)
+    st = net.stats()
+    assert st["flop_executed"] == f and st["max_intermediate"] == 1 << 32
+    per_amp = jet.from_network(tn)
+    per_amp.path_greedy(seed=1, n_trials=8)
+    per_amp.plan(w.outputs)
+    assert per_amp.stats()["flop_executed"] > 100 * f
+
+
+def test_batch_greedy_argument_errors():
+    w, net = _net("param20")
+    with pytest.raises(jet.JetError) as e:
+        net.path_greedy_batch(np.full((2, 20), 2, np.int32))
+    assert e.value.code == jet.JET_EINVAL
+    with pytest.raises(jet.JetError) as e:
+        net.path_greedy_batch(np.zeros((0, 20), np.int32))
+    assert e.value.code == jet.JET_EINVAL

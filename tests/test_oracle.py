@@ -345,3 +345,51 @@ def test_bosonic_sector_closed_form_single_bs():
     idx = [0 * 4 + 1, 1 * 4 + 0]   # basis (n1=0,n2=1), (n1=1,n2=0)
     got = U[np.ix_(idx, idx)]
     assert np.max(abs(got - blk)) < 1e-14
+
+
+def test_sector_counting_table_closed_form():
+    """Compositions of N into n parts below d: sum_j (-1)^j C(n,j) C(N - d j + n - 1, n - 1)."""
+    for n, d in [(16, 4), (6, 4), (5, 3)]:
+        for N in range(0, n * (d - 1) + 1):
+            ref = sum((-1) ** j * math.comb(n, j) * math.comb(N - d * j + n - 1, n - 1)
+                      for j in range(0, n + 1) if N - d * j >= 0)
+            assert oracle.sector_dim(n, d, N) == ref
+
+
+def test_sector_state_vector_equals_dense_on_every_pattern():
+    """Per-sector state vector = dense state vector on all 4^6 patterns of a
+    2x3 lattice (beamsplitters with random theta, phi: a transposed block, a
+    wrong rank or a dropped sector member would show)."""
+    from itertools import product as iproduct
+    circ = gbs_lattice_circuit(2, 3, 4, 2, seed=17)
+    pats = np.array(list(iproduct(range(4), repeat=6)), np.int32)
+    got = oracle.sector_amplitudes(circ, pats)
+    ref = oracle.sv_amplitudes(circ, pats)
+    assert np.max(np.abs(got - ref)) < 1e-14
+    # and against the pairwise route on a few patterns of a 3x2 lattice (other digit strides)
+    circ2 = gbs_lattice_circuit(3, 2, 4, 1, seed=23)
+    tn2 = circuit_to_network(circ2)
+    for p in ([0, 2, 1, 1, 0, 0], [3, 1, 0, 2, 2, 0], [1, 1, 1, 1, 1, 1]):
+        assert abs(oracle.sector_amplitudes(circ2, [p])[0] - oracle.amplitude(tn2, p)) < 1e-14
+
+
+def test_sector_oracle_refuses_gates_that_mix_sectors():
+    circ = gbs_lattice_circuit(2, 2, 4, 1, seed=29)
+    mats = [g.matrix for g in circ.gates]
+    bad = np.array(mats[0], np.complex128)
+    bad[0, 5] = 1e-3   # (0,0) <- (1,1): photon number 2 -> 0
+    mats[0] = bad
+    with pytest.raises(ValueError):
+        oracle.sector_amplitudes(circ, [[0, 0, 0, 0]], gate_mats=mats)
+
+
+def test_sector_oracle_full_lattice_vacuum_and_parity():
+    """The 16-mode, d = 4 lattice at full size: the vacuum amplitude is the
+    product of the squeezers' vacuum coefficients (passive beamsplitters leave
+    N = 0 alone), odd totals vanish exactly."""
+    w = configs.build("gbs16")
+    circ = w.circuit
+    ref = np.prod([1 / math.sqrt(math.cosh(r)) for r in circ.squeezing])
+    a = oracle.sector_amplitudes(circ, [[0] * 16, [1] + [0] * 15, [1, 2] + [0] * 14])
+    assert abs(a[0] - ref) < 1e-14
+    assert a[1] == 0 and a[2] == 0
