@@ -1,0 +1,245 @@
+// Small-operand application (Section 2.3, one step of Eq. sequence, in the
+// shape a circuit's gate takes when it is absorbed into a large state-like
+// tensor):
+//     C[r, f] = sum_q B[f, q] * A[r, q]
+// A is the large operand, B a small one (at most JET_APPLY_MAXK summed and
+// JET_APPLY_MAXF free entries, JET_APPLY_MAXB in all: a gate, a bra
+// projection, an outer factor);
+// r runs over A's free labels ("fibers"), q over the summed labels and f over
+// B's free labels.  Each thread takes two fibers: it reads their nk values of
+// A once into registers, multiplies them by B (staged in shared memory, read
+// as warp-wide broadcasts) and writes the nf results, so every element of A is
+// loaded by one thread only (the generic strided direct kernel loads it once
+// per output it feeds) and A and C cross HBM once.  Fibers are numbered along
+// A's smallest free stride first, so a warp's loads of one summed entry are
+// coalesced whenever the summed labels are not the fastest ones.  The
+// contraction is HBM-bound (8 * nk * nf FLOP per 8 * (nk + nf) bytes).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernel_args.h"
+#include "kernels.cuh"
+
+namespace jet {
+
+template <typename V>
+__device__ __forceinline__ void cfma(V &acc, V b, V x)
+{
+    acc.x = fma(b.x, x.x, acc.x);
+    acc.x = fma(-b.y, x.y, acc.x);
+    acc.y = fma(b.x, x.y, acc.y);
+    acc.y = fma(b.y, x.x, acc.y);
+}
+
+// Packed FP32 pair FMA of sm_100+ (fma.rn.f32x2): d = a * b + c lane-wise,
+// each lane rounded once like a scalar fma.  One instruction does the two FMAs
+// a complex multiply-add needs per operand entry (see cmac2 below), halving
+// the issue slots of the FP32 contraction.
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+
+__device__ __forceinline__ float2 unpack2(unsigned long long v)
+{
+    return make_float2(__uint_as_float((unsigned)(v & 0xffffffffu)), __uint_as_float((unsigned)(v >> 32)));
+}
+
+// Complex multiply-add split over two packed accumulators: with b = br + i bi,
+//   p += (br, br) * (xr, xi),   m += (bi, bi) * (xr, xi),
+// and the product sum is (p.x - m.y) + i (p.y + m.x) (cfinish).  sb holds the
+// pairs (br, br, bi, bi) of one entry of B.
+__device__ __forceinline__ void cmac2(unsigned long long &p, unsigned long long &m, const ulonglong2 &sb,
+                                      unsigned long long x)
+{
+    p = ffma2(sb.x, x, p);
+    m = ffma2(sb.y, x, m);
+}
+
+__device__ __forceinline__ float2 cfinish(unsigned long long p, unsigned long long m)
+{
+    const float2 a = unpack2(p), b = unpack2(m);
+    return make_float2(a.x - b.y, a.y + b.x);
+}
+
+template <bool POW2>
+__device__ __forceinline__ void fiber_offsets(int64_t r, const ApplyArgs &a, int64_t &oa, int64_t &oc)
+{
+    oa = 0;
+    oc = 0;
+    for (int j = 0; j < a.rank; ++j) {
+        const int64_t d = a.dim[j];
+        int64_t q, dg;
+        if (POW2) {
+            const int sh = __ffsll((unsigned long long)d) - 1;
+            q = r >> sh;
+            dg = r & (d - 1);
+        } else {
+            q = r / d;
+            dg = r - q * d;
+        }
+        oa += dg * a.sA[j];
+        oc += dg * a.sC[j];
+        r = q;
+    }
+}
+
+// complex64: B staged as packed pairs (br, br, bi, bi); two fibers per thread,
+// every B entry read from shared memory once feeds the packed FMAs of both.
+template <int NK, bool POW2>
+__global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ ApplyArgs a)
+{
+    __shared__ ulonglong2 sB[JET_APPLY_MAXB];
+    constexpr int FIB = 2;
+    const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
+    const int nf = a.nf;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB;
+    for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
+        const unsigned long long *__restrict__ A = (const unsigned long long *)pA[inst];
+        const float2 *__restrict__ B = (const float2 *)pB[inst];
+        unsigned long long *__restrict__ C = (unsigned long long *)pC[inst];
+        __syncthreads();   // the previous instance's readers of sB are done
+        for (int i = threadIdx.x; i < nf * NK; i += blockDim.x) {
+            const int f = i / NK, q = i - f * NK;
+            const float2 b = q < a.nk ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);   // padding is zero
+            sB[i] = make_ulonglong2(pack2(b.x, b.x), pack2(b.y, b.y));
+        }
+        __syncthreads();
+        for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x * FIB + threadIdx.x; r0 < a.n_fib; r0 += step) {
+            int64_t oa[FIB], oc[FIB];
+            bool ok[FIB];
+            unsigned long long x[FIB][NK];
+#pragma unroll
+            for (int u = 0; u < FIB; ++u) {
+                const int64_t r = r0 + (int64_t)u * blockDim.x;
+                ok[u] = r < a.n_fib;
+                fiber_offsets<POW2>(ok[u] ? r : 0, a, oa[u], oc[u]);
+#pragma unroll
+                for (int q = 0; q < NK; ++q) x[u][q] = ok[u] ? __ldg(A + oa[u] + a.kA[q]) : 0ull;
+            }
+            for (int f = 0; f < nf; ++f) {
+                unsigned long long p[FIB], m[FIB];
+#pragma unroll
+                for (int u = 0; u < FIB; ++u) p[u] = m[u] = 0ull;
+#pragma unroll
+                for (int q = 0; q < NK; ++q) {
+                    const ulonglong2 b = sB[f * NK + q];
+#pragma unroll
+                    for (int u = 0; u < FIB; ++u) cmac2(p[u], m[u], b, x[u][q]);
+                }
+                const int64_t cf = a.cF[f];
+#pragma unroll
+                for (int u = 0; u < FIB; ++u)
+                    if (ok[u]) {
+                        const float2 c = cfinish(p[u], m[u]);
+                        __stcs(C + oc[u] + cf, pack2(c.x, c.y));
+                    }
+            }
+        }
+    }
+}
+
+// NK: summed entries (compile time, so the fiber stays in registers); FIB:
+// fibers per thread (complex128: 1).
+template <typename V, int NK, int FIB, bool POW2>
+__global__ void __launch_bounds__(256) apply_kernel(const __grid_constant__ ApplyArgs a)
+{
+    __shared__ V sB[JET_APPLY_MAXB];
+    const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
+    const int nf = a.nf;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB;
+    for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
+        const V *__restrict__ A = (const V *)pA[inst];
+        const V *__restrict__ B = (const V *)pB[inst];
+        V *__restrict__ C = (V *)pC[inst];
+        __syncthreads();   // the previous instance's readers of sB are done
+        for (int i = threadIdx.x; i < nf * NK; i += blockDim.x) {
+            const int f = i / NK, q = i - f * NK;
+            sB[i] = q < a.nk ? B[a.bF[f] + a.bK[q]] : V{0, 0};   // padded entries are zero
+        }
+        __syncthreads();
+        for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x * FIB + threadIdx.x; r0 < a.n_fib; r0 += step) {
+            int64_t oa[FIB], oc[FIB];
+            bool ok[FIB];
+            V x[FIB][NK];
+#pragma unroll
+            for (int u = 0; u < FIB; ++u) {
+                const int64_t r = r0 + (int64_t)u * blockDim.x;
+                ok[u] = r < a.n_fib;
+                fiber_offsets<POW2>(ok[u] ? r : 0, a, oa[u], oc[u]);
+#pragma unroll
+                for (int q = 0; q < NK; ++q) x[u][q] = ok[u] ? __ldg(A + oa[u] + a.kA[q]) : V{0, 0};
+            }
+            for (int f = 0; f < nf; ++f) {
+                V acc[FIB];
+#pragma unroll
+                for (int u = 0; u < FIB; ++u) acc[u] = V{0, 0};
+#pragma unroll
+                for (int q = 0; q < NK; ++q) {
+                    const V b = sB[f * NK + q];
+#pragma unroll
+                    for (int u = 0; u < FIB; ++u) cfma(acc[u], b, x[u][q]);
+                }
+                const int64_t cf = a.cF[f];
+#pragma unroll
+                for (int u = 0; u < FIB; ++u)
+                    if (ok[u]) __stcs(C + oc[u] + cf, acc[u]);
+            }
+        }
+    }
+}
+
+template <typename V, int FIB>
+static void launch_nk(const ApplyArgs &a, dim3 grid, bool pow2, cudaStream_t s)
+{
+#define JET_APPLY(NK)                                                                       \
+    do {                                                                                    \
+        if (pow2) apply_kernel<V, NK, FIB, true><<<grid, 256, 0, s>>>(a);                    \
+        else apply_kernel<V, NK, FIB, false><<<grid, 256, 0, s>>>(a);                        \
+    } while (0)
+    switch (a.nk_tmpl) {
+    case 1: JET_APPLY(1); break;
+    case 2: JET_APPLY(2); break;
+    case 4: JET_APPLY(4); break;
+    case 8: JET_APPLY(8); break;
+    default: JET_APPLY(16); break;
+    }
+#undef JET_APPLY
+}
+
+cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    const bool tmpl_ok = a.nk_tmpl == 1 || a.nk_tmpl == 2 || a.nk_tmpl == 4 || a.nk_tmpl == 8 || a.nk_tmpl == 16;
+    if (!tmpl_ok || a.nk < 1 || a.nk > a.nk_tmpl || a.nf < 1 || a.nf > JET_APPLY_MAXF ||
+        a.nf * a.nk_tmpl > JET_APPLY_MAXB || a.rank > JET_MAXR)
+        return cudaErrorInvalidValue;
+    dim3 grid(c.gx, c.gy, 1);
+    const bool pow2 = c.variant & 4;
+    if (c.variant & 1) {
+        launch_nk<double2, 1>(a, grid, pow2, s);
+        return cudaGetLastError();
+    }
+#define JET_C64(NK)                                                                        \
+    do {                                                                                   \
+        if (pow2) apply_kernel_c64<NK, true><<<grid, 256, 0, s>>>(a);                       \
+        else apply_kernel_c64<NK, false><<<grid, 256, 0, s>>>(a);                           \
+    } while (0)
+    switch (a.nk_tmpl) {
+    case 1: JET_C64(1); break;
+    case 2: JET_C64(2); break;
+    case 4: JET_C64(4); break;
+    case 8: JET_C64(8); break;
+    default: JET_C64(16); break;
+    }
+#undef JET_C64
+    return cudaGetLastError();
+}
+
+}  // namespace jet

@@ -196,6 +196,12 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
         e = launch_direct(a, c, s);
         break;
     }
+    case OpKind::Apply: {
+        ApplyArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_apply(a, c, s);
+        break;
+    }
     case OpKind::SplitKReduce: {
         SplitKReduceArgs a;
         std::memcpy(&a, p, sizeof a);

@@ -351,7 +351,22 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const View &VBig = N.a_big ? VA : VB;
         const View &VSmall = N.a_big ? VB : VA;
         const std::vector<int64_t> &fbig = N.a_big ? N.fa : N.fb, &fsmall = N.a_big ? N.fb : N.fa;
-        if (!N.use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size) {
+        // in-place pairing: the small operand's j-th free label (in its own
+        // order) takes the place of its j-th summed label, when the counts and
+        // dims agree (a gate [outs..., ins...] then maps each output wire onto
+        // its input wire and the large operand's layout is kept)
+        std::vector<int64_t> ks_small, fs_small_order;
+        for (int64_t l : VSmall.labels) (find_pos(N.K, l) >= 0 ? ks_small : fs_small_order).push_back(l);
+        bool pairable = !N.use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size && !ks_small.empty() &&
+                        ks_small.size() == fs_small_order.size();
+        for (size_t j = 0; pairable && j < ks_small.size(); ++j)
+            pairable = net.labels.at(ks_small[j]).dim == net.labels.at(fs_small_order[j]).dim;
+        if (pairable) {
+            for (int64_t l : VBig.labels) {
+                const int p = find_pos(ks_small, l);
+                out.push_back(p >= 0 ? fs_small_order[p] : l);
+            }
+        } else if (!N.use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size) {
             // keep the big operand's order; the small operand's free labels take
             // the place of the first summed label (gate application in place)
             int ins = -1;
@@ -651,6 +666,101 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 rop.grid_x = (int32_t)std::min<int64_t>((tot + 255) / 256, 65535);
                 P.ops.push_back(rop);
             }
+    };
+
+    // Small-operand application route: the small operand holds at most
+    // JET_APPLY_MAXK summed and JET_APPLY_MAXF free entries (at most
+    // JET_APPLY_MAXB in all) and the large one has enough fibers to fill the GPU.
+    auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
+        const View &VS = N.a_big ? VB : VA, &VL = N.a_big ? VA : VB;
+        const std::vector<int64_t> &fs = N.a_big ? N.fb : N.fa, &fl = N.a_big ? N.fa : N.fb;
+        const int64_t nk = dimprod(N.K), nf = dimprod(fs), nfib = dimprod(fl);
+        int64_t nk2 = 1;   // the kernel's compile-time summed extent (power of two >= nk)
+        while (nk2 < nk) nk2 *= 2;
+        return nk >= 1 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_MAXF && nk2 * nf <= JET_APPLY_MAXB &&
+               nfib >= (1 << 15) &&
+               (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
+    };
+    auto emit_apply = [&](int32_t v, const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K,
+                          bool a_big, int64_t n_inst, const std::vector<std::pair<int32_t, int64_t>> &pa,
+                          const std::vector<std::pair<int32_t, int64_t>> &pb,
+                          const std::vector<std::pair<int32_t, int64_t>> &pc, double flop, double bytes) {
+        const View &VL = a_big ? VA : VB, &VS = a_big ? VB : VA;
+        const NodeInfo &N = node[v];
+        const std::vector<int64_t> &fs = a_big ? N.fb : N.fa, &fl = a_big ? N.fa : N.fb;
+        auto stride = [&](const View &V, int64_t l) {
+            const int p = find_pos(V.labels, l);
+            return p < 0 ? (int64_t)0 : V.strides[p];
+        };
+        ApplyArgs d;
+        std::memset(&d, 0, sizeof d);
+        const int64_t nk = dimprod(K), nf = std::max<int64_t>(1, dimprod(fs));
+        d.nk = (int32_t)nk;
+        d.nf = (int32_t)nf;
+        d.nk_tmpl = 1;
+        while (d.nk_tmpl < d.nk) d.nk_tmpl *= 2;
+        // summed entries: mixed radix over K, the label of smallest stride in A
+        // fastest; B's free entries: the label of smallest stride in C fastest
+        std::vector<int64_t> Ks = K, Fs = fs;
+        std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) { return stride(VL, x) > stride(VL, y); });
+        std::stable_sort(Fs.begin(), Fs.end(), [&](int64_t x, int64_t y) { return stride(Cv, x) > stride(Cv, y); });
+        for (int64_t q = 0; q < nk; ++q) {
+            int64_t r = q;
+            for (int j = (int)Ks.size() - 1; j >= 0; --j) {
+                const int64_t dm = net.labels.at(Ks[j]).dim, dg = r % dm;
+                r /= dm;
+                d.kA[q] += dg * stride(VL, Ks[j]);
+                d.bK[q] += dg * stride(VS, Ks[j]);
+            }
+        }
+        for (int64_t f = 0; f < nf; ++f) {
+            int64_t r = f;
+            for (int j = (int)Fs.size() - 1; j >= 0; --j) {
+                const int64_t dm = net.labels.at(Fs[j]).dim, dg = r % dm;
+                r /= dm;
+                d.cF[f] += dg * stride(Cv, Fs[j]);
+                d.bF[f] += dg * stride(VS, Fs[j]);
+            }
+        }
+        // fibers: A's free labels, smallest A stride decoded first
+        std::vector<int64_t> rl = fl;
+        std::stable_sort(rl.begin(), rl.end(), [&](int64_t x, int64_t y) { return stride(VL, x) < stride(VL, y); });
+        d.rank = (int32_t)rl.size();
+        d.n_fib = 1;
+        bool pow2 = true;
+        for (int j = 0; j < d.rank; ++j) {
+            d.dim[j] = net.labels.at(rl[j]).dim;
+            d.sA[j] = stride(VL, rl[j]);
+            d.sC[j] = stride(Cv, rl[j]);
+            d.n_fib *= d.dim[j];
+            pow2 = pow2 && (d.dim[j] & (d.dim[j] - 1)) == 0;
+        }
+        d.n_inst = (int32_t)n_inst;
+        size_t off_pl = blob.put_ptrs(a_big ? pa : pb), off_ps = blob.put_ptrs(a_big ? pb : pa);
+        size_t off_pc = blob.put_ptrs(pc);
+        size_t so = blob.reserve(sizeof d);
+        std::memcpy(blob.bytes.data() + so, &d, sizeof d);
+        blob.patch_field(so, offsetof(ApplyArgs, ptrA), BASE_BLOB, (int64_t)off_pl);
+        blob.patch_field(so, offsetof(ApplyArgs, ptrB), BASE_BLOB, (int64_t)off_ps);
+        blob.patch_field(so, offsetof(ApplyArgs, ptrC), BASE_BLOB, (int64_t)off_pc);
+        Op op;
+        op.kind = OpKind::Apply;
+        op.node = v;
+        op.n_inst = n_inst;
+        op.args_off = so;
+        op.args_bytes = sizeof d;
+        op.flop = flop;
+        op.bytes = bytes;
+        op.variant = (fp64 ? 1 : 0) | (pow2 ? 4 : 0);
+        // 256-thread blocks; complex64 threads take two fibers, complex128 one
+        op.block = 256;
+        const int64_t gy = std::min<int64_t>(n_inst, 65535);
+        const int64_t per_block = fp64 ? 256 : 512;
+        const int64_t blocks = (d.n_fib + per_block - 1) / per_block;
+        const int64_t per_sm = 8;
+        op.grid_y = (int32_t)gy;
+        op.grid_x = (int32_t)std::max<int64_t>(1, std::min<int64_t>(blocks, std::max<int64_t>(1, 148 * per_sm / gy)));
+        P.ops.push_back(op);
     };
 
     // ---- pass 2, launch order: arena offsets, pointer tables, launches
@@ -1032,6 +1142,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             op.grid_z = (int32_t)std::min<int64_t>(N.n_inst, 65535);
             P.ops.push_back(op);
             }
+        }
+        // ------------------------------------------------ small operand applied to a large one
+        else if (apply_ok(N, VA, VB)) {
+            ++P.n_direct;
+            emit_apply(v, VA, VB, N.view, K, a_big, N.n_inst, pa, pb, pc, flop, bytes);
         }
         // ------------------------------------------------ direct contraction
         else {

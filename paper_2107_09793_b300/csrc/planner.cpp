@@ -389,8 +389,10 @@ static std::vector<std::pair<int32_t, int32_t>> greedy_linear(const Network &net
 
 // Linear path in leaf order.  strict: absorb leaves 1, 2, ... in turn (for a
 // circuit whose leaves are listed in time order with the initial states first,
-// the state-vector order); else: absorb the lowest-index leaf that shares a
-// label with the growing tensor (initial states join when first touched).
+// the state-vector order); else: absorb the lowest-index leaf x that shares a
+// label with the growing tensor, each unused lower-index leaf that shares a
+// label with x (and none with the tensor) joining just before x as an outer
+// factor (initial states join when their qudit is first touched).
 // Weighted FLOP and peak as in the greedy passes.
 static std::vector<std::pair<int32_t, int32_t>> leaf_order_linear(const Network &net, bool strict, double *flop_out,
                                                                   BatchInstances *bt, double *peak_out)
@@ -414,17 +416,30 @@ static std::vector<std::pair<int32_t, int32_t>> leaf_order_linear(const Network 
     int32_t tid = 0;
     std::vector<std::pair<int32_t, int32_t>> path;
     double total = 0, peak = 0;
+    auto shares = [&](const std::vector<int64_t> &L, int32_t i) {
+        for (int64_t l : net.leaves[i].labels)
+            if (std::find(L.begin(), L.end(), l) != L.end()) return true;
+        return false;
+    };
+    std::vector<int32_t> pending;   // outer factors queued before the next connected leaf
     for (int32_t k = 0; k + 1 < n; ++k) {
         int32_t x = -1;
-        if (!strict)
-            for (int32_t i = 1; i < n && x < 0; ++i) {
-                if (used[i]) continue;
-                for (int64_t l : net.leaves[i].labels)
-                    if (std::find(T.begin(), T.end(), l) != T.end()) {
-                        x = i;
-                        break;
-                    }
+        if (!pending.empty()) {
+            x = pending.front();
+            pending.erase(pending.begin());
+        } else if (!strict) {
+            for (int32_t i = 1; i < n && x < 0; ++i)
+                if (!used[i] && shares(T, i)) x = i;
+            if (x >= 0) {
+                for (int32_t y = 1; y < x; ++y)
+                    if (!used[y] && !shares(T, y) && shares(net.leaves[x].labels, y)) pending.push_back(y);
+                if (!pending.empty()) {
+                    pending.push_back(x);
+                    x = pending.front();
+                    pending.erase(pending.begin());
+                }
             }
+        }
         if (x < 0)
             for (int32_t i = 1; i < n; ++i)
                 if (!used[i]) {

@@ -215,17 +215,21 @@ def test_batch_greedy_flop_matches_reuse_dag_brute_force():
 
 def test_batch_greedy_keeps_bras_late_on_the_bosonic_lattice():
     """16 modes, d = 4, 256 patterns: with the weighted cap at 2^32 the planner
-    keeps the state-vector order (every tensor shared by the batch until the
-    last layer), far below the per-amplitude greedy path run for the batch."""
+    keeps a state-vector-like order (every tensor shared by the batch until the
+    last layer), at or below the strict state-vector order and far below the
+    per-amplitude greedy path run for the batch."""
     w = configs.build("gbs16")
     tn = w.network
     n = len(tn.labels)
     net = jet.from_network(tn)
     f = net.path_greedy_batch(w.outputs, seed=1, n_trials=8, max_elems=1 << 32)
-    assert net.path_get() == [(0, 1)] + [(k + 2, n + k) for k in range(n - 2)]
     net.plan(w.outputs)
     st = net.stats()
     assert st["flop_executed"] == f and st["max_intermediate"] == 1 << 32
+    sv = jet.from_network(tn)
+    sv.path_set([(0, 1)] + [(k + 2, n + k) for k in range(n - 2)])
+    sv.plan(w.outputs)
+    assert f <= sv.stats()["flop_executed"]
     per_amp = jet.from_network(tn)
     per_amp.path_greedy(seed=1, n_trials=8)
     per_amp.plan(w.outputs)
