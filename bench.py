@@ -167,6 +167,126 @@ def oracle_slice_sample(w, sliced, n_slices, outputs):
                       f"{dt:.1f} s"}, part
 
 
+def _timed(fn, stream, ev0, ev1, steps):
+    out = []
+    for _ in range(steps):
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        out.append(ev0.elapsed_time(ev1))
+    return out
+
+
+def run_other_workloads(dev, peaks, peak_src):
+    """The other workloads of the method at full size, one short timing each:
+    the 16-mode d=4 bosonic lattice batch (256 patterns), the 20-qubit
+    parameterised circuit's 64-amplitude forward + adjoint, and a measured
+    fraction of the 53-qubit grid's slices (its full slice set is far too long
+    to run)."""
+    import torch
+    from circuits import configs
+    from paper_2107_09793_b300 import jet
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {}
+
+    # bosonic lattice: batch planner keeps the bras late; inputs (32 GiB state) exceed L2
+    w = configs.build("gbs16")
+    net = jet.from_network(w.network, precision="fp32", device=dev)
+    t0 = time.perf_counter()
+    flop = net.path_greedy_batch(w.outputs, seed=1, n_trials=8, max_elems=1 << 32)
+    t_plan = time.perf_counter() - t0
+    amps = torch.zeros(len(w.outputs), dtype=torch.complex128, device="cuda")
+    run = lambda: net.contract_async(w.outputs, amps.data_ptr(), sh)
+    run()
+    torch.cuda.synchronize()
+    ms = _timed(run, stream, ev0, ev1, 3)
+    a = amps.cpu().numpy()
+    st = net.stats()
+    net.close()
+    tot = w.outputs.sum(axis=1)
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "gbs16.json")))
+    ref = np.array([complex(x, y) for x, y in g["amplitudes"]])
+    err = float(np.linalg.norm(a[g["batch_index"]] - ref) / np.linalg.norm(ref))
+    prof = jet.from_network(w.network, precision="fp32", profile=2, device=dev)
+    prof.path_greedy_batch(w.outputs, seed=1, n_trials=8, max_elems=1 << 32)
+    prof.contract_async(w.outputs, amps.data_ptr(), sh)
+    torch.cuda.synchronize()
+    recs = [r for r in prof.profile() if r["ms"] > 0]
+    prof.close()
+    top = max(recs, key=lambda r: r["ms"])
+    apply_ms = sum(r["ms"] for r in recs if r["kind"] == "apply")
+    apply_b = sum(r["bytes"] for r in recs if r["kind"] == "apply")
+    res["gbs16"] = {
+        "workload": "16-mode 4x4 lattice, Fock cutoff 4, 16 squeezed inputs, 96 beamsplitters (4 layers), "
+                    "256 seeded photon patterns in one batch",
+        "amplitudes_per_s": len(w.outputs) / (statistics.mean(ms) * 1e-3), "ms_per_batch": statistics.mean(ms),
+        "flop_per_batch": st["flop_executed"], "workspace_gb": st["workspace_bytes"] / 1e9,
+        "path": "batch planner (seed 1, 8 trials, weighted cap 2^32)", "planner_s": t_plan,
+        "precision": "fp32", "rel_err_vs_oracle_8_patterns": err,
+        "odd_total_exact_zeros": int(np.sum(a[tot % 2 == 1] == 0)), "odd_totals": int(np.sum(tot % 2 == 1)),
+        "apply_share": apply_ms / sum(r["ms"] for r in recs),
+        "roofline": {"bound": "hbm", "kernel": "apply_kernel_c64", "achieved": top["bytes"] / (top["ms"] * 1e-3) / 1e9,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": top["bytes"] / (top["ms"] * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                     "per_launch_ms": top["ms"], "bytes_per_launch": top["bytes"],
+                     "all_apply_gb_s": apply_b / (apply_ms * 1e-3) / 1e9, "peak_source": f"hbm_gbs of {peak_src}"},
+    }
+
+    # parameterised circuit: 64 amplitudes, loss sum |amp|^2, adjoint environments of every gate
+    w = configs.build("param20")
+    net = jet.from_network(w.network, precision="fp32", device=dev)
+    net.path_greedy_batch(w.outputs, seed=1, n_trials=16)
+    ids = list(w.network.gate_tensor)
+    a = net.contract(w.outputs)
+    fw, bw = [], []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a = net.contract(w.outputs)
+        fw.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        net.contract_grad(w.outputs, np.conj(a), ids)
+        bw.append(time.perf_counter() - t0)
+    st = net.stats()
+    net.close()
+    res["param20"] = {"workload": "20-qubit 4x5 parameterised circuit, 12 cycles, 64 amplitudes, gradient of "
+                                  "sum |amp|^2 w.r.t. every gate tensor",
+                      "forward_ms": 1e3 * statistics.median(fw), "forward_plus_adjoint_ms": 1e3 * statistics.median(bw),
+                      "n_gate_tensors": len(ids), "flop_forward": st["flop_executed"], "precision": "fp32",
+                      "timing": "host wall clock through the C ABI (host buffers), median of 3"}
+
+    # 53-qubit grid: library greedy + slicing to 2^28, a measured fraction of the slices
+    w = configs.build("grid53")
+    net = jet.from_network(w.network, precision="fp16x3", device=dev)
+    net.path_greedy(seed=1, n_trials=512)
+    sl = net.slice_auto(1 << 28, min_n=0, max_n=60)
+    st = net.stats()
+    ids = [0, 1]
+    per = {}
+    for prec in ("fp16x3", "fp32"):
+        nm = jet.from_network(w.network, precision=prec, device=dev)
+        nm.path_set(net.path_get())
+        nm.slice(sl)
+        nm.contract_slices(w.outputs, ids)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nm.contract_slices(w.outputs, ids)
+        per[prec] = 1e3 * (time.perf_counter() - t0) / len(ids)
+        nm.close()
+    net.close()
+    res["grid53"] = {"workload": "53-qubit 9x6 grid minus one corner, 12 cycles, one amplitude",
+                     "path": "library greedy, 512 trials, seed 1", "sliced_labels": len(sl), "n_slices": st["n_slices"],
+                     "max_intermediate": st["max_intermediate"], "flop_per_slice": st["flop_sliced"] / st["n_slices"],
+                     "ms_per_slice": per, "measured_slices": len(ids),
+                     "measured_fraction": len(ids) / st["n_slices"],
+                     "implied_amplitude_s": {k: v * 1e-3 * st["n_slices"] for k, v in per.items()},
+                     "timing": "host wall clock of jet_contract_slices over 2 slices (second call), per slice"}
+    return res
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -361,6 +481,9 @@ def run_impl(args):
     cpu = None
     if world == 1 and not args.skip_cpu:
         cpu, _ = oracle_slice_sample(w, sliced, st["n_slices"], outs)
+    others = None
+    if world == 1 and not args.skip_others:
+        others = run_other_workloads(dev, peaks, peak_src)
     kinds = {}
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
@@ -376,6 +499,7 @@ def run_impl(args):
         "amplitude": [amp.real, amp.imag], "rel_err_vs_oracle": err,
         "fp32_simt": modes.get("fp32"), "modes": modes, "roofline": roof, "breakdown": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(st["n_launches"]) * args.steps,
+        "other_workloads": others,
         "wall_s_timed": t_wall1 - t_wall0,
     }
     print(json.dumps(line), flush=True)
@@ -434,6 +558,8 @@ def main():
     ap.add_argument("--precision", default="fp16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
+    ap.add_argument("--skip-others", action="store_true", help="skip the other workloads (bosonic lattice, "
+                    "parameterised circuit gradient, 53-qubit slices)")
     ap.add_argument("--case", default="workload", choices=["workload", "gemm"],
                     help="gemm: a single complex GEMM node sized for ncu captures")
     args = ap.parse_args()

@@ -1,0 +1,67 @@
+"""Slices of one contraction spread over several processes (one GPU each).
+
+Section 2.4 (Eq. sliced_sum): the slices of an amplitude are independent
+contractions whose results are summed, so a multi-GPU run needs no exchange
+while contracting.  Each rank takes one contiguous range of slice ids (mixed
+radix, first sliced label most significant, so a range shares its high-order
+digits and with them the shared subtrees of Section 3.2), contracts it with
+jet_contract_slices, and the per-slice partials (n_amps x n_ids complex128,
+a few KB) are gathered to every rank and summed in increasing slice id: the
+same FP64 order as a single-GPU jet_contract, so the result does not depend
+on the number of ranks.
+"""
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+
+def slice_ranges(n_slices: int, world: int) -> List[Tuple[int, int]]:
+    """Contiguous [start, stop) ranges of slice ids, one per rank, sizes differing by at most one."""
+    if n_slices < 0 or world < 1:
+        raise ValueError("need n_slices >= 0 and world >= 1")
+    base, extra = divmod(n_slices, world)
+    out, start = [], 0
+    for r in range(world):
+        stop = start + base + (1 if r < extra else 0)
+        out.append((start, stop))
+        start = stop
+    return out
+
+
+def ordered_sum(partials_by_rank: Sequence[np.ndarray], ranges: Sequence[Tuple[int, int]]) -> np.ndarray:
+    """amp_b = sum over slice ids in increasing order of the gathered partials
+    (rank r's array is n_amps x (stop_r - start_r))."""
+    n_amps = next((p.shape[0] for p in partials_by_rank if p.size), 0)
+    acc = np.zeros(n_amps, dtype=np.complex128)
+    for (start, stop), p in sorted(zip(ranges, partials_by_rank), key=lambda x: x[0][0]):
+        if stop <= start:
+            continue
+        assert p.shape[1] == stop - start
+        for j in range(p.shape[1]):
+            acc += p[:, j]
+    return acc
+
+
+def gather_partials(local: np.ndarray, world: int, group=None) -> List[np.ndarray]:
+    """Every rank's partials on every rank (torch.distributed, any backend)."""
+    if world == 1:
+        return [local]
+    import torch
+    import torch.distributed as dist
+    out: List = [None] * world
+    dist.all_gather_object(out, np.ascontiguousarray(local), group=group)
+    return [np.asarray(x) for x in out]
+
+
+def contract_sharded(net, outputs, rank: int, world: int, group=None, stream: int = 0) -> np.ndarray:
+    """This rank's slice range through jet_contract_slices, then the ordered
+    FP64 sum over all ranks' partials.  Every rank returns the amplitudes."""
+    n_slices = net.stats()["n_slices"]
+    ranges = slice_ranges(n_slices, world)
+    start, stop = ranges[rank]
+    o = net._outputs(outputs)
+    if stop > start:
+        local = net.contract_slices(o, list(range(start, stop)), stream=stream)
+    else:
+        local = np.zeros((o.shape[0], 0), dtype=np.complex128)
+    return ordered_sum(gather_partials(local, world, group), ranges)
