@@ -104,11 +104,13 @@ typedef struct {
     int32_t  n_direct_nodes;      /* tree nodes routed to the direct-contraction kernel   */
 } jet_stats_t;
 
-/* One launch of the current plan, for jet_profile. */
+/* One launch of the plan run last, for jet_profile. */
 typedef struct {
     int32_t kind;             /* 0 direct, 1 permute, 2 SIMT GEMM, 3 tensor-core GEMM,
                                  4 slice reduction, 5 split-K reduction, 6 operand split,
-                                 7 batched small contractions of one tree level          */
+                                 7 batched small contractions of one tree level,
+                                 8 adjoint accumulation, 9 memset, 10 small operand
+                                 applied to a large one                                  */
     int32_t node;             /* tree node (SSA id) the launch belongs to               */
     int64_t n_inst;           /* instances the launch processes                         */
     double  flop;             /* algorithmic real FLOP of the launch                    */
@@ -253,17 +255,21 @@ int jet_set_workspace(jet_network *net, void *dptr, size_t bytes);
  * then swept backwards: for C = sum_K A B, env(A) = env(C) contracted with B
  * over B's free labels.  Environments accumulate over slices in FP64.
  * env_out[i] points to prod(dims) complex64 values of HOST memory for tensor
- * tensor_ids[i]; amps_out (may be NULL) receives the amplitudes.  Runs the
- * launches eagerly on cuda_stream and synchronises it.
+ * tensor_ids[i]; amps_out (may be NULL) receives the amplitudes.  Synchronises
+ * cuda_stream before returning.  An unsliced network keeps its adjoint plan
+ * (replayed as a CUDA graph): a later call with the same outputs and tensor ids
+ * only rewrites the cotangent seed; a sliced network plans and runs its slices
+ * one after the other.
  * Errors as jet_contract, plus JET_EINVAL (bad or repeated tensor id,
  * a network of one tensor). */
 int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs,
                       const jet_c128 *cot, int32_t n_req, const int32_t *tensor_ids,
                       jet_c64 *const *env_out, jet_c128 *amps_out, void *cuda_stream);
 
-/* The launches of the current plan in issue order, with the device time of
- * each timed launch in the last contraction (jet_options.profile).  Waits for
- * that contraction to finish.  Writes min(cap, count) records and the count.
+/* The launches of the plan run last (a contraction, a slice subset or an
+ * unsliced adjoint; otherwise the current forward plan) in issue order, with
+ * the device time of each timed launch in that run (jet_options.profile).
+ * Waits for that run to finish.  Writes min(cap, count) records and the count.
  * Errors: JET_ESTATE (no plan yet). */
 int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t *n_out);
 

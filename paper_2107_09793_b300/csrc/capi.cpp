@@ -43,9 +43,33 @@ static int guarded(F &&f)
 static void invalidate_plan(Network &net)
 {
     if (net.plan) {
+        if (net.last_run == net.plan.get()) net.last_run = nullptr;
         release_plan_device(*net.plan);
         net.plan.reset();
     }
+}
+
+// New cotangents into a cached adjoint plan: seed(root instance i) = sum of
+// cot_b over the (amplitude b, slice) assignments mapped to i.
+static void write_seed(Plan &P, const std::vector<double> &cot, bool fp64)
+{
+    std::vector<double> seed(2 * (size_t)P.seed_n_inst, 0.0);
+    for (size_t x = 0; x < P.seed_inst.size(); ++x) {
+        const int32_t i = P.seed_inst[x];
+        const size_t b = x / (size_t)P.seed_n_sl;
+        seed[2 * i] += cot[2 * b];
+        seed[2 * i + 1] += cot[2 * b + 1];
+    }
+    uint8_t *dst = P.host_args.data() + P.seed_off;
+    for (int64_t i = 0; i < P.seed_n_inst; ++i) {
+        if (fp64) {
+            std::memcpy(dst + i * 16, &seed[2 * i], 16);
+        } else {
+            const float f[2] = {(float)seed[2 * i], (float)seed[2 * i + 1]};
+            std::memcpy(dst + i * 8, f, 8);
+        }
+    }
+    P.seed_dirty = true;
 }
 
 static Plan &get_plan(Network &net, int32_t n_amps, const int32_t *outputs,
@@ -378,9 +402,31 @@ int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs, 
             total += net->leaves[id].size;
             g.leaves.push_back(id);
         }
-        {   // plan the first slice on the host before any device work (argument errors surface here)
-            std::vector<int64_t> first{0};
-            build_plan(*net, n_amps, outputs, &first, &g);
+        int64_t n_sl = 1;
+        for (int64_t l : net->sliced) n_sl *= net->labels.at(l).dim;
+        const bool fp64 = net->opt.precision == JET_PREC_FP64;
+        // an unsliced network keeps its adjoint plan: later calls with the same
+        // outputs and tensor ids only rewrite the cotangent seed
+        const bool cacheable = n_sl == 1;
+        Plan *GP = net->grad_plan.get();
+        const bool hit = cacheable && GP && GP->n_amps == n_amps && GP->path_version == net->path_version &&
+                         GP->slice_version == net->slice_version && GP->precision == net->opt.precision &&
+                         GP->reuse == net->opt.reuse && GP->outputs.size() == (size_t)n_amps * net->open.size() &&
+                         std::equal(GP->outputs.begin(), GP->outputs.end(), outputs) && GP->grad_leaves == g.leaves;
+        std::unique_ptr<Plan> first;
+        if (hit) {
+            write_seed(*GP, g.cot, fp64);
+        } else {   // plan the first slice on the host before any device work (argument errors surface here)
+            std::vector<int64_t> ids0{0};
+            first = build_plan(*net, n_amps, outputs, &ids0, &g);
+            if (cacheable) {
+                if (net->grad_plan) {
+                    if (net->last_run == net->grad_plan.get()) net->last_run = nullptr;
+                    release_plan_device(*net->grad_plan);
+                }
+                net->grad_plan = std::move(first);
+                GP = net->grad_plan.get();
+            }
         }
         ensure_leaves_on_device(*net);
         void *s = cuda_stream ? cuda_stream : net->stream;
@@ -391,23 +437,33 @@ int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs, 
             net->d_env_cap = std::max<int64_t>(total, 1);
         }
         device_memset_async(net->d_env, (size_t)std::max<int64_t>(total, 1) * sizeof(jet_c128), s);
-        int64_t n_sl = 1;
-        for (int64_t l : net->sliced) n_sl *= net->labels.at(l).dim;
         // per slice: recompute the forward tree (shared work reused across the
         // amplitudes, not across slices), sweep it backwards, accumulate in FP64
         std::vector<double> amps(2 * (size_t)n_amps, 0.0);
         std::vector<jet_c128> part(n_amps);
         for (int64_t sl = 0; sl < n_sl; ++sl) {
-            std::vector<int64_t> ids{sl};
-            auto P = build_plan(*net, n_amps, outputs, &ids, &g);
-            try {
-                bind_and_run(*net, *P, nullptr, cuda_stream, false);
+            if (cacheable) {   // one plan, kept (and its graph) for the next call
+                bind_and_run(*net, *GP, nullptr, cuda_stream, true);
                 copy_d2h(part.data(), net->d_amps, (size_t)n_amps * sizeof(jet_c128), s);
-            } catch (...) {
+            } else {
+                std::unique_ptr<Plan> P;
+                if (sl == 0 && first) {
+                    P = std::move(first);
+                } else {
+                    std::vector<int64_t> ids{sl};
+                    P = build_plan(*net, n_amps, outputs, &ids, &g);
+                }
+                try {
+                    bind_and_run(*net, *P, nullptr, cuda_stream, false);
+                    copy_d2h(part.data(), net->d_amps, (size_t)n_amps * sizeof(jet_c128), s);
+                } catch (...) {
+                    net->last_run = nullptr;
+                    release_plan_device(*P);
+                    throw;
+                }
+                net->last_run = nullptr;
                 release_plan_device(*P);
-                throw;
             }
-            release_plan_device(*P);
             for (int32_t b = 0; b < n_amps; ++b) {
                 amps[2 * b] += part[b].re;
                 amps[2 * b + 1] += part[b].im;
@@ -430,8 +486,9 @@ int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t
 {
     return guarded([&] {
         if (!net) fail(JET_EINVAL, "net is NULL");
-        if (!net->plan) fail(JET_ESTATE, "no plan yet");
-        const Plan &P = *net->plan;
+        const Plan *PP = net->last_run ? net->last_run : net->plan.get();
+        if (!PP) fail(JET_ESTATE, "no plan yet");
+        const Plan &P = *PP;
         if (n_out) *n_out = (int32_t)P.ops.size();
         for (size_t i = 0; out && i < P.ops.size() && (int32_t)i < cap; ++i) {
             const Op &op = P.ops[i];

@@ -169,6 +169,8 @@ void release_plan_device(Plan &plan)
 void free_network_device(Network &net)
 {
     if (net.plan) release_plan_device(*net.plan);
+    if (net.grad_plan) release_plan_device(*net.grad_plan);
+    net.last_run = nullptr;
     device_free(net.d_leaves);
     device_free(net.d_leaves64);
     device_free(net.own_arena);
@@ -302,7 +304,8 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
     void *leaves = net.opt.precision == JET_PREC_FP64 ? net.d_leaves64 : net.d_leaves;
 
     // (re)bind pointers
-    bool rebind = P.dirty_args || P.bound_arena != arena || P.bound_leaves != leaves || P.bound_amps != net.d_amps;
+    bool rebind = P.dirty_args || P.bound_arena != arena || P.bound_leaves != leaves || P.bound_amps != net.d_amps ||
+                  P.bound_env != net.d_env;
     if (rebind) {
         if (P.graph_exec) {
             JET_CUDA(cudaStreamSynchronize(s));
@@ -334,8 +337,17 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
         P.bound_arena = arena;
         P.bound_leaves = leaves;
         P.bound_amps = net.d_amps;
+        P.bound_env = net.d_env;
         P.dirty_args = false;
+        P.seed_dirty = false;
+    } else if (P.seed_dirty) {   // new cotangents of a cached adjoint plan: only the seed bytes change
+        const size_t es = net.opt.precision == JET_PREC_FP64 ? 16 : 8;
+        JET_CUDA(cudaMemcpyAsync((uint8_t *)P.d_args + P.seed_off, P.host_args.data() + P.seed_off,
+                                 (size_t)P.seed_n_inst * es, cudaMemcpyHostToDevice, s));
+        JET_CUDA(cudaStreamSynchronize(s));   // the pageable source may change before a later call
+        P.seed_dirty = false;
     }
+    net.last_run = &P;
 
     // optional per-launch timing: event records become nodes of the captured graph
     if (P.profile_level != net.opt.profile) {
@@ -361,13 +373,18 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
         }
         P.profile_level = net.opt.profile;
     }
-    auto issue_all = [&](cudaStream_t st) {
+    auto issue_all = [&](cudaStream_t st, bool capturing) {
+        // while capturing, external event records become real timestamp nodes of the
+        // graph; issued directly, they are plain records
+        auto record = [&](void *ev) {
+            if (capturing) JET_CUDA(cudaEventRecordWithFlags((cudaEvent_t)ev, st, cudaEventRecordExternal));
+            else JET_CUDA(cudaEventRecord((cudaEvent_t)ev, st));
+        };
         for (size_t i = 0; i < P.ops.size(); ++i) {
             const bool timed = i < P.ev_begin.size() && P.ev_begin[i];
-            // external event records: real timestamp nodes when the stream is being captured
-            if (timed) JET_CUDA(cudaEventRecordWithFlags((cudaEvent_t)P.ev_begin[i], st, cudaEventRecordExternal));
+            if (timed) record(P.ev_begin[i]);
             launch_op(P, P.host_args, P.ops[i], st);
-            if (timed) JET_CUDA(cudaEventRecordWithFlags((cudaEvent_t)P.ev_end[i], st, cudaEventRecordExternal));
+            if (timed) record(P.ev_end[i]);
         }
     };
 
@@ -384,7 +401,7 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
             cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 try {
-                    issue_all(cap);
+                    issue_all(cap, true);
                 } catch (...) {
                     cudaStreamEndCapture(cap, &g);
                     if (g) cudaGraphDestroy(g);
@@ -404,7 +421,7 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
         }
         JET_CUDA(cudaGraphLaunch((cudaGraphExec_t)P.graph_exec, s));
     } else {
-        issue_all(s);
+        issue_all(s, false);
     }
 }
 

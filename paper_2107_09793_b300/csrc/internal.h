@@ -112,6 +112,17 @@ struct Plan {
     void *bound_arena = nullptr;
     void *bound_leaves = nullptr;
     void *bound_amps = nullptr;
+    void *bound_env = nullptr;
+
+    // adjoint plans: where the root's cotangent seed sits in the argument buffer,
+    // so that a cached plan takes new cotangents without being rebuilt
+    bool grad = false;
+    std::vector<int32_t> grad_leaves;    // requested tensor ids, in request order
+    std::vector<int64_t> grad_env_off;   // their environment offsets
+    size_t seed_off = 0;                 // byte offset of the seed values in host_args
+    std::vector<int32_t> seed_inst;      // root instance of each (amplitude, slice) assignment
+    int64_t seed_n_inst = 0, seed_n_sl = 1;
+    bool seed_dirty = false;
     std::vector<void *> ev_begin, ev_end;   // per op: cudaEvent_t pair when profiled
     int32_t profile_level = 0;
     void *graph_exec = nullptr;       // cudaGraphExec_t
@@ -138,6 +149,8 @@ struct Network {
     void *stream = nullptr;          // library-internal stream for uploads
 
     std::unique_ptr<Plan> plan;
+    std::unique_ptr<Plan> grad_plan;     // cached adjoint plan (unsliced networks)
+    const Plan *last_run = nullptr;      // the plan jet_profile reports
     void *own_arena = nullptr;
     size_t own_arena_bytes = 0;
     void *user_arena = nullptr;

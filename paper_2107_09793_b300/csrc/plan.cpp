@@ -1193,6 +1193,13 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 }
             }
             env_base[rootv] = {BASE_BLOB, (int64_t)off};
+            P.grad = true;
+            P.grad_leaves = grad->leaves;
+            P.grad_env_off = grad->env_off;
+            P.seed_off = off;
+            P.seed_n_inst = R.n_inst;
+            P.seed_n_sl = n_sl;
+            P.seed_inst.assign(inst_of[rootv].begin(), inst_of[rootv].begin() + n_assign);
         }
         auto emit_memset = [&](size_t off, size_t nbytes) {
             MemsetArgs m;
