@@ -514,14 +514,18 @@ def run_impl(args):
 
 
 def run_gemm_case(args):
-    """One pairwise contraction shaped like the workload's dominant node, large
-    enough to exceed L2 but small enough for an ncu capture: C[8192 x 8192] =
-    A[8192 x 2048] B[2048 x 8192], complex64, in the chosen precision."""
+    """One pairwise contraction node, large enough to exceed L2 but small enough
+    for an ncu capture: C[M x N] = A[M x K] B[K x N] complex64 for each of INST
+    instances of A (sliced labels) sharing one B, in the chosen precision.
+    Default 8192 x 8192 x 2048, one instance; --gemm-shape M,N,K,INST (powers of two)."""
     import torch
     from circuits import SplitMix64
     from paper_2107_09793_b300 import jet
     torch.cuda.set_device(0)
-    rm, rk, rn = 13, 11, 13
+    gm, gn, gk, gi = [int(x) for x in args.gemm_shape.split(",")]
+    lg = lambda v: int(round(np.log2(v)))
+    ri = lg(gi)
+    rm, rk, rn = lg(gm) + ri, lg(gk), lg(gn)
     la = list(range(rm)) + list(range(100, 100 + rk))
     lb = list(range(100, 100 + rk)) + list(range(200, 200 + rn))
     rng = np.random.default_rng(SplitMix64(9).next_u64() % (1 << 32))
@@ -537,6 +541,8 @@ def run_gemm_case(args):
         path.append((cur, i))
         cur += 1
     net.path_set(path)
+    if ri:
+        net.slice(list(range(ri)))   # the slowest M labels of A: INST instances of the GEMM node
     outs = np.zeros((1, 0), np.int32)
     amps = torch.zeros(1, dtype=torch.complex128, device="cuda")
     sh = torch.cuda.current_stream().cuda_stream
@@ -548,8 +554,60 @@ def run_gemm_case(args):
             ms += [r["ms"] for r in net.profile() if r["kind"] in ("gemm_tc", "gemm_simt")]
     flop = 8.0 * 2 ** (rm + rk + rn)
     t = statistics.mean(ms) * 1e-3
-    print(json.dumps({"case": "gemm M=N=8192 K=2048 complex", "precision": args.precision, "gemm_ms": t * 1e3,
-                      "algorithmic_tflops": flop / t / 1e12}), flush=True)
+    print(json.dumps({"case": f"gemm M={gm} N={gn} K={gk} x {gi} instances, complex", "precision": args.precision,
+                      "gemm_ms": t * 1e3, "algorithmic_tflops": flop / t / 1e12}), flush=True)
+    return 0
+
+
+def run_apply_case(args):
+    """The small-operand application kernel on a case small enough for an ncu
+    capture: a 14-mode 2x7 bosonic lattice (d=4, 2 layers) contracted in the
+    state-vector order (2^28-element intermediates, 2 GiB), 4 photon patterns."""
+    import torch
+    from circuits import gbs_lattice_circuit, circuit_to_network, random_patterns
+    from paper_2107_09793_b300 import jet
+    torch.cuda.set_device(0)
+    tn = circuit_to_network(gbs_lattice_circuit(2, 7, 4, 2, seed=3))
+    outs = random_patterns(14, 4, 9, 4)
+    net = jet.Network(tn.labels, tn.data, precision="fp32", profile=2)
+    net.set_open(tn.open_labels)
+    n = len(tn.labels)
+    net.path_set([(0, 1)] + [(k + 2, n + k) for k in range(n - 2)])
+    amps = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+    sh = torch.cuda.current_stream().cuda_stream
+    ms, nb = [], 0.0
+    for i in range(args.warmup + args.steps):
+        net.contract_async(outs, amps.data_ptr(), sh)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            recs = [r for r in net.profile() if r["kind"] == "apply" and r["ms"] > 0]
+            ms.append(sum(r["ms"] for r in recs))
+            nb = sum(r["bytes"] for r in recs)
+    t = statistics.mean(ms) * 1e-3
+    print(json.dumps({"case": "apply: 14-mode 2x7 lattice, d=4, state-vector order, 4 patterns", "apply_ms": t * 1e3,
+                      "apply_launches": len(recs), "algorithmic_gb_s": nb / t / 1e9}), flush=True)
+    return 0
+
+
+def run_gbs16_case(args):
+    """Only the 256-pattern bosonic batch (for a launch list of that workload)."""
+    import torch
+    from circuits import configs
+    from paper_2107_09793_b300 import jet
+    torch.cuda.set_device(0)
+    w = configs.build("gbs16")
+    net = jet.from_network(w.network, precision="fp32")
+    net.path_greedy_batch(w.outputs, seed=1, n_trials=8, max_elems=1 << 32)
+    amps = torch.zeros(len(w.outputs), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        net.contract_async(w.outputs, amps.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms = _timed(lambda: net.contract_async(w.outputs, amps.data_ptr(), stream.cuda_stream), stream, ev0, ev1,
+                args.steps)
+    print(json.dumps({"case": "gbs16: 256-pattern batch", "ms_per_batch": statistics.mean(ms),
+                      "amplitudes_per_s": len(w.outputs) / (statistics.mean(ms) * 1e-3)}), flush=True)
     return 0
 
 
@@ -564,11 +622,17 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
     ap.add_argument("--skip-others", action="store_true", help="skip the other workloads (bosonic lattice, "
                     "parameterised circuit gradient, 53-qubit slices)")
-    ap.add_argument("--case", default="workload", choices=["workload", "gemm"],
-                    help="gemm: a single complex GEMM node sized for ncu captures")
+    ap.add_argument("--gemm-shape", default="8192,8192,2048,1", help="--case gemm: M,N,K,INST")
+    ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16"],
+                    help="gemm / apply: one kernel family on a case sized for ncu captures; "
+                         "gbs16: only the bosonic batch")
     args = ap.parse_args()
     if args.case == "gemm":
         return run_gemm_case(args)
+    if args.case == "apply":
+        return run_apply_case(args)
+    if args.case == "gbs16":
+        return run_gbs16_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_impl(args)

@@ -46,19 +46,19 @@ struct TcCfg<JET_PREC_TF32> {
 };
 template <>
 struct TcCfg<JET_PREC_TF32X3> {
-    static constexpr int NP = 4, NT = 3, EB = 4, KIND = 1, STAGES = 3, FMT = 2, CHUNK_K = 32;
+    static constexpr int NP = 4, NT = 3, EB = 4, KIND = 1, STAGES = 2, FMT = 2, CHUNK_K = 32;
     static constexpr bool SCALED = false;
     __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }   // lo.lo dropped
 };
 template <>
 struct TcCfg<JET_PREC_BF16X3> {
-    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 3, FMT = 1, CHUNK_K = 64;
+    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 2, FMT = 1, CHUNK_K = 64;
     static constexpr bool SCALED = false;
     __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }
 };
 template <>
 struct TcCfg<JET_PREC_FP16X3> {
-    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 3, FMT = 0, CHUNK_K = 64;
+    static constexpr int NP = 4, NT = 3, EB = 2, KIND = 0, STAGES = 2, FMT = 0, CHUNK_K = 64;
     static constexpr bool SCALED = true;
     __device__ static void term(int t, int &p, int &q) { p = (t == 2); q = (t == 1); }
 };
@@ -216,9 +216,9 @@ __device__ __forceinline__ void split_parts(float x, float (&p)[3])
     }
 }
 
-constexpr int SPLIT_TR = 32, SPLIT_TK = 64;
+constexpr int SPLIT_TR = 64, SPLIT_TK = 64;
 
-// Tiled gather + split: a block owns a 32-row x 64-column tile of the planes.
+// Tiled gather + split: a block owns a 64-row x 64-column tile of the planes.
 // The source offsets of its rows and columns are decoded once into shared
 // memory; the tile is read with threads running along the source's fastest
 // label (rows or K, fast_k) and written along K, two values per thread.
@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
             const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
             const int64_t row0 = rt * SPLIT_TR, k0 = kt * SPLIT_TK;
             __syncthreads();
+            static_assert(SPLIT_TR + SPLIT_TK <= 256, "one decoding thread per tile row and column");
             if (tid < SPLIT_TR + SPLIT_TK) {
                 const bool is_row = tid < SPLIT_TR;
                 int64_t x = is_row ? row0 + tid : k0 + (tid - SPLIT_TR), off = -1;
@@ -271,10 +272,10 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
                 int r, kk;
                 if (a.fast_k) {
                     kk = tid & (SPLIT_TK - 1);
-                    r = (tid >> 6) + 4 * i;
+                    r = (tid >> 6) + (256 / SPLIT_TK) * i;
                 } else {
                     r = tid & (SPLIT_TR - 1);
-                    kk = (tid >> 5) + 8 * i;
+                    kk = (tid >> 6) + (256 / SPLIT_TR) * i;
                 }
                 const int64_t ro = rowOff[r], ko = kOff[kk];
                 tile[r][kk] = (ro >= 0 && ko >= 0) ? __ldg(S + ro + ko) : make_float2(0.f, 0.f);
@@ -283,16 +284,16 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
             if (TcCfg<MODE>::SCALED) {
                 // one power-of-two scale per (row, 64-wide K chunk = this tile's columns):
                 // the chunk's largest |re| or |im| lands in [2^14, 2^15), inside FP16's range
-                const int r = tid >> 3, sub = tid & 7;
+                static_assert(SPLIT_TR == 64 && SPLIT_TK == 64, "four threads per row of 64");
+                const int r = tid >> 2, sub = tid & 3;
                 float m = 0.f;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float2 v = tile[r][sub * 8 + q];
+                for (int q = 0; q < 16; ++q) {
+                    const float2 v = tile[r][sub * 16 + q];
                     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
                 }
                 m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
                 m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 4));
                 int e = 0;
                 if (m > 0.f) {
                     frexpf(m, &e);                     // m = f * 2^e, f in [0.5, 1)
@@ -360,6 +361,19 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
 // Restarting the tensor-core accumulator every 32 of K keeps the long sums as
 // accurate as an FP32 FMA chain.
 constexpr int TC_EPI_WARPS = 8;
+// C staging: each epilogue warp writes its 32 rows x 16 columns through shared
+// memory (rows padded by one complex value) so that global stores cover whole
+// 128-byte lines, four rows per instruction.
+constexpr int TC_CST_ROW = 17;
+constexpr int TC_CST_BYTES = TC_EPI_WARPS * 32 * TC_CST_ROW * 8;
+constexpr int TC_SMEM_LIMIT = 232448;   // opt-in dynamic shared memory per block
+constexpr int TC_STATIC_SMEM = 4096;    // barriers, scale staging and flags (upper bound)
+template <int MODE>
+__host__ __device__ constexpr bool tc_cstage()
+{
+    return TcCfg<MODE>::STAGES * 2 * TcCfg<MODE>::NP * TC_PLANE_TILE + 1024 + TC_CST_BYTES + TC_STATIC_SMEM <=
+           TC_SMEM_LIMIT;
+}
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr int TC_GROUP_M = 8;   // tile rasterisation: groups of 8 M-tiles walk the N-tiles together
 
@@ -507,6 +521,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     } else {
         // promotion + epilogue: rows 32*(warp%4) + lane, columns half*64 .. +63 of the tile
         const int quarter = warp & 3, half = (warp - 2) >> 2;
+        __shared__ float sfn[TC_EPI_WARPS][64];   // SCALED: this warp's 64 column scales of the chunk
         int64_t cg = 0;
         for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
             int inst, tm, tn;
@@ -526,12 +541,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 const uint32_t base = tmem + buf * 2 * TC_BN + ((uint32_t)(quarter * 32) << 16) + half * 64;
                 // SCALED: undo the operands' power-of-two chunk scales (exact)
                 float fm = 1.f;
-                const float *fn = nullptr;
+                float *fn = sfn[warp - 2];
                 if (Cfg::SCALED) {
                     const int64_t instA = ((const int32_t *)a.zA)[inst] / NP, instB = ((const int32_t *)a.zB)[inst] / NP;
                     const int64_t row = (int64_t)tm * TC_BM + quarter * 32 + lane;
                     fm = ((const float *)a.scaleA)[(instA * n_chunks + c) * a.m_pad + row];
-                    fn = (const float *)a.scaleB + (instB * n_chunks + c) * a.n_pad + (int64_t)tn * TC_BN + half * 64;
+                    // the warp's 64 column scales: two loads per lane, read back as broadcasts
+                    const float *g = (const float *)a.scaleB + (instB * n_chunks + c) * a.n_pad + (int64_t)tn * TC_BN +
+                                     half * 64;
+                    __syncwarp();
+                    fn[lane] = __ldg(g + lane);
+                    fn[lane + 32] = __ldg(g + lane + 32);
+                    __syncwarp();
                 }
                 // 16 columns per TMEM load (8 in the scaled mode, whose scales need registers too)
                 constexpr int LW = Cfg::SCALED ? 8 : 16;
@@ -549,7 +570,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 #pragma unroll
                     for (int j = 0; j < LW; ++j) {
                         if (Cfg::SCALED) {
-                            const float f = fm * __ldg(fn + h * LW + j);
+                            const float f = fm * fn[h * LW + j];
                             racc[h * LW + j] = fmaf(__uint_as_float(R[j]), f, racc[h * LW + j]);
                             iacc[h * LW + j] = fmaf(__uint_as_float(I[j]), f, iacc[h * LW + j]);
                         } else {
@@ -564,9 +585,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             }
             if (!ok) break;
             const int64_t row = (int64_t)tm * TC_BM + quarter * 32 + lane;
-            if (row < a.M) {
-                float2 *C = (float2 *)((const uint64_t *)a.ptrC)[inst];
-                const int64_t col0 = (int64_t)tn * TC_BN + half * 64;
+            float2 *C = (float2 *)((const uint64_t *)a.ptrC)[inst];
+            const int64_t col0 = (int64_t)tn * TC_BN + half * 64;
+            if (tc_cstage<MODE>() && (a.N & 15) == 0 && col0 + 64 <= a.N) {
+                // whole 64-column half tile in range: stage 16 columns at a time
+                float2 *st = (float2 *)(smem + (size_t)S * STAGE_BYTES) + (size_t)(warp - 2) * 32 * TC_CST_ROW;
+                const int64_t row0 = (int64_t)tm * TC_BM + quarter * 32;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) st[lane * TC_CST_ROW + j] = make_float2(racc[p * 16 + j], iacc[p * 16 + j]);
+                    __syncwarp();
+#pragma unroll
+                    for (int it = 0; it < 8; ++it) {
+                        const int r = it * 4 + (lane >> 3), cc = (lane & 7) * 2;
+                        if (row0 + r < a.M) {
+                            const float2 v0 = st[r * TC_CST_ROW + cc], v1 = st[r * TC_CST_ROW + cc + 1];
+                            *(float4 *)(C + (row0 + r) * a.N + col0 + p * 16 + cc) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                        }
+                    }
+                    __syncwarp();
+                }
+            } else if (row < a.M) {
                 float2 *dst = C + row * a.N + col0;
                 if ((a.N & 1) == 0 && col0 + 64 <= a.N) {
 #pragma unroll
@@ -593,7 +633,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
 template <int MODE>
 static int tc_smem_bytes()
 {
-    return TcCfg<MODE>::STAGES * 2 * TcCfg<MODE>::NP * TC_PLANE_TILE + 1024;
+    return TcCfg<MODE>::STAGES * 2 * TcCfg<MODE>::NP * TC_PLANE_TILE + 1024 + (tc_cstage<MODE>() ? TC_CST_BYTES : 0);
 }
 
 int tc_planes(int mode)

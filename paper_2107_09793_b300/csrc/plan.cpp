@@ -16,6 +16,8 @@
 // a best-fit allocator simulated in launch order, so the arena size is the
 // peak of live intermediates.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <unordered_map>
@@ -968,6 +970,16 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                             st *= V.dims[q];
                         }
                     }
+                    if (getenv("JET_DEBUG_PLAN")) {
+                        fprintf(stderr, "node %d split child %d (leaf %d gemm %d) inst %ld size %ld conv %d | V:", v, id,
+                                id < n_leaves, id >= n_leaves ? (int)node[id].use_gemm : -1, (long)ninst, (long)V.size, (int)conv);
+                        for (size_t q = 0; q < V.labels.size(); ++q) fprintf(stderr, " %ld", (long)V.labels[q]);
+                        fprintf(stderr, " | f:");
+                        for (int64_t l : f) fprintf(stderr, " %ld", (long)l);
+                        fprintf(stderr, " | kappa:");
+                        for (int64_t l : kappa) fprintf(stderr, " %ld", (long)l);
+                        fprintf(stderr, "\n");
+                    }
                     std::vector<std::pair<int32_t, int64_t>> ps;
                     for (int64_t j = 0; j < ninst; ++j) ps.push_back(base_ref(id, (int32_t)j));
                     size_t o_ps = blob.put_ptrs(ps);
@@ -985,7 +997,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     op.bytes = (double)ninst * ((double)V.size * 8.0 + (double)NP * rows_pad * k_pad * eb);
                     int64_t gy = std::min<int64_t>(ninst, 65535);
                     op.grid_y = (int32_t)gy;
-                    const int64_t tiles = (rows_pad / 32) * ((k_pad + 63) / 64);
+                    const int64_t tiles = (rows_pad / 64) * ((k_pad + 63) / 64);   // 64 x 64 tiles
                     op.grid_x = (int32_t)std::max<int64_t>(
                         1, std::min<int64_t>(tiles, std::max<int64_t>(1, 148 * 16 / gy)));
                     {
