@@ -217,70 +217,105 @@ __device__ __forceinline__ void split_parts(float x, float (&p)[3])
 }
 
 constexpr int SPLIT_TR = 64, SPLIT_TK = 64;
+constexpr int SPLIT_ROW = SPLIT_TK + 1;                              // padded tile row (float2)
+constexpr int SPLIT_SMEM = 2 * SPLIT_TR * SPLIT_ROW * 8               // two tiles
+                           + 2 * (SPLIT_TR + SPLIT_TK) * 8;           // their row / column offsets
 
-// Tiled gather + split: a block owns a 64-row x 64-column tile of the planes.
-// The source offsets of its rows and columns are decoded once into shared
-// memory; the tile is read with threads running along the source's fastest
-// label (rows or K, fast_k) and written along K, two values per thread.
+__device__ __forceinline__ void cp_async8_zfill(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// Tiled gather + split: a block walks 64-row x 64-column tiles of the planes.
+// Two tiles are in flight: while one is split and written, the next one's
+// source elements are already being copied into shared memory by cp.async
+// (8-byte copies, zero-filled outside the operand), so the loads of a block
+// never wait behind its own conversion work.  The source offsets of a tile's
+// rows and columns are decoded once into shared memory; elements are read with
+// threads running along the source's fastest label (rows or K, fast_k) and
+// written along K, two values per thread.
 template <int MODE, bool POW2>
-__global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant__ TcSplitArgs a)
+__global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant__ TcSplitArgs a)
 {
     constexpr int NP = TcCfg<MODE>::NP, EB = TcCfg<MODE>::EB, NPH = NP / 2;
-    __shared__ float2 tile[SPLIT_TR][SPLIT_TK + 1];
-    __shared__ int64_t rowOff[SPLIT_TR], kOff[SPLIT_TK];
+    extern __shared__ __align__(16) uint8_t split_smem[];
+    float2 *tiles_s = (float2 *)split_smem;                                        // [2][64][65]
+    int64_t *offs = (int64_t *)(split_smem + 2 * SPLIT_TR * SPLIT_ROW * 8);       // [2][64 + 64]
     __shared__ float mul[SPLIT_TR];   // SCALED: 2^s of each row of this 64-wide chunk
     const int tid = threadIdx.x;
     const int64_t k_tiles = (a.k_pad + SPLIT_TK - 1) / SPLIT_TK;
-    const int64_t tiles = (a.rows_pad / SPLIT_TR) * k_tiles;
+    const int64_t n_tiles = (a.rows_pad / SPLIT_TR) * k_tiles;
     const int64_t plane_elems = a.rows_pad * a.k_pad;
+
+    auto decode = [&](int64_t t, int buf) {   // threads 0..127: one row or column offset each
+        static_assert(SPLIT_TR + SPLIT_TK <= 256, "one decoding thread per tile row and column");
+        if (tid < SPLIT_TR + SPLIT_TK) {
+            const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
+            const bool is_row = tid < SPLIT_TR;
+            int64_t x = is_row ? rt * SPLIT_TR + tid : kt * SPLIT_TK + (tid - SPLIT_TR), off = -1;
+            if (x < (is_row ? a.rows : a.k)) {
+                off = 0;
+                const int rank = is_row ? a.rank_r : a.rank_k;
+                const int64_t *dim = is_row ? a.r_dim : a.k_dim, *str = is_row ? a.r_s : a.k_s;
+                for (int jj = 0; jj < rank; ++jj) {
+                    const int64_t d = dim[jj];
+                    int64_t q, r;
+                    if (POW2) {
+                        const int sh = __ffsll((unsigned long long)d) - 1;
+                        q = x >> sh;
+                        r = x & (d - 1);
+                    } else {
+                        q = x / d;
+                        r = x - q * d;
+                    }
+                    off += r * str[jj];
+                    x = q;
+                }
+            }
+            offs[buf * (SPLIT_TR + SPLIT_TK) + tid] = off;
+        }
+    };
+    auto issue = [&](const float2 *S, int buf) {   // 16 zero-filling 8-byte copies per thread
+        const int64_t *rowOff = offs + buf * (SPLIT_TR + SPLIT_TK), *kOff = rowOff + SPLIT_TR;
+        float2 *tile = tiles_s + (size_t)buf * SPLIT_TR * SPLIT_ROW;
+#pragma unroll
+        for (int i = 0; i < (SPLIT_TR * SPLIT_TK) / 256; ++i) {
+            int r, kk;
+            if (a.fast_k) {
+                kk = tid & (SPLIT_TK - 1);
+                r = (tid >> 6) + (256 / SPLIT_TK) * i;
+            } else {
+                r = tid & (SPLIT_TR - 1);
+                kk = (tid >> 6) + (256 / SPLIT_TR) * i;
+            }
+            const int64_t ro = rowOff[r], ko = kOff[kk];
+            const bool in = ro >= 0 && ko >= 0;
+            cp_async8_zfill(smem_u32(tile + r * SPLIT_ROW + kk), in ? (const void *)(S + ro + ko) : (const void *)S,
+                            in ? 8u : 0u);
+        }
+    };
+
     for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
         const float2 *__restrict__ S = (const float2 *)((const uint64_t *)a.ptrSrc)[inst];
         uint8_t *base = (uint8_t *)a.planes + (int64_t)inst * NP * plane_elems * EB;
-        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        __syncthreads();   // the previous instance's readers of the buffers are done
+        if (blockIdx.x < n_tiles) decode(blockIdx.x, 0);
+        __syncthreads();
+        if (blockIdx.x < n_tiles) issue(S, 0);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        int k = 0;
+        for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
+            const int cur = k & 1, nxt = cur ^ 1;
+            const int64_t t1 = t + gridDim.x;
+            if (t1 < n_tiles) decode(t1, nxt);
+            __syncthreads();   // next offsets visible; the buffer of tile k-1 is free
+            if (t1 < n_tiles) issue(S, nxt);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group 1;" ::: "memory");   // this thread's copies of tile t
+            __syncthreads();                                        // everyone's
+            const float2 *tile = tiles_s + (size_t)cur * SPLIT_TR * SPLIT_ROW;
             const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
             const int64_t row0 = rt * SPLIT_TR, k0 = kt * SPLIT_TK;
-            __syncthreads();
-            static_assert(SPLIT_TR + SPLIT_TK <= 256, "one decoding thread per tile row and column");
-            if (tid < SPLIT_TR + SPLIT_TK) {
-                const bool is_row = tid < SPLIT_TR;
-                int64_t x = is_row ? row0 + tid : k0 + (tid - SPLIT_TR), off = -1;
-                if (x < (is_row ? a.rows : a.k)) {
-                    off = 0;
-                    const int rank = is_row ? a.rank_r : a.rank_k;
-                    const int64_t *dim = is_row ? a.r_dim : a.k_dim, *str = is_row ? a.r_s : a.k_s;
-                    for (int j = 0; j < rank; ++j) {
-                        const int64_t d = dim[j];
-                        int64_t q, r;
-                        if (POW2) {
-                            const int sh = __ffsll((unsigned long long)d) - 1;
-                            q = x >> sh;
-                            r = x & (d - 1);
-                        } else {
-                            q = x / d;
-                            r = x - q * d;
-                        }
-                        off += r * str[j];
-                        x = q;
-                    }
-                }
-                if (is_row) rowOff[tid] = off;
-                else kOff[tid - SPLIT_TR] = off;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < (SPLIT_TR * SPLIT_TK) / 256; ++i) {
-                int r, kk;
-                if (a.fast_k) {
-                    kk = tid & (SPLIT_TK - 1);
-                    r = (tid >> 6) + (256 / SPLIT_TK) * i;
-                } else {
-                    r = tid & (SPLIT_TR - 1);
-                    kk = (tid >> 6) + (256 / SPLIT_TR) * i;
-                }
-                const int64_t ro = rowOff[r], ko = kOff[kk];
-                tile[r][kk] = (ro >= 0 && ko >= 0) ? __ldg(S + ro + ko) : make_float2(0.f, 0.f);
-            }
-            __syncthreads();
             if (TcCfg<MODE>::SCALED) {
                 // one power-of-two scale per (row, 64-wide K chunk = this tile's columns):
                 // the chunk's largest |re| or |im| lands in [2^14, 2^15), inside FP16's range
@@ -289,7 +324,7 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
                 float m = 0.f;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float2 v = tile[r][sub * 16 + q];
+                    const float2 v = tile[r * SPLIT_ROW + sub * 16 + q];
                     m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
                 }
                 m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
@@ -310,10 +345,10 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
             for (int i = 0; i < (SPLIT_TR * SPLIT_TK / 2) / 256; ++i) {
                 const int idx = tid + 256 * i;
                 const int r = idx / (SPLIT_TK / 2), kp = 2 * (idx % (SPLIT_TK / 2));
-                const int64_t k = k0 + kp;
-                if (k >= a.k_pad) continue;
-                const int64_t e = (row0 + r) * a.k_pad + k;
-                float2 v0 = tile[r][kp], v1 = tile[r][kp + 1];
+                const int64_t kcol = k0 + kp;
+                if (kcol >= a.k_pad) continue;
+                const int64_t e = (row0 + r) * a.k_pad + kcol;
+                float2 v0 = tile[r * SPLIT_ROW + kp], v1 = tile[r * SPLIT_ROW + kp + 1];
                 if (TcCfg<MODE>::SCALED) {
                     const float f = mul[r];
                     v0.x *= f;
@@ -346,6 +381,7 @@ __global__ void __launch_bounds__(256, 6) tc_split_kernel(const __grid_constant_
                 }
             }
         }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
 }
 
@@ -664,6 +700,19 @@ cudaError_t set_tc_smem_limits()
     JET_TCSM(JET_PREC_BF16X6);
     JET_TCSM(JET_PREC_FP16X3);
 #undef JET_TCSM
+#define JET_SPSM(M)                                                                                          \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(tc_split_kernel<M JET_COMMA true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 SPLIT_SMEM);                                                                \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(tc_split_kernel<M JET_COMMA false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 SPLIT_SMEM);
+    JET_SPSM(JET_PREC_TF32)
+    JET_SPSM(JET_PREC_TF32X3)
+    JET_SPSM(JET_PREC_BF16X3)
+    JET_SPSM(JET_PREC_BF16X6)
+    JET_SPSM(JET_PREC_FP16X3)
+#undef JET_SPSM
     return e;
 }
 
@@ -673,8 +722,8 @@ cudaError_t launch_tc_split(const TcSplitArgs &a, const LaunchCfg &c, cudaStream
     const bool pow2 = c.variant & 2;
 #define JET_SPLIT(M)                                                                         \
     do {                                                                                     \
-        if (pow2) tc_split_kernel<M, true><<<grid, 256, 0, s>>>(a);                          \
-        else tc_split_kernel<M, false><<<grid, 256, 0, s>>>(a);                              \
+        if (pow2) tc_split_kernel<M, true><<<grid, 256, SPLIT_SMEM, s>>>(a);                 \
+        else tc_split_kernel<M, false><<<grid, 256, SPLIT_SMEM, s>>>(a);                     \
     } while (0)
     switch (a.mode) {
     case JET_PREC_TF32: JET_SPLIT(JET_PREC_TF32); break;
