@@ -146,6 +146,73 @@ __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ 
     }
 }
 
+// Streamed form, for a small operand with more summed entries (up to
+// JET_APPLY_MAXK) and few free ones (up to JET_APPLY_STREAMF): the thread keeps
+// NF outputs of its fibers in registers at a time (free entries in chunks of
+// NF) and walks the summed index, one entry of A at a time, instead of holding
+// the whole fiber.
+template <int NF, int FIB, bool POW2>
+__global__ void __launch_bounds__(256) apply_stream_c64(const __grid_constant__ ApplyArgs a)
+{
+    __shared__ ulonglong2 sB[JET_APPLY_MAXK * JET_APPLY_STREAMF];   // [q][f], rows of nfp entries
+    const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
+    const int nk = a.nk, nf = a.nf;
+    const int nfp = (nf + NF - 1) / NF * NF;   // row length: free entries padded to whole chunks
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB;
+    for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
+        const unsigned long long *__restrict__ A = (const unsigned long long *)pA[inst];
+        const float2 *__restrict__ B = (const float2 *)pB[inst];
+        unsigned long long *__restrict__ C = (unsigned long long *)pC[inst];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nk * nfp; i += blockDim.x) {
+            const int q = i / nfp, f = i - q * nfp;
+            const float2 b = f < nf ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);
+            sB[i] = make_ulonglong2(pack2(b.x, b.x), pack2(b.y, b.y));
+        }
+        __syncthreads();
+        for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x * FIB + threadIdx.x; r0 < a.n_fib; r0 += step) {
+            int64_t oa[FIB], oc[FIB];
+            bool ok[FIB];
+#pragma unroll
+            for (int u = 0; u < FIB; ++u) {
+                const int64_t r = r0 + (int64_t)u * blockDim.x;
+                ok[u] = r < a.n_fib;
+                fiber_offsets<POW2>(ok[u] ? r : 0, a, oa[u], oc[u]);
+            }
+            for (int f0 = 0; f0 < nf; f0 += NF) {
+                unsigned long long p[FIB][NF], m[FIB][NF];
+#pragma unroll
+                for (int u = 0; u < FIB; ++u)
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) p[u][f] = m[u][f] = 0ull;
+#pragma unroll 2
+                for (int q = 0; q < nk; ++q) {
+                    unsigned long long x[FIB];
+#pragma unroll
+                    for (int u = 0; u < FIB; ++u) x[u] = ok[u] ? __ldg(A + oa[u] + a.kA[q]) : 0ull;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) {
+                        const ulonglong2 b = sB[q * nfp + f0 + f];
+#pragma unroll
+                        for (int u = 0; u < FIB; ++u) cmac2(p[u][f], m[u][f], b, x[u]);
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NF; ++f)
+                    if (f0 + f < nf) {
+                        const int64_t cf = a.cF[f0 + f];
+#pragma unroll
+                        for (int u = 0; u < FIB; ++u)
+                            if (ok[u]) {
+                                const float2 c = cfinish(p[u][f], m[u][f]);
+                                __stcs(C + oc[u] + cf, pack2(c.x, c.y));
+                            }
+                    }
+            }
+        }
+    }
+}
+
 // NK: summed entries (compile time, so the fiber stays in registers); FIB:
 // fibers per thread (complex128: 1).
 template <typename V, int NK, int FIB, bool POW2>
@@ -216,8 +283,31 @@ static void launch_nk(const ApplyArgs &a, dim3 grid, bool pow2, cudaStream_t s)
 
 cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
+    if (a.nf_tmpl > 0) {   // streamed form (complex64)
+        // nf_tmpl: free entries per register chunk
+        const bool ok = (a.nf_tmpl == 1 || a.nf_tmpl == 2 || a.nf_tmpl == 4 || a.nf_tmpl == 8 || a.nf_tmpl == 16) &&
+                        a.nf >= 1 && a.nf <= JET_APPLY_STREAMF && a.nk >= 1 && a.nk <= JET_APPLY_MAXK &&
+                        a.rank <= JET_MAXR && !(c.variant & 1);
+        if (!ok) return cudaErrorInvalidValue;
+        dim3 grid(c.gx, c.gy, 1);
+        const bool pow2 = c.variant & 4;
+#define JET_ST(NF, FIB)                                                                     \
+    do {                                                                                    \
+        if (pow2) apply_stream_c64<NF, FIB, true><<<grid, 256, 0, s>>>(a);                   \
+        else apply_stream_c64<NF, FIB, false><<<grid, 256, 0, s>>>(a);                       \
+    } while (0)
+        switch (a.nf_tmpl) {
+        case 1: JET_ST(1, 2); break;
+        case 2: JET_ST(2, 2); break;
+        case 4: JET_ST(4, 2); break;
+        case 8: JET_ST(8, 2); break;
+        default: JET_ST(16, 1); break;
+        }
+#undef JET_ST
+        return cudaGetLastError();
+    }
     const bool tmpl_ok = a.nk_tmpl == 1 || a.nk_tmpl == 2 || a.nk_tmpl == 4 || a.nk_tmpl == 8 || a.nk_tmpl == 16;
-    if (!tmpl_ok || a.nk < 1 || a.nk > a.nk_tmpl || a.nf < 1 || a.nf > JET_APPLY_MAXF ||
+    if (!tmpl_ok || a.nk < 1 || a.nk > a.nk_tmpl || a.nk_tmpl > JET_APPLY_HOLDK || a.nf < 1 || a.nf > JET_APPLY_MAXF ||
         a.nf * a.nk_tmpl > JET_APPLY_MAXB || a.rank > JET_MAXR)
         return cudaErrorInvalidValue;
     dim3 grid(c.gx, c.gy, 1);

@@ -9,9 +9,11 @@
 #define JET_COLMAX 1024      // max entries of a column offset table
 #define JET_KLOMAX 1024      // max entries of an inner-K offset table
 #define JET_SPLITK_G 8       // outputs per block in the split-K direct kernel
-#define JET_APPLY_MAXK 16    // small-operand application: max summed entries
+#define JET_APPLY_MAXK 64    // small-operand application: max summed entries (streamed form)
+#define JET_APPLY_HOLDK 16   // ... held in registers: max summed entries
 #define JET_APPLY_MAXF 256   // small-operand application: max free entries of the small operand
-#define JET_APPLY_MAXB 256   // small-operand application: max entries of the small operand
+#define JET_APPLY_MAXB 256   // held form: max entries of the small operand
+#define JET_APPLY_STREAMF 32 // streamed form: max free entries of the small operand
 
 // Pairwise contraction C = sum_K A * B evaluated directly from strides
 // (Section 2.3).  The output index is split as (row, col): col is the trailing
@@ -40,7 +42,8 @@ struct ApplyArgs {
     uint64_t ptrA, ptrB, ptrC;      // device arrays of n_inst addresses (A large, B small)
     int64_t n_fib;                  // fibers per instance: product of A's free dims
     int32_t n_inst, nk, nf, rank;   // nk <= nk_tmpl (entries nk..nk_tmpl-1 are padding)
-    int32_t nk_tmpl, pad_;
+    int32_t nk_tmpl;                // held form: compile-time summed extent
+    int32_t nf_tmpl;                // streamed form (nf_tmpl > 0): free entries per register chunk
     int64_t kA[JET_APPLY_MAXK], bK[JET_APPLY_MAXK];   // summed entry q: offset in A, in B
     int64_t cF[JET_APPLY_MAXF], bF[JET_APPLY_MAXF];   // B-free entry f: offset in C, in B
     int64_t dim[JET_MAXR], sA[JET_MAXR], sC[JET_MAXR];

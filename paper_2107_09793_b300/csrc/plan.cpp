@@ -679,8 +679,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const int64_t nk = dimprod(N.K), nf = dimprod(fs), nfib = dimprod(fl);
         int64_t nk2 = 1;   // the kernel's compile-time summed extent (power of two >= nk)
         while (nk2 < nk) nk2 *= 2;
-        return nk >= 1 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_MAXF && nk2 * nf <= JET_APPLY_MAXB &&
-               nfib >= (1 << 15) &&
+        const bool held = nk <= JET_APPLY_HOLDK && nk2 * nf <= JET_APPLY_MAXB;
+        const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF;
+        return nk >= 1 && (held || streamed) && nf <= JET_APPLY_MAXF && nfib >= (1 << 15) &&
                (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
     };
     auto emit_apply = [&](int32_t v, const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K,
@@ -701,6 +702,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         d.nf = (int32_t)nf;
         d.nk_tmpl = 1;
         while (d.nk_tmpl < d.nk) d.nk_tmpl *= 2;
+        if (!(d.nk <= JET_APPLY_HOLDK && d.nk_tmpl * d.nf <= JET_APPLY_MAXB)) {   // streamed form
+            d.nf_tmpl = 1;   // register chunk of free entries
+            while (d.nf_tmpl < d.nf && d.nf_tmpl < 16) d.nf_tmpl *= 2;
+        }
         // summed entries: mixed radix over K, the label of smallest stride in A
         // fastest; B's free entries: the label of smallest stride in C fastest
         std::vector<int64_t> Ks = K, Fs = fs;
@@ -1162,6 +1167,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         }
         // ------------------------------------------------ direct contraction
         else {
+            if (getenv("JET_DEBUG_PLAN"))
+                fprintf(stderr, "direct node %d inst %ld |A| %ld |B| %ld |C| %ld nK %ld nFa %ld nFb %ld flop %.3g\n", v,
+                        (long)N.n_inst, (long)VA.size, (long)VB.size, (long)N.view.size, (long)nK, (long)nFa, (long)nFb,
+                        flop);
             ++P.n_direct;
             emit_direct(v, VA, VB, N.view, K, a_big, N.n_inst, pa, pb, pc, flop, bytes, scratch, scratch_bytes);
         }

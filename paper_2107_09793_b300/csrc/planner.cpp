@@ -7,7 +7,9 @@
 // with shared work reused, a tree node is computed once per distinct assignment
 // of the sliced labels that occur under it, not once per slice.
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <functional>
 #include <iterator>
 #include <map>
 #include <set>
@@ -460,6 +462,209 @@ static std::vector<std::pair<int32_t, int32_t>> leaf_order_linear(const Network 
     return path;
 }
 
+// Subtree reconfiguration: for every internal node, take the sub-tree below it
+// down to a frontier of at most k tensors (splitting the largest intermediate
+// first), find the cheapest order of contracting that frontier exactly by
+// dynamic programming over its subsets, and substitute it when it lowers the
+// (instance-weighted) FLOP without creating an intermediate above max_size.
+// Repeated for a few passes over the tree.  Returns the new path.
+static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
+                                                            const std::vector<std::pair<int32_t, int32_t>> &path,
+                                                            BatchInstances *bt, int passes, int k, double max_size)
+{
+    auto fixed = fixed_set(net, {});
+    const int32_t n = (int32_t)net.leaves.size();
+    if (path.size() < 2) return path;
+    const int32_t n_nodes = n + (int32_t)path.size();
+    std::vector<std::array<int32_t, 2>> ch(n_nodes, {-1, -1});
+    std::vector<std::vector<int64_t>> lab(n_nodes);
+    std::vector<std::vector<int32_t>> opos(n_nodes);
+    for (int32_t i = 0; i < n; ++i) {
+        lab[i] = net.leaves[i].labels;
+        std::sort(lab[i].begin(), lab[i].end());
+        if (bt)
+            for (int64_t l : lab[i]) {
+                auto it = bt->digit.find(l);
+                if (it != bt->digit.end()) opos[i].push_back(it->second);
+            }
+        std::sort(opos[i].begin(), opos[i].end());
+    }
+    auto xor_sorted = [](const std::vector<int64_t> &a, const std::vector<int64_t> &b) {
+        std::vector<int64_t> out;
+        std::set_symmetric_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(out));
+        return out;
+    };
+    auto union_sorted = [](const std::vector<int64_t> &a, const std::vector<int64_t> &b) {
+        std::vector<int64_t> out;
+        std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(out));
+        return out;
+    };
+    auto set_node = [&](int32_t v, int32_t a, int32_t b) {
+        ch[v] = {a, b};
+        lab[v] = xor_sorted(lab[a], lab[b]);
+        opos[v] = merge_pos(opos[a], opos[b]);
+    };
+    for (size_t s = 0; s < path.size(); ++s) set_node(n + (int32_t)s, path[s].first, path[s].second);
+    const int32_t root = n_nodes - 1;
+    auto weight = [&](const std::vector<int32_t> &pos) { return bt ? bt->count(pos) : 1.0; };
+
+    for (int pass = 0; pass < passes; ++pass) {
+        // internal nodes, parents before children
+        std::vector<int32_t> order, st{root};
+        while (!st.empty()) {
+            const int32_t v = st.back();
+            st.pop_back();
+            if (v < n) continue;
+            order.push_back(v);
+            st.push_back(ch[v][0]);
+            st.push_back(ch[v][1]);
+        }
+        int changed = 0;
+        for (int32_t v : order) {
+            if (v < n || ch[v][0] < 0) continue;
+            // frontier: split the largest internal frontier tensor until k tensors
+            std::vector<int32_t> front{v}, internal;
+            while ((int)front.size() < k) {
+                int best_i = -1;
+                double best_s = -1;
+                for (int i = 0; i < (int)front.size(); ++i)
+                    if (front[i] >= n) {
+                        const double sz = label_size(net, lab[front[i]], fixed) * weight(opos[front[i]]);
+                        if (sz > best_s) {
+                            best_s = sz;
+                            best_i = i;
+                        }
+                    }
+                if (best_i < 0) break;
+                const int32_t x = front[best_i];
+                front.erase(front.begin() + best_i);
+                internal.push_back(x);
+                front.push_back(ch[x][0]);
+                front.push_back(ch[x][1]);
+            }
+            const int m = (int)front.size();
+            if (m < 3) continue;
+            double cur = 0;
+            for (int32_t x : internal)
+                cur += weight(opos[x]) * 8.0 * label_size(net, union_sorted(lab[ch[x][0]], lab[ch[x][1]]), fixed);
+            // subset outputs and weights
+            const int full = (1 << m) - 1;
+            std::vector<std::vector<int64_t>> outs(full + 1);
+            std::vector<double> wts(full + 1, 1.0), osz(full + 1, 1.0);
+            for (int S = 1; S <= full; ++S) {
+                const int low = __builtin_ctz(S);
+                const int rest = S & (S - 1);
+                outs[S] = rest ? xor_sorted(outs[rest], lab[front[low]]) : lab[front[low]];
+                if (bt) {
+                    std::vector<int32_t> pos;
+                    for (int i = 0; i < m; ++i)
+                        if (S >> i & 1) pos = merge_pos(pos, opos[front[i]]);
+                    wts[S] = bt->count(pos);
+                }
+                osz[S] = label_size(net, outs[S], fixed);
+            }
+            std::vector<double> best(full + 1, 0.0);
+            std::vector<int> split(full + 1, 0);
+            for (int S = 1; S <= full; ++S) {
+                if ((S & (S - 1)) == 0) continue;
+                double bc = -1;
+                int bs = 0;
+                for (int s1 = (S - 1) & S; s1; s1 = (s1 - 1) & S) {
+                    const int s2 = S ^ s1;
+                    if (s1 > s2) continue;
+                    if (S != full && osz[S] * wts[S] > max_size) continue;   // intermediate above the cap
+                    const double c = best[s1] + best[s2] +
+                                     wts[S] * 8.0 * label_size(net, union_sorted(outs[s1], outs[s2]), fixed);
+                    if (bc < 0 || c < bc) {
+                        bc = c;
+                        bs = s1;
+                    }
+                }
+                best[S] = bc < 0 ? INFINITY : bc;
+                split[S] = bs;
+            }
+            if (!(best[full] < cur * (1.0 - 1e-12))) continue;
+            // rebuild: the removed internal ids carry the new internal nodes (v stays the sub-root)
+            std::vector<int32_t> ids(internal.begin(), internal.end());
+            std::vector<int32_t> spare;
+            for (int32_t x : ids)
+                if (x != v) spare.push_back(x);
+            std::function<int32_t(int)> build = [&](int S) -> int32_t {
+                if ((S & (S - 1)) == 0) return front[__builtin_ctz(S)];
+                const int s1 = split[S], s2 = S ^ s1;
+                const int32_t a = build(s1), b = build(s2);
+                int32_t node;
+                if (S == full) {
+                    node = v;
+                } else {
+                    node = spare.back();
+                    spare.pop_back();
+                }
+                set_node(node, a, b);
+                return node;
+            };
+            build(full);
+            ++changed;
+        }
+        if (!changed) break;
+    }
+    // SSA path, children before parents
+    std::vector<std::pair<int32_t, int32_t>> out;
+    std::vector<int32_t> ssa(n_nodes, -1);
+    for (int32_t i = 0; i < n; ++i) ssa[i] = i;
+    int32_t next = n;
+    std::vector<std::pair<int32_t, int>> st{{root, 0}};
+    while (!st.empty()) {
+        auto &top = st.back();
+        const int32_t v = top.first;
+        if (v < n) {
+            st.pop_back();
+            continue;
+        }
+        if (top.second == 0) {
+            top.second = 1;
+            st.push_back({ch[v][0], 0});
+            st.push_back({ch[v][1], 0});
+        } else {
+            const int32_t a = ssa[ch[v][0]], b = ssa[ch[v][1]];
+            out.push_back({std::min(a, b), std::max(a, b)});
+            ssa[v] = next++;
+            st.pop_back();
+        }
+    }
+    return out;
+}
+
+// Weighted FLOP and largest weighted intermediate of a path (the greedy's model).
+static double weighted_flop(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
+                            BatchInstances *bt, double *peak_out)
+{
+    auto fixed = fixed_set(net, {});
+    const int32_t n = (int32_t)net.leaves.size();
+    std::vector<std::vector<int64_t>> lab(n + path.size());
+    std::vector<std::vector<int32_t>> opos(n + path.size());
+    for (int32_t i = 0; i < n; ++i) {
+        lab[i] = net.leaves[i].labels;
+        if (bt)
+            for (int64_t l : lab[i]) {
+                auto it = bt->digit.find(l);
+                if (it != bt->digit.end()) opos[i].push_back(it->second);
+            }
+        std::sort(opos[i].begin(), opos[i].end());
+    }
+    double total = 0, peak = 0;
+    for (size_t s = 0; s < path.size(); ++s) {
+        const int32_t a = path[s].first, b = path[s].second, c = n + (int32_t)s;
+        lab[c] = sym_diff(lab[a], lab[b]);
+        opos[c] = merge_pos(opos[a], opos[b]);
+        const double w = bt ? bt->count(opos[c]) : 1.0;
+        total += w * 8.0 * label_size(net, set_union(lab[a], lab[b]), fixed);
+        peak = std::max(peak, w * label_size(net, lab[c], fixed));
+    }
+    if (peak_out) *peak_out = peak;
+    return total;
+}
+
 std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_t seed, int32_t n_trials,
                                                      double *flop_out, int32_t n_amps, const int32_t *outputs,
                                                      double max_elems)
@@ -514,6 +719,20 @@ std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_
             best_flop = f;
             best_peak = pk;
             best = p;
+        }
+    }
+    // local improvement of the kept path; intermediates stay within the larger of
+    // the cap and the path's own largest one
+    {
+        double pk = 0;
+        weighted_flop(net, best, bt, &pk);
+        const double limit = std::isfinite(cap) ? std::max(cap, pk) : pk;
+        auto better_path = reconfigure(net, best, bt, 4, 8, limit);
+        double pk2 = 0;
+        const double f2 = weighted_flop(net, better_path, bt, &pk2);
+        if (f2 < best_flop && pk2 <= limit) {
+            best = better_path;
+            best_flop = f2;
         }
     }
     if (flop_out) *flop_out = best_flop;

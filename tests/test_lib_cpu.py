@@ -244,3 +244,63 @@ def test_batch_greedy_argument_errors():
     with pytest.raises(jet.JetError) as e:
         net.path_greedy_batch(np.zeros((0, 20), np.int32))
     assert e.value.code == jet.JET_EINVAL
+
+
+def _optimal_flop_brute(labels, dims, cap):
+    """Cheapest pairwise order of a few tensors, exhaustively (every binary tree), in the
+    library's model: a step costs 8 * prod(dims of the union of its operands' labels);
+    intermediates (not the final result) hold at most `cap` elements."""
+    from functools import lru_cache
+    sets = [frozenset(l) for l in labels]
+    n = len(sets)
+
+    def out(S):
+        o = frozenset()
+        for i in range(n):
+            if S >> i & 1:
+                o = o ^ sets[i]
+        return o
+
+    def size(S):
+        return int(np.prod([dims[x] for x in out(S)] or [1]))
+
+    @lru_cache(maxsize=None)
+    def best(S):
+        if S & (S - 1) == 0:
+            return 0
+        if S != (1 << n) - 1 and size(S) > cap:
+            return float("inf")
+        b = None
+        s1 = (S - 1) & S
+        while s1:
+            s2 = S ^ s1
+            if s1 < s2:
+                c = best(s1) + best(s2) + 8 * int(np.prod([dims[x] for x in (out(s1) | out(s2))] or [1]))
+                b = c if b is None or c < b else b
+            s1 = (s1 - 1) & S
+        return b
+    return best((1 << n) - 1)
+
+
+def test_planner_is_flop_optimal_on_networks_of_eight_tensors():
+    """Up to eight tensors the subtree reconfiguration covers the whole tree, so the
+    kept path must cost exactly the exhaustive optimum among the paths whose
+    intermediates stay within the kept path's largest one."""
+    rng = np.random.default_rng(5)
+    for trial in range(12):
+        n = int(rng.integers(4, 9))
+        labels = [[] for _ in range(n)]
+        nxt = 0
+        for i in range(1, n):                      # a random spanning tree keeps it connected
+            j = int(rng.integers(0, i))
+            labels[i].append(nxt); labels[j].append(nxt); nxt += 1
+        for _ in range(int(rng.integers(1, n + 2))):  # extra bonds
+            i, j = rng.choice(n, 2, replace=False)
+            labels[int(i)].append(nxt); labels[int(j)].append(nxt); nxt += 1
+        dims = {l: int(rng.choice([2, 3, 4])) for l in range(nxt)}
+        data = [np.ones([dims[l] for l in ls], np.complex64) for ls in labels]
+        net = jet.Network(labels, data)
+        net.set_open([])
+        f = net.path_greedy(seed=trial, n_trials=2)
+        cap = net.stats()["max_intermediate"]
+        assert f == _optimal_flop_brute(labels, dims, cap), trial
