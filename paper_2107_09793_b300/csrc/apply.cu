@@ -91,13 +91,13 @@ __device__ __forceinline__ void fiber_offsets(int64_t r, const ApplyArgs &a, int
     }
 }
 
-// complex64: B staged as packed pairs (br, br, bi, bi); two fibers per thread,
-// every B entry read from shared memory once feeds the packed FMAs of both.
-template <int NK, bool POW2>
+// complex64: B staged as packed pairs (br, br, bi, bi); FIB fibers per thread
+// (two up to 16 summed entries, one for 32), every B entry read from shared
+// memory once feeds the packed FMAs of all of them.
+template <int NK, int FIB, bool POW2>
 __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ ApplyArgs a)
 {
     __shared__ ulonglong2 sB[JET_APPLY_MAXB];
-    constexpr int FIB = 2;
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
     const int nf = a.nf;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB;
@@ -213,6 +213,77 @@ __global__ void __launch_bounds__(256) apply_stream_c64(const __grid_constant__ 
     }
 }
 
+// Streamed form for 4 < nf <= JET_APPLY_STREAMF: a group of four lanes shares
+// four fibers and splits the free entries, each lane keeping 4 fibers x 4
+// outputs in registers (16 free entries per pass).  Every entry of B read from
+// shared memory feeds 8 packed FMAs, and the four lanes of a group load the
+// same A addresses (one request).  Fibers of a warp: w0 + 8 i + group.
+template <bool POW2>
+__global__ void __launch_bounds__(256, 2) apply_quad_c64(const __grid_constant__ ApplyArgs a)
+{
+    __shared__ ulonglong2 sB[JET_APPLY_MAXK * JET_APPLY_STREAMF];   // [q][f], rows of nfp entries
+    const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
+    const int nk = a.nk, nf = a.nf;
+    const int nfp = (nf + 15) / 16 * 16;
+    const int lane = threadIdx.x & 31, grp = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
+    const int64_t step = (int64_t)gridDim.x * (blockDim.x / 32) * 32;
+    for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
+        const unsigned long long *__restrict__ A = (const unsigned long long *)pA[inst];
+        const float2 *__restrict__ B = (const float2 *)pB[inst];
+        unsigned long long *__restrict__ C = (unsigned long long *)pC[inst];
+        __syncthreads();
+        for (int i = threadIdx.x; i < nk * nfp; i += blockDim.x) {
+            const int q = i / nfp, f = i - q * nfp;
+            const float2 b = f < nf ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);
+            sB[i] = make_ulonglong2(pack2(b.x, b.x), pack2(b.y, b.y));
+        }
+        __syncthreads();
+        for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + warp) * 32; w0 < a.n_fib; w0 += step) {
+            int64_t oa[4], oc[4];
+            bool ok[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t r = w0 + 8 * i + grp;
+                ok[i] = r < a.n_fib;
+                fiber_offsets<POW2>(ok[i] ? r : 0, a, oa[i], oc[i]);
+            }
+            for (int f0 = 0; f0 < nf; f0 += 16) {
+                unsigned long long p[4][4], m[4][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int ff = 0; ff < 4; ++ff) p[i][ff] = m[i][ff] = 0ull;
+                const ulonglong2 *bq = sB + f0 + 4 * t;
+#pragma unroll 2
+                for (int q = 0; q < nk; ++q) {
+                    unsigned long long x[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) x[i] = ok[i] ? __ldg(A + oa[i] + a.kA[q]) : 0ull;
+#pragma unroll
+                    for (int ff = 0; ff < 4; ++ff) {
+                        const ulonglong2 b = bq[q * nfp + ff];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) cmac2(p[i][ff], m[i][ff], b, x[i]);
+                    }
+                }
+#pragma unroll
+                for (int ff = 0; ff < 4; ++ff) {
+                    const int f = f0 + 4 * t + ff;
+                    if (f < nf) {
+                        const int64_t cf = a.cF[f];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (ok[i]) {
+                                const float2 c = cfinish(p[i][ff], m[i][ff]);
+                                __stcs(C + oc[i] + cf, pack2(c.x, c.y));
+                            }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // NK: summed entries (compile time, so the fiber stays in registers); FIB:
 // fibers per thread (complex128: 1).
 template <typename V, int NK, int FIB, bool POW2>
@@ -284,13 +355,18 @@ static void launch_nk(const ApplyArgs &a, dim3 grid, bool pow2, cudaStream_t s)
 cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
     if (a.nf_tmpl > 0) {   // streamed form (complex64)
-        // nf_tmpl: free entries per register chunk
-        const bool ok = (a.nf_tmpl == 1 || a.nf_tmpl == 2 || a.nf_tmpl == 4 || a.nf_tmpl == 8 || a.nf_tmpl == 16) &&
+        // nf_tmpl: free entries per register chunk (1, 2, 4); 16: lane groups of four
+        const bool ok = (a.nf_tmpl == 1 || a.nf_tmpl == 2 || a.nf_tmpl == 4 || a.nf_tmpl == 16) &&
                         a.nf >= 1 && a.nf <= JET_APPLY_STREAMF && a.nk >= 1 && a.nk <= JET_APPLY_MAXK &&
                         a.rank <= JET_MAXR && !(c.variant & 1);
         if (!ok) return cudaErrorInvalidValue;
         dim3 grid(c.gx, c.gy, 1);
         const bool pow2 = c.variant & 4;
+        if (a.nf_tmpl == 16) {
+            if (pow2) apply_quad_c64<true><<<grid, 256, 0, s>>>(a);
+            else apply_quad_c64<false><<<grid, 256, 0, s>>>(a);
+            return cudaGetLastError();
+        }
 #define JET_ST(NF, FIB)                                                                     \
     do {                                                                                    \
         if (pow2) apply_stream_c64<NF, FIB, true><<<grid, 256, 0, s>>>(a);                   \
@@ -299,14 +375,13 @@ cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
         switch (a.nf_tmpl) {
         case 1: JET_ST(1, 2); break;
         case 2: JET_ST(2, 2); break;
-        case 4: JET_ST(4, 2); break;
-        case 8: JET_ST(8, 2); break;
-        default: JET_ST(16, 1); break;
+        default: JET_ST(4, 2); break;
         }
 #undef JET_ST
         return cudaGetLastError();
     }
-    const bool tmpl_ok = a.nk_tmpl == 1 || a.nk_tmpl == 2 || a.nk_tmpl == 4 || a.nk_tmpl == 8 || a.nk_tmpl == 16;
+    const bool tmpl_ok = a.nk_tmpl == 1 || a.nk_tmpl == 2 || a.nk_tmpl == 4 || a.nk_tmpl == 8 || a.nk_tmpl == 16 ||
+                         (a.nk_tmpl == 32 && !(c.variant & 1));
     if (!tmpl_ok || a.nk < 1 || a.nk > a.nk_tmpl || a.nk_tmpl > JET_APPLY_HOLDK || a.nf < 1 || a.nf > JET_APPLY_MAXF ||
         a.nf * a.nk_tmpl > JET_APPLY_MAXB || a.rank > JET_MAXR)
         return cudaErrorInvalidValue;
@@ -316,17 +391,18 @@ cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
         launch_nk<double2, 1>(a, grid, pow2, s);
         return cudaGetLastError();
     }
-#define JET_C64(NK)                                                                        \
+#define JET_C64(NK, FIB)                                                                   \
     do {                                                                                   \
-        if (pow2) apply_kernel_c64<NK, true><<<grid, 256, 0, s>>>(a);                       \
-        else apply_kernel_c64<NK, false><<<grid, 256, 0, s>>>(a);                           \
+        if (pow2) apply_kernel_c64<NK, FIB, true><<<grid, 256, 0, s>>>(a);                  \
+        else apply_kernel_c64<NK, FIB, false><<<grid, 256, 0, s>>>(a);                      \
     } while (0)
     switch (a.nk_tmpl) {
-    case 1: JET_C64(1); break;
-    case 2: JET_C64(2); break;
-    case 4: JET_C64(4); break;
-    case 8: JET_C64(8); break;
-    default: JET_C64(16); break;
+    case 1: JET_C64(1, 2); break;
+    case 2: JET_C64(2, 2); break;
+    case 4: JET_C64(4, 2); break;
+    case 8: JET_C64(8, 2); break;
+    case 16: JET_C64(16, 2); break;
+    default: JET_C64(32, 1); break;
     }
 #undef JET_C64
     return cudaGetLastError();

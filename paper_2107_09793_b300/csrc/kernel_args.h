@@ -10,9 +10,9 @@
 #define JET_KLOMAX 1024      // max entries of an inner-K offset table
 #define JET_SPLITK_G 8       // outputs per block in the split-K direct kernel
 #define JET_APPLY_MAXK 64    // small-operand application: max summed entries (streamed form)
-#define JET_APPLY_HOLDK 16   // ... held in registers: max summed entries
+#define JET_APPLY_HOLDK 32   // ... held in registers: max summed entries
 #define JET_APPLY_MAXF 256   // small-operand application: max free entries of the small operand
-#define JET_APPLY_MAXB 256   // held form: max entries of the small operand
+#define JET_APPLY_MAXB 1024  // held form: max entries of the small operand (summed extent padded)
 #define JET_APPLY_STREAMF 32 // streamed form: max free entries of the small operand
 
 // Pairwise contraction C = sum_K A * B evaluated directly from strides

@@ -359,7 +359,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         // its input wire and the large operand's layout is kept)
         std::vector<int64_t> ks_small, fs_small_order;
         for (int64_t l : VSmall.labels) (find_pos(N.K, l) >= 0 ? ks_small : fs_small_order).push_back(l);
-        bool pairable = !N.use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size && !ks_small.empty() &&
+        bool pairable = !N.use_gemm && VSmall.size <= 2048 && VBig.size > VSmall.size && !ks_small.empty() &&
                         ks_small.size() == fs_small_order.size();
         for (size_t j = 0; pairable && j < ks_small.size(); ++j)
             pairable = net.labels.at(ks_small[j]).dim == net.labels.at(fs_small_order[j]).dim;
@@ -368,7 +368,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 const int p = find_pos(ks_small, l);
                 out.push_back(p >= 0 ? fs_small_order[p] : l);
             }
-        } else if (!N.use_gemm && VSmall.size <= 256 && VBig.size > VSmall.size) {
+        } else if (!N.use_gemm && VSmall.size <= 2048 && VBig.size > VSmall.size) {
             // keep the big operand's order; the small operand's free labels take
             // the place of the first summed label (gate application in place)
             int ins = -1;
@@ -679,7 +679,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const int64_t nk = dimprod(N.K), nf = dimprod(fs), nfib = dimprod(fl);
         int64_t nk2 = 1;   // the kernel's compile-time summed extent (power of two >= nk)
         while (nk2 < nk) nk2 *= 2;
-        const bool held = nk <= JET_APPLY_HOLDK && nk2 * nf <= JET_APPLY_MAXB;
+        // held in registers: up to 16 summed entries (complex128 too), or 32 (complex64)
+        const bool held = nk <= (fp64 ? 16 : JET_APPLY_HOLDK) && nk2 * nf <= JET_APPLY_MAXB;
         const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF;
         return nk >= 1 && (held || streamed) && nf <= JET_APPLY_MAXF && nfib >= (1 << 15) &&
                (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
@@ -702,9 +703,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         d.nf = (int32_t)nf;
         d.nk_tmpl = 1;
         while (d.nk_tmpl < d.nk) d.nk_tmpl *= 2;
-        if (!(d.nk <= JET_APPLY_HOLDK && d.nk_tmpl * d.nf <= JET_APPLY_MAXB)) {   // streamed form
-            d.nf_tmpl = 1;   // register chunk of free entries
-            while (d.nf_tmpl < d.nf && d.nf_tmpl < 16) d.nf_tmpl *= 2;
+        if (!(d.nk <= (fp64 ? 16 : JET_APPLY_HOLDK) && d.nk_tmpl * d.nf <= JET_APPLY_MAXB)) {   // streamed form
+            d.nf_tmpl = 1;   // register chunk of free entries; above 4: lane groups (16 per pass)
+            while (d.nf_tmpl < d.nf && d.nf_tmpl < 4) d.nf_tmpl *= 2;
+            if (d.nf > 4) d.nf_tmpl = 16;
         }
         // summed entries: mixed radix over K, the label of smallest stride in A
         // fastest; B's free entries: the label of smallest stride in C fastest
@@ -743,6 +745,16 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             pow2 = pow2 && (d.dim[j] & (d.dim[j] - 1)) == 0;
         }
         d.n_inst = (int32_t)n_inst;
+        if (getenv("JET_DEBUG_PLAN")) {
+            fprintf(stderr, "apply node %d inst %ld nk %d nf %d nfib %ld | K strides in A:", v, (long)n_inst, d.nk, d.nf,
+                    (long)d.n_fib);
+            for (int64_t l : Ks) fprintf(stderr, " %ld", (long)stride(VL, l));
+            fprintf(stderr, " | fiber strides A/C:");
+            for (int j = 0; j < std::min(d.rank, 4); ++j) fprintf(stderr, " %ld/%ld", (long)d.sA[j], (long)d.sC[j]);
+            fprintf(stderr, " | F strides in C:");
+            for (int64_t l : Fs) fprintf(stderr, " %ld", (long)stride(Cv, l));
+            fprintf(stderr, "\n");
+        }
         size_t off_pl = blob.put_ptrs(a_big ? pa : pb), off_ps = blob.put_ptrs(a_big ? pb : pa);
         size_t off_pc = blob.put_ptrs(pc);
         size_t so = blob.reserve(sizeof d);
