@@ -151,20 +151,27 @@ def golden_amplitude():
         return None, None
 
 
-def oracle_slice_sample(w, sliced, n_slices, outputs):
-    """FP64 oracle (pairwise numpy.tensordot) on slice 0 only: a bounded sample."""
+def oracle_slice_sample(w, sliced, n_slices, outputs, n_sample=3):
+    """FP64 oracle (pairwise numpy.tensordot, its own greedy path) on a bounded
+    sample: the first n_sample of the 64 slices of the amplitude for the
+    rule-chosen sliced labels stored with the grid30 expected values (wire
+    labels of qubits 12..17 after their 8th single-qubit gate; any 6 labels
+    give the same amplitude as the sum of their 64 slices)."""
     import oracle
     try:
         from threadpoolctl import threadpool_info
         cores = max((i.get("num_threads", 0) for i in threadpool_info()), default=0) or len(os.sched_getaffinity(0))
     except Exception:
         cores = len(os.sched_getaffinity(0))
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "grid30.json")))
+    labels = g["sliced_labels"]
+    n_sl = 2 ** len(labels)
     t0 = time.perf_counter()
-    part = oracle.sliced_partials(w.network.as_complex64(), outputs[0], sliced, [0])
+    part = oracle.sliced_partials(w.network.as_complex64(), outputs[0], labels, list(range(n_sample)))
     dt = time.perf_counter() - t0
-    return {"value": (1.0 / n_slices) / dt, "unit": "amplitudes/s", "cores": int(cores), "kind": "oracle",
-            "sample": f"1 of {n_slices} slices of the grid30 amplitude (FP64 pairwise tensordot, own greedy path), "
-                      f"{dt:.1f} s"}, part
+    return {"value": (n_sample / n_sl) / dt, "unit": "amplitudes/s", "cores": int(cores), "kind": "oracle",
+            "sample": f"{n_sample} of the {n_sl} slices of the grid30 amplitude (FP64 pairwise tensordot, own greedy "
+                      f"path, sliced labels {labels}), {dt:.1f} s"}, part
 
 
 def _timed(fn, stream, ev0, ev1, steps):
@@ -297,17 +304,13 @@ def run_reference(args):
         return 0
     from circuits import configs
     w = configs.build("grid30")
-    from paper_2107_09793_b300 import jet  # planner only (host), to pick the same sliced labels
-    net = jet.from_network(w.network)
-    net.path_greedy(seed=PATH_SEED, n_trials=PATH_TRIALS)
-    sliced = net.slice_auto(CAP, min_n=N_SLICED, max_n=max(N_SLICED, 24))
-    n_sl = 2 ** len(sliced)
+    n_sl = 64
     steps = max(1, min(args.steps, 3))
     warm = min(args.warmup, 1)
     times = []
     base = None
-    for i in range(warm + steps):
-        b, _ = oracle_slice_sample(w, sliced, n_sl, w.outputs)
+    for i in range(warm + steps):   # a step: one of the 64 slices (oracle only, no library)
+        b, _ = oracle_slice_sample(w, None, n_sl, w.outputs, n_sample=1)
         if i >= warm:
             times.append(1.0 / b["value"] / n_sl)
         base = b
@@ -382,26 +385,49 @@ def run_impl(args):
     st = net.stats()
     recs = net.profile()
 
-    # roofline of the dominant (tensor-core GEMM) launches, timed live above
-    gl = [(i, recs[i]) for i in gemm_ms]
+    # roofline of the dominant kernel: the timed kind (GEMM, operand split,
+    # small-operand application) with the largest share of the live step; its
+    # longest launch for the GEMM (tensor bound), all its launches for the
+    # HBM-bound kinds
+    timed = {i: statistics.mean(v) for i, v in gemm_ms.items()}
+    by_kind = {}
+    for i, ms in timed.items():
+        by_kind.setdefault(recs[i]["kind"], []).append(i)
     roof = None
-    if gl:
-        tot_ms = {i: statistics.mean(v) for i, v in gemm_ms.items()}
-        big = max(gl, key=lambda x: tot_ms[x[0]])[0]
-        ms = tot_ms[big]
-        achieved = recs[big]["flop"] / (ms * 1e-3) / 1e12
-        tc = args.precision not in ("fp32", "fp64")
-        issue = {"bf16x3": 3, "tf32x3": 3, "bf16x6": 6, "fp16x3": 3, "tf32": 1}.get(args.precision, 1)
-        peak = peaks["bf16_tflops_sustained"] * (0.5 if args.precision.startswith("tf32") else 1.0)
-        kname = f"tc_gemm_kernel<{args.precision}>" if args.precision not in ("fp32", "fp64") else "gemm_simt_kernel"
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["flop"])),
-                "kernel": kname,
-                "per_launch_ms": ms, "flop_per_launch": recs[big]["flop"],
-                "issued_tensor_tflops": achieved * issue if tc else None,
-                "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)"
-                                                                         if args.precision.startswith("tf32") else ""),
-                "gemm_share_of_step": sum(tot_ms.values()) / (sum(step_ms) / len(step_ms))}
+    if by_kind:
+        mean_step_ms = sum(step_ms) / len(step_ms)
+        dom = max(by_kind, key=lambda k: sum(timed[i] for i in by_kind[k]))
+        ids = by_kind[dom]
+        share = sum(timed[i] for i in ids) / mean_step_ms
+        if dom in ("gemm_tc", "gemm_simt"):
+            big = max(ids, key=lambda i: timed[i])
+            ms = timed[big]
+            achieved = recs[big]["flop"] / (ms * 1e-3) / 1e12
+            tc = dom == "gemm_tc"
+            issue = {"bf16x3": 3, "tf32x3": 3, "bf16x6": 6, "fp16x3": 3, "tf32": 1}.get(args.precision, 1)
+            peak = peaks["bf16_tflops_sustained"] * (0.5 if args.precision.startswith("tf32") else 1.0)
+            kname = f"tc_gemm_kernel<{args.precision}>" if tc else "gemm_simt_kernel"
+            roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["flop"])), "kernel": kname,
+                    "per_launch_ms": ms, "flop_per_launch": recs[big]["flop"],
+                    "issued_tensor_tflops": achieved * issue if tc else None,
+                    "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)"
+                                                                             if args.precision.startswith("tf32") else ""),
+                    "share_of_step": share}
+        else:
+            kname = {"apply": "apply_kernel_c64", "tc_split": f"tc_split_kernel<{args.precision}>"}[dom]
+            nbytes = sum(recs[i]["bytes"] for i in ids)
+            ms = sum(timed[i] for i in ids)
+            big = max(ids, key=lambda i: timed[i])
+            achieved = nbytes / (ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "kernel": kname,
+                    "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["bytes"])),
+                    "traffic_launch": {"node": recs[big]["node"], "bytes": recs[big]["bytes"],
+                                       "ms": timed[big], "gb_s": recs[big]["bytes"] / (timed[big] * 1e-3) / 1e9},
+                    "launches_per_step": len(ids), "bytes_per_step": nbytes, "ms_per_step": ms,
+                    "peak_source": f"hbm_gbs of {peak_src}", "share_of_step": share}
+        roof["kinds_timed_ms"] = {k: sum(timed[i] for i in v) for k, v in by_kind.items()}
 
     # where the step's time goes: one extra profiled step with every launch timed
     breakdown = {}

@@ -75,8 +75,9 @@ typedef struct {
     int64_t gemm_min_k;       /* contractions with a summed extent >= this (and both free
                                  extents >= 64) take the GEMM route; default 16           */
     int64_t workspace_limit;  /* bytes of device workspace the plan may use; 0 = none    */
-    int32_t profile;          /* 0 (default): off; 1: CUDA events around every GEMM-route
-                                 launch; 2: around every launch (read with jet_profile)  */
+    int32_t profile;          /* 0 (default): off; 1: CUDA events around every GEMM, operand
+                                 split and small-operand launch; 2: around every launch
+                                 (read with jet_profile)                                  */
     int32_t pad_;
 } jet_options;
 

@@ -362,7 +362,8 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
             P.ev_end.assign(P.ops.size(), nullptr);
             for (size_t i = 0; i < P.ops.size(); ++i) {
                 OpKind k = P.ops[i].kind;
-                bool want = net.opt.profile >= 2 || k == OpKind::GemmTc || k == OpKind::GemmSimt;
+                bool want = net.opt.profile >= 2 || k == OpKind::GemmTc || k == OpKind::GemmSimt ||
+                            k == OpKind::Apply || k == OpKind::TcSplit;
                 if (!want) continue;
                 cudaEvent_t a, b;
                 JET_CUDA(cudaEventCreate(&a));
