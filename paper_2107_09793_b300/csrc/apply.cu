@@ -97,7 +97,9 @@ __device__ __forceinline__ void fiber_offsets(int64_t r, const ApplyArgs &a, int
 template <int NK, int FIB, bool POW2>
 __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ ApplyArgs a)
 {
-    __shared__ ulonglong2 sB[JET_APPLY_MAXB];
+    // B as plain complex values, read two summed entries per 16-byte load; the
+    // packed pairs (br, br), (bi, bi) are formed in registers
+    __shared__ __align__(16) float2 sB[JET_APPLY_MAXB];
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
     const int nf = a.nf;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB;
@@ -108,8 +110,7 @@ __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ 
         __syncthreads();   // the previous instance's readers of sB are done
         for (int i = threadIdx.x; i < nf * NK; i += blockDim.x) {
             const int f = i / NK, q = i - f * NK;
-            const float2 b = q < a.nk ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);   // padding is zero
-            sB[i] = make_ulonglong2(pack2(b.x, b.x), pack2(b.y, b.y));
+            sB[i] = q < a.nk ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);   // padding is zero
         }
         __syncthreads();
         for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x * FIB + threadIdx.x; r0 < a.n_fib; r0 += step) {
@@ -128,11 +129,24 @@ __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ 
                 unsigned long long p[FIB], m[FIB];
 #pragma unroll
                 for (int u = 0; u < FIB; ++u) p[u] = m[u] = 0ull;
+                if (NK == 1) {
+                    const float2 v = sB[f];
+                    const ulonglong2 b = make_ulonglong2(pack2(v.x, v.x), pack2(v.y, v.y));
 #pragma unroll
-                for (int q = 0; q < NK; ++q) {
-                    const ulonglong2 b = sB[f * NK + q];
+                    for (int u = 0; u < FIB; ++u) cmac2(p[u], m[u], b, x[u][0]);
+                } else {
+                    const float4 *row = (const float4 *)(sB + f * NK);
 #pragma unroll
-                    for (int u = 0; u < FIB; ++u) cmac2(p[u], m[u], b, x[u][q]);
+                    for (int q = 0; q < NK; q += 2) {
+                        const float4 v = row[q / 2];
+                        const ulonglong2 b0 = make_ulonglong2(pack2(v.x, v.x), pack2(v.y, v.y));
+                        const ulonglong2 b1 = make_ulonglong2(pack2(v.z, v.z), pack2(v.w, v.w));
+#pragma unroll
+                        for (int u = 0; u < FIB; ++u) {
+                            cmac2(p[u], m[u], b0, x[u][q]);
+                            cmac2(p[u], m[u], b1, x[u][q + 1]);
+                        }
+                    }
                 }
                 const int64_t cf = a.cF[f];
 #pragma unroll
