@@ -111,7 +111,8 @@ typedef struct {
                                  4 slice reduction, 5 split-K reduction, 6 operand split,
                                  7 batched small contractions of one tree level,
                                  8 adjoint accumulation, 9 memset, 10 small operand
-                                 applied to a large one                                  */
+                                 applied to a large one, 11 batched adjoint
+                                 accumulations of one tree level                          */
     int32_t node;             /* tree node (SSA id) the launch belongs to               */
     int64_t n_inst;           /* instances the launch processes                         */
     double  flop;             /* algorithmic real FLOP of the launch                    */

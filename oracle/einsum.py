@@ -180,3 +180,150 @@ def network_flops(labels, dims: Dict[int, int], path) -> int:
         live[nxt] = [x for x in la if x not in lb] + [x for x in lb if x not in la]
         nxt += 1
     return total
+
+
+def _tree_flop(children, labels_of, dims, node):
+    """FLOP of the internal steps under `node` (8 per complex multiply-add)."""
+    total, stack = 0, [node]
+    while stack:
+        v = stack.pop()
+        if v in children:
+            a, b = children[v]
+            u = set(labels_of[a]) | set(labels_of[b])
+            total += 8 * _size(u, dims)
+            stack += [a, b]
+    return total
+
+
+def improve_path(labels, dims: Dict[int, int], path, k: int = 8, passes: int = 4, cap=None):
+    """Local re-optimisation of a pairwise path (Section 2.3: any order gives the
+    same result, only the cost differs).  For every internal node, the sub-tree
+    below it is opened down to at most k tensors (splitting the largest first)
+    and their cheapest contraction order is found by exhaustive dynamic
+    programming over subsets; it replaces the old sub-tree when it costs fewer
+    FLOP and creates no intermediate above `cap` (default: the path's largest).
+    Returns a new SSA path over the same tensors."""
+    n = len(labels)
+    labels_of = {i: frozenset(l) for i, l in enumerate(labels)}
+    children = {}
+    for s, (a, b) in enumerate(path):
+        children[n + s] = (a, b)
+        labels_of[n + s] = labels_of[a] ^ labels_of[b]
+    root = n + len(path) - 1
+    if cap is None:
+        cap = max(_size(labels_of[v], dims) for v in children)
+    fresh = [root + 1]
+    for _ in range(passes):
+        changed = False
+        order, stack = [], [root]
+        while stack:
+            v = stack.pop()
+            if v in children:
+                order.append(v)
+                stack += list(children[v])
+        for v in order:
+            if v not in children:
+                continue
+            front, inner = [v], []
+            while len(front) < k:
+                cand = [x for x in front if x in children]
+                if not cand:
+                    break
+                x = max(cand, key=lambda y: _size(labels_of[y], dims))
+                front.remove(x)
+                inner.append(x)
+                front += list(children[x])
+            m = len(front)
+            if m < 3:
+                continue
+            current = sum(8 * _size(labels_of[children[x][0]] | labels_of[children[x][1]], dims) for x in inner)
+            outs = {}
+            for S in range(1, 1 << m):
+                o = frozenset()
+                for i in range(m):
+                    if S >> i & 1:
+                        o = o ^ labels_of[front[i]]
+                outs[S] = o
+            full = (1 << m) - 1
+            best = {1 << i: (0, None) for i in range(m)}
+            for S in range(1, full + 1):
+                if S & (S - 1) == 0:
+                    continue
+                if S != full and _size(outs[S], dims) > cap:
+                    best[S] = (float("inf"), None)
+                    continue
+                choice = (float("inf"), None)
+                s1 = (S - 1) & S
+                while s1:
+                    s2 = S ^ s1
+                    if s1 < s2:
+                        c = best[s1][0] + best[s2][0] + 8 * _size(outs[s1] | outs[s2], dims)
+                        if c < choice[0]:
+                            choice = (c, (s1, s2))
+                    s1 = (s1 - 1) & S
+                best[S] = choice
+            if best[full][0] < current:
+                for x in inner:
+                    if x != v:
+                        del children[x]
+
+                def build(S):
+                    if S & (S - 1) == 0:
+                        return front[S.bit_length() - 1]
+                    s1, s2 = best[S][1]
+                    a, b = build(s1), build(s2)
+                    node = v if S == full else fresh[0]
+                    if S != full:
+                        fresh[0] += 1
+                    children[node] = (a, b)
+                    labels_of[node] = labels_of[a] ^ labels_of[b]
+                    return node
+                build(full)
+                changed = True
+        if not changed:
+            break
+    out, ssa, nxt = [], {i: i for i in range(n)}, [n]
+
+    def emit(v):
+        if v < n:
+            return v
+        a, b = emit(children[v][0]), emit(children[v][1])
+        out.append((min(a, b), max(a, b)))
+        ssa[v] = nxt[0]
+        nxt[0] += 1
+        return ssa[v]
+    emit(root)
+    return out
+
+
+def slice_until(labels, dims: Dict[int, int], path, cap: int, max_n: int = 64):
+    """Choose labels to slice (Section 2.4) along a fixed path until no
+    intermediate exceeds `cap` elements: each time, among the labels of the
+    largest intermediate, the one whose slicing gives the smallest total FLOP
+    over all slices.  Returns the list of sliced labels."""
+    sliced = []
+    while True:
+        d = {x: (1 if x in sliced else s) for x, s in dims.items()}
+        n = len(labels)
+        live = {i: list(l) for i, l in enumerate(labels)}
+        biggest, where = 0, None
+        for s, (a, b) in enumerate(path):
+            out = [x for x in live[a] if x not in live[b]] + [x for x in live[b] if x not in live[a]]
+            live[n + s] = out
+            sz = _size(out, d)
+            if sz > biggest:
+                biggest, where = sz, out
+        if biggest <= cap:
+            return sliced
+        if len(sliced) >= max_n:
+            raise ValueError("slice_until: cap not reached")
+        best = None
+        for x in where:
+            if d[x] == 1:
+                continue
+            d2 = dict(d)
+            d2[x] = 1
+            total = network_flops(labels, d2, path) * int(np.prod([dims[y] for y in sliced + [x]]))
+            if best is None or total < best[0]:
+                best = (total, x)
+        sliced.append(best[1])

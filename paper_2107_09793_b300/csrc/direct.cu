@@ -250,6 +250,59 @@ __global__ void __launch_bounds__(256) accum_kernel(const __grid_constant__ Accu
     }
 }
 
+// One element of an accumulation: target t, source element e (dense source layout).
+template <typename VS, typename VT>
+__device__ __forceinline__ void accum_one(const AccumArgs &a, int64_t idx)
+{
+    const int32_t *ptr = (const int32_t *)a.csr_ptr, *src = (const int32_t *)a.csr_src;
+    const uint64_t *tgt = (const uint64_t *)a.tgt;
+    const VS *S = (const VS *)a.src;
+    const int64_t t = idx / a.n, e = idx - t * a.n;
+    int64_t r = e, off = 0;
+    for (int j = 0; j < a.rank; ++j) {
+        const int64_t q = r / a.dim[j];
+        off += (r - q * a.dim[j]) * a.tstride[j];
+        r = q;
+    }
+    VT acc = vzero<VT>();
+    for (int p = ptr[t]; p < ptr[t + 1]; ++p) {
+        const VS v = S[(int64_t)src[p] * a.n + e];
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    VT *d = (VT *)tgt[t] + off;
+    VT cur = *d;
+    cur.x += acc.x;
+    cur.y += acc.y;
+    *d = cur;
+}
+
+__global__ void __launch_bounds__(256) accum_batch_kernel(const __grid_constant__ AccumBatchArgs b)
+{
+    const AccumTask *T = (const AccumTask *)b.tasks;
+    int lo = 0, hi = b.n_tasks - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T[mid].block0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const AccumArgs &a = T[lo].a;
+    const int nb = (lo + 1 < b.n_tasks ? T[lo + 1].block0 : b.n_blocks) - T[lo].block0;
+    const int64_t total = (int64_t)a.n_tgt * a.n;
+    for (int64_t i = (int64_t)(blockIdx.x - T[lo].block0) * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)nb * blockDim.x) {
+        if (a.src_fp64 && a.tgt_fp64) accum_one<double2, double2>(a, i);
+        else if (a.tgt_fp64) accum_one<float2, double2>(a, i);
+        else accum_one<float2, float2>(a, i);
+    }
+}
+
+cudaError_t launch_accum_batch(const AccumBatchArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    accum_batch_kernel<<<c.gx, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_accum(const AccumArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
     if (a.src_fp64 && a.tgt_fp64) accum_kernel<double2, double2><<<c.gx, 256, 0, s>>>(a);

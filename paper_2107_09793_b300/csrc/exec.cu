@@ -222,6 +222,12 @@ static void launch_op(const Plan &P, const std::vector<uint8_t> &args, const Op 
         e = launch_accum(a, c, s);
         break;
     }
+    case OpKind::AccumBatch: {
+        AccumBatchArgs a;
+        std::memcpy(&a, p, sizeof a);
+        e = launch_accum_batch(a, c, s);
+        break;
+    }
     case OpKind::Memset: {
         MemsetArgs a;
         std::memcpy(&a, p, sizeof a);

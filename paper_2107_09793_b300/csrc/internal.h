@@ -53,7 +53,7 @@ struct PathCost {
 };
 
 // -------------------------------------------------------------- plan / ops
-enum class OpKind : int32_t { Direct = 0, Permute = 1, GemmSimt = 2, GemmTc = 3, Reduce = 4, SplitKReduce = 5, TcSplit = 6, SmallBatch = 7, Accum = 8, Memset = 9, Apply = 10 };
+enum class OpKind : int32_t { Direct = 0, Permute = 1, GemmSimt = 2, GemmTc = 3, Reduce = 4, SplitKReduce = 5, TcSplit = 6, SmallBatch = 7, Accum = 8, Memset = 9, Apply = 10, AccumBatch = 11 };
 
 struct Op {
     OpKind kind;

@@ -108,6 +108,17 @@ struct AccumArgs {
     int64_t tstride[JET_MAXR];      // matching target strides
 };
 
+// Several adjoint accumulations of one tree level in one launch: task t owns
+// blocks [block0_t, block0_{t+1}); each task is an AccumArgs.
+struct AccumTask {
+    AccumArgs a;
+    int32_t block0, pad_[3];
+};
+struct AccumBatchArgs {
+    uint64_t tasks;                 // device AccumTask[n_tasks], ordered by block0
+    int32_t n_tasks, n_blocks;
+};
+
 // cudaMemsetAsync(ptr, 0, bytes) as a plan step.
 struct MemsetArgs {
     uint64_t ptr;

@@ -22,6 +22,7 @@ cudaError_t launch_splitk_reduce(const SplitKReduceArgs &a, const LaunchCfg &c, 
 cudaError_t launch_slice_reduce(const ReduceArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_small_batch(const SmallBatchArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_accum(const AccumArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t launch_accum_batch(const AccumBatchArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_permute(const PermuteArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_gemm_simt(const GemmArgs &a, const LaunchCfg &c, cudaStream_t s);

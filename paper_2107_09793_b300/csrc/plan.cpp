@@ -470,7 +470,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         blob.patch_field(so, offsetof(SmallBatchArgs, tasks), BASE_BLOB, (int64_t)o_tasks);
         Op op;
         op.kind = OpKind::SmallBatch;
-        op.node = batch_nodes.front();
+        op.node = batch_nodes.empty() ? -1 : batch_nodes.front();
         op.n_inst = (int64_t)batch.size();
         op.args_off = so;
         op.args_bytes = sizeof sb;
@@ -484,6 +484,66 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         batch_nodes.clear();
         batch_patches.clear();
         batch_flop = batch_bytes = 0;
+    };
+
+    // A small contraction C (dense layout Cv) = sum over K of A (view VA) * B
+    // (view VB) as one task of the current level batch: full offset tables.
+    auto add_small_task = [&](const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K, bool a_big,
+                              const std::vector<std::pair<int32_t, int64_t>> &pa,
+                              const std::vector<std::pair<int32_t, int64_t>> &pb,
+                              const std::vector<std::pair<int32_t, int64_t>> &pc, int64_t n_inst) {
+        auto strideOf = [&](const View &V, int64_t l) {
+            int p = find_pos(V.labels, l);
+            return p < 0 ? (int64_t)0 : V.strides[p];
+        };
+        const auto &C = Cv;
+        const int64_t nK = dimprod(K);
+        std::vector<int32_t> oA(C.size), oB(C.size), kA(nK), kB(nK);
+        for (int64_t o = 0; o < C.size; ++o) {
+            int64_t r = o, x = 0, y = 0;
+            for (int j = (int)C.labels.size() - 1; j >= 0; --j) {
+                int64_t dg = r % C.dims[j];
+                r /= C.dims[j];
+                x += dg * strideOf(VA, C.labels[j]);
+                y += dg * strideOf(VB, C.labels[j]);
+            }
+            oA[o] = (int32_t)x;
+            oB[o] = (int32_t)y;
+        }
+        // summed labels in the direct kernel's order (slowest first by stride in the
+        // larger operand), so both kernels add the terms in the same sequence
+        const View &VX = a_big ? VA : VB;
+        std::vector<int64_t> Ks = K;
+        std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) { return strideOf(VX, x) > strideOf(VX, y); });
+        std::vector<int64_t> Kd;
+        for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
+        for (int64_t q = 0; q < nK; ++q) {
+            int64_t r = q, x = 0, y = 0;
+            for (int j = (int)Ks.size() - 1; j >= 0; --j) {
+                int64_t dg = r % Kd[j];
+                r /= Kd[j];
+                x += dg * strideOf(VA, Ks[j]);
+                y += dg * strideOf(VB, Ks[j]);
+            }
+            kA[q] = (int32_t)x;
+            kB[q] = (int32_t)y;
+        }
+        SmallTask t;
+        std::memset(&t, 0, sizeof t);
+        t.n_out = (int32_t)C.size;
+        t.n_k = (int32_t)nK;
+        t.n_inst = (int32_t)n_inst;
+        const size_t i0 = batch.size() * sizeof(SmallTask);
+        size_t o_pa = blob.put_ptrs(pa), o_pb = blob.put_ptrs(pb), o_pc = blob.put_ptrs(pc);
+        size_t o_oa = blob.put_i32(oA), o_ob = blob.put_i32(oB), o_ka = blob.put_i32(kA), o_kb = blob.put_i32(kB);
+        batch_patches.push_back({i0 + offsetof(SmallTask, ptrA), BASE_BLOB, (int64_t)o_pa});
+        batch_patches.push_back({i0 + offsetof(SmallTask, ptrB), BASE_BLOB, (int64_t)o_pb});
+        batch_patches.push_back({i0 + offsetof(SmallTask, ptrC), BASE_BLOB, (int64_t)o_pc});
+        batch_patches.push_back({i0 + offsetof(SmallTask, offA), BASE_BLOB, (int64_t)o_oa});
+        batch_patches.push_back({i0 + offsetof(SmallTask, offB), BASE_BLOB, (int64_t)o_ob});
+        batch_patches.push_back({i0 + offsetof(SmallTask, kA), BASE_BLOB, (int64_t)o_ka});
+        batch_patches.push_back({i0 + offsetof(SmallTask, kB), BASE_BLOB, (int64_t)o_kb});
+        batch.push_back(t);
     };
 
     // Direct strided contraction of every instance: C (dense, layout Cv) = sum over
@@ -673,10 +733,17 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     // Small-operand application route: the small operand holds at most
     // JET_APPLY_MAXK summed and JET_APPLY_MAXF free entries (at most
     // JET_APPLY_MAXB in all) and the large one has enough fibers to fill the GPU.
-    auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
-        const View &VS = N.a_big ? VB : VA, &VL = N.a_big ? VA : VB;
-        const std::vector<int64_t> &fs = N.a_big ? N.fb : N.fa, &fl = N.a_big ? N.fa : N.fb;
-        const int64_t nk = dimprod(N.K), nf = dimprod(fs), nfib = dimprod(fl);
+    // free labels of a view: those not summed
+    auto free_of = [&](const View &V, const std::vector<int64_t> &K) {
+        std::vector<int64_t> f;
+        for (int64_t l : V.labels)
+            if (find_pos(K, l) < 0) f.push_back(l);
+        return f;
+    };
+    auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big) {
+        const View &VS = a_big ? VB : VA, &VL = a_big ? VA : VB;
+        const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
+        const int64_t nk = dimprod(K), nf = dimprod(fs), nfib = dimprod(fl);
         int64_t nk2 = 1;   // the kernel's compile-time summed extent (power of two >= nk)
         while (nk2 < nk) nk2 *= 2;
         // held in registers: up to 16 summed entries (complex128 too), or 32 (complex64)
@@ -685,13 +752,15 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         return nk >= 1 && (held || streamed) && nf <= JET_APPLY_MAXF && nfib >= (1 << 15) &&
                (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
     };
+    auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
+        return apply_ok_views(VA, VB, N.K, N.a_big);
+    };
     auto emit_apply = [&](int32_t v, const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K,
                           bool a_big, int64_t n_inst, const std::vector<std::pair<int32_t, int64_t>> &pa,
                           const std::vector<std::pair<int32_t, int64_t>> &pb,
                           const std::vector<std::pair<int32_t, int64_t>> &pc, double flop, double bytes) {
         const View &VL = a_big ? VA : VB, &VS = a_big ? VB : VA;
-        const NodeInfo &N = node[v];
-        const std::vector<int64_t> &fs = a_big ? N.fb : N.fa, &fl = a_big ? N.fa : N.fb;
+        const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
         auto stride = [&](const View &V, int64_t l) {
             const int p = find_pos(V.labels, l);
             return p < 0 ? (int64_t)0 : V.strides[p];
@@ -814,61 +883,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         P.n_instances += N.n_inst;
 
         if (N.small) {
-            // full offset tables: out -> (offA, offB), summed -> (kA, kB)
             ++P.n_direct;
-            auto strideOf = [&](const View &V, int64_t l) {
-                int p = find_pos(V.labels, l);
-                return p < 0 ? (int64_t)0 : V.strides[p];
-            };
-            const auto &C = N.view;
-            std::vector<int32_t> oA(C.size), oB(C.size), kA(nK), kB(nK);
-            for (int64_t o = 0; o < C.size; ++o) {
-                int64_t r = o, x = 0, y = 0;
-                for (int j = (int)C.labels.size() - 1; j >= 0; --j) {
-                    int64_t dg = r % C.dims[j];
-                    r /= C.dims[j];
-                    x += dg * strideOf(VA, C.labels[j]);
-                    y += dg * strideOf(VB, C.labels[j]);
-                }
-                oA[o] = (int32_t)x;
-                oB[o] = (int32_t)y;
-            }
-            // summed labels in the direct kernel's order (slowest first by stride in the
-            // larger operand), so both kernels add the terms in the same sequence
-            const View &VX = a_big ? VA : VB;
-            std::vector<int64_t> Ks = K;
-            std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) {
-                return strideOf(VX, x) > strideOf(VX, y);
-            });
-            std::vector<int64_t> Kd;
-            for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
-            for (int64_t q = 0; q < nK; ++q) {
-                int64_t r = q, x = 0, y = 0;
-                for (int j = (int)Ks.size() - 1; j >= 0; --j) {
-                    int64_t dg = r % Kd[j];
-                    r /= Kd[j];
-                    x += dg * strideOf(VA, Ks[j]);
-                    y += dg * strideOf(VB, Ks[j]);
-                }
-                kA[q] = (int32_t)x;
-                kB[q] = (int32_t)y;
-            }
-            SmallTask t;
-            std::memset(&t, 0, sizeof t);
-            t.n_out = (int32_t)C.size;
-            t.n_k = (int32_t)nK;
-            t.n_inst = (int32_t)N.n_inst;
-            const size_t i0 = batch.size() * sizeof(SmallTask);
-            size_t o_pa = blob.put_ptrs(pa), o_pb = blob.put_ptrs(pb), o_pc = blob.put_ptrs(pc);
-            size_t o_oa = blob.put_i32(oA), o_ob = blob.put_i32(oB), o_ka = blob.put_i32(kA), o_kb = blob.put_i32(kB);
-            batch_patches.push_back({i0 + offsetof(SmallTask, ptrA), BASE_BLOB, (int64_t)o_pa});
-            batch_patches.push_back({i0 + offsetof(SmallTask, ptrB), BASE_BLOB, (int64_t)o_pb});
-            batch_patches.push_back({i0 + offsetof(SmallTask, ptrC), BASE_BLOB, (int64_t)o_pc});
-            batch_patches.push_back({i0 + offsetof(SmallTask, offA), BASE_BLOB, (int64_t)o_oa});
-            batch_patches.push_back({i0 + offsetof(SmallTask, offB), BASE_BLOB, (int64_t)o_ob});
-            batch_patches.push_back({i0 + offsetof(SmallTask, kA), BASE_BLOB, (int64_t)o_ka});
-            batch_patches.push_back({i0 + offsetof(SmallTask, kB), BASE_BLOB, (int64_t)o_kb});
-            batch.push_back(t);
+            add_small_task(VA, VB, N.view, K, a_big, pa, pb, pc, N.n_inst);
             batch_nodes.push_back(v);
             batch_flop += flop;
             batch_bytes += bytes;
@@ -1247,91 +1263,161 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             op.args_bytes = sizeof m;
             P.ops.push_back(op);
         };
-        for (int32_t v : order)
-            if (need[v] && v != rootv) {
-                const size_t nb = (size_t)node[v].n_inst * node[v].view.size * es;
-                const size_t off = arena.alloc(nb);
-                env_base[v] = {BASE_ARENA, (int64_t)off};
-                emit_memset(off, nb);
+        // every environment in one block of the arena, cleared by one memset
+        {
+            std::vector<size_t> local(n_nodes, 0);
+            size_t total = 0;
+            for (int32_t v : order)
+                if (need[v] && v != rootv) {
+                    local[v] = total;
+                    total += ((size_t)node[v].n_inst * node[v].view.size * es + 255) / 256 * 256;
+                }
+            if (total) {
+                const size_t blk = arena.alloc(total);
+                for (int32_t v : order)
+                    if (need[v] && v != rootv) env_base[v] = {BASE_ARENA, (int64_t)(blk + local[v])};
+                emit_memset(blk, total);
             }
-        for (auto it = order.rbegin(); it != order.rend(); ++it) {
-            const int32_t v = *it;
-            if (!need[v]) continue;
-            const NodeInfo &N = node[v];
-            for (int side = 0; side < 2; ++side) {
-                const int32_t c = side == 0 ? N.a : N.b, o = side == 0 ? N.b : N.a;
-                if (!need[c]) continue;
-                const std::vector<int32_t> &ic = side == 0 ? N.ia : N.ib, &io = side == 0 ? N.ib : N.ia;
-                const NodeInfo &NC = node[c], &NO = node[o];
-                const View Tv = dense_view(NC.view.labels, net);
-                std::vector<int64_t> Kb;   // summed: labels of C that come from the other child
-                for (int64_t l : N.view.labels)
-                    if (find_pos(NO.view.labels, l) >= 0) Kb.push_back(l);
-                const size_t tbytes = (size_t)N.n_inst * Tv.size * es;
-                const size_t toff = arena.alloc(tbytes);
-                std::vector<std::pair<int32_t, int64_t>> pe, po, pt;
-                for (int64_t i = 0; i < N.n_inst; ++i) {
-                    pe.push_back({env_base[v].first, env_base[v].second + i * N.view.size * es});
-                    po.push_back(base_ref(o, io[i]));
-                    pt.push_back({BASE_ARENA, (int64_t)toff + i * Tv.size * es});
+        }
+        // sweep one tree level at a time, deepest first: a level's environment
+        // contractions (the small ones batched into one launch), then all of its
+        // accumulations into the children's environments in one launch
+        std::vector<int32_t> rev(order.rbegin(), order.rend());
+        for (size_t i0 = 0; i0 < rev.size();) {
+            size_t i1 = i0;
+            while (i1 < rev.size() && node[rev[i1]].depth == node[rev[i0]].depth) ++i1;
+            std::vector<AccumTask> atasks;
+            std::vector<Plan::Patch> apatches;   // offsets relative to the task array
+            std::vector<std::pair<size_t, size_t>> tbufs;
+            int32_t ablocks = 0;
+            double abytes = 0;
+            for (size_t ii = i0; ii < i1; ++ii) {
+                const int32_t v = rev[ii];
+                if (!need[v]) continue;
+                const NodeInfo &N = node[v];
+                for (int side = 0; side < 2; ++side) {
+                    const int32_t c = side == 0 ? N.a : N.b, o = side == 0 ? N.b : N.a;
+                    if (!need[c]) continue;
+                    const std::vector<int32_t> &ic = side == 0 ? N.ia : N.ib, &io = side == 0 ? N.ib : N.ia;
+                    const NodeInfo &NC = node[c], &NO = node[o];
+                    const View Tv = dense_view(NC.view.labels, net);
+                    std::vector<int64_t> Kb;   // summed: labels of C that come from the other child
+                    for (int64_t l : N.view.labels)
+                        if (find_pos(NO.view.labels, l) >= 0) Kb.push_back(l);
+                    const bool leaf = c < n_leaves;
+                    // an internal child whose every instance gets exactly one contribution
+                    // takes it directly in its (zeroed, dense) environment: no accumulation
+                    bool direct_env = !leaf && NC.n_inst == N.n_inst;
+                    if (direct_env) {
+                        std::vector<int32_t> cnt(NC.n_inst, 0);
+                        for (int64_t i = 0; i < N.n_inst; ++i) direct_env = direct_env && ++cnt[ic[i]] == 1;
+                    }
+                    size_t toff = 0, tbytes = 0;
+                    if (!direct_env) {
+                        tbytes = (size_t)N.n_inst * Tv.size * es;
+                        toff = arena.alloc(tbytes);
+                        tbufs.push_back({toff, tbytes});
+                    }
+                    std::vector<std::pair<int32_t, int64_t>> pe, po, pt;
+                    for (int64_t i = 0; i < N.n_inst; ++i) {
+                        pe.push_back({env_base[v].first, env_base[v].second + i * N.view.size * es});
+                        po.push_back(base_ref(o, io[i]));
+                        if (direct_env)
+                            pt.push_back({env_base[c].first, env_base[c].second + (int64_t)ic[i] * NC.view.size * es});
+                        else
+                            pt.push_back({BASE_ARENA, (int64_t)toff + i * Tv.size * es});
+                    }
+                    std::vector<int64_t> un = N.view.labels;
+                    for (int64_t l : NO.view.labels)
+                        if (find_pos(un, l) < 0) un.push_back(l);
+                    const double flop = 8.0 * (double)dimprod(un) * (double)N.n_inst;
+                    const double bytes = (double)es * (double)N.n_inst * (double)(N.view.size + NO.view.size + Tv.size);
+                    const int64_t nKb = dimprod(Kb);
+                    const bool small = Tv.size <= 4096 && nKb <= 2048 &&
+                                       (double)N.n_inst * (double)Tv.size * (double)nKb <= (double)(1 << 24) &&
+                                       N.view.size <= INT32_MAX && NO.view.size <= INT32_MAX;
+                    if (small) {
+                        add_small_task(N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, pe, po, pt, N.n_inst);
+                        batch_flop += flop;
+                        batch_bytes += bytes;
+                    } else if (apply_ok_views(N.view, NO.view, Kb, N.view.size >= NO.view.size)) {
+                        emit_apply(v, N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, N.n_inst, pe, po, pt, flop,
+                                   bytes);
+                    } else {
+                        std::vector<size_t> scr, scrb;
+                        emit_direct(v, N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, N.n_inst, pe, po, pt,
+                                    flop, bytes, scr, scrb);
+                        for (size_t q = 0; q < scr.size(); ++q) arena.release(scr[q], scrb[q]);
+                    }
+                    P.flop_executed += flop;
+                    if (direct_env) continue;
+                    // the accumulation of these contributions into env(c)
+                    AccumTask at;
+                    std::memset(&at, 0, sizeof at);
+                    AccumArgs &ac = at.a;
+                    ac.n = Tv.size;
+                    ac.n_tgt = (int32_t)NC.n_inst;
+                    ac.rank = (int32_t)Tv.labels.size();
+                    ac.src_fp64 = fp64 ? 1 : 0;
+                    ac.tgt_fp64 = (leaf || fp64) ? 1 : 0;
+                    if (ac.rank > JET_MAXR) fail(JET_EINVAL, "environment rank too large");
+                    for (int j = 0; j < ac.rank; ++j) {
+                        const size_t li = Tv.labels.size() - 1 - j;
+                        ac.dim[j] = Tv.dims[li];
+                        ac.tstride[j] = leaf ? NC.view.strides[li] : Tv.strides[li];
+                    }
+                    std::vector<int32_t> cptr(NC.n_inst + 1, 0), csrc(N.n_inst);
+                    for (int64_t i = 0; i < N.n_inst; ++i) ++cptr[ic[i] + 1];
+                    for (int64_t j = 0; j < NC.n_inst; ++j) cptr[j + 1] += cptr[j];
+                    {
+                        std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+                        for (int64_t i = 0; i < N.n_inst; ++i) csrc[fill[ic[i]]++] = (int32_t)i;
+                    }
+                    std::vector<std::pair<int32_t, int64_t>> tg;
+                    for (int64_t j = 0; j < NC.n_inst; ++j) {
+                        if (leaf)
+                            tg.push_back({BASE_ENV, (grad->env_off[c] + (NC.inst_off[j] - net.leaves[c].offset)) * 16});
+                        else
+                            tg.push_back({env_base[c].first, env_base[c].second + j * NC.view.size * es});
+                    }
+                    const size_t o_p = blob.put_i32(cptr), o_s = blob.put_i32(csrc), o_t = blob.put_ptrs(tg);
+                    const size_t base = atasks.size() * sizeof(AccumTask) + offsetof(AccumTask, a);
+                    apatches.push_back({base + offsetof(AccumArgs, src), BASE_ARENA, (int64_t)toff});
+                    apatches.push_back({base + offsetof(AccumArgs, tgt), BASE_BLOB, (int64_t)o_t});
+                    apatches.push_back({base + offsetof(AccumArgs, csr_ptr), BASE_BLOB, (int64_t)o_p});
+                    apatches.push_back({base + offsetof(AccumArgs, csr_src), BASE_BLOB, (int64_t)o_s});
+                    at.block0 = ablocks;
+                    const int64_t items = (int64_t)NC.n_inst * Tv.size;
+                    ablocks += (int32_t)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 1024));
+                    abytes += (double)es * (double)N.n_inst * (double)Tv.size * 2.0;
+                    atasks.push_back(at);
                 }
-                std::vector<int64_t> un = N.view.labels;
-                for (int64_t l : NO.view.labels)
-                    if (find_pos(un, l) < 0) un.push_back(l);
-                const double flop = 8.0 * (double)dimprod(un) * (double)N.n_inst;
-                const double bytes = (double)es * (double)N.n_inst * (double)(N.view.size + NO.view.size + Tv.size);
-                std::vector<size_t> scr, scrb;
-                emit_direct(v, N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, N.n_inst, pe, po, pt, flop,
-                            bytes, scr, scrb);
-                for (size_t q = 0; q < scr.size(); ++q) arena.release(scr[q], scrb[q]);
-                P.flop_executed += flop;
-                // sum the contributions into env(c)
-                AccumArgs ac;
-                std::memset(&ac, 0, sizeof ac);
-                ac.n = Tv.size;
-                ac.n_tgt = (int32_t)NC.n_inst;
-                ac.rank = (int32_t)Tv.labels.size();
-                ac.src_fp64 = fp64 ? 1 : 0;
-                const bool leaf = c < n_leaves;
-                ac.tgt_fp64 = (leaf || fp64) ? 1 : 0;
-                for (int j = 0; j < ac.rank; ++j) {
-                    const size_t li = Tv.labels.size() - 1 - j;
-                    ac.dim[j] = Tv.dims[li];
-                    ac.tstride[j] = leaf ? NC.view.strides[li] : Tv.strides[li];
-                }
-                std::vector<int32_t> cptr(NC.n_inst + 1, 0), csrc(N.n_inst);
-                for (int64_t i = 0; i < N.n_inst; ++i) ++cptr[ic[i] + 1];
-                for (int64_t j = 0; j < NC.n_inst; ++j) cptr[j + 1] += cptr[j];
-                {
-                    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
-                    for (int64_t i = 0; i < N.n_inst; ++i) csrc[fill[ic[i]]++] = (int32_t)i;
-                }
-                std::vector<std::pair<int32_t, int64_t>> tg;
-                for (int64_t j = 0; j < NC.n_inst; ++j) {
-                    if (leaf)
-                        tg.push_back({BASE_ENV, (grad->env_off[c] + (NC.inst_off[j] - net.leaves[c].offset)) * 16});
-                    else
-                        tg.push_back({env_base[c].first, env_base[c].second + j * NC.view.size * es});
-                }
-                const size_t o_p = blob.put_i32(cptr), o_s = blob.put_i32(csrc), o_t = blob.put_ptrs(tg);
-                const size_t so = blob.reserve(sizeof ac);
-                std::memcpy(blob.bytes.data() + so, &ac, sizeof ac);
-                blob.patch_field(so, offsetof(AccumArgs, src), BASE_ARENA, (int64_t)toff);
-                blob.patch_field(so, offsetof(AccumArgs, tgt), BASE_BLOB, (int64_t)o_t);
-                blob.patch_field(so, offsetof(AccumArgs, csr_ptr), BASE_BLOB, (int64_t)o_p);
-                blob.patch_field(so, offsetof(AccumArgs, csr_src), BASE_BLOB, (int64_t)o_s);
+            }
+            flush_batch();
+            if (!atasks.empty()) {
+                const size_t o_tasks = blob.reserve(sizeof(AccumTask) * atasks.size(), 64);
+                for (size_t k = 0; k < atasks.size(); ++k)
+                    std::memcpy(blob.bytes.data() + o_tasks + k * sizeof(AccumTask), &atasks[k], sizeof(AccumTask));
+                for (auto &pt : apatches) blob.patches.push_back({o_tasks + pt.at, pt.base, pt.byte_off});
+                AccumBatchArgs ab;
+                std::memset(&ab, 0, sizeof ab);
+                ab.n_tasks = (int32_t)atasks.size();
+                ab.n_blocks = ablocks;
+                const size_t so = blob.reserve(sizeof ab);
+                std::memcpy(blob.bytes.data() + so, &ab, sizeof ab);
+                blob.patch_field(so, offsetof(AccumBatchArgs, tasks), BASE_BLOB, (int64_t)o_tasks);
                 Op op;
-                op.kind = OpKind::Accum;
-                op.node = c;
-                op.n_inst = NC.n_inst;
+                op.kind = OpKind::AccumBatch;
+                op.node = rev[i0];
+                op.n_inst = (int64_t)atasks.size();
                 op.args_off = so;
-                op.args_bytes = sizeof ac;
-                op.bytes = (double)es * (double)N.n_inst * (double)Tv.size * 2.0;
-                op.grid_x = (int32_t)std::max<int64_t>(
-                    1, std::min<int64_t>(((int64_t)NC.n_inst * Tv.size + 255) / 256, 148 * 16));
+                op.args_bytes = sizeof ab;
+                op.bytes = abytes;
+                op.grid_x = ablocks;
                 P.ops.push_back(op);
-                arena.release(toff, tbytes);
             }
+            for (auto &tb : tbufs) arena.release(tb.first, tb.second);
+            i0 = i1;
         }
     }
 

@@ -44,7 +44,7 @@ class OpRecord(ctypes.Structure):
 
 
 OP_KINDS = {0: "direct", 1: "permute", 2: "gemm_simt", 3: "gemm_tc", 4: "slice_reduce", 5: "splitk_reduce",
-            6: "tc_split", 7: "small_batch", 8: "accum", 9: "memset", 10: "apply"}
+            6: "tc_split", 7: "small_batch", 8: "accum", 9: "memset", 10: "apply", 11: "accum_batch"}
 
 
 class TensorDesc(ctypes.Structure):

@@ -18,7 +18,14 @@ path receives it, then upcast to complex128.
      conserve the photon number; Section 4, Algorithm 1).  Odd totals are exactly
      zero and need no stored value.
 
-Usage: python tests/golden/make_golden.py grid30 gbs16
+  grid53.json : 53-qubit 9x6-minus-corner grid circuit, 12 cycles (seed 3), the
+     workload's bitstring: the oracle's own contraction order (its greedy path,
+     improved by exhaustive re-ordering of sub-trees of up to 8 tensors until it
+     stops improving) and its own sliced labels (largest intermediate <= 2^28
+     elements), and the O2 partials (Eq. sliced_sum) of 8 seeded slice ids.  The
+     GPU test contracts the same network along the stored order and slicing.
+
+Usage: python tests/golden/make_golden.py grid30 gbs16 grid53
 """
 import json
 import os
@@ -104,7 +111,53 @@ def gbs16():
     print(json.dumps(rec["seconds"]))
 
 
+def grid53():
+    from oracle.einsum import greedy_path, improve_path, slice_until, network_flops, slice_network, contract_network
+    from circuits import SplitMix64
+    w = configs.build("grid53")
+    tn = w.network.as_complex64()
+    dims = {}
+    for l, t in zip(tn.labels, tn.data):
+        for x, sz in zip(l, t.shape):
+            dims[x] = 1 if x in tn.open_labels else sz
+    t0 = time.time()
+    path = greedy_path(tn.labels, dims)
+    prev = None
+    while True:
+        path = improve_path(tn.labels, dims, path, k=8, passes=5)
+        f = network_flops(tn.labels, dims, path)
+        if prev is not None and f >= prev:
+            break
+        prev = f
+    sliced = slice_until(tn.labels, dims, path, 1 << 28)
+    t_plan = time.time() - t0
+    n_sl = 2 ** len(sliced)
+    rng = SplitMix64(53)
+    ids = sorted({int(rng.next_u64() % n_sl) for _ in range(8)})
+    d2 = {x: (1 if x in sliced else v) for x, v in dims.items()}
+    parts = []
+    t0 = time.time()
+    for i in ids:
+        digits = [(i >> (len(sliced) - 1 - j)) & 1 for j in range(len(sliced))]
+        labs, dat = slice_network(tn.labels, tn.data, list(tn.open_labels) + sliced, list(w.outputs[0]) + digits)
+        _, t = contract_network(labs, dat, path)
+        parts.append(complex(t))
+        print(f"slice {i}: {parts[-1]}", flush=True)
+    t_sl = time.time() - t0
+    rec = {
+        "workload": "grid53", "source": "oracle O2 (pairwise numpy.tensordot) along the oracle's own path and slicing",
+        "outputs": w.outputs.tolist(), "path": [list(map(int, p)) for p in path],
+        "path_flop": float(f), "sliced_labels": [int(x) for x in sliced],
+        "flop_per_slice": float(network_flops(tn.labels, d2, path)),
+        "slice_ids": ids, "slice_partials": [[p.real, p.imag] for p in parts],
+        "seconds": {"planning": round(t_plan, 1), "slices": round(t_sl, 1)},
+    }
+    with open(os.path.join(HERE, "grid53.json"), "w") as fh:
+        json.dump(rec, fh)
+    print(json.dumps(rec["seconds"]))
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["grid30"]
     for name in which:
-        {"grid30": grid30, "gbs16": gbs16}[name]()
+        {"grid30": grid30, "gbs16": gbs16, "grid53": grid53}[name]()
