@@ -163,12 +163,18 @@ int jet_path_set(jet_network *net, int32_t n_steps, const int32_t *pairs);
 /* Read back the current path (2 * (n_tensors - 1) ints). */
 int jet_path_get(const jet_network *net, int32_t *pairs_out);
 
-/* The library's own planner (greedy; the paper delegates path search to an
- * external tool, Section 3): repeatedly contract the pair of tensors sharing a
+/* The library's own planner (the paper delegates path search to an external
+ * tool, Section 3).  Greedy: repeatedly contract the pair of tensors sharing a
  * label that minimises size(out) - size(A) - size(B), ties to smaller FLOP then
  * smaller ids; trial t > 0 perturbs the score with seeded noise; the path of
- * lowest total FLOP is kept and set.  flop_out (may be NULL) receives its FLOP.
- * Open legs count as fixed (dim 1) because every amplitude fixes them. */
+ * lowest total FLOP is kept.  It is then improved by sub-tree reconfiguration:
+ * for every internal node, the sub-tree below it is opened down to at most 10
+ * tensors (largest intermediate first) and re-ordered optimally by dynamic
+ * programming over subsets, when that lowers the FLOP without an intermediate
+ * above the path's largest (8 passes over the tree).  The result is set;
+ * flop_out (may be NULL) receives its FLOP.  Open legs count as fixed (dim 1)
+ * because every amplitude fixes them.  Networks of up to 10 tensors get an
+ * optimal order under that size bound. */
 int jet_path_greedy(jet_network *net, uint64_t seed, int32_t n_trials, double *flop_out);
 
 /* Batch-aware form of jet_path_greedy for a batch of amplitudes contracted

@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ 
 template <int NF, int FIB, bool POW2>
 __global__ void __launch_bounds__(256) apply_stream_c64(const __grid_constant__ ApplyArgs a)
 {
-    __shared__ ulonglong2 sB[JET_APPLY_MAXK * JET_APPLY_STREAMF];   // [q][f], rows of nfp entries
+    __shared__ ulonglong2 sB[JET_APPLY_MAXK * 4];   // [q][f], rows of nfp <= 4 entries
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
     const int nk = a.nk, nf = a.nf;
     const int nfp = (nf + NF - 1) / NF * NF;   // row length: free entries padded to whole chunks
@@ -235,12 +235,13 @@ __global__ void __launch_bounds__(256) apply_stream_c64(const __grid_constant__ 
 template <bool POW2>
 __global__ void __launch_bounds__(256, 2) apply_quad_c64(const __grid_constant__ ApplyArgs a)
 {
-    __shared__ ulonglong2 sB[JET_APPLY_MAXK * JET_APPLY_STREAMF];   // [q][f], rows of nfp entries
+    __shared__ __align__(16) float2 sB[JET_APPLY_STREAMB];   // [q][f], rows of nfp entries
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
     const int nk = a.nk, nf = a.nf;
     const int nfp = (nf + 15) / 16 * 16;
     const int lane = threadIdx.x & 31, grp = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
     const int64_t step = (int64_t)gridDim.x * (blockDim.x / 32) * 32;
+    constexpr int QC = 4;   // summed entries loaded ahead per round
     for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
         const unsigned long long *__restrict__ A = (const unsigned long long *)pA[inst];
         const float2 *__restrict__ B = (const float2 *)pB[inst];
@@ -248,8 +249,7 @@ __global__ void __launch_bounds__(256, 2) apply_quad_c64(const __grid_constant__
         __syncthreads();
         for (int i = threadIdx.x; i < nk * nfp; i += blockDim.x) {
             const int q = i / nfp, f = i - q * nfp;
-            const float2 b = f < nf ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);
-            sB[i] = make_ulonglong2(pack2(b.x, b.x), pack2(b.y, b.y));
+            sB[i] = f < nf ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);
         }
         __syncthreads();
         for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x / 32) + warp) * 32; w0 < a.n_fib; w0 += step) {
@@ -267,17 +267,26 @@ __global__ void __launch_bounds__(256, 2) apply_quad_c64(const __grid_constant__
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int ff = 0; ff < 4; ++ff) p[i][ff] = m[i][ff] = 0ull;
-                const ulonglong2 *bq = sB + f0 + 4 * t;
-#pragma unroll 2
-                for (int q = 0; q < nk; ++q) {
-                    unsigned long long x[4];
+                const float4 *brow = (const float4 *)(sB + f0 + 4 * t);   // 4 free entries = 2 float4
+                for (int q0 = 0; q0 < nk; q0 += QC) {
+                    unsigned long long x[QC][4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) x[i] = ok[i] ? __ldg(A + oa[i] + a.kA[q]) : 0ull;
+                    for (int qq = 0; qq < QC; ++qq)
 #pragma unroll
-                    for (int ff = 0; ff < 4; ++ff) {
-                        const ulonglong2 b = bq[q * nfp + ff];
+                        for (int i = 0; i < 4; ++i)
+                            x[qq][i] = (ok[i] && q0 + qq < nk) ? __ldg(A + oa[i] + a.kA[q0 + qq]) : 0ull;
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) cmac2(p[i][ff], m[i][ff], b, x[i]);
+                    for (int qq = 0; qq < QC; ++qq) {
+                        if (q0 + qq >= nk) break;
+                        const float4 v01 = brow[(size_t)(q0 + qq) * nfp / 2], v23 = brow[(size_t)(q0 + qq) * nfp / 2 + 1];
+                        const ulonglong2 b[4] = {make_ulonglong2(pack2(v01.x, v01.x), pack2(v01.y, v01.y)),
+                                                 make_ulonglong2(pack2(v01.z, v01.z), pack2(v01.w, v01.w)),
+                                                 make_ulonglong2(pack2(v23.x, v23.x), pack2(v23.y, v23.y)),
+                                                 make_ulonglong2(pack2(v23.z, v23.z), pack2(v23.w, v23.w))};
+#pragma unroll
+                        for (int ff = 0; ff < 4; ++ff)
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) cmac2(p[i][ff], m[i][ff], b[ff], x[qq][i]);
                     }
                 }
 #pragma unroll
@@ -370,9 +379,11 @@ cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
     if (a.nf_tmpl > 0) {   // streamed form (complex64)
         // nf_tmpl: free entries per register chunk (1, 2, 4); 16: lane groups of four
+        const int nfp = a.nf_tmpl == 16 ? (a.nf + 15) / 16 * 16 : (a.nf + a.nf_tmpl - 1) / a.nf_tmpl * a.nf_tmpl;
         const bool ok = (a.nf_tmpl == 1 || a.nf_tmpl == 2 || a.nf_tmpl == 4 || a.nf_tmpl == 16) &&
                         a.nf >= 1 && a.nf <= JET_APPLY_STREAMF && a.nk >= 1 && a.nk <= JET_APPLY_MAXK &&
-                        a.rank <= JET_MAXR && !(c.variant & 1);
+                        (a.nf_tmpl == 16 ? a.nk * nfp <= JET_APPLY_STREAMB : nfp <= 4) && a.rank <= JET_MAXR &&
+                        !(c.variant & 1);
         if (!ok) return cudaErrorInvalidValue;
         dim3 grid(c.gx, c.gy, 1);
         const bool pow2 = c.variant & 4;

@@ -9,7 +9,8 @@
 #define JET_COLMAX 1024      // max entries of a column offset table
 #define JET_KLOMAX 1024      // max entries of an inner-K offset table
 #define JET_SPLITK_G 8       // outputs per block in the split-K direct kernel
-#define JET_APPLY_MAXK 64    // small-operand application: max summed entries (streamed form)
+#define JET_APPLY_MAXK 256   // small-operand application: max summed entries (streamed form)
+#define JET_APPLY_STREAMB 4096 // streamed form: max entries of the small operand (free padded to 16)
 #define JET_APPLY_HOLDK 32   // ... held in registers: max summed entries
 #define JET_APPLY_MAXF 256   // small-operand application: max free entries of the small operand
 #define JET_APPLY_MAXB 1024  // held form: max entries of the small operand (summed extent padded)

@@ -740,7 +740,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             if (find_pos(K, l) < 0) f.push_back(l);
         return f;
     };
-    auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big) {
+    auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big,
+                              int64_t n_inst) {
         const View &VS = a_big ? VB : VA, &VL = a_big ? VA : VB;
         const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
         const int64_t nk = dimprod(K), nf = dimprod(fs), nfib = dimprod(fl);
@@ -748,12 +749,14 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         while (nk2 < nk) nk2 *= 2;
         // held in registers: up to 16 summed entries (complex128 too), or 32 (complex64)
         const bool held = nk <= (fp64 ? 16 : JET_APPLY_HOLDK) && nk2 * nf <= JET_APPLY_MAXB;
-        const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF;
-        return nk >= 1 && (held || streamed) && nf <= JET_APPLY_MAXF && nfib >= (1 << 15) &&
+        const int64_t nfp = nf <= 4 ? nf : (nf + 15) / 16 * 16;
+        const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF &&
+                              (nf <= 4 || nk * nfp <= JET_APPLY_STREAMB);
+        return nk >= 1 && (held || streamed) && nf <= JET_APPLY_MAXF && nfib * n_inst >= (1 << 15) &&
                (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
     };
     auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
-        return apply_ok_views(VA, VB, N.K, N.a_big);
+        return apply_ok_views(VA, VB, N.K, N.a_big, N.n_inst);
     };
     auto emit_apply = [&](int32_t v, const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K,
                           bool a_big, int64_t n_inst, const std::vector<std::pair<int32_t, int64_t>> &pa,
@@ -1340,7 +1343,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                         add_small_task(N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, pe, po, pt, N.n_inst);
                         batch_flop += flop;
                         batch_bytes += bytes;
-                    } else if (apply_ok_views(N.view, NO.view, Kb, N.view.size >= NO.view.size)) {
+                    } else if (apply_ok_views(N.view, NO.view, Kb, N.view.size >= NO.view.size, N.n_inst)) {
                         emit_apply(v, N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, N.n_inst, pe, po, pt, flop,
                                    bytes);
                     } else {

@@ -463,7 +463,7 @@ static std::vector<std::pair<int32_t, int32_t>> leaf_order_linear(const Network 
 }
 
 // Subtree reconfiguration: for every internal node, take the sub-tree below it
-// down to a frontier of at most k tensors (splitting the largest intermediate
+// down to a frontier of at most k tensors (k = 10 below) (splitting the largest intermediate
 // first), find the cheapest order of contracting that frontier exactly by
 // dynamic programming over its subsets, and substitute it when it lowers the
 // (instance-weighted) FLOP without creating an intermediate above max_size.
@@ -727,7 +727,7 @@ std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_
         double pk = 0;
         weighted_flop(net, best, bt, &pk);
         const double limit = std::isfinite(cap) ? std::max(cap, pk) : pk;
-        auto better_path = reconfigure(net, best, bt, 4, 8, limit);
+        auto better_path = reconfigure(net, best, bt, 8, 10, limit);
         double pk2 = 0;
         const double f2 = weighted_flop(net, better_path, bt, &pk2);
         if (f2 < best_flop && pk2 <= limit) {
