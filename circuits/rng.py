@@ -26,3 +26,18 @@ class SplitMix64:
     def randint(self, n: int) -> int:
         """Uniform integer in [0, n)."""
         return min(int(self.uniform() * n), n - 1)
+
+
+def uniform_array(seed: int, n: int):
+    """The first n uniform() draws of SplitMix64(seed) as a float64 numpy array.
+
+    SplitMix64 is counter based: draw i (from 0) mixes seed + (i + 1) * gamma,
+    so the whole sequence is computed at once with wrapping uint64 arithmetic."""
+    import numpy as np
+    i = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _MASK) + i * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)

@@ -50,8 +50,12 @@ typedef struct jet_network jet_network;            /* opaque, owned by the libra
 typedef struct { float re, im; } jet_c64;
 typedef struct { double re, im; } jet_c128;
 
-/* Arithmetic used for the large (GEMM-shaped) pairwise contractions.  Small
- * contractions always run on CUDA cores in FP32 (FP64 in JET_PREC_FP64).
+/* Arithmetic used for the large (GEMM-shaped) pairwise contractions and, in
+ * the split modes (every mode but FP32 and FP64), for the application of a
+ * small operand with at most 256 summed and 32 free entries, and at least
+ * apply_tc_min_kf of them in all (summed x free), to a large one (TF32 hi + lo,
+ * three products; one in JET_PREC_TF32).  Other small contractions always run
+ * on CUDA cores in FP32 (FP64 in JET_PREC_FP64).
  * Intermediates are complex64, except in JET_PREC_FP64 (complex128).  Slice
  * and amplitude sums are always FP64. */
 typedef enum {
@@ -78,7 +82,10 @@ typedef struct {
     int32_t profile;          /* 0 (default): off; 1: CUDA events around every GEMM, operand
                                  split and small-operand launch; 2: around every launch
                                  (read with jet_profile)                                  */
-    int32_t pad_;
+    int32_t apply_tc_min_kf;  /* split modes: small-operand applications whose small operand
+                                 has at least this many entries (summed x free) run on the
+                                 tensor cores; default 1024 (below it the CUDA-core forms
+                                 are HBM-bound), above 8192 none does                     */
 } jet_options;
 
 typedef struct {

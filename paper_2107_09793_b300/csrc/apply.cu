@@ -19,6 +19,7 @@
 
 #include "kernel_args.h"
 #include "kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace jet {
 
@@ -69,11 +70,23 @@ __device__ __forceinline__ float2 cfinish(unsigned long long p, unsigned long lo
     return make_float2(a.x - b.y, a.y + b.x);
 }
 
+// Offsets in A and C of fiber r (mixed radix over A's free labels, fastest
+// first).  Power-of-two dims: digit j is the bit field of r at shift[j], so the
+// digits decode independently of one another.
 template <bool POW2>
 __device__ __forceinline__ void fiber_offsets(int64_t r, const ApplyArgs &a, int64_t &oa, int64_t &oc)
 {
     oa = 0;
     oc = 0;
+    if (POW2) {
+#pragma unroll 4
+        for (int j = 0; j < a.rank; ++j) {
+            const int64_t dg = (r >> a.shift[j]) & (a.dim[j] - 1);
+            oa += dg * a.sA[j];
+            oc += dg * a.sC[j];
+        }
+        return;
+    }
     for (int j = 0; j < a.rank; ++j) {
         const int64_t d = a.dim[j];
         int64_t q, dg;
@@ -307,6 +320,278 @@ __global__ void __launch_bounds__(256, 2) apply_quad_c64(const __grid_constant__
     }
 }
 
+// ------------------------------------------------------------ tensor-core form
+// The same contraction on the 5th-generation tensor cores, for a small operand
+// with many summed entries (where the CUDA-core forms above are bound by their
+// FMA issue rate rather than by HBM).  Written as one real matrix product per
+// tile of 128 fibers:
+//     D[m, 2f + c'] = sum_{q, c} A2[m, 2q + c] * B2[2f + c', 2q + c]
+// with A2 the interleaved (re, im) values of A's fiber m and B2 the 2 x 2 real
+// block [[Br, -Bi], [Bi, Br]] of each entry B[f, q], so row m of D holds the
+// fiber's nf complex outputs as (re, im) pairs.  Both operands are split into
+// TF32 hi + lo parts and the products hi.hi + hi.lo + lo.hi (one term in plain
+// TF32 mode) accumulate in FP32 in tensor memory, restarting every 32 summed
+// entries; chunk results are added up in FP32 registers.
+//
+// A CTA holds G groups of 128 threads (one fiber per thread; warp w of a group
+// owns TMEM lanes 32 (w % 4) ..).  The CTA walks a contiguous range of units
+// (instance, G consecutive tiles), group g taking tile g of each unit; the
+// small operand's planes are rebuilt in shared memory when the instance
+// changes.  Per chunk of 32 summed entries a thread: splits its gathered values
+// into the group's K-major SWIZZLE_64B planes, the group synchronises, one
+// thread issues the MMAs and commits them to the group's mbarrier, every thread
+// issues the gathers of its next chunk (they stay in flight through the wait
+// and the epilogue), waits for the MMAs (bounded: ~2 s, then the group stops and
+// the kernel records status bit 2) and reads its row of D.
+constexpr int ATC_M = 128;     // fibers per tile: MMA M, TMEM lanes
+constexpr int ATC_KC = 32;     // summed entries per chunk (64 real K = 4 blocks of 16 TF32)
+constexpr int ATC_KBB = ATC_M * 64;   // bytes of one 64-byte-wide K block of an A plane
+
+__device__ __forceinline__ uint32_t sw64(int row, int chunk16)
+{
+    // SWIZZLE_64B: 16-byte chunk index XOR row bits 1..2 (rows of 64 bytes, 512-byte atoms)
+    return (uint32_t)(row * 64 + ((chunk16 ^ ((row >> 1) & 3)) << 4));
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, float x, float y, float z, float w)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
+
+__device__ __forceinline__ void group_sync(int id)
+{
+    asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+}
+
+__device__ __forceinline__ bool group_any(bool v, int id)
+{
+    uint32_t r;
+    asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, %2, 128, q;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(r)
+                 : "r"((uint32_t)v), "r"(id)
+                 : "memory");
+    return r != 0;
+}
+
+// TF32 hi / lo planes of the small operand for one instance: row 2f + c' of
+// K block kb holds, for the 8 summed entries q of the block, the pairs that
+// multiply (re, im) of A[., q] into the real (c' = 0) or imaginary (c' = 1)
+// part of output f.
+__device__ __forceinline__ void atc_fill_b(const ApplyArgs &a, const float2 *__restrict__ B, uint32_t sB, int nkb,
+                                           int nrl, uint32_t bplane, int tid, int nthr)
+{
+    const int per_blk = nrl * 4;   // 16-byte chunks per K block
+    for (int i = tid; i < nkb * per_blk; i += nthr) {
+        const int kb = i / per_blk, rem = i - kb * per_blk, row = rem >> 2, j = rem & 3;
+        const int f = row >> 1, q0 = kb * 8 + 2 * j;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int q = q0 + e;
+            float2 b = make_float2(0.f, 0.f);
+            if (f < a.nf && q < a.nk) b = B[a.bF[f] + a.bK[q]];
+            if (row & 1) {   // imaginary output: Bi * Ar + Br * Ai
+                v[2 * e] = b.y;
+                v[2 * e + 1] = b.x;
+            } else {         // real output: Br * Ar - Bi * Ai
+                v[2 * e] = b.x;
+                v[2 * e + 1] = -b.y;
+            }
+        }
+        float h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = tf32_rna(v[e]);
+            l[e] = tf32_rna(v[e] - h[e]);
+        }
+        const uint32_t off = (uint32_t)kb * (uint32_t)(nrl * 64) + sw64(row, j);
+        st_shared_v4(sB + off, h[0], h[1], h[2], h[3]);
+        st_shared_v4(sB + bplane + off, l[0], l[1], l[2], l[3]);
+    }
+}
+
+// Bounded mbarrier wait, inlined so that the gathers a thread has in flight
+// stay in flight across it (~2 s, or until another group has given up).
+__device__ __forceinline__ bool mbar_wait_inline(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > 2000000000ull) return false;
+        }
+    }
+    return false;
+}
+
+// MULTI: more than one chunk per tile (summed entries above 32), partial sums
+// promoted into FP32 registers; without it a tile is one chunk.
+template <int G, bool MULTI, bool POW2>
+__global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant__ ApplyArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bars[G];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int fail_any;
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, g = tid >> 7, m = tid & 127, warp = tid >> 5;
+    const int nk = a.nk, nf = a.nf, nkb = (nk + 7) >> 3, nch = MULTI ? (nk + ATC_KC - 1) / ATC_KC : 1;
+    const int nr = (nf + 7) >> 3;           // 16-column groups of D (8 complex outputs each)
+    const int nrl = 16 * nr;                // real columns: the MMA's N
+    const uint32_t bplane = (uint32_t)(nkb * nrl * 64);
+    const int64_t T = (a.n_fib + ATC_M - 1) / ATC_M, U = (T + G - 1) / G, total = U * a.n_inst;
+    const int64_t u0 = total * blockIdx.x / gridDim.x, u1 = total * (blockIdx.x + 1) / gridDim.x;
+    const uint32_t sA = smem_u32(smem + g * JET_APPLY_TC_ABYTES), sB = smem_u32(smem + G * JET_APPLY_TC_ABYTES);
+    const uint32_t bar = smem_u32(&bars[g]);
+    const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
+    constexpr uint32_t COLS = G <= 2 ? 128 : 256;   // 64 columns per group, allocated as a power of two
+
+    if (tid == 0) {
+        for (int i = 0; i < G; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        fail_any = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder + 64 * g;
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    // kind::tf32, FP32 D, K-major A and B, M = 128, N = nrl
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nrl >> 3) << 17) | ((uint32_t)(ATC_M >> 4) << 24);
+    const int terms = a.tc_terms;
+
+    auto valid = [&](int64_t u) { return (u % U) * G + g < T; };
+    // gather one chunk of one fiber (zeros outside the operand)
+    uint64_t X[ATC_KC];
+    int64_t oc_next = 0;
+    auto gather = [&](int64_t u, int c) {
+        const int64_t inst = u / U, r = ((u % U) * G + g) * ATC_M + m;
+        const bool ok = r < a.n_fib;
+        int64_t oa, oc;
+        fiber_offsets<POW2>(ok ? r : 0, a, oa, oc);
+        oc_next = oc;
+        const unsigned long long *A = (const unsigned long long *)pA[inst] + oa;
+        const int kv = min(ATC_KC, nk - c * ATC_KC);
+        const int64_t *kA = a.kA + c * ATC_KC;
+#pragma unroll
+        for (int q = 0; q < ATC_KC; ++q) X[q] = (ok && q < kv) ? __ldg(A + kA[q]) : 0ull;
+    };
+
+    int64_t pu = u0;   // this group's next item (unit, chunk) to gather
+    while (pu < u1 && !valid(pu)) ++pu;
+    int pc = 0;
+    if (pu < u1) gather(pu, 0);
+    int64_t cur_inst = -1;
+    uint32_t phase = 0;
+    bool failed = false;
+    float acc[MULTI ? 64 : 1];
+
+    for (int64_t u = u0; u < u1; ++u) {
+        const int64_t inst = u / U;
+        if (inst != cur_inst) {   // CTA-uniform: every group's MMAs on the old planes have completed
+            __syncthreads();
+            atc_fill_b(a, (const float2 *)pB[inst], sB, nkb, nrl, bplane, tid, 128 * G);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            cur_inst = inst;
+        }
+        if (failed || !valid(u)) continue;   // group-uniform
+        const int64_t r = ((u % U) * G + g) * ATC_M + m;
+        const bool rok = r < a.n_fib;
+        const int64_t oc = oc_next;
+        unsigned long long *C = (unsigned long long *)pC[inst];
+        for (int c = 0; c < nch; ++c) {
+            const int kv = min(ATC_KC, nk - c * ATC_KC), kbc = (kv + 7) >> 3;
+            // split the gathered chunk into the hi / lo planes of row m
+#pragma unroll
+            for (int p = 0; p < ATC_KC / 2; ++p) {
+                if ((p >> 2) < kbc) {
+                    const float2 v0 = unpack2(X[2 * p]), v1 = unpack2(X[2 * p + 1]);
+                    const float h0 = tf32_rna(v0.x), h1 = tf32_rna(v0.y), h2 = tf32_rna(v1.x), h3 = tf32_rna(v1.y);
+                    const uint32_t off = (uint32_t)(p >> 2) * ATC_KBB + sw64(m, p & 3);
+                    st_shared_v4(sA + off, h0, h1, h2, h3);
+                    st_shared_v4(sA + JET_APPLY_TC_ABYTES / 2 + off, tf32_rna(v0.x - h0), tf32_rna(v0.y - h1),
+                                 tf32_rna(v1.x - h2), tf32_rna(v1.y - h3));
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            group_sync(1 + g);
+            if (m == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int kb = 0; kb < kbc; ++kb)
+                    for (int sub = 0; sub < 2; ++sub)
+                        for (int t = 0; t < terms; ++t) {
+                            const int pa = t == 2, pb = t == 1;   // hi.hi, hi.lo, lo.hi
+                            const uint64_t ad = sdesc(sA + pa * (JET_APPLY_TC_ABYTES / 2) + kb * ATC_KBB + sub * 32);
+                            const uint64_t bd =
+                                sdesc(sB + pb * bplane + (uint32_t)(c * 4 + kb) * (uint32_t)(nrl * 64) + sub * 32);
+                            umma<1>(tmem, ad, bd, idesc, (kb | sub | t) ? 1u : 0u);
+                        }
+                umma_commit(bar);
+            }
+            // the gathers of this group's next chunk go out before the wait
+            if (c + 1 < nch) {
+                pc = c + 1;
+            } else {
+                ++pu;
+                while (pu < u1 && !valid(pu)) ++pu;
+                pc = 0;
+            }
+            if (pu < u1) gather(pu, pc);
+            const bool ok = mbar_wait_inline(bar, phase, (volatile int *)&fail_any);
+            phase ^= 1u;
+            if (group_any(!ok, 1 + g)) {
+                failed = true;
+                if (m == 0) fail_any = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const bool last = c + 1 == nch;
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                if (h < nr) {
+                    uint32_t R[16];
+                    JET_TMEM_LD16(trow + 16 * h, R);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (MULTI) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float v = __uint_as_float(R[j]);
+                            acc[(16 * h + j) % (MULTI ? 64 : 1)] = c == 0 ? v : acc[(16 * h + j) % (MULTI ? 64 : 1)] + v;
+                        }
+                    }
+                    if (last && rok) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int f = 8 * h + j;
+                            if (f < nf) {
+                                const float re = MULTI ? acc[(16 * h + 2 * j) % (MULTI ? 64 : 1)] : __uint_as_float(R[2 * j]);
+                                const float im = MULTI ? acc[(16 * h + 2 * j + 1) % (MULTI ? 64 : 1)]
+                                                       : __uint_as_float(R[2 * j + 1]);
+                                __stcs(C + oc + a.cF[f], pack2(re, im));
+                            }
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_holder), "r"(COLS));
+    if (tid == 0 && fail_any) atomicOr((unsigned int *)a.status, 2u);
+}
+
 // NK: summed entries (compile time, so the fiber stays in registers); FIB:
 // fibers per thread (complex128: 1).
 template <typename V, int NK, int FIB, bool POW2>
@@ -375,8 +660,52 @@ static void launch_nk(const ApplyArgs &a, dim3 grid, bool pow2, cudaStream_t s)
 #undef JET_APPLY
 }
 
+constexpr int ATC_SMEM_MAX = JET_APPLY_TC_SMEM_MAX;
+
+cudaError_t set_apply_tc_smem_limits()
+{
+    cudaError_t e = cudaSuccess;
+#define JET_ATCSM(G, MU, P2)                                                                                      \
+    if (e == cudaSuccess)                                                                                         \
+        e = cudaFuncSetAttribute(apply_tc_c64<G JET_COMMA MU JET_COMMA P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 ATC_SMEM_MAX)
+    JET_ATCSM(2, true, true);
+    JET_ATCSM(2, true, false);
+    JET_ATCSM(2, false, true);
+    JET_ATCSM(2, false, false);
+    JET_ATCSM(3, false, true);
+    JET_ATCSM(3, false, false);
+#undef JET_ATCSM
+    return e;
+}
+
+static cudaError_t launch_apply_tc(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    const int G = c.block / 128;
+    if ((G != 2 && G != 3) || c.block != 128 * G || a.nk < 1 || a.nk > JET_APPLY_MAXK || a.nf < 1 ||
+        a.nf > JET_APPLY_TC_MAXF || (a.tc_terms != 1 && a.tc_terms != 3) || a.rank > JET_MAXR || a.n_inst < 1 ||
+        a.n_fib < 1 || !a.status || (c.variant & 1) || c.gx < 1 || c.gy != 1)
+        return cudaErrorInvalidValue;
+    const int smem = jet_apply_tc_smem(G, a.nk, a.nf);
+    if (smem > ATC_SMEM_MAX) return cudaErrorInvalidValue;
+    const bool pow2 = c.variant & 4, multi = a.nk > ATC_KC;
+    if (multi && G != 2) return cudaErrorInvalidValue;   // promotion registers: two groups only
+    if (multi) {
+        if (pow2) apply_tc_c64<2, true, true><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, true, false><<<c.gx, 256, smem, s>>>(a);
+    } else if (G == 2) {
+        if (pow2) apply_tc_c64<2, false, true><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, false, false><<<c.gx, 256, smem, s>>>(a);
+    } else {
+        if (pow2) apply_tc_c64<3, false, true><<<c.gx, 384, smem, s>>>(a);
+        else apply_tc_c64<3, false, false><<<c.gx, 384, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
+    if (c.variant & 8) return launch_apply_tc(a, c, s);   // tensor-core form
     if (a.nf_tmpl > 0) {   // streamed form (complex64)
         // nf_tmpl: free entries per register chunk (1, 2, 4); 16: lane groups of four
         const int nfp = a.nf_tmpl == 16 ? (a.nf + 15) / 16 * 16 : (a.nf + a.nf_tmpl - 1) / a.nf_tmpl * a.nf_tmpl;

@@ -110,6 +110,7 @@ void jet_options_default(jet_options *opt)
     opt->gemm_min_k = 16;
     opt->workspace_limit = 0;
     opt->profile = 0;
+    opt->apply_tc_min_kf = 1024;
 }
 
 int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_options *opt, jet_network **out)
@@ -124,6 +125,7 @@ int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_opti
         if (net->opt.precision < JET_PREC_FP32 || net->opt.precision > JET_PREC_FP16X3)
             fail(JET_EINVAL, "unknown precision mode");
         if (net->opt.gemm_min_k < 1) net->opt.gemm_min_k = 16;
+        if (net->opt.apply_tc_min_kf < 1) net->opt.apply_tc_min_kf = 1024;
         int64_t off = 0;
         for (int32_t t = 0; t < n; ++t) {
             const jet_tensor_desc &d = tensors[t];

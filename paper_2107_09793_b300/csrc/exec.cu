@@ -45,6 +45,7 @@ static void init_device_once(const Network &net)
     if (dev >= 0 && dev < 64 && !g_smem_set[dev]) {
         JET_CUDA(set_direct_smem_limits());
         JET_CUDA(set_tc_smem_limits());
+        JET_CUDA(set_apply_tc_smem_limits());
         g_smem_set[dev] = true;
     }
 }

@@ -15,6 +15,18 @@
 #define JET_APPLY_MAXF 256   // small-operand application: max free entries of the small operand
 #define JET_APPLY_MAXB 1024  // held form: max entries of the small operand (summed extent padded)
 #define JET_APPLY_STREAMF 32 // streamed form: max free entries of the small operand
+#define JET_APPLY_TC_MAXF 32 // tensor-core form: max free entries of the small operand (N <= 64 real columns)
+#define JET_APPLY_TC_ABYTES 65536 // tensor-core form: one group's A chunk, hi + lo TF32 planes of 128 x 64
+#define JET_APPLY_TC_SMEM_MAX 231424 // tensor-core form: dynamic shared memory cap (227 KiB less 1 KiB)
+
+// Dynamic shared memory of the tensor-core application: 1 KiB alignment slack,
+// one A chunk per thread group and the hi / lo TF32 planes of the small operand
+// (summed entries padded to blocks of 8, free entries to 8, two real rows each).
+static inline int jet_apply_tc_smem(int groups, int nk, int nf)
+{
+    const int nkb = (nk + 7) / 8, nr = 2 * ((nf + 7) / 8 * 8);
+    return 1024 + groups * JET_APPLY_TC_ABYTES + 2 * nkb * nr * 64;
+}
 
 // Pairwise contraction C = sum_K A * B evaluated directly from strides
 // (Section 2.3).  The output index is split as (row, col): col is the trailing
@@ -41,13 +53,16 @@ struct DirectArgs {
 // free labels.  Offsets are in elements.
 struct ApplyArgs {
     uint64_t ptrA, ptrB, ptrC;      // device arrays of n_inst addresses (A large, B small)
+    uint64_t status;                // device uint32 error word (tensor-core form: bounded-wait time-outs)
     int64_t n_fib;                  // fibers per instance: product of A's free dims
     int32_t n_inst, nk, nf, rank;   // nk <= nk_tmpl (entries nk..nk_tmpl-1 are padding)
     int32_t nk_tmpl;                // held form: compile-time summed extent
     int32_t nf_tmpl;                // streamed form (nf_tmpl > 0): free entries per register chunk
+    int32_t tc_terms, pad_;         // tensor-core form: TF32 products per real product (1 or 3)
     int64_t kA[JET_APPLY_MAXK], bK[JET_APPLY_MAXK];   // summed entry q: offset in A, in B
     int64_t cF[JET_APPLY_MAXF], bF[JET_APPLY_MAXF];   // B-free entry f: offset in C, in B
     int64_t dim[JET_MAXR], sA[JET_MAXR], sC[JET_MAXR];
+    int32_t shift[JET_MAXR];        // power-of-two dims: digit j of a fiber index starts at bit shift[j]
 };
 
 // Sum the split-K partials of each output in a fixed order (deterministic).

@@ -24,6 +24,7 @@ cudaError_t launch_small_batch(const SmallBatchArgs &a, const LaunchCfg &c, cuda
 cudaError_t launch_accum(const AccumArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_accum_batch(const AccumBatchArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s);
+cudaError_t set_apply_tc_smem_limits();
 cudaError_t launch_permute(const PermuteArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_gemm_simt(const GemmArgs &a, const LaunchCfg &c, cudaStream_t s);
 cudaError_t launch_tc_split(const TcSplitArgs &a, const LaunchCfg &c, cudaStream_t s);

@@ -16,8 +16,6 @@
 // a best-fit allocator simulated in launch order, so the arena size is the
 // peak of live intermediates.
 #include <algorithm>
-#include <cstdio>
-#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <unordered_map>
@@ -740,6 +738,19 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             if (find_pos(K, l) < 0) f.push_back(l);
         return f;
     };
+    // tensor-core form (split modes), for small operands of at least
+    // apply_tc_min_kf entries (where the CUDA-core forms run out of FMA issue
+    // slots before HBM bandwidth): thread groups per CTA that fit the operand
+    // planes in shared memory (three for one chunk of summed entries, else
+    // two), 0 when the form does not apply
+    auto apply_tc_groups = [&](int64_t nk, int64_t nf) -> int {
+        if (!tc_mode || fp64 || nk * nf < net.opt.apply_tc_min_kf || nk > JET_APPLY_MAXK || nf < 1 ||
+            nf > JET_APPLY_TC_MAXF)
+            return 0;
+        if (nk <= 32 && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 3;
+        if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
+        return 0;
+    };
     auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big,
                               int64_t n_inst) {
         const View &VS = a_big ? VB : VA, &VL = a_big ? VA : VB;
@@ -752,7 +763,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const int64_t nfp = nf <= 4 ? nf : (nf + 15) / 16 * 16;
         const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF &&
                               (nf <= 4 || nk * nfp <= JET_APPLY_STREAMB);
-        return nk >= 1 && (held || streamed) && nf <= JET_APPLY_MAXF && nfib * n_inst >= (1 << 15) &&
+        const bool tc = apply_tc_groups(nk, nf) > 0;
+        return nk >= 1 && (held || streamed || tc) && nf <= JET_APPLY_MAXF && nfib * n_inst >= (1 << 15) &&
                (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
     };
     auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
@@ -809,24 +821,18 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         d.rank = (int32_t)rl.size();
         d.n_fib = 1;
         bool pow2 = true;
+        int32_t bit = 0;
         for (int j = 0; j < d.rank; ++j) {
             d.dim[j] = net.labels.at(rl[j]).dim;
             d.sA[j] = stride(VL, rl[j]);
             d.sC[j] = stride(Cv, rl[j]);
             d.n_fib *= d.dim[j];
             pow2 = pow2 && (d.dim[j] & (d.dim[j] - 1)) == 0;
+            d.shift[j] = bit;
+            while (((int64_t)1 << bit) < d.n_fib) ++bit;   // power-of-two dims: log2 of the running product
         }
         d.n_inst = (int32_t)n_inst;
-        if (getenv("JET_DEBUG_PLAN")) {
-            fprintf(stderr, "apply node %d inst %ld nk %d nf %d nfib %ld | K strides in A:", v, (long)n_inst, d.nk, d.nf,
-                    (long)d.n_fib);
-            for (int64_t l : Ks) fprintf(stderr, " %ld", (long)stride(VL, l));
-            fprintf(stderr, " | fiber strides A/C:");
-            for (int j = 0; j < std::min(d.rank, 4); ++j) fprintf(stderr, " %ld/%ld", (long)d.sA[j], (long)d.sC[j]);
-            fprintf(stderr, " | F strides in C:");
-            for (int64_t l : Fs) fprintf(stderr, " %ld", (long)stride(Cv, l));
-            fprintf(stderr, "\n");
-        }
+        d.tc_terms = net.opt.precision == JET_PREC_TF32 ? 1 : 3;
         size_t off_pl = blob.put_ptrs(a_big ? pa : pb), off_ps = blob.put_ptrs(a_big ? pb : pa);
         size_t off_pc = blob.put_ptrs(pc);
         size_t so = blob.reserve(sizeof d);
@@ -843,6 +849,19 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         op.flop = flop;
         op.bytes = bytes;
         op.variant = (fp64 ? 1 : 0) | (pow2 ? 4 : 0);
+        if (const int G = apply_tc_groups(nk, nf)) {
+            // tensor-core form: one CTA per SM over contiguous ranges of (instance,
+            // G tiles of 128 fibers); the status word takes its wait time-outs
+            blob.patch_field(so, offsetof(ApplyArgs, status), BASE_STATUS, 0);
+            const int64_t units = n_inst * (((d.n_fib + 127) / 128 + G - 1) / G);
+            op.variant |= 8;
+            op.block = 128 * G;
+            op.smem = jet_apply_tc_smem(G, (int)nk, (int)nf);
+            op.grid_x = (int32_t)std::min<int64_t>(148, units);
+            op.grid_y = 1;
+            P.ops.push_back(op);
+            return;
+        }
         // 256-thread blocks; complex64 threads take two fibers, complex128 one
         op.block = 256;
         const int64_t gy = std::min<int64_t>(n_inst, 65535);
@@ -1005,16 +1024,6 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                             conv = V.strides[q] == st;
                             st *= V.dims[q];
                         }
-                    }
-                    if (getenv("JET_DEBUG_PLAN")) {
-                        fprintf(stderr, "node %d split child %d (leaf %d gemm %d) inst %ld size %ld conv %d | V:", v, id,
-                                id < n_leaves, id >= n_leaves ? (int)node[id].use_gemm : -1, (long)ninst, (long)V.size, (int)conv);
-                        for (size_t q = 0; q < V.labels.size(); ++q) fprintf(stderr, " %ld", (long)V.labels[q]);
-                        fprintf(stderr, " | f:");
-                        for (int64_t l : f) fprintf(stderr, " %ld", (long)l);
-                        fprintf(stderr, " | kappa:");
-                        for (int64_t l : kappa) fprintf(stderr, " %ld", (long)l);
-                        fprintf(stderr, "\n");
                     }
                     std::vector<std::pair<int32_t, int64_t>> ps;
                     for (int64_t j = 0; j < ninst; ++j) ps.push_back(base_ref(id, (int32_t)j));
@@ -1198,10 +1207,6 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         }
         // ------------------------------------------------ direct contraction
         else {
-            if (getenv("JET_DEBUG_PLAN"))
-                fprintf(stderr, "direct node %d inst %ld |A| %ld |B| %ld |C| %ld nK %ld nFa %ld nFb %ld flop %.3g\n", v,
-                        (long)N.n_inst, (long)VA.size, (long)VB.size, (long)N.view.size, (long)nK, (long)nFa, (long)nFb,
-                        flop);
             ++P.n_direct;
             emit_direct(v, VA, VB, N.view, K, a_big, N.n_inst, pa, pb, pc, flop, bytes, scratch, scratch_bytes);
         }

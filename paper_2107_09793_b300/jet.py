@@ -33,7 +33,7 @@ class JetError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("gemm_min_k", ctypes.c_int64), ("workspace_limit", ctypes.c_int64),
-                ("profile", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("apply_tc_min_kf", ctypes.c_int32)]
 
 
 class OpRecord(ctypes.Structure):
@@ -110,7 +110,8 @@ def _check(rc: int):
         raise JetError(rc, lib().jet_last_error().decode())
 
 
-def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=16, profile=0) -> Options:
+def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=16, profile=0,
+                    apply_tc_min_kf=1024) -> Options:
     o = Options()
     lib().jet_options_default(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -119,6 +120,7 @@ def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm
     o.device = int(device)
     o.gemm_min_k = int(gemm_min_k)
     o.profile = int(profile)
+    o.apply_tc_min_kf = int(apply_tc_min_kf)
     return o
 
 

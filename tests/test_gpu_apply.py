@@ -1,0 +1,161 @@
+"""Small-operand application route (Section 2.3, one pairwise step in the shape
+of a gate absorbed into a large state-like tensor): C[r, f] = sum_q B[f, q] A[r, q]
+vs the oracle's pairwise contraction, in the tensor-core form (split modes:
+TF32 hi + lo, three products; one in plain TF32) and on CUDA cores (FP32 mode,
+and the split modes with the tensor-core form switched off).
+
+Shapes cover: one chunk of 32 summed entries with a ragged, non-power-of-two
+fiber count; summed and free extents that are not multiples of the 8-entry
+blocks (21 x 5, 200 x 3); several chunks per tile (128 and 200 summed entries,
+the FP32 register promotion); the largest free extent (32, N = 64 real
+columns); a summed label at stride 1 in A (fibers at stride 2); and a sliced
+summed label, so the node runs as two instances in one launch (the small
+operand is rebuilt per instance).  The fast_ cases put the 7 fastest labels of A
+on the fibers (one of them reading a leaf that is 8- but not 16-byte aligned).
+The tensor-core form is forced on every shape (apply_tc_min_kf=1); the default
+routing is checked separately.
+
+The pair's result is kept whole inside the tree: each free leg of the pair is
+then absorbed by a seeded (dim x 3) selector whose second leg is an output, and
+four output rows are compared with the oracle's contraction of the same
+network."""
+import numpy as np
+import pytest
+
+from circuits import SplitMix64
+from circuits.rng import uniform_array
+from oracle.einsum import contract_network
+from paper_2107_09793_b300 import jet
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "bf16x3": 1e-5, "bf16x6": 1e-5, "fp16x3": 1e-5, "tf32": 3e-3}
+
+
+def _rand(seed, shape):
+    n = int(np.prod(shape))
+    u = uniform_array(seed, 2 * n)
+    return ((u[:n] - 0.5) + 1j * (u[n:] - 0.5)).reshape(shape).astype(np.complex64)
+
+
+# (labels of A, labels of B, dims, sliced labels); A is the large operand
+CASES = {
+    # 32 summed (4 x 8) interleaved with the fibers, 16 free; fibers 64 * 32 * 17
+    "k32_f16_ragged_fibers": ([10, 0, 11, 1, 2], [20, 10, 11], {0: 64, 1: 32, 2: 17, 10: 4, 11: 8, 20: 16}, []),
+    # 21 summed (3 x 7), 5 free, 2^15 fibers, summed labels slowest in A
+    "k21_f5": ([10, 11] + list(range(100, 115)), [11, 20, 10], {10: 3, 11: 7, 20: 5}, []),
+    # 128 summed over 7 binary labels (4 chunks), 16 free (4 x 4)
+    "k128_f16_chunks": ([0] + list(range(10, 17)) + [1], list(range(10, 17)) + [20, 21],
+                        {0: 128, 1: 256, 20: 4, 21: 4}, []),
+    # 200 summed (8 x 25: 7 chunks, the last one block of 8), 3 free, fibers 33 * 31 * 33
+    "k200_f3_chunks": ([0, 1, 2, 10, 11], [20, 11, 10], {0: 33, 1: 31, 2: 33, 10: 8, 11: 25, 20: 3}, []),
+    # 16 summed in the middle of A, 32 free: N = 64 real columns
+    "k16_f32": ([0, 10, 1], [10, 20], {0: 256, 1: 256, 10: 16, 20: 32}, []),
+    # a summed binary label at stride 1 in A: the fibers sit at stride 2
+    "k32_stride2": (list(range(100, 115)) + [10, 11, 12, 13, 14], [20, 10, 11, 12, 13, 14], {20: 8}, []),
+    # 64 summed with one label sliced: the node runs as 2 instances of 32 summed
+    "k32_two_instances": (list(range(100, 115)) + [10, 11, 12], [10, 11, 12, 20], {10: 4, 11: 8, 12: 2, 20: 8}, [12]),
+    # the 7 fastest labels of A are fibers, 128 summed: 4 chunks
+    "fast_k128_chunks": ([0] + list(range(10, 17)) + list(range(100, 107)), list(range(10, 17)) + [20, 21],
+                       {0: 256, 20: 4, 21: 4}, []),
+    # 2 instances (a sliced summed label above the fiber block)
+    "fast_k32_two_instances": ([0, 10, 11, 12] + list(range(100, 107)), [12, 11, 10, 20],
+                             {0: 256, 10: 4, 11: 8, 12: 2, 20: 16}, [12]),
+    # A read from a leaf whose base is 8 but not 16-byte aligned (a 3-entry leaf
+    # is stored first)
+    "fast_k32_unaligned": ([0, 10, 11] + list(range(100, 107)), [11, 20, 10], {0: 256, 10: 4, 11: 8, 20: 12}, "lead"),
+}
+
+
+def _network(case, prec, **opt):
+    la, lb, dd, sliced = CASES[case]
+    lead = sliced == "lead"
+    sliced = [] if lead else sliced
+    dims = {l: dd.get(l, 2) for l in la + lb}
+    seed = 1000 + 17 * sorted(CASES).index(case)
+    A = _rand(seed, [dims[l] for l in la])
+    B = _rand(seed + 1, [dims[l] for l in lb])
+    fa = [l for l in la if l not in lb]
+    fb = [l for l in lb if l not in la]
+    sels = [_rand(seed + 2 + i, [dims[l], 3]) for i, l in enumerate(fa + fb)]
+    labels = [la, lb] + [[l, 1000 + i] for i, l in enumerate(fa + fb)]
+    data = [A, B] + sels
+    opens = [1000 + i for i in range(len(fa + fb))]
+    if lead:   # a 3-entry leaf ahead of A in the leaf buffer, with an open leg of its own
+        labels, data, opens = [[999]] + labels, [_rand(seed - 1, [3])] + data, opens + [999]
+    net = jet.Network(labels, data, precision=prec, profile=1, **opt)
+    net.set_open(opens)
+    a0 = 1 if lead else 0
+    path = [(a0, a0 + 1)]
+    cur = len(labels)
+    for i in list(range(a0 + 2, len(labels))) + ([0] if lead else []):
+        path.append((cur, i))
+        cur += 1
+    net.path_set(path)
+    if sliced:
+        net.slice(sliced)
+    return net, labels, data, opens
+
+
+def _reference(labels, data, opens, outs):
+    ref = []
+    for o in outs:
+        lab = [list(l) for l in labels]
+        dat = [d.astype(np.complex128) for d in data]
+        for lbl, x in zip(opens, o):
+            e = np.zeros(3)
+            e[x] = 1
+            lab.append([lbl])
+            dat.append(e)
+        ref.append(complex(contract_network(lab, dat)[1]))
+    return np.array(ref)
+
+
+_REF = {}
+
+
+def _check(case, prec, expect_tc, **opt):
+    net, labels, data, opens = _network(case, prec, **opt)
+    rng = SplitMix64(7)
+    outs = np.array([[rng.randint(3) for _ in opens] for _ in range(4)], np.int32)
+    amps = net.contract(outs)
+    pair = [r for r in net.profile() if r["node"] == len(labels) and r["kind"] == "apply"]
+    assert pair, "the pair did not take the small-operand route"
+    assert all(bool(r["variant"] & 8) == expect_tc for r in pair), pair
+    if case not in _REF:
+        _REF[case] = _reference(labels, data, opens, outs)
+    ref = _REF[case]
+    err = float(np.linalg.norm(amps - ref) / np.linalg.norm(ref))
+    print(f"{case} {prec} tc={expect_tc}: rel err {err:.3e}")
+    net.close()
+    return err
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("prec", ["fp16x3", "tf32x3"])
+def test_apply_tensor_core_form(case, prec):
+    assert _check(case, prec, True, apply_tc_min_kf=1) <= TOL[prec]
+
+
+@pytest.mark.parametrize("case", ["k32_f16_ragged_fibers", "k128_f16_chunks", "k32_two_instances", "fast_k128_chunks"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16x3", "bf16x6"])
+def test_apply_tensor_core_other_modes(case, prec):
+    assert _check(case, prec, True, apply_tc_min_kf=1) <= TOL[prec]
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_apply_cuda_core_forms(case):
+    """FP32 mode, and a split mode with the tensor-core form switched off."""
+    assert _check(case, "fp32", False) <= TOL["fp32"]
+    assert _check(case, "fp16x3", False, apply_tc_min_kf=1 << 20) <= TOL["fp16x3"]
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_apply_default_routing(case):
+    """Default threshold: the tensor-core form for small operands of 1024
+    entries or more (32 x 32, 128 x 16), the CUDA-core forms below."""
+    la, lb, dd, sliced = CASES[case]
+    sliced = [] if sliced == "lead" else sliced
+    dims = {l: dd.get(l, 2) for l in la + lb}
+    kf = int(np.prod([dims[l] for l in lb if l not in sliced]))   # entries of one instance
+    assert _check(case, "fp16x3", kf >= 1024) <= TOL["fp16x3"]
