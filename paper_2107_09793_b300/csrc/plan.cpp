@@ -302,6 +302,26 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         sibling[b] = a;
     }
 
+    // The summed labels of v's parent when the parent applies a small operand
+    // (at most 2048 entries, not the GEMM route) to v as its large operand:
+    // laying them out slowest in v lets the parent read, for each summed
+    // entry, runs of consecutive fibers (whole sectors per warp) and write its
+    // own small operand's labels in their place, again slowest.
+    auto consumer_summed = [&](int32_t v) -> std::vector<int64_t> {
+        const int32_t pp = parent[v];
+        if (pp < 0) return {};
+        const auto &ls = labset[sibling[v]];
+        std::vector<int64_t> Kp, Fp, Fs;
+        for (int64_t l : labset[v]) (find_pos(ls, l) >= 0 ? Kp : Fp).push_back(l);
+        for (int64_t l : ls)
+            if (find_pos(labset[v], l) < 0) Fs.push_back(l);
+        const int64_t sv = dimprod(labset[v]), ss = dimprod(ls);
+        const bool p_gemm = gemm_ok && !Kp.empty() && dimprod(Kp) >= net.opt.gemm_min_k && dimprod(Fp) >= 64 &&
+                            dimprod(Fs) >= 64;
+        if (p_gemm || Kp.empty() || ss > 2048 || sv <= ss) return {};
+        return Kp;
+    };
+
     // ---- pass 1, tree order: instances (reuse DAG), label classes, route, layout, depth
     for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
         const int32_t a = net.path[k].first, b = net.path[k].second, v = n_leaves + k;
@@ -410,11 +430,43 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                         if (find_pos(Kp, l) >= 0) N.fN.push_back(l);
                 }
             }
+            // for a parent that applies a small operand: its summed labels slowest,
+            // when one side holds them all (that side becomes M, their rows first)
+            // (tensor-core route: the operand split gathers rows in any order)
+            const std::vector<int64_t> Kc = tc_mode ? consumer_summed(v) : std::vector<int64_t>();
+            if (!Kc.empty()) {
+                auto holds_all = [&](const std::vector<int64_t> &X) {
+                    for (int64_t l : Kc)
+                        if (find_pos(X, l) < 0) return false;
+                    return true;
+                };
+                const int side = holds_all(N.fa) ? 0 : holds_all(N.fb) ? 1 : -1;
+                if (side >= 0) {
+                    N.a_is_m = side == 0;
+                    const auto &fMs = N.a_is_m ? N.fa : N.fb;
+                    N.fM = Kc;
+                    for (int64_t l : fMs)
+                        if (find_pos(Kc, l) < 0) N.fM.push_back(l);
+                    N.fN = N.a_is_m ? N.fb : N.fa;
+                }
+            }
             out = N.fM;
             out.insert(out.end(), N.fN.begin(), N.fN.end());
         } else {
             out = fbig;
             out.insert(out.end(), fsmall.begin(), fsmall.end());
+        }
+        if (!N.use_gemm) {
+            // a parent that applies a small operand reads its summed labels slowest
+            const std::vector<int64_t> Kc = consumer_summed(v);
+            if (!Kc.empty()) {
+                std::vector<int64_t> re;
+                for (int64_t l : out)
+                    if (find_pos(Kc, l) >= 0) re.push_back(l);
+                for (int64_t l : out)
+                    if (find_pos(Kc, l) < 0) re.push_back(l);
+                out = re;
+            }
         }
         N.view = dense_view(out, net);
         max_inter = std::max(max_inter, N.view.size);
