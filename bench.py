@@ -36,7 +36,7 @@ PATH_TRIALS, PATH_SEED, CAP, N_SLICED = 1024, 1, 1 << 24, 6
 # (dram__bytes_read.sum + dram__bytes_write.sum) on this workload with the kernel
 # as it stands; keyed by (kernel, algorithmic FLOP or bytes of the launch) so that
 # a different plan or precision reports null instead of a stale figure.
-MEASURED_TRAFFIC = {("apply_kernel_c64", 3221487616.0): 3.187e9}
+MEASURED_TRAFFIC = {("apply_kernel_c64", 1342308352.0): 1.322e9}
 
 
 def load_peaks():
@@ -415,15 +415,19 @@ def run_impl(args):
                                                                              if args.precision.startswith("tf32") else ""),
                     "share_of_step": share}
         else:
-            kname = {"apply": "apply_kernel_c64", "tc_split": f"tc_split_kernel<{args.precision}>"}[dom]
             nbytes = sum(recs[i]["bytes"] for i in ids)
             ms = sum(timed[i] for i in ids)
             big = max(ids, key=lambda i: timed[i])
+            if dom == "apply":   # CUDA-core forms and the tensor-core form (variant bit 8)
+                kname = "apply_kernel_c64 + apply_tc_c64"
+                kbig = "apply_tc_c64" if recs[big]["variant"] & 8 else "apply_kernel_c64"
+            else:
+                kname = kbig = f"tc_split_kernel<{args.precision}>"
             achieved = nbytes / (ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "kernel": kname,
-                    "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["bytes"])),
-                    "traffic_launch": {"node": recs[big]["node"], "bytes": recs[big]["bytes"],
+                    "traffic": MEASURED_TRAFFIC.get((kbig, recs[big]["bytes"])),
+                    "traffic_launch": {"node": recs[big]["node"], "kernel": kbig, "bytes": recs[big]["bytes"],
                                        "ms": timed[big], "gb_s": recs[big]["bytes"] / (timed[big] * 1e-3) / 1e9},
                     "launches_per_step": len(ids), "bytes_per_step": nbytes, "ms_per_step": ms,
                     "peak_source": f"hbm_gbs of {peak_src}", "share_of_step": share}
