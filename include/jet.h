@@ -149,6 +149,24 @@ int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_opti
  * Errors: JET_EINVAL (a label that is not an open leg, a duplicate, a missing leg). */
 int jet_network_set_open(jet_network *net, int32_t n_out, const int64_t *out_labels);
 
+/* Leave some output legs free (Section 2.2.1: an open leg without a bra stays
+ * an index of the result; Section 3.2: a batch of amplitudes is one
+ * multi-contraction whose shared work is done once).  Every contraction then
+ * returns, for each row of outputs, all E = prod(dims of the free legs) values
+ * of those legs at once, every intermediate that does not hold a free leg
+ * computed once for all of them.  free_labels lists open legs (a subset of
+ * jet_network_set_open's); their digits in outputs are ignored.  Value e of a
+ * row is the mixed-radix number over the free legs in this order, the first
+ * most significant: jet_contract writes amps_out[b * E + e], jet_contract_async
+ * the same layout in device memory, jet_contract_slices
+ * partials_out[(b * n_ids + j) * E + e].  The path planners count a free leg
+ * with its dim (a fixed one counts as 1).  n_free = 0 fixes every open leg
+ * again; jet_network_set_open clears the list; jet_contract_grad refuses free
+ * legs.  Clears the plan.
+ * Errors: JET_EINVAL (not an open leg, a duplicate, more than 2^24 values per
+ * row), JET_ESTATE (open legs not declared yet). */
+int jet_network_set_free(jet_network *net, int32_t n_free, const int64_t *free_labels);
+
 /* Replace the values of tensor tensor_id (same shape).  Host pointer; the copy to
  * the device is ordered on the library's internal stream before the next
  * contraction.  Errors: JET_EINVAL (bad id / NULL), JET_ECUDA. */
@@ -225,8 +243,9 @@ int jet_slice_auto(jet_network *net, int64_t max_elems, int32_t min_n, int32_t m
 /* Contract the network to n_amps amplitudes.  outputs holds n_amps rows of
  * n_out digits (the values of the open legs, in jet_network_set_open order).
  * amp_b = sum over slices s (increasing s, FP64) of the sliced contraction.
- * amps_out: n_amps complex128 values in HOST memory; the call copies them back
- * and synchronises the stream before returning.
+ * amps_out: n_amps complex128 values in HOST memory (n_amps * E with free legs,
+ * see jet_network_set_free); the call copies them back and synchronises the
+ * stream before returning.
  * Errors: JET_EINVAL (digit out of range, n_amps < 1), JET_ESTATE (no path),
  * JET_ENOMEM (workspace), JET_ECUDA, JET_ETIMEOUT. */
 int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs,
@@ -239,13 +258,15 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs,
  * the listed slices are computed once.  Summing the partials of every slice in
  * increasing id order gives jet_contract's amplitude; disjoint id ranges are
  * how independent processes (one per GPU) split one amplitude's work.
- * partials_out: n_amps * n_ids complex128 values of HOST memory; the call
+ * partials_out: n_amps * n_ids complex128 values of HOST memory (times E with
+ * free legs, value e innermost); the call
  * synchronises the stream.  Errors as jet_contract, plus JET_EINVAL (empty list
  * or an id outside [0, number of slices)). */
 int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs, int32_t n_ids,
                         const int64_t *slice_ids, jet_c128 *partials_out, void *cuda_stream);
 
-/* Same as jet_contract but amps_dev is DEVICE memory (n_amps complex128) and
+/* Same as jet_contract but amps_dev is DEVICE memory (n_amps complex128, times
+ * E with free legs) and
  * the call returns without synchronising: the amplitudes are ready when work
  * issued on cuda_stream before the next call completes. */
 int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,
@@ -276,7 +297,7 @@ int jet_set_workspace(jet_network *net, void *dptr, size_t bytes);
  * only rewrites the cotangent seed; a sliced network plans and runs its slices
  * one after the other.
  * Errors as jet_contract, plus JET_EINVAL (bad or repeated tensor id,
- * a network of one tensor). */
+ * a network of one tensor, free output legs). */
 int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs,
                       const jet_c128 *cot, int32_t n_req, const int32_t *tensor_ids,
                       jet_c64 *const *env_out, jet_c128 *amps_out, void *cuda_stream);

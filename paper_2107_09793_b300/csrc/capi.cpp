@@ -185,11 +185,32 @@ int jet_network_set_open(jet_network *net, int32_t n_out, const int64_t *out_lab
             fail(JET_EINVAL, "every open leg must be listed (" + std::to_string(n_open) + " open legs)");
         net->open.assign(out_labels, out_labels + n_out);
         net->open_set = true;
+        net->free_open.clear();
         for (int64_t l : net->open)
             if (std::find(net->sliced.begin(), net->sliced.end(), l) != net->sliced.end()) {
                 net->sliced.clear();
                 ++net->slice_version;
             }
+        invalidate_plan(*net);
+    });
+}
+
+int jet_network_set_free(jet_network *net, int32_t n_free, const int64_t *free_labels)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (n_free < 0 || (n_free > 0 && !free_labels)) fail(JET_EINVAL, "bad free-leg list");
+        if (!net->open_set && n_free > 0) fail(JET_ESTATE, "declare the open legs first");
+        std::vector<int64_t> fr(free_labels, free_labels + n_free);
+        int64_t n_elem = 1;
+        for (int32_t j = 0; j < n_free; ++j) {
+            if (std::find(net->open.begin(), net->open.end(), fr[j]) == net->open.end())
+                fail(JET_EINVAL, "label " + std::to_string(fr[j]) + " is not an open leg");
+            if (std::find(fr.begin(), fr.begin() + j, fr[j]) != fr.begin() + j) fail(JET_EINVAL, "free leg listed twice");
+            n_elem *= net->labels.at(fr[j]).dim;
+            if (n_elem > ((int64_t)1 << 24)) fail(JET_EINVAL, "more than 2^24 values per row");
+        }
+        net->free_open = fr;
         invalidate_plan(*net);
     });
 }
@@ -347,7 +368,7 @@ int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,
         if (!net || !amps_dev) fail(JET_EINVAL, "NULL argument");
         Plan &P = get_plan(*net, n_amps, outputs);
         bind_and_run(*net, P, nullptr, cuda_stream);
-        copy_d2d_async(amps_dev, net->d_amps, (size_t)n_amps * sizeof(jet_c128),
+        copy_d2d_async(amps_dev, net->d_amps, (size_t)n_amps * P.n_elem * sizeof(jet_c128),
                        cuda_stream ? cuda_stream : net->stream);
     });
 }
@@ -358,7 +379,8 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c
         if (!net || !amps_out) fail(JET_EINVAL, "NULL argument");
         Plan &P = get_plan(*net, n_amps, outputs);
         bind_and_run(*net, P, nullptr, cuda_stream);
-        copy_d2h(amps_out, net->d_amps, (size_t)n_amps * sizeof(jet_c128), cuda_stream ? cuda_stream : net->stream);
+        copy_d2h(amps_out, net->d_amps, (size_t)n_amps * P.n_elem * sizeof(jet_c128),
+                 cuda_stream ? cuda_stream : net->stream);
         if (read_clear_status(*net, cuda_stream))
             fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
     });
@@ -372,7 +394,7 @@ int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs
         std::vector<int64_t> ids(slice_ids, slice_ids + n_ids);
         Plan &P = get_plan(*net, n_amps, outputs, &ids);
         bind_and_run(*net, P, nullptr, cuda_stream);
-        copy_d2h(partials_out, net->d_amps, (size_t)n_amps * n_ids * sizeof(jet_c128),
+        copy_d2h(partials_out, net->d_amps, (size_t)n_amps * n_ids * P.n_elem * sizeof(jet_c128),
                  cuda_stream ? cuda_stream : net->stream);
         if (read_clear_status(*net, cuda_stream))
             fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
@@ -384,6 +406,7 @@ int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs, 
                       void *cuda_stream)
 {
     return guarded([&] {
+        if (net && !net->free_open.empty()) fail(JET_EINVAL, "gradients need every open leg fixed (no free legs)");
         if (!net || !cot || n_amps < 1 || n_req < 0 || (n_req > 0 && (!tensor_ids || !env_out)))
             fail(JET_EINVAL, "bad arguments");
         if (net->path.size() + 1 != net->leaves.size()) fail(JET_ESTATE, "no contraction path set");

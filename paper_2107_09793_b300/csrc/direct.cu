@@ -311,39 +311,34 @@ cudaError_t launch_accum(const AccumArgs &a, const LaunchCfg &c, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// amp[b] = sum_{s = 0 .. n_sl-1} root(b, s), in FP64, one thread per amplitude.
+// amp[b][e] = sum_{s = 0 .. n_sl-1} root(b, s)[e], in FP64, one thread per
+// value (e runs over the free open legs, one value when there are none).
 __global__ void slice_reduce_kernel(const __grid_constant__ ReduceArgs a)
 {
     const uint64_t *roots = (const uint64_t *)a.roots;
+    const int64_t *eoff = (const int64_t *)a.eoff;
+    const int64_t es = a.fp64_in ? 16 : 8, ne = a.n_elem;
+    auto load = [&](uint64_t p, int64_t e) {
+        if (ne > 1) p += (uint64_t)(eoff[e] * es);
+        if (a.fp64_in) return *(const double2 *)p;
+        const float2 f = *(const float2 *)p;
+        return make_double2(f.x, f.y);
+    };
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a.partials) {   // per-slice partials, no summation
-        const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= (int64_t)a.n_amps * a.n_slices) return;
-        const uint64_t p = roots[i];
-        double2 v;
-        if (a.fp64_in) v = *(const double2 *)p;
-        else {
-            const float2 f = *(const float2 *)p;
-            v = make_double2(f.x, f.y);
-        }
-        ((double2 *)a.amps)[i] = v;
+        if (i >= (int64_t)a.n_amps * a.n_slices * ne) return;
+        ((double2 *)a.amps)[i] = load(roots[i / ne], i % ne);
         return;
     }
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.n_amps) return;
+    if (i >= (int64_t)a.n_amps * ne) return;
+    const int64_t b = i / ne, e = i % ne;
     double re = 0, im = 0;
     for (int s = 0; s < a.n_slices; ++s) {
-        uint64_t p = roots[(int64_t)b * a.n_slices + s];
-        if (a.fp64_in) {
-            double2 v = *(const double2 *)p;
-            re += v.x;
-            im += v.y;
-        } else {
-            float2 v = *(const float2 *)p;
-            re += (double)v.x;
-            im += (double)v.y;
-        }
+        const double2 v = load(roots[b * a.n_slices + s], e);
+        re += v.x;
+        im += v.y;
     }
-    ((double2 *)a.amps)[b] = make_double2(re, im);
+    ((double2 *)a.amps)[i] = make_double2(re, im);
 }
 
 __global__ void c64_to_c128_kernel(const float2 *src, double2 *dst, int64_t n)
@@ -399,6 +394,7 @@ cudaError_t launch_splitk_reduce(const SplitKReduceArgs &a, const LaunchCfg &c, 
 
 cudaError_t launch_slice_reduce(const ReduceArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
+    if (a.n_elem < 1 || (a.n_elem > 1 && !a.eoff)) return cudaErrorInvalidValue;
     slice_reduce_kernel<<<c.gx, c.block, 0, s>>>(a);
     return cudaGetLastError();
 }

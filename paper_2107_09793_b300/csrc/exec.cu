@@ -300,7 +300,7 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
         }
         arena = net.own_arena;
     }
-    const int64_t n_out_vals = P.partials ? (int64_t)P.n_amps * P.n_slices : P.n_amps;
+    const int64_t n_out_vals = (P.partials ? (int64_t)P.n_amps * P.n_slices : P.n_amps) * P.n_elem;
     if (net.d_amps_cap < n_out_vals) {
         JET_CUDA(cudaStreamSynchronize(s));
         device_free(net.d_amps);

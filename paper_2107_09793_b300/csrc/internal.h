@@ -92,6 +92,7 @@ struct Plan {
 
     // sizes
     int64_t n_slices = 1;
+    int64_t n_elem = 1;              // values per amplitude row (product of the free legs' dims)
     size_t arena_bytes = 0;          // intermediates + scratch (device workspace)
     std::vector<Op> ops;
     std::vector<uint8_t> host_args;   // argument blocks (pointers patched at bind time)
@@ -136,6 +137,8 @@ struct Network {
     std::unordered_map<int64_t, LabelInfo> labels;
     std::vector<int64_t> open;        // declared output legs (order = pattern digit order)
     bool open_set = false;
+    std::vector<int64_t> free_open;   // open legs left unfixed: every value of them per row
+                                      // (order = digit order of the values, first slowest)
     std::vector<std::pair<int32_t, int32_t>> path;
     uint64_t path_version = 0;
     std::vector<int64_t> sliced;

@@ -144,9 +144,12 @@ struct MemsetArgs {
 // amp[b] = sum over slices s (increasing s) of root[inst(b, s)], FP64
 // (Section 2.4, Eq. sliced_sum; the single reduction over slices).
 struct ReduceArgs {
-    uint64_t roots;                 // device array of n_amps * n_slices addresses of scalars
-    uint64_t amps;                  // complex128[n_amps] (or [n_amps][n_slices] partials)
+    uint64_t roots;                 // device array of n_amps * n_slices root-instance addresses
+    uint64_t amps;                  // complex128[n_amps][n_elem] (or [n_amps][n_slices][n_elem] partials)
+    uint64_t eoff;                  // device int64[n_elem]: element offset in a root instance of
+                                    // value e of the free open legs (0 when n_elem == 1)
     int32_t n_amps, n_slices;
     int32_t fp64_in;
     int32_t partials;               // 1: write every root value instead of the sums
+    int32_t n_elem, pad_;           // values per amplitude row
 };

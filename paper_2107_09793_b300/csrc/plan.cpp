@@ -184,7 +184,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
 
     // ---- fixed labels and their values under an assignment alpha = b * n_sl + s
     std::unordered_map<int64_t, int32_t> open_pos, slice_pos;
-    for (int32_t j = 0; j < n_open; ++j) open_pos[net.open[j]] = j;
+    for (int32_t j = 0; j < n_open; ++j)   // free open legs stay in the tensors: every value is computed
+        if (std::find(net.free_open.begin(), net.free_open.end(), net.open[j]) == net.free_open.end())
+            open_pos[net.open[j]] = j;
     std::vector<int64_t> sl_dim, sl_w;
     for (size_t j = 0; j < net.sliced.size(); ++j) {
         slice_pos[net.sliced[j]] = (int32_t)j;
@@ -204,8 +206,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     }
     const int64_t n_sl = slice_ids ? (int64_t)slice_ids->size() : n_sl_all;
     P.n_slices = n_sl;
+    for (int64_t l : net.free_open) P.n_elem *= net.labels.at(l).dim;
     const int64_t n_assign = (int64_t)n_amps * n_sl;
     if (n_assign > (int64_t)1 << 30) fail(JET_EINVAL, "too many (amplitude, slice) assignments");
+    if (n_assign * P.n_elem > (int64_t)1 << 31) fail(JET_EINVAL, "too many output values");
     auto value = [&](int64_t l, int64_t alpha) -> int64_t {
         auto o = open_pos.find(l);
         int64_t b = alpha / n_sl, s = alpha % n_sl;
@@ -1524,30 +1528,51 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     }
 
     // ---- slice / amplitude reduction (Eq. sliced_sum), FP64, slices in increasing order
+    // every root instance holds the free open legs (a scalar when there are none)
     const int32_t root = n_nodes - 1;
-    if (!node[root].view.labels.empty()) fail(JET_EINVAL, "the network has undeclared open legs");
+    const View &RV = node[root].view;
+    if (RV.labels.size() != net.free_open.size()) fail(JET_EINVAL, "the network has undeclared open legs");
     {
         std::vector<std::pair<int32_t, int64_t>> roots;
         roots.reserve(n_assign);
         for (int64_t x = 0; x < n_assign; ++x) roots.push_back(base_ref(root, inst_of[root][x]));
         size_t off_roots = blob.put_ptrs(roots);
+        // value e of the free legs (mixed radix, first free leg slowest) -> element offset
+        std::vector<int64_t> eoff((size_t)P.n_elem, 0);
+        for (int64_t e = 0; e < P.n_elem; ++e) {
+            int64_t x = e;
+            for (int j = (int)net.free_open.size() - 1; j >= 0; --j) {
+                const int p = find_pos(RV.labels, net.free_open[j]);
+                if (p < 0) fail(JET_EINVAL, "free open leg missing from the result");
+                const int64_t dm = RV.dims[p];
+                eoff[(size_t)e] += (x % dm) * RV.strides[p];
+                x /= dm;
+            }
+        }
+        size_t off_eoff = 0;
+        if (P.n_elem > 1) {
+            off_eoff = blob.reserve(eoff.size() * sizeof(int64_t));
+            std::memcpy(blob.bytes.data() + off_eoff, eoff.data(), eoff.size() * sizeof(int64_t));
+        }
         ReduceArgs r;
         std::memset(&r, 0, sizeof r);
         r.n_amps = n_amps;
         r.n_slices = (int32_t)n_sl;
         r.partials = P.partials ? 1 : 0;
         r.fp64_in = fp64 ? 1 : 0;
+        r.n_elem = (int32_t)P.n_elem;
         size_t ro = blob.reserve(sizeof r);
         std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
         blob.patch_field(ro, offsetof(ReduceArgs, roots), BASE_BLOB, (int64_t)off_roots);
         blob.patch_field(ro, offsetof(ReduceArgs, amps), BASE_AMPS, 0);
+        if (P.n_elem > 1) blob.patch_field(ro, offsetof(ReduceArgs, eoff), BASE_BLOB, (int64_t)off_eoff);
         Op op;
         op.kind = OpKind::Reduce;
         op.node = root;
         op.n_inst = n_amps;
         op.args_off = ro;
         op.args_bytes = sizeof r;
-        op.grid_x = (int32_t)(((P.partials ? n_assign : n_amps) + 127) / 128);
+        op.grid_x = (int32_t)(((P.partials ? n_assign : n_amps) * P.n_elem + 127) / 128);
         op.block = 128;
         P.ops.push_back(op);
     }

@@ -82,8 +82,10 @@ Tree build_tree(const Network &net, const std::vector<std::pair<int32_t, int32_t
 static std::unordered_set<int64_t> fixed_set(const Network &net, const std::vector<int64_t> &extra)
 {
     std::unordered_set<int64_t> f(extra.begin(), extra.end());
-    for (auto &kv : net.labels)
-        if (kv.second.n_owner == 1) f.insert(kv.first);  // open legs: fixed by every amplitude
+    for (auto &kv : net.labels)   // open legs: fixed by every amplitude, unless left free
+        if (kv.second.n_owner == 1 &&
+            std::find(net.free_open.begin(), net.free_open.end(), kv.first) == net.free_open.end())
+            f.insert(kv.first);
     return f;
 }
 
@@ -679,7 +681,9 @@ std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_
         batch.n_amps = n_amps;
         batch.n_out = (int32_t)net.open.size();
         batch.outputs = outputs;
-        for (int32_t j = 0; j < batch.n_out; ++j) batch.digit[net.open[j]] = j;
+        for (int32_t j = 0; j < batch.n_out; ++j)   // free open legs are not restricted by the rows
+            if (std::find(net.free_open.begin(), net.free_open.end(), net.open[j]) == net.free_open.end())
+                batch.digit[net.open[j]] = j;
         bt = &batch;
     }
     const double cap = max_elems > 0 ? max_elems : INFINITY;

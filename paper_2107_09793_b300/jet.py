@@ -21,7 +21,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_path_greedy", "jet_path_greedy_batch", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
-           "jet_contract_slices"]
+           "jet_contract_slices", "jet_network_set_free"]
 
 
 class JetError(RuntimeError):
@@ -76,6 +76,7 @@ def lib():
             "jet_options_default": (None, [P]),
             "jet_network_create": (I32, [P, I32, P, P]),
             "jet_network_set_open": (I32, [P, I32, P]),
+            "jet_network_set_free": (I32, [P, I32, P]),
             "jet_tensor_update": (I32, [P, I32, P]),
             "jet_tensors_upload": (I32, [P, P, P]),
             "jet_network_n_values": (I64, [P]),
@@ -131,6 +132,7 @@ class Network:
                  **opt_kwargs):
         L = lib()
         self._keep = []
+        self._dims = {}
         n = len(data)
         descs = (TensorDesc * n)()
         self.shapes = []
@@ -146,6 +148,8 @@ class Network:
             descs[i].dims = di.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
             descs[i].data = t.ctypes.data
             self.shapes.append(t.shape)
+            for l, d in zip(la.tolist(), t.shape):
+                self._dims[l] = d
         opts = options if options is not None else default_options(**opt_kwargs)
         h = ctypes.c_void_p()
         _check(L.jet_network_create(descs, n, ctypes.byref(opts), ctypes.byref(h)))
@@ -153,6 +157,7 @@ class Network:
         self._keep = []
         self.n_tensors = n
         self.n_out = 0
+        self.n_elem = 1   # values per amplitude row (product of the free open legs' dims)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -173,6 +178,14 @@ class Network:
         a = np.ascontiguousarray(np.asarray(out_labels, dtype=np.int64))
         _check(lib().jet_network_set_open(self._h, a.size, a.ctypes.data))
         self.n_out = a.size
+        self.n_elem = 1
+
+    def set_free(self, free_labels: Sequence[int]):
+        """jet_network_set_free: these open legs stay unfixed; every contraction
+        returns all their values per row (last axis, first free leg slowest)."""
+        a = np.ascontiguousarray(np.asarray(free_labels, dtype=np.int64))
+        _check(lib().jet_network_set_free(self._h, a.size, a.ctypes.data))
+        self.n_elem = int(np.prod([self._dims[int(l)] for l in a])) if a.size else 1
 
     def update(self, tensor_id: int, data: np.ndarray):
         t = np.ascontiguousarray(data, dtype=np.complex64)
@@ -237,15 +250,16 @@ class Network:
 
     def contract(self, outputs, stream: int = 0) -> np.ndarray:
         o = self._outputs(outputs)
-        amps = np.zeros(o.shape[0], dtype=np.complex128)
+        amps = np.zeros(o.shape[0] * self.n_elem, dtype=np.complex128)
         _check(lib().jet_contract(self._h, o.shape[0], o.ctypes.data, amps.ctypes.data, ctypes.c_void_p(stream)))
-        return amps
+        return amps if self.n_elem == 1 else amps.reshape(o.shape[0], self.n_elem)
 
     def contract_slices(self, outputs, slice_ids, stream: int = 0) -> np.ndarray:
-        """Per-slice partials, shape (n_amps, len(slice_ids))."""
+        """Per-slice partials, shape (n_amps, len(slice_ids)) (with free legs: a
+        last axis of their values)."""
         o = self._outputs(outputs)
         ids = np.ascontiguousarray(np.asarray(slice_ids, dtype=np.int64))
-        out = np.zeros((o.shape[0], ids.size), dtype=np.complex128)
+        out = np.zeros((o.shape[0], ids.size) + ((self.n_elem,) if self.n_elem > 1 else ()), dtype=np.complex128)
         _check(lib().jet_contract_slices(self._h, o.shape[0], o.ctypes.data, ids.size, ids.ctypes.data,
                                          out.ctypes.data, ctypes.c_void_p(stream)))
         return out

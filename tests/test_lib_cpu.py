@@ -304,3 +304,30 @@ def test_planner_is_flop_optimal_on_networks_of_ten_tensors():
         f = net.path_greedy(seed=trial, n_trials=2)
         cap = net.stats()["max_intermediate"]
         assert f == _optimal_flop_brute(labels, dims, cap), trial
+
+
+def test_free_open_legs_arguments_and_planning():
+    """jet_network_set_free: argument errors, and the planners count a free leg
+    with its dim (a fixed open leg counts as 1), so freeing legs raises the
+    planned FLOP; the plan of a free-leg network builds without a GPU."""
+    from circuits import configs
+    w = configs.build("grid12")
+    net = jet.from_network(w.network)
+    opens = w.network.open_labels
+    with pytest.raises(jet.JetError):
+        net.set_free([12345])                      # not an open leg
+    with pytest.raises(jet.JetError):
+        net.set_free([opens[0], opens[0]])         # listed twice
+    f_fixed = net.path_greedy(seed=1, n_trials=4)
+    net.set_free(opens[:6])
+    assert net.n_elem == 64
+    f_free = net.path_greedy(seed=1, n_trials=4)
+    assert f_free > f_fixed
+    net.plan(np.zeros((2, 12), np.int32))
+    net.set_free([])
+    assert net.n_elem == 1
+    closed = jet.Network([[0, 1], [1, 0]], [np.eye(2, dtype=np.complex64)] * 2)
+    with pytest.raises(jet.JetError):
+        closed.set_free([0])                       # open legs not declared (none exist)
+    net.close()
+    closed.close()
