@@ -190,8 +190,8 @@ def run_other_workloads(dev, peaks, peak_src):
     the 16-mode d=4 bosonic lattice batch (256 patterns), the 20-qubit
     parameterised circuit's 64-amplitude forward + adjoint, a measured
     fraction of the 53-qubit grid's slices (its full slice set is far too long
-    to run), and grid30 with 4 output legs left open (16 amplitudes per
-    contraction)."""
+    to run), grid30 with 4 output legs left open (16 amplitudes per
+    contraction), a 3-D bosonic lattice and the 8x8 lattice at Fock cutoff 8."""
     import torch
     from circuits import configs
     from paper_2107_09793_b300 import jet
@@ -326,6 +326,38 @@ def run_other_workloads(dev, peaks, peak_src):
                            "path": "library greedy, 256 trials, seed 1, free legs counted; slice finder to 2^24",
                            "planner_s": t_plan, "rel_err_vs_stored_amplitude": abs(v[e] - ref) / abs(ref),
                            "timing": "CUDA events, mean of 5 after a warm-up (L2 not flushed)"}
+
+    # 3-D lattice (Algorithm 1, dim 3) and the 8x8 lattice at Fock cutoff 8
+    for name in ("gbs3d", "gbs88d8"):
+        w = configs.build(name)
+        per = {}
+        for prec in ("fp32", "fp16x3"):
+            net = jet.from_network(w.network, precision=prec, device=dev)
+            t0 = time.perf_counter()
+            if len(w.outputs) > 1:   # (8 trials find no path under the cap on this lattice)
+                net.path_greedy_batch(w.outputs, seed=1, n_trials=16, max_elems=1 << 30)
+            else:
+                net.path_greedy(seed=1, n_trials=64)
+            t_plan = time.perf_counter() - t0
+            vals = torch.zeros(len(w.outputs), dtype=torch.complex128, device="cuda")
+            run = lambda: net.contract_async(w.outputs, vals.data_ptr(), sh)
+            run()
+            torch.cuda.synchronize()
+            ms = _timed(run, stream, ev0, ev1, 3)
+            st = net.stats()
+            per[prec] = {"ms_per_batch": statistics.mean(ms),
+                         "amplitudes_per_s": len(w.outputs) / (statistics.mean(ms) * 1e-3),
+                         "flop": st["flop_executed"], "tflops": st["flop_executed"] / (statistics.mean(ms) * 1e-3) / 1e12,
+                         "workspace_gb": st["workspace_bytes"] / 1e9, "planner_s": t_plan}
+            net.close()
+        res[name] = {"workload": {"gbs3d": "18 modes on a 2x3x3 lattice (Algorithm 1, dim 3), Fock cutoff 4, "
+                                           "2 beamsplitter layers, 16 seeded patterns in one batch",
+                                  "gbs88d8": "64 modes on an 8x8 lattice, Fock cutoff 8, one beamsplitter layer, "
+                                             "r = 0.5, one pattern with every mode in [0, 4)"}[name],
+                     "path": "batch planner, 16 trials, weighted cap 2^30" if len(w.outputs) > 1
+                     else "library greedy, 64 trials", "modes": per,
+                     "parity": "tests/test_gpu_gbs_nd.py (low photon totals vs the per-sector state vector)",
+                     "timing": "CUDA events, mean of 3 after a warm-up"}
     return res
 
 

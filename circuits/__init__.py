@@ -11,13 +11,13 @@ from .rng import SplitMix64
 from .rqc import (Circuit, Gate, grid_layout, coupler_layers, random_grid_circuit,
                   param_grid_circuit, fsim, sqrt_x, sqrt_y, sqrt_w, rz, ry, rzry,
                   random_bitstrings)
-from .gbs import gbs_lattice_circuit, squeezed_vacuum, beamsplitter, random_patterns
+from .gbs import gbs_lattice_circuit, gbs_nd_circuit, squeezed_vacuum, beamsplitter, random_patterns
 from .network import TensorNetwork, circuit_to_network
 from . import configs
 
 __all__ = [
     "SplitMix64", "Circuit", "Gate", "grid_layout", "coupler_layers",
     "random_grid_circuit", "param_grid_circuit", "fsim", "sqrt_x", "sqrt_y", "sqrt_w",
-    "rz", "ry", "rzry", "random_bitstrings", "gbs_lattice_circuit", "squeezed_vacuum",
+    "rz", "ry", "rzry", "random_bitstrings", "gbs_lattice_circuit", "gbs_nd_circuit", "squeezed_vacuum",
     "beamsplitter", "random_patterns", "TensorNetwork", "circuit_to_network", "configs",
 ]

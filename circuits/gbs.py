@@ -1,6 +1,7 @@
-"""Random 2-D Gaussian-boson-sampling lattice in a truncated Fock basis
-(Algorithm 1 of Section 4 with dim = 2), a bosonic qudit network with every
-index of dimension d (the Fock cutoff).
+"""Random Gaussian-boson-sampling lattices in a truncated Fock basis
+(Algorithm 1 of Section 4; dim = 2 for the 2-D lattice, any dim for
+gbs_nd_circuit), bosonic qudit networks with every index of dimension d (the
+Fock cutoff).
 
 Readings of what the paper leaves open:
   * Squeezed vacuum S(r)|0>, squeezing phase 0, truncated at d and NOT
@@ -13,6 +14,11 @@ Readings of what the paper leaves open:
   * Only true lattice neighbours are coupled: per cycle the horizontal bonds
     (r,c)-(r,c+1) in increasing mode order, then the vertical bonds
     (r,c)-(r+1,c).  theta ~ U[0, pi/2], phi ~ U[0, 2 pi), r ~ U[0.5, 1.0].
+  * n dimensions (Algorithm 1's llens[l] = width^(l-1) strides): modes are
+    numbered in mixed radix over the lattice shape, last axis fastest; per cycle
+    the bonds along the fastest axis (stride 1), then along each slower axis in
+    turn, each in increasing mode order, true neighbours only.  For a 2-D shape
+    this is the 2-D lattice above, draw for draw.
 """
 import math
 from typing import Tuple
@@ -74,6 +80,30 @@ def gbs_lattice_circuit(rows: int, cols: int, d: int, layers: int, seed: int,
             th = rng.uniform_range(*theta_range)
             ph = rng.uniform_range(*phi_range)
             circ.gates.append(Gate(beamsplitter(th, ph, d), (a, b), (th, ph), kind="bs"))
+    return circ
+
+
+def gbs_nd_circuit(shape: Tuple[int, ...], d: int, layers: int, seed: int,
+                   r_range: Tuple[float, float] = (0.5, 1.0),
+                   theta_range: Tuple[float, float] = (0.0, math.pi / 2),
+                   phi_range: Tuple[float, float] = (0.0, 2 * math.pi)) -> Circuit:
+    shape = tuple(int(w) for w in shape)
+    n = int(np.prod(shape))
+    strides = [int(np.prod(shape[a + 1:])) for a in range(len(shape))]
+    coords = [tuple((i // strides[a]) % shape[a] for a in range(len(shape))) for i in range(n)]
+    rng = SplitMix64(seed)
+    circ = Circuit(n=n, d=d, sites=coords)
+    rs = [rng.uniform_range(*r_range) for _ in range(n)]
+    circ.initial = [squeezed_vacuum(r, d) for r in rs]
+    circ.squeezing = rs
+    bonds = []
+    for a in reversed(range(len(shape))):   # fastest axis first
+        bonds += [(i, i + strides[a]) for i in range(n) if coords[i][a] < shape[a] - 1]
+    for _ in range(layers):
+        for (p, q) in bonds:
+            th = rng.uniform_range(*theta_range)
+            ph = rng.uniform_range(*phi_range)
+            circ.gates.append(Gate(beamsplitter(th, ph, d), (p, q), (th, ph), kind="bs"))
     return circ
 
 

@@ -10,7 +10,7 @@ import oracle
 from oracle.einsum import contract_network, greedy_path, network_flops, slice_network
 from circuits import (Circuit, Gate, circuit_to_network, configs, fsim, sqrt_x, sqrt_y,
                       sqrt_w, random_grid_circuit, param_grid_circuit, gbs_lattice_circuit,
-                      random_bitstrings, SplitMix64)
+                      gbs_nd_circuit, random_bitstrings, SplitMix64)
 from circuits.rqc import gate_with_params, gate_param_derivs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -393,3 +393,33 @@ def test_sector_oracle_full_lattice_vacuum_and_parity():
     a = oracle.sector_amplitudes(circ, [[0] * 16, [1] + [0] * 15, [1, 2] + [0] * 14])
     assert abs(a[0] - ref) < 1e-14
     assert a[1] == 0 and a[2] == 0
+
+
+def test_nd_lattice_generator_reduces_to_2d_and_counts_bonds():
+    """Algorithm 1 in n dimensions: for a 2-D shape the n-D generator is the 2-D
+    lattice draw for draw (same squeezers, bonds, angles); a w0 x w1 x w2
+    lattice has sum_a (w_a - 1) * n / w_a bonds per layer, each joining modes
+    whose coordinates differ by one along one axis."""
+    a, b = gbs_lattice_circuit(3, 4, 4, 2, seed=7), gbs_nd_circuit((3, 4), 4, 2, seed=7)
+    assert [g.qubits for g in a.gates] == [g.qubits for g in b.gates]
+    assert all(np.array_equal(g.matrix, h.matrix) for g, h in zip(a.gates, b.gates))
+    assert all(np.array_equal(x, y) for x, y in zip(a.initial, b.initial))
+    c = gbs_nd_circuit((2, 3, 4), 3, 2, seed=9)
+    n = 24
+    per_layer = sum((w - 1) * n // w for w in (2, 3, 4))
+    assert len(c.gates) == 2 * per_layer
+    for g in c.gates:
+        p, q = g.qubits
+        diff = [abs(x - y) for x, y in zip(c.sites[p], c.sites[q])]
+        assert sorted(diff) == [0, 0, 1]
+
+
+def test_sector_oracle_on_a_3d_lattice_every_pattern():
+    """The per-sector state vector equals the dense one on all 3^8 patterns of
+    a 2x2x2 lattice at cutoff 3 (bonds along all three axes)."""
+    from itertools import product as iproduct
+    circ = gbs_nd_circuit((2, 2, 2), 3, 2, seed=31)
+    pats = np.array(list(iproduct(range(3), repeat=8)), np.int32)
+    got = oracle.sector_amplitudes(circ, pats)
+    ref = oracle.sv_amplitudes(circ, pats)
+    assert np.max(np.abs(got - ref)) < 1e-14
