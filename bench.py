@@ -270,32 +270,68 @@ def run_other_workloads(dev, peaks, peak_src):
                       "n_gate_tensors": len(ids), "flop_forward": st["flop_executed"], "precision": "fp32",
                       "timing": "host wall clock through the C ABI (host buffers), median of 3"}
 
-    # 53-qubit grid: library greedy + slicing to 2^28, a measured fraction of the slices
+    # 53-qubit grid: library greedy + slicing to 2^28 + the slice-aware reconfiguration
+    # (Eq. task_based_amplitude_flops); the whole amplitude runs as consecutive
+    # slice-id ranges (each range's shared intermediates computed once), the largest
+    # range size whose workspace fits the free device memory, one workspace shared
+    # by the ranges' handles
     w = configs.build("grid53")
     net = jet.from_network(w.network, precision="fp16x3", device=dev)
+    t0 = time.perf_counter()
     net.path_greedy(seed=1, n_trials=512)
     sl = net.slice_auto(1 << 28, min_n=0, max_n=60)
+    f_before, f_after = net.path_reconfigure(8)
+    t_plan = time.perf_counter() - t0
     st = net.stats()
-    ids = [0, 1]
-    per = {}
+    n_sl = st["n_slices"]
+    path = net.path_get()
+    net.close()
+    per, amps_all, ranges_used = {}, {}, {}
     for prec in ("fp16x3", "fp32"):
-        nm = jet.from_network(w.network, precision=prec, device=dev)
-        nm.path_set(net.path_get())
-        nm.slice(sl)
-        nm.contract_slices(w.outputs, ids)
+        free = torch.cuda.mem_get_info()[0]
+        probe = jet.from_network(w.network, precision=prec, device=dev)
+        probe.path_set(path)
+        probe.slice(sl)
+        R = n_sl
+        while R > 1 and probe.plan_slices(w.outputs, list(range(R))) > 0.85 * free:
+            R //= 2
+        probe.close()
+        nets, nbytes, flop = [], [], 0.0
+        for k in range(n_sl // R):
+            nk = jet.from_network(w.network, precision=prec, device=dev)
+            nk.path_set(path)
+            nk.slice(sl)
+            nbytes.append(nk.plan_slices(w.outputs, list(range(k * R, (k + 1) * R))))
+            flop += nk.stats()["flop_executed"]
+            nets.append(nk)
+        ws = torch.empty(max(nbytes), dtype=torch.uint8, device="cuda")
+        for nk in nets:
+            nk.set_workspace(ws.data_ptr(), ws.numel())
+        run = lambda: [nk.contract_slices(w.outputs, list(range(k * R, (k + 1) * R))) for k, nk in enumerate(nets)]
+        run()   # first pass: uploads, graph capture
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        nm.contract_slices(w.outputs, ids)
-        per[prec] = 1e3 * (time.perf_counter() - t0) / len(ids)
-        nm.close()
-    net.close()
-    res["grid53"] = {"workload": "53-qubit 9x6 grid minus one corner, 12 cycles, one amplitude",
-                     "path": "library greedy, 512 trials, seed 1", "sliced_labels": len(sl), "n_slices": st["n_slices"],
-                     "max_intermediate": st["max_intermediate"], "flop_per_slice": st["flop_sliced"] / st["n_slices"],
-                     "ms_per_slice": per, "measured_slices": len(ids),
-                     "measured_fraction": len(ids) / st["n_slices"],
-                     "implied_amplitude_s": {k: v * 1e-3 * st["n_slices"] for k, v in per.items()},
-                     "timing": "host wall clock of jet_contract_slices over 2 slices (second call), per slice"}
+        parts = run()
+        t_amp = time.perf_counter() - t0
+        amp = complex(sum(p[0].sum() for p in parts))   # slices in increasing id order, FP64
+        for nk in nets:
+            nk.close()
+        del ws
+        torch.cuda.empty_cache()
+        per[prec] = {"amplitude_s": t_amp, "tflops": flop / t_amp / 1e12, "flop": flop, "ranges": n_sl // R,
+                     "slices_per_range": R, "workspace_gb": max(nbytes) / 1e9}
+        amps_all[prec] = [amp.real, amp.imag]
+    res["grid53"] = {"workload": "53-qubit 9x6 grid minus one corner, 12 cycles, one amplitude (all slices)",
+                     "path": "library greedy, 512 trials, seed 1; slice finder to 2^28; slice-aware sub-tree "
+                             "reconfiguration (8 passes)",
+                     "sliced_labels": len(sl), "n_slices": n_sl, "max_intermediate": st["max_intermediate"],
+                     "flop_whole_amplitude_reuse": f_after, "flop_before_reconfiguration": f_before,
+                     "flop_per_slice_no_reuse": st["flop_sliced"] / n_sl, "planner_s": t_plan,
+                     "modes": per, "amplitude": amps_all,
+                     "fp16x3_vs_fp32": abs(complex(*amps_all["fp16x3"]) - complex(*amps_all["fp32"]))
+                     / abs(complex(*amps_all["fp32"])),
+                     "timing": "host wall clock of the whole amplitude (every slice range through "
+                               "jet_contract_slices, second pass)"}
 
     # open-leg batch: grid30 with its last 4 output legs left free, 16 amplitudes per
     # contraction of the benchmark bitstring's other 26 digits; path and slicing
@@ -587,7 +623,7 @@ def run_impl(args):
         "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_slices": st["n_slices"], "sliced_labels": sliced,
-                   "path": f"library greedy, {PATH_TRIALS} trials, seed {PATH_SEED}",
+                   "path": f"library greedy, {PATH_TRIALS} trials, seed {PATH_SEED}; slice finder",
                    "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                    "launch": "one CUDA graph per step"},
         "tflops": st["flop_executed"] / (total_s / args.steps) / 1e12 * world,

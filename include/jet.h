@@ -225,6 +225,22 @@ int jet_path_greedy(jet_network *net, uint64_t seed, int32_t n_trials, double *f
 int jet_path_greedy_batch(jet_network *net, int32_t n_amps, const int32_t *outputs, int64_t max_elems,
                           uint64_t seed, int32_t n_trials, double *flop_out);
 
+/* Improve the current path for its current slicing (Section 3.2: minimise
+ * Eq. task_based_amplitude_flops itself rather than the FLOP of one slice).
+ * Every node's FLOP counts once per distinct assignment of the sliced labels
+ * under it, and once per distinct restriction of the batch rows to the open
+ * legs under it when outputs lists n_amps > 1 rows (NULL: one amplitude);
+ * every sub-tree is opened down to at most 10 tensors and re-ordered optimally
+ * by dynamic programming over subsets, `passes` times over the tree, and no
+ * intermediate of one slice (times its batch instances) may grow above the
+ * current path's largest, so the slicing stays valid.  The path is replaced
+ * only when that cost falls.  flop_before / flop_after (may be NULL): the cost
+ * before and after.
+ * Errors: JET_ESTATE (no path, or a batch without declared open legs),
+ * JET_EINVAL (passes outside [1, 64], digit out of range). */
+int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t n_amps, const int32_t *outputs,
+                         double *flop_before, double *flop_after);
+
 /* Slice the given closed labels (Section 2.4); n = 0 clears the slicing.
  * Slice id s is the mixed-radix number over the sliced labels, the first label
  * most significant.  Errors: JET_EINVAL (open or unknown label, duplicate). */
@@ -279,6 +295,12 @@ int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,
  * keeps the memory alive until the handle is destroyed or another workspace is
  * set.  Without a workspace the library allocates one itself. */
 int jet_plan(jet_network *net, int32_t n_amps, const int32_t *outputs, size_t *bytes_out);
+/* jet_plan for the plan jet_contract_slices runs with the same arguments (only
+ * the listed slice ids, their shared intermediates computed once): builds and
+ * keeps it, and writes the workspace bytes it needs.  Errors as
+ * jet_contract_slices. */
+int jet_plan_slices(jet_network *net, int32_t n_amps, const int32_t *outputs, int32_t n_ids,
+                    const int64_t *slice_ids, size_t *bytes_out);
 int jet_set_workspace(jet_network *net, void *dptr, size_t bytes);
 
 /* Adjoint (environment) contraction; not in the paper.

@@ -303,6 +303,37 @@ int jet_path_greedy_batch(jet_network *net, int32_t n_amps, const int32_t *outpu
     });
 }
 
+int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t n_amps, const int32_t *outputs,
+                         double *flop_before, double *flop_after)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (net->path.size() + 1 != net->leaves.size()) fail(JET_ESTATE, "no contraction path set");
+        if (passes < 1 || passes > 64) fail(JET_EINVAL, "passes must be in [1, 64]");
+        if (outputs && n_amps > 1) {
+            if (!net->open_set) fail(JET_ESTATE, "open legs not declared (jet_network_set_open)");
+            const int32_t n_open = (int32_t)net->open.size();
+            for (int32_t b = 0; b < n_amps; ++b)
+                for (int32_t j = 0; j < n_open; ++j) {
+                    const int32_t v = outputs[(int64_t)b * n_open + j];
+                    if (v < 0 || v >= net->labels.at(net->open[j]).dim)
+                        fail(JET_EINVAL, "output digit out of range at amplitude " + std::to_string(b));
+                }
+        }
+        double f0 = 0, f1 = 0;
+        auto p = reconfigure_sliced(*net, passes, n_amps, outputs, &f0, &f1);
+        validate_path(*net, p);
+        if (f1 < f0) {
+            net->path = p;
+            ++net->path_version;
+            net->flop_planned = path_cost(*net, p, {}).flop;
+            invalidate_plan(*net);
+        }
+        if (flop_before) *flop_before = f0;
+        if (flop_after) *flop_after = f1;
+    });
+}
+
 int jet_slice(jet_network *net, int32_t n, const int64_t *labels)
 {
     return guarded([&] {
@@ -347,6 +378,17 @@ int jet_plan(jet_network *net, int32_t n_amps, const int32_t *outputs, size_t *b
     return guarded([&] {
         if (!net) fail(JET_EINVAL, "net is NULL");
         Plan &P = get_plan(*net, n_amps, outputs);
+        if (bytes_out) *bytes_out = P.arena_bytes;
+    });
+}
+
+int jet_plan_slices(jet_network *net, int32_t n_amps, const int32_t *outputs, int32_t n_ids,
+                    const int64_t *slice_ids, size_t *bytes_out)
+{
+    return guarded([&] {
+        if (!net || !slice_ids || n_ids < 1) fail(JET_EINVAL, "bad arguments");
+        std::vector<int64_t> ids(slice_ids, slice_ids + n_ids);
+        Plan &P = get_plan(*net, n_amps, outputs, &ids);
         if (bytes_out) *bytes_out = P.arena_bytes;
     });
 }

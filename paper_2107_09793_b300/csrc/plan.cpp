@@ -306,6 +306,48 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         sibling[b] = a;
     }
 
+    // Small-operand application route: the small operand holds at most
+    // JET_APPLY_MAXK summed and JET_APPLY_MAXF free entries (at most
+    // JET_APPLY_MAXB in all) and the large one has enough fibers to fill the GPU.
+    // free labels of a view: those not summed
+    auto free_of = [&](const View &V, const std::vector<int64_t> &K) {
+        std::vector<int64_t> f;
+        for (int64_t l : V.labels)
+            if (find_pos(K, l) < 0) f.push_back(l);
+        return f;
+    };
+    // tensor-core form (split modes), for small operands of at least
+    // apply_tc_min_kf entries (where the CUDA-core forms run out of FMA issue
+    // slots before HBM bandwidth): thread groups per CTA that fit the operand
+    // planes in shared memory (three for one chunk of summed entries, else
+    // two), 0 when the form does not apply
+    auto apply_tc_groups = [&](int64_t nk, int64_t nf) -> int {
+        if (!tc_mode || fp64 || nk * nf < net.opt.apply_tc_min_kf || nk > JET_APPLY_MAXK || nf < 1 ||
+            nf > JET_APPLY_TC_MAXF)
+            return 0;
+        if (nk <= 32 && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 3;
+        if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
+        return 0;
+    };
+    auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big,
+                              int64_t n_inst) {
+        const View &VS = a_big ? VB : VA, &VL = a_big ? VA : VB;
+        const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
+        const int64_t nk = dimprod(K), nf = dimprod(fs), nfib = dimprod(fl);
+        int64_t nk2 = 1;   // the kernel's compile-time summed extent (power of two >= nk)
+        while (nk2 < nk) nk2 *= 2;
+        // held in registers: up to 16 summed entries (complex128 too), or 32 (complex64)
+        const bool held = nk <= (fp64 ? 16 : JET_APPLY_HOLDK) && nk2 * nf <= JET_APPLY_MAXB;
+        const int64_t nfp = nf <= 4 ? nf : (nf + 15) / 16 * 16;
+        const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF &&
+                              (nf <= 4 || nk * nfp <= JET_APPLY_STREAMB);
+        const bool tc = apply_tc_groups(nk, nf) > 0;
+        return nk >= 1 && (held || streamed || tc) && nf <= JET_APPLY_MAXF && nfib * n_inst >= (1 << 15) &&
+               (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
+    };
+    auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
+        return apply_ok_views(VA, VB, N.K, N.a_big, N.n_inst);
+    };
     // The summed labels of v's parent when the parent applies a small operand
     // (at most 2048 entries, not the GEMM route) to v as its large operand:
     // laying them out slowest in v lets the parent read, for each summed
@@ -368,6 +410,12 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             if (find_pos(VA.labels, l) < 0) N.fb.push_back(l);
         const int64_t nK = dimprod(N.K), nFa = dimprod(N.fa), nFb = dimprod(N.fb);
         N.use_gemm = gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64;
+        // a skinny product (one free side of 8..63 entries, the other large) that no
+        // small-operand form takes: the GEMM route with partly filled tiles still runs
+        // far faster than the strided direct contraction
+        if (!N.use_gemm && gemm_ok && nK >= net.opt.gemm_min_k && std::min(nFa, nFb) >= 8 &&
+            std::max(nFa, nFb) >= 4096 && !apply_ok_views(VA, VB, N.K, VA.size >= VB.size, N.n_inst))
+            N.use_gemm = true;
 
         // output layout
         std::vector<int64_t> out;
@@ -826,48 +874,6 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             }
     };
 
-    // Small-operand application route: the small operand holds at most
-    // JET_APPLY_MAXK summed and JET_APPLY_MAXF free entries (at most
-    // JET_APPLY_MAXB in all) and the large one has enough fibers to fill the GPU.
-    // free labels of a view: those not summed
-    auto free_of = [&](const View &V, const std::vector<int64_t> &K) {
-        std::vector<int64_t> f;
-        for (int64_t l : V.labels)
-            if (find_pos(K, l) < 0) f.push_back(l);
-        return f;
-    };
-    // tensor-core form (split modes), for small operands of at least
-    // apply_tc_min_kf entries (where the CUDA-core forms run out of FMA issue
-    // slots before HBM bandwidth): thread groups per CTA that fit the operand
-    // planes in shared memory (three for one chunk of summed entries, else
-    // two), 0 when the form does not apply
-    auto apply_tc_groups = [&](int64_t nk, int64_t nf) -> int {
-        if (!tc_mode || fp64 || nk * nf < net.opt.apply_tc_min_kf || nk > JET_APPLY_MAXK || nf < 1 ||
-            nf > JET_APPLY_TC_MAXF)
-            return 0;
-        if (nk <= 32 && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 3;
-        if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
-        return 0;
-    };
-    auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big,
-                              int64_t n_inst) {
-        const View &VS = a_big ? VB : VA, &VL = a_big ? VA : VB;
-        const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
-        const int64_t nk = dimprod(K), nf = dimprod(fs), nfib = dimprod(fl);
-        int64_t nk2 = 1;   // the kernel's compile-time summed extent (power of two >= nk)
-        while (nk2 < nk) nk2 *= 2;
-        // held in registers: up to 16 summed entries (complex128 too), or 32 (complex64)
-        const bool held = nk <= (fp64 ? 16 : JET_APPLY_HOLDK) && nk2 * nf <= JET_APPLY_MAXB;
-        const int64_t nfp = nf <= 4 ? nf : (nf + 15) / 16 * 16;
-        const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF &&
-                              (nf <= 4 || nk * nfp <= JET_APPLY_STREAMB);
-        const bool tc = apply_tc_groups(nk, nf) > 0;
-        return nk >= 1 && (held || streamed || tc) && nf <= JET_APPLY_MAXF && nfib * n_inst >= (1 << 15) &&
-               (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
-    };
-    auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
-        return apply_ok_views(VA, VB, N.K, N.a_big, N.n_inst);
-    };
     auto emit_apply = [&](int32_t v, const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K,
                           bool a_big, int64_t n_inst, const std::vector<std::pair<int32_t, int64_t>> &pa,
                           const std::vector<std::pair<int32_t, int64_t>> &pb,

@@ -470,20 +470,29 @@ static std::vector<std::pair<int32_t, int32_t>> leaf_order_linear(const Network 
 // dynamic programming over its subsets, and substitute it when it lowers the
 // (instance-weighted) FLOP without creating an intermediate above max_size.
 // Repeated for a few passes over the tree.  Returns the new path.
+// sliced (optional): labels fixed per slice.  A node's cost is then counted
+// once per distinct assignment of the sliced labels under it (Eq.
+// task_based_amplitude_flops) and its size is that of one slice; max_size caps
+// the size of one slice's intermediate (times its batch instances).
 static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
                                                             const std::vector<std::pair<int32_t, int32_t>> &path,
-                                                            BatchInstances *bt, int passes, int k, double max_size)
+                                                            BatchInstances *bt, int passes, int k, double max_size,
+                                                            const std::vector<int64_t> &sliced = {})
 {
-    auto fixed = fixed_set(net, {});
+    auto fixed = fixed_set(net, sliced);
+    std::unordered_set<int64_t> slset(sliced.begin(), sliced.end());
     const int32_t n = (int32_t)net.leaves.size();
     if (path.size() < 2) return path;
     const int32_t n_nodes = n + (int32_t)path.size();
     std::vector<std::array<int32_t, 2>> ch(n_nodes, {-1, -1});
     std::vector<std::vector<int64_t>> lab(n_nodes);
     std::vector<std::vector<int32_t>> opos(n_nodes);
+    std::vector<std::vector<int64_t>> slu(n_nodes);   // sliced labels under each node (sorted)
     for (int32_t i = 0; i < n; ++i) {
         lab[i] = net.leaves[i].labels;
         std::sort(lab[i].begin(), lab[i].end());
+        for (int64_t l : lab[i])
+            if (slset.count(l)) slu[i].push_back(l);
         if (bt)
             for (int64_t l : lab[i]) {
                 auto it = bt->digit.find(l);
@@ -505,10 +514,16 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
         ch[v] = {a, b};
         lab[v] = xor_sorted(lab[a], lab[b]);
         opos[v] = merge_pos(opos[a], opos[b]);
+        slu[v] = union_sorted(slu[a], slu[b]);
     };
     for (size_t s = 0; s < path.size(); ++s) set_node(n + (int32_t)s, path[s].first, path[s].second);
     const int32_t root = n_nodes - 1;
     auto weight = [&](const std::vector<int32_t> &pos) { return bt ? bt->count(pos) : 1.0; };
+    auto sl_inst = [&](const std::vector<int64_t> &ls) {
+        double p = 1;
+        for (int64_t l : ls) p *= net.labels.at(l).dim;
+        return p;
+    };
 
     for (int pass = 0; pass < passes; ++pass) {
         // internal nodes, parents before children
@@ -531,7 +546,8 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
                 double best_s = -1;
                 for (int i = 0; i < (int)front.size(); ++i)
                     if (front[i] >= n) {
-                        const double sz = label_size(net, lab[front[i]], fixed) * weight(opos[front[i]]);
+                        const double sz =
+                            label_size(net, lab[front[i]], fixed) * weight(opos[front[i]]) * sl_inst(slu[front[i]]);
                         if (sz > best_s) {
                             best_s = sz;
                             best_i = i;
@@ -548,15 +564,19 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
             if (m < 3) continue;
             double cur = 0;
             for (int32_t x : internal)
-                cur += weight(opos[x]) * 8.0 * label_size(net, union_sorted(lab[ch[x][0]], lab[ch[x][1]]), fixed);
+                cur += weight(opos[x]) * sl_inst(slu[x]) * 8.0 *
+                       label_size(net, union_sorted(lab[ch[x][0]], lab[ch[x][1]]), fixed);
             // subset outputs and weights
             const int full = (1 << m) - 1;
             std::vector<std::vector<int64_t>> outs(full + 1);
-            std::vector<double> wts(full + 1, 1.0), osz(full + 1, 1.0);
+            std::vector<double> wts(full + 1, 1.0), osz(full + 1, 1.0), swt(full + 1, 1.0);
+            std::vector<std::vector<int64_t>> sls(full + 1);
             for (int S = 1; S <= full; ++S) {
                 const int low = __builtin_ctz(S);
                 const int rest = S & (S - 1);
                 outs[S] = rest ? xor_sorted(outs[rest], lab[front[low]]) : lab[front[low]];
+                sls[S] = rest ? union_sorted(sls[rest], slu[front[low]]) : slu[front[low]];
+                swt[S] = sl_inst(sls[S]);
                 if (bt) {
                     std::vector<int32_t> pos;
                     for (int i = 0; i < m; ++i)
@@ -576,7 +596,7 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
                     if (s1 > s2) continue;
                     if (S != full && osz[S] * wts[S] > max_size) continue;   // intermediate above the cap
                     const double c = best[s1] + best[s2] +
-                                     wts[S] * 8.0 * label_size(net, union_sorted(outs[s1], outs[s2]), fixed);
+                                     wts[S] * swt[S] * 8.0 * label_size(net, union_sorted(outs[s1], outs[s2]), fixed);
                     if (bc < 0 || c < bc) {
                         bc = c;
                         bs = s1;
@@ -638,15 +658,22 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
 }
 
 // Weighted FLOP and largest weighted intermediate of a path (the greedy's model).
+// FLOP of a path, every node counted once per batch instance (bt) and per
+// distinct assignment of the sliced labels under it; peak_out: the largest
+// intermediate of one slice times its batch instances.
 static double weighted_flop(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
-                            BatchInstances *bt, double *peak_out)
+                            BatchInstances *bt, double *peak_out, const std::vector<int64_t> &sliced = {})
 {
-    auto fixed = fixed_set(net, {});
+    auto fixed = fixed_set(net, sliced);
+    std::unordered_set<int64_t> slset(sliced.begin(), sliced.end());
     const int32_t n = (int32_t)net.leaves.size();
-    std::vector<std::vector<int64_t>> lab(n + path.size());
+    std::vector<std::vector<int64_t>> lab(n + path.size()), slu(n + path.size());
     std::vector<std::vector<int32_t>> opos(n + path.size());
     for (int32_t i = 0; i < n; ++i) {
         lab[i] = net.leaves[i].labels;
+        for (int64_t l : lab[i])
+            if (slset.count(l)) slu[i].push_back(l);
+        std::sort(slu[i].begin(), slu[i].end());
         if (bt)
             for (int64_t l : lab[i]) {
                 auto it = bt->digit.find(l);
@@ -659,8 +686,11 @@ static double weighted_flop(const Network &net, const std::vector<std::pair<int3
         const int32_t a = path[s].first, b = path[s].second, c = n + (int32_t)s;
         lab[c] = sym_diff(lab[a], lab[b]);
         opos[c] = merge_pos(opos[a], opos[b]);
+        std::set_union(slu[a].begin(), slu[a].end(), slu[b].begin(), slu[b].end(), std::back_inserter(slu[c]));
+        double si = 1;
+        for (int64_t l : slu[c]) si *= net.labels.at(l).dim;
         const double w = bt ? bt->count(opos[c]) : 1.0;
-        total += w * 8.0 * label_size(net, set_union(lab[a], lab[b]), fixed);
+        total += w * si * 8.0 * label_size(net, set_union(lab[a], lab[b]), fixed);
         peak = std::max(peak, w * label_size(net, lab[c], fixed));
     }
     if (peak_out) *peak_out = peak;
@@ -785,4 +815,37 @@ std::vector<int64_t> slice_auto(const Network &net, int64_t max_elems, int32_t m
     }
 }
 
+// Sub-tree reconfiguration of the current path under its slicing (Section 3.2:
+// minimise Eq. task_based_amplitude_flops itself): every node's FLOP counts
+// once per distinct assignment of the sliced labels under it (and per batch
+// instance when outputs lists a batch), every sub-tree of up to 10 tensors is
+// re-ordered optimally, and no intermediate of one slice grows above the
+// current path's largest.  Returns the current path when nothing improves.
+std::vector<std::pair<int32_t, int32_t>> reconfigure_sliced(const Network &net, int32_t passes, int32_t n_amps,
+                                                            const int32_t *outputs, double *before, double *after)
+{
+    BatchInstances batch, *bt = nullptr;
+    if (outputs && n_amps > 1) {
+        batch.n_amps = n_amps;
+        batch.n_out = (int32_t)net.open.size();
+        batch.outputs = outputs;
+        for (int32_t j = 0; j < batch.n_out; ++j)
+            if (std::find(net.free_open.begin(), net.free_open.end(), net.open[j]) == net.free_open.end())
+                batch.digit[net.open[j]] = j;
+        bt = &batch;
+    }
+    double pk = 0, pk2 = 0;
+    const double f0 = weighted_flop(net, net.path, bt, &pk, net.sliced);
+    auto p = reconfigure(net, net.path, bt, passes, 10, pk, net.sliced);
+    double f1 = weighted_flop(net, p, bt, &pk2, net.sliced);
+    if (!(f1 < f0 && pk2 <= pk)) {
+        p = net.path;
+        f1 = f0;
+    }
+    if (before) *before = f0;
+    if (after) *after = f1;
+    return p;
+}
+
 }  // namespace jet
+

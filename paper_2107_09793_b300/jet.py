@@ -21,7 +21,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_path_greedy", "jet_path_greedy_batch", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
-           "jet_contract_slices", "jet_network_set_free"]
+           "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices"]
 
 
 class JetError(RuntimeError):
@@ -77,6 +77,8 @@ def lib():
             "jet_network_create": (I32, [P, I32, P, P]),
             "jet_network_set_open": (I32, [P, I32, P]),
             "jet_network_set_free": (I32, [P, I32, P]),
+            "jet_path_reconfigure": (I32, [P, I32, I32, P, P, P]),
+            "jet_plan_slices": (I32, [P, I32, P, I32, P, P]),
             "jet_tensor_update": (I32, [P, I32, P]),
             "jet_tensors_upload": (I32, [P, P, P]),
             "jet_network_n_values": (I64, [P]),
@@ -222,6 +224,17 @@ class Network:
                                            ctypes.c_uint64(seed), int(n_trials), ctypes.byref(f)))
         return f.value
 
+    def path_reconfigure(self, passes: int = 8, outputs=None) -> Tuple[float, float]:
+        """jet_path_reconfigure: (reuse-aware FLOP before, after) for the current slicing."""
+        b, a = ctypes.c_double(), ctypes.c_double()
+        if outputs is None:
+            _check(lib().jet_path_reconfigure(self._h, int(passes), 1, None, ctypes.byref(b), ctypes.byref(a)))
+        else:
+            o = self._outputs(outputs)
+            _check(lib().jet_path_reconfigure(self._h, int(passes), o.shape[0], o.ctypes.data, ctypes.byref(b),
+                                              ctypes.byref(a)))
+        return b.value, a.value
+
     def slice(self, labels: Sequence[int]):
         a = np.ascontiguousarray(np.asarray(labels, dtype=np.int64))
         _check(lib().jet_slice(self._h, a.size, a.ctypes.data))
@@ -243,6 +256,14 @@ class Network:
         o = self._outputs(outputs)
         b = ctypes.c_size_t()
         _check(lib().jet_plan(self._h, o.shape[0], o.ctypes.data, ctypes.byref(b)))
+        return b.value
+
+    def plan_slices(self, outputs, slice_ids) -> int:
+        """jet_plan_slices: build (and keep) contract_slices' plan; workspace bytes."""
+        o = self._outputs(outputs)
+        ids = np.ascontiguousarray(np.asarray(slice_ids, dtype=np.int64))
+        b = ctypes.c_size_t()
+        _check(lib().jet_plan_slices(self._h, o.shape[0], o.ctypes.data, ids.size, ids.ctypes.data, ctypes.byref(b)))
         return b.value
 
     def set_workspace(self, dptr: int, nbytes: int):

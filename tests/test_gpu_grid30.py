@@ -78,3 +78,25 @@ def test_grid30_sliced_sum_equals_unsliced_on_gpu(bench_plan):
     un = _net(w, path, [], "fp64")
     a_un = un.contract(w.outputs)[0]
     assert abs(a_un - a_sliced) <= 1e-12 * abs(a_sliced)
+
+
+def test_grid30_path_reconfigured_for_its_slicing():
+    """The benchmark's path after the slice-aware sub-tree reconfiguration
+    (Section 3.2, Eq. task_based_amplitude_flops): the amplitude still matches
+    the stored 2^30 state-vector value."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid30.json")))
+    w = configs.build("grid30")
+    net = jet.from_network(w.network, precision="fp16x3")
+    net.path_greedy(seed=1, n_trials=64)
+    net.slice_auto(1 << 24, min_n=6, max_n=24)
+    before, after = net.path_reconfigure(8)
+    assert after < before
+    rows = np.array(g["outputs"][:2], np.int32)
+    got = net.contract(rows)
+    ref = np.array([complex(a, b) for a, b in g["amplitudes"][:2]])
+    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    print(f"reconfigured path {before:.3g} -> {after:.3g} FLOP, rel err {err:.2e}")
+    assert err <= 1e-5
+    net.close()

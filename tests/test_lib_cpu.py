@@ -331,3 +331,35 @@ def test_free_open_legs_arguments_and_planning():
         closed.set_free([0])                       # open legs not declared (none exist)
     net.close()
     closed.close()
+
+
+def test_path_reconfigure_for_slicing():
+    """jet_path_reconfigure: the cost it reports is Eq. task_based_amplitude_flops
+    of the path under its slicing (equal to the FLOP the plan executes, reuse
+    on), it never increases, the largest intermediate of one slice does not
+    grow, and a batch-weighted call and argument errors behave."""
+    w = configs.build("grid30")
+    net = jet.from_network(w.network)
+    net.path_greedy(seed=1, n_trials=16)
+    net.slice_auto(1 << 24, min_n=6, max_n=24)
+    net.plan(w.outputs)
+    st0 = net.stats()
+    before, after = net.path_reconfigure(4)
+    assert before == pytest.approx(st0["flop_executed"], rel=1e-12)
+    assert after <= before
+    net.plan(w.outputs)
+    st1 = net.stats()
+    assert st1["flop_executed"] == pytest.approx(after, rel=1e-12)
+    assert st1["max_intermediate"] <= st0["max_intermediate"]
+    b2, a2 = net.path_reconfigure(2)          # a second call starts from the improved path
+    assert b2 == pytest.approx(after, rel=1e-12) and a2 <= b2
+    with pytest.raises(jet.JetError):
+        net.path_reconfigure(0)
+    rows = np.array([[0] * 30, [1] * 30], np.int32)
+    bb, ab = net.path_reconfigure(2, outputs=rows)
+    assert ab <= bb
+    fresh = jet.from_network(w.network)
+    with pytest.raises(jet.JetError):
+        fresh.path_reconfigure(2)             # no path yet
+    net.close()
+    fresh.close()
