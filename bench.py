@@ -447,11 +447,23 @@ def run_impl(args):
     amps_dev = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    # The step is timed on a handle without instrumentation (its graph holds only the
+    # kernels); the per-kernel times of the roofline come from the same plan with a
+    # CUDA event pair around every heavy launch (profile=1), timed right after it
+    # in the same region: the event nodes add ~9% to that step.
+    run_net = jet.from_network(w.network, precision=args.precision, device=dev)
+    run_net.path_set(path)
+    run_net.slice(sliced)
+
     def step():
+        run_net.contract_async(outs, amps_dev.data_ptr(), sh)
+
+    def prof_step():
         net.contract_async(outs, amps_dev.data_ptr(), sh)
 
     for _ in range(max(args.warmup, 3)):
         step()
+        prof_step()
     torch.cuda.synchronize()
     sampler = ClockSampler(dev)
     sampler.start()
@@ -459,7 +471,7 @@ def run_impl(args):
     barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.time()
-    step_ms, gemm_ms = [], {}
+    step_ms, prof_ms, gemm_ms = [], [], {}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(args.steps):
         flush.zero_()                      # evict L2 between timed steps (256 MiB > 126 MB L2)
@@ -468,6 +480,13 @@ def run_impl(args):
         ev1.record(stream)
         ev1.synchronize()
         step_ms.append(ev0.elapsed_time(ev1))
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        prof_step()
+        ev1.record(stream)
+        ev1.synchronize()
+        prof_ms.append(ev0.elapsed_time(ev1))
         for i, r in enumerate(net.profile()):
             if r["ms"] >= 0:
                 gemm_ms.setdefault(i, []).append(r["ms"])
@@ -494,7 +513,7 @@ def run_impl(args):
         by_kind.setdefault(recs[i]["kind"], []).append(i)
     roof = None
     if by_kind:
-        mean_step_ms = sum(step_ms) / len(step_ms)
+        mean_step_ms = sum(prof_ms) / len(prof_ms)   # the instrumented step the kernel times come from
         dom = max(by_kind, key=lambda k: sum(timed[i] for i in by_kind[k]))
         ids = by_kind[dom]
         share = sum(timed[i] for i in ids) / mean_step_ms
@@ -531,6 +550,7 @@ def run_impl(args):
                     "launches_per_step": len(ids), "bytes_per_step": nbytes, "ms_per_step": ms,
                     "peak_source": f"hbm_gbs of {peak_src}", "share_of_step": share}
         roof["kinds_timed_ms"] = {k: sum(timed[i] for i in v) for k, v in by_kind.items()}
+        roof["instrumented_step_ms"] = mean_step_ms
 
     # where the step's time goes: one extra profiled step with every launch timed
     breakdown = {}
@@ -585,7 +605,7 @@ def run_impl(args):
             nm.close()
 
     # end to end through the C ABI: pinned host inputs -> device, contract, amplitude back to host
-    nv = net.n_values()
+    nv = run_net.n_values()
     host_vals = torch.empty(nv, dtype=torch.complex64, pin_memory=True)
     host_vals.numpy()[:] = np.concatenate([np.asarray(t, np.complex64).ravel() for t in w.network.data])
     e2e_s = []
@@ -593,8 +613,8 @@ def run_impl(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        net.upload(host_vals.data_ptr(), sh)
-        a = net.contract(outs, stream=sh)
+        run_net.upload(host_vals.data_ptr(), sh)
+        a = run_net.contract(outs, stream=sh)
         dt = time.perf_counter() - t0
         if i:
             e2e_s.append(dt)
@@ -746,7 +766,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jet", choices=["jet", "reference"])
-    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
     ap.add_argument("--skip-others", action="store_true", help="skip the other workloads (bosonic lattice, "
