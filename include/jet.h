@@ -78,7 +78,17 @@ typedef struct {
     int32_t device;           /* CUDA device ordinal, default 0                          */
     int64_t gemm_min_k;       /* contractions with a summed extent >= this (and both free
                                  extents >= 64) take the GEMM route; default 16           */
-    int64_t workspace_limit;  /* bytes of device workspace the plan may use; 0 = none    */
+    int64_t workspace_limit;  /* bytes of device workspace a contraction may use; 0 = no
+                                 limit.  When the plan for every slice needs more,
+                                 jet_contract / jet_contract_async run the slices in
+                                 consecutive id ranges (the largest power-of-two
+                                 fraction of the slices whose plan fits), each range's
+                                 shared intermediates computed once, and sum the
+                                 per-slice partials in increasing slice id in FP64 (the
+                                 order of one plan; a range's plan may route a node with
+                                 fewer instances to another kernel form, so the values
+                                 agree to the arithmetic's rounding).  A caller-provided
+                                 workspace smaller than the plan caps it the same way. */
     int32_t profile;          /* 0 (default): off; 1: CUDA events around every GEMM, operand
                                  split and small-operand launch; 2: around every launch
                                  (read with jet_profile)                                  */
@@ -282,7 +292,8 @@ int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs
                         const int64_t *slice_ids, jet_c128 *partials_out, void *cuda_stream);
 
 /* Same as jet_contract but amps_dev is DEVICE memory (n_amps complex128, times
- * E with free legs) and
+ * E with free legs; when workspace_limit splits the slices into ranges the call
+ * synchronises) and
  * the call returns without synchronising: the amplitudes are ready when work
  * issued on cuda_stream before the next call completes. */
 int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,

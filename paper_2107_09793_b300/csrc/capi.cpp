@@ -5,6 +5,7 @@
 #include <cstring>
 #include <exception>
 #include <new>
+#include <numeric>
 #include <string>
 #include <unordered_set>
 
@@ -403,12 +404,72 @@ int jet_set_workspace(jet_network *net, void *dptr, size_t bytes)
     });
 }
 
+// Workspace the plan may use: jet_options.workspace_limit, and no more than a
+// caller-provided workspace (0: no limit).
+static size_t workspace_cap(const Network &net)
+{
+    size_t cap = net.opt.workspace_limit > 0 ? (size_t)net.opt.workspace_limit : 0;
+    if (net.user_arena && (cap == 0 || net.user_arena_bytes < cap)) cap = net.user_arena_bytes;
+    return cap;
+}
+
+// Section 4: when every slice's shared work does not fit at once, a subset of
+// the slices is held in memory at a time, its size determined a priori: the
+// slices run as consecutive id ranges (the largest power-of-two fraction of
+// the slice count whose plan fits the cap), each range's shared intermediates
+// computed once, and the per-slice partials are summed in increasing slice id
+// in FP64 -- the order of the single plan's reduction (a range's plan may route
+// a node with fewer instances to another kernel form).  Writes n_amps * n_elem
+// sums to `sums` (host).
+static void contract_in_ranges(Network &net, int32_t n_amps, const int32_t *outputs, size_t cap, void *stream,
+                               std::vector<jet_c128> &sums)
+{
+    const int64_t n_sl = net.plan->n_slices, n_elem = net.plan->n_elem;
+    int64_t R = n_sl;
+    for (;;) {
+        R = (R + 1) / 2;
+        std::vector<int64_t> ids(R);
+        std::iota(ids.begin(), ids.end(), 0);
+        if (get_plan(net, n_amps, outputs, &ids).arena_bytes <= cap) break;
+        if (R == 1) fail(JET_ENOMEM, "one slice needs more workspace than the limit");
+    }
+    sums.assign((size_t)n_amps * n_elem, jet_c128{0.0, 0.0});
+    std::vector<jet_c128> part;
+    void *s = stream ? stream : net.stream;
+    for (int64_t s0 = 0; s0 < n_sl; s0 += R) {
+        const int64_t n_ids = std::min(R, n_sl - s0);
+        std::vector<int64_t> ids(n_ids);
+        std::iota(ids.begin(), ids.end(), s0);
+        Plan &P = get_plan(net, n_amps, outputs, &ids);
+        bind_and_run(net, P, nullptr, stream);
+        part.resize((size_t)n_amps * n_ids * n_elem);
+        copy_d2h(part.data(), net.d_amps, part.size() * sizeof(jet_c128), s);
+        if (read_clear_status(net, stream))
+            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+        for (int32_t b = 0; b < n_amps; ++b)
+            for (int64_t j = 0; j < n_ids; ++j)
+                for (int64_t e = 0; e < n_elem; ++e) {
+                    const jet_c128 &v = part[((size_t)b * n_ids + j) * n_elem + e];
+                    jet_c128 &acc = sums[(size_t)b * n_elem + e];
+                    acc.re += v.re;
+                    acc.im += v.im;
+                }
+    }
+}
+
 int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c128 *amps_dev,
                        void *cuda_stream)
 {
     return guarded([&] {
         if (!net || !amps_dev) fail(JET_EINVAL, "NULL argument");
         Plan &P = get_plan(*net, n_amps, outputs);
+        const size_t cap = workspace_cap(*net);
+        if (cap && P.arena_bytes > cap && P.n_slices > 1) {   // slice ranges: synchronous
+            std::vector<jet_c128> sums;
+            contract_in_ranges(*net, n_amps, outputs, cap, cuda_stream, sums);
+            copy_h2d_sync(amps_dev, sums.data(), sums.size() * sizeof(jet_c128), cuda_stream ? cuda_stream : net->stream);
+            return;
+        }
         bind_and_run(*net, P, nullptr, cuda_stream);
         copy_d2d_async(amps_dev, net->d_amps, (size_t)n_amps * P.n_elem * sizeof(jet_c128),
                        cuda_stream ? cuda_stream : net->stream);
@@ -420,6 +481,13 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c
     return guarded([&] {
         if (!net || !amps_out) fail(JET_EINVAL, "NULL argument");
         Plan &P = get_plan(*net, n_amps, outputs);
+        const size_t cap = workspace_cap(*net);
+        if (cap && P.arena_bytes > cap && P.n_slices > 1) {
+            std::vector<jet_c128> sums;
+            contract_in_ranges(*net, n_amps, outputs, cap, cuda_stream, sums);
+            std::memcpy(amps_out, sums.data(), sums.size() * sizeof(jet_c128));
+            return;
+        }
         bind_and_run(*net, P, nullptr, cuda_stream);
         copy_d2h(amps_out, net->d_amps, (size_t)n_amps * P.n_elem * sizeof(jet_c128),
                  cuda_stream ? cuda_stream : net->stream);

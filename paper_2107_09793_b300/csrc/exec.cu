@@ -121,6 +121,12 @@ void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream)
     JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
 }
 
+void copy_h2d_sync(void *dst, const void *src, size_t bytes, void *stream)
+{
+    JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    JET_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+}
+
 bool gemm_available(int32_t) { return true; }
 
 int read_clear_status(Network &net, void *stream)

@@ -202,6 +202,7 @@ void *device_alloc(size_t bytes);
 void device_free(void *p);
 void copy_d2h(void *dst, const void *src, size_t bytes, void *stream);
 void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream);
+void copy_h2d_sync(void *dst, const void *src, size_t bytes, void *stream);
 void device_memset_async(void *dst, size_t bytes, void *stream);
 bool gemm_available(int32_t precision);
 int read_clear_status(Network &net, void *stream);

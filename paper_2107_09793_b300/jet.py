@@ -114,7 +114,7 @@ def _check(rc: int):
 
 
 def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=16, profile=0,
-                    apply_tc_min_kf=1024) -> Options:
+                    apply_tc_min_kf=1024, workspace_limit=0) -> Options:
     o = Options()
     lib().jet_options_default(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -124,6 +124,7 @@ def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm
     o.gemm_min_k = int(gemm_min_k)
     o.profile = int(profile)
     o.apply_tc_min_kf = int(apply_tc_min_kf)
+    o.workspace_limit = int(workspace_limit)
     return o
 
 

@@ -100,3 +100,31 @@ def test_grid30_path_reconfigured_for_its_slicing():
     print(f"reconfigured path {before:.3g} -> {after:.3g} FLOP, rel err {err:.2e}")
     assert err <= 1e-5
     net.close()
+
+
+def test_grid30_workspace_limit_runs_slice_ranges_bitwise():
+    """jet_options.workspace_limit below the plan's workspace: the slices run in
+    consecutive id ranges whose plans fit (a subset of the slices held at a
+    time, sized a priori); the sums match one plan's to the complex64
+    arithmetic's rounding (a range's plan may pick other kernel forms for nodes
+    with fewer instances) and the stored state-vector amplitudes to 1e-5."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid30.json")))
+    w = configs.build("grid30")
+    full = jet.from_network(w.network, precision="fp16x3")
+    full.path_greedy(seed=1, n_trials=64)
+    labels = full.slice_auto(1 << 24, min_n=6, max_n=24)
+    rows = np.array(g["outputs"][:2], np.int32)
+    need = full.plan(rows)
+    ref = full.contract(rows)
+    lim = jet.from_network(w.network, precision="fp16x3", workspace_limit=need // 3)
+    lim.path_set(full.path_get())
+    lim.slice(labels)
+    got = lim.contract(rows)
+    assert np.max(np.abs(got - ref) / np.abs(ref)) <= 2e-6
+    gold = np.array([complex(a, b) for a, b in g["amplitudes"][:2]])
+    assert np.linalg.norm(got - gold) / np.linalg.norm(gold) <= 1e-5
+    assert lim.stats()["workspace_bytes"] <= need // 3     # the last range's plan
+    full.close()
+    lim.close()
