@@ -237,19 +237,22 @@ int jet_path_greedy_batch(jet_network *net, int32_t n_amps, const int32_t *outpu
 
 /* Improve the current path for its current slicing (Section 3.2: minimise
  * Eq. task_based_amplitude_flops itself rather than the FLOP of one slice).
- * Every node's FLOP counts once per distinct assignment of the sliced labels
- * under it, and once per distinct restriction of the batch rows to the open
- * legs under it when outputs lists n_amps > 1 rows (NULL: one amplitude);
- * every sub-tree is opened down to at most 10 tensors and re-ordered optimally
- * by dynamic programming over subsets, `passes` times over the tree, and no
+ * Every node counts once per distinct assignment of the sliced labels under
+ * it, and once per distinct restriction of the batch rows to the open legs
+ * under it when outputs lists n_amps > 1 rows (NULL: one amplitude).  objective
+ * 0: a node costs its FLOP (the sum is Eq. task_based_amplitude_flops);
+ * 1: it costs max(FLOP / 100 TFLOP/s, 8 B x (|A| + |B| + |C|) / 4 TB/s), an
+ * estimated time that weighs the HBM traffic of small-operand steps.  Every
+ * sub-tree is opened down to at most 10 tensors and re-ordered optimally by
+ * dynamic programming over subsets, `passes` times over the tree, and no
  * intermediate of one slice (times its batch instances) may grow above the
  * current path's largest, so the slicing stays valid.  The path is replaced
- * only when that cost falls.  flop_before / flop_after (may be NULL): the cost
- * before and after.
+ * only when the cost falls.  cost_before / cost_after (may be NULL): the cost
+ * before and after (FLOP, or seconds).
  * Errors: JET_ESTATE (no path, or a batch without declared open legs),
- * JET_EINVAL (passes outside [1, 64], digit out of range). */
-int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t n_amps, const int32_t *outputs,
-                         double *flop_before, double *flop_after);
+ * JET_EINVAL (passes outside [1, 64], objective not 0 or 1, digit out of range). */
+int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t objective, int32_t n_amps,
+                         const int32_t *outputs, double *cost_before, double *cost_after);
 
 /* Slice the given closed labels (Section 2.4); n = 0 clears the slicing.
  * Slice id s is the mixed-radix number over the sliced labels, the first label

@@ -304,13 +304,14 @@ int jet_path_greedy_batch(jet_network *net, int32_t n_amps, const int32_t *outpu
     });
 }
 
-int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t n_amps, const int32_t *outputs,
-                         double *flop_before, double *flop_after)
+int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t objective, int32_t n_amps, const int32_t *outputs,
+                         double *cost_before, double *cost_after)
 {
     return guarded([&] {
         if (!net) fail(JET_EINVAL, "net is NULL");
         if (net->path.size() + 1 != net->leaves.size()) fail(JET_ESTATE, "no contraction path set");
         if (passes < 1 || passes > 64) fail(JET_EINVAL, "passes must be in [1, 64]");
+        if (objective != 0 && objective != 1) fail(JET_EINVAL, "objective must be 0 (FLOP) or 1 (time model)");
         if (outputs && n_amps > 1) {
             if (!net->open_set) fail(JET_ESTATE, "open legs not declared (jet_network_set_open)");
             const int32_t n_open = (int32_t)net->open.size();
@@ -322,7 +323,7 @@ int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t n_amps, const
                 }
         }
         double f0 = 0, f1 = 0;
-        auto p = reconfigure_sliced(*net, passes, n_amps, outputs, &f0, &f1);
+        auto p = reconfigure_sliced(*net, passes, n_amps, outputs, &f0, &f1, objective == 1);
         validate_path(*net, p);
         if (f1 < f0) {
             net->path = p;
@@ -330,8 +331,8 @@ int jet_path_reconfigure(jet_network *net, int32_t passes, int32_t n_amps, const
             net->flop_planned = path_cost(*net, p, {}).flop;
             invalidate_plan(*net);
         }
-        if (flop_before) *flop_before = f0;
-        if (flop_after) *flop_after = f1;
+        if (cost_before) *cost_before = f0;
+        if (cost_after) *cost_after = f1;
     });
 }
 

@@ -181,7 +181,8 @@ std::vector<std::pair<int32_t, int32_t>> greedy_path(const Network &net, uint64_
                                                      const int32_t *outputs = nullptr, double max_elems = 0);
 std::vector<int64_t> slice_auto(const Network &net, int64_t max_elems, int32_t min_n, int32_t max_n);
 std::vector<std::pair<int32_t, int32_t>> reconfigure_sliced(const Network &net, int32_t passes, int32_t n_amps,
-                                                            const int32_t *outputs, double *before, double *after);
+                                                            const int32_t *outputs, double *before, double *after,
+                                                            bool time_model);
 double reuse_aware_flop(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
                         const std::vector<int64_t> &sliced);
 void validate_path(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path);

@@ -796,9 +796,14 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             const int64_t total_out = d.n_out * n_inst;
             const int64_t n_k = d.n_khi * d.n_klo;
             d.ksplit = 1;
-            if (total_out < 16384 && n_k >= 4096 && d.n_khi > 1) {
+            // the split form (8 outputs per block, the block's threads sharing the
+            // summed index) also when the one-output-per-thread form would launch
+            // fewer than 4 blocks per SM: at least two parts then
+            const int64_t plain_blocks = (d.n_out + 255) / 256 * n_inst;
+            const bool few_blocks = plain_blocks < 148 * 4;
+            if ((total_out < 16384 || few_blocks) && n_k >= 4096 && d.n_khi > 1) {
                 int64_t groups = (d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G * n_inst;
-                int64_t want = std::max<int64_t>(1, (148 * 8 + groups - 1) / groups);
+                int64_t want = std::max<int64_t>(few_blocks ? 2 : 1, (148 * 8 + groups - 1) / groups);
                 int64_t parts = std::min<int64_t>(want, d.n_khi);
                 d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
                 d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);

@@ -474,10 +474,14 @@ static std::vector<std::pair<int32_t, int32_t>> leaf_order_linear(const Network 
 // once per distinct assignment of the sliced labels under it (Eq.
 // task_based_amplitude_flops) and its size is that of one slice; max_size caps
 // the size of one slice's intermediate (times its batch instances).
+// time_model: a node costs max(FLOP / 100 TFLOP/s, bytes / 4 TB/s) per
+// instance instead of its FLOP, bytes = 8 B x (|A| + |B| + |C|): a contraction
+// that only streams operands through HBM weighs by its traffic.
 static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
                                                             const std::vector<std::pair<int32_t, int32_t>> &path,
                                                             BatchInstances *bt, int passes, int k, double max_size,
-                                                            const std::vector<int64_t> &sliced = {})
+                                                            const std::vector<int64_t> &sliced = {},
+                                                            bool time_model = false)
 {
     auto fixed = fixed_set(net, sliced);
     std::unordered_set<int64_t> slset(sliced.begin(), sliced.end());
@@ -524,6 +528,11 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
         for (int64_t l : ls) p *= net.labels.at(l).dim;
         return p;
     };
+    // cost of one instance of a pairwise step with operand sizes sa, sb, result sc, index union su
+    auto step_cost = [&](double sa, double sb, double sc, double su) {
+        if (!time_model) return 8.0 * su;
+        return std::max(8.0 * su / 100e12, 8.0 * (sa + sb + sc) / 4e12);
+    };
 
     for (int pass = 0; pass < passes; ++pass) {
         // internal nodes, parents before children
@@ -564,8 +573,10 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
             if (m < 3) continue;
             double cur = 0;
             for (int32_t x : internal)
-                cur += weight(opos[x]) * sl_inst(slu[x]) * 8.0 *
-                       label_size(net, union_sorted(lab[ch[x][0]], lab[ch[x][1]]), fixed);
+                cur += weight(opos[x]) * sl_inst(slu[x]) *
+                       step_cost(label_size(net, lab[ch[x][0]], fixed), label_size(net, lab[ch[x][1]], fixed),
+                                 label_size(net, lab[x], fixed),
+                                 label_size(net, union_sorted(lab[ch[x][0]], lab[ch[x][1]]), fixed));
             // subset outputs and weights
             const int full = (1 << m) - 1;
             std::vector<std::vector<int64_t>> outs(full + 1);
@@ -596,7 +607,9 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
                     if (s1 > s2) continue;
                     if (S != full && osz[S] * wts[S] > max_size) continue;   // intermediate above the cap
                     const double c = best[s1] + best[s2] +
-                                     wts[S] * swt[S] * 8.0 * label_size(net, union_sorted(outs[s1], outs[s2]), fixed);
+                                     wts[S] * swt[S] *
+                                         step_cost(osz[s1], osz[s2], osz[S],
+                                                   label_size(net, union_sorted(outs[s1], outs[s2]), fixed));
                     if (bc < 0 || c < bc) {
                         bc = c;
                         bs = s1;
@@ -662,7 +675,8 @@ static std::vector<std::pair<int32_t, int32_t>> reconfigure(const Network &net,
 // distinct assignment of the sliced labels under it; peak_out: the largest
 // intermediate of one slice times its batch instances.
 static double weighted_flop(const Network &net, const std::vector<std::pair<int32_t, int32_t>> &path,
-                            BatchInstances *bt, double *peak_out, const std::vector<int64_t> &sliced = {})
+                            BatchInstances *bt, double *peak_out, const std::vector<int64_t> &sliced = {},
+                            bool time_model = false)
 {
     auto fixed = fixed_set(net, sliced);
     std::unordered_set<int64_t> slset(sliced.begin(), sliced.end());
@@ -690,7 +704,10 @@ static double weighted_flop(const Network &net, const std::vector<std::pair<int3
         double si = 1;
         for (int64_t l : slu[c]) si *= net.labels.at(l).dim;
         const double w = bt ? bt->count(opos[c]) : 1.0;
-        total += w * si * 8.0 * label_size(net, set_union(lab[a], lab[b]), fixed);
+        const double su = label_size(net, set_union(lab[a], lab[b]), fixed);
+        const double bytes = 8.0 * (label_size(net, lab[a], fixed) + label_size(net, lab[b], fixed) +
+                                    label_size(net, lab[c], fixed));
+        total += w * si * (time_model ? std::max(8.0 * su / 100e12, bytes / 4e12) : 8.0 * su);
         peak = std::max(peak, w * label_size(net, lab[c], fixed));
     }
     if (peak_out) *peak_out = peak;
@@ -822,7 +839,8 @@ std::vector<int64_t> slice_auto(const Network &net, int64_t max_elems, int32_t m
 // re-ordered optimally, and no intermediate of one slice grows above the
 // current path's largest.  Returns the current path when nothing improves.
 std::vector<std::pair<int32_t, int32_t>> reconfigure_sliced(const Network &net, int32_t passes, int32_t n_amps,
-                                                            const int32_t *outputs, double *before, double *after)
+                                                            const int32_t *outputs, double *before, double *after,
+                                                            bool time_model)
 {
     BatchInstances batch, *bt = nullptr;
     if (outputs && n_amps > 1) {
@@ -835,9 +853,9 @@ std::vector<std::pair<int32_t, int32_t>> reconfigure_sliced(const Network &net, 
         bt = &batch;
     }
     double pk = 0, pk2 = 0;
-    const double f0 = weighted_flop(net, net.path, bt, &pk, net.sliced);
-    auto p = reconfigure(net, net.path, bt, passes, 10, pk, net.sliced);
-    double f1 = weighted_flop(net, p, bt, &pk2, net.sliced);
+    const double f0 = weighted_flop(net, net.path, bt, &pk, net.sliced, time_model);
+    auto p = reconfigure(net, net.path, bt, passes, 10, pk, net.sliced, time_model);
+    double f1 = weighted_flop(net, p, bt, &pk2, net.sliced, time_model);
     if (!(f1 < f0 && pk2 <= pk)) {
         p = net.path;
         f1 = f0;

@@ -77,7 +77,7 @@ def lib():
             "jet_network_create": (I32, [P, I32, P, P]),
             "jet_network_set_open": (I32, [P, I32, P]),
             "jet_network_set_free": (I32, [P, I32, P]),
-            "jet_path_reconfigure": (I32, [P, I32, I32, P, P, P]),
+            "jet_path_reconfigure": (I32, [P, I32, I32, I32, P, P, P]),
             "jet_plan_slices": (I32, [P, I32, P, I32, P, P]),
             "jet_tensor_update": (I32, [P, I32, P]),
             "jet_tensors_upload": (I32, [P, P, P]),
@@ -225,14 +225,16 @@ class Network:
                                            ctypes.c_uint64(seed), int(n_trials), ctypes.byref(f)))
         return f.value
 
-    def path_reconfigure(self, passes: int = 8, outputs=None) -> Tuple[float, float]:
-        """jet_path_reconfigure: (reuse-aware FLOP before, after) for the current slicing."""
+    def path_reconfigure(self, passes: int = 8, outputs=None, objective: str = "flop") -> Tuple[float, float]:
+        """jet_path_reconfigure: (cost before, after) for the current slicing;
+        objective "flop" (Eq. task_based_amplitude_flops) or "time" (estimated seconds)."""
         b, a = ctypes.c_double(), ctypes.c_double()
+        obj = {"flop": 0, "time": 1}[objective]
         if outputs is None:
-            _check(lib().jet_path_reconfigure(self._h, int(passes), 1, None, ctypes.byref(b), ctypes.byref(a)))
+            _check(lib().jet_path_reconfigure(self._h, int(passes), obj, 1, None, ctypes.byref(b), ctypes.byref(a)))
         else:
             o = self._outputs(outputs)
-            _check(lib().jet_path_reconfigure(self._h, int(passes), o.shape[0], o.ctypes.data, ctypes.byref(b),
+            _check(lib().jet_path_reconfigure(self._h, int(passes), obj, o.shape[0], o.ctypes.data, ctypes.byref(b),
                                               ctypes.byref(a)))
         return b.value, a.value
 

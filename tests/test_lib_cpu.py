@@ -358,6 +358,8 @@ def test_path_reconfigure_for_slicing():
     rows = np.array([[0] * 30, [1] * 30], np.int32)
     bb, ab = net.path_reconfigure(2, outputs=rows)
     assert ab <= bb
+    tb, ta = net.path_reconfigure(2, objective="time")   # estimated seconds
+    assert 0 < ta <= tb < 1
     fresh = jet.from_network(w.network)
     with pytest.raises(jet.JetError):
         fresh.path_reconfigure(2)             # no path yet
