@@ -213,6 +213,18 @@ def run_other_workloads(dev, peaks, peak_src):
     ms = _timed(run, stream, ev0, ev1, 3)
     a = amps.cpu().numpy()
     st = net.stats()
+    # kept shared work: the bra-free part of the batch path (the state up to the
+    # bras) computed once, then a second batch of 256 other patterns reads it
+    from circuits import random_patterns
+    other = random_patterns(w.circuit.n, len(w.outputs), 4242, w.circuit.d)
+    net.keep_shared(1 << 20)
+    net.contract_async(w.outputs, amps.data_ptr(), sh)   # fills the pool
+    torch.cuda.synchronize()
+    run2 = lambda: net.contract_async(other, amps.data_ptr(), sh)
+    run2()
+    torch.cuda.synchronize()
+    ms_kept = _timed(run2, stream, ev0, ev1, 3)
+    st_kept = net.stats()
     net.close()
     tot = w.outputs.sum(axis=1)
     g = json.load(open(os.path.join(ROOT, "tests", "golden", "gbs16.json")))
@@ -236,6 +248,10 @@ def run_other_workloads(dev, peaks, peak_src):
         "precision": "fp32", "rel_err_vs_oracle_8_patterns": err,
         "odd_total_exact_zeros": int(np.sum(a[tot % 2 == 1] == 0)), "odd_totals": int(np.sum(tot % 2 == 1)),
         "apply_share": apply_ms / sum(r["ms"] for r in recs),
+        "kept_shared": {"ms_per_batch": statistics.mean(ms_kept),
+                        "amplitudes_per_s": len(other) / (statistics.mean(ms_kept) * 1e-3),
+                        "flop_per_batch": st_kept["flop_executed"],
+                        "note": "another 256 patterns after jet_network_keep_shared kept the bra-free state"},
         # the dominant kernel (apply, ~all of the batch): algorithmic bytes of all its
         # launches over their summed device time; the slowest single launch beside it
         "roofline": {"bound": "hbm", "kernel": "apply_kernel_c64", "achieved": apply_b / (apply_ms * 1e-3) / 1e9,

@@ -159,6 +159,21 @@ int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_opti
  * Errors: JET_EINVAL (a label that is not an open leg, a duplicate, a missing leg). */
 int jet_network_set_open(jet_network *net, int32_t n_out, const int64_t *out_labels);
 
+/* Keep shared work for later contractions (Section 3.2: work shared between
+ * contractions is done once; the paper's conclusion: it can be stored for any
+ * later slice or amplitude calculation).  A sub-tree of the path whose tensors
+ * carry no fixed label (no sliced label, no open leg fixed by a bra) has the
+ * same value in every contraction of this network.  With min_elems > 0 every
+ * maximal such sub-tree whose result has at least min_elems elements keeps its
+ * result in a device pool after the first contraction computes it; later
+ * contractions (any outputs or slices) read it instead of launching the
+ * sub-tree.  A contraction that fills the pool synchronises its stream at the
+ * end.  The pool starts afresh when the path, slicing, open or free legs or any
+ * tensor value change; min_elems = 0 switches keeping off and frees the pool.
+ * Gradients and networks planned without reuse do not keep.
+ * Errors: JET_EINVAL (min_elems < 0). */
+int jet_network_keep_shared(jet_network *net, int64_t min_elems);
+
 /* Leave some output legs free (Section 2.2.1: an open leg without a bra stays
  * an index of the result; Section 3.2: a batch of amplitudes is one
  * multi-contraction whose shared work is done once).  Every contraction then

@@ -73,18 +73,54 @@ static void write_seed(Plan &P, const std::vector<double> &cot, bool fp64)
     P.seed_dirty = true;
 }
 
+// New tensor values: kept results are stale; a plan that reads them is dropped.
+static void drop_kept(Network &net)
+{
+    ++net.tensors_version;
+    if (net.kept.empty()) return;
+    net.kept.clear();
+    invalidate_plan(net);
+}
+
+// Kept results belong to one path, slicing, set of tensor values and of fixed
+// legs: any change starts the pool afresh.
+static void check_kept_key(Network &net)
+{
+    std::vector<int64_t> key{(int64_t)net.path_version, (int64_t)net.slice_version, (int64_t)net.tensors_version,
+                             net.keep_min, (int64_t)net.open.size()};
+    key.insert(key.end(), net.open.begin(), net.open.end());
+    key.push_back(-1);
+    key.insert(key.end(), net.free_open.begin(), net.free_open.end());
+    if (key != net.kept_key) {
+        net.kept.clear();
+        net.kept_key = key;
+    }
+}
+
+// After a run that computed kept results: they are ready, and the next call
+// plans afresh to read them instead of their sub-trees (the stream is drained
+// here, so the plan being replaced has finished running by then).
+static void mark_kept(Network &net, Plan &P, void *stream)
+{
+    if (P.kept_fill.empty()) return;
+    sync_stream(net, stream);
+    for (int32_t v : P.kept_fill) net.kept.at(v).ready = true;
+    P.superseded = true;
+}
+
 static Plan &get_plan(Network &net, int32_t n_amps, const int32_t *outputs,
                       const std::vector<int64_t> *slice_ids = nullptr)
 {
     if (!outputs && !net.open.empty()) fail(JET_EINVAL, "outputs is NULL");
     const size_t n = (size_t)n_amps * net.open.size();
     Plan *P = net.plan.get();
-    bool reuse = P && P->n_amps == n_amps && P->path_version == net.path_version &&
+    bool reuse = P && !P->superseded && P->n_amps == n_amps && P->path_version == net.path_version &&
                  P->slice_version == net.slice_version && P->precision == net.opt.precision &&
                  P->reuse == net.opt.reuse && P->outputs.size() == n &&
                  std::equal(P->outputs.begin(), P->outputs.end(), outputs) &&
                  P->partials == (slice_ids != nullptr) && (!slice_ids || P->slice_ids == *slice_ids);
     if (!reuse) {
+        check_kept_key(net);
         auto fresh = build_plan(net, n_amps, outputs, slice_ids);
         invalidate_plan(net);
         net.plan = std::move(fresh);
@@ -216,6 +252,23 @@ int jet_network_set_free(jet_network *net, int32_t n_free, const int64_t *free_l
     });
 }
 
+int jet_network_keep_shared(jet_network *net, int64_t min_elems)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (min_elems < 0) fail(JET_EINVAL, "min_elems must be >= 0");
+        net->keep_min = min_elems;
+        net->kept.clear();
+        invalidate_plan(*net);
+        if (min_elems == 0) {
+            sync_stream(*net, nullptr);
+            device_free(net->d_kept);
+            net->d_kept = nullptr;
+            net->d_kept_bytes = 0;
+        }
+    });
+}
+
 int jet_tensor_update(jet_network *net, int32_t tensor_id, const jet_c64 *data)
 {
     return guarded([&] {
@@ -224,6 +277,7 @@ int jet_tensor_update(jet_network *net, int32_t tensor_id, const jet_c64 *data)
         const Leaf &L = net->leaves[tensor_id];
         std::memcpy(net->host_values.data() + L.offset, data, (size_t)L.size * sizeof(jet_c64));
         upload_leaf(*net, tensor_id, nullptr);
+        drop_kept(*net);
     });
 }
 
@@ -232,6 +286,7 @@ int jet_tensors_upload(jet_network *net, const jet_c64 *data, void *cuda_stream)
     return guarded([&] {
         if (!net || !data) fail(JET_EINVAL, "NULL argument");
         upload_all(*net, data, cuda_stream);
+        drop_kept(*net);
     });
 }
 
@@ -447,6 +502,7 @@ static void contract_in_ranges(Network &net, int32_t n_amps, const int32_t *outp
         copy_d2h(part.data(), net.d_amps, part.size() * sizeof(jet_c128), s);
         if (read_clear_status(net, stream))
             fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+        mark_kept(net, P, stream);
         for (int32_t b = 0; b < n_amps; ++b)
             for (int64_t j = 0; j < n_ids; ++j)
                 for (int64_t e = 0; e < n_elem; ++e) {
@@ -474,6 +530,7 @@ int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,
         bind_and_run(*net, P, nullptr, cuda_stream);
         copy_d2d_async(amps_dev, net->d_amps, (size_t)n_amps * P.n_elem * sizeof(jet_c128),
                        cuda_stream ? cuda_stream : net->stream);
+        mark_kept(*net, P, cuda_stream);
     });
 }
 
@@ -494,6 +551,7 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c
                  cuda_stream ? cuda_stream : net->stream);
         if (read_clear_status(*net, cuda_stream))
             fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+        mark_kept(*net, P, cuda_stream);
     });
 }
 
@@ -509,6 +567,7 @@ int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs
                  cuda_stream ? cuda_stream : net->stream);
         if (read_clear_status(*net, cuda_stream))
             fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+        mark_kept(*net, P, cuda_stream);
     });
 }
 

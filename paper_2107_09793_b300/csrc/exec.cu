@@ -121,6 +121,11 @@ void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream)
     JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
 }
 
+void sync_stream(Network &net, void *stream)
+{
+    if (stream || net.stream) JET_CUDA(cudaStreamSynchronize((cudaStream_t)(stream ? stream : net.stream)));
+}
+
 void copy_h2d_sync(void *dst, const void *src, size_t bytes, void *stream)
 {
     JET_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, (cudaStream_t)stream));
@@ -187,6 +192,9 @@ void free_network_device(Network &net)
     device_free(net.d_env);
     net.d_env = nullptr;
     net.d_env_cap = 0;
+    device_free(net.d_kept);
+    net.d_kept = nullptr;
+    net.d_kept_bytes = 0;
     if (net.stream) cudaStreamDestroy((cudaStream_t)net.stream);
     net.d_leaves = net.d_leaves64 = net.own_arena = net.d_amps = nullptr;
     net.stream = nullptr;
@@ -315,10 +323,19 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
         net.d_amps_cap = n_out_vals;
     }
     void *leaves = net.opt.precision == JET_PREC_FP64 ? net.d_leaves64 : net.d_leaves;
+    // kept shared results: grow the pool, carrying over the ready ones
+    if (net.d_kept_bytes < P.kept_pool_bytes) {
+        JET_CUDA(cudaStreamSynchronize(s));
+        void *pool = device_alloc(P.kept_pool_bytes);
+        if (net.d_kept && net.d_kept_bytes) JET_CUDA(cudaMemcpy(pool, net.d_kept, net.d_kept_bytes, cudaMemcpyDeviceToDevice));
+        device_free(net.d_kept);
+        net.d_kept = pool;
+        net.d_kept_bytes = P.kept_pool_bytes;
+    }
 
     // (re)bind pointers
     bool rebind = P.dirty_args || P.bound_arena != arena || P.bound_leaves != leaves || P.bound_amps != net.d_amps ||
-                  P.bound_env != net.d_env;
+                  P.bound_env != net.d_env || P.bound_kept != net.d_kept;
     if (rebind) {
         if (P.graph_exec) {
             JET_CUDA(cudaStreamSynchronize(s));
@@ -331,8 +348,8 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
             P.d_args = device_alloc(P.host_args.size());
             P.d_args_bytes = P.host_args.size();
         }
-        uintptr_t bases[6] = {(uintptr_t)leaves, (uintptr_t)arena, (uintptr_t)P.d_args, (uintptr_t)net.d_amps,
-                              (uintptr_t)net.d_status, (uintptr_t)net.d_env};
+        uintptr_t bases[7] = {(uintptr_t)leaves, (uintptr_t)arena, (uintptr_t)P.d_args, (uintptr_t)net.d_amps,
+                              (uintptr_t)net.d_status, (uintptr_t)net.d_env, (uintptr_t)net.d_kept};
         for (const auto &pt : P.patches) {
             uint64_t v = (uint64_t)(bases[pt.base] + (uintptr_t)pt.byte_off);
             std::memcpy(P.host_args.data() + pt.at, &v, 8);
@@ -351,6 +368,7 @@ void bind_and_run(Network &net, Plan &P, void *, void *stream, bool allow_graph)
         P.bound_leaves = leaves;
         P.bound_amps = net.d_amps;
         P.bound_env = net.d_env;
+        P.bound_kept = net.d_kept;
         P.dirty_args = false;
         P.seed_dirty = false;
     } else if (P.seed_dirty) {   // new cotangents of a cached adjoint plan: only the seed bytes change

@@ -93,6 +93,9 @@ struct Plan {
     // sizes
     int64_t n_slices = 1;
     int64_t n_elem = 1;              // values per amplitude row (product of the free legs' dims)
+    std::vector<int32_t> kept_fill;  // kept entries this plan computes (ready once it has run)
+    bool superseded = false;         // its kept entries are ready: the next call plans afresh
+    size_t kept_pool_bytes = 0;      // device pool the plan's kept entries need
     size_t arena_bytes = 0;          // intermediates + scratch (device workspace)
     std::vector<Op> ops;
     std::vector<uint8_t> host_args;   // argument blocks (pointers patched at bind time)
@@ -114,6 +117,7 @@ struct Plan {
     void *bound_leaves = nullptr;
     void *bound_amps = nullptr;
     void *bound_env = nullptr;
+    void *bound_kept = nullptr;
 
     // adjoint plans: where the root's cotangent seed sits in the argument buffer,
     // so that a cached plan takes new cotangents without being rebuilt
@@ -139,6 +143,18 @@ struct Network {
     bool open_set = false;
     std::vector<int64_t> free_open;   // open legs left unfixed: every value of them per row
                                       // (order = digit order of the values, first slowest)
+    // kept shared work: results of sub-trees without fixed labels, kept on the
+    // device across contractions while `kept_key` (path, slicing, tensors, legs) holds
+    struct KeptEntry {
+        size_t off = 0, bytes = 0;
+        bool ready = false;
+    };
+    int64_t keep_min = 0;             // keep such results of at least this many elements; 0: off
+    uint64_t tensors_version = 0;     // bumped by every tensor update
+    std::unordered_map<int32_t, KeptEntry> kept;   // tree node -> its result in d_kept
+    std::vector<int64_t> kept_key;
+    void *d_kept = nullptr;
+    size_t d_kept_bytes = 0;
     std::vector<std::pair<int32_t, int32_t>> path;
     uint64_t path_version = 0;
     std::vector<int64_t> sliced;
@@ -201,6 +217,7 @@ void upload_leaf(Network &net, int32_t tensor_id, void *stream);
 void upload_all(Network &net, const jet_c64 *data, void *stream);
 void *device_alloc(size_t bytes);
 void device_free(void *p);
+void sync_stream(Network &net, void *stream);   // the given stream, or the library's own when NULL
 void copy_d2h(void *dst, const void *src, size_t bytes, void *stream);
 void copy_d2d_async(void *dst, const void *src, size_t bytes, void *stream);
 void copy_h2d_sync(void *dst, const void *src, size_t bytes, void *stream);

@@ -28,7 +28,9 @@ namespace jet {
 
 namespace {
 
-enum Base : int32_t { BASE_LEAVES = 0, BASE_ARENA = 1, BASE_BLOB = 2, BASE_AMPS = 3, BASE_STATUS = 4, BASE_ENV = 5 };
+enum Base : int32_t {
+    BASE_LEAVES = 0, BASE_ARENA = 1, BASE_BLOB = 2, BASE_AMPS = 3, BASE_STATUS = 4, BASE_ENV = 5, BASE_KEPT = 6
+};
 
 struct View {
     std::vector<int64_t> labels;   // layout order, slowest first
@@ -225,6 +227,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     std::vector<NodeInfo> node(n_nodes);
     std::vector<std::vector<int32_t>> inst_of(n_nodes);   // per node: instance id for each alpha
 
+    std::vector<char> leaf_fixed(n_leaves, 0);   // the leaf carries a fixed (sliced or bra) label
     // ---- leaves: strided views with the fixed labels removed
     for (int32_t i = 0; i < n_leaves; ++i) {
         const Leaf &L = net.leaves[i];
@@ -245,6 +248,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             }
         }
         N.view.size = prod(N.view.dims);
+        leaf_fixed[i] = !fx.empty();
         auto &ids = inst_of[i];
         ids.resize(n_assign);
         if (fx.empty()) {
@@ -281,7 +285,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     auto base_ref = [&](int32_t id, int32_t inst) -> std::pair<int32_t, int64_t> {
         const NodeInfo &N = node[id];
         if (N.base == BASE_LEAVES) return {BASE_LEAVES, N.inst_off[inst] * es};
-        return {BASE_ARENA, N.buf_off + (int64_t)inst * N.view.size * es};
+        return {N.base, N.buf_off + (int64_t)inst * N.view.size * es};
     };
 
     auto dimprod = [&](const std::vector<int64_t> &ls) {
@@ -580,6 +584,51 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         if (node[x].depth != node[y].depth) return node[x].depth < node[y].depth;
         return (int)node[x].small > (int)node[y].small;
     });
+
+    // ---- kept shared work: a sub-tree whose leaves carry no fixed label has the
+    // same value in every contraction of this network (Section 3.2's shared work,
+    // kept for later use).  Its maximal such nodes of at least keep_min elements
+    // keep their results in a device pool: a ready result replaces its sub-tree
+    // (no launches), a missing one is computed into the pool by this plan.
+    std::vector<char> skip(n_nodes, 0);
+    if (net.keep_min > 0 && !grad && P.reuse) {
+        std::vector<char> inv(n_nodes, 0);
+        for (int32_t i = 0; i < n_leaves; ++i) inv[i] = !leaf_fixed[i];
+        for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
+            const int32_t v = n_leaves + k;
+            inv[v] = inv[node[v].a] && inv[node[v].b];
+        }
+        size_t pool = 0;
+        for (auto &kv : net.kept) pool = std::max(pool, kv.second.off + kv.second.bytes);
+        for (int32_t k = 0; k < (int32_t)net.path.size(); ++k) {
+            const int32_t v = n_leaves + k;
+            if (!inv[v] || (parent[v] >= 0 && inv[parent[v]]) || node[v].view.size < net.keep_min) continue;
+            auto it = net.kept.find(v);
+            if (it == net.kept.end()) {
+                Network::KeptEntry e;
+                e.off = (pool + 255) / 256 * 256;
+                e.bytes = (size_t)node[v].view.size * es;
+                pool = e.off + e.bytes;
+                it = net.kept.emplace(v, e).first;
+            }
+            if (it->second.ready) {   // the sub-tree's work is done: read the kept result
+                std::vector<int32_t> st{v};
+                while (!st.empty()) {
+                    const int32_t x = st.back();
+                    st.pop_back();
+                    if (x < n_leaves) continue;
+                    skip[x] = 1;
+                    st.push_back(node[x].a);
+                    st.push_back(node[x].b);
+                }
+                node[v].base = BASE_KEPT;
+                node[v].buf_off = (int64_t)it->second.off;
+            } else {
+                P.kept_fill.push_back(v);
+            }
+        }
+        P.kept_pool_bytes = pool;
+    }
 
     // pending batch of small contractions (one tree level)
     std::vector<Plan::Patch> batch_patches;   // offsets relative to the batch's task array
@@ -984,6 +1033,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
 
     // ---- pass 2, launch order: arena offsets, pointer tables, launches
     for (int32_t v : order) {
+        if (skip[v]) continue;   // a kept result stands for this sub-tree
         NodeInfo &N = node[v];
         const int32_t a = N.a, b = N.b;
         const NodeInfo &NA = node[a], &NB = node[b];
@@ -993,17 +1043,22 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const bool use_gemm = N.use_gemm, a_big = N.a_big;
         if (!N.small || (!batch_nodes.empty() && node[batch_nodes.front()].depth != N.depth)) flush_batch();
 
-        // arena buffer for all instances
+        // arena buffer for all instances (a kept result: its slot in the pool)
         size_t nbytes = (size_t)N.n_inst * N.view.size * es;
-        N.buf_off = (int64_t)arena.alloc(nbytes);
-        N.base = BASE_ARENA;
+        if (std::find(P.kept_fill.begin(), P.kept_fill.end(), v) != P.kept_fill.end()) {
+            N.base = BASE_KEPT;
+            N.buf_off = (int64_t)net.kept.at(v).off;
+        } else {
+            N.buf_off = (int64_t)arena.alloc(nbytes);
+            N.base = BASE_ARENA;
+        }
 
         // per-instance pointer tables
         std::vector<std::pair<int32_t, int64_t>> pa, pb, pc;
         for (int64_t i = 0; i < N.n_inst; ++i) {
             pa.push_back(base_ref(a, N.ia[i]));
             pb.push_back(base_ref(b, N.ib[i]));
-            pc.push_back({BASE_ARENA, N.buf_off + i * N.view.size * es});
+            pc.push_back({N.base, N.buf_off + i * N.view.size * es});
         }
         std::vector<int64_t> un = VA.labels;
         for (int64_t l : fb) un.push_back(l);

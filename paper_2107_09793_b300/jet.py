@@ -21,7 +21,8 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_path_greedy", "jet_path_greedy_batch", "jet_slice", "jet_slice_auto", "jet_contract", "jet_contract_async",
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
-           "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices"]
+           "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices",
+           "jet_network_keep_shared"]
 
 
 class JetError(RuntimeError):
@@ -79,6 +80,7 @@ def lib():
             "jet_network_set_free": (I32, [P, I32, P]),
             "jet_path_reconfigure": (I32, [P, I32, I32, I32, P, P, P]),
             "jet_plan_slices": (I32, [P, I32, P, I32, P, P]),
+            "jet_network_keep_shared": (I32, [P, I64]),
             "jet_tensor_update": (I32, [P, I32, P]),
             "jet_tensors_upload": (I32, [P, P, P]),
             "jet_network_n_values": (I64, [P]),
@@ -182,6 +184,11 @@ class Network:
         _check(lib().jet_network_set_open(self._h, a.size, a.ctypes.data))
         self.n_out = a.size
         self.n_elem = 1
+
+    def keep_shared(self, min_elems: int):
+        """jet_network_keep_shared: keep results of sub-trees without fixed labels
+        (at least min_elems elements) for later contractions; 0 switches it off."""
+        _check(lib().jet_network_keep_shared(self._h, int(min_elems)))
 
     def set_free(self, free_labels: Sequence[int]):
         """jet_network_set_free: these open legs stay unfixed; every contraction
