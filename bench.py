@@ -667,7 +667,8 @@ def run_impl(args):
         "reuse_fraction": st["reuse_fraction"], "workspace_gb": st["workspace_bytes"] / 1e9,
         "amplitude": [amp.real, amp.imag], "rel_err_vs_oracle": err,
         "fp32_simt": modes.get("fp32"), "modes": modes, "roofline": roof, "breakdown": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": int(st["n_launches"]) * args.steps,
+        # both loops of the timed region (the step, then the instrumented plan)
+        "gpu_launches": 2 * int(st["n_launches"]) * args.steps,
         "other_workloads": others,
         "wall_s_timed": t_wall1 - t_wall0,
     }
