@@ -174,6 +174,20 @@ int jet_network_set_open(jet_network *net, int32_t n_out, const int64_t *out_lab
  * Errors: JET_EINVAL (min_elems < 0). */
 int jet_network_keep_shared(jet_network *net, int64_t min_elems);
 
+/* Store the kept shared work in a file, and read it back into a network that
+ * has the same tensors (by value), path, sliced labels, open and free legs,
+ * precision and keep threshold -- in this process or another one (the
+ * paper's conclusion: shared work stored on disk for any later slice or
+ * amplitude calculation).  save writes every ready kept result (HOST file:
+ * a key of what the results depend on, then the results).  load (keeping must
+ * be on) checks that key against the network and marks the results ready; the
+ * next contraction reads them instead of computing their sub-trees.
+ * Errors: JET_ESTATE (nothing kept yet / keeping off), JET_EINVAL (file
+ * unreadable or not written by save, or written for another network, path,
+ * slicing, legs, precision, threshold or tensor values). */
+int jet_network_save_shared(jet_network *net, const char *file);
+int jet_network_load_shared(jet_network *net, const char *file);
+
 /* Leave some output legs free (Section 2.2.1: an open leg without a bra stays
  * an index of the result; Section 3.2: a batch of amplitudes is one
  * multi-contraction whose shared work is done once).  Every contraction then

@@ -2,6 +2,8 @@
 // arguments, works on copies, and converts internal errors into JET_E* codes
 // plus a thread-local message; nothing escapes the boundary as an exception.
 #include <algorithm>
+#include <array>
+#include <cstdio>
 #include <cstring>
 #include <exception>
 #include <new>
@@ -265,6 +267,112 @@ int jet_network_keep_shared(jet_network *net, int64_t min_elems)
             device_free(net->d_kept);
             net->d_kept = nullptr;
             net->d_kept_bytes = 0;
+        }
+    });
+}
+
+// What kept results depend on, by content (so that a file written by one
+// process can be checked by another): precision, keep threshold, the path, the
+// sliced labels, the open and free legs, and an FNV-1a hash of every tensor
+// value as it sits on the device.
+static std::vector<uint64_t> kept_content_key(Network &net)
+{
+    auto fnv = [](const void *p, size_t n, uint64_t h) {
+        const uint8_t *b = (const uint8_t *)p;
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+        return h;
+    };
+    ensure_leaves_on_device(net);
+    std::vector<jet_c64> vals((size_t)net.n_values);
+    copy_d2h(vals.data(), net.d_leaves, vals.size() * sizeof(jet_c64), net.stream);
+    std::vector<uint64_t> key{0x4A45544B45505431ull, (uint64_t)net.opt.precision, (uint64_t)net.keep_min,
+                              (uint64_t)net.leaves.size(), (uint64_t)net.path.size()};
+    for (auto &pr : net.path) key.push_back(((uint64_t)(uint32_t)pr.first << 32) | (uint32_t)pr.second);
+    for (auto *ls : {&net.sliced, &net.open, &net.free_open}) {
+        key.push_back(ls->size());
+        for (int64_t l : *ls) key.push_back((uint64_t)l);
+    }
+    key.push_back(fnv(vals.data(), vals.size() * sizeof(jet_c64), 1469598103934665603ull));
+    return key;
+}
+
+int jet_network_save_shared(jet_network *net, const char *file)
+{
+    return guarded([&] {
+        if (!net || !file) fail(JET_EINVAL, "NULL argument");
+        std::vector<std::pair<int32_t, Network::KeptEntry>> ready;
+        for (auto &kv : net->kept)
+            if (kv.second.ready) ready.push_back(kv);
+        if (ready.empty()) fail(JET_ESTATE, "no kept shared work yet (jet_network_keep_shared, then contract)");
+        std::sort(ready.begin(), ready.end(), [](auto &x, auto &y) { return x.first < y.first; });
+        const auto key = kept_content_key(*net);
+        std::vector<uint8_t> pool(net->d_kept_bytes);
+        copy_d2h(pool.data(), net->d_kept, pool.size(), net->stream);
+        FILE *f = std::fopen(file, "wb");
+        if (!f) fail(JET_EINVAL, std::string("cannot open ") + file);
+        bool ok = true;
+        auto put = [&](const void *p, size_t n) { ok = ok && std::fwrite(p, 1, n, f) == n; };
+        const uint64_t nk = key.size(), ne = ready.size(), np = pool.size();
+        put(&nk, 8);
+        put(key.data(), 8 * nk);
+        put(&ne, 8);
+        for (auto &e : ready) {
+            const uint64_t rec[3] = {(uint64_t)e.first, e.second.off, e.second.bytes};
+            put(rec, sizeof rec);
+        }
+        put(&np, 8);
+        put(pool.data(), np);
+        ok = (std::fclose(f) == 0) && ok;
+        if (!ok) fail(JET_EINVAL, std::string("write failed: ") + file);
+    });
+}
+
+int jet_network_load_shared(jet_network *net, const char *file)
+{
+    return guarded([&] {
+        if (!net || !file) fail(JET_EINVAL, "NULL argument");
+        if (net->keep_min <= 0) fail(JET_ESTATE, "keeping is off (jet_network_keep_shared)");
+        FILE *f = std::fopen(file, "rb");
+        if (!f) fail(JET_EINVAL, std::string("cannot open ") + file);
+        bool ok = true;
+        auto get = [&](void *p, size_t n) { ok = ok && std::fread(p, 1, n, f) == n; };
+        uint64_t nk = 0;
+        get(&nk, 8);
+        std::vector<uint64_t> key(ok && nk < (1u << 24) ? nk : 0);
+        get(key.data(), 8 * key.size());
+        uint64_t ne = 0;
+        get(&ne, 8);
+        std::vector<std::array<uint64_t, 3>> recs(ok && ne < (1u << 24) ? ne : 0);
+        for (auto &r : recs) get(r.data(), sizeof r);
+        uint64_t np = 0;
+        get(&np, 8);
+        std::vector<uint8_t> pool(ok ? np : 0);
+        get(pool.data(), pool.size());
+        std::fclose(f);
+        if (!ok || key.size() != nk || recs.size() != ne) fail(JET_EINVAL, std::string("not a kept-work file: ") + file);
+        if (key != kept_content_key(*net))
+            fail(JET_EINVAL, "the saved shared work belongs to another network, path, slicing, legs, precision, "
+                             "threshold or tensor values");
+        for (auto &r : recs)
+            if (r[1] + r[2] > np) fail(JET_EINVAL, "corrupt kept-work file");
+        invalidate_plan(*net);
+        check_kept_key(*net);
+        net->kept.clear();
+        if (net->d_kept_bytes < np) {
+            sync_stream(*net, nullptr);
+            device_free(net->d_kept);
+            net->d_kept = nullptr;
+            net->d_kept_bytes = 0;
+            net->d_kept = device_alloc(np);
+            net->d_kept_bytes = np;
+        }
+        copy_h2d_sync(net->d_kept, pool.data(), np, net->stream);
+        for (auto &r : recs) {
+            Network::KeptEntry e;
+            e.off = r[1];
+            e.bytes = r[2];
+            e.ready = true;
+            net->kept[(int32_t)r[0]] = e;
         }
     });
 }

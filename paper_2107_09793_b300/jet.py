@@ -22,7 +22,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
            "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices",
-           "jet_network_keep_shared"]
+           "jet_network_keep_shared", "jet_network_save_shared", "jet_network_load_shared"]
 
 
 class JetError(RuntimeError):
@@ -81,6 +81,8 @@ def lib():
             "jet_path_reconfigure": (I32, [P, I32, I32, I32, P, P, P]),
             "jet_plan_slices": (I32, [P, I32, P, I32, P, P]),
             "jet_network_keep_shared": (I32, [P, I64]),
+            "jet_network_save_shared": (I32, [P, ctypes.c_char_p]),
+            "jet_network_load_shared": (I32, [P, ctypes.c_char_p]),
             "jet_tensor_update": (I32, [P, I32, P]),
             "jet_tensors_upload": (I32, [P, P, P]),
             "jet_network_n_values": (I64, [P]),
@@ -189,6 +191,14 @@ class Network:
         """jet_network_keep_shared: keep results of sub-trees without fixed labels
         (at least min_elems elements) for later contractions; 0 switches it off."""
         _check(lib().jet_network_keep_shared(self._h, int(min_elems)))
+
+    def save_shared(self, path: str):
+        """jet_network_save_shared: the kept shared work to a file."""
+        _check(lib().jet_network_save_shared(self._h, os.fsencode(path)))
+
+    def load_shared(self, path: str):
+        """jet_network_load_shared: kept shared work from a file written for this network."""
+        _check(lib().jet_network_load_shared(self._h, os.fsencode(path)))
 
     def set_free(self, free_labels: Sequence[int]):
         """jet_network_set_free: these open legs stay unfixed; every contraction

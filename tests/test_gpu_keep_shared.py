@@ -101,3 +101,39 @@ def test_whole_network_kept_with_free_legs():
     third = net.contract(rows)[0]
     assert np.allclose(third, first, rtol=1e-6, atol=1e-9)
     net.close()
+
+
+def test_kept_work_saved_and_loaded_by_another_handle(tmp_path):
+    """The kept shared work written to a file and read by a fresh handle of the
+    same network (same tensors, path, legs, threshold): its first contraction
+    already skips the kept sub-trees and matches; a handle with one tensor
+    changed refuses the file."""
+    circ = gbs_lattice_circuit(2, 5, 4, 2, seed=13)
+    tn = circuit_to_network(circ)
+    b1, b2 = _batches(circ.n, 4, 5)
+    first = jet.from_network(tn, precision="fp32")
+    first.path_greedy_batch(b1, seed=1, n_trials=8)
+    path = first.path_get()
+    first.keep_shared(1 << 10)
+    first.contract(b1)
+    ref = first.contract(b2)
+    f_kept = first.stats()["flop_executed"]
+    fn = str(tmp_path / "kept.bin")
+    first.save_shared(fn)
+    second = jet.from_network(tn, precision="fp32")
+    second.path_set(path)
+    second.keep_shared(1 << 10)
+    second.load_shared(fn)
+    got = second.contract(b2)
+    assert second.stats()["flop_executed"] == f_kept
+    assert np.allclose(got, ref, rtol=1e-6, atol=1e-7 * np.abs(ref).max())
+    data = list(tn.data)
+    data[0] = np.asarray(data[0], np.complex64) * np.complex64(0.5)
+    other = jet.Network(tn.labels, data, precision="fp32")
+    other.set_open(tn.open_labels)
+    other.path_set(path)
+    other.keep_shared(1 << 10)
+    with pytest.raises(jet.JetError):
+        other.load_shared(fn)
+    for n in (first, second, other):
+        n.close()
