@@ -52,8 +52,9 @@ typedef struct { double re, im; } jet_c128;
 
 /* Arithmetic used for the large (GEMM-shaped) pairwise contractions and, in
  * the split modes (every mode but FP32 and FP64), for the application of a
- * small operand with at most 256 summed and 32 free entries, and at least
- * apply_tc_min_kf of them in all (summed x free), to a large one (TF32 hi + lo,
+ * small operand with at most 256 summed and 32 free entries (64 free when it
+ * has at most 32 summed), and at least apply_tc_min_kf of them in all
+ * (summed x free), to a large one (TF32 hi + lo,
  * three products; one in JET_PREC_TF32).  Other small contractions always run
  * on CUDA cores in FP32 (FP64 in JET_PREC_FP64).
  * Intermediates are complex64, except in JET_PREC_FP64 (complex128).  Slice
@@ -77,7 +78,10 @@ typedef struct {
     int32_t use_graph;        /* 1 (default): record the launch sequence in a CUDA graph */
     int32_t device;           /* CUDA device ordinal, default 0                          */
     int64_t gemm_min_k;       /* contractions with a summed extent >= this (and both free
-                                 extents >= 64) take the GEMM route; default 16           */
+                                 extents >= 64) take the GEMM route, except, in the split
+                                 modes, those with a summed extent <= 32 and one free
+                                 extent <= 64 that the tensor-core small-operand form
+                                 takes; default 16                                        */
     int64_t workspace_limit;  /* bytes of device workspace a contraction may use; 0 = no
                                  limit.  When the plan for every slice needs more,
                                  jet_contract / jet_contract_async run the slices in

@@ -446,7 +446,8 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
     const uint32_t sA = smem_u32(smem + g * JET_APPLY_TC_ABYTES), sB = smem_u32(smem + G * JET_APPLY_TC_ABYTES);
     const uint32_t bar = smem_u32(&bars[g]);
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
-    constexpr uint32_t COLS = G <= 2 ? 128 : 256;   // 64 columns per group, allocated as a power of two
+    // TMEM columns per group (the MMA's N, up to 64 or 128), allocated as a power of two
+    const uint32_t span = nrl <= 64 ? 64u : 128u, COLS = (G <= 2 ? 2u : 4u) * span;
 
     if (tid == 0) {
         for (int i = 0; i < G; ++i) mbar_init(smem_u32(&bars[i]), 1);
@@ -461,7 +462,7 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_holder + 64 * g;
+    const uint32_t tmem = tmem_holder + span * g;
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
     // kind::tf32, FP32 D, K-major A and B, M = 128, N = nrl
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nrl >> 3) << 17) | ((uint32_t)(ATC_M >> 4) << 24);
@@ -555,8 +556,9 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool last = c + 1 == nch;
+            constexpr int HMAX = MULTI ? JET_APPLY_TC_MAXF_MULTI / 8 : JET_APPLY_TC_MAXF / 8;   // 16-column groups
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
+            for (int h = 0; h < HMAX; ++h) {
                 if (h < nr) {
                     uint32_t R[16];
                     JET_TMEM_LD16(trow + 16 * h, R);
@@ -689,7 +691,8 @@ static cudaError_t launch_apply_tc(const ApplyArgs &a, const LaunchCfg &c, cudaS
     const int smem = jet_apply_tc_smem(G, a.nk, a.nf);
     if (smem > ATC_SMEM_MAX) return cudaErrorInvalidValue;
     const bool pow2 = c.variant & 4, multi = a.nk > ATC_KC;
-    if (multi && G != 2) return cudaErrorInvalidValue;   // promotion registers: two groups only
+    // promotion registers: two groups and at most 32 free entries only
+    if (multi && (G != 2 || a.nf > JET_APPLY_TC_MAXF_MULTI)) return cudaErrorInvalidValue;
     if (multi) {
         if (pow2) apply_tc_c64<2, true, true><<<c.gx, 256, smem, s>>>(a);
         else apply_tc_c64<2, true, false><<<c.gx, 256, smem, s>>>(a);

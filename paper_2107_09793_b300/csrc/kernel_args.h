@@ -15,7 +15,8 @@
 #define JET_APPLY_MAXF 256   // small-operand application: max free entries of the small operand
 #define JET_APPLY_MAXB 1024  // held form: max entries of the small operand (summed extent padded)
 #define JET_APPLY_STREAMF 32 // streamed form: max free entries of the small operand
-#define JET_APPLY_TC_MAXF 32 // tensor-core form: max free entries of the small operand (N <= 64 real columns)
+#define JET_APPLY_TC_MAXF 64 // tensor-core form: max free entries of the small operand (N <= 128 real columns)
+#define JET_APPLY_TC_MAXF_MULTI 32 // ... when the summed extent is above one 32-entry chunk (FP32 promotion registers)
 #define JET_APPLY_TC_ABYTES 65536 // tensor-core form: one group's A chunk, hi + lo TF32 planes of 128 x 64
 #define JET_APPLY_TC_SMEM_MAX 231424 // tensor-core form: dynamic shared memory cap (227 KiB less 1 KiB)
 

@@ -327,11 +327,23 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     // two), 0 when the form does not apply
     auto apply_tc_groups = [&](int64_t nk, int64_t nf) -> int {
         if (!tc_mode || fp64 || nk * nf < net.opt.apply_tc_min_kf || nk > JET_APPLY_MAXK || nf < 1 ||
-            nf > JET_APPLY_TC_MAXF)
+            nf > JET_APPLY_TC_MAXF || (nk > 32 && nf > JET_APPLY_TC_MAXF_MULTI))
             return 0;
         if (nk <= 32 && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 3;
         if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
         return 0;
+    };
+    // The GEMM route: a summed extent of at least gemm_min_k and both free
+    // extents of 64 or more, except where the summed extent is one chunk (<= 32)
+    // and one free side has at most 64 entries: the tensor-core small-operand
+    // form then reads the large operand once, where the GEMM route first splits
+    // it into planes (reading it once and writing it twice over).
+    auto tc_apply_short = [&](int64_t nK, int64_t nFa, int64_t nFb) {
+        const int64_t nfs = std::min(nFa, nFb);
+        return nK <= 32 && nfs <= JET_APPLY_TC_MAXF && apply_tc_groups(nK, nfs) > 0;
+    };
+    auto gemm_route = [&](int64_t nK, int64_t nFa, int64_t nFb) {
+        return gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64 && !tc_apply_short(nK, nFa, nFb);
     };
     auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big,
                               int64_t n_inst) {
@@ -366,8 +378,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         for (int64_t l : ls)
             if (find_pos(labset[v], l) < 0) Fs.push_back(l);
         const int64_t sv = dimprod(labset[v]), ss = dimprod(ls);
-        const bool p_gemm = gemm_ok && !Kp.empty() && dimprod(Kp) >= net.opt.gemm_min_k && dimprod(Fp) >= 64 &&
-                            dimprod(Fs) >= 64;
+        const bool p_gemm = !Kp.empty() && gemm_route(dimprod(Kp), dimprod(Fp), dimprod(Fs));
         if (p_gemm || Kp.empty() || ss > 2048 || sv <= ss) return {};
         return Kp;
     };
@@ -413,7 +424,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         for (int64_t l : VB.labels)
             if (find_pos(VA.labels, l) < 0) N.fb.push_back(l);
         const int64_t nK = dimprod(N.K), nFa = dimprod(N.fa), nFb = dimprod(N.fb);
-        N.use_gemm = gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64;
+        N.use_gemm = gemm_route(nK, nFa, nFb) ||
+                     (gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64 &&
+                      !apply_ok_views(VA, VB, N.K, VA.size >= VB.size, N.n_inst));
         // a skinny product (one free side of 8..63 entries, the other large) that no
         // small-operand form takes: the GEMM route with partly filled tiles still runs
         // far faster than the strided direct contraction
@@ -467,8 +480,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 for (int64_t l : labset[v]) (find_pos(ls, l) >= 0 ? Kp : Fp).push_back(l);
                 for (int64_t l : ls)
                     if (find_pos(labset[v], l) < 0) Fs.push_back(l);
-                const bool p_gemm = !Kp.empty() && dimprod(Kp) >= net.opt.gemm_min_k && dimprod(Fp) >= 64 &&
-                                    dimprod(Fs) >= 64;
+                const bool p_gemm = !Kp.empty() && gemm_route(dimprod(Kp), dimprod(Fp), dimprod(Fs));
                 auto holds_all = [&](const std::vector<int64_t> &X) {
                     for (int64_t l : Kp)
                         if (find_pos(X, l) < 0) return false;

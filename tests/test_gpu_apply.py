@@ -7,8 +7,10 @@ and the split modes with the tensor-core form switched off).
 Shapes cover: one chunk of 32 summed entries with a ragged, non-power-of-two
 fiber count; summed and free extents that are not multiples of the 8-entry
 blocks (21 x 5, 200 x 3); several chunks per tile (128 and 200 summed entries,
-the FP32 register promotion); the largest free extent (32, N = 64 real
-columns); a summed label at stride 1 in A (fibers at stride 2); and a sliced
+the FP32 register promotion); wide free extents (32, 48 and 64: N = 64, 96 and
+128 real columns, the last two with 128 TMEM columns per thread group; 16 x 64
+has both free sides of 64 or more, a product the GEMM route would otherwise
+take); a summed label at stride 1 in A (fibers at stride 2); and a sliced
 summed label, so the node runs as two instances in one launch (the small
 operand is rebuilt per instance).  The fast_ cases put the 7 fastest labels of A
 on the fibers (one of them reading a leaf that is 8- but not 16-byte aligned).
@@ -51,6 +53,10 @@ CASES = {
     "k200_f3_chunks": ([0, 1, 2, 10, 11], [20, 11, 10], {0: 33, 1: 31, 2: 33, 10: 8, 11: 25, 20: 3}, []),
     # 16 summed in the middle of A, 32 free: N = 64 real columns
     "k16_f32": ([0, 10, 1], [10, 20], {0: 256, 1: 256, 10: 16, 20: 32}, []),
+    # 16 summed, 64 free (N = 128 real columns, three groups); both free sides >= 64
+    "k16_f64": ([0, 10, 1], [10, 20], {0: 256, 1: 256, 10: 16, 20: 64}, []),
+    # 32 summed (4 x 8), 48 free (N = 96; the operand planes leave room for two groups)
+    "k32_f48": ([0, 10, 11, 1], [11, 20, 10], {0: 128, 1: 256, 10: 4, 11: 8, 20: 48}, []),
     # a summed binary label at stride 1 in A: the fibers sit at stride 2
     "k32_stride2": (list(range(100, 115)) + [10, 11, 12, 13, 14], [20, 10, 11, 12, 13, 14], {20: 8}, []),
     # 64 summed with one label sliced: the node runs as 2 instances of 32 summed
@@ -143,11 +149,13 @@ def test_apply_tensor_core_other_modes(case, prec):
     assert _check(case, prec, True, apply_tc_min_kf=1) <= TOL[prec]
 
 
-@pytest.mark.parametrize("case", sorted(CASES))
+# 32 x 48 is past the CUDA-core forms (held: 1024 padded entries; streamed: 32 free)
+@pytest.mark.parametrize("case", sorted(set(CASES) - {"k32_f48"}))
 def test_apply_cuda_core_forms(case):
-    """FP32 mode, and a split mode with the tensor-core form switched off."""
-    assert _check(case, "fp32", False) <= TOL["fp32"]
-    assert _check(case, "fp16x3", False, apply_tc_min_kf=1 << 20) <= TOL["fp16x3"]
+    """FP32 mode, and a split mode with the tensor-core form switched off (the
+    GEMM route too, which would take the 16 x 64 product)."""
+    assert _check(case, "fp32", False, gemm_min_k=1 << 20) <= TOL["fp32"]
+    assert _check(case, "fp16x3", False, apply_tc_min_kf=1 << 20, gemm_min_k=1 << 20) <= TOL["fp16x3"]
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
