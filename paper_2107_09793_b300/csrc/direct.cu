@@ -97,7 +97,11 @@ __global__ void __launch_bounds__(256) direct_kernel(const __grid_constant__ Dir
 
 // Few outputs, long summed index: block (part, output group, instance) sums
 // its slice of khi values over all klo entries, block-reduces, writes a partial.
-template <typename V, bool POW2>
+// P > 0: the group's 8 outputs are the outer product of values of A and B, each
+// loaded once per summed entry (NA + NB loads, not 16): P = NA in {1, 2, 4, 8}
+// with A's NA values fastest (output j = ib * NA + ia), or P = 16 + NB with B's
+// NB values fastest (j = ia * NB + ib).
+template <typename V, bool POW2, int P>
 __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constant__ DirectArgs a)
 {
     extern __shared__ int32_t sm[];
@@ -133,14 +137,35 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
     }
     const int64_t h0 = (int64_t)blockIdx.x * a.khi_per_part;
     const int64_t h1 = (h0 + a.khi_per_part) < a.n_khi ? (h0 + a.khi_per_part) : a.n_khi;
-    for (int64_t h = h0; h < h1; ++h) {
-        int64_t ha = 0, hb = 0;
-        decode<POW2>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
-        for (int q = threadIdx.x; q < a.n_klo; q += blockDim.x) {
-            const int64_t ka = ha + sKA[q], kb = hb + sKB[q];
+    if (P > 0) {
+        constexpr bool BF = P & 16;   // B's values fastest
+        constexpr int NF = (P & 15) ? (P & 15) : 1, NS = JET_SPLITK_G / NF;   // fastest side's values, slowest side's
+        constexpr int NA = BF ? NS : NF, NB = BF ? NF : NS;
+        for (int64_t h = h0; h < h1; ++h) {
+            int64_t ha = 0, hb = 0;
+            decode<POW2>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
+            for (int q = threadIdx.x; q < a.n_klo; q += blockDim.x) {
+                const int64_t ka = ha + sKA[q], kb = hb + sKB[q];
+                V xa[NA], xb[NB];
 #pragma unroll
-            for (int j = 0; j < JET_SPLITK_G; ++j)
-                if (j < nout) acc[j] = cmul_add(acc[j], __ldg(A + oa[j] + ka), __ldg(B + ob[j] + kb));
+                for (int i = 0; i < NA; ++i) xa[i] = __ldg(A + oa[BF ? i * NB : i] + ka);
+#pragma unroll
+                for (int i = 0; i < NB; ++i) xb[i] = __ldg(B + ob[BF ? i : i * NA] + kb);
+#pragma unroll
+                for (int j = 0; j < JET_SPLITK_G; ++j)
+                    acc[j] = cmul_add(acc[j], xa[BF ? j / NB : j % NA], xb[BF ? j % NB : j / NA]);
+            }
+        }
+    } else {
+        for (int64_t h = h0; h < h1; ++h) {
+            int64_t ha = 0, hb = 0;
+            decode<POW2>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
+            for (int q = threadIdx.x; q < a.n_klo; q += blockDim.x) {
+                const int64_t ka = ha + sKA[q], kb = hb + sKB[q];
+#pragma unroll
+                for (int j = 0; j < JET_SPLITK_G; ++j)
+                    if (j < nout) acc[j] = cmul_add(acc[j], __ldg(A + oa[j] + ka), __ldg(B + ob[j] + kb));
+            }
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -355,10 +380,23 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
     dim3 grid(c.gx, c.gy, c.gz);
     bool fp64 = c.variant & 1, splitk = c.variant & 2, pow2 = c.variant & 4;
     size_t smem = c.smem;
+    const int na = a.splitk_na;
+    if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20) ||
+                    a.n_out % JET_SPLITK_G != 0))
+        return cudaErrorInvalidValue;
 #define JET_DIRECT_LAUNCH(V, P)                                                                 \
     do {                                                                                        \
-        if (splitk) direct_splitk_kernel<V, P><<<grid, c.block, smem, s>>>(a);                  \
-        else direct_kernel<V, P><<<grid, c.block, smem, s>>>(a);                                \
+        if (splitk) {                                                                           \
+            switch (na) {                                                                       \
+            case 1: direct_splitk_kernel<V, P, 1><<<grid, c.block, smem, s>>>(a); break;        \
+            case 2: direct_splitk_kernel<V, P, 2><<<grid, c.block, smem, s>>>(a); break;        \
+            case 4: direct_splitk_kernel<V, P, 4><<<grid, c.block, smem, s>>>(a); break;        \
+            case 8: direct_splitk_kernel<V, P, 8><<<grid, c.block, smem, s>>>(a); break;        \
+            case 18: direct_splitk_kernel<V, P, 18><<<grid, c.block, smem, s>>>(a); break;      \
+            case 20: direct_splitk_kernel<V, P, 20><<<grid, c.block, smem, s>>>(a); break;      \
+            default: direct_splitk_kernel<V, P, 0><<<grid, c.block, smem, s>>>(a); break;       \
+            }                                                                                   \
+        } else direct_kernel<V, P><<<grid, c.block, smem, s>>>(a);                              \
     } while (0)
     if (fp64) {
         if (pow2) JET_DIRECT_LAUNCH(double2, true);

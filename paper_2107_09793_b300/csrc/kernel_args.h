@@ -44,7 +44,10 @@ struct DirectArgs {
     int32_t n_inst, ksplit;
     int32_t row_rank, khi_rank;
     int32_t khi_per_part;           // split-K: khi values per part
-    int32_t pad_;
+    int32_t splitk_na;              // split-K: 0, or the outer-product pattern of every group of
+                                    // 8 outputs, whose operand values are then read once per
+                                    // summed entry: NA in {1, 2, 4, 8} = NA values of A (fastest)
+                                    // x 8 / NA of B; 16 + NB (NB in {2, 4}) = NB of B fastest
     int64_t row_dim[JET_MAXR], row_sA[JET_MAXR], row_sB[JET_MAXR];   // fastest label first
     int64_t khi_dim[JET_MAXR], khi_sA[JET_MAXR], khi_sB[JET_MAXR];   // fastest label first
 };

@@ -869,6 +869,38 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
                 d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
             }
+            // split form: when every group of 8 outputs is an outer product of NA
+            // values of A and NB = 8 / NA of B, each is loaded once per summed entry
+            // (fewest loads first: NA = 2 or 4 take 6, NA = 1 or 8 take 9); A's
+            // values fastest (pattern NA) or B's (pattern 16 + NB)
+            if (d.ksplit > 1 && d.n_out % JET_SPLITK_G == 0 && d.n_out <= (1 << 16)) {
+                std::vector<int64_t> eA(d.n_out), eB(d.n_out);
+                for (int64_t e = 0; e < d.n_out; ++e) {
+                    int64_t r = e / ncols, c = e - r * ncols, oa = colA[c], ob = colB[c];
+                    for (int j = 0; j < d.row_rank; ++j) {
+                        const int64_t dg = r % d.row_dim[j];
+                        r /= d.row_dim[j];
+                        oa += dg * d.row_sA[j];
+                        ob += dg * d.row_sB[j];
+                    }
+                    eA[e] = oa;
+                    eB[e] = ob;
+                }
+                for (int pat : {2, 4, 18, 20, 1, 8}) {
+                    const bool bf = pat & 16;
+                    const int nf = pat & 15;   // values of the fastest side
+                    bool ok = true;
+                    for (int64_t e = 0; ok && e < d.n_out; ++e) {
+                        const int64_t g0 = e - e % JET_SPLITK_G, j = e - g0;
+                        const int64_t fast = g0 + j % nf, slow = g0 + nf * (j / nf);
+                        ok = bf ? (eB[e] == eB[fast] && eA[e] == eA[slow]) : (eA[e] == eA[fast] && eB[e] == eB[slow]);
+                    }
+                    if (ok) {
+                        d.splitk_na = pat;
+                        break;
+                    }
+                }
+            }
             size_t off_colA = blob.put_i32(colA), off_colB = blob.put_i32(colB);
             size_t off_kA = blob.put_i32(kA), off_kB = blob.put_i32(kB);
             size_t off_pa = blob.put_ptrs(pa), off_pb = blob.put_ptrs(pb), off_pc = blob.put_ptrs(pc);
@@ -907,7 +939,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 op.grid_x = d.ksplit;
                 op.grid_y = (int32_t)((d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G);
                 op.grid_z = (int32_t)std::min<int64_t>(n_inst, 65535);
-                op.variant |= 2;
+                op.variant |= 2 | (d.splitk_na << 8);   // the outer-product factor, for the launch records
             } else {
                 int64_t blocks = (d.n_out + 255) / 256;
                 int64_t gy = std::min<int64_t>(n_inst, 65535);

@@ -1,0 +1,79 @@
+"""Direct pairwise contraction with few outputs and a long summed index
+(Section 2.3; the last steps of an amplitude's tree): the summed index is split
+across blocks and the per-part partials are added in a second launch.  When
+every group of 8 consecutive outputs is the outer product of NA values of A
+(fastest) and 8 / NA of B, each operand value is read once per summed entry.
+
+Two tensors A[a..., k...] and B[b..., k...] with 2^16 summed entries (16
+binary labels, ordered differently in A and B) and every free leg left open.
+Without a consumer the pair's output is laid out as the larger operand's free
+labels, then the smaller one's (fastest), which fixes the pattern of each group
+of 8 outputs:
+- A's values fastest, NA = 2, 4, 8; all 8 from B (NA = 1);
+- B's values fastest, NB = 2, 4;
+- groups that straddle a dim-3 label (the generic form, 16 loads per summed
+  entry);
+- a free label of dim 3 (slowest) and two instances (one summed label sliced).
+Checked against the oracle's contraction of the same pair, FP32 and FP64."""
+import numpy as np
+import pytest
+
+from circuits.rng import uniform_array
+from oracle.einsum import contract_network
+from paper_2107_09793_b300 import jet
+
+pytestmark = pytest.mark.gpu
+
+K = list(range(100, 116))   # 16 binary summed labels
+
+
+def _rand(seed, shape):
+    n = int(np.prod(shape))
+    u = uniform_array(seed, 2 * n)
+    return ((u[:n] - 0.5) + 1j * (u[n:] - 0.5)).reshape(shape)
+
+
+# name: (A free labels, B free labels, dims, sliced, expected pattern)
+CASES = {
+    "a_fast_na2": ([1], [11, 12, 13], {}, [], 2),
+    "a_fast_na4": ([1, 2], [11, 12, 13], {}, [], 4),
+    "a_fast_na8": ([1, 2, 3], [11, 12, 13, 14], {}, [], 8),
+    "b_only_na1": ([1, 2, 3, 4], [11, 12, 13], {}, [], 1),
+    "b_fast_nb2": ([1, 2, 3], [11], {}, [], 18),
+    "b_fast_nb4": ([1, 2, 3], [11, 12], {}, [], 20),
+    "generic_dim3_fastest": ([1, 2, 3], [11], {11: 3}, [], 0),
+    "dim3_slowest_two_instances": ([1, 2], [11, 12], {11: 3}, [K[5]], 4),
+}
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-13)])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_split_k_forms(case, prec, tol):
+    fa, fb, dd, sliced, na = CASES[case]
+    dims = {l: dd.get(l, 2) for l in fa + fb + K}
+    size = lambda f: int(np.prod([dims[l] for l in f]))
+    order = fa + fb if size(fa) >= size(fb) else fb + fa    # the pair's own layout
+    ka = list(K)
+    kb = list(K[8:]) + list(K[:8])          # B reads the summed labels in another order
+    la, lb = ka[:8] + fa + ka[8:], fb + kb
+    seed = 5000 + 31 * sorted(CASES).index(case)
+    A = _rand(seed, [dims[l] for l in la])
+    B = _rand(seed + 1, [dims[l] for l in lb])
+    A, B = A.astype(np.complex64), B.astype(np.complex64)   # leaves are complex64 in every mode
+    net = jet.Network([la, lb], [A, B], precision=prec, profile=2)
+    net.set_open(order)
+    net.set_free(order)
+    net.path_set([(0, 1)])
+    if sliced:
+        net.slice(sliced)
+    got = net.contract(np.zeros((1, len(order)), np.int32))[0]
+    recs = [r for r in net.profile() if r["kind"] == "direct"]
+    assert len(recs) == 1 and recs[0]["variant"] & 2, recs        # the split form
+    assert recs[0]["variant"] >> 8 == na, (recs[0]["variant"], recs[0]["grid"])
+    assert recs[0]["n_inst"] == (2 if sliced else 1)
+    rl, ref = contract_network([la, lb], [A.astype(np.complex128), B.astype(np.complex128)])
+    ref = np.transpose(ref, [rl.index(l) for l in order]).reshape(-1)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    print(f"{case} {prec}: NA {na}, rel err {err:.2e}")
+    assert err <= tol
+    net.close()
