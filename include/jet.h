@@ -98,8 +98,10 @@ typedef struct {
                                  (read with jet_profile)                                  */
     int32_t apply_tc_min_kf;  /* split modes: small-operand applications whose small operand
                                  has at least this many entries (summed x free) run on the
-                                 tensor cores; default 1024 (below it the CUDA-core forms
-                                 are HBM-bound), above 8192 none does                     */
+                                 tensor cores, and from half as many those with at most 32
+                                 summed entries and summed x free >= 10 (summed + free),
+                                 where the CUDA-core forms are FMA-bound; default 1024,
+                                 above 8192 none does                                     */
 } jet_options;
 
 typedef struct {

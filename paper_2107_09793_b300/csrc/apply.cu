@@ -468,46 +468,89 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nrl >> 3) << 17) | ((uint32_t)(ATC_M >> 4) << 24);
     const int terms = a.tc_terms;
 
-    auto valid = [&](int64_t u) { return (u % U) * G + g < T; };
+    // Unit u is tile group u % U of instance u / U; positions advance by counters.
+    // The prefetch position (the next unit whose chunk is gathered):
+    int64_t p_u = u0, p_inst = u0 / U, p_tt = u0 - (u0 / U) * U;
+    auto p_valid = [&]() { return p_tt * G + g < T; };
+    auto p_advance = [&]() {
+        ++p_u;
+        if (++p_tt == U) {
+            p_tt = 0;
+            ++p_inst;
+        }
+    };
+    // Power-of-two dims: a fiber's offsets are linear in the bits of its index, so
+    // they are the sum of this thread's part (bits 0..6, the row m of the tile) and
+    // the tile's (the higher bits, the same for the whole group).  Each warp decodes
+    // the tile parts of 32 consecutive units at a time, lane l holding unit w_u + l.
+    int64_t m_oa = 0, m_oc = 0, w_u = -1, w_oa = 0, w_oc = 0;
+    if (POW2) fiber_offsets<true>(m, a, m_oa, m_oc);
+    const int lane = tid & 31;
+    auto tile_offsets = [&](int64_t &oa, int64_t &oc) {   // of the prefetch unit (warp-uniform)
+        if (w_u < 0 || p_u - w_u >= 32) {
+            w_u = p_u;
+            const int64_t tt = (p_tt + lane) % U;
+            fiber_offsets<true>((tt * G + g) * ATC_M, a, w_oa, w_oc);
+        }
+        const int src = (int)(p_u - w_u);
+        oa = (int64_t)__shfl_sync(0xffffffffu, (long long)w_oa, src);
+        oc = (int64_t)__shfl_sync(0xffffffffu, (long long)w_oc, src);
+    };
     // gather one chunk of one fiber (zeros outside the operand)
     uint64_t X[ATC_KC];
-    int64_t oc_next = 0;
-    auto gather = [&](int64_t u, int c) {
-        const int64_t inst = u / U, r = ((u % U) * G + g) * ATC_M + m;
+    int64_t oc_next = 0, a_inst = -1;
+    const unsigned long long *a_base = nullptr;
+    auto gather = [&](int c) {
+        const int64_t r = (p_tt * G + g) * ATC_M + m;
         const bool ok = r < a.n_fib;
         int64_t oa, oc;
-        fiber_offsets<POW2>(ok ? r : 0, a, oa, oc);
+        if (POW2) {
+            tile_offsets(oa, oc);
+            oa += m_oa;
+            oc += m_oc;
+        } else {
+            fiber_offsets<false>(ok ? r : 0, a, oa, oc);
+        }
         oc_next = oc;
-        const unsigned long long *A = (const unsigned long long *)pA[inst] + oa;
+        if (p_inst != a_inst) {   // the instance's base address, loaded once per instance
+            a_inst = p_inst;
+            a_base = (const unsigned long long *)pA[p_inst];
+        }
+        const unsigned long long *A = a_base + oa;
         const int kv = min(ATC_KC, nk - c * ATC_KC);
-        const int64_t *kA = a.kA + c * ATC_KC;
 #pragma unroll
-        for (int q = 0; q < ATC_KC; ++q) X[q] = (ok && q < kv) ? __ldg(A + kA[q]) : 0ull;
+        for (int q = 0; q < ATC_KC; ++q)   // one chunk: compile-time table offsets
+            X[q] = (ok && q < kv) ? __ldg(A + a.kA[(MULTI ? c * ATC_KC : 0) + q]) : 0ull;
     };
 
-    int64_t pu = u0;   // this group's next item (unit, chunk) to gather
-    while (pu < u1 && !valid(pu)) ++pu;
+    while (p_u < u1 && !p_valid()) p_advance();
     int pc = 0;
-    if (pu < u1) gather(pu, 0);
+    if (p_u < u1) gather(0);
     int64_t cur_inst = -1;
+    unsigned long long *C = nullptr;
     uint32_t phase = 0;
     bool failed = false;
     float acc[MULTI ? 64 : 1];
 
+    int64_t n_inst_u = u0 / U, n_tt = u0 - (u0 / U) * U;   // position of the loop's next unit
     for (int64_t u = u0; u < u1; ++u) {
-        const int64_t inst = u / U;
+        const int64_t inst = n_inst_u, tt = n_tt;
+        if (++n_tt == U) {
+            n_tt = 0;
+            ++n_inst_u;
+        }
         if (inst != cur_inst) {   // CTA-uniform: every group's MMAs on the old planes have completed
             __syncthreads();
             atc_fill_b(a, (const float2 *)pB[inst], sB, nkb, nrl, bplane, tid, 128 * G);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             cur_inst = inst;
+            C = (unsigned long long *)pC[inst];
         }
-        if (failed || !valid(u)) continue;   // group-uniform
-        const int64_t r = ((u % U) * G + g) * ATC_M + m;
+        if (failed || tt * G + g >= T) continue;   // group-uniform
+        const int64_t r = (tt * G + g) * ATC_M + m;
         const bool rok = r < a.n_fib;
         const int64_t oc = oc_next;
-        unsigned long long *C = (unsigned long long *)pC[inst];
         for (int c = 0; c < nch; ++c) {
             const int kv = min(ATC_KC, nk - c * ATC_KC), kbc = (kv + 7) >> 3;
             // split the gathered chunk into the hi / lo planes of row m
@@ -542,11 +585,11 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
             if (c + 1 < nch) {
                 pc = c + 1;
             } else {
-                ++pu;
-                while (pu < u1 && !valid(pu)) ++pu;
+                p_advance();
+                while (p_u < u1 && !p_valid()) p_advance();
                 pc = 0;
             }
-            if (pu < u1) gather(pu, pc);
+            if (p_u < u1) gather(pc);
             const bool ok = mbar_wait_inline(bar, phase, (volatile int *)&fail_any);
             phase ^= 1u;
             if (group_any(!ok, 1 + g)) {
@@ -557,31 +600,37 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool last = c + 1 == nch;
             constexpr int HMAX = MULTI ? JET_APPLY_TC_MAXF_MULTI / 8 : JET_APPLY_TC_MAXF / 8;   // 16-column groups
+            auto emit = [&](const int h, const uint32_t (&R)[16]) {
+                if (MULTI) {
 #pragma unroll
-            for (int h = 0; h < HMAX; ++h) {
+                    for (int j = 0; j < 16; ++j) {
+                        const float v = __uint_as_float(R[j]);
+                        acc[(16 * h + j) % (MULTI ? 64 : 1)] = c == 0 ? v : acc[(16 * h + j) % (MULTI ? 64 : 1)] + v;
+                    }
+                }
+                if (last && rok) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int f = 8 * h + j;
+                        if (f < nf) {
+                            const float re = MULTI ? acc[(16 * h + 2 * j) % (MULTI ? 64 : 1)] : __uint_as_float(R[2 * j]);
+                            const float im = MULTI ? acc[(16 * h + 2 * j + 1) % (MULTI ? 64 : 1)]
+                                                   : __uint_as_float(R[2 * j + 1]);
+                            __stcs(C + oc + a.cF[f], pack2(re, im));
+                        }
+                    }
+                }
+            };
+            // 16-column groups read two at a time, one wait per pair
+#pragma unroll
+            for (int h = 0; h < HMAX; h += 2) {
                 if (h < nr) {
-                    uint32_t R[16];
-                    JET_TMEM_LD16(trow + 16 * h, R);
+                    uint32_t R0[16], R1[16];
+                    JET_TMEM_LD16(trow + 16 * h, R0);
+                    if (h + 1 < nr) JET_TMEM_LD16(trow + 16 * (h + 1), R1);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (MULTI) {
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const float v = __uint_as_float(R[j]);
-                            acc[(16 * h + j) % (MULTI ? 64 : 1)] = c == 0 ? v : acc[(16 * h + j) % (MULTI ? 64 : 1)] + v;
-                        }
-                    }
-                    if (last && rok) {
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int f = 8 * h + j;
-                            if (f < nf) {
-                                const float re = MULTI ? acc[(16 * h + 2 * j) % (MULTI ? 64 : 1)] : __uint_as_float(R[2 * j]);
-                                const float im = MULTI ? acc[(16 * h + 2 * j + 1) % (MULTI ? 64 : 1)]
-                                                       : __uint_as_float(R[2 * j + 1]);
-                                __stcs(C + oc + a.cF[f], pack2(re, im));
-                            }
-                        }
-                    }
+                    emit(h, R0);
+                    if (h + 1 < nr) emit(h + 1, R1);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -199,10 +199,17 @@ __global__ void splitk_reduce_kernel(const __grid_constant__ SplitKReduceArgs a)
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t inst = e / a.n_out, o = e - inst * a.n_out;
         V s = vzero<V>();
-        for (int p = 0; p < a.ksplit; ++p) {
-            V x = part[(inst * a.ksplit + p) * a.n_out + o];
-            s.x += x.x;
-            s.y += x.y;
+        // 8 partials loaded at a time, added in increasing part order
+        for (int p0 = 0; p0 < a.ksplit; p0 += 8) {
+            V x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = p0 + u < a.ksplit ? part[(inst * a.ksplit + p0 + u) * a.n_out + o] : vzero<V>();
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (p0 + u < a.ksplit) {
+                    s.x += x[u].x;
+                    s.y += x[u].y;
+                }
         }
         ((V *)pC[inst])[o] = s;
     }
@@ -358,10 +365,18 @@ __global__ void slice_reduce_kernel(const __grid_constant__ ReduceArgs a)
     if (i >= (int64_t)a.n_amps * ne) return;
     const int64_t b = i / ne, e = i % ne;
     double re = 0, im = 0;
-    for (int s = 0; s < a.n_slices; ++s) {
-        const double2 v = load(roots[b * a.n_slices + s], e);
-        re += v.x;
-        im += v.y;
+    // 16 partials loaded at a time (their loads overlap), added in increasing slice id
+    constexpr int U = 16;
+    for (int s0 = 0; s0 < a.n_slices; s0 += U) {
+        double2 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = s0 + u < a.n_slices ? load(roots[b * a.n_slices + s0 + u], e) : double2{0, 0};
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (s0 + u < a.n_slices) {
+                re += v[u].x;
+                im += v[u].y;
+            }
     }
     ((double2 *)a.amps)[i] = make_double2(re, im);
 }

@@ -325,9 +325,14 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     // slots before HBM bandwidth): thread groups per CTA that fit the operand
     // planes in shared memory (three for one chunk of summed entries, else
     // two), 0 when the form does not apply
+    // A small operand of one chunk (at most 32 summed entries) qualifies from half
+    // the threshold on when the CUDA-core forms are FMA-bound on it: at least 10
+    // complex multiply-adds per operand entry loaded or stored, nk nf >= 10 (nk + nf).
     auto apply_tc_groups = [&](int64_t nk, int64_t nf) -> int {
-        if (!tc_mode || fp64 || nk * nf < net.opt.apply_tc_min_kf || nk > JET_APPLY_MAXK || nf < 1 ||
-            nf > JET_APPLY_TC_MAXF || (nk > 32 && nf > JET_APPLY_TC_MAXF_MULTI))
+        const int64_t kf = nk * nf, min_kf = net.opt.apply_tc_min_kf;
+        const bool big = kf >= min_kf || (nk <= 32 && 2 * kf >= min_kf && kf >= 10 * (nk + nf));
+        if (!tc_mode || fp64 || !big || nk > JET_APPLY_MAXK || nf < 1 || nf > JET_APPLY_TC_MAXF ||
+            (nk > 32 && nf > JET_APPLY_TC_MAXF_MULTI))
             return 0;
         if (nk <= 32 && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 3;
         if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;

@@ -161,9 +161,13 @@ def test_apply_cuda_core_forms(case):
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_apply_default_routing(case):
     """Default threshold: the tensor-core form for small operands of 1024
-    entries or more (32 x 32, 128 x 16), the CUDA-core forms below."""
+    entries or more (32 x 32, 128 x 16), and from 512 for one chunk of summed
+    entries with nk nf >= 10 (nk + nf) (32 x 16, 16 x 32); the CUDA-core forms
+    below."""
     la, lb, dd, sliced = CASES[case]
     sliced = [] if sliced == "lead" else sliced
     dims = {l: dd.get(l, 2) for l in la + lb}
-    kf = int(np.prod([dims[l] for l in lb if l not in sliced]))   # entries of one instance
-    assert _check(case, "fp16x3", kf >= 1024) <= TOL["fp16x3"]
+    nk = int(np.prod([dims[l] for l in lb if l in la and l not in sliced]))   # one instance
+    nf = int(np.prod([dims[l] for l in lb if l not in la]))
+    tc = nk * nf >= 1024 or (nk <= 32 and 2 * nk * nf >= 1024 and nk * nf >= 10 * (nk + nf))
+    assert _check(case, "fp16x3", tc) <= TOL["fp16x3"]
