@@ -104,6 +104,26 @@ __device__ __forceinline__ void fiber_offsets(int64_t r, const ApplyArgs &a, int
     }
 }
 
+// Offsets of the fiber indices b0 + k * stride (k = 0, 1, ...), the same for a
+// whole warp, when every digit is a power of two (a fiber's offsets are then
+// linear in the bits of its index, so a thread adds its own low part): lane l
+// decodes index k0 + l, 32 values of k at a time, read by shuffle.  Calls are
+// warp-uniform.
+struct TileWindow {
+    int64_t k0 = -64, oa = 0, oc = 0;
+    __device__ __forceinline__ void get(const ApplyArgs &a, int64_t b0, int64_t stride, int64_t k, int64_t &ra,
+                                        int64_t &rc)
+    {
+        if (k < k0 || k - k0 >= 32) {
+            k0 = k;
+            fiber_offsets<true>(b0 + (k0 + (int64_t)(threadIdx.x & 31)) * stride, a, oa, oc);
+        }
+        const int src = (int)(k - k0);
+        ra = (int64_t)__shfl_sync(0xffffffffu, (long long)oa, src);
+        rc = (int64_t)__shfl_sync(0xffffffffu, (long long)oc, src);
+    }
+};
+
 // complex64: B staged as packed pairs (br, br, bi, bi); FIB fibers per thread
 // (two up to 16 summed entries, one for 32), every B entry read from shared
 // memory once feeds the packed FMAs of all of them.
@@ -115,7 +135,14 @@ __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ 
     __shared__ __align__(16) float2 sB[JET_APPLY_MAXB];
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
     const int nf = a.nf;
-    const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB, b0 = (int64_t)blockIdx.x * blockDim.x * FIB;
+    int64_t t_oa[FIB], t_oc[FIB];   // power-of-two digits: this thread's part of its fibers' offsets
+#pragma unroll
+    for (int u = 0; u < FIB; ++u) {
+        t_oa[u] = t_oc[u] = 0;
+        if (POW2) fiber_offsets<true>(threadIdx.x + (int64_t)u * blockDim.x, a, t_oa[u], t_oc[u]);
+    }
+    TileWindow win;
     for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
         const unsigned long long *__restrict__ A = (const unsigned long long *)pA[inst];
         const float2 *__restrict__ B = (const float2 *)pB[inst];
@@ -126,15 +153,22 @@ __global__ void __launch_bounds__(256) apply_kernel_c64(const __grid_constant__ 
             sB[i] = q < a.nk ? B[a.bF[f] + a.bK[q]] : make_float2(0.f, 0.f);   // padding is zero
         }
         __syncthreads();
-        for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x * FIB + threadIdx.x; r0 < a.n_fib; r0 += step) {
-            int64_t oa[FIB], oc[FIB];
+        int64_t k = 0;
+        for (int64_t rb = b0; rb < a.n_fib; rb += step, ++k) {   // block-uniform fiber bases
+            int64_t oa[FIB], oc[FIB], wa = 0, wc = 0;
             bool ok[FIB];
             unsigned long long x[FIB][NK];
+            if (POW2) win.get(a, b0, step, k, wa, wc);
 #pragma unroll
             for (int u = 0; u < FIB; ++u) {
-                const int64_t r = r0 + (int64_t)u * blockDim.x;
+                const int64_t r = rb + threadIdx.x + (int64_t)u * blockDim.x;
                 ok[u] = r < a.n_fib;
-                fiber_offsets<POW2>(ok[u] ? r : 0, a, oa[u], oc[u]);
+                if (POW2) {
+                    oa[u] = wa + t_oa[u];
+                    oc[u] = wc + t_oc[u];
+                } else {
+                    fiber_offsets<false>(ok[u] ? r : 0, a, oa[u], oc[u]);
+                }
 #pragma unroll
                 for (int q = 0; q < NK; ++q) x[u][q] = ok[u] ? __ldg(A + oa[u] + a.kA[q]) : 0ull;
             }
@@ -185,7 +219,14 @@ __global__ void __launch_bounds__(256) apply_stream_c64(const __grid_constant__ 
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
     const int nk = a.nk, nf = a.nf;
     const int nfp = (nf + NF - 1) / NF * NF;   // row length: free entries padded to whole chunks
-    const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * FIB, b0 = (int64_t)blockIdx.x * blockDim.x * FIB;
+    int64_t t_oa[FIB], t_oc[FIB];   // power-of-two digits: this thread's part of its fibers' offsets
+#pragma unroll
+    for (int u = 0; u < FIB; ++u) {
+        t_oa[u] = t_oc[u] = 0;
+        if (POW2) fiber_offsets<true>(threadIdx.x + (int64_t)u * blockDim.x, a, t_oa[u], t_oc[u]);
+    }
+    TileWindow win;
     for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
         const unsigned long long *__restrict__ A = (const unsigned long long *)pA[inst];
         const float2 *__restrict__ B = (const float2 *)pB[inst];
@@ -197,14 +238,21 @@ __global__ void __launch_bounds__(256) apply_stream_c64(const __grid_constant__ 
             sB[i] = make_ulonglong2(pack2(b.x, b.x), pack2(b.y, b.y));
         }
         __syncthreads();
-        for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x * FIB + threadIdx.x; r0 < a.n_fib; r0 += step) {
-            int64_t oa[FIB], oc[FIB];
+        int64_t k = 0;
+        for (int64_t rb = b0; rb < a.n_fib; rb += step, ++k) {   // block-uniform fiber bases
+            int64_t oa[FIB], oc[FIB], wa = 0, wc = 0;
             bool ok[FIB];
+            if (POW2) win.get(a, b0, step, k, wa, wc);
 #pragma unroll
             for (int u = 0; u < FIB; ++u) {
-                const int64_t r = r0 + (int64_t)u * blockDim.x;
+                const int64_t r = rb + threadIdx.x + (int64_t)u * blockDim.x;
                 ok[u] = r < a.n_fib;
-                fiber_offsets<POW2>(ok[u] ? r : 0, a, oa[u], oc[u]);
+                if (POW2) {
+                    oa[u] = wa + t_oa[u];
+                    oc[u] = wc + t_oc[u];
+                } else {
+                    fiber_offsets<false>(ok[u] ? r : 0, a, oa[u], oc[u]);
+                }
             }
             for (int f0 = 0; f0 < nf; f0 += NF) {
                 unsigned long long p[FIB][NF], m[FIB][NF];
