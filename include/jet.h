@@ -52,7 +52,7 @@ typedef struct { double re, im; } jet_c128;
 
 /* Arithmetic used for the large (GEMM-shaped) pairwise contractions and, in
  * the split modes (every mode but FP32 and FP64), for the application of a
- * small operand with at most 256 summed and 32 free entries (64 free when it
+ * small operand with at most 256 summed and 32 free entries (128 free when it
  * has at most 32 summed), and at least apply_tc_min_kf of them in all
  * (summed x free), to a large one (TF32 hi + lo,
  * three products; one in JET_PREC_TF32).  Other small contractions always run
@@ -80,7 +80,7 @@ typedef struct {
     int64_t gemm_min_k;       /* contractions with a summed extent >= this (and both free
                                  extents >= 64) take the GEMM route, except, in the split
                                  modes, those with a summed extent <= 32 and one free
-                                 extent <= 64 that the tensor-core small-operand form
+                                 extent <= 128 that the tensor-core small-operand form
                                  takes; default 16                                        */
     int64_t workspace_limit;  /* bytes of device workspace a contraction may use; 0 = no
                                  limit.  When the plan for every slice needs more,

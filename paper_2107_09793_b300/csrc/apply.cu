@@ -14,6 +14,7 @@
 // A's smallest free stride first, so a warp's loads of one summed entry are
 // coalesced whenever the summed labels are not the fastest ones.  The
 // contraction is HBM-bound (8 * nk * nf FLOP per 8 * (nk + nf) bytes).
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -475,27 +476,32 @@ __device__ __forceinline__ bool mbar_wait_inline(uint32_t bar, uint32_t parity, 
 }
 
 // MULTI: more than one chunk per tile (summed entries above 32), partial sums
-// promoted into FP32 registers; without it a tile is one chunk.
-template <int G, bool MULTI, bool POW2>
+// promoted into FP32 registers; without it a tile is one chunk.  WIDE (more
+// than 64 free entries, at most 32 summed, two groups): the gathered chunk is
+// staged in two halves of 16 summed entries, accumulated in the same TMEM
+// columns (as many accumulations as one chunk of 32).
+template <int G, bool MULTI, bool POW2, bool WIDE>
 __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant__ ApplyArgs a)
 {
+    constexpr int KC = WIDE ? ATC_KC / 2 : ATC_KC;   // summed entries per staged chunk
+    constexpr uint32_t ABY = WIDE ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;   // a group's A planes
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[G];
     __shared__ uint32_t tmem_holder;
     __shared__ int fail_any;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, g = tid >> 7, m = tid & 127, warp = tid >> 5;
-    const int nk = a.nk, nf = a.nf, nkb = (nk + 7) >> 3, nch = MULTI ? (nk + ATC_KC - 1) / ATC_KC : 1;
+    const int nk = a.nk, nf = a.nf, nkb = (nk + 7) >> 3, nch = (MULTI || WIDE) ? (nk + KC - 1) / KC : 1;
     const int nr = (nf + 7) >> 3;           // 16-column groups of D (8 complex outputs each)
     const int nrl = 16 * nr;                // real columns: the MMA's N
     const uint32_t bplane = (uint32_t)(nkb * nrl * 64);
     const int64_t T = (a.n_fib + ATC_M - 1) / ATC_M, U = (T + G - 1) / G, total = U * a.n_inst;
     const int64_t u0 = total * blockIdx.x / gridDim.x, u1 = total * (blockIdx.x + 1) / gridDim.x;
-    const uint32_t sA = smem_u32(smem + g * JET_APPLY_TC_ABYTES), sB = smem_u32(smem + G * JET_APPLY_TC_ABYTES);
+    const uint32_t sA = smem_u32(smem + g * ABY), sB = smem_u32(smem + G * ABY);
     const uint32_t bar = smem_u32(&bars[g]);
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
-    // TMEM columns per group (the MMA's N, up to 64 or 128), allocated as a power of two
-    const uint32_t span = nrl <= 64 ? 64u : 128u, COLS = (G <= 2 ? 2u : 4u) * span;
+    // TMEM columns per group (the MMA's N: up to 64, 128 or 256), allocated as a power of two
+    const uint32_t span = nrl <= 64 ? 64u : nrl <= 128 ? 128u : 256u, COLS = (G <= 2 ? 2u : 4u) * span;
 
     if (tid == 0) {
         for (int i = 0; i < G; ++i) mbar_init(smem_u32(&bars[i]), 1);
@@ -600,19 +606,25 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
         const bool rok = r < a.n_fib;
         const int64_t oc = oc_next;
         for (int c = 0; c < nch; ++c) {
-            const int kv = min(ATC_KC, nk - c * ATC_KC), kbc = (kv + 7) >> 3;
-            // split the gathered chunk into the hi / lo planes of row m
+            const int kv = min(KC, nk - c * KC), kbc = (kv + 7) >> 3;
+            // split the staged entries X[OFF ..] into the hi / lo planes of row m
+            // (OFF a compile-time offset: the second half of a wide chunk)
+            auto stage = [&](auto off_tag) {
+                constexpr int OFF = decltype(off_tag)::value;
 #pragma unroll
-            for (int p = 0; p < ATC_KC / 2; ++p) {
-                if ((p >> 2) < kbc) {
-                    const float2 v0 = unpack2(X[2 * p]), v1 = unpack2(X[2 * p + 1]);
-                    const float h0 = tf32_rna(v0.x), h1 = tf32_rna(v0.y), h2 = tf32_rna(v1.x), h3 = tf32_rna(v1.y);
-                    const uint32_t off = (uint32_t)(p >> 2) * ATC_KBB + sw64(m, p & 3);
-                    st_shared_v4(sA + off, h0, h1, h2, h3);
-                    st_shared_v4(sA + JET_APPLY_TC_ABYTES / 2 + off, tf32_rna(v0.x - h0), tf32_rna(v0.y - h1),
-                                 tf32_rna(v1.x - h2), tf32_rna(v1.y - h3));
+                for (int p = 0; p < KC / 2; ++p) {
+                    if ((p >> 2) < kbc) {
+                        const float2 v0 = unpack2(X[OFF + 2 * p]), v1 = unpack2(X[OFF + 2 * p + 1]);
+                        const float h0 = tf32_rna(v0.x), h1 = tf32_rna(v0.y), h2 = tf32_rna(v1.x), h3 = tf32_rna(v1.y);
+                        const uint32_t off = (uint32_t)(p >> 2) * ATC_KBB + sw64(m, p & 3);
+                        st_shared_v4(sA + off, h0, h1, h2, h3);
+                        st_shared_v4(sA + ABY / 2 + off, tf32_rna(v0.x - h0), tf32_rna(v0.y - h1),
+                                     tf32_rna(v1.x - h2), tf32_rna(v1.y - h3));
+                    }
                 }
-            }
+            };
+            if (WIDE && c == 1) stage(std::integral_constant<int, KC>{});
+            else stage(std::integral_constant<int, 0>{});
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             group_sync(1 + g);
@@ -622,22 +634,26 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                     for (int sub = 0; sub < 2; ++sub)
                         for (int t = 0; t < terms; ++t) {
                             const int pa = t == 2, pb = t == 1;   // hi.hi, hi.lo, lo.hi
-                            const uint64_t ad = sdesc(sA + pa * (JET_APPLY_TC_ABYTES / 2) + kb * ATC_KBB + sub * 32);
+                            const uint64_t ad = sdesc(sA + pa * (ABY / 2) + kb * ATC_KBB + sub * 32);
                             const uint64_t bd =
-                                sdesc(sB + pb * bplane + (uint32_t)(c * 4 + kb) * (uint32_t)(nrl * 64) + sub * 32);
-                            umma<1>(tmem, ad, bd, idesc, (kb | sub | t) ? 1u : 0u);
+                                sdesc(sB + pb * bplane + (uint32_t)(c * (KC / 8) + kb) * (uint32_t)(nrl * 64) + sub * 32);
+                            // WIDE: the second half adds to the first in TMEM
+                            umma<1>(tmem, ad, bd, idesc, ((WIDE ? c : 0) | kb | sub | t) ? 1u : 0u);
                         }
                 umma_commit(bar);
             }
-            // the gathers of this group's next chunk go out before the wait
+            // the gathers of this group's next chunk go out before the wait (a wide
+            // tile's second half is already in registers)
+            bool next = true;
             if (c + 1 < nch) {
                 pc = c + 1;
+                next = MULTI;
             } else {
                 p_advance();
                 while (p_u < u1 && !p_valid()) p_advance();
                 pc = 0;
             }
-            if (p_u < u1) gather(pc);
+            if (next && p_u < u1) gather(pc);
             const bool ok = mbar_wait_inline(bar, phase, (volatile int *)&fail_any);
             phase ^= 1u;
             if (group_any(!ok, 1 + g)) {
@@ -647,7 +663,8 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool last = c + 1 == nch;
-            constexpr int HMAX = MULTI ? JET_APPLY_TC_MAXF_MULTI / 8 : JET_APPLY_TC_MAXF / 8;   // 16-column groups
+            // 16-column groups of D
+            constexpr int HMAX = MULTI ? JET_APPLY_TC_MAXF_MULTI / 8 : WIDE ? JET_APPLY_TC_MAXF / 8 : JET_APPLY_TC_WIDEF / 8;
             auto emit = [&](const int h, const uint32_t (&R)[16]) {
                 if (MULTI) {
 #pragma unroll
@@ -669,10 +686,11 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                     }
                 }
             };
-            // 16-column groups read two at a time, one wait per pair
+            // 16-column groups read two at a time, one wait per pair (a wide tile's
+            // D once, after its second half)
 #pragma unroll
             for (int h = 0; h < HMAX; h += 2) {
-                if (h < nr) {
+                if (h < nr && (!WIDE || last)) {
                     uint32_t R0[16], R1[16];
                     JET_TMEM_LD16(trow + 16 * h, R0);
                     if (h + 1 < nr) JET_TMEM_LD16(trow + 16 * (h + 1), R1);
@@ -764,16 +782,18 @@ constexpr int ATC_SMEM_MAX = JET_APPLY_TC_SMEM_MAX;
 cudaError_t set_apply_tc_smem_limits()
 {
     cudaError_t e = cudaSuccess;
-#define JET_ATCSM(G, MU, P2)                                                                                      \
+#define JET_ATCSM(G, MU, P2, W)                                                                                   \
     if (e == cudaSuccess)                                                                                         \
-        e = cudaFuncSetAttribute(apply_tc_c64<G JET_COMMA MU JET_COMMA P2>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 ATC_SMEM_MAX)
-    JET_ATCSM(2, true, true);
-    JET_ATCSM(2, true, false);
-    JET_ATCSM(2, false, true);
-    JET_ATCSM(2, false, false);
-    JET_ATCSM(3, false, true);
-    JET_ATCSM(3, false, false);
+        e = cudaFuncSetAttribute(apply_tc_c64<G JET_COMMA MU JET_COMMA P2 JET_COMMA W>,                            \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ATC_SMEM_MAX)
+    JET_ATCSM(2, true, true, false);
+    JET_ATCSM(2, true, false, false);
+    JET_ATCSM(2, false, true, false);
+    JET_ATCSM(2, false, false, false);
+    JET_ATCSM(3, false, true, false);
+    JET_ATCSM(3, false, false, false);
+    JET_ATCSM(2, false, true, true);
+    JET_ATCSM(2, false, false, true);
 #undef JET_ATCSM
     return e;
 }
@@ -787,18 +807,23 @@ static cudaError_t launch_apply_tc(const ApplyArgs &a, const LaunchCfg &c, cudaS
         return cudaErrorInvalidValue;
     const int smem = jet_apply_tc_smem(G, a.nk, a.nf);
     if (smem > ATC_SMEM_MAX) return cudaErrorInvalidValue;
-    const bool pow2 = c.variant & 4, multi = a.nk > ATC_KC;
-    // promotion registers: two groups and at most 32 free entries only
+    const bool pow2 = c.variant & 4, multi = a.nk > ATC_KC, wide = a.nf > JET_APPLY_TC_WIDEF;
+    // promotion registers: two groups and at most 32 free entries only; the wide
+    // form: two groups (256 TMEM columns each), one chunk of summed entries
     if (multi && (G != 2 || a.nf > JET_APPLY_TC_MAXF_MULTI)) return cudaErrorInvalidValue;
+    if (wide && (G != 2 || multi)) return cudaErrorInvalidValue;
     if (multi) {
-        if (pow2) apply_tc_c64<2, true, true><<<c.gx, 256, smem, s>>>(a);
-        else apply_tc_c64<2, true, false><<<c.gx, 256, smem, s>>>(a);
+        if (pow2) apply_tc_c64<2, true, true, false><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, true, false, false><<<c.gx, 256, smem, s>>>(a);
+    } else if (wide) {
+        if (pow2) apply_tc_c64<2, false, true, true><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, false, false, true><<<c.gx, 256, smem, s>>>(a);
     } else if (G == 2) {
-        if (pow2) apply_tc_c64<2, false, true><<<c.gx, 256, smem, s>>>(a);
-        else apply_tc_c64<2, false, false><<<c.gx, 256, smem, s>>>(a);
+        if (pow2) apply_tc_c64<2, false, true, false><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, false, false, false><<<c.gx, 256, smem, s>>>(a);
     } else {
-        if (pow2) apply_tc_c64<3, false, true><<<c.gx, 384, smem, s>>>(a);
-        else apply_tc_c64<3, false, false><<<c.gx, 384, smem, s>>>(a);
+        if (pow2) apply_tc_c64<3, false, true, false><<<c.gx, 384, smem, s>>>(a);
+        else apply_tc_c64<3, false, false, false><<<c.gx, 384, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -15,18 +15,21 @@
 #define JET_APPLY_MAXF 256   // small-operand application: max free entries of the small operand
 #define JET_APPLY_MAXB 1024  // held form: max entries of the small operand (summed extent padded)
 #define JET_APPLY_STREAMF 32 // streamed form: max free entries of the small operand
-#define JET_APPLY_TC_MAXF 64 // tensor-core form: max free entries of the small operand (N <= 128 real columns)
+#define JET_APPLY_TC_MAXF 128 // tensor-core form: max free entries of the small operand (N <= 256 real columns)
 #define JET_APPLY_TC_MAXF_MULTI 32 // ... when the summed extent is above one 32-entry chunk (FP32 promotion registers)
+#define JET_APPLY_TC_WIDEF 64 // above this many free entries (at most 32 summed): the A chunk is staged in halves
 #define JET_APPLY_TC_ABYTES 65536 // tensor-core form: one group's A chunk, hi + lo TF32 planes of 128 x 64
 #define JET_APPLY_TC_SMEM_MAX 231424 // tensor-core form: dynamic shared memory cap (227 KiB less 1 KiB)
 
 // Dynamic shared memory of the tensor-core application: 1 KiB alignment slack,
-// one A chunk per thread group and the hi / lo TF32 planes of the small operand
-// (summed entries padded to blocks of 8, free entries to 8, two real rows each).
+// one A chunk per thread group (half a chunk above JET_APPLY_TC_WIDEF free
+// entries) and the hi / lo TF32 planes of the small operand (summed entries
+// padded to blocks of 8, free entries to 8, two real rows each).
 static inline int jet_apply_tc_smem(int groups, int nk, int nf)
 {
     const int nkb = (nk + 7) / 8, nr = 2 * ((nf + 7) / 8 * 8);
-    return 1024 + groups * JET_APPLY_TC_ABYTES + 2 * nkb * nr * 64;
+    const int abytes = nf > JET_APPLY_TC_WIDEF ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;
+    return 1024 + groups * abytes + 2 * nkb * nr * 64;
 }
 
 // Pairwise contraction C = sum_K A * B evaluated directly from strides

@@ -334,7 +334,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         if (!tc_mode || fp64 || !big || nk > JET_APPLY_MAXK || nf < 1 || nf > JET_APPLY_TC_MAXF ||
             (nk > 32 && nf > JET_APPLY_TC_MAXF_MULTI))
             return 0;
-        if (nk <= 32 && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 3;
+        if (nk <= 32 && nf <= JET_APPLY_TC_WIDEF && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX)
+            return 3;   // (the wide form takes two groups: 256 TMEM columns each)
         if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
         return 0;
     };
@@ -350,11 +351,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     auto gemm_route = [&](int64_t nK, int64_t nFa, int64_t nFb) {
         return gemm_ok && nK >= net.opt.gemm_min_k && nFa >= 64 && nFb >= 64 && !tc_apply_short(nK, nFa, nFb);
     };
-    auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big,
-                              int64_t n_inst) {
-        const View &VS = a_big ? VB : VA, &VL = a_big ? VA : VB;
-        const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
-        const int64_t nk = dimprod(K), nf = dimprod(fs), nfib = dimprod(fl);
+    // a small operand of nk summed and nf free entries that some application form takes
+    auto apply_shape_ok = [&](int64_t nk, int64_t nf) {
         int64_t nk2 = 1;   // the kernel's compile-time summed extent (power of two >= nk)
         while (nk2 < nk) nk2 *= 2;
         // held in registers: up to 16 summed entries (complex128 too), or 32 (complex64)
@@ -363,14 +361,22 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const bool streamed = !fp64 && nk <= JET_APPLY_MAXK && nf <= JET_APPLY_STREAMF &&
                               (nf <= 4 || nk * nfp <= JET_APPLY_STREAMB);
         const bool tc = apply_tc_groups(nk, nf) > 0;
-        return nk >= 1 && (held || streamed || tc) && nf <= JET_APPLY_MAXF && nfib * n_inst >= (1 << 15) &&
-               (int64_t)fl.size() <= JET_MAXR && VS.size == nk * nf && VL.size == nk * nfib;
+        return nk >= 1 && (held || streamed || tc) && nf <= JET_APPLY_MAXF;
+    };
+    auto apply_ok_views = [&](const View &VA, const View &VB, const std::vector<int64_t> &K, bool a_big,
+                              int64_t n_inst) {
+        const View &VS = a_big ? VB : VA, &VL = a_big ? VA : VB;
+        const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
+        const int64_t nk = dimprod(K), nf = dimprod(fs), nfib = dimprod(fl);
+        return apply_shape_ok(nk, nf) && nfib * n_inst >= (1 << 15) && (int64_t)fl.size() <= JET_MAXR &&
+               VS.size == nk * nf && VL.size == nk * nfib;
     };
     auto apply_ok = [&](const NodeInfo &N, const View &VA, const View &VB) {
         return apply_ok_views(VA, VB, N.K, N.a_big, N.n_inst);
     };
     // The summed labels of v's parent when the parent applies a small operand
-    // (at most 2048 entries, not the GEMM route) to v as its large operand:
+    // (up to 2048 entries or a shape an application form takes, not the GEMM
+    // route) to v as its large operand:
     // laying them out slowest in v lets the parent read, for each summed
     // entry, runs of consecutive fibers (whole sectors per warp) and write its
     // own small operand's labels in their place, again slowest.
@@ -384,7 +390,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             if (find_pos(labset[v], l) < 0) Fs.push_back(l);
         const int64_t sv = dimprod(labset[v]), ss = dimprod(ls);
         const bool p_gemm = !Kp.empty() && gemm_route(dimprod(Kp), dimprod(Fp), dimprod(Fs));
-        if (p_gemm || Kp.empty() || ss > 2048 || sv <= ss) return {};
+        if (p_gemm || Kp.empty() || sv <= ss || (ss > 2048 && !apply_shape_ok(dimprod(Kp), dimprod(Fs)))) return {};
         return Kp;
     };
 
@@ -451,7 +457,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         // its input wire and the large operand's layout is kept)
         std::vector<int64_t> ks_small, fs_small_order;
         for (int64_t l : VSmall.labels) (find_pos(N.K, l) >= 0 ? ks_small : fs_small_order).push_back(l);
-        bool pairable = !N.use_gemm && VSmall.size <= 2048 && VBig.size > VSmall.size && !ks_small.empty() &&
+        // this node applies its small operand to the large one (a small operand of
+        // up to 2048 entries, or one that an application form takes)
+        const bool v_applies = !N.use_gemm && VBig.size > VSmall.size &&
+                               (VSmall.size <= 2048 || apply_ok_views(VA, VB, N.K, N.a_big, N.n_inst));
+        bool pairable = v_applies && !ks_small.empty() &&
                         ks_small.size() == fs_small_order.size();
         for (size_t j = 0; pairable && j < ks_small.size(); ++j)
             pairable = net.labels.at(ks_small[j]).dim == net.labels.at(fs_small_order[j]).dim;
@@ -460,7 +470,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 const int p = find_pos(ks_small, l);
                 out.push_back(p >= 0 ? fs_small_order[p] : l);
             }
-        } else if (!N.use_gemm && VSmall.size <= 2048 && VBig.size > VSmall.size) {
+        } else if (v_applies) {
             // keep the big operand's order; the small operand's free labels take
             // the place of the first summed label (gate application in place)
             int ins = -1;
@@ -549,7 +559,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     if (find_pos(Kc, l) >= 0) re.push_back(l);
                 for (int64_t l : out)
                     if (find_pos(Kc, l) < 0) re.push_back(l);
-                const bool v_apply = VSmall.size <= 2048 && VBig.size > VSmall.size;
+                const bool v_apply = v_applies;
                 std::vector<int64_t> vfib;   // this node's fibers in its decode order (large operand's strides)
                 if (v_apply) {
                     for (size_t i = VBig.labels.size(); i-- > 0;)

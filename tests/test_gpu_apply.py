@@ -10,7 +10,9 @@ blocks (21 x 5, 200 x 3); several chunks per tile (128 and 200 summed entries,
 the FP32 register promotion); wide free extents (32, 48 and 64: N = 64, 96 and
 128 real columns, the last two with 128 TMEM columns per thread group; 16 x 64
 has both free sides of 64 or more, a product the GEMM route would otherwise
-take); a summed label at stride 1 in A (fibers at stride 2); and a sliced
+take; 72 and 128 free entries with 20 and 32 summed: the wide form, N up to 256,
+the chunk staged in two halves); a summed label at stride 1 in A (fibers at
+stride 2); and a sliced
 summed label, so the node runs as two instances in one launch (the small
 operand is rebuilt per instance).  The fast_ cases put the 7 fastest labels of A
 on the fibers (one of them reading a leaf that is 8- but not 16-byte aligned).
@@ -57,6 +59,10 @@ CASES = {
     "k16_f64": ([0, 10, 1], [10, 20], {0: 256, 1: 256, 10: 16, 20: 64}, []),
     # 32 summed (4 x 8), 48 free (N = 96; the operand planes leave room for two groups)
     "k32_f48": ([0, 10, 11, 1], [11, 20, 10], {0: 128, 1: 256, 10: 4, 11: 8, 20: 48}, []),
+    # wide: 32 summed, 128 free (N = 256; the chunk staged in two halves of 16)
+    "k32_f128_wide": ([0, 10, 11, 1], [10, 20, 11], {0: 128, 1: 256, 10: 4, 11: 8, 20: 128}, []),
+    # wide with a ragged summed extent (20: one half of 16, one of 4) and 72 free
+    "k20_f72_wide": ([0, 10, 11, 1], [11, 20, 10], {0: 128, 1: 256, 10: 4, 11: 5, 20: 72}, []),
     # a summed binary label at stride 1 in A: the fibers sit at stride 2
     "k32_stride2": (list(range(100, 115)) + [10, 11, 12, 13, 14], [20, 10, 11, 12, 13, 14], {20: 8}, []),
     # 64 summed with one label sliced: the node runs as 2 instances of 32 summed
@@ -149,8 +155,9 @@ def test_apply_tensor_core_other_modes(case, prec):
     assert _check(case, prec, True, apply_tc_min_kf=1) <= TOL[prec]
 
 
-# 32 x 48 is past the CUDA-core forms (held: 1024 padded entries; streamed: 32 free)
-@pytest.mark.parametrize("case", sorted(set(CASES) - {"k32_f48"}))
+# 32 x 48 and the wide shapes are past the CUDA-core forms (held: 1024 padded
+# entries; streamed: 32 free)
+@pytest.mark.parametrize("case", sorted(set(CASES) - {"k32_f48", "k32_f128_wide", "k20_f72_wide"}))
 def test_apply_cuda_core_forms(case):
     """FP32 mode, and a split mode with the tensor-core form switched off (the
     GEMM route too, which would take the 16 x 64 product)."""
