@@ -476,22 +476,23 @@ __device__ __forceinline__ bool mbar_wait_inline(uint32_t bar, uint32_t parity, 
 }
 
 // MULTI: more than one chunk per tile (summed entries above 32), partial sums
-// promoted into FP32 registers; without it a tile is one chunk.  WIDE (more
-// than 64 free entries, at most 32 summed, two groups): the gathered chunk is
-// staged in two halves of 16 summed entries, accumulated in the same TMEM
-// columns (as many accumulations as one chunk of 32).
-template <int G, bool MULTI, bool POW2, bool WIDE>
+// promoted into FP32 registers; without it a tile is one chunk.  HALF (more
+// than 64 free entries, or operand planes too large for whole chunks; two
+// groups): each gathered chunk of 32 is staged in two halves of 16 summed
+// entries accumulated in the same TMEM columns (as many accumulations per
+// promotion as a whole chunk).
+template <int G, bool MULTI, bool POW2, bool HALF>
 __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant__ ApplyArgs a)
 {
-    constexpr int KC = WIDE ? ATC_KC / 2 : ATC_KC;   // summed entries per staged chunk
-    constexpr uint32_t ABY = WIDE ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;   // a group's A planes
+    constexpr int KC = HALF ? ATC_KC / 2 : ATC_KC;   // summed entries per staged chunk
+    constexpr uint32_t ABY = HALF ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;   // a group's A planes
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[G];
     __shared__ uint32_t tmem_holder;
     __shared__ int fail_any;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, g = tid >> 7, m = tid & 127, warp = tid >> 5;
-    const int nk = a.nk, nf = a.nf, nkb = (nk + 7) >> 3, nch = (MULTI || WIDE) ? (nk + KC - 1) / KC : 1;
+    const int nk = a.nk, nf = a.nf, nkb = (nk + 7) >> 3, nch = (MULTI || HALF) ? (nk + KC - 1) / KC : 1;
     const int nr = (nf + 7) >> 3;           // 16-column groups of D (8 complex outputs each)
     const int nrl = 16 * nr;                // real columns: the MMA's N
     const uint32_t bplane = (uint32_t)(nkb * nrl * 64);
@@ -608,7 +609,7 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
         for (int c = 0; c < nch; ++c) {
             const int kv = min(KC, nk - c * KC), kbc = (kv + 7) >> 3;
             // split the staged entries X[OFF ..] into the hi / lo planes of row m
-            // (OFF a compile-time offset: the second half of a wide chunk)
+            // (OFF a compile-time offset: the second half of a chunk)
             auto stage = [&](auto off_tag) {
                 constexpr int OFF = decltype(off_tag)::value;
 #pragma unroll
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                     }
                 }
             };
-            if (WIDE && c == 1) stage(std::integral_constant<int, KC>{});
+            if (HALF && (c & 1)) stage(std::integral_constant<int, KC>{});
             else stage(std::integral_constant<int, 0>{});
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -637,17 +638,17 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                             const uint64_t ad = sdesc(sA + pa * (ABY / 2) + kb * ATC_KBB + sub * 32);
                             const uint64_t bd =
                                 sdesc(sB + pb * bplane + (uint32_t)(c * (KC / 8) + kb) * (uint32_t)(nrl * 64) + sub * 32);
-                            // WIDE: the second half adds to the first in TMEM
-                            umma<1>(tmem, ad, bd, idesc, ((WIDE ? c : 0) | kb | sub | t) ? 1u : 0u);
+                            // a second half adds to the first in TMEM
+                            umma<1>(tmem, ad, bd, idesc, ((HALF ? (c & 1) : 0) | kb | sub | t) ? 1u : 0u);
                         }
                 umma_commit(bar);
             }
-            // the gathers of this group's next chunk go out before the wait (a wide
-            // tile's second half is already in registers)
+            // the gathers of this group's next chunk go out before the wait (a
+            // chunk's second half is already in registers)
             bool next = true;
             if (c + 1 < nch) {
-                pc = c + 1;
-                next = MULTI;
+                pc = HALF ? (c + 1) >> 1 : c + 1;   // the next chunk of 32
+                next = MULTI && (!HALF || (c & 1));
             } else {
                 p_advance();
                 while (p_u < u1 && !p_valid()) p_advance();
@@ -663,14 +664,17 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const bool last = c + 1 == nch;
+            // D is read after every chunk of 32 (promotion) or once at the end
+            const bool read_d = MULTI ? (!HALF || (c & 1) || last) : last;
+            const bool first = (HALF ? c >> 1 : c) == 0;   // the tile's first chunk of 32
             // 16-column groups of D
-            constexpr int HMAX = MULTI ? JET_APPLY_TC_MAXF_MULTI / 8 : WIDE ? JET_APPLY_TC_MAXF / 8 : JET_APPLY_TC_WIDEF / 8;
+            constexpr int HMAX = MULTI ? JET_APPLY_TC_MAXF_MULTI / 8 : HALF ? JET_APPLY_TC_MAXF / 8 : JET_APPLY_TC_WIDEF / 8;
             auto emit = [&](const int h, const uint32_t (&R)[16]) {
                 if (MULTI) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float v = __uint_as_float(R[j]);
-                        acc[(16 * h + j) % (MULTI ? 64 : 1)] = c == 0 ? v : acc[(16 * h + j) % (MULTI ? 64 : 1)] + v;
+                        acc[(16 * h + j) % (MULTI ? 64 : 1)] = first ? v : acc[(16 * h + j) % (MULTI ? 64 : 1)] + v;
                     }
                 }
                 if (last && rok) {
@@ -686,11 +690,10 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                     }
                 }
             };
-            // 16-column groups read two at a time, one wait per pair (a wide tile's
-            // D once, after its second half)
+            // 16-column groups read two at a time, one wait per pair
 #pragma unroll
             for (int h = 0; h < HMAX; h += 2) {
-                if (h < nr && (!WIDE || last)) {
+                if (h < nr && read_d) {
                     uint32_t R0[16], R1[16];
                     JET_TMEM_LD16(trow + 16 * h, R0);
                     if (h + 1 < nr) JET_TMEM_LD16(trow + 16 * (h + 1), R1);
@@ -794,6 +797,8 @@ cudaError_t set_apply_tc_smem_limits()
     JET_ATCSM(3, false, false, false);
     JET_ATCSM(2, false, true, true);
     JET_ATCSM(2, false, false, true);
+    JET_ATCSM(2, true, true, true);
+    JET_ATCSM(2, true, false, true);
 #undef JET_ATCSM
     return e;
 }
@@ -807,15 +812,18 @@ static cudaError_t launch_apply_tc(const ApplyArgs &a, const LaunchCfg &c, cudaS
         return cudaErrorInvalidValue;
     const int smem = jet_apply_tc_smem(G, a.nk, a.nf);
     if (smem > ATC_SMEM_MAX) return cudaErrorInvalidValue;
-    const bool pow2 = c.variant & 4, multi = a.nk > ATC_KC, wide = a.nf > JET_APPLY_TC_WIDEF;
-    // promotion registers: two groups and at most 32 free entries only; the wide
-    // form: two groups (256 TMEM columns each), one chunk of summed entries
+    const bool pow2 = c.variant & 4, multi = a.nk > ATC_KC, half = jet_apply_tc_half(a.nk, a.nf);
+    // promotion registers: two groups and at most 32 free entries only; halves:
+    // two groups (up to 256 TMEM columns each)
     if (multi && (G != 2 || a.nf > JET_APPLY_TC_MAXF_MULTI)) return cudaErrorInvalidValue;
-    if (wide && (G != 2 || multi)) return cudaErrorInvalidValue;
-    if (multi) {
+    if (half && G != 2) return cudaErrorInvalidValue;
+    if (multi && half) {
+        if (pow2) apply_tc_c64<2, true, true, true><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, true, false, true><<<c.gx, 256, smem, s>>>(a);
+    } else if (multi) {
         if (pow2) apply_tc_c64<2, true, true, false><<<c.gx, 256, smem, s>>>(a);
         else apply_tc_c64<2, true, false, false><<<c.gx, 256, smem, s>>>(a);
-    } else if (wide) {
+    } else if (half) {
         if (pow2) apply_tc_c64<2, false, true, true><<<c.gx, 256, smem, s>>>(a);
         else apply_tc_c64<2, false, false, true><<<c.gx, 256, smem, s>>>(a);
     } else if (G == 2) {

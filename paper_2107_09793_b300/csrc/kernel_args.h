@@ -22,13 +22,20 @@
 #define JET_APPLY_TC_SMEM_MAX 231424 // tensor-core form: dynamic shared memory cap (227 KiB less 1 KiB)
 
 // Dynamic shared memory of the tensor-core application: 1 KiB alignment slack,
-// one A chunk per thread group (half a chunk above JET_APPLY_TC_WIDEF free
-// entries) and the hi / lo TF32 planes of the small operand (summed entries
-// padded to blocks of 8, free entries to 8, two real rows each).
+// one A chunk per thread group (half a chunk when staged in halves) and the hi /
+// lo TF32 planes of the small operand (summed entries padded to blocks of 8,
+// free entries to 8, two real rows each).
+// Chunks staged in halves of 16 summed entries: above JET_APPLY_TC_WIDEF free
+// entries, or when two groups' whole chunks and the operand planes do not fit.
+static inline bool jet_apply_tc_half(int nk, int nf)
+{
+    const int nkb = (nk + 7) / 8, nr = 2 * ((nf + 7) / 8 * 8);
+    return nf > JET_APPLY_TC_WIDEF || 1024 + 2 * JET_APPLY_TC_ABYTES + 2 * nkb * nr * 64 > JET_APPLY_TC_SMEM_MAX;
+}
 static inline int jet_apply_tc_smem(int groups, int nk, int nf)
 {
     const int nkb = (nk + 7) / 8, nr = 2 * ((nf + 7) / 8 * 8);
-    const int abytes = nf > JET_APPLY_TC_WIDEF ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;
+    const int abytes = jet_apply_tc_half(nk, nf) ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;
     return 1024 + groups * abytes + 2 * nkb * nr * 64;
 }
 

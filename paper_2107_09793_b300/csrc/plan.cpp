@@ -334,8 +334,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         if (!tc_mode || fp64 || !big || nk > JET_APPLY_MAXK || nf < 1 || nf > JET_APPLY_TC_MAXF ||
             (nk > 32 && nf > JET_APPLY_TC_MAXF_MULTI))
             return 0;
-        if (nk <= 32 && nf <= JET_APPLY_TC_WIDEF && jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX)
-            return 3;   // (the wide form takes two groups: 256 TMEM columns each)
+        if (nk <= 32 && !jet_apply_tc_half((int)nk, (int)nf) &&
+            jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX)
+            return 3;   // (chunks staged in halves take two groups: up to 256 TMEM columns each)
         if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
         return 0;
     };

@@ -10,9 +10,10 @@ blocks (21 x 5, 200 x 3); several chunks per tile (128 and 200 summed entries,
 the FP32 register promotion); wide free extents (32, 48 and 64: N = 64, 96 and
 128 real columns, the last two with 128 TMEM columns per thread group; 16 x 64
 has both free sides of 64 or more, a product the GEMM route would otherwise
-take; 72 and 128 free entries with 20 and 32 summed: the wide form, N up to 256,
-the chunk staged in two halves); a summed label at stride 1 in A (fibers at
-stride 2); and a sliced
+take; 72 and 128 free entries with 20 and 32 summed: N up to 256, the chunk
+staged in two halves; 128 x 32 and 144 x 24, whose operand planes leave room
+only for half chunks: 8 and 9 halves, promoted in pairs); a summed label at
+stride 1 in A (fibers at stride 2); and a sliced
 summed label, so the node runs as two instances in one launch (the small
 operand is rebuilt per instance).  The fast_ cases put the 7 fastest labels of A
 on the fibers (one of them reading a leaf that is 8- but not 16-byte aligned).
@@ -61,6 +62,11 @@ CASES = {
     "k32_f48": ([0, 10, 11, 1], [11, 20, 10], {0: 128, 1: 256, 10: 4, 11: 8, 20: 48}, []),
     # wide: 32 summed, 128 free (N = 256; the chunk staged in two halves of 16)
     "k32_f128_wide": ([0, 10, 11, 1], [10, 20, 11], {0: 128, 1: 256, 10: 4, 11: 8, 20: 128}, []),
+    # 128 summed x 32 free: the operand planes (128 KB) leave room only for half
+    # chunks, 8 halves promoted in pairs
+    "k128_f32_halves": ([0] + list(range(10, 17)) + [1], list(range(10, 17)) + [20], {0: 128, 1: 256, 20: 32}, []),
+    # 144 summed (9 x 16) x 24 free: 9 halves, the last one promoted alone
+    "k144_f24_halves": ([0, 10, 11, 1], [11, 20, 10], {0: 128, 1: 256, 10: 9, 11: 16, 20: 24}, []),
     # wide with a ragged summed extent (20: one half of 16, one of 4) and 72 free
     "k20_f72_wide": ([0, 10, 11, 1], [11, 20, 10], {0: 128, 1: 256, 10: 4, 11: 5, 20: 72}, []),
     # a summed binary label at stride 1 in A: the fibers sit at stride 2
@@ -155,9 +161,9 @@ def test_apply_tensor_core_other_modes(case, prec):
     assert _check(case, prec, True, apply_tc_min_kf=1) <= TOL[prec]
 
 
-# 32 x 48 and the wide shapes are past the CUDA-core forms (held: 1024 padded
-# entries; streamed: 32 free)
-@pytest.mark.parametrize("case", sorted(set(CASES) - {"k32_f48", "k32_f128_wide", "k20_f72_wide"}))
+# 32 x 48, 144 x 24 and the wide shapes are past the CUDA-core forms (held: 1024
+# padded entries; streamed: 32 free, 4096 entries with the free ones padded to 16)
+@pytest.mark.parametrize("case", sorted(set(CASES) - {"k32_f48", "k32_f128_wide", "k20_f72_wide", "k144_f24_halves"}))
 def test_apply_cuda_core_forms(case):
     """FP32 mode, and a split mode with the tensor-core form switched off (the
     GEMM route too, which would take the 16 x 64 product)."""
