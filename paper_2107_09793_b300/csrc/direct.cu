@@ -100,7 +100,10 @@ __global__ void __launch_bounds__(256) direct_kernel(const __grid_constant__ Dir
 // P > 0: the group's 8 outputs are the outer product of values of A and B, each
 // loaded once per summed entry (NA + NB loads, not 16): P = NA in {1, 2, 4, 8}
 // with A's NA values fastest (output j = ib * NA + ia), or P = 16 + NB with B's
-// NB values fastest (j = ia * NB + ib).
+// NB values fastest (j = ia * NB + ib); P = 32: one output (a dot product).
+// A thread loads U table entries ahead (their loads overlap) and adds them in
+// increasing entry order; with power-of-two digits the outer summed values are
+// decoded 32 at a time, one per lane, and read by shuffle.
 template <typename V, bool POW2, int P>
 __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constant__ DirectArgs a)
 {
@@ -137,34 +140,95 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
     }
     const int64_t h0 = (int64_t)blockIdx.x * a.khi_per_part;
     const int64_t h1 = (h0 + a.khi_per_part) < a.n_khi ? (h0 + a.khi_per_part) : a.n_khi;
-    if (P > 0) {
+    int64_t w_h = -1, w_a = 0, w_b = 0;
+    auto h_offsets = [&](int64_t h, int64_t &ha, int64_t &hb) {   // block-uniform h
+        ha = hb = 0;
+        if (POW2) {
+            if (w_h < 0 || h - w_h >= 32) {
+                w_h = h;
+                w_a = w_b = 0;
+                decode<true>(h + (threadIdx.x & 31), a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, w_a, w_b);
+            }
+            ha = (int64_t)__shfl_sync(0xffffffffu, (long long)w_a, (int)(h - w_h));
+            hb = (int64_t)__shfl_sync(0xffffffffu, (long long)w_b, (int)(h - w_h));
+        } else {
+            decode<false>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
+        }
+    };
+    const int nklo = a.n_klo, bd = blockDim.x;
+    if (P == 32) {   // one output
+        constexpr int U = 8;
+        const V *__restrict__ A0 = A + oa[0];
+        const V *__restrict__ B0 = B + ob[0];
+        for (int64_t h = h0; h < h1; ++h) {
+            int64_t ha, hb;
+            h_offsets(h, ha, hb);
+            for (int q0 = threadIdx.x; q0 < nklo; q0 += U * bd) {
+                V xa[U], xb[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int q = q0 + u * bd;
+                    xa[u] = q < nklo ? __ldg(A0 + ha + sKA[q]) : vzero<V>();
+                    xb[u] = q < nklo ? __ldg(B0 + hb + sKB[q]) : vzero<V>();
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (q0 + u * bd < nklo) acc[0] = cmul_add(acc[0], xa[u], xb[u]);
+            }
+        }
+    } else if (P > 0) {
         constexpr bool BF = P & 16;   // B's values fastest
         constexpr int NF = (P & 15) ? (P & 15) : 1, NS = JET_SPLITK_G / NF;   // fastest side's values, slowest side's
-        constexpr int NA = BF ? NS : NF, NB = BF ? NF : NS;
+        constexpr int NA = BF ? NS : NF, NB = BF ? NF : NS, U = 4;
         for (int64_t h = h0; h < h1; ++h) {
-            int64_t ha = 0, hb = 0;
-            decode<POW2>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
-            for (int q = threadIdx.x; q < a.n_klo; q += blockDim.x) {
-                const int64_t ka = ha + sKA[q], kb = hb + sKB[q];
-                V xa[NA], xb[NB];
+            int64_t ha, hb;
+            h_offsets(h, ha, hb);
+            for (int q0 = threadIdx.x; q0 < nklo; q0 += U * bd) {
+                V xa[U][NA], xb[U][NB];
 #pragma unroll
-                for (int i = 0; i < NA; ++i) xa[i] = __ldg(A + oa[BF ? i * NB : i] + ka);
+                for (int u = 0; u < U; ++u) {
+                    const int q = q0 + u * bd;
+                    const bool ok = q < nklo;
+                    const int64_t ka = ha + (ok ? sKA[q] : 0), kb = hb + (ok ? sKB[q] : 0);
 #pragma unroll
-                for (int i = 0; i < NB; ++i) xb[i] = __ldg(B + ob[BF ? i : i * NA] + kb);
+                    for (int i = 0; i < NA; ++i) xa[u][i] = ok ? __ldg(A + oa[BF ? i * NB : i] + ka) : vzero<V>();
 #pragma unroll
-                for (int j = 0; j < JET_SPLITK_G; ++j)
-                    acc[j] = cmul_add(acc[j], xa[BF ? j / NB : j % NA], xb[BF ? j % NB : j / NA]);
+                    for (int i = 0; i < NB; ++i) xb[u][i] = ok ? __ldg(B + ob[BF ? i : i * NA] + kb) : vzero<V>();
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (q0 + u * bd < nklo) {
+#pragma unroll
+                        for (int j = 0; j < JET_SPLITK_G; ++j)
+                            acc[j] = cmul_add(acc[j], xa[u][BF ? j / NB : j % NA], xb[u][BF ? j % NB : j / NA]);
+                    }
             }
         }
     } else {
+        constexpr int U = 2;
         for (int64_t h = h0; h < h1; ++h) {
-            int64_t ha = 0, hb = 0;
-            decode<POW2>(h, a.khi_rank, a.khi_dim, a.khi_sA, a.khi_sB, ha, hb);
-            for (int q = threadIdx.x; q < a.n_klo; q += blockDim.x) {
-                const int64_t ka = ha + sKA[q], kb = hb + sKB[q];
+            int64_t ha, hb;
+            h_offsets(h, ha, hb);
+            for (int q0 = threadIdx.x; q0 < nklo; q0 += U * bd) {
+                V xa[U][JET_SPLITK_G], xb[U][JET_SPLITK_G];
 #pragma unroll
-                for (int j = 0; j < JET_SPLITK_G; ++j)
-                    if (j < nout) acc[j] = cmul_add(acc[j], __ldg(A + oa[j] + ka), __ldg(B + ob[j] + kb));
+                for (int u = 0; u < U; ++u) {
+                    const int q = q0 + u * bd;
+                    const bool ok = q < nklo;
+                    const int64_t ka = ha + (ok ? sKA[q] : 0), kb = hb + (ok ? sKB[q] : 0);
+#pragma unroll
+                    for (int j = 0; j < JET_SPLITK_G; ++j) {
+                        xa[u][j] = ok && j < nout ? __ldg(A + oa[j] + ka) : vzero<V>();
+                        xb[u][j] = ok && j < nout ? __ldg(B + ob[j] + kb) : vzero<V>();
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (q0 + u * bd < nklo) {
+#pragma unroll
+                        for (int j = 0; j < JET_SPLITK_G; ++j)
+                            if (j < nout) acc[j] = cmul_add(acc[j], xa[u][j], xb[u][j]);
+                    }
             }
         }
     }
@@ -396,8 +460,8 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
     bool fp64 = c.variant & 1, splitk = c.variant & 2, pow2 = c.variant & 4;
     size_t smem = c.smem;
     const int na = a.splitk_na;
-    if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20) ||
-                    a.n_out % JET_SPLITK_G != 0))
+    if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20 && na != 32) ||
+                    (na == 32 ? a.n_out != 1 : a.n_out % JET_SPLITK_G != 0)))
         return cudaErrorInvalidValue;
 #define JET_DIRECT_LAUNCH(V, P)                                                                 \
     do {                                                                                        \
@@ -409,6 +473,7 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
             case 8: direct_splitk_kernel<V, P, 8><<<grid, c.block, smem, s>>>(a); break;        \
             case 18: direct_splitk_kernel<V, P, 18><<<grid, c.block, smem, s>>>(a); break;      \
             case 20: direct_splitk_kernel<V, P, 20><<<grid, c.block, smem, s>>>(a); break;      \
+            case 32: direct_splitk_kernel<V, P, 32><<<grid, c.block, smem, s>>>(a); break;      \
             default: direct_splitk_kernel<V, P, 0><<<grid, c.block, smem, s>>>(a); break;       \
             }                                                                                   \
         } else direct_kernel<V, P><<<grid, c.block, smem, s>>>(a);                              \

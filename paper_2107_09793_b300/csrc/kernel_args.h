@@ -57,7 +57,8 @@ struct DirectArgs {
     int32_t splitk_na;              // split-K: 0, or the outer-product pattern of every group of
                                     // 8 outputs, whose operand values are then read once per
                                     // summed entry: NA in {1, 2, 4, 8} = NA values of A (fastest)
-                                    // x 8 / NA of B; 16 + NB (NB in {2, 4}) = NB of B fastest
+                                    // x 8 / NA of B; 16 + NB (NB in {2, 4}) = NB of B fastest;
+                                    // 32 = a single output (a dot product)
     int64_t row_dim[JET_MAXR], row_sA[JET_MAXR], row_sB[JET_MAXR];   // fastest label first
     int64_t khi_dim[JET_MAXR], khi_sA[JET_MAXR], khi_sB[JET_MAXR];   // fastest label first
 };

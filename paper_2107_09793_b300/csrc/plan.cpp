@@ -820,12 +820,43 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 d.row_sA[j] = strideA(C.labels[li]);
                 d.row_sB[j] = strideB(C.labels[li]);
             }
-            // summed labels: slowest first by stride in the larger operand
-            std::vector<int64_t> Ks = K;
-            std::stable_sort(Ks.begin(), Ks.end(), [&](int64_t x, int64_t y) {
-                int px = find_pos(VX.labels, x), py = find_pos(VX.labels, y);
-                return VX.strides[px] > VX.strides[py];
-            });
+            // summed labels, slowest first.  The inner part (a table of up to
+            // JET_KLOMAX entries whose entries a block's threads share out) takes
+            // the fastest summed labels of the two operands in turn, so that both
+            // read whole sectors within a block when they order these labels
+            // differently; inside each part, slowest first by stride in the larger
+            // operand.
+            const View &VY = a_big ? VB : VA;
+            auto slower_in = [&](const View &V) {
+                return [&V](int64_t x, int64_t y) {
+                    return V.strides[find_pos(V.labels, x)] > V.strides[find_pos(V.labels, y)];
+                };
+            };
+            std::vector<int64_t> fx = K, fy = K, lo, hi;
+            std::stable_sort(fx.begin(), fx.end(), slower_in(VX));
+            std::stable_sort(fy.begin(), fy.end(), slower_in(VY));
+            {
+                int64_t n_lo = 1, mA = 0, mB = 0;
+                auto take = [&](int64_t l) {
+                    const int64_t d = net.labels.at(l).dim;
+                    if (find_pos(lo, l) >= 0 || n_lo * d > JET_KLOMAX || mA + (d - 1) * strideA(l) > INT32_MAX ||
+                        mB + (d - 1) * strideB(l) > INT32_MAX)
+                        return;
+                    lo.push_back(l);
+                    n_lo *= d;
+                    mA += (d - 1) * strideA(l);
+                    mB += (d - 1) * strideB(l);
+                };
+                for (size_t i = K.size(); i-- > 0;) {   // fastest first in each operand, in turn
+                    take(fx[i]);
+                    take(fy[i]);
+                }
+            }
+            for (int64_t l : fx)
+                if (find_pos(lo, l) < 0) hi.push_back(l);
+            std::stable_sort(lo.begin(), lo.end(), slower_in(VX));
+            std::vector<int64_t> Ks = hi;   // hi already slowest first in VX
+            Ks.insert(Ks.end(), lo.begin(), lo.end());
             std::vector<int64_t> Kd;
             for (int64_t l : Ks) Kd.push_back(net.labels.at(l).dim);
             size_t nklo_labels = 0;
@@ -879,8 +910,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             const int64_t plain_blocks = (d.n_out + 255) / 256 * n_inst;
             const bool few_blocks = plain_blocks < 148 * 4;
             if ((total_out < 16384 || few_blocks) && n_k >= 4096 && d.n_khi > 1) {
+                // about four waves of 8 blocks per SM, each part at least 4096 summed entries
                 int64_t groups = (d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G * n_inst;
-                int64_t want = std::max<int64_t>(few_blocks ? 2 : 1, (148 * 8 + groups - 1) / groups);
+                int64_t want = std::max<int64_t>(few_blocks ? 2 : 1, (148 * 8 * 4 + groups - 1) / groups);
+                want = std::min<int64_t>(want, std::max<int64_t>(1, d.n_khi * d.n_klo / 4096));
                 int64_t parts = std::min<int64_t>(want, d.n_khi);
                 d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
                 d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
@@ -889,6 +922,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             // values of A and NB = 8 / NA of B, each is loaded once per summed entry
             // (fewest loads first: NA = 2 or 4 take 6, NA = 1 or 8 take 9); A's
             // values fastest (pattern NA) or B's (pattern 16 + NB)
+            if (d.ksplit > 1 && d.n_out == 1) d.splitk_na = 32;   // a dot product
             if (d.ksplit > 1 && d.n_out % JET_SPLITK_G == 0 && d.n_out <= (1 << 16)) {
                 std::vector<int64_t> eA(d.n_out), eB(d.n_out);
                 for (int64_t e = 0; e < d.n_out; ++e) {
