@@ -910,10 +910,12 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             const int64_t plain_blocks = (d.n_out + 255) / 256 * n_inst;
             const bool few_blocks = plain_blocks < 148 * 4;
             if ((total_out < 16384 || few_blocks) && n_k >= 4096 && d.n_khi > 1) {
-                // about four waves of 8 blocks per SM, each part at least 4096 summed entries
+                // one wave of 8 blocks per SM, four for summed extents of 2^20 or more
+                // (whose parts stay long; more parts for shorter ones cost more in
+                // partials and launch tails than they gain: the adjoint's environments)
                 int64_t groups = (d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G * n_inst;
-                int64_t want = std::max<int64_t>(few_blocks ? 2 : 1, (148 * 8 * 4 + groups - 1) / groups);
-                want = std::min<int64_t>(want, std::max<int64_t>(1, d.n_khi * d.n_klo / 4096));
+                const int64_t waves = n_k >= (1 << 20) ? 4 : 1;
+                int64_t want = std::max<int64_t>(few_blocks ? 2 : 1, (148 * 8 * waves + groups - 1) / groups);
                 int64_t parts = std::min<int64_t>(want, d.n_khi);
                 d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
                 d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
