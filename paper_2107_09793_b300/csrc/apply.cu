@@ -387,11 +387,12 @@ __global__ void __launch_bounds__(256, 2) apply_quad_c64(const __grid_constant__
 // (instance, G consecutive tiles), group g taking tile g of each unit; the
 // small operand's planes are rebuilt in shared memory when the instance
 // changes.  Per chunk of 32 summed entries a thread: splits its gathered values
-// into the group's K-major SWIZZLE_64B planes, the group synchronises, one
-// thread issues the MMAs and commits them to the group's mbarrier, every thread
-// issues the gathers of its next chunk (they stay in flight through the wait
-// and the epilogue), waits for the MMAs (bounded: ~2 s, then the group stops and
-// the kernel records status bit 2) and reads its row of D.
+// into the group's K-major SWIZZLE_64B planes, issues the gathers of its next
+// chunk (before the group barrier with one chunk per tile, after the MMA issue
+// with several; they stay in flight through the wait and the epilogue), the
+// group synchronises, one thread issues the MMAs and commits them to the
+// group's mbarrier, every thread waits for the MMAs (bounded: ~2 s, then the
+// group stops and the kernel records status bit 2) and reads its row of D.
 constexpr int ATC_M = 128;     // fibers per tile: MMA M, TMEM lanes
 constexpr int ATC_KC = 32;     // summed entries per chunk (64 real K = 4 blocks of 16 TF32)
 constexpr int ATC_KBB = ATC_M * 64;   // bytes of one 64-byte-wide K block of an A plane
@@ -628,8 +629,31 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
             else stage(std::integral_constant<int, 0>{});
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            // The gathers of this group's next chunk (the staged registers are free;
+            // a chunk's second half is already in registers) stay in flight through
+            // the MMA wait and the epilogue.  With one chunk per tile they go out
+            // here, ahead of the barrier and of the MMA issue, whose thread would
+            // otherwise hold back the rest of its warp: the next tile's loads are
+            // the tile's critical path.  With several chunks the MMAs are (the next
+            // chunk is staged only once they have read the planes), so they go out
+            // after the issue.
+            auto gather_next = [&]() {
+                bool next = true;
+                if (c + 1 < nch) {
+                    pc = HALF ? (c + 1) >> 1 : c + 1;   // the next chunk of 32
+                    next = MULTI && (!HALF || (c & 1));
+                } else {
+                    p_advance();
+                    while (p_u < u1 && !p_valid()) p_advance();
+                    pc = 0;
+                }
+                if (next && p_u < u1) gather(pc);
+            };
+            if (!MULTI) gather_next();
             group_sync(1 + g);
-            if (m == 0) {
+            // Several chunks: a plain issue loop (the unrolled form below measured a few
+            // per cent slower on those tiles, faster on one-chunk tiles).
+            if (MULTI && m == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int kb = 0; kb < kbc; ++kb)
                     for (int sub = 0; sub < 2; ++sub)
@@ -638,23 +662,40 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                             const uint64_t ad = sdesc(sA + pa * (ABY / 2) + kb * ATC_KBB + sub * 32);
                             const uint64_t bd =
                                 sdesc(sB + pb * bplane + (uint32_t)(c * (KC / 8) + kb) * (uint32_t)(nrl * 64) + sub * 32);
-                            // a second half adds to the first in TMEM
                             umma<1>(tmem, ad, bd, idesc, ((HALF ? (c & 1) : 0) | kb | sub | t) ? 1u : 0u);
                         }
                 umma_commit(bar);
             }
-            // the gathers of this group's next chunk go out before the wait (a
-            // chunk's second half is already in registers)
-            bool next = true;
-            if (c + 1 < nch) {
-                pc = HALF ? (c + 1) >> 1 : c + 1;   // the next chunk of 32
-                next = MULTI && (!HALF || (c & 1));
-            } else {
-                p_advance();
-                while (p_u < u1 && !p_valid()) p_advance();
-                pc = 0;
+            if (!MULTI && m == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // The issue loop is unrolled with the descriptors of the chunk's first
+                // K block formed once: every other operand position is an added
+                // constant (descriptor start addresses count 16-byte units and all
+                // planes lie below 256 KB, so an add never carries out of that field).
+                // Products per (K block, 32-byte half): hi.hi, hi.lo, lo.hi.
+                const uint64_t ad0 = sdesc(sA);
+                const uint64_t bd0 = sdesc(sB + (uint32_t)(c * (KC / 8)) * (uint32_t)(nrl * 64));
+                const uint64_t b_kb = (uint64_t)(nrl * 4), b_lo = (uint64_t)(bplane >> 4);
+                constexpr uint64_t a_lo = (ABY / 2) >> 4;
+                const uint32_t acc0 = HALF ? (uint32_t)(c & 1) : 0u;   // a second half adds to the first in TMEM
+#pragma unroll
+                for (int kb = 0; kb < KC / 8; ++kb) {
+                    if (kb < kbc) {
+#pragma unroll
+                        for (int sub = 0; sub < 2; ++sub) {
+                            const uint64_t ad = ad0 + (uint64_t)((kb * ATC_KBB + sub * 32) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)kb * b_kb + (uint64_t)(sub * 2);
+                            umma<1>(tmem, ad, bd, idesc, (acc0 | (uint32_t)kb | (uint32_t)sub) ? 1u : 0u);
+                            if (terms > 1) {
+                                umma<1>(tmem, ad, bd + b_lo, idesc, 1u);
+                                umma<1>(tmem, ad + a_lo, bd, idesc, 1u);
+                            }
+                        }
+                    }
+                }
+                umma_commit(bar);
             }
-            if (next && p_u < u1) gather(pc);
+            if (MULTI) gather_next();
             const bool ok = mbar_wait_inline(bar, phase, (volatile int *)&fail_any);
             phase ^= 1u;
             if (group_any(!ok, 1 + g)) {
