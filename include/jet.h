@@ -380,6 +380,34 @@ int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs,
  * Errors: JET_ESTATE (no plan yet). */
 int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t *n_out);
 
+/* One device-workspace allocation of a plan, for jet_plan_buffers.  Times
+ * count launches in issue order: an allocation made with t launches issued is
+ * first usable by launch t, and a release made with t launches issued frees
+ * the bytes for launches t and later. */
+typedef struct {
+    int32_t node;             /* tree node (SSA id) whose instances it holds; -1 = scratch
+                                 of one node's launches (split-K partials, operand planes) */
+    int32_t t_alloc;          /* launches issued when it was allocated                   */
+    int32_t t_release;        /* launches issued when it was released; -1 = never (held
+                                 to the end, e.g. by an adjoint sweep)                    */
+    int32_t first_use;        /* node buffers: first launch of the node (it writes them)  */
+    int32_t last_use;         /* node buffers: last launch of the node or of its parent
+                                 (the reader); -1 for scratch                             */
+    int32_t pad_;
+    int64_t offset;           /* byte offset in the workspace                           */
+    int64_t bytes;            /* bytes (rounded up to 256)                               */
+} jet_buffer_record;
+
+/* Intermediate deletion (Section 4: an intermediate is deleted once every
+ * task that reads it has run): the liveness record of the device workspace of
+ * the plan run last (else the current forward plan), one record per
+ * allocation in allocation order.  A correct plan releases a node's buffer
+ * only after its last reader was issued (last_use < t_release), and never
+ * gives overlapping bytes to two allocations whose [t_alloc, t_release)
+ * windows meet.  Host only; writes min(cap, count) records and the count.
+ * Errors: JET_ESTATE (no plan yet), JET_EINVAL (net NULL). */
+int jet_plan_buffers(const jet_network *net, jet_buffer_record *out, int32_t cap, int32_t *n_out);
+
 /* Statistics of the network and the last plan (see jet_stats_t). */
 int jet_stats(const jet_network *net, jet_stats_t *out);
 
@@ -396,7 +424,11 @@ int jet_stats(const jet_network *net, jet_stats_t *out);
  * device array inside the library, held by every GPU that loads the library
  * until the process exits; the output may have at most 524280 elements
  * (larger outputs are rejected with JET_EINVAL), each tensor fewer than 2^31
- * elements, at most 40 labels each.  The first call on a device looks up that
+ * elements, at most 40 labels each (labels of dim 1 are accepted and ignored).
+ * The offset tables are written into the scratch by a small kernel on
+ * cuda_stream (three launches per call, no host-to-device copy).  A CUDA error
+ * already pending on the calling thread is reported as JET_ECUDA and left
+ * pending.  The first call on a device looks up that
  * array's device address (cudaGetSymbolAddress); make that first call before
  * any stream capture on the device.  Every call shares the array: calls that
  * overlap on the GPU (different streams, or different host threads) race, so

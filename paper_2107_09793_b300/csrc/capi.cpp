@@ -812,6 +812,50 @@ int jet_profile(const jet_network *net, jet_op_record *out, int32_t cap, int32_t
     });
 }
 
+int jet_plan_buffers(const jet_network *net, jet_buffer_record *out, int32_t cap, int32_t *n_out)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        const Plan *PP = net->last_run ? net->last_run : net->plan.get();
+        if (!PP) fail(JET_ESTATE, "no plan yet");
+        const Plan &P = *PP;
+        // launches of each tree node (a batched launch counts for every node it
+        // holds); the slice reduction reads only the root's own result, so it
+        // does not count as a read of the root's children
+        std::vector<int32_t> first(P.parent.size(), -1), last(P.parent.size(), -1), last_contract(P.parent.size(), -1);
+        auto touch = [&](int32_t v, int32_t i, bool reduce) {
+            if (v < 0 || (size_t)v >= first.size()) return;
+            if (first[v] < 0) first[v] = i;
+            last[v] = i;
+            if (!reduce) last_contract[v] = i;
+        };
+        for (size_t i = 0; i < P.ops.size(); ++i) {
+            const Op &op = P.ops[i];
+            if (op.batch_count > 0)
+                for (int32_t j = 0; j < op.batch_count; ++j) touch(P.batch_nodes[op.batch_first + j], (int32_t)i, false);
+            else
+                touch(op.node, (int32_t)i, op.kind == OpKind::Reduce);
+        }
+        if (n_out) *n_out = (int32_t)P.buffers.size();
+        for (size_t i = 0; out && i < P.buffers.size() && (int32_t)i < cap; ++i) {
+            const Plan::BufferRec &b = P.buffers[i];
+            jet_buffer_record &r = out[i];
+            std::memset(&r, 0, sizeof r);
+            r.node = b.node;
+            r.offset = b.offset;
+            r.bytes = b.bytes;
+            r.t_alloc = b.t_alloc;
+            r.t_release = b.t_release;
+            r.first_use = r.last_use = -1;
+            if (b.node >= 0) {
+                r.first_use = first[b.node];
+                const int32_t pa = P.parent[b.node];
+                r.last_use = std::max(last[b.node], pa >= 0 ? last_contract[pa] : -1);
+            }
+        }
+    });
+}
+
 int jet_stats(const jet_network *net, jet_stats_t *out)
 {
     return guarded([&] {

@@ -66,6 +66,8 @@ struct Op {
     int32_t grid_x = 1, grid_y = 1, grid_z = 1, block = 256;
     int32_t smem = 0;
     int32_t variant = 0;      // kernel-specific variant selector
+    int32_t batch_first = -1; // batched small contractions: their nodes in Plan::batch_nodes
+    int32_t batch_count = 0;
 };
 
 struct Network;
@@ -98,6 +100,15 @@ struct Plan {
     size_t kept_pool_bytes = 0;      // device pool the plan's kept entries need
     size_t arena_bytes = 0;          // intermediates + scratch (device workspace)
     std::vector<Op> ops;
+    std::vector<int32_t> batch_nodes;  // nodes of the batched small-contraction launches
+    // arena liveness record: one entry per allocation, times in launches issued
+    struct BufferRec {
+        int32_t node;             // tree node whose result it holds, -1 = scratch
+        int64_t offset, bytes;
+        int32_t t_alloc, t_release;   // launches issued before the allocation / the release (-1: never)
+    };
+    std::vector<BufferRec> buffers;
+    std::vector<int32_t> parent;       // per tree node (SSA id), -1 for the root
     std::vector<uint8_t> host_args;   // argument blocks (pointers patched at bind time)
     // pointer patch list: (byte offset in host_args, buffer id, element/byte offset)
     struct Patch { size_t at; int32_t base; int64_t byte_off; };

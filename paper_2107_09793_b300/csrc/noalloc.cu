@@ -8,6 +8,7 @@
 // live in one fixed, file-scope device array instead of the plan workspace.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -56,6 +57,52 @@ static void check(cudaError_t e, const char *what)
     }
 }
 
+// The offset tables and the three address slots, written into the scratch by
+// one small kernel from the labels' dims and strides (passed by value), so that
+// no host staging buffer or host-to-device copy is involved.
+constexpr int NOALLOC_TABLE_LABELS = 16;   // a 1024-entry table spans at most 10 labels of dim >= 2
+struct NoallocTableArgs {
+    uint64_t slots;                        // 3 uint64 address slots (A, B, C)
+    uint64_t pa, pb, pc;
+    uint64_t colA, colB, kA, kB;           // int32 tables
+    int32_t ncols, nklo, nc, nk;
+    int64_t cdim[NOALLOC_TABLE_LABELS], csA[NOALLOC_TABLE_LABELS], csB[NOALLOC_TABLE_LABELS];   // fastest first
+    int64_t kdim[NOALLOC_TABLE_LABELS], ksA[NOALLOC_TABLE_LABELS], ksB[NOALLOC_TABLE_LABELS];
+};
+
+__global__ void noalloc_tables_kernel(NoallocTableArgs t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        uint64_t *slot = (uint64_t *)t.slots;
+        slot[0] = t.pa;
+        slot[1] = t.pb;
+        slot[2] = t.pc;
+    }
+    if (i < t.ncols) {
+        int64_t r = i, x = 0, y = 0;
+        for (int j = 0; j < t.nc; ++j) {
+            const int64_t v = r % t.cdim[j];
+            x += v * t.csA[j];
+            y += v * t.csB[j];
+            r /= t.cdim[j];
+        }
+        ((int32_t *)t.colA)[i] = (int32_t)x;
+        ((int32_t *)t.colB)[i] = (int32_t)y;
+    }
+    if (i < t.nklo) {
+        int64_t r = i, x = 0, y = 0;
+        for (int j = 0; j < t.nk; ++j) {
+            const int64_t v = r % t.kdim[j];
+            x += v * t.ksA[j];
+            y += v * t.ksB[j];
+            r /= t.kdim[j];
+        }
+        ((int32_t *)t.kA)[i] = (int32_t)x;
+        ((int32_t *)t.kB)[i] = (int32_t)y;
+    }
+}
+
 void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_t *dims_a, const void *a_dev,
                            int32_t rank_b, const int64_t *labels_b, const int32_t *dims_b, const void *b_dev,
                            void *c_dev, int32_t device, void *stream)
@@ -91,15 +138,19 @@ void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_
     };
     // output = A's free labels then B's free labels; summed = shared labels
     std::vector<int64_t> out, od, oa, ob, K, kd, ka, kb;
+    // A label of dim 1 has the single value 0: it moves no offset and is left
+    // out of the output and summed decodes (the output's row-major layout is
+    // the same with or without it).
     for (size_t i = 0; i < A.l.size(); ++i) {
         int p = pos(B.l, A.l[i]);
+        if (p >= 0 && B.d[p] != A.d[i]) fail(JET_EINVAL, "shared label with different dims");
+        if (A.d[i] == 1) continue;
         if (p < 0) {
             out.push_back(A.l[i]);
             od.push_back(A.d[i]);
             oa.push_back(A.s[i]);
             ob.push_back(0);
         } else {
-            if (B.d[p] != A.d[i]) fail(JET_EINVAL, "shared label with different dims");
             K.push_back(A.l[i]);
             kd.push_back(A.d[i]);
             ka.push_back(A.s[i]);
@@ -107,7 +158,7 @@ void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_
         }
     }
     for (size_t i = 0; i < B.l.size(); ++i)
-        if (pos(A.l, B.l[i]) < 0) {
+        if (B.d[i] > 1 && pos(A.l, B.l[i]) < 0) {
             out.push_back(B.l[i]);
             od.push_back(B.d[i]);
             oa.push_back(0);
@@ -125,18 +176,19 @@ void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_
     size_t nc = 0;
     int64_t ncols = 1;
     while (nc < out.size() && ncols * od[out.size() - 1 - nc] <= JET_COLMAX) ncols *= od[out.size() - 1 - nc++];
-    std::vector<int32_t> colA(ncols), colB(ncols);
-    for (int64_t c = 0; c < ncols; ++c) {
-        int64_t r = c, x = 0, y = 0;
-        for (size_t j = 0; j < nc; ++j) {
-            size_t li = out.size() - 1 - j;
-            x += (r % od[li]) * oa[li];
-            y += (r % od[li]) * ob[li];
-            r /= od[li];
-        }
-        colA[c] = (int32_t)x;
-        colB[c] = (int32_t)y;
+    if (out.size() - nc > (size_t)JET_MAXR)
+        fail(JET_EINVAL, "output rank too large (at most " + std::to_string(JET_MAXR) + " labels of dim > 1 besides "
+                         "the fastest " + std::to_string(nc) + ")");
+    NoallocTableArgs t;
+    std::memset(&t, 0, sizeof t);
+    t.nc = (int32_t)nc;
+    for (size_t j = 0; j < nc; ++j) {
+        size_t li = out.size() - 1 - j;
+        t.cdim[j] = od[li];
+        t.csA[j] = oa[li];
+        t.csB[j] = ob[li];
     }
+    t.ncols = (int32_t)ncols;
     d.n_cols = (int32_t)ncols;
     d.row_rank = (int32_t)(out.size() - nc);
     d.n_rows = 1;
@@ -151,18 +203,17 @@ void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_
     size_t nk = 0;
     int64_t nklo = 1;
     while (nk < K.size() && nklo * kd[K.size() - 1 - nk] <= JET_KLOMAX) nklo *= kd[K.size() - 1 - nk++];
-    std::vector<int32_t> tkA(nklo), tkB(nklo);
-    for (int64_t q = 0; q < nklo; ++q) {
-        int64_t r = q, x = 0, y = 0;
-        for (size_t j = 0; j < nk; ++j) {
-            size_t li = K.size() - 1 - j;
-            x += (r % kd[li]) * ka[li];
-            y += (r % kd[li]) * kb[li];
-            r /= kd[li];
-        }
-        tkA[q] = (int32_t)x;
-        tkB[q] = (int32_t)y;
+    if (K.size() - nk > (size_t)JET_MAXR)
+        fail(JET_EINVAL, "too many summed labels (at most " + std::to_string(JET_MAXR) + " of dim > 1 besides "
+                         "the fastest " + std::to_string(nk) + ")");
+    t.nk = (int32_t)nk;
+    for (size_t j = 0; j < nk; ++j) {
+        size_t li = K.size() - 1 - j;
+        t.kdim[j] = kd[li];
+        t.ksA[j] = ka[li];
+        t.ksB[j] = kb[li];
     }
+    t.nklo = (int32_t)nklo;
     d.n_klo = (int32_t)nklo;
     d.khi_rank = (int32_t)(K.size() - nk);
     d.n_khi = 1;
@@ -184,7 +235,7 @@ void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_
     d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
     d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
 
-    // stage the tables and address slots into the scratch, then launch on the caller's stream
+    // write the tables and address slots into the scratch, then launch on the caller's stream
     int prev = -1;
     check(cudaGetDevice(&prev), "cudaGetDevice");
     check(cudaSetDevice(device), "cudaSetDevice");
@@ -192,35 +243,46 @@ void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_
         int dev;
         ~Restore() { cudaSetDevice(dev); }
     } restore{prev};
+    // an error left pending by the caller's earlier CUDA work is reported, not cleared
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        fail(JET_ECUDA, std::string("a CUDA error was pending before the call: ") + cudaGetErrorString(pending));
     unsigned char *scratch = (unsigned char *)noalloc_scratch_address(device);
-    std::vector<unsigned char> host(NOALLOC_TABLE_BYTES, 0);
     size_t off = 0;
-    auto put = [&](const void *src, size_t n) {
+    auto place = [&](size_t n) {
         size_t at = off;
-        std::memcpy(host.data() + at, src, n);
         off = (off + n + 15) / 16 * 16;
         return at;
     };
-    uint64_t pa = (uint64_t)a_dev, pb = (uint64_t)b_dev, pc = (uint64_t)c_dev;
-    size_t o_pa = put(&pa, 8), o_pb = put(&pb, 8), o_pc = put(&pc, 8);
-    size_t o_ca = put(colA.data(), colA.size() * 4), o_cb = put(colB.data(), colB.size() * 4);
-    size_t o_ka = put(tkA.data(), tkA.size() * 4), o_kb = put(tkB.data(), tkB.size() * 4);
+    const size_t o_slots = place(3 * 8);
+    const size_t o_ca = place((size_t)ncols * 4), o_cb = place((size_t)ncols * 4);
+    const size_t o_ka = place((size_t)nklo * 4), o_kb = place((size_t)nklo * 4);
+    if (off > NOALLOC_TABLE_BYTES) fail(JET_EINVAL, "offset tables exceed the scratch table area");
+    t.slots = (uint64_t)(scratch + o_slots);
+    t.pa = (uint64_t)a_dev;
+    t.pb = (uint64_t)b_dev;
+    t.pc = (uint64_t)c_dev;
+    t.colA = (uint64_t)(scratch + o_ca);
+    t.colB = (uint64_t)(scratch + o_cb);
+    t.kA = (uint64_t)(scratch + o_ka);
+    t.kB = (uint64_t)(scratch + o_kb);
     cudaStream_t s = (cudaStream_t)stream;
-    check(cudaMemcpyAsync(scratch, host.data(), off, cudaMemcpyHostToDevice, s), "cudaMemcpyAsync(tables)");
-    d.ptrA = (uint64_t)(scratch + o_pa);
-    d.ptrB = (uint64_t)(scratch + o_pb);
-    d.ptrC = (uint64_t)(scratch + o_pc);
-    d.colA = (uint64_t)(scratch + o_ca);
-    d.colB = (uint64_t)(scratch + o_cb);
-    d.kA = (uint64_t)(scratch + o_ka);
-    d.kB = (uint64_t)(scratch + o_kb);
+    const int64_t n_tab = std::max<int64_t>({ncols, nklo, 1});
+    noalloc_tables_kernel<<<(unsigned)((n_tab + 255) / 256), 256, 0, s>>>(t);
+    check(cudaGetLastError(), "offset-table launch");
+    d.ptrA = t.slots;
+    d.ptrB = t.slots + 8;
+    d.ptrC = t.slots + 16;
+    d.colA = t.colA;
+    d.colB = t.colB;
+    d.kA = t.kA;
+    d.kB = t.kB;
     d.partials = (uint64_t)(scratch + NOALLOC_TABLE_BYTES);   // every partial is written before it is read
 
     bool pow2 = true;
     for (int j = 0; j < d.row_rank; ++j) pow2 = pow2 && (d.row_dim[j] & (d.row_dim[j] - 1)) == 0;
     for (int j = 0; j < d.khi_rank; ++j) pow2 = pow2 && (d.khi_dim[j] & (d.khi_dim[j] - 1)) == 0;
     LaunchCfg c{d.ksplit, (int)groups, 1, 256, (int)(8 * nklo), 2 | (pow2 ? 4 : 0)};
-    cudaGetLastError();
     check(launch_direct(d, c, s), "split-K contraction launch");
     SplitKReduceArgs r;
     std::memset(&r, 0, sizeof r);

@@ -81,12 +81,23 @@ struct Blob {
     }
 };
 
-// Best-fit allocator over a linear arena, 256-byte granules.
+// Best-fit allocator over a linear arena, 256-byte granules.  Every allocation
+// is logged with the launch count at the time it was made and released (the
+// plan's liveness record, read back by jet_plan_buffers).
 struct Arena {
     std::map<size_t, size_t> free_;   // offset -> size
     size_t top = 0, peak = 0;
+    const std::vector<Op> *clock = nullptr;
+    std::vector<Plan::BufferRec> log;
     static size_t round(size_t b) { return (b + 255) / 256 * 256; }
+    int32_t now() const { return clock ? (int32_t)clock->size() : 0; }
     size_t alloc(size_t bytes)
+    {
+        const size_t off = alloc_(bytes);
+        log.push_back({-1, (int64_t)off, (int64_t)round(std::max<size_t>(bytes, 1)), now(), -1});
+        return off;
+    }
+    size_t alloc_(size_t bytes)
     {
         bytes = round(std::max<size_t>(bytes, 1));
         auto best = free_.end();
@@ -105,6 +116,11 @@ struct Arena {
     }
     void release(size_t off, size_t bytes)
     {
+        for (auto r = log.rbegin(); r != log.rend(); ++r)
+            if (r->offset == (int64_t)off && r->t_release < 0) {
+                r->t_release = now();
+                break;
+            }
         bytes = round(std::max<size_t>(bytes, 1));
         auto it = free_.emplace(off, bytes).first;
         auto nx = std::next(it);
@@ -277,6 +293,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
 
     // ---- internal nodes: instances, layouts, routing
     Arena arena;
+    arena.clock = &P.ops;
     Blob blob;
     const bool gemm_ok = gemm_available(net.opt.precision);
     const bool tc_mode = tc_planes(net.opt.precision) > 0;
@@ -699,6 +716,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         op.bytes = batch_bytes;
         op.variant = fp64 ? 1 : 0;
         op.grid_x = blocks;
+        op.batch_first = (int32_t)P.batch_nodes.size();
+        op.batch_count = (int32_t)batch_nodes.size();
+        P.batch_nodes.insert(P.batch_nodes.end(), batch_nodes.begin(), batch_nodes.end());
         P.ops.push_back(op);
         for (int32_t v : batch_nodes) release_children(v);
         batch.clear();
@@ -1146,6 +1166,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             N.buf_off = (int64_t)net.kept.at(v).off;
         } else {
             N.buf_off = (int64_t)arena.alloc(nbytes);
+            arena.log.back().node = v;
             N.base = BASE_ARENA;
         }
 
@@ -1740,6 +1761,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     }
 
     P.arena_bytes = std::max<size_t>(arena.peak, 256);
+    P.buffers = std::move(arena.log);
+    P.parent.assign(parent.begin(), parent.end());
     P.host_args = std::move(blob.bytes);
     P.patches = std::move(blob.patches);
     P.max_intermediate = max_inter;

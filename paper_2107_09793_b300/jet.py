@@ -22,7 +22,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
            "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices",
-           "jet_network_keep_shared", "jet_network_save_shared", "jet_network_load_shared"]
+           "jet_network_keep_shared", "jet_network_save_shared", "jet_network_load_shared", "jet_plan_buffers"]
 
 
 class JetError(RuntimeError):
@@ -46,6 +46,12 @@ class OpRecord(ctypes.Structure):
 
 OP_KINDS = {0: "direct", 1: "permute", 2: "gemm_simt", 3: "gemm_tc", 4: "slice_reduce", 5: "splitk_reduce",
             6: "tc_split", 7: "small_batch", 8: "accum", 9: "memset", 10: "apply", 11: "accum_batch"}
+
+
+class BufferRecord(ctypes.Structure):
+    _fields_ = [("node", ctypes.c_int32), ("t_alloc", ctypes.c_int32), ("t_release", ctypes.c_int32),
+                ("first_use", ctypes.c_int32), ("last_use", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("offset", ctypes.c_int64), ("bytes", ctypes.c_int64)]
 
 
 class TensorDesc(ctypes.Structure):
@@ -100,6 +106,7 @@ def lib():
             "jet_contract_grad": (I32, [P, I32, P, P, I32, P, P, P, P]),
             "jet_stats": (I32, [P, P]),
             "jet_profile": (I32, [P, P, I32, P]),
+            "jet_plan_buffers": (I32, [P, P, I32, P]),
             "jet_pair_contract_noalloc": (I32, [I32, P, P, P, I32, P, P, P, P, I32, P]),
             "jet_network_destroy": (None, [P]),
             "jet_last_error": (ctypes.c_char_p, []),
@@ -332,6 +339,16 @@ class Network:
                  "variant": r.variant}
                 for r in recs[:n.value]]
 
+    def plan_buffers(self) -> List[Dict[str, int]]:
+        """jet_plan_buffers: the workspace allocations of the last plan with their
+        launch-time windows (the intermediate-deletion record)."""
+        n = ctypes.c_int32()
+        _check(lib().jet_plan_buffers(self._h, None, 0, ctypes.byref(n)))
+        recs = (BufferRecord * max(n.value, 1))()
+        _check(lib().jet_plan_buffers(self._h, recs, n.value, ctypes.byref(n)))
+        return [{name: getattr(r, name) for name, _ in BufferRecord._fields_ if name != "pad_"}
+                for r in recs[:n.value]]
+
     def stats(self) -> Dict[str, float]:
         s = Stats()
         _check(lib().jet_stats(self._h, ctypes.byref(s)))
@@ -346,6 +363,8 @@ def pair_contract_noalloc(labels_a, shape_a, a_dev_ptr: int, labels_b, shape_b, 
     lb = np.ascontiguousarray(np.asarray(labels_b, dtype=np.int64))
     da = np.ascontiguousarray(np.asarray(shape_a, dtype=np.int32))
     db = np.ascontiguousarray(np.asarray(shape_b, dtype=np.int32))
+    if la.size != da.size or lb.size != db.size:
+        raise ValueError("each operand needs one dim per label")
     _check(lib().jet_pair_contract_noalloc(la.size, la.ctypes.data, da.ctypes.data, ctypes.c_void_p(a_dev_ptr),
                                            lb.size, lb.ctypes.data, db.ctypes.data, ctypes.c_void_p(b_dev_ptr),
                                            ctypes.c_void_p(c_dev_ptr), int(device), ctypes.c_void_p(stream)))

@@ -25,7 +25,14 @@ path receives it, then upcast to complex128.
      elements), and the O2 partials (Eq. sliced_sum) of 8 seeded slice ids.  The
      GPU test contracts the same network along the stored order and slicing.
 
-Usage: python tests/golden/make_golden.py grid30 gbs16 grid53
+  grid53_bench.json : the same circuit and bitstring along the order and the 12
+     sliced labels the benchmark contracts (tests/golden/grid53_plan.json, read
+     as data: Section 2.3 makes the value independent of the order, and the
+     sliced labels only say which partial sums s_i of Eq. sliced_sum exist), the
+     O2 partials of 8 seeded slice ids, each slice contracted pairwise along that
+     order by the oracle's tensordot step.
+
+Usage: python tests/golden/make_golden.py grid30 gbs16 grid53 grid53_bench
 """
 import json
 import os
@@ -157,7 +164,72 @@ def grid53():
     print(json.dumps(rec["seconds"]))
 
 
+def grid53_bench():
+    from oracle.einsum import slice_network, contract_network
+    from circuits import SplitMix64
+    w = configs.build("grid53")
+    tn = w.network.as_complex64()
+    plan = json.load(open(os.path.join(HERE, "grid53_plan.json")))
+    path = [tuple(p) for p in plan["path"]]
+    sliced = plan["sliced_labels"]
+    n = len(sliced)
+    # Case selection (no expected value comes from it): with the bras' digits
+    # and a slice's digits fixed, a tensor whose remaining sub-tensor is all
+    # zero makes that slice's partial exactly zero (here: fSim's zero entries
+    # between states of different Hamming weight, next to the bras).  Half of
+    # the 4096 slices are such.  Take 8 seeded slices that no tensor zeroes and
+    # 2 that one does (their partial must come out exactly zero).
+    fixed0 = dict(zip(tn.open_labels, map(int, w.outputs[0])))
+    touch = [ti for ti, l in enumerate(tn.labels) if any(x in fixed0 or x in sliced for x in l)]
+
+    def zeroed(sid):
+        fx = dict(fixed0)
+        fx.update(zip(sliced, [(sid >> (n - 1 - j)) & 1 for j in range(n)]))
+        for ti in touch:
+            idx = tuple(fx[x] if x in fx else slice(None) for x in tn.labels[ti])
+            if not np.any(np.asarray(tn.data[ti])[idx]):
+                return True
+        return False
+    rng = SplitMix64(5353)
+    ids, n_zero = [], 0
+    while len(ids) < 10:
+        i = int(rng.next_u64() % (1 << n))
+        if i in ids:
+            continue
+        z = zeroed(i)
+        if z and n_zero < 2:
+            ids.append(i)
+            n_zero += 1
+        elif not z and len(ids) - n_zero < 8:
+            ids.append(i)
+    ids.sort()
+    zero_ids = [i for i in ids if zeroed(i)]
+    parts, secs = [], []
+    for i in ids:
+        digits = [(i >> (n - 1 - j)) & 1 for j in range(n)]
+        t0 = time.time()
+        # the bra <x| on each open leg fixes that leg to its digit (Section 2.2.1),
+        # exactly like a sliced label (Section 2.4)
+        sl, sd = slice_network(tn.labels, tn.data, list(tn.open_labels) + sliced, list(w.outputs[0]) + digits)
+        _, t = contract_network(sl, sd, path)
+        parts.append(complex(t))
+        secs.append(time.time() - t0)
+        print(f"slice {i}: {parts[-1]} ({secs[-1]:.1f} s)", flush=True)
+    rec = {
+        "workload": "grid53", "source": "oracle O2 (pairwise numpy.tensordot) along the benchmark's order and "
+                                        "sliced labels (tests/golden/grid53_plan.json, read as data)",
+        "outputs": w.outputs.tolist(), "sliced_labels": [int(x) for x in sliced],
+        "slice_ids": ids, "slice_digits": [[(i >> (n - 1 - j)) & 1 for j in range(n)] for i in ids],
+        "structurally_zero_ids": zero_ids,
+        "slice_partials": [[p.real, p.imag] for p in parts],
+        "seconds": {"slices": round(sum(secs), 1)},
+    }
+    with open(os.path.join(HERE, "grid53_bench.json"), "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(json.dumps(rec["seconds"]))
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["grid30"]
     for name in which:
-        {"grid30": grid30, "gbs16": gbs16, "grid53": grid53}[name]()
+        {"grid30": grid30, "gbs16": gbs16, "grid53": grid53, "grid53_bench": grid53_bench}[name]()

@@ -1,10 +1,28 @@
-"""The 53-qubit 9x6-minus-corner grid circuit (12 cycles) at full size: slices
-of the workload amplitude contracted on the GPU along the oracle's own
-contraction order and sliced labels (largest intermediate <= 2^28 elements,
-2^17 slices), against the FP64 pairwise contraction of the same 8 seeded
-slices stored in tests/golden/grid53.json (written by
-tests/golden/make_golden.py).  The 2^17-slice sum itself is far too long to run
-here; the benchmark reports the per-slice time and the measured fraction."""
+"""The 53-qubit 9x6-minus-corner grid circuit (12 cycles) at full size: slice
+partials s_i (Section 2.4, Eq. sliced_sum) of the workload amplitude on the GPU
+against the FP64 oracle's pairwise contraction of the same slices, each
+partial checked against its own magnitude.
+
+Two stored sets (tests/golden/, written by make_golden.py, which calls only the
+oracle):
+  * grid53_bench.json: along the order and the 12 sliced labels the benchmark
+    contracts (tests/golden/grid53_plan.json), 8 seeded slices that no tensor
+    zeroes and 2 that one does (with the bras' digits and the slice's digits
+    fixed, an fSim gate next to the bras keeps an all-zero sub-tensor: the
+    partial is exactly zero);
+  * grid53.json: along the oracle's own order and its own 17 sliced labels,
+    8 seeded slices (3 exactly zero, 4 below 1e-25 from fSim(pi/2)'s cos entry
+    of 6e-17, one of typical size).
+
+Tolerances per mode, from the arithmetic (u = unit roundoff of the operand
+representation, complex64 intermediates accumulated in FP32):
+  fp32, tf32x3, fp16x3, bf16x6: 1e-5 (u <= 2^-22 per operand; the measured
+      error is set by FP32 accumulation over the path, ~1e-6 per slice);
+  bf16x3: 5e-4 (hi + lo in BF16 keeps 16 significant bits, u = 2^-17 = 7.6e-6
+      per operand entry, over a few hundred dependent contraction steps);
+  tf32: 5e-2 (one TF32 product, u = 2^-11 = 4.9e-4 per operand entry, the same
+      steps); it fails the 1e-5 bar on purpose and is reported for comparison;
+  fp64: 1e-12 (complex128 everywhere, FP64 on CUDA cores)."""
 import json
 import os
 
@@ -16,29 +34,66 @@ from paper_2107_09793_b300 import jet
 
 pytestmark = pytest.mark.gpu
 
-GOLDEN_PATH = os.path.join(os.path.dirname(__file__), "golden", "grid53.json")
+HERE = os.path.join(os.path.dirname(__file__), "golden")
+TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "bf16x6": 1e-5, "bf16x3": 5e-4, "tf32": 5e-2, "fp64": 1e-12}
+
+
+def _load(name):
+    p = os.path.join(HERE, name)
+    if not os.path.exists(p):
+        pytest.fail(f"tests/golden/{name} missing: run tests/golden/make_golden.py")
+    return json.load(open(p))
 
 
 @pytest.fixture(scope="module")
-def golden():
-    if not os.path.exists(GOLDEN_PATH):
-        pytest.fail("tests/golden/grid53.json missing: run tests/golden/make_golden.py grid53")
-    return json.load(open(GOLDEN_PATH))
+def workload():
+    return configs.build("grid53")
 
 
-# Normwise over the 8 partials (they span many orders of magnitude; the norm
-# is set by the largest).  FP32 and the 3-way-accurate splits: 1e-5.
-@pytest.mark.parametrize("prec,tol", [("fp16x3", 1e-5), ("fp32", 1e-5)])
-def test_grid53_slice_partials_vs_pairwise_oracle(golden, prec, tol):
-    w = configs.build("grid53")
-    net = jet.from_network(w.network, precision=prec)
-    net.path_set([tuple(p) for p in golden["path"]])
-    net.slice(golden["sliced_labels"])
-    st = net.stats()
-    assert st["max_intermediate"] <= 1 << 28
-    got = net.contract_slices(np.array(golden["outputs"], np.int32), golden["slice_ids"])[0]
-    ref = np.array([complex(a, b) for a, b in golden["slice_partials"]])
-    err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-    print(f"grid53 {prec}: normwise rel err over {len(ref)} slices {err:.3e}")
-    assert err <= tol
+def _check_partials(got, ref, zero_ids, ids, tol, prec):
+    """Each partial against its own magnitude; a structurally zero partial must
+    come out exactly zero."""
+    big = np.max(np.abs(ref))
+    worst = 0.0
+    for j, (g, r, i) in enumerate(zip(got, ref, ids)):
+        if i in zero_ids:
+            assert r == 0 and g == 0, (prec, i, g, r)
+        elif abs(r) >= 1e-3 * big:
+            e = abs(g - r) / abs(r)
+            worst = max(worst, e)
+            assert e <= tol, (prec, i, e)
+        else:   # partials far below the amplitude's scale: at that scale
+            assert abs(g - r) <= tol * big, (prec, i, g, r)
+    return worst
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp32", "bf16x3", "tf32", "fp16x3", "bf16x6", "fp64"])
+def test_grid53_benchmark_plan_slice_partials(workload, prec):
+    plan = _load("grid53_plan.json")
+    g = _load("grid53_bench.json")
+    assert g["sliced_labels"] == plan["sliced_labels"]
+    net = jet.from_network(workload.network, precision=prec)
+    net.path_set([tuple(p) for p in plan["path"]])
+    net.slice(plan["sliced_labels"])
+    assert net.stats()["max_intermediate"] <= 1 << 28
+    got = net.contract_slices(np.array(g["outputs"], np.int32), g["slice_ids"])[0]
+    ref = np.array([complex(a, b) for a, b in g["slice_partials"]])
+    worst = _check_partials(got, ref, set(g["structurally_zero_ids"]), g["slice_ids"], TOL[prec], prec)
+    print(f"grid53 benchmark plan {prec}: worst per-slice rel err {worst:.3e} over "
+          f"{len(ref) - len(g['structurally_zero_ids'])} slices")
+    net.close()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp32", "fp16x3"])
+def test_grid53_oracle_plan_slice_partials(workload, prec):
+    g = _load("grid53.json")
+    net = jet.from_network(workload.network, precision=prec)
+    net.path_set([tuple(p) for p in g["path"]])
+    net.slice(g["sliced_labels"])
+    assert net.stats()["max_intermediate"] <= 1 << 28
+    got = net.contract_slices(np.array(g["outputs"], np.int32), g["slice_ids"])[0]
+    ref = np.array([complex(a, b) for a, b in g["slice_partials"]])
+    zero = {i for i, r in zip(g["slice_ids"], ref) if r == 0}
+    worst = _check_partials(got, ref, zero, g["slice_ids"], TOL[prec], prec)
+    print(f"grid53 oracle plan {prec}: worst per-slice rel err {worst:.3e}")
     net.close()

@@ -365,3 +365,71 @@ def test_path_reconfigure_for_slicing():
         fresh.path_reconfigure(2)             # no path yet
     net.close()
     fresh.close()
+
+
+def _check_liveness(net):
+    """Intermediate deletion (Section 4): a node's buffer is released only after
+    every launch that reads it was issued, and no two allocations whose launch
+    windows meet share a byte of the workspace."""
+    bufs = net.plan_buffers()
+    ws = net.stats()["workspace_bytes"]
+    assert bufs
+    for b in bufs:
+        assert 0 <= b["offset"] and b["offset"] + b["bytes"] <= ws, b
+        assert b["t_release"] < 0 or b["t_alloc"] <= b["t_release"], b
+        if b["node"] >= 0:
+            assert b["first_use"] >= b["t_alloc"], b           # allocated before its node writes it
+            assert b["t_release"] < 0 or b["last_use"] < b["t_release"], b   # released after its last reader
+    INF = 1 << 40
+    ev = sorted(bufs, key=lambda b: b["t_alloc"])
+    live = []   # sweep over launch time: windows [t_alloc, t_release)
+    n_pairs = 0
+    for b in ev:
+        live = [x for x in live if (x["t_release"] if x["t_release"] >= 0 else INF) > b["t_alloc"]]
+        for x in live:
+            n_pairs += 1
+            assert x["offset"] + x["bytes"] <= b["offset"] or b["offset"] + b["bytes"] <= x["offset"], (x, b)
+        live.append(b)
+    return len(bufs), n_pairs
+
+
+@pytest.mark.parametrize("name,prec", [("grid12", "fp32"), ("grid30", "fp32"), ("grid30", "tf32x3"),
+                                       ("param20", "fp32"), ("gbs16", "fp32")])
+def test_arena_liveness_no_overlap_among_live_buffers(name, prec):
+    w = configs.build(name)
+    net = jet.from_network(w.network, precision=prec)
+    if len(w.outputs) > 1:
+        net.path_greedy_batch(w.outputs, seed=1, n_trials=2, max_elems=1 << 32)
+    else:
+        net.path_greedy(seed=1, n_trials=4)
+        net.slice_auto(1 << (8 if name == "grid12" else 24), min_n=2, max_n=24)
+    net.plan(w.outputs)
+    n, pairs = _check_liveness(net)
+    assert n >= 3 and pairs >= 1
+    net.close()
+
+
+def test_arena_liveness_catches_a_planted_overlap():
+    """The check itself: moving one live buffer onto another is caught."""
+    w = configs.build("grid12")
+    net = jet.from_network(w.network)
+    net.path_greedy(seed=1, n_trials=4)
+    net.plan(w.outputs)
+    bufs = net.plan_buffers()
+    orig = jet.Network.plan_buffers
+    # find two buffers with meeting windows and put the second on the first
+    for i, a in enumerate(bufs):
+        for b in bufs[i + 1:]:
+            ra = a["t_release"] if a["t_release"] >= 0 else 1 << 40
+            if b["t_alloc"] < ra:
+                bad = [dict(x) for x in bufs]
+                bad[bufs.index(b)]["offset"] = a["offset"]
+                try:
+                    jet.Network.plan_buffers = lambda self: bad
+                    with pytest.raises(AssertionError):
+                        _check_liveness(net)
+                finally:
+                    jet.Network.plan_buffers = orig
+                net.close()
+                return
+    pytest.fail("no two buffers live at once")
