@@ -1,14 +1,20 @@
 #!/usr/bin/env python
-"""Benchmark: sliced pairwise contraction of the 30-qubit 5x6 grid circuit
-(14 cycles, 6 sliced indices = 64 slices, largest intermediate <= 2^24 complex64)
-down to one amplitude, on one B300, through the library's C ABI.
+"""Benchmark: sliced pairwise contraction of the 53-qubit grid circuit (9x6
+minus one corner, 12 cycles, 12 sliced indices = 4096 slices, largest
+intermediate <= 2^28 complex64) down to one amplitude, on one B300, through the
+library's C ABI.
 
-A step = one full contraction (all slices, shared intermediates computed once,
-FP64 slice sum), replayed from the captured CUDA graph.  `value` is whole-job
-amplitudes/s with the inputs resident in HBM; `e2e` is the same metric through
+A step = the whole amplitude: every slice, run as the slice ranges that fit
+the device workspace (each range fixes a few sliced labels chosen to keep the
+shared work shared, its intermediates shared by its slices computed once, one
+CUDA graph per range), FP64 sum over the slices.  `value` is amplitudes/s with
+the inputs resident in HBM; `e2e` is the same metric through
 jet_tensors_upload + jet_contract with pinned host buffers (host<->device
-copies inside the timed region).  The FP32 CUDA-core path runs the same plan
-for comparison.  `--impl reference` times the FP64 CPU oracle instead.
+copies inside the timed region).  The other arithmetic modes (FP32 CUDA cores,
+TF32, the other splits) run the same plan for comparison, and every mode is
+checked against the oracle's partials of stored slices.  The 30-qubit grid
+(64 slices) and the other workloads follow as nested records.
+`--impl reference` times the FP64 CPU oracle instead.
 
 Multi-GPU (torchrun): every rank contracts its own seeded bitstring (weak
 scaling, no collective on the data path); time = max over ranks.
@@ -28,9 +34,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "contraction TFLOP/s & amplitudes/s, split-prec vs plain FP32 at ≤1e-5 rel err"
-WORKLOAD = ("grid30: 30-qubit 5x6 grid random circuit, 14 cycles, sqrt(X|Y|W) + fSim(pi/2,pi/6) ABCDCDAB, "
+WORKLOAD30 = ("grid30: 30-qubit 5x6 grid random circuit, 14 cycles, sqrt(X|Y|W) + fSim(pi/2,pi/6) ABCDCDAB, "
             "6 sliced indices (64 slices), largest intermediate <= 2^24 complex64, one amplitude")
 PATH_TRIALS, PATH_SEED, CAP, N_SLICED = 1024, 1, 1 << 24, 6
+WORKLOAD53 = ("grid53: 53-qubit 9x6 grid minus one corner random circuit, 12 cycles, sqrt(X|Y|W) + fSim(pi/2,pi/6) "
+              "ABCDCDAB, 12 sliced indices (4096 slices), largest intermediate <= 2^28 complex64, one amplitude")
+# planner settings of the stored grid53 order and slicing (tests/golden/grid53_plan.json)
+GRID53_PLAN = dict(seed=1, n_trials=512, cap=1 << 28, reconfigure_passes=8)
 
 # DRAM bytes (read + write) of the dominant launch, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on this workload with the kernel
@@ -286,69 +296,6 @@ def run_other_workloads(dev, peaks, peak_src):
                       "n_gate_tensors": len(ids), "flop_forward": st["flop_executed"], "precision": "fp32",
                       "timing": "host wall clock through the C ABI (host buffers), median of 3"}
 
-    # 53-qubit grid: library greedy + slicing to 2^28 + the slice-aware reconfiguration
-    # (Eq. task_based_amplitude_flops); the whole amplitude runs as consecutive
-    # slice-id ranges (each range's shared intermediates computed once), the largest
-    # range size whose workspace fits the free device memory, one workspace shared
-    # by the ranges' handles
-    w = configs.build("grid53")
-    net = jet.from_network(w.network, precision="fp16x3", device=dev)
-    t0 = time.perf_counter()
-    net.path_greedy(seed=1, n_trials=512)
-    sl = net.slice_auto(1 << 28, min_n=0, max_n=60)
-    f_before, f_after = net.path_reconfigure(8)
-    t_plan = time.perf_counter() - t0
-    st = net.stats()
-    n_sl = st["n_slices"]
-    path = net.path_get()
-    net.close()
-    per, amps_all, ranges_used = {}, {}, {}
-    for prec in ("fp16x3", "fp32"):
-        free = torch.cuda.mem_get_info()[0]
-        probe = jet.from_network(w.network, precision=prec, device=dev)
-        probe.path_set(path)
-        probe.slice(sl)
-        R = n_sl
-        while R > 1 and probe.plan_slices(w.outputs, list(range(R))) > 0.85 * free:
-            R //= 2
-        probe.close()
-        nets, nbytes, flop = [], [], 0.0
-        for k in range(n_sl // R):
-            nk = jet.from_network(w.network, precision=prec, device=dev)
-            nk.path_set(path)
-            nk.slice(sl)
-            nbytes.append(nk.plan_slices(w.outputs, list(range(k * R, (k + 1) * R))))
-            flop += nk.stats()["flop_executed"]
-            nets.append(nk)
-        ws = torch.empty(max(nbytes), dtype=torch.uint8, device="cuda")
-        for nk in nets:
-            nk.set_workspace(ws.data_ptr(), ws.numel())
-        run = lambda: [nk.contract_slices(w.outputs, list(range(k * R, (k + 1) * R))) for k, nk in enumerate(nets)]
-        run()   # first pass: uploads, graph capture
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        parts = run()
-        t_amp = time.perf_counter() - t0
-        amp = complex(sum(p[0].sum() for p in parts))   # slices in increasing id order, FP64
-        for nk in nets:
-            nk.close()
-        del ws
-        torch.cuda.empty_cache()
-        per[prec] = {"amplitude_s": t_amp, "tflops": flop / t_amp / 1e12, "flop": flop, "ranges": n_sl // R,
-                     "slices_per_range": R, "workspace_gb": max(nbytes) / 1e9}
-        amps_all[prec] = [amp.real, amp.imag]
-    res["grid53"] = {"workload": "53-qubit 9x6 grid minus one corner, 12 cycles, one amplitude (all slices)",
-                     "path": "library greedy, 512 trials, seed 1; slice finder to 2^28; slice-aware sub-tree "
-                             "reconfiguration (8 passes)",
-                     "sliced_labels": len(sl), "n_slices": n_sl, "max_intermediate": st["max_intermediate"],
-                     "flop_whole_amplitude_reuse": f_after, "flop_before_reconfiguration": f_before,
-                     "flop_per_slice_no_reuse": st["flop_sliced"] / n_sl, "planner_s": t_plan,
-                     "modes": per, "amplitude": amps_all,
-                     "fp16x3_vs_fp32": abs(complex(*amps_all["fp16x3"]) - complex(*amps_all["fp32"]))
-                     / abs(complex(*amps_all["fp32"])),
-                     "timing": "host wall clock of the whole amplitude (every slice range through "
-                               "jet_contract_slices, second pass)"}
-
     # open-leg batch: grid30 with its last 4 output legs left free, 16 amplitudes per
     # contraction of the benchmark bitstring's other 26 digits; path and slicing
     # planned with the free legs counted; checked at the stored amplitude's digits
@@ -414,27 +361,33 @@ def run_other_workloads(dev, peaks, peak_src):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, on the host's cores,
+    on the headline's workload; a step is one of its 4096 slices (a bounded
+    sample, scaled to amplitudes/s over all of them)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     from circuits import configs
-    w = configs.build("grid30")
-    n_sl = 64
-    steps = max(1, min(args.steps, 3))
+    w = configs.build("grid53")
+    path, sliced, plan_src = grid53_plan(w)
+    g, _ = grid53_golden()
+    cand = [i for i in (g["slice_ids"] if g else [0]) if not g or i not in set(g["structurally_zero_ids"])]
+    steps = max(1, min(args.steps, 2))
     warm = min(args.warmup, 1)
-    times = []
-    base = None
-    for i in range(warm + steps):   # a step: one of the 64 slices (oracle only, no library)
-        b, _ = oracle_slice_sample(w, None, n_sl, w.outputs, n_sample=1)
+    times, base = [], None
+    for i in range(warm + steps):   # a step: one slice (oracle only, no library)
+        b, _, dt = oracle_grid53_sample(w, path, sliced, cand[i % len(cand)])
         if i >= warm:
-            times.append(1.0 / b["value"] / n_sl)
+            times.append(dt)
         base = b
+    n_sl = 2 ** len(sliced)
     t = sum(times)
-    value = steps * (1.0 / n_sl) / t
+    value = steps / (n_sl * t)
     line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": steps,
             "warmup": warm, "ms_per_step": 1000 * t / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "one slice of the 64 (bounded sample)"},
+            "config": {"workload": WORKLOAD53, "step": f"one slice of the {n_sl} (bounded sample), along the "
+                                                       f"benchmark's order ({plan_src})"},
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
@@ -443,18 +396,15 @@ def run_reference(args):
     return 0
 
 
-def run_impl(args):
+def grid30_line(args, dev, peaks, peak_src):
+    """The 30-qubit grid amplitude (64 slices, one plan, one CUDA graph per
+    step): the headline of the smaller sliced workload, with its roofline,
+    modes, breakdown and e2e, as a nested record."""
     import torch
     from circuits import configs
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    dev = local if torch.cuda.is_available() else 0
-    torch.cuda.set_device(dev)
-    peaks, peak_src = load_peaks()
+    rank, world = 0, 1
     w = configs.build("grid30")
-    outs = rank_outputs(w.outputs, rank, w.circuit.n)
+    outs = np.asarray(w.outputs, np.int32)
 
     net, path, sliced = build_network(w, args.precision, profile=1, device=dev)
     from paper_2107_09793_b300 import jet
@@ -481,10 +431,6 @@ def run_impl(args):
         step()
         prof_step()
     torch.cuda.synchronize()
-    sampler = ClockSampler(dev)
-    sampler.start()
-    time.sleep(0.3)
-    barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.time()
     step_ms, prof_ms, gemm_ms = [], [], {}
@@ -507,14 +453,9 @@ def run_impl(args):
             if r["ms"] >= 0:
                 gemm_ms.setdefault(i, []).append(r["ms"])
     torch.cuda.synchronize()
-    barrier(world)
     t_wall1 = time.time()
-    time.sleep(0.25)
-    sampler.stop()
-    clocks = sampler.summary(t_wall0, t_wall1)
     amp = complex(amps_dev[0].item())
-    local_s = sum(step_ms) / 1000.0
-    total_s = max_over_ranks(local_s, world)
+    total_s = sum(step_ms) / 1000.0
     value = world * args.steps / total_s
     st = net.stats()
     recs = net.profile()
@@ -634,12 +575,10 @@ def run_impl(args):
         dt = time.perf_counter() - t0
         if i:
             e2e_s.append(dt)
-    e2e_total = max_over_ranks(sum(e2e_s), world)
+    e2e_total = sum(e2e_s)
     e2e = {"value": world * len(e2e_s) / e2e_total, "unit": "amplitudes/s", "h2d_bytes_per_step": int(nv * 8),
            "d2h_bytes_per_step": int(len(outs) * 16 + 4)}
 
-    if rank != 0:
-        return 0
     g_amp, g_out = golden_amplitude()
     err = None
     if g_amp is not None and list(g_out) == list(map(int, outs[0])):
@@ -647,18 +586,10 @@ def run_impl(args):
         for prec, m in modes.items():
             m["rel_err_vs_oracle"] = abs(complex(*m["amp"]) - g_amp) / abs(g_amp)
             err[prec] = m["rel_err_vs_oracle"]
-    cpu = None
-    if world == 1 and not args.skip_cpu:
-        cpu, _ = oracle_slice_sample(w, sliced, st["n_slices"], outs)
-    others = None
-    if world == 1 and not args.skip_others:
-        others = run_other_workloads(dev, peaks, peak_src)
-    kinds = {}
     line = {
-        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+        "value": value, "unit": "amplitudes/s", "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_slices": st["n_slices"], "sliced_labels": sliced,
+        "dtype": args.precision, "config": {"workload": WORKLOAD30, "n_slices": st["n_slices"], "sliced_labels": sliced,
                    "path": f"library greedy, {PATH_TRIALS} trials, seed {PATH_SEED}; slice finder",
                    "precision": args.precision, "l2": "flushed between timed steps (256 MiB write)",
                    "launch": "one CUDA graph per step"},
@@ -666,9 +597,340 @@ def run_impl(args):
         "flop_per_step": st["flop_executed"], "flop_no_reuse": st["flop_sliced"],
         "reuse_fraction": st["reuse_fraction"], "workspace_gb": st["workspace_bytes"] / 1e9,
         "amplitude": [amp.real, amp.imag], "rel_err_vs_oracle": err,
-        "fp32_simt": modes.get("fp32"), "modes": modes, "roofline": roof, "breakdown": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        # both loops of the timed region (the step, then the instrumented plan)
+        "fp32_simt": modes.get("fp32"), "modes": modes, "roofline": roof, "breakdown": breakdown, "e2e": e2e,
+        # both loops of its timed region (the step, then the instrumented plan)
         "gpu_launches": 2 * int(st["n_launches"]) * args.steps,
+        "wall_s_timed": t_wall1 - t_wall0,
+    }
+    for h in (net, run_net):
+        h.close()
+    return line
+
+
+def grid53_plan(w):
+    """The stored order and sliced labels of the 53-qubit amplitude (written by
+    tests/golden/make_plan.py with GRID53_PLAN; the parity tests contract the
+    same plan), else planned here the same way."""
+    try:
+        p = json.load(open(os.path.join(ROOT, "tests", "golden", "grid53_plan.json")))
+        return [tuple(x) for x in p["path"]], list(p["sliced_labels"]), "stored plan (tests/golden/grid53_plan.json)"
+    except (OSError, ValueError, KeyError):
+        from paper_2107_09793_b300 import jet
+        net = jet.from_network(w.network, precision="fp32")
+        net.path_greedy(seed=GRID53_PLAN["seed"], n_trials=GRID53_PLAN["n_trials"])
+        sl = net.slice_auto(GRID53_PLAN["cap"], min_n=0, max_n=60)
+        net.path_reconfigure(GRID53_PLAN["reconfigure_passes"])
+        path = net.path_get()
+        net.close()
+        return path, sl, "planned in this run"
+
+
+def grid53_golden():
+    """The oracle's partials of 10 stored slices (8 nonzero, 2 exactly zero)."""
+    try:
+        g = json.load(open(os.path.join(ROOT, "tests", "golden", "grid53_bench.json")))
+        return g, np.array([complex(a, b) for a, b in g["slice_partials"]])
+    except (OSError, ValueError, KeyError):
+        return None, None
+
+
+def partial_errors(got, ref, zero_ids, ids):
+    """Normwise and worst per-slice relative error over the nonzero partials;
+    whether the structurally zero ones came out exactly zero."""
+    nz = np.array([i not in zero_ids for i in ids])
+    return {"normwise": float(np.linalg.norm(got[nz] - ref[nz]) / np.linalg.norm(ref[nz])),
+            "worst_per_slice": float(np.max(np.abs(got[nz] - ref[nz]) / np.abs(ref[nz]))),
+            "zero_slices_exact": bool(np.all(got[~nz] == 0)), "slices": int(nz.sum())}
+
+
+def oracle_grid53_sample(w, path, sliced, slice_id):
+    """FP64 oracle (pairwise numpy.tensordot) on one slice of the 53-qubit
+    amplitude along the benchmark's order; scaled to amplitudes/s over all
+    4096 slices."""
+    import oracle
+    from oracle.einsum import slice_network, contract_network
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max((i.get("num_threads", 0) for i in threadpool_info()), default=0) or len(os.sched_getaffinity(0))
+    except Exception:
+        cores = len(os.sched_getaffinity(0))
+    tn = w.network.as_complex64()
+    n = len(sliced)
+    digits = [(slice_id >> (n - 1 - j)) & 1 for j in range(n)]
+    t0 = time.perf_counter()
+    sl, sd = slice_network(tn.labels, tn.data, list(tn.open_labels) + list(sliced), list(w.outputs[0]) + digits)
+    _, t = contract_network(sl, sd, path)
+    dt = time.perf_counter() - t0
+    n_sl = 2 ** n
+    return {"value": 1.0 / (n_sl * dt), "unit": "amplitudes/s", "cores": int(cores), "kind": "oracle",
+            "sample": f"slice {slice_id} of the {n_sl} slices of the grid53 amplitude (FP64 pairwise tensordot along "
+                      f"the benchmark's order), {dt:.1f} s, scaled by {n_sl}"}, complex(t), dt
+
+
+def roofline_of(recs, timed, prec, peaks, peak_src, step_ms):
+    """Roofline of the dominant kernel kind of one instrumented range: the
+    timed kind with the largest share; its launches' algorithmic FLOP and
+    bytes over their summed mean device time, against the bound that its
+    arithmetic intensity sets (tensor pipe for a tensor-core GEMM whose issued
+    FLOP take longer at peak than its bytes, else HBM)."""
+    by_kind = {}
+    for i in timed:
+        by_kind.setdefault(recs[i]["kind"], []).append(i)
+    if not by_kind:
+        return None
+    dom = max(by_kind, key=lambda k: sum(timed[i] for i in by_kind[k]))
+    ids = by_kind[dom]
+    ms = sum(timed[i] for i in ids)
+    flop = sum(recs[i]["flop"] for i in ids)
+    nbytes = sum(recs[i]["bytes"] for i in ids)
+    big = max(ids, key=lambda i: timed[i])
+    issue = {"bf16x3": 3, "tf32x3": 3, "bf16x6": 6, "fp16x3": 3, "tf32": 1}.get(prec, 1)
+    tf32 = prec.startswith("tf32")
+    tc_peak = peaks["bf16_tflops_sustained"] * (0.5 if tf32 else 1.0)
+    kname = {"gemm_tc": f"tc_gemm_kernel<{prec}>", "apply": "apply_kernel_c64 + apply_tc_c64",
+             "tc_split": f"tc_split_kernel<{prec}>", "direct": "direct_kernel / direct_splitk_kernel",
+             "gemm_simt": "gemm_simt_kernel"}.get(dom, dom)
+    t_tensor = flop * issue / (tc_peak * 1e12) if dom == "gemm_tc" else 0.0
+    t_hbm = nbytes / (peaks["hbm_gbs"] * 1e9)
+    common = {"kernel": kname, "launches_per_range": len(ids), "ms_per_range": ms, "share_of_range": ms / step_ms,
+              "flop_per_range": flop, "bytes_per_range": nbytes,
+              "longest_launch": {"node": recs[big]["node"], "ms": timed[big], "flop": recs[big]["flop"],
+                                 "bytes": recs[big]["bytes"]},
+              "traffic_note": "dram bytes per launch from the ncu summary under profiles/ (null when not captured "
+                              "for this kernel as it stands)"}
+    if t_tensor > t_hbm:
+        achieved = flop / (ms * 1e-3) / 1e12
+        peak = tc_peak / issue
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["flop"])),
+                "issued_tensor_tflops": achieved * issue, "tensor_peak_for_dtype": tc_peak,
+                "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)" if tf32 else "")
+                               + f" / {issue} ({issue} tensor products per real product): the algorithmic ceiling"}
+    else:
+        achieved = nbytes / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["bytes"])),
+                "peak_source": f"hbm_gbs of {peak_src}"}
+    roof.update(common)
+    roof["kinds_timed_ms_per_range"] = {k: sum(timed[i] for i in v) for k, v in by_kind.items()}
+    return roof
+
+
+def run_impl(args):
+    import torch
+    from circuits import configs
+    from paper_2107_09793_b300 import jet
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = local if torch.cuda.is_available() else 0
+    torch.cuda.set_device(dev)
+    peaks, peak_src = load_peaks()
+    w = configs.build("grid53")
+    outs = rank_outputs(w.outputs, rank, w.circuit.n, seed=3)
+    path, sliced, plan_src = grid53_plan(w)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    # one device workspace shared by every handle (they run one after the other
+    # on one stream): the slice ranges are chosen to fit it
+    free = torch.cuda.mem_get_info()[0]
+    ws = torch.empty(int(0.8 * free) // 256 * 256, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def handle(prec, profile=0):
+        h = jet.from_network(w.network, precision=prec, profile=profile, device=dev)
+        h.path_set(path)
+        h.slice(sliced)
+        h.set_workspace(ws.data_ptr(), ws.numel())
+        return h
+
+    amps_dev = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+    run_net = handle(args.precision)
+    t0 = time.perf_counter()
+    ranges = run_net.plan_ranges(outs, ws.numel())
+    t_ranges = time.perf_counter() - t0
+    prof_net = handle(args.precision, profile=1)
+
+    def step():
+        run_net.contract_async(outs, amps_dev.data_ptr(), sh)
+
+    def prof_step():
+        prof_net.contract_async(outs, amps_dev.data_ptr(), sh)
+
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        step()
+    prof_step()
+    torch.cuda.synchronize()
+    launches_per_range = len(run_net.profile())
+    sampler = ClockSampler(dev)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()                      # evict L2 between timed steps (256 MiB > 126 MB L2)
+        ev0.record(stream)
+        step()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    # per-kernel times: the instrumented handle (CUDA event pair around every heavy
+    # launch), in the same timed region; the library reports its last range, and
+    # every range has the same launches
+    n_prof = max(1, min(args.steps, 3))
+    kern_ms, prof_ms = {}, []
+    for _ in range(n_prof):
+        flush.zero_()
+        ev0.record(stream)
+        prof_step()
+        ev1.record(stream)
+        ev1.synchronize()
+        prof_ms.append(ev0.elapsed_time(ev1))
+        for i, r in enumerate(prof_net.profile()):
+            if r["ms"] >= 0:
+                kern_ms.setdefault(i, []).append(r["ms"])
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall1 = time.time()
+    time.sleep(0.25)
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    amp = complex(amps_dev[0].item())
+    total_s = max_over_ranks(sum(step_ms) / 1000.0, world)
+    value = world * args.steps / total_s
+    recs = prof_net.profile()
+    prof_net.close()
+    timed = {i: statistics.mean(v) for i, v in kern_ms.items()}
+    range_ms = statistics.mean(prof_ms) / ranges["n_ranges"]
+    roof = roofline_of(recs, timed, args.precision, peaks, peak_src, range_ms)
+
+    # where a range's time goes: one more step with every launch timed
+    breakdown = {}
+    nprof = handle(args.precision, profile=2)
+    aprof = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+    nprof.contract_async(outs, aprof.data_ptr(), sh)
+    torch.cuda.synchronize()
+    for r in nprof.profile():
+        if r["ms"] < 0:
+            continue
+        b = breakdown.setdefault(r["kind"], {"ms": 0.0, "launches": 0, "bytes": 0.0, "flop": 0.0})
+        b["ms"] += r["ms"]
+        b["launches"] += 1
+        b["bytes"] += r["bytes"]
+        b["flop"] += r["flop"]
+    tot_b = sum(b["ms"] for b in breakdown.values()) or 1.0
+    for b in breakdown.values():
+        b["share"] = b["ms"] / tot_b
+        b["gb_s"] = b["bytes"] / (b["ms"] * 1e-3) / 1e9 if b["ms"] > 0 else None
+        b["tflops"] = b["flop"] / (b["ms"] * 1e-3) / 1e12 if b["ms"] > 0 else None
+    nprof.close()
+
+    # accuracy: the oracle's partials of the stored slices, in every mode
+    g, gref = grid53_golden()
+    ids = g["slice_ids"] if g else []
+    zero_ids = set(g["structurally_zero_ids"]) if g else set()
+
+    def parity(prec):
+        if g is None or list(map(int, outs[0])) != list(map(int, g["outputs"][0])):
+            return None
+        h = handle(prec)
+        try:
+            got = h.contract_slices(outs, ids)[0]
+        finally:
+            h.close()
+        return partial_errors(got, gref, zero_ids, ids)
+
+    err_head = parity(args.precision)
+    # the same plan in the other arithmetic modes: FP32 CUDA cores (the plain
+    # reference path), TF32 and the other splits: time, amplitude, and errors
+    modes = {}
+    if not args.skip_fp32:
+        for prec in [m for m in ("fp32", "tf32", "bf16x3", "fp16x3", "bf16x6", "tf32x3") if m != args.precision]:
+            h = handle(prec)
+            am = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+            h.contract_async(outs, am.data_ptr(), sh)   # plans the ranges, captures the graphs
+            torch.cuda.synchronize()
+            msm = []
+            for _ in range(2):
+                flush.zero_()
+                ev0.record(stream)
+                h.contract_async(outs, am.data_ptr(), sh)
+                ev1.record(stream)
+                ev1.synchronize()
+                msm.append(ev0.elapsed_time(ev1))
+            h.close()
+            amp_m = complex(am[0].item())
+            modes[prec] = {"value": 1000.0 / statistics.mean(msm), "unit": "amplitudes/s",
+                           "ms_per_step": statistics.mean(msm),
+                           "tflops": ranges["flop"] / (statistics.mean(msm) * 1e-3) / 1e12,
+                           "amp": [amp_m.real, amp_m.imag], "err_vs_oracle_partials": parity(prec)}
+        if "fp32" in modes:
+            a32 = complex(*modes["fp32"]["amp"])
+            for prec, m in modes.items():
+                m["amp_rel_diff_vs_fp32"] = abs(complex(*m["amp"]) - a32) / abs(a32)
+
+    # end to end through the C ABI: pinned host inputs -> device, contract, amplitude back to host
+    nv = run_net.n_values()
+    host_vals = torch.empty(nv, dtype=torch.complex64, pin_memory=True)
+    host_vals.numpy()[:] = np.concatenate([np.asarray(t, np.complex64).ravel() for t in w.network.data])
+    e2e_s = []
+    for i in range(min(args.steps, 5) + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run_net.upload(host_vals.data_ptr(), sh)
+        run_net.contract(outs, stream=sh)
+        dt = time.perf_counter() - t0
+        if i:
+            e2e_s.append(dt)
+    e2e_total = max_over_ranks(sum(e2e_s), world)
+    e2e = {"value": world * len(e2e_s) / e2e_total, "unit": "amplitudes/s", "h2d_bytes_per_step": int(nv * 8),
+           "d2h_bytes_per_step": int(len(outs) * 16), "steps": len(e2e_s)}
+    run_net.close()
+    del ws, flush
+    torch.cuda.empty_cache()
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        sid = next((i for i in ids if i not in zero_ids), 0)
+        cpu, part, _ = oracle_grid53_sample(w, path, sliced, sid)
+    others = None
+    if world == 1 and not args.skip_others:
+        others = {"grid30": grid30_line(args, dev, peaks, peak_src)}
+        others.update(run_other_workloads(dev, peaks, peak_src))
+    line = {
+        "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": warm, "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD53, "n_slices": 2 ** len(sliced), "sliced_labels": sliced,
+                   "path": f"library greedy, {GRID53_PLAN['n_trials']} trials, seed {GRID53_PLAN['seed']}; slice "
+                           f"finder to 2^28; slice-aware sub-tree reconfiguration ({plan_src})",
+                   "precision": args.precision,
+                   "step": "the whole amplitude: every slice, in slice ranges that fit the workspace (each range "
+                           "one CUDA graph), FP64 sum over the slices",
+                   "ranges": ranges["n_ranges"], "range_fixed_labels": ranges["fixed_labels"],
+                   "workspace_gb_per_range": ranges["bytes"] / 1e9, "range_planning_s": t_ranges,
+                   "l2": "flushed between timed steps (256 MiB write); intermediates up to 2 GiB exceed L2"},
+        "tflops": ranges["flop"] / (total_s / args.steps) / 1e12 * world,
+        "flop_per_step": ranges["flop"],
+        "amplitude": [amp.real, amp.imag],
+        "rel_err_vs_oracle": {"headline": err_head,
+                              "note": "per stored slice (8 nonzero partials of the 4096, 2 exactly zero): the whole "
+                                      "amplitude has no oracle value (4096 FP64 slices of ~45 s each)"},
+        "fp32_simt": modes.get("fp32"), "modes": modes, "roofline": roof,
+        "breakdown_per_range": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        # both loops of the timed region (the steps, then the instrumented steps)
+        "gpu_launches": (args.steps + n_prof) * ranges["n_ranges"] * launches_per_range,
         "other_workloads": others,
         "wall_s_timed": t_wall1 - t_wall0,
     }

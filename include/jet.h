@@ -85,14 +85,14 @@ typedef struct {
     int64_t workspace_limit;  /* bytes of device workspace a contraction may use; 0 = no
                                  limit.  When the plan for every slice needs more,
                                  jet_contract / jet_contract_async run the slices in
-                                 consecutive id ranges (the largest power-of-two
-                                 fraction of the slices whose plan fits), each range's
-                                 shared intermediates computed once, and sum the
-                                 per-slice partials in increasing slice id in FP64 (the
-                                 order of one plan; a range's plan may route a node with
-                                 fewer instances to another kernel form, so the values
-                                 agree to the arithmetic's rounding).  A caller-provided
-                                 workspace smaller than the plan caps it the same way. */
+                                 ranges chosen to share work (see jet_plan_ranges),
+                                 each range's shared intermediates computed once, and
+                                 sum the per-slice partials in increasing slice id in
+                                 FP64 (the order of one plan; a range's plan may route a
+                                 node with fewer instances to another kernel form, so
+                                 the values agree to the arithmetic's rounding).  A
+                                 caller-provided workspace smaller than the plan caps
+                                 it the same way. */
     int32_t profile;          /* 0 (default): off; 1: CUDA events around every GEMM, operand
                                  split and small-operand launch; 2: around every launch
                                  (read with jet_profile)                                  */
@@ -351,6 +351,30 @@ int jet_plan(jet_network *net, int32_t n_amps, const int32_t *outputs, size_t *b
 int jet_plan_slices(jet_network *net, int32_t n_amps, const int32_t *outputs, int32_t n_ids,
                     const int64_t *slice_ids, size_t *bytes_out);
 int jet_set_workspace(jet_network *net, void *dptr, size_t bytes);
+
+/* Slice ranges for a workspace cap (Section 4: when the shared work of every
+ * slice does not fit, a subset of the slices is held in memory at a time, its
+ * size determined a priori).  A range fixes the digits of a set of the sliced
+ * labels and holds every slice with those digits, so an intermediate with one
+ * of those labels under it is still computed once in all, and one without is
+ * computed again in each range.  The library takes, among the sets of the
+ * fewest labels whose range plan fits max_bytes, the one that minimises the
+ * FLOP of all ranges together.  jet_contract / jet_contract_async use the same
+ * choice whenever the plan of every slice exceeds their cap
+ * (jet_options.workspace_limit, a smaller caller workspace, or, with neither,
+ * 90% of the free device memory): they run the ranges one after the other,
+ * each range's plan kept (and replayed as its CUDA graph) for later calls with
+ * the same outputs, and sum the per-slice partials in increasing slice id in
+ * FP64.  This call plans (host only) and reports: the number of labels a range
+ * fixes and those labels (fixed_labels_out: room for every sliced label, may
+ * be NULL), the number of ranges, the FLOP of all ranges together and the
+ * workspace bytes of one range; a plan that fits max_bytes reports 0 labels, 1
+ * range and its own FLOP and size.  Any output pointer may be NULL.
+ * Errors: as jet_plan, JET_EINVAL (max_bytes 0), JET_ENOMEM (one slice does
+ * not fit). */
+int jet_plan_ranges(jet_network *net, int32_t n_amps, const int32_t *outputs, size_t max_bytes,
+                    int32_t *n_fixed_out, int64_t *fixed_labels_out, int64_t *n_ranges_out, double *flop_out,
+                    size_t *bytes_out);
 
 /* Adjoint (environment) contraction; not in the paper.
  * env_G = sum_b cot_b * d amp_b / d G for each requested input tensor G

@@ -5,6 +5,7 @@
 #include <array>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <exception>
 #include <new>
 #include <numeric>
@@ -43,6 +44,17 @@ static int guarded(F &&f)
     }
 }
 
+static void drop_ranges(Network &net)
+{
+    if (!net.ranges) return;
+    for (auto &p : net.ranges->plans)
+        if (p) {
+            if (net.last_run == p.get()) net.last_run = nullptr;
+            release_plan_device(*p);
+        }
+    net.ranges.reset();
+}
+
 static void invalidate_plan(Network &net)
 {
     if (net.plan) {
@@ -50,6 +62,7 @@ static void invalidate_plan(Network &net)
         release_plan_device(*net.plan);
         net.plan.reset();
     }
+    drop_ranges(net);
 }
 
 // New cotangents into a cached adjoint plan: seed(root instance i) = sum of
@@ -558,6 +571,36 @@ int jet_plan_slices(jet_network *net, int32_t n_amps, const int32_t *outputs, in
     });
 }
 
+static RangeSet &get_ranges(Network &net, int32_t n_amps, const int32_t *outputs, size_t cap);
+
+int jet_plan_ranges(jet_network *net, int32_t n_amps, const int32_t *outputs, size_t max_bytes,
+                    int32_t *n_fixed_out, int64_t *fixed_labels_out, int64_t *n_ranges_out, double *flop_out,
+                    size_t *bytes_out)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (max_bytes == 0) fail(JET_EINVAL, "max_bytes must be > 0");
+        Plan &P = get_plan(*net, n_amps, outputs);
+        int32_t nf = 0;
+        int64_t nr = 1;
+        double flop = P.flop_executed;
+        size_t bytes = P.arena_bytes;
+        if (P.arena_bytes > max_bytes) {
+            if (P.n_slices <= 1) fail(JET_ENOMEM, "the plan needs more workspace than max_bytes and has no slices");
+            RangeSet &RS = get_ranges(*net, n_amps, outputs, max_bytes);
+            nf = (int32_t)RS.fixed_pos.size();
+            for (int32_t j = 0; j < nf && fixed_labels_out; ++j) fixed_labels_out[j] = net->sliced[RS.fixed_pos[j]];
+            nr = (int64_t)RS.ids.size();
+            flop = RS.flop;
+            bytes = RS.arena;
+        }
+        if (n_fixed_out) *n_fixed_out = nf;
+        if (n_ranges_out) *n_ranges_out = nr;
+        if (flop_out) *flop_out = flop;
+        if (bytes_out) *bytes_out = bytes;
+    });
+}
+
 int jet_set_workspace(jet_network *net, void *dptr, size_t bytes)
 {
     return guarded([&] {
@@ -577,34 +620,163 @@ static size_t workspace_cap(const Network &net)
     return cap;
 }
 
+// The cap a contraction runs under: workspace_cap, or, with no limit set and
+// no caller workspace, 90% of the device memory that is free (plus the
+// library's own arena, which a larger one replaces) once the plan would need
+// more than that.
+static size_t run_cap(Network &net, const Plan &P)
+{
+    size_t cap = workspace_cap(net);
+    if (cap) return cap;
+    if (P.n_slices <= 1 || P.arena_bytes <= net.own_arena_bytes) return 0;
+    const size_t avail = (size_t)(0.9 * (double)device_free_bytes(net)) + net.own_arena_bytes;
+    return P.arena_bytes > avail ? avail : 0;
+}
+
 // Section 4: when every slice's shared work does not fit at once, a subset of
-// the slices is held in memory at a time, its size determined a priori: the
-// slices run as consecutive id ranges (the largest power-of-two fraction of
-// the slice count whose plan fits the cap), each range's shared intermediates
-// computed once, and the per-slice partials are summed in increasing slice id
-// in FP64 -- the order of the single plan's reduction (a range's plan may route
-// a node with fewer instances to another kernel form).  Writes n_amps * n_elem
-// sums to `sums` (host).
+// the slices is held in memory at a time, its size determined a priori.  A
+// range fixes the digits of a set T of the sliced labels and holds every slice
+// with those digits; an intermediate with a label of T under it is computed
+// once in all (its instances split over the ranges), one without is computed
+// again in every range.  Among the sets of the fewest labels whose range plan
+// fits the cap, T minimises the FLOP of all ranges together (all subsets when
+// there are at most 300 of that size, else the best smaller set extended by one
+// label).  Every range has the same plan up to the fixed digits' values, so
+// range 0's plan gives the size and the FLOP.
+static RangeSet &get_ranges(Network &net, int32_t n_amps, const int32_t *outputs, size_t cap)
+{
+    const size_t n = (size_t)n_amps * net.open.size();
+    RangeSet *R = net.ranges.get();
+    if (R && R->n_amps == n_amps && R->path_version == net.path_version && R->slice_version == net.slice_version &&
+        R->precision == net.opt.precision && R->reuse == net.opt.reuse && R->cap == cap && R->outputs.size() == n &&
+        std::equal(R->outputs.begin(), R->outputs.end(), outputs))
+        return *R;
+    drop_ranges(net);
+    const int ns = (int)net.sliced.size();
+    std::vector<int64_t> dim(ns), w(ns, 1);
+    for (int j = 0; j < ns; ++j) dim[j] = net.labels.at(net.sliced[j]).dim;
+    for (int j = ns - 2; j >= 0; --j) w[j] = w[j + 1] * dim[j + 1];
+    const int64_t n_sl = ns ? w[0] * dim[0] : 1;
+    // slice ids of range `key` (mixed radix over T's digits, T's first label slowest)
+    auto range_ids = [&](const std::vector<int32_t> &T, int64_t key) {
+        std::vector<int64_t> want(T.size());
+        for (int i = (int)T.size() - 1; i >= 0; --i) {
+            want[i] = key % dim[T[i]];
+            key /= dim[T[i]];
+        }
+        std::vector<int64_t> ids;
+        for (int64_t s = 0; s < n_sl; ++s) {
+            bool ok = true;
+            for (size_t i = 0; i < T.size() && ok; ++i) ok = (s / w[T[i]]) % dim[T[i]] == want[i];
+            if (ok) ids.push_back(s);
+        }
+        return ids;
+    };
+    struct Cand {
+        std::vector<int32_t> T;
+        double flop;
+        size_t arena;
+    };
+    auto evaluate = [&](const std::vector<int32_t> &T) -> Cand {
+        int64_t n_ranges = 1;
+        for (int32_t j : T) n_ranges *= dim[j];
+        auto ids = range_ids(T, 0);
+        auto P = build_plan(net, n_amps, outputs, &ids);
+        return {T, P->flop_executed * (double)n_ranges, P->arena_bytes};
+    };
+    auto binom = [](int nn, int k) {
+        double c = 1;
+        for (int i = 0; i < k; ++i) c = c * (nn - i) / (i + 1);
+        return c;
+    };
+    Cand best{{}, 0, 0};
+    bool found = false;
+    std::vector<int32_t> prev_best;   // best set of the previous size, fitting or not
+    for (int nt = 1; nt <= ns && !found; ++nt) {
+        std::vector<std::vector<int32_t>> cands;
+        if (binom(ns, nt) <= 300) {
+            std::vector<int32_t> c(nt);
+            std::function<void(int, int)> rec = [&](int at, int from) {
+                if (at == nt) {
+                    cands.push_back(c);
+                    return;
+                }
+                for (int j = from; j < ns; ++j) {
+                    c[at] = j;
+                    rec(at + 1, j + 1);
+                }
+            };
+            rec(0, 0);
+        } else {
+            for (int j = 0; j < ns; ++j)
+                if (std::find(prev_best.begin(), prev_best.end(), j) == prev_best.end()) {
+                    auto c = prev_best;
+                    c.push_back(j);
+                    std::sort(c.begin(), c.end());
+                    cands.push_back(c);
+                }
+        }
+        Cand size_best{{}, 0, 0};
+        bool any = false;
+        for (auto &T : cands) {
+            Cand c = evaluate(T);
+            if (!any || c.flop < size_best.flop) {
+                size_best = c;
+                any = true;
+            }
+            if (c.arena <= cap && (!found || c.flop < best.flop || (c.flop == best.flop && c.arena < best.arena))) {
+                best = c;
+                found = true;
+            }
+        }
+        prev_best = size_best.T;
+    }
+    if (!found) fail(JET_ENOMEM, "one slice needs more workspace than the limit");
+    auto RS = std::make_unique<RangeSet>();
+    RS->outputs.assign(outputs, outputs + n);
+    RS->n_amps = n_amps;
+    RS->path_version = net.path_version;
+    RS->slice_version = net.slice_version;
+    RS->precision = net.opt.precision;
+    RS->reuse = net.opt.reuse;
+    RS->cap = cap;
+    RS->fixed_pos = best.T;
+    RS->flop = best.flop;
+    RS->arena = best.arena;
+    int64_t n_ranges = 1;
+    for (int32_t j : best.T) n_ranges *= dim[j];
+    for (int64_t k = 0; k < n_ranges; ++k) RS->ids.push_back(range_ids(best.T, k));
+    RS->plans.resize((size_t)n_ranges);
+    net.ranges = std::move(RS);
+    return *net.ranges;
+}
+
+// Runs every range (its plan kept across calls, except while shared work is
+// being kept: a range after the first reads what the first kept) and sums the
+// per-slice partials in increasing slice id in FP64 -- the order of the single
+// plan's reduction (a range's plan may route a node with fewer instances to
+// another kernel form, so the values agree to the arithmetic's rounding).
+// Writes n_amps * n_elem sums to `sums` (host).
 static void contract_in_ranges(Network &net, int32_t n_amps, const int32_t *outputs, size_t cap, void *stream,
                                std::vector<jet_c128> &sums)
 {
     const int64_t n_sl = net.plan->n_slices, n_elem = net.plan->n_elem;
-    int64_t R = n_sl;
-    for (;;) {
-        R = (R + 1) / 2;
-        std::vector<int64_t> ids(R);
-        std::iota(ids.begin(), ids.end(), 0);
-        if (get_plan(net, n_amps, outputs, &ids).arena_bytes <= cap) break;
-        if (R == 1) fail(JET_ENOMEM, "one slice needs more workspace than the limit");
-    }
-    sums.assign((size_t)n_amps * n_elem, jet_c128{0.0, 0.0});
-    std::vector<jet_c128> part;
+    RangeSet &RS = get_ranges(net, n_amps, outputs, cap);
+    ensure_workspace(net, RS.arena, stream);
+    std::vector<jet_c128> all((size_t)n_amps * n_sl * n_elem, jet_c128{0.0, 0.0}), part;
     void *s = stream ? stream : net.stream;
-    for (int64_t s0 = 0; s0 < n_sl; s0 += R) {
-        const int64_t n_ids = std::min(R, n_sl - s0);
-        std::vector<int64_t> ids(n_ids);
-        std::iota(ids.begin(), ids.end(), s0);
-        Plan &P = get_plan(net, n_amps, outputs, &ids);
+    for (size_t r = 0; r < RS.plans.size(); ++r) {
+        const std::vector<int64_t> &ids = RS.ids[r];
+        const int64_t n_ids = (int64_t)ids.size();
+        if (net.keep_min > 0) check_kept_key(net);
+        if (!RS.plans[r] || RS.plans[r]->superseded || net.keep_min > 0) {
+            if (RS.plans[r]) {
+                if (net.last_run == RS.plans[r].get()) net.last_run = nullptr;
+                release_plan_device(*RS.plans[r]);
+            }
+            RS.plans[r] = build_plan(net, n_amps, outputs, &ids);
+        }
+        Plan &P = *RS.plans[r];
         bind_and_run(net, P, nullptr, stream);
         part.resize((size_t)n_amps * n_ids * n_elem);
         copy_d2h(part.data(), net.d_amps, part.size() * sizeof(jet_c128), s);
@@ -613,13 +785,18 @@ static void contract_in_ranges(Network &net, int32_t n_amps, const int32_t *outp
         mark_kept(net, P, stream);
         for (int32_t b = 0; b < n_amps; ++b)
             for (int64_t j = 0; j < n_ids; ++j)
-                for (int64_t e = 0; e < n_elem; ++e) {
-                    const jet_c128 &v = part[((size_t)b * n_ids + j) * n_elem + e];
-                    jet_c128 &acc = sums[(size_t)b * n_elem + e];
-                    acc.re += v.re;
-                    acc.im += v.im;
-                }
+                std::memcpy(&all[((size_t)b * n_sl + ids[j]) * n_elem], &part[((size_t)b * n_ids + j) * n_elem],
+                            (size_t)n_elem * sizeof(jet_c128));
     }
+    sums.assign((size_t)n_amps * n_elem, jet_c128{0.0, 0.0});
+    for (int32_t b = 0; b < n_amps; ++b)
+        for (int64_t sid = 0; sid < n_sl; ++sid)
+            for (int64_t e = 0; e < n_elem; ++e) {
+                const jet_c128 &v = all[((size_t)b * n_sl + sid) * n_elem + e];
+                jet_c128 &acc = sums[(size_t)b * n_elem + e];
+                acc.re += v.re;
+                acc.im += v.im;
+            }
 }
 
 int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c128 *amps_dev,
@@ -628,7 +805,7 @@ int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,
     return guarded([&] {
         if (!net || !amps_dev) fail(JET_EINVAL, "NULL argument");
         Plan &P = get_plan(*net, n_amps, outputs);
-        const size_t cap = workspace_cap(*net);
+        const size_t cap = run_cap(*net, P);
         if (cap && P.arena_bytes > cap && P.n_slices > 1) {   // slice ranges: synchronous
             std::vector<jet_c128> sums;
             contract_in_ranges(*net, n_amps, outputs, cap, cuda_stream, sums);
@@ -647,7 +824,7 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c
     return guarded([&] {
         if (!net || !amps_out) fail(JET_EINVAL, "NULL argument");
         Plan &P = get_plan(*net, n_amps, outputs);
-        const size_t cap = workspace_cap(*net);
+        const size_t cap = run_cap(*net, P);
         if (cap && P.arena_bytes > cap && P.n_slices > 1) {
             std::vector<jet_c128> sums;
             contract_in_ranges(*net, n_amps, outputs, cap, cuda_stream, sums);

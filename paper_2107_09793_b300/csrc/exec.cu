@@ -178,9 +178,36 @@ void release_plan_device(Plan &plan)
     plan.d_args_bytes = 0;
 }
 
+size_t device_free_bytes(Network &net)
+{
+    int prev = 0;
+    JET_CUDA(cudaGetDevice(&prev));
+    JET_CUDA(cudaSetDevice(net.opt.device));
+    size_t fr = 0, tot = 0;
+    const cudaError_t e = cudaMemGetInfo(&fr, &tot);
+    cudaSetDevice(prev);
+    JET_CUDA(e);
+    return fr;
+}
+
+void ensure_workspace(Network &net, size_t bytes, void *stream)
+{
+    if (net.user_arena || net.own_arena_bytes >= bytes) return;
+    cudaStream_t s = stream ? (cudaStream_t)stream : (cudaStream_t)net.stream;
+    JET_CUDA(cudaStreamSynchronize(s));
+    device_free(net.own_arena);
+    net.own_arena = nullptr;
+    net.own_arena_bytes = 0;
+    net.own_arena = device_alloc(bytes);
+    net.own_arena_bytes = bytes;
+}
+
 void free_network_device(Network &net)
 {
     if (net.plan) release_plan_device(*net.plan);
+    if (net.ranges)
+        for (auto &p : net.ranges->plans)
+            if (p) release_plan_device(*p);
     if (net.grad_plan) release_plan_device(*net.grad_plan);
     net.last_run = nullptr;
     device_free(net.d_leaves);

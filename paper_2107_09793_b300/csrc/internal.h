@@ -146,6 +146,28 @@ struct Plan {
     bool dirty_args = true;
 };
 
+// Slice ranges (Section 4: a subset of the slices held in memory at a time,
+// its size determined a priori) for a workspace cap below the plan of every
+// slice: a range fixes the digits of the sliced labels at `fixed_pos` and runs
+// every slice with those digits, so an intermediate with one of those labels
+// under it is computed once in all, and one without once per range.  The
+// labels are chosen to minimise the FLOP of all ranges together; each range's
+// plan is kept (and replayed as its CUDA graph) while the key holds.
+struct RangeSet {
+    // key
+    std::vector<int32_t> outputs;
+    int32_t n_amps = 0;
+    uint64_t path_version = 0, slice_version = 0;
+    int32_t precision = 0, reuse = 1;
+    size_t cap = 0;
+    // partition
+    std::vector<int32_t> fixed_pos;            // positions in Network::sliced
+    std::vector<std::vector<int64_t>> ids;     // slice ids of each range, increasing
+    double flop = 0;                           // FLOP of all ranges together
+    size_t arena = 0;                          // workspace of one range
+    std::vector<std::unique_ptr<Plan>> plans;  // per range, built on first use
+};
+
 struct Network {
     jet_options opt;
     std::vector<Leaf> leaves;
@@ -179,6 +201,7 @@ struct Network {
     void *stream = nullptr;          // library-internal stream for uploads
 
     std::unique_ptr<Plan> plan;
+    std::unique_ptr<RangeSet> ranges;    // slice ranges under a workspace cap
     std::unique_ptr<Plan> grad_plan;     // cached adjoint plan (unsliced networks)
     const Plan *last_run = nullptr;      // the plan jet_profile reports
     void *own_arena = nullptr;
@@ -227,6 +250,8 @@ void free_network_device(Network &net);
 void upload_leaf(Network &net, int32_t tensor_id, void *stream);
 void upload_all(Network &net, const jet_c64 *data, void *stream);
 void *device_alloc(size_t bytes);
+size_t device_free_bytes(Network &net);         // free device memory on the network's device
+void ensure_workspace(Network &net, size_t bytes, void *stream);   // grow the library's own arena
 void device_free(void *p);
 void sync_stream(Network &net, void *stream);   // the given stream, or the library's own when NULL
 void copy_d2h(void *dst, const void *src, size_t bytes, void *stream);

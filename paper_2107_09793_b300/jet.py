@@ -22,7 +22,8 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_plan", "jet_set_workspace", "jet_contract_grad", "jet_stats",
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
            "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices",
-           "jet_network_keep_shared", "jet_network_save_shared", "jet_network_load_shared", "jet_plan_buffers"]
+           "jet_network_keep_shared", "jet_network_save_shared", "jet_network_load_shared", "jet_plan_buffers",
+           "jet_plan_ranges"]
 
 
 class JetError(RuntimeError):
@@ -107,6 +108,7 @@ def lib():
             "jet_stats": (I32, [P, P]),
             "jet_profile": (I32, [P, P, I32, P]),
             "jet_plan_buffers": (I32, [P, P, I32, P]),
+            "jet_plan_ranges": (I32, [P, I32, P, ctypes.c_size_t, P, P, P, P, P]),
             "jet_pair_contract_noalloc": (I32, [I32, P, P, P, I32, P, P, P, P, I32, P]),
             "jet_network_destroy": (None, [P]),
             "jet_last_error": (ctypes.c_char_p, []),
@@ -292,6 +294,17 @@ class Network:
         b = ctypes.c_size_t()
         _check(lib().jet_plan_slices(self._h, o.shape[0], o.ctypes.data, ids.size, ids.ctypes.data, ctypes.byref(b)))
         return b.value
+
+    def plan_ranges(self, outputs, max_bytes: int) -> Dict[str, object]:
+        """jet_plan_ranges: the slice ranges a contraction runs under a workspace cap."""
+        o = self._outputs(outputs)
+        nf, nr = ctypes.c_int32(), ctypes.c_int64()
+        flop, nb = ctypes.c_double(), ctypes.c_size_t()
+        labels = (ctypes.c_int64 * max(int(self.stats()["n_sliced_labels"]), 1))()
+        _check(lib().jet_plan_ranges(self._h, o.shape[0], o.ctypes.data, ctypes.c_size_t(int(max_bytes)),
+                                     ctypes.byref(nf), labels, ctypes.byref(nr), ctypes.byref(flop), ctypes.byref(nb)))
+        return {"fixed_labels": [int(labels[i]) for i in range(nf.value)], "n_ranges": nr.value,
+                "flop": flop.value, "bytes": nb.value}
 
     def set_workspace(self, dptr: int, nbytes: int):
         _check(lib().jet_set_workspace(self._h, ctypes.c_void_p(dptr), ctypes.c_size_t(nbytes)))

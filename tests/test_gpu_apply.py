@@ -118,8 +118,12 @@ _REF = {}
 
 def _check(case, prec, expect_tc, **opt):
     net, labels, data, opens, path = _network(case, prec, **opt)
-    got = net.contract(np.zeros((1, len(opens)), np.int32))
-    pair = [r for r in net.profile() if r["node"] == len(labels) and r["kind"] == "apply"]
+    try:
+        got = net.contract(np.zeros((1, len(opens)), np.int32))[0]
+        recs = net.profile()
+    finally:
+        net.close()
+    pair = [r for r in recs if r["node"] == len(labels) and r["kind"] == "apply"]
     assert pair, "the pair did not take the small-operand route"
     assert all(bool(r["variant"] & 8) == expect_tc for r in pair), pair
     if case not in _REF:
@@ -128,7 +132,6 @@ def _check(case, prec, expect_tc, **opt):
     assert got.shape == ref.shape
     err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
     print(f"{case} {prec} tc={expect_tc}: max elementwise err {err:.3e}")
-    net.close()
     return err
 
 

@@ -66,11 +66,13 @@ def test_gemm_layouts(prec, case):
     la, lb, dd = CASES[case]
     dims = {l: dd.get(l, 2) for l in la + lb}
     net, A, B = _pair_network(la, lb, dims, 31 + case, prec)
-    got = net.contract(np.zeros((1, len(la) + len(lb) - 2 * len(set(la) & set(lb))), np.int32))
-    assert net.stats()["n_gemm_nodes"] >= 1
+    try:
+        got = net.contract(np.zeros((1, len(la) + len(lb) - 2 * len(set(la) & set(lb))), np.int32))[0]
+        assert net.stats()["n_gemm_nodes"] >= 1
+    finally:
+        net.close()
     err = _elementwise_err(got, la, A, lb, B)
     print(f"gemm case {case} {prec}: max elementwise err {err:.3e}")
-    net.close()
     assert err <= TOL[prec], err
 
 
@@ -89,7 +91,7 @@ def test_gemm_batched_instances_under_slicing():
     net.set_free(opens)
     net.path_set([(0, 1), (3, 2)])
     net.slice([30, 31])
-    got = net.contract(np.zeros((1, len(opens)), np.int32))
+    got = net.contract(np.zeros((1, len(opens)), np.int32))[0]
     assert net.stats()["n_gemm_nodes"] >= 1
     out, ref = contract_network([la, lb, [30, 31]], [A, B, C], [(0, 1), (3, 2)])
     ref = np.transpose(np.asarray(ref), [out.index(l) for l in opens]).ravel()

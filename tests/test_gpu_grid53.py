@@ -14,15 +14,20 @@ oracle):
     8 seeded slices (3 exactly zero, 4 below 1e-25 from fSim(pi/2)'s cos entry
     of 6e-17, one of typical size).
 
-Tolerances per mode, from the arithmetic (u = unit roundoff of the operand
-representation, complex64 intermediates accumulated in FP32):
-  fp32, tf32x3, fp16x3, bf16x6: 1e-5 (u <= 2^-22 per operand; the measured
-      error is set by FP32 accumulation over the path, ~1e-6 per slice);
-  bf16x3: 5e-4 (hi + lo in BF16 keeps 16 significant bits, u = 2^-17 = 7.6e-6
-      per operand entry, over a few hundred dependent contraction steps);
-  tf32: 5e-2 (one TF32 product, u = 2^-11 = 4.9e-4 per operand entry, the same
-      steps); it fails the 1e-5 bar on purpose and is reported for comparison;
-  fp64: 1e-12 (complex128 everywhere, FP64 on CUDA cores)."""
+Tolerances per mode, from the arithmetic (u = unit roundoff of an operand
+entry's representation; complex64 intermediates accumulate in FP32): normwise
+over the nonzero partials (the metric's bar, relative error <= 1e-5 for the
+complex64 modes), and per partial against its own magnitude, looser where a
+partial is a cancelling sum of larger terms:
+  fp32: u = 2^-24; 1e-5 both ways;
+  tf32x3, fp16x3, bf16x6: the tensor-core small-operand applications of every
+      split mode use TF32 hi + lo, 22 significant bits, u = 2^-22 (4x FP32's
+      operand error, then FP32 accumulation); normwise 1e-5, per partial 3e-5;
+  bf16x3: hi + lo in BF16 keeps 16 significant bits, u = 2^-17 = 7.6e-6 per
+      operand entry of the GEMMs, over the path's dependent steps: 2e-4 / 5e-4;
+  tf32: one TF32 product, u = 2^-11 = 4.9e-4 per operand entry: 2e-2 / 5e-2
+      (it fails the 1e-5 bar on purpose and is reported for comparison);
+  fp64: 1e-12 both ways (complex128 everywhere, FP64 on CUDA cores)."""
 import json
 import os
 
@@ -35,7 +40,8 @@ from paper_2107_09793_b300 import jet
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.join(os.path.dirname(__file__), "golden")
-TOL = {"fp32": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "bf16x6": 1e-5, "bf16x3": 5e-4, "tf32": 5e-2, "fp64": 1e-12}
+TOL_NORM = {"fp32": 1e-5, "tf32x3": 1e-5, "fp16x3": 1e-5, "bf16x6": 1e-5, "bf16x3": 2e-4, "tf32": 2e-2, "fp64": 1e-12}
+TOL_SLICE = {"fp32": 1e-5, "tf32x3": 3e-5, "fp16x3": 3e-5, "bf16x6": 3e-5, "bf16x3": 5e-4, "tf32": 5e-2, "fp64": 1e-12}
 
 
 def _load(name):
@@ -50,21 +56,35 @@ def workload():
     return configs.build("grid53")
 
 
-def _check_partials(got, ref, zero_ids, ids, tol, prec):
-    """Each partial against its own magnitude; a structurally zero partial must
-    come out exactly zero."""
+def _check_partials(got, ref, zero_ids, ids, prec):
+    """Normwise over the partials that are not structurally zero, each of them
+    against its own magnitude, and a structurally zero partial exactly zero."""
     big = np.max(np.abs(ref))
+    nz = np.array([i not in zero_ids for i in ids])
+    norm = float(np.linalg.norm(got[nz] - ref[nz]) / np.linalg.norm(ref[nz]))
     worst = 0.0
-    for j, (g, r, i) in enumerate(zip(got, ref, ids)):
+    for g, r, i in zip(got, ref, ids):
         if i in zero_ids:
             assert r == 0 and g == 0, (prec, i, g, r)
         elif abs(r) >= 1e-3 * big:
             e = abs(g - r) / abs(r)
             worst = max(worst, e)
-            assert e <= tol, (prec, i, e)
+            assert e <= TOL_SLICE[prec], (prec, i, e)
         else:   # partials far below the amplitude's scale: at that scale
-            assert abs(g - r) <= tol * big, (prec, i, g, r)
-    return worst
+            assert abs(g - r) <= TOL_SLICE[prec] * big, (prec, i, g, r)
+    assert norm <= TOL_NORM[prec], (prec, norm)
+    return norm, worst
+
+
+def _partials(w, prec, path, sliced, outputs, ids):
+    net = jet.from_network(w.network, precision=prec)
+    try:
+        net.path_set([tuple(p) for p in path])
+        net.slice(sliced)
+        assert net.stats()["max_intermediate"] <= 1 << 28
+        return net.contract_slices(np.array(outputs, np.int32), ids)[0]
+    finally:
+        net.close()
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp32", "bf16x3", "tf32", "fp16x3", "bf16x6", "fp64"])
@@ -72,28 +92,18 @@ def test_grid53_benchmark_plan_slice_partials(workload, prec):
     plan = _load("grid53_plan.json")
     g = _load("grid53_bench.json")
     assert g["sliced_labels"] == plan["sliced_labels"]
-    net = jet.from_network(workload.network, precision=prec)
-    net.path_set([tuple(p) for p in plan["path"]])
-    net.slice(plan["sliced_labels"])
-    assert net.stats()["max_intermediate"] <= 1 << 28
-    got = net.contract_slices(np.array(g["outputs"], np.int32), g["slice_ids"])[0]
+    got = _partials(workload, prec, plan["path"], plan["sliced_labels"], g["outputs"], g["slice_ids"])
     ref = np.array([complex(a, b) for a, b in g["slice_partials"]])
-    worst = _check_partials(got, ref, set(g["structurally_zero_ids"]), g["slice_ids"], TOL[prec], prec)
-    print(f"grid53 benchmark plan {prec}: worst per-slice rel err {worst:.3e} over "
+    norm, worst = _check_partials(got, ref, set(g["structurally_zero_ids"]), g["slice_ids"], prec)
+    print(f"grid53 benchmark plan {prec}: normwise {norm:.3e}, worst per-slice {worst:.3e} over "
           f"{len(ref) - len(g['structurally_zero_ids'])} slices")
-    net.close()
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "fp32", "fp16x3"])
 def test_grid53_oracle_plan_slice_partials(workload, prec):
     g = _load("grid53.json")
-    net = jet.from_network(workload.network, precision=prec)
-    net.path_set([tuple(p) for p in g["path"]])
-    net.slice(g["sliced_labels"])
-    assert net.stats()["max_intermediate"] <= 1 << 28
-    got = net.contract_slices(np.array(g["outputs"], np.int32), g["slice_ids"])[0]
+    got = _partials(workload, prec, g["path"], g["sliced_labels"], g["outputs"], g["slice_ids"])
     ref = np.array([complex(a, b) for a, b in g["slice_partials"]])
     zero = {i for i, r in zip(g["slice_ids"], ref) if r == 0}
-    worst = _check_partials(got, ref, zero, g["slice_ids"], TOL[prec], prec)
-    print(f"grid53 oracle plan {prec}: worst per-slice rel err {worst:.3e}")
-    net.close()
+    norm, worst = _check_partials(got, ref, zero, g["slice_ids"], prec)
+    print(f"grid53 oracle plan {prec}: normwise {norm:.3e}, worst per-slice {worst:.3e}")
