@@ -1045,7 +1045,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jet", choices=["jet", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3", "fp64"])
+    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
     ap.add_argument("--skip-others", action="store_true", help="skip the other workloads (bosonic lattice, "

@@ -104,11 +104,13 @@ def test_grid30_path_reconfigured_for_its_slicing():
 
 def test_grid30_workspace_limit_runs_slice_ranges():
     """jet_options.workspace_limit below the plan's workspace: the slices run in
-    consecutive id ranges whose plans fit (a subset of the slices held at a
-    time, sized a priori); the sums match the stored state-vector amplitudes to
-    1e-5 (the split modes' accuracy target), and one plan's sums within that
-    target per amplitude (a range's plan may take other kernel forms, with
-    another rounding, for nodes with fewer instances)."""
+    ranges whose plans fit (a subset of the slices held at a time, sized a
+    priori; each range fixes the sliced labels that keep the most work shared);
+    the sums match the stored state-vector amplitudes to 1e-5 (the split modes'
+    accuracy target), and one plan's sums within that target per amplitude (a
+    range's plan may take other kernel forms, with another rounding, for nodes
+    with fewer instances); a second call replays the kept range plans and gives
+    the same sums bit for bit."""
     import json
     import os
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid30.json")))
@@ -126,6 +128,13 @@ def test_grid30_workspace_limit_runs_slice_ranges():
     assert np.max(np.abs(got - ref) / np.abs(ref)) <= 1e-5
     gold = np.array([complex(a, b) for a, b in g["amplitudes"][:2]])
     assert np.linalg.norm(got - gold) / np.linalg.norm(gold) <= 1e-5
-    assert lim.stats()["workspace_bytes"] <= need // 3     # the last range's plan
+    rg = lim.plan_ranges(rows, need // 3)
+    assert rg["n_ranges"] > 1 and rg["bytes"] <= need // 3 and len(rg["fixed_labels"]) >= 1
+    assert set(rg["fixed_labels"]) <= set(labels)
+    assert rg["flop"] >= full.stats()["flop_executed"]   # a range recomputes what it does not share
+    bufs = lim.plan_buffers()                            # the last range's plan ran in the cap
+    assert max(b["offset"] + b["bytes"] for b in bufs) <= need // 3
+    again = lim.contract(rows)
+    assert np.array_equal(again, got)
     full.close()
     lim.close()
