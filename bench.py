@@ -713,6 +713,9 @@ def roofline_of(recs, timed, prec, peaks, peak_src, step_ms):
                 "peak_source": f"hbm_gbs of {peak_src}"}
     roof.update(common)
     roof["kinds_timed_ms_per_range"] = {k: sum(timed[i] for i in v) for k, v in by_kind.items()}
+    roof["launches"] = [{"node": recs[i]["node"], "ms": timed[i], "flop": recs[i]["flop"], "bytes": recs[i]["bytes"],
+                         "n_inst": recs[i]["n_inst"], "grid": recs[i]["grid"], "variant": recs[i]["variant"]}
+                        for i in sorted(ids, key=lambda i: -timed[i])]
     return roof
 
 
@@ -738,8 +741,8 @@ def run_impl(args):
     ws = torch.empty(int(0.8 * free) // 256 * 256, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def handle(prec, profile=0):
-        h = jet.from_network(w.network, precision=prec, profile=profile, device=dev)
+    def handle(prec, profile=0, **opt):
+        h = jet.from_network(w.network, precision=prec, profile=profile, device=dev, **opt)
         h.path_set(path)
         h.slice(sliced)
         h.set_workspace(ws.data_ptr(), ws.numel())
@@ -869,10 +872,28 @@ def run_impl(args):
                            "ms_per_step": statistics.mean(msm),
                            "tflops": ranges["flop"] / (statistics.mean(msm) * 1e-3) / 1e12,
                            "amp": [amp_m.real, amp_m.imag], "err_vs_oracle_partials": parity(prec)}
+        # the headline mode with every GEMM instance run as its own product
+        h = handle(args.precision, gemm_group=False)
+        am = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
+        h.contract_async(outs, am.data_ptr(), sh)
+        torch.cuda.synchronize()
+        msm = []
+        for _ in range(2):
+            flush.zero_()
+            ev0.record(stream)
+            h.contract_async(outs, am.data_ptr(), sh)
+            ev1.record(stream)
+            ev1.synchronize()
+            msm.append(ev0.elapsed_time(ev1))
+        h.close()
+        modes[args.precision + "_ungrouped"] = {"value": 1000.0 / statistics.mean(msm), "unit": "amplitudes/s",
+                                                "ms_per_step": statistics.mean(msm),
+                                                "note": "jet_options.gemm_group = 0: one GEMM per instance"}
         if "fp32" in modes:
             a32 = complex(*modes["fp32"]["amp"])
             for prec, m in modes.items():
-                m["amp_rel_diff_vs_fp32"] = abs(complex(*m["amp"]) - a32) / abs(a32)
+                if "amp" in m:
+                    m["amp_rel_diff_vs_fp32"] = abs(complex(*m["amp"]) - a32) / abs(a32)
 
     # end to end through the C ABI: pinned host inputs -> device, contract, amplitude back to host
     nv = run_net.n_values()

@@ -102,6 +102,12 @@ typedef struct {
                                  summed entries and summed x free >= 10 (summed + free),
                                  where the CUDA-core forms are FMA-bound; default 1024,
                                  above 8192 none does                                     */
+    int32_t gemm_group;       /* 1 (default): a GEMM-route node whose instances pair every
+                                 instance of one operand with the same instances of the
+                                 other runs those pairs as one wider product per block
+                                 (a shared operand read once per tile row or column, short
+                                 sides packed into full tiles); 0: one product per
+                                 instance                                                 */
 } jet_options;
 
 typedef struct {
@@ -336,6 +342,15 @@ int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs
  * issued on cuda_stream before the next call completes. */
 int jet_contract_async(jet_network *net, int32_t n_amps, const int32_t *outputs,
                        jet_c128 *amps_dev, void *cuda_stream);
+
+/* The cross-slice reduction of Eq. sliced_sum on the host: sums_out[b * n_elem
+ * + e] = sum over j = 0, 1, ..., n_ids - 1, in that order, in FP64, of
+ * partials[(b * n_ids + j) * n_elem + e].  Partials gathered from processes
+ * that each contracted a slice-id range (jet_contract_slices), concatenated in
+ * increasing slice id, sum in the order of a single jet_contract, so the result
+ * does not depend on how the slices were split.  HOST buffers; n_ids = 0 gives
+ * zeros.  Errors: JET_EINVAL (negative sizes, n_elem < 1, NULL buffers). */
+int jet_sum_partials(int32_t n_amps, int64_t n_ids, int64_t n_elem, const jet_c128 *partials, jet_c128 *sums_out);
 
 /* Device workspace.  jet_plan prepares the plan for this batch of outputs and
  * reports the bytes of device workspace it needs.  jet_set_workspace hands the

@@ -163,6 +163,7 @@ void jet_options_default(jet_options *opt)
     opt->workspace_limit = 0;
     opt->profile = 0;
     opt->apply_tc_min_kf = 1024;
+    opt->gemm_group = 1;
 }
 
 int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_options *opt, jet_network **out)
@@ -598,6 +599,24 @@ int jet_plan_ranges(jet_network *net, int32_t n_amps, const int32_t *outputs, si
         if (n_ranges_out) *n_ranges_out = nr;
         if (flop_out) *flop_out = flop;
         if (bytes_out) *bytes_out = bytes;
+    });
+}
+
+int jet_sum_partials(int32_t n_amps, int64_t n_ids, int64_t n_elem, const jet_c128 *partials, jet_c128 *sums_out)
+{
+    return guarded([&] {
+        if (n_amps < 0 || n_ids < 0 || n_elem < 1) fail(JET_EINVAL, "bad sizes");
+        if ((n_amps > 0 && n_ids > 0 && !partials) || (n_amps > 0 && !sums_out)) fail(JET_EINVAL, "NULL argument");
+        for (int64_t b = 0; b < n_amps; ++b)
+            for (int64_t e = 0; e < n_elem; ++e) {
+                double re = 0.0, im = 0.0;
+                for (int64_t j = 0; j < n_ids; ++j) {
+                    const jet_c128 &v = partials[(b * n_ids + j) * n_elem + e];
+                    re += v.re;
+                    im += v.im;
+                }
+                sums_out[b * n_elem + e] = jet_c128{re, im};
+            }
     });
 }
 

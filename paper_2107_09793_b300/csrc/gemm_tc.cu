@@ -129,8 +129,7 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
     __shared__ float mul[SPLIT_TR];   // SCALED: 2^s of each row of this 64-wide chunk
     const int tid = threadIdx.x;
     const int64_t k_tiles = (a.k_pad + SPLIT_TK - 1) / SPLIT_TK;
-    const int64_t n_tiles = (a.rows_pad / SPLIT_TR) * k_tiles;
-    const int64_t plane_elems = a.rows_pad * a.k_pad;
+    const int64_t plane_elems = a.rows_group * a.k_pad;
 
     auto decode = [&](int64_t t, int buf) {   // threads 0..127: one row or column offset each
         static_assert(SPLIT_TR + SPLIT_TK <= 256, "one decoding thread per tile row and column");
@@ -182,7 +181,13 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
 
     for (int64_t inst = blockIdx.y; inst < a.n_inst; inst += gridDim.y) {
         const float2 *__restrict__ S = (const float2 *)((const uint64_t *)a.ptrSrc)[inst];
-        uint8_t *base = (uint8_t *)a.planes + (int64_t)inst * NP * plane_elems * EB;
+        // instance j of group g: rows j * rows.. of the group's planes; the last
+        // instance of a group also writes the group's padding rows (zeros)
+        const int64_t g = inst / a.per_group, j = inst - g * a.per_group;
+        const int64_t row_base = j * a.rows;
+        const int64_t rows_w = j == a.per_group - 1 ? a.rows_group - row_base : a.rows;
+        const int64_t n_tiles = ((rows_w + SPLIT_TR - 1) / SPLIT_TR) * k_tiles;
+        uint8_t *base = (uint8_t *)a.planes + (g * NP * plane_elems + row_base * a.k_pad) * EB;
         __syncthreads();   // the previous instance's readers of the buffers are done
         if (blockIdx.x < n_tiles) decode(blockIdx.x, 0);
         __syncthreads();
@@ -222,7 +227,8 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
                 if (sub == 0) {
                     mul[r] = ldexpf(1.f, e);
                     const int64_t n_ch = (a.k_pad + 63) >> 6;
-                    ((float *)a.scales)[(inst * n_ch + kt) * a.rows_pad + row0 + r] = ldexpf(1.f, -e);
+                    if (row0 + r < rows_w)
+                        ((float *)a.scales)[(g * n_ch + kt) * a.rows_group + row_base + row0 + r] = ldexpf(1.f, -e);
                 }
                 __syncthreads();
             }
@@ -231,7 +237,7 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
                 const int idx = tid + 256 * i;
                 const int r = idx / (SPLIT_TK / 2), kp = 2 * (idx % (SPLIT_TK / 2));
                 const int64_t kcol = k0 + kp;
-                if (kcol >= a.k_pad) continue;
+                if (kcol >= a.k_pad || row0 + r >= rows_w) continue;
                 const int64_t e = (row0 + r) * a.k_pad + kcol;
                 float2 v0 = tile[r * SPLIT_ROW + kp], v1 = tile[r * SPLIT_ROW + kp + 1];
                 if (TcCfg<MODE>::SCALED) {
@@ -501,10 +507,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             }
             if (!ok) break;
             const int64_t row = (int64_t)tm * TC_BM + quarter * 32 + lane;
-            float2 *C = (float2 *)((const uint64_t *)a.ptrC)[inst];
+            const uint64_t *ptrC = (const uint64_t *)a.ptrC;
+            const bool grouped = a.itab != 0;
             const int64_t col0 = (int64_t)tn * TC_BN + half * 64;
-            if (tc_cstage<MODE>() && (a.N & 15) == 0 && col0 + 64 <= a.N) {
-                // whole 64-column half tile in range: stage 16 columns at a time
+            // output address of block entry (R, c): instance `inst` itself, or, for a
+            // block of grouped instances, the instance that (R, c) falls in (null
+            // where that pair is not an instance of the node)
+            auto out_ptr = [&](int64_t R, int64_t c) -> float2 * {
+                if (!grouped) return (float2 *)ptrC[inst] + R * a.N + c;
+                const int64_t jj = R / a.Mi, m = R - jj * a.Mi;
+                const int64_t l = c / a.Ni, n = c - l * a.Ni;
+                const int32_t it = ((const int32_t *)a.itab)[((int64_t)inst * a.nA + jj) * a.nB + l];
+                return it < 0 ? nullptr : (float2 *)ptrC[it] + m * a.Ni + n;
+            };
+            if (tc_cstage<MODE>() && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
+                // whole 64-column half tile in range: stage 16 columns at a time (a
+                // 16-column group lies in one instance)
                 float2 *st = (float2 *)(smem + (size_t)S * STAGE_BYTES) + (size_t)(warp - 2) * 32 * TC_CST_ROW;
                 const int64_t row0 = (int64_t)tm * TC_BM + quarter * 32;
 #pragma unroll
@@ -516,22 +534,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     for (int it = 0; it < 8; ++it) {
                         const int r = it * 4 + (lane >> 3), cc = (lane & 7) * 2;
                         if (row0 + r < a.M) {
+                            float2 *dst = out_ptr(row0 + r, col0 + p * 16 + cc);
                             const float2 v0 = st[r * TC_CST_ROW + cc], v1 = st[r * TC_CST_ROW + cc + 1];
-                            *(float4 *)(C + (row0 + r) * a.N + col0 + p * 16 + cc) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                            if (dst) *(float4 *)dst = make_float4(v0.x, v0.y, v1.x, v1.y);
                         }
                     }
                     __syncwarp();
                 }
             } else if (row < a.M) {
-                float2 *dst = C + row * a.N + col0;
-                if ((a.N & 1) == 0 && col0 + 64 <= a.N) {
+                if ((a.Ni & 1) == 0 && col0 + 64 <= a.N) {
 #pragma unroll
-                    for (int j = 0; j < 64; j += 2)
-                        *(float4 *)(dst + j) = make_float4(racc[j], iacc[j], racc[j + 1], iacc[j + 1]);
+                    for (int j = 0; j < 64; j += 2) {
+                        float2 *dst = out_ptr(row, col0 + j);
+                        if (dst) *(float4 *)dst = make_float4(racc[j], iacc[j], racc[j + 1], iacc[j + 1]);
+                    }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 64; ++j)
-                        if (col0 + j < a.N) dst[j] = make_float2(racc[j], iacc[j]);
+                        if (col0 + j < a.N) {
+                            float2 *dst = out_ptr(row, col0 + j);
+                            if (dst) *dst = make_float2(racc[j], iacc[j]);
+                        }
                 }
             }
         }

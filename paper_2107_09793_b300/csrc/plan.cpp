@@ -167,6 +167,69 @@ int find_pos(const std::vector<int64_t> &v, int64_t x)
     return it == v.end() ? -1 : (int)(it - v.begin());
 }
 
+// Blocks of a GEMM node's instances.  Instance i pairs M-side child instance
+// mi[i] with N-side child instance ni[i].  Grouping by one side: the instances
+// of that side that pair with the same set of the other side's instances form
+// one group, that set another, and the two make a block whose product covers
+// each of those pairs once; blocks of equal shape run as one launch of wider
+// products (a shared operand instance is read once per tile row or column
+// instead of once per pair, and short sides fill the tiles).
+struct GemmGroups {
+    std::vector<std::vector<int32_t>> gM, gN;   // child instances of each group
+    std::vector<int32_t> bM, bN;                // per block: its M group and N group
+    std::vector<int32_t> itab;                  // per block: [j][l] -> node instance
+    int32_t nA = 1, nB = 1;                     // instances per M group, per N group
+    int64_t dup = 0;                            // child instances split into more than one group
+};
+
+bool group_instances(const std::vector<int32_t> &mi, const std::vector<int32_t> &ni, bool by_m, GemmGroups &G)
+{
+    const std::vector<int32_t> &p = by_m ? mi : ni, &q = by_m ? ni : mi;
+    std::map<int32_t, std::vector<std::pair<int32_t, int32_t>>> byp;   // p instance -> (q instance, node instance)
+    for (size_t i = 0; i < p.size(); ++i) byp[p[i]].push_back({q[i], (int32_t)i});
+    std::map<std::vector<int32_t>, int32_t> block_of;
+    std::vector<std::vector<int32_t>> bp, bq;
+    std::vector<std::vector<std::vector<int32_t>>> binst;   // block -> [j] -> node instance per l
+    for (auto &kv : byp) {
+        auto &lst = kv.second;
+        std::sort(lst.begin(), lst.end());
+        std::vector<int32_t> key;
+        for (auto &x : lst) key.push_back(x.first);
+        if (std::adjacent_find(key.begin(), key.end()) != key.end()) return false;   // a repeated pair
+        auto it = block_of.find(key);
+        if (it == block_of.end()) {
+            it = block_of.emplace(key, (int32_t)bp.size()).first;
+            bp.emplace_back();
+            bq.push_back(key);
+            binst.emplace_back();
+        }
+        bp[it->second].push_back(kv.first);
+        std::vector<int32_t> row;
+        for (auto &x : lst) row.push_back(x.second);
+        binst[it->second].push_back(row);
+    }
+    const size_t np = bp[0].size(), nq = bq[0].size();
+    for (size_t b = 0; b < bp.size(); ++b)
+        if (bp[b].size() != np || bq[b].size() != nq) return false;
+    G = GemmGroups();
+    std::map<int32_t, int> seen_q;
+    for (auto &k : bq)
+        for (int32_t x : k) ++seen_q[x];
+    for (auto &kv : seen_q) G.dup += kv.second - 1;
+    for (size_t b = 0; b < bp.size(); ++b) {
+        (by_m ? G.gM : G.gN).push_back(bp[b]);
+        (by_m ? G.gN : G.gM).push_back(bq[b]);
+        G.bM.push_back((int32_t)b);
+        G.bN.push_back((int32_t)b);
+        for (size_t jm = 0; jm < (by_m ? np : nq); ++jm)
+            for (size_t ln = 0; ln < (by_m ? nq : np); ++ln)
+                G.itab.push_back(by_m ? binst[b][jm][ln] : binst[b][ln][jm]);
+    }
+    G.nA = (int32_t)(by_m ? np : nq);
+    G.nB = (int32_t)(by_m ? nq : np);
+    return true;
+}
+
 }  // namespace
 
 // tensor-core route geometry (gemm_tc.cu)
@@ -1247,19 +1310,44 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 const int NP = tc_planes(net.opt.precision), eb = tc_elem_bytes(net.opt.precision);
                 const int64_t kblk = tc_k_block(net.opt.precision), T = tc_tile();
                 const int64_t Mv = dimprod(fM), Nv = dimprod(fN);
-                const int64_t m_pad = (Mv + T - 1) / T * T, n_pad = (Nv + T - 1) / T * T;
+                // instance blocks: group the instances into full products of M-side
+                // and N-side child instances when every block has the same shape and
+                // (nearly) no child instance is split twice; else one block per instance
+                GemmGroups G;
+                {
+                    GemmGroups gm, gn;
+                    const bool okm = group_instances(instM, instN, true, gm);
+                    const bool okn = group_instances(instM, instN, false, gn);
+                    const double vm = (double)VM.size, vn = (double)VN.size;
+                    const double cm = okm ? gm.dup * vn : 1e300, cn = okn ? gn.dup * vm : 1e300;
+                    const double budget = 0.25 * ((double)node[idM].n_inst * vm + (double)node[idN].n_inst * vn);
+                    const bool merge = net.opt.gemm_group && (okm || okn) && std::min(cm, cn) <= budget &&
+                                       (okm && cm <= cn ? gm : gn).bM.size() < (size_t)N.n_inst;
+                    if (merge) {
+                        G = okm && cm <= cn ? gm : gn;
+                    } else {   // one block per instance; every child instance one group
+                        for (int64_t j = 0; j < node[idM].n_inst; ++j) G.gM.push_back({(int32_t)j});
+                        for (int64_t j = 0; j < node[idN].n_inst; ++j) G.gN.push_back({(int32_t)j});
+                        G.bM.assign(instM.begin(), instM.end());
+                        G.bN.assign(instN.begin(), instN.end());
+                    }
+                }
+                const bool grouped = !G.itab.empty();
+                const int64_t m_rows = G.nA * Mv, n_rows = G.nB * Nv;
+                const int64_t m_pad = (m_rows + T - 1) / T * T, n_pad = (n_rows + T - 1) / T * T;
                 const int64_t k_pad = (nK + kblk - 1) / kblk * kblk;
                 const bool scaled = net.opt.precision == JET_PREC_FP16X3;
                 auto split_child = [&](int32_t id, const View &V, const std::vector<int64_t> &f, int64_t rows_pad,
-                                       size_t &scale_off) {
-                    const int64_t ninst = node[id].n_inst;
-                    const size_t nbytes_p = (size_t)ninst * NP * rows_pad * k_pad * eb;
+                                       const std::vector<std::vector<int32_t>> &groups, size_t &scale_off) {
+                    const int64_t n_groups = (int64_t)groups.size(), per = (int64_t)groups[0].size();
+                    const int64_t ninst = n_groups * per;
+                    const size_t nbytes_p = (size_t)n_groups * NP * rows_pad * k_pad * eb;
                     size_t off = arena.alloc(nbytes_p);
                     scratch.push_back(off);
                     scratch_bytes.push_back(nbytes_p);
                     scale_off = 0;
-                    if (scaled) {   // one float per (instance, 64-wide K chunk, row)
-                        const size_t sb = (size_t)ninst * ((k_pad + 63) / 64) * rows_pad * 4;
+                    if (scaled) {   // one float per (group, 64-wide K chunk, row)
+                        const size_t sb = (size_t)n_groups * ((k_pad + 63) / 64) * rows_pad * 4;
                         scale_off = arena.alloc(sb);
                         scratch.push_back(scale_off);
                         scratch_bytes.push_back(sb);
@@ -1268,9 +1356,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     std::memset(&sa, 0, sizeof sa);
                     sa.rows = dimprod(f);
                     sa.k = nK;
-                    sa.rows_pad = rows_pad;
+                    sa.rows_group = rows_pad;
                     sa.k_pad = k_pad;
                     sa.n_inst = (int32_t)ninst;
+                    sa.per_group = (int32_t)per;
                     sa.n_planes = NP;
                     sa.mode = net.opt.precision;
                     sa.rank_r = (int32_t)f.size();
@@ -1307,7 +1396,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                         }
                     }
                     std::vector<std::pair<int32_t, int64_t>> ps;
-                    for (int64_t j = 0; j < ninst; ++j) ps.push_back(base_ref(id, (int32_t)j));
+                    for (const auto &gr : groups)
+                        for (int32_t j : gr) ps.push_back(base_ref(id, j));
                     size_t o_ps = blob.put_ptrs(ps);
                     size_t so = blob.reserve(sizeof sa);
                     std::memcpy(blob.bytes.data() + so, &sa, sizeof sa);
@@ -1320,10 +1410,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     op.n_inst = ninst;
                     op.args_off = so;
                     op.args_bytes = sizeof sa;
-                    op.bytes = (double)ninst * ((double)V.size * 8.0 + (double)NP * rows_pad * k_pad * eb);
+                    op.bytes = (double)ninst * (double)V.size * 8.0 + (double)n_groups * NP * rows_pad * k_pad * eb;
                     int64_t gy = std::min<int64_t>(ninst, 65535);
                     op.grid_y = (int32_t)gy;
-                    const int64_t tiles = (rows_pad / 64) * ((k_pad + 63) / 64);   // 64 x 64 tiles
+                    const int64_t tiles = ((sa.rows + 63) / 64) * ((k_pad + 63) / 64);   // 64 x 64 tiles
                     op.grid_x = (int32_t)std::max<int64_t>(
                         1, std::min<int64_t>(tiles, std::max<int64_t>(1, 148 * 16 / gy)));
                     {
@@ -1335,35 +1425,41 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     if (conv) {
                         op.variant |= 1;
                         op.grid_x = (int32_t)std::max<int64_t>(
-                            1, std::min<int64_t>((rows_pad * k_pad / 4 + 255) / 256, std::max<int64_t>(1, 148 * 16 / gy)));
+                            1, std::min<int64_t>((sa.rows * k_pad / 4 + 255) / 256, std::max<int64_t>(1, 148 * 16 / gy)));
                     }
                     P.ops.push_back(op);
                     P.bytes_executed += op.bytes;
                     return off;
                 };
                 size_t sclA = 0, sclB = 0;
-                size_t offA = split_child(idM, VM, fM, m_pad, sclA);
-                size_t offB = split_child(idN, VN, fN, n_pad, sclB);
+                size_t offA = split_child(idM, VM, fM, m_pad, G.gM, sclA);
+                size_t offB = split_child(idN, VN, fN, n_pad, G.gN, sclB);
+                const int64_t n_blocks = (int64_t)G.bM.size();
                 std::vector<int32_t> zA, zB;
-                for (int64_t i = 0; i < N.n_inst; ++i) {
-                    zA.push_back(instM[i] * NP);
-                    zB.push_back(instN[i] * NP);
+                if ((int64_t)(G.gM.size() + G.gN.size()) * NP > INT32_MAX) fail(JET_EINVAL, "too many instances of one GEMM node");
+                for (int64_t i = 0; i < n_blocks; ++i) {
+                    zA.push_back(G.bM[i] * NP);
+                    zB.push_back(G.bN[i] * NP);
                 }
-                if (N.n_inst * NP > INT32_MAX) fail(JET_EINVAL, "too many instances of one GEMM node");
                 TcGemmArgs g;
                 std::memset(&g, 0, sizeof g);
-                g.M = Mv;
-                g.N = Nv;
+                g.M = m_rows;
+                g.N = n_rows;
                 g.K = nK;
+                g.Mi = Mv;
+                g.Ni = Nv;
+                g.nA = G.nA;
+                g.nB = G.nB;
                 g.m_pad = m_pad;
                 g.n_pad = n_pad;
                 g.k_pad = k_pad;
-                g.planesA_total = node[idM].n_inst * NP;
-                g.planesB_total = node[idN].n_inst * NP;
-                g.n_inst = (int32_t)N.n_inst;
+                g.planesA_total = (int64_t)G.gM.size() * NP;
+                g.planesB_total = (int64_t)G.gN.size() * NP;
+                g.n_inst = (int32_t)n_blocks;
                 g.mode = net.opt.precision;
                 g.n_kb = (int32_t)(k_pad / kblk);
                 size_t o_za = blob.put_i32(zA), o_zb = blob.put_i32(zB), o_c = blob.put_ptrs(pc);
+                size_t o_it = grouped ? blob.put_i32(G.itab) : 0;
                 size_t so = blob.reserve(sizeof g, 128);
                 std::memcpy(blob.bytes.data() + so, &g, sizeof g);
                 blob.patch_field(so, offsetof(TcGemmArgs, planesA), BASE_ARENA, (int64_t)offA);
@@ -1371,6 +1467,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 blob.patch_field(so, offsetof(TcGemmArgs, zA), BASE_BLOB, (int64_t)o_za);
                 blob.patch_field(so, offsetof(TcGemmArgs, zB), BASE_BLOB, (int64_t)o_zb);
                 blob.patch_field(so, offsetof(TcGemmArgs, ptrC), BASE_BLOB, (int64_t)o_c);
+                if (grouped) blob.patch_field(so, offsetof(TcGemmArgs, itab), BASE_BLOB, (int64_t)o_it);
                 blob.patch_field(so, offsetof(TcGemmArgs, status), BASE_STATUS, 0);
                 if (scaled) {
                     blob.patch_field(so, offsetof(TcGemmArgs, scaleA), BASE_ARENA, (int64_t)sclA);
@@ -1386,7 +1483,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 op.bytes = bytes;
                 op.grid_x = (int32_t)(n_pad / T);
                 op.grid_y = (int32_t)(m_pad / T);
-                op.grid_z = (int32_t)N.n_inst;   // persistent launch: the tile count only
+                op.grid_z = (int32_t)n_blocks;   // persistent launch: the tile count only
+                op.variant = grouped ? 1 : 0;
                 P.ops.push_back(op);
             } else {
             int formM = form(VM, fM), formN = form(VN, fN);

@@ -7,37 +7,49 @@
 #include "../../include/jet.h"
 
 // Operand split: a complex64 operand, gathered from any strides into
-// [rows_pad][k_pad] K-contiguous planes.  Plane order per instance:
+// K-contiguous planes.  Instances come in groups of per_group; group g owns
+// planes z = g * n_planes + p of rows_group rows x k_pad, and its j-th
+// instance fills rows [j * rows, (j + 1) * rows) of each (the last one also
+// zeroes the group's padding rows up to rows_group).  Plane order per group:
 //   bf16x3 / tf32x3 : re_hi, re_lo, im_hi, im_lo
 //   bf16x6          : re_hi, re_mid, re_lo, im_hi, im_mid, im_lo
 //   tf32            : re, im
-// Padding rows/columns are written as zeros.
+// Padding columns (k >= k) are written as zeros.
 struct TcSplitArgs {
     uint64_t ptrSrc;                 // device array of n_inst source addresses (complex64)
     uint64_t planes;                 // plane base (device)
-    uint64_t scales;                 // FP16X3: float 2^-s per [instance][K chunk][row] (else 0)
-    int64_t rows, k, rows_pad, k_pad;
+    uint64_t scales;                 // FP16X3: float 2^-s per [group][K chunk][row of the group] (else 0)
+    int64_t rows, k, rows_group, k_pad;
     int32_t n_inst, n_planes;
+    int32_t per_group, pad_;
     int32_t rank_r, rank_k;
     int32_t mode, fast_k;           // fast_k: the source's stride-1 label is a summed label
     int64_t r_dim[JET_MAXR], r_s[JET_MAXR];   // row labels, fastest first, source strides
     int64_t k_dim[JET_MAXR], k_s[JET_MAXR];   // summed labels, fastest first, source strides
 };
 
-// C[m][n] = sum_k A[m][k] B[n][k] over split planes, complex 4M form with three
-// FP32 accumulators in TMEM: P = Ar.Br, Q = Ai.Bi, I = Ar.Bi + Ai.Br;
-// C = (P - Q) + i I.  Each real product expands into the split terms of the mode.
+// C[m][n] = sum_k A[m][k] B[n][k] over split planes, complex 4M form: the real
+// accumulator takes Ar.Br + (-Ai).Bi, the imaginary one Ar.Bi + Ai.Br, each
+// real product expanded into the split terms of the mode.
+// A launch runs n_inst blocks.  Block b is one product of an A group of nA
+// operand instances (rows j * Mi + m) and a B group of nB (columns l * Ni + n):
+// M = nA * Mi rows, N = nB * Ni columns; its entry (j, m; l, n) belongs to node
+// instance itab[(b * nA + j) * nB + l] (-1: not computed), element m * Ni + n
+// of that instance's output.  Without itab (nA = nB = 1) block b is instance b.
 struct TcGemmArgs {
     CUtensorMap tmA;                 // 3-D map over A planes: (k_pad, m_pad, planes)
     CUtensorMap tmB;                 // 3-D map over B planes: (k_pad, n_pad, planes)
     uint64_t planesA, planesB;       // plane bases (device), used to encode the maps
-    uint64_t zA, zB;                 // device int32[n_inst]: first plane index of each instance
-    uint64_t ptrC;                   // device array of n_inst output addresses (complex64)
+    uint64_t zA, zB;                 // device int32[n_inst]: first plane index of each block's groups
+    uint64_t ptrC;                   // device array of the node instances' output addresses (complex64)
     uint64_t status;                 // device uint32 error word (bounded-wait time-outs)
-    uint64_t scaleA, scaleB;         // FP16X3: 2^-s per [instance][K chunk][row] of each operand
-    int64_t M, N, K;
-    int64_t m_pad, n_pad, k_pad;
+    uint64_t scaleA, scaleB;         // FP16X3: 2^-s per [group][K chunk][row] of each operand
+    uint64_t itab;                   // device int32[n_inst * nA * nB], or 0
+    int64_t M, N, K;                 // rows and columns of one block, summed extent
+    int64_t m_pad, n_pad, k_pad;     // rows of an A group's planes, of a B group's, padded K
+    int64_t Mi, Ni;                  // rows and columns of one node instance
     int64_t planesA_total, planesB_total;   // plane count along the maps' third dimension
-    int32_t n_inst, mode;
-    int32_t n_kb, pad_;
+    int32_t n_inst, mode;            // blocks
+    int32_t n_kb, nA;
+    int32_t nB, pad_;
 };

@@ -23,7 +23,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
            "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices",
            "jet_network_keep_shared", "jet_network_save_shared", "jet_network_load_shared", "jet_plan_buffers",
-           "jet_plan_ranges"]
+           "jet_plan_ranges", "jet_sum_partials"]
 
 
 class JetError(RuntimeError):
@@ -35,7 +35,7 @@ class JetError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("gemm_min_k", ctypes.c_int64), ("workspace_limit", ctypes.c_int64),
-                ("profile", ctypes.c_int32), ("apply_tc_min_kf", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("apply_tc_min_kf", ctypes.c_int32), ("gemm_group", ctypes.c_int32)]
 
 
 class OpRecord(ctypes.Structure):
@@ -109,6 +109,7 @@ def lib():
             "jet_profile": (I32, [P, P, I32, P]),
             "jet_plan_buffers": (I32, [P, P, I32, P]),
             "jet_plan_ranges": (I32, [P, I32, P, ctypes.c_size_t, P, P, P, P, P]),
+            "jet_sum_partials": (I32, [I32, I64, I64, P, P]),
             "jet_pair_contract_noalloc": (I32, [I32, P, P, P, I32, P, P, P, P, I32, P]),
             "jet_network_destroy": (None, [P]),
             "jet_last_error": (ctypes.c_char_p, []),
@@ -127,7 +128,7 @@ def _check(rc: int):
 
 
 def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=16, profile=0,
-                    apply_tc_min_kf=1024, workspace_limit=0) -> Options:
+                    apply_tc_min_kf=1024, workspace_limit=0, gemm_group=True) -> Options:
     o = Options()
     lib().jet_options_default(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -138,6 +139,7 @@ def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm
     o.profile = int(profile)
     o.apply_tc_min_kf = int(apply_tc_min_kf)
     o.workspace_limit = int(workspace_limit)
+    o.gemm_group = int(bool(gemm_group))
     return o
 
 
@@ -381,6 +383,18 @@ def pair_contract_noalloc(labels_a, shape_a, a_dev_ptr: int, labels_b, shape_b, 
     _check(lib().jet_pair_contract_noalloc(la.size, la.ctypes.data, da.ctypes.data, ctypes.c_void_p(a_dev_ptr),
                                            lb.size, lb.ctypes.data, db.ctypes.data, ctypes.c_void_p(b_dev_ptr),
                                            ctypes.c_void_p(c_dev_ptr), int(device), ctypes.c_void_p(stream)))
+
+
+def sum_partials(partials: np.ndarray) -> np.ndarray:
+    """jet_sum_partials: partials[b, j(, e)] summed over j in increasing order, FP64."""
+    p = np.ascontiguousarray(np.asarray(partials, dtype=np.complex128))
+    if p.ndim == 2:
+        p = p[:, :, None]
+    n_amps, n_ids, n_elem = p.shape
+    out = np.zeros((n_amps, n_elem), dtype=np.complex128)
+    _check(lib().jet_sum_partials(n_amps, n_ids, max(n_elem, 1), p.ctypes.data if p.size else None,
+                                  out.ctypes.data))
+    return out[:, 0] if np.ndim(partials) == 2 else out
 
 
 def from_network(tn, **opt_kwargs) -> Network:

@@ -30,16 +30,21 @@ def slice_ranges(n_slices: int, world: int) -> List[Tuple[int, int]]:
 
 def ordered_sum(partials_by_rank: Sequence[np.ndarray], ranges: Sequence[Tuple[int, int]]) -> np.ndarray:
     """amp_b = sum over slice ids in increasing order of the gathered partials
-    (rank r's array is n_amps x (stop_r - start_r))."""
+    (rank r's array is n_amps x (stop_r - start_r)): the ranks' partials are
+    concatenated in increasing slice id and summed by the library
+    (jet_sum_partials, FP64, in that order)."""
+    from .jet import sum_partials
     n_amps = next((p.shape[0] for p in partials_by_rank if p.size), 0)
-    acc = np.zeros(n_amps, dtype=np.complex128)
+    parts = []
     for (start, stop), p in sorted(zip(ranges, partials_by_rank), key=lambda x: x[0][0]):
         if stop <= start:
             continue
-        assert p.shape[1] == stop - start
-        for j in range(p.shape[1]):
-            acc += p[:, j]
-    return acc
+        if p.shape[1] != stop - start:
+            raise ValueError("a rank's partials do not match its slice range")
+        parts.append(np.asarray(p, np.complex128))
+    if not parts:
+        return np.zeros(n_amps, dtype=np.complex128)
+    return sum_partials(np.concatenate(parts, axis=1))
 
 
 def gather_partials(local: np.ndarray, world: int, group=None) -> List[np.ndarray]:

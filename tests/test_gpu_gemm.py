@@ -98,3 +98,56 @@ def test_gemm_batched_instances_under_slicing():
     err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
     net.close()
     assert err <= 1e-5, err
+
+
+# Grouped instance blocks: the instances of a GEMM node that pair every
+# instance of one operand with the same instances of the other run as one wider
+# product (rows j * M + m, columns l * N + n).  The sliced labels s* sit on one
+# operand each (a full product of instances), x on both (instances pair only
+# when x agrees: two blocks); the small tensors joining them are absorbed after
+# the pair, and every free value is compared with the oracle.
+GROUPED = {
+    # M = 64 per instance, 2 x 2 instances: one block of 128 x 512
+    "m64_2x2": (list(range(0, 6)) + list(range(10, 17)) + [40], list(range(10, 17)) + list(range(20, 28)) + [41],
+                [[40, 41]], [40, 41]),
+    # N = 32 per instance (a skinny side filling a quarter of a tile), 4 x 2 instances
+    "n32_4x2": (list(range(0, 12)) + list(range(10 + 20, 18 + 20)) + [40, 42],
+                list(range(30, 38)) + list(range(20, 25)) + [41], [[40, 41], [42]], [40, 41, 42]),
+    # a sliced label x (50) on both operands: 2 blocks of 2 x 2
+    "shared_x": (list(range(0, 7)) + list(range(10, 17)) + [50, 40], list(range(10, 17)) + list(range(20, 27)) + [50, 41],
+                 [[40, 41]], [50, 40, 41]),
+}
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "bf16x6", "tf32"])
+@pytest.mark.parametrize("case", sorted(GROUPED))
+def test_gemm_grouped_instance_blocks(prec, case):
+    la, lb, extra, sliced = GROUPED[case]
+    rng = SplitMix64(77 + sorted(GROUPED).index(case))
+    A = _rand(rng, [2] * len(la))
+    B = _rand(rng, [2] * len(lb))
+    X = [_rand(rng, [2] * len(e)) for e in extra]
+    labels = [la, lb] + extra
+    opens = [l for l in la if l not in lb and not any(l in e for e in extra)] + \
+            [l for l in lb if l not in la and not any(l in e for e in extra)]
+    net = jet.Network(labels, [A, B] + X, precision=prec, profile=2)
+    try:
+        net.set_open(opens)
+        net.set_free(opens)
+        path = [(0, 1)]
+        cur = len(labels)
+        for i in range(2, len(labels)):
+            path.append((cur, i))
+            cur += 1
+        net.path_set(path)
+        net.slice(sliced)
+        got = net.contract(np.zeros((1, len(opens)), np.int32))[0]
+        gem = [r for r in net.profile() if r["kind"] == "gemm_tc" and r["node"] == len(labels)]
+    finally:
+        net.close()
+    assert gem and all(r["variant"] & 1 for r in gem), gem   # the pair ran as grouped blocks
+    out, ref = contract_network(labels, [A, B] + X, path)
+    ref = np.transpose(np.asarray(ref), [out.index(l) for l in opens]).ravel()
+    err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+    print(f"grouped {case} {prec}: max elementwise err {err:.3e}")
+    assert err <= TOL[prec], err
