@@ -964,34 +964,43 @@ def run_impl(args):
 
 def run_gemm_case(args):
     """One pairwise contraction node, large enough to exceed L2 but small enough
-    for an ncu capture: C[M x N] = A[M x K] B[K x N] complex64 for each of INST
-    instances of A (sliced labels) sharing one B, in the chosen precision.
-    Default 8192 x 8192 x 2048, one instance; --gemm-shape M,N,K,INST (powers of two)."""
+    for an ncu capture: C[M x N] = A[M x K] B[K x N] complex64 for IA instances
+    of A and IB of B (sliced labels on each operand, joined by one small tensor
+    absorbed after the pair), every pair an instance of the node, in the chosen
+    precision; --gemm-shape M,N,K,IA[,IB] (powers of two), --gemm-group 0 runs
+    each instance as its own product."""
     import torch
     from circuits import SplitMix64
     from paper_2107_09793_b300 import jet
     torch.cuda.set_device(0)
-    gm, gn, gk, gi = [int(x) for x in args.gemm_shape.split(",")]
+    shape = [int(x) for x in args.gemm_shape.split(",")]
+    gm, gn, gk, ia = shape[:4]
+    ib = shape[4] if len(shape) > 4 else 1
     lg = lambda v: int(round(np.log2(v)))
-    ri = lg(gi)
-    rm, rk, rn = lg(gm) + ri, lg(gk), lg(gn)
-    la = list(range(rm)) + list(range(100, 100 + rk))
-    lb = list(range(100, 100 + rk)) + list(range(200, 200 + rn))
+    rm, rk, rn, ra, rb = lg(gm), lg(gk), lg(gn), lg(ia), lg(ib)
+    sa, sb = list(range(300, 300 + ra)), list(range(400, 400 + rb))
+    la = sa + list(range(rm)) + list(range(100, 100 + rk))
+    lb = list(range(100, 100 + rk)) + list(range(200, 200 + rn)) + sb
     rng = np.random.default_rng(SplitMix64(9).next_u64() % (1 << 32))
-    A = (rng.random([2] * len(la)) - 0.5 + 1j * (rng.random([2] * len(la)) - 0.5)).astype(np.complex64)
-    B = (rng.random([2] * len(lb)) - 0.5 + 1j * (rng.random([2] * len(lb)) - 0.5)).astype(np.complex64)
-    # the pair is one GEMM node; a rank-1 selector on each free leg closes the network
-    sel = [np.ones(2, np.complex64)] * (rm + rn)
-    labels = [la, lb] + [[l] for l in list(range(rm)) + list(range(200, 200 + rn))]
-    net = jet.Network(labels, [A, B] + sel, precision=args.precision, profile=1)
+    rnd = lambda r: (rng.random([2] * r) - 0.5 + 1j * (rng.random([2] * r) - 0.5)).astype(np.complex64)
+    A, B = rnd(len(la)), rnd(len(lb))
+    labels, data = [la, lb], [A, B]
+    if sa or sb:
+        labels.append(sa + sb)
+        data.append(rnd(len(sa + sb)))
+    # a rank-1 selector on each free leg closes the network
+    for l in list(range(rm)) + list(range(200, 200 + rn)):
+        labels.append([l])
+        data.append(np.ones(2, np.complex64))
+    net = jet.Network(labels, data, precision=args.precision, profile=1, gemm_group=bool(args.gemm_group))
     net.set_open([])
     path, cur = [(0, 1)], len(labels)
     for i in range(2, len(labels)):
         path.append((cur, i))
         cur += 1
     net.path_set(path)
-    if ri:
-        net.slice(list(range(ri)))   # the slowest M labels of A: INST instances of the GEMM node
+    if sa or sb:
+        net.slice(sa + sb)
     outs = np.zeros((1, 0), np.int32)
     amps = torch.zeros(1, dtype=torch.complex128, device="cuda")
     sh = torch.cuda.current_stream().cuda_stream
@@ -1001,10 +1010,12 @@ def run_gemm_case(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             ms += [r["ms"] for r in net.profile() if r["kind"] in ("gemm_tc", "gemm_simt")]
-    flop = 8.0 * 2 ** (rm + rk + rn)
+    flop = 8.0 * 2 ** (rm + rk + rn) * ia * ib
     t = statistics.mean(ms) * 1e-3
-    print(json.dumps({"case": f"gemm M={gm} N={gn} K={gk} x {gi} instances, complex", "precision": args.precision,
+    print(json.dumps({"case": f"gemm M={gm} N={gn} K={gk} x {ia} A x {ib} B instances, complex",
+                      "precision": args.precision, "gemm_group": int(args.gemm_group),
                       "gemm_ms": t * 1e3, "algorithmic_tflops": flop / t / 1e12}), flush=True)
+    net.close()
     return 0
 
 
@@ -1071,7 +1082,8 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
     ap.add_argument("--skip-others", action="store_true", help="skip the other workloads (bosonic lattice, "
                     "parameterised circuit gradient, 53-qubit slices)")
-    ap.add_argument("--gemm-shape", default="8192,8192,2048,1", help="--case gemm: M,N,K,INST")
+    ap.add_argument("--gemm-shape", default="8192,8192,2048,1", help="--case gemm: M,N,K,IA[,IB]")
+    ap.add_argument("--gemm-group", type=int, default=1, help="--case gemm: 1 groups instance pairs into blocks")
     ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16"],
                     help="gemm / apply: one kernel family on a case sized for ncu captures; "
                          "gbs16: only the bosonic batch")

@@ -510,51 +510,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             const uint64_t *ptrC = (const uint64_t *)a.ptrC;
             const bool grouped = a.itab != 0;
             const int64_t col0 = (int64_t)tn * TC_BN + half * 64;
-            // output address of block entry (R, c): instance `inst` itself, or, for a
-            // block of grouped instances, the instance that (R, c) falls in (null
-            // where that pair is not an instance of the node)
-            auto out_ptr = [&](int64_t R, int64_t c) -> float2 * {
-                if (!grouped) return (float2 *)ptrC[inst] + R * a.N + c;
-                const int64_t jj = R / a.Mi, m = R - jj * a.Mi;
-                const int64_t l = c / a.Ni, n = c - l * a.Ni;
-                const int32_t it = ((const int32_t *)a.itab)[((int64_t)inst * a.nA + jj) * a.nB + l];
-                return it < 0 ? nullptr : (float2 *)ptrC[it] + m * a.Ni + n;
+            const int32_t *itab = (const int32_t *)a.itab;
+            // a block entry (R, c) is entry (m, n) of instance itab[(inst nA + j) nB + l]
+            // with R = j Mi + m and c = l Ni + n (shifts for power-of-two Mi, Ni)
+            auto split_row = [&](int64_t R, int64_t &jj, int64_t &mm) {
+                if (a.mi_shift >= 0) {
+                    jj = R >> a.mi_shift;
+                    mm = R & (a.Mi - 1);
+                } else {
+                    jj = R / a.Mi;
+                    mm = R - jj * a.Mi;
+                }
+            };
+            auto split_col = [&](int64_t c, int64_t &ll, int64_t &nn) {
+                if (a.ni_shift >= 0) {
+                    ll = c >> a.ni_shift;
+                    nn = c & (a.Ni - 1);
+                } else {
+                    ll = c / a.Ni;
+                    nn = c - ll * a.Ni;
+                }
+            };
+            // the output base of (j, l), looked up again only when (j, l) changes
+            // (rows and columns of a tile mostly share one instance)
+            int64_t cj = -1, cl = -1;
+            float2 *cptr = grouped ? nullptr : (float2 *)ptrC[inst];
+            auto inst_ptr = [&](int64_t jj, int64_t ll) -> float2 * {
+                if (!grouped) return cptr;
+                if (jj != cj || ll != cl) {
+                    cj = jj;
+                    cl = ll;
+                    const int32_t it = __ldg(itab + ((int64_t)inst * a.nA + jj) * a.nB + ll);
+                    cptr = it < 0 ? nullptr : (float2 *)__ldg((const unsigned long long *)ptrC + it);
+                }
+                return cptr;
             };
             if (tc_cstage<MODE>() && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
                 // whole 64-column half tile in range: stage 16 columns at a time (a
-                // 16-column group lies in one instance)
+                // 16-column group lies in one instance); each lane stores 8 rows
                 float2 *st = (float2 *)(smem + (size_t)S * STAGE_BYTES) + (size_t)(warp - 2) * 32 * TC_CST_ROW;
                 const int64_t row0 = (int64_t)tm * TC_BM + quarter * 32;
+                const int cc = (lane & 7) * 2;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) st[lane * TC_CST_ROW + j] = make_float2(racc[p * 16 + j], iacc[p * 16 + j]);
                     __syncwarp();
+                    int64_t lq = 0, nq = col0 + p * 16 + cc;
+                    if (grouped) split_col(col0 + p * 16 + cc, lq, nq);
 #pragma unroll
                     for (int it = 0; it < 8; ++it) {
-                        const int r = it * 4 + (lane >> 3), cc = (lane & 7) * 2;
+                        const int r = it * 4 + (lane >> 3);
                         if (row0 + r < a.M) {
-                            float2 *dst = out_ptr(row0 + r, col0 + p * 16 + cc);
+                            int64_t jj = 0, mm = row0 + r;
+                            if (grouped) split_row(row0 + r, jj, mm);
+                            float2 *C = inst_ptr(jj, lq);
                             const float2 v0 = st[r * TC_CST_ROW + cc], v1 = st[r * TC_CST_ROW + cc + 1];
-                            if (dst) *(float4 *)dst = make_float4(v0.x, v0.y, v1.x, v1.y);
+                            if (C) *(float4 *)(C + mm * a.Ni + nq) = make_float4(v0.x, v0.y, v1.x, v1.y);
                         }
                     }
                     __syncwarp();
                 }
             } else if (row < a.M) {
+                int64_t jj = 0, mm = row, ll = 0, nn = col0;
+                if (grouped) {
+                    split_row(row, jj, mm);
+                    split_col(col0, ll, nn);
+                }
                 if ((a.Ni & 1) == 0 && col0 + 64 <= a.N) {
 #pragma unroll
                     for (int j = 0; j < 64; j += 2) {
-                        float2 *dst = out_ptr(row, col0 + j);
-                        if (dst) *(float4 *)dst = make_float4(racc[j], iacc[j], racc[j + 1], iacc[j + 1]);
+                        float2 *C = inst_ptr(jj, ll);
+                        if (C) *(float4 *)(C + mm * a.Ni + nn) = make_float4(racc[j], iacc[j], racc[j + 1], iacc[j + 1]);
+                        nn += 2;
+                        if (nn >= a.Ni) {
+                            nn -= a.Ni;
+                            ++ll;
+                        }
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 64; ++j)
+                    for (int j = 0; j < 64; ++j) {
                         if (col0 + j < a.N) {
-                            float2 *dst = out_ptr(row, col0 + j);
-                            if (dst) *dst = make_float2(racc[j], iacc[j]);
+                            float2 *C = inst_ptr(jj, ll);
+                            if (C) C[mm * a.Ni + nn] = make_float2(racc[j], iacc[j]);
                         }
+                        if (++nn >= a.Ni) {
+                            nn -= a.Ni;
+                            ++ll;
+                        }
+                    }
                 }
             }
         }

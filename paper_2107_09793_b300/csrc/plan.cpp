@@ -1450,6 +1450,14 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 g.Ni = Nv;
                 g.nA = G.nA;
                 g.nB = G.nB;
+                auto log2_or = [](int64_t x) {
+                    if (x < 1 || (x & (x - 1))) return -1;
+                    int sh = 0;
+                    while ((int64_t)1 << sh < x) ++sh;
+                    return sh;
+                };
+                g.mi_shift = log2_or(Mv);
+                g.ni_shift = log2_or(Nv);
                 g.m_pad = m_pad;
                 g.n_pad = n_pad;
                 g.k_pad = k_pad;

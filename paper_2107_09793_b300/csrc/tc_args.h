@@ -51,5 +51,6 @@ struct TcGemmArgs {
     int64_t planesA_total, planesB_total;   // plane count along the maps' third dimension
     int32_t n_inst, mode;            // blocks
     int32_t n_kb, nA;
-    int32_t nB, pad_;
+    int32_t nB, mi_shift;            // log2(Mi) and log2(Ni) when powers of two, else -1
+    int32_t ni_shift, pad_;
 };
