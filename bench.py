@@ -1049,6 +1049,36 @@ def run_apply_case(args):
     return 0
 
 
+def run_grid53_case(args):
+    """Only the headline contraction (the 53-qubit amplitude, every slice range,
+    --precision), warm-up + steps times: for a launch list of the step."""
+    import torch
+    from circuits import configs
+    from paper_2107_09793_b300 import jet
+    torch.cuda.set_device(0)
+    w = configs.build("grid53")
+    path, sliced, _ = grid53_plan(w)
+    free = torch.cuda.mem_get_info()[0]
+    ws = torch.empty(int(0.8 * free) // 256 * 256, dtype=torch.uint8, device="cuda")
+    net = jet.from_network(w.network, precision=args.precision)
+    net.path_set(path)
+    net.slice(sliced)
+    net.set_workspace(ws.data_ptr(), ws.numel())
+    amps = torch.zeros(1, dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        net.contract_async(w.outputs, amps.data_ptr(), stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms = _timed(lambda: net.contract_async(w.outputs, amps.data_ptr(), stream.cuda_stream), stream, ev0, ev1,
+                args.steps)
+    print(json.dumps({"case": "grid53: the whole amplitude", "precision": args.precision,
+                      "ms_per_amplitude": statistics.mean(ms), "amp": [amps[0].item().real, amps[0].item().imag]}),
+          flush=True)
+    net.close()
+    return 0
+
+
 def run_gbs16_case(args):
     """Only the 256-pattern bosonic batch (for a launch list of that workload)."""
     import torch
@@ -1084,9 +1114,9 @@ def main():
                     "parameterised circuit gradient, 53-qubit slices)")
     ap.add_argument("--gemm-shape", default="8192,8192,2048,1", help="--case gemm: M,N,K,IA[,IB]")
     ap.add_argument("--gemm-group", type=int, default=1, help="--case gemm: 1 groups instance pairs into blocks")
-    ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16"],
+    ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16", "grid53"],
                     help="gemm / apply: one kernel family on a case sized for ncu captures; "
-                         "gbs16: only the bosonic batch")
+                         "gbs16: only the bosonic batch; grid53: only the headline contraction")
     args = ap.parse_args()
     if args.case == "gemm":
         return run_gemm_case(args)
@@ -1094,6 +1124,8 @@ def main():
         return run_apply_case(args)
     if args.case == "gbs16":
         return run_gbs16_case(args)
+    if args.case == "grid53":
+        return run_grid53_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_impl(args)

@@ -450,6 +450,19 @@ int jet_plan_buffers(const jet_network *net, jet_buffer_record *out, int32_t cap
 /* Statistics of the network and the last plan (see jet_stats_t). */
 int jet_stats(const jet_network *net, jet_stats_t *out);
 
+/* Self-test of the bounded device-side waits (the tensor-core kernels give up
+ * a wait after ~2 s, record it in the network's status word, release their
+ * tensor memory and return; a contraction then fails with JET_ETIMEOUT).  One
+ * CTA on the network's device, on cuda_stream, allocates tensor memory, waits
+ * with the same bounded-wait helper on an mbarrier that nothing arrives on,
+ * gives up after limit_us microseconds, records the time-out, frees the tensor
+ * memory and returns; the call reads and clears the status word.  Nothing is
+ * left in flight and the handle stays usable.  Returns JET_ETIMEOUT (the
+ * expected outcome: the wait ran out and was reported), JET_ECUDA if the wait
+ * did not run out or the launch failed, JET_EINVAL (limit_us outside
+ * [1, 10^7]).  Synchronises cuda_stream.  Not in the paper. */
+int jet_selftest_wait(jet_network *net, int64_t limit_us, void *cuda_stream);
+
 /* Pairwise contraction of two dense tensors that allocates no device memory.
  * The paper has no counterpart; it serves callers that cannot call cudaMalloc:
  * a process whose GPU memory is pre-reserved by its own allocator (an

@@ -1085,6 +1085,17 @@ int jet_stats(const jet_network *net, jet_stats_t *out)
     });
 }
 
+int jet_selftest_wait(jet_network *net, int64_t limit_us, void *cuda_stream)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        if (limit_us < 1 || limit_us > 10000000) fail(JET_EINVAL, "limit_us must be in [1, 10^7]");
+        const int st = selftest_wait(*net, limit_us, cuda_stream);
+        if (st & 4) fail(JET_ETIMEOUT, "the bounded device-side wait ran out (self-test)");
+        fail(JET_ECUDA, "the self-test's wait completed although nothing arrives on its barrier");
+    });
+}
+
 int jet_pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_t *dims_a, const jet_c64 *a_dev,
                               int32_t rank_b, const int64_t *labels_b, const int32_t *dims_b, const jet_c64 *b_dev,
                               jet_c64 *c_dev, int32_t device, void *cuda_stream)

@@ -117,19 +117,21 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
         sKB[i] = gKB[i];
     }
     __syncthreads();
-    const int64_t inst = blockIdx.z;
+    const int64_t inst = blockIdx.z;   // P = 64: an instance block
     if (inst >= a.n_inst) return;
-    const V *__restrict__ A = (const V *)((const uint64_t *)a.ptrA)[inst];
-    const V *__restrict__ B = (const V *)((const uint64_t *)a.ptrB)[inst];
+    const int32_t *itab = (const int32_t *)a.itab;
+    const int nbk = P == 64 ? a.blk_na * a.blk_nb : 1;
+    const V *__restrict__ A = (const V *)((const uint64_t *)a.ptrA)[P == 64 ? itab[inst * nbk] : inst];
+    const V *__restrict__ B = (const V *)((const uint64_t *)a.ptrB)[P == 64 ? itab[inst * nbk] : inst];
     const int64_t out0 = (int64_t)blockIdx.y * JET_SPLITK_G;
-    const int nout = (int)((a.n_out - out0) < JET_SPLITK_G ? (a.n_out - out0) : JET_SPLITK_G);
+    const int nout = P == 64 ? nbk : (int)((a.n_out - out0) < JET_SPLITK_G ? (a.n_out - out0) : JET_SPLITK_G);
     int64_t oa[JET_SPLITK_G], ob[JET_SPLITK_G];
     V acc[JET_SPLITK_G];
 #pragma unroll
     for (int j = 0; j < JET_SPLITK_G; ++j) {
         oa[j] = ob[j] = 0;
         acc[j] = vzero<V>();
-        if (j < nout) {
+        if (j < (P == 64 ? 1 : nout)) {   // (an instance block has one output per instance)
             int64_t e = out0 + j;
             int64_t r = e / a.n_cols;
             int c = (int)(e - r * a.n_cols);
@@ -156,7 +158,42 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
         }
     };
     const int nklo = a.n_klo, bd = blockDim.x;
-    if (P == 32) {   // one output
+    if (P == 64) {   // dot products of an instance block: blk_na A vectors x blk_nb B vectors
+        constexpr int U = 4, MB = 4;   // at most 4 of each (and 8 products)
+        const int na = a.blk_na, nb = a.blk_nb;
+        const V *__restrict__ Aj[MB];
+        const V *__restrict__ Bl[MB];
+#pragma unroll
+        for (int j = 0; j < MB; ++j) {
+            Aj[j] = j < na ? (const V *)((const uint64_t *)a.ptrA)[itab[inst * nbk + j * nb]] + oa[0] : A;
+            Bl[j] = j < nb ? (const V *)((const uint64_t *)a.ptrB)[itab[inst * nbk + j]] + ob[0] : B;
+        }
+        for (int64_t h = h0; h < h1; ++h) {
+            int64_t ha, hb;
+            h_offsets(h, ha, hb);
+            for (int q0 = threadIdx.x; q0 < nklo; q0 += U * bd) {
+                V xa[U][MB], xb[U][MB];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int q = q0 + u * bd;
+                    const bool ok = q < nklo;
+                    const int64_t ka = ha + (ok ? sKA[q] : 0), kb = hb + (ok ? sKB[q] : 0);
+#pragma unroll
+                    for (int j = 0; j < MB; ++j) {
+                        xa[u][j] = ok && j < na ? __ldg(Aj[j] + ka) : vzero<V>();
+                        xb[u][j] = ok && j < nb ? __ldg(Bl[j] + kb) : vzero<V>();
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (q0 + u * bd < nklo) {
+#pragma unroll
+                        for (int t = 0; t < JET_SPLITK_G; ++t)
+                            if (t < nbk) acc[t] = cmul_add(acc[t], xa[u][t / nb], xb[u][t % nb]);
+                    }
+            }
+        }
+    } else if (P == 32) {   // one output
         constexpr int U = 8;
         const V *__restrict__ A0 = A + oa[0];
         const V *__restrict__ B0 = B + ob[0];
@@ -250,7 +287,8 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
             s.y += red[threadIdx.x][w].y;
         }
         V *part = (V *)a.partials;
-        part[(inst * a.ksplit + blockIdx.x) * a.n_out + out0 + threadIdx.x] = s;
+        if (P == 64) part[(int64_t)itab[inst * nbk + threadIdx.x] * a.ksplit + blockIdx.x] = s;   // one output each
+        else part[(inst * a.ksplit + blockIdx.x) * a.n_out + out0 + threadIdx.x] = s;
     }
 }
 
@@ -460,8 +498,11 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
     bool fp64 = c.variant & 1, splitk = c.variant & 2, pow2 = c.variant & 4;
     size_t smem = c.smem;
     const int na = a.splitk_na;
-    if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20 && na != 32) ||
-                    (na == 32 ? a.n_out != 1 : a.n_out % JET_SPLITK_G != 0)))
+    if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20 && na != 32 && na != 64) ||
+                    (na >= 32 ? a.n_out != 1 : a.n_out % JET_SPLITK_G != 0)))
+        return cudaErrorInvalidValue;
+    if (na == 64 && (!a.itab || a.blk_na < 1 || a.blk_nb < 1 || a.blk_na > 4 || a.blk_nb > 4 ||
+                     a.blk_na * a.blk_nb > JET_SPLITK_G || c.gy != 1))
         return cudaErrorInvalidValue;
 #define JET_DIRECT_LAUNCH(V, P)                                                                 \
     do {                                                                                        \
@@ -474,6 +515,7 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
             case 18: direct_splitk_kernel<V, P, 18><<<grid, c.block, smem, s>>>(a); break;      \
             case 20: direct_splitk_kernel<V, P, 20><<<grid, c.block, smem, s>>>(a); break;      \
             case 32: direct_splitk_kernel<V, P, 32><<<grid, c.block, smem, s>>>(a); break;      \
+            case 64: direct_splitk_kernel<V, P, 64><<<grid, c.block, smem, s>>>(a); break;      \
             default: direct_splitk_kernel<V, P, 0><<<grid, c.block, smem, s>>>(a); break;       \
             }                                                                                   \
         } else direct_kernel<V, P><<<grid, c.block, smem, s>>>(a);                              \

@@ -262,6 +262,9 @@ bool gemm_available(int32_t precision);
 int read_clear_status(Network &net, void *stream);
 float op_elapsed_ms(const Plan &plan, size_t i);
 
+// selftest.cu: the bounded-wait self-test; returns the status word it left (and clears it)
+int selftest_wait(Network &net, int64_t limit_us, void *stream);
+
 // noalloc.cu
 void pair_contract_noalloc(int32_t rank_a, const int64_t *labels_a, const int32_t *dims_a, const void *a_dev,
                            int32_t rank_b, const int64_t *labels_b, const int32_t *dims_b, const void *b_dev,

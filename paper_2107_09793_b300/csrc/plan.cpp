@@ -1008,6 +1008,30 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             // (fewest loads first: NA = 2 or 4 take 6, NA = 1 or 8 take 9); A's
             // values fastest (pattern NA) or B's (pattern 16 + NB)
             if (d.ksplit > 1 && d.n_out == 1) d.splitk_na = 32;   // a dot product
+            // dot products whose instances pair every A instance of a block with the
+            // same B instances (at most 4 x 4, 8 products): one block of threads
+            // loads each operand value once for all of the block's products
+            std::vector<int32_t> blk_itab;
+            int64_t n_launch_inst = n_inst;
+            if (d.splitk_na == 32 && n_inst > 1) {
+                GemmGroups G;
+                const std::vector<int32_t> &ia = node[v].ia, &ib = node[v].ib;
+                bool ok = (int64_t)ia.size() == n_inst && group_instances(ia, ib, true, G) && G.dup == 0;
+                if (!ok && (int64_t)ia.size() == n_inst) ok = group_instances(ia, ib, false, G) && G.dup == 0;
+                if (ok && G.nA * G.nB >= 2 && G.nA <= 4 && G.nB <= 4 && G.nA * G.nB <= JET_SPLITK_G) {
+                    d.splitk_na = 64;
+                    d.blk_na = G.nA;
+                    d.blk_nb = G.nB;
+                    blk_itab = G.itab;
+                    n_launch_inst = (int64_t)G.bM.size();
+                    // as many parts again as the blocks need to fill the same waves
+                    const int64_t waves = n_k >= (1 << 20) ? 4 : 1;
+                    const int64_t want = std::max<int64_t>(2, (148 * 8 * waves + n_launch_inst - 1) / n_launch_inst);
+                    const int64_t parts = std::min<int64_t>(want, d.n_khi);
+                    d.khi_per_part = (int32_t)((d.n_khi + parts - 1) / parts);
+                    d.ksplit = (int32_t)((d.n_khi + d.khi_per_part - 1) / d.khi_per_part);
+                }
+            }
             if (d.ksplit > 1 && d.n_out % JET_SPLITK_G == 0 && d.n_out <= (1 << 16)) {
                 std::vector<int64_t> eA(d.n_out), eB(d.n_out);
                 for (int64_t e = 0; e < d.n_out; ++e) {
@@ -1039,6 +1063,17 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             size_t off_colA = blob.put_i32(colA), off_colB = blob.put_i32(colB);
             size_t off_kA = blob.put_i32(kA), off_kB = blob.put_i32(kB);
             size_t off_pa = blob.put_ptrs(pa), off_pb = blob.put_ptrs(pb), off_pc = blob.put_ptrs(pc);
+            size_t off_itab = blk_itab.empty() ? 0 : blob.put_i32(blk_itab);
+            if (!blk_itab.empty()) d.n_inst = (int32_t)n_launch_inst;   // the kernel's blocks
+            // bytes the launch must move: every distinct operand instance once (an
+            // instance block reads a shared operand once for all its pairs)
+            double op_bytes = bytes;
+            if (!blk_itab.empty()) {
+                const NodeInfo &N = node[v];
+                op_bytes = (double)es * ((double)node[N.a].n_inst * (double)node[N.a].view.size +
+                                         (double)node[N.b].n_inst * (double)node[N.b].view.size +
+                                         (double)n_inst * (double)Cv.size);
+            }
             size_t part_off = 0, part_bytes = 0;
             if (d.ksplit > 1) {
                 part_bytes = (size_t)n_inst * d.ksplit * d.n_out * es;
@@ -1056,6 +1091,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             blob.patch_field(so, offsetof(DirectArgs, kA), BASE_BLOB, (int64_t)off_kA);
             blob.patch_field(so, offsetof(DirectArgs, kB), BASE_BLOB, (int64_t)off_kB);
             if (d.ksplit > 1) blob.patch_field(so, offsetof(DirectArgs, partials), BASE_ARENA, (int64_t)part_off);
+            if (!blk_itab.empty()) blob.patch_field(so, offsetof(DirectArgs, itab), BASE_BLOB, (int64_t)off_itab);
             Op op;
             op.kind = OpKind::Direct;
             op.node = v;
@@ -1063,7 +1099,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             op.args_off = so;
             op.args_bytes = sizeof(DirectArgs);
             op.flop = flop;
-            op.bytes = bytes;
+            op.bytes = op_bytes;
             op.variant = fp64 ? 1 : 0;
             bool pow2 = true;
             for (int j = 0; j < d.row_rank; ++j) pow2 = pow2 && (d.row_dim[j] & (d.row_dim[j] - 1)) == 0;
@@ -1073,7 +1109,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             if (d.ksplit > 1) {
                 op.grid_x = d.ksplit;
                 op.grid_y = (int32_t)((d.n_out + JET_SPLITK_G - 1) / JET_SPLITK_G);
-                op.grid_z = (int32_t)std::min<int64_t>(n_inst, 65535);
+                op.grid_z = (int32_t)std::min<int64_t>(n_launch_inst, 65535);
                 op.variant |= 2 | (d.splitk_na << 8);   // the outer-product factor, for the launch records
             } else {
                 int64_t blocks = (d.n_out + 255) / 256;
@@ -1088,7 +1124,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 SplitKReduceArgs r;
                 std::memset(&r, 0, sizeof r);
                 r.n_out = d.n_out;
-                r.n_inst = d.n_inst;
+                r.n_inst = (int32_t)n_inst;   // partials are per node instance in every form
                 r.ksplit = d.ksplit;
                 size_t ro = blob.reserve(sizeof r);
                 std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
@@ -1488,7 +1524,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 op.args_off = so;
                 op.args_bytes = sizeof g;
                 op.flop = flop;
-                op.bytes = bytes;
+                // grouped blocks read every operand instance once per launch: the
+                // bytes to move are those of the distinct operand instances
+                op.bytes = grouped ? (double)es * ((double)node[idM].n_inst * VM.size + (double)node[idN].n_inst * VN.size +
+                                                   (double)N.n_inst * N.view.size)
+                                   : bytes;
                 op.grid_x = (int32_t)(n_pad / T);
                 op.grid_y = (int32_t)(m_pad / T);
                 op.grid_z = (int32_t)n_blocks;   // persistent launch: the tile count only

@@ -38,9 +38,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: gives up after ~2 s of wall time (or when another role of the
-// CTA has already given up) and returns false.
-static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+// Bounded wait: gives up after limit_ns of wall time (~2 s by default), when
+// another role of the CTA has already given up, or after 2^30 polls, and
+// returns false.
+static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                                      uint64_t limit_ns = 2000000000ull)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
@@ -48,7 +50,7 @@ static __device__ __noinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t par
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255) == 0) {
             if (*abort_flag) return false;
-            if (globaltimer() - t0 > 2000000000ull) return false;
+            if (globaltimer() - t0 > limit_ns) return false;
         }
     }
     return false;

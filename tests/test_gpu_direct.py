@@ -77,3 +77,38 @@ def test_split_k_forms(case, prec, tol):
     print(f"{case} {prec}: NA {na}, rel err {err:.2e}")
     assert err <= tol
     net.close()
+
+
+# Dot products of instance blocks: A[x, y, k...] and B[x, z, k...] with x, y, z
+# sliced (x on both operands, y and z joined by Y after the pair).  The pair's
+# 8 instances (x, y, z) form 2 blocks (x = 0, 1) of 2 A instances (y) x 2 B
+# instances (z); each block's 4 dot products read every operand value once.
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-13)])
+def test_split_k_instance_block_dot_products(prec, tol):
+    from oracle.einsum import slice_network
+    x, y, z = 200, 201, 202
+    la, lb = [x, y] + K[:8] + K[8:], [x, z] + K[8:] + K[:8]
+    A = _rand(7001, [2] * len(la)).astype(np.complex64)
+    B = _rand(7002, [2] * len(lb)).astype(np.complex64)
+    Y = _rand(7003, [2, 2]).astype(np.complex64)
+    labels, data = [la, lb, [y, z]], [A, B, Y]
+    net = jet.Network(labels, data, precision=prec, profile=2)
+    try:
+        net.set_open([])
+        net.path_set([(0, 1), (3, 2)])
+        net.slice([x, y, z])
+        got = net.contract_slices(np.zeros((1, 0), np.int32), list(range(8)))[0]
+        recs = [r for r in net.profile() if r["kind"] == "direct" and r["node"] == 3]
+    finally:
+        net.close()
+    assert len(recs) == 1 and recs[0]["variant"] >> 8 == 64 and recs[0]["grid"][2] == 2, recs
+    d64 = [t.astype(np.complex128) for t in data]
+    ref = []
+    for s in range(8):
+        vals = [(s >> 2) & 1, (s >> 1) & 1, s & 1]
+        sl, sd = slice_network(labels, d64, [x, y, z], vals)
+        ref.append(complex(contract_network(sl, sd, [(0, 1), (3, 2)])[1]))
+    ref = np.array(ref)
+    err = float(np.max(np.abs(got - ref) / np.abs(ref)))
+    print(f"block dot products {prec}: max per-slice rel err {err:.2e}")
+    assert err <= tol

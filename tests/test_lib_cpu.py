@@ -433,3 +433,22 @@ def test_arena_liveness_catches_a_planted_overlap():
                 net.close()
                 return
     pytest.fail("no two buffers live at once")
+
+
+def test_selftest_wait_rejects_bad_limits_before_any_device_work():
+    w, net = _net()
+    for bad in (0, -5, 10 ** 8):
+        with pytest.raises(jet.JetError) as e:
+            net.selftest_wait(bad)
+        assert e.value.code == jet.JET_EINVAL
+
+
+def test_sum_partials_adds_in_increasing_slice_order():
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal((3, 7, 2)) + 1j * rng.standard_normal((3, 7, 2))
+    got = jet.sum_partials(p)
+    ref = np.zeros((3, 2), np.complex128)
+    for j in range(7):
+        ref += p[:, j, :]
+    assert got.tobytes() == ref.tobytes()   # the same FP64 order, bit for bit
+    assert np.array_equal(jet.sum_partials(p[:, :0, :]), np.zeros((3, 2)))
