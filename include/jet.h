@@ -450,6 +450,27 @@ int jet_plan_buffers(const jet_network *net, jet_buffer_record *out, int32_t cap
 /* Statistics of the network and the last plan (see jet_stats_t). */
 int jet_stats(const jet_network *net, jet_stats_t *out);
 
+/* Autotuner (not in the paper): for the contraction of these outputs, choose
+ * per tree node between the kernel forms that both take the node's shape --
+ * the GEMM route's instance blocks or one product per instance, and a small
+ * operand's tensor-core application or its CUDA-core form -- by timing them on
+ * the device.  Two timed runs (each the second of two, CUDA events around every
+ * launch): every tunable node in its default form, then every one in its
+ * other form; a node takes the other form where that ran at least 3% faster,
+ * and the choices are kept only if a third run of the whole plan is not slower
+ * than the defaults by more than 2%.  A contraction that runs in slice ranges
+ * is tuned on its first range (every range has the same launches).  The
+ * choices hold for the current path and slicing (any contraction plans with
+ * them from then on) and are stored in cache_file (HOST path, may be NULL; one
+ * "signature choice" line per node shape: precision, form kind and the node's
+ * extents and instance counts), which a later call reads first: when every
+ * tunable node's shape is there, no alternative is timed.  default_ms /
+ * tuned_ms (may be NULL): device time of the default and the tuned plan;
+ * n_changed: nodes that left their default form.  Synchronises cuda_stream.
+ * Errors: as jet_contract. */
+int jet_autotune(jet_network *net, int32_t n_amps, const int32_t *outputs, const char *cache_file,
+                 void *cuda_stream, double *default_ms, double *tuned_ms, int32_t *n_changed);
+
 /* Self-test of the bounded device-side waits (the tensor-core kernels give up
  * a wait after ~2 s, record it in the network's status word, release their
  * tensor memory and return; a contraction then fails with JET_ETIMEOUT).  One

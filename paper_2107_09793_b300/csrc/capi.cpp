@@ -7,6 +7,7 @@
 #include <cstring>
 #include <functional>
 #include <exception>
+#include <map>
 #include <new>
 #include <numeric>
 #include <string>
@@ -1082,6 +1083,123 @@ int jet_stats(const jet_network *net, jet_stats_t *out)
             if (n_assign > 1 && per_assign > 0)
                 out->reuse_fraction = (noreuse - P.flop_executed) / ((n_assign - 1) * per_assign);
         }
+    });
+}
+
+int jet_autotune(jet_network *net, int32_t n_amps, const int32_t *outputs, const char *cache_file,
+                 void *cuda_stream, double *default_ms, double *tuned_ms, int32_t *n_changed)
+{
+    return guarded([&] {
+        if (!net) fail(JET_EINVAL, "net is NULL");
+        Network &N = *net;
+        // the slices a tuning run contracts: every slice, or the first range of the
+        // partition the workspace cap asks for (every range has the same launches)
+        Plan &Pfull = get_plan(N, n_amps, outputs);
+        const size_t cap = run_cap(N, Pfull);
+        std::vector<int64_t> ids;
+        const std::vector<int64_t> *idp = nullptr;
+        if (cap && Pfull.arena_bytes > cap && Pfull.n_slices > 1) {
+            RangeSet &RS = get_ranges(N, n_amps, outputs, cap);
+            ids = RS.ids[0];
+            idp = &ids;
+        }
+        N.tune.clear();
+        N.tune_path_version = N.path_version;
+        N.tune_slice_version = N.slice_version;
+        invalidate_plan(N);
+        // cache: one "signature choice" line per tunable shape
+        std::map<std::string, int> cache;
+        if (cache_file && *cache_file) {
+            if (FILE *f = std::fopen(cache_file, "r")) {
+                char key[512];
+                int val;
+                while (std::fscanf(f, "%511s %d", key, &val) == 2) cache[key] = val;
+                std::fclose(f);
+            }
+        }
+        // one timed run (the second of two) with every tunable node in its default
+        // form (flip 0) or its other one (flip 1): per-node and total device time
+        auto run = [&](int flip, std::map<int32_t, double> &node_ms, std::vector<Plan::Tunable> &tun) {
+            N.tune_flip = flip;
+            std::unique_ptr<Plan> P;
+            try {
+                P = build_plan(N, n_amps, outputs, idp);
+            } catch (...) {
+                N.tune_flip = 0;
+                throw;
+            }
+            N.tune_flip = 0;
+            const int32_t saved = N.opt.profile;
+            N.opt.profile = 2;
+            double total = 0;
+            try {
+                for (int rep = 0; rep < 2; ++rep) {
+                    bind_and_run(N, *P, nullptr, cuda_stream);
+                    sync_stream(N, cuda_stream);
+                }
+                if (read_clear_status(N, cuda_stream)) fail(JET_ETIMEOUT, "a bounded device-side wait ran out");
+                for (size_t i = 0; i < P->ops.size(); ++i) {
+                    const float ms = op_elapsed_ms(*P, i);
+                    if (ms <= 0) continue;
+                    total += ms;
+                    if (P->ops[i].batch_count == 0) node_ms[P->ops[i].node] += ms;
+                }
+            } catch (...) {
+                N.opt.profile = saved;
+                if (N.last_run == P.get()) N.last_run = nullptr;
+                release_plan_device(*P);
+                throw;
+            }
+            N.opt.profile = saved;
+            tun = P->tunables;
+            if (N.last_run == P.get()) N.last_run = nullptr;
+            release_plan_device(*P);
+            return total;
+        };
+        std::map<int32_t, double> ms0, ms1, msx;
+        std::vector<Plan::Tunable> tun0, tun1, tunx;
+        const double t_default = run(0, ms0, tun0);
+        int changed = 0;
+        bool all_cached = !tun0.empty();
+        for (const auto &t : tun0) all_cached = all_cached && cache.count(t.sig);
+        auto set_choice = [&](const Plan::Tunable &t, int taken) {
+            TuneChoice &c = N.tune[t.node];
+            (t.kind == 0 ? c.group : c.apply_tc) = (int8_t)taken;
+            if (taken != t.taken) ++changed;
+        };
+        if (all_cached) {
+            for (const auto &t : tun0) set_choice(t, cache[t.sig]);
+        } else if (!tun0.empty()) {
+            run(1, ms1, tun1);
+            std::map<std::pair<int32_t, int32_t>, int32_t> other;
+            for (const auto &t : tun1) other[{t.node, t.kind}] = t.taken;
+            for (const auto &t : tun0) {
+                auto it = other.find({t.node, t.kind});
+                const bool flip = it != other.end() && it->second != t.taken && ms1[t.node] < 0.97 * ms0[t.node];
+                set_choice(t, flip ? it->second : t.taken);
+                cache[t.sig] = flip ? it->second : t.taken;
+            }
+        }
+        double t_tuned = t_default;
+        if (changed) {
+            t_tuned = run(0, msx, tunx);
+            if (t_tuned > 1.02 * t_default) {   // the choices did not combine well: keep the defaults
+                N.tune.clear();
+                for (const auto &t : tun0) cache[t.sig] = t.taken;
+                changed = 0;
+                t_tuned = t_default;
+            }
+        }
+        if (cache_file && *cache_file && !all_cached && !tun0.empty()) {
+            if (FILE *f = std::fopen(cache_file, "w")) {
+                for (const auto &kv : cache) std::fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+                std::fclose(f);
+            }
+        }
+        invalidate_plan(N);   // the next contraction plans with the choices
+        if (default_ms) *default_ms = t_default;
+        if (tuned_ms) *tuned_ms = t_tuned;
+        if (n_changed) *n_changed = changed;
     });
 }
 

@@ -109,6 +109,11 @@ struct Plan {
     };
     std::vector<BufferRec> buffers;
     std::vector<int32_t> parent;       // per tree node (SSA id), -1 for the root
+    // nodes with two feasible forms the autotuner may choose between: (node,
+    // kind 0 = GEMM grouping / 1 = application form, the form taken) and a
+    // signature of the node's shape that keys the tuner's cache
+    struct Tunable { int32_t node, kind, taken; std::string sig; };
+    std::vector<Tunable> tunables;
     std::vector<uint8_t> host_args;   // argument blocks (pointers patched at bind time)
     // pointer patch list: (byte offset in host_args, buffer id, element/byte offset)
     struct Patch { size_t at; int32_t base; int64_t byte_off; };
@@ -168,6 +173,12 @@ struct RangeSet {
     std::vector<std::unique_ptr<Plan>> plans;  // per range, built on first use
 };
 
+// Route choice of the autotuner for one tree node; -1 leaves the planner's own.
+struct TuneChoice {
+    int8_t group = -1;      // GEMM route: instance blocks (1) or one product per instance (0)
+    int8_t apply_tc = -1;   // small-operand application: tensor-core form (1) or CUDA-core form (0)
+};
+
 struct Network {
     jet_options opt;
     std::vector<Leaf> leaves;
@@ -202,6 +213,10 @@ struct Network {
 
     std::unique_ptr<Plan> plan;
     std::unique_ptr<RangeSet> ranges;    // slice ranges under a workspace cap
+    // autotuned route choices, valid for the path and slicing they were tuned on
+    std::unordered_map<int32_t, TuneChoice> tune;
+    uint64_t tune_path_version = 0, tune_slice_version = 0;
+    int32_t tune_flip = 0;               // while tuning: every tunable node takes its other choice
     std::unique_ptr<Plan> grad_plan;     // cached adjoint plan (unsliced networks)
     const Plan *last_run = nullptr;      // the plan jet_profile reports
     void *own_arena = nullptr;

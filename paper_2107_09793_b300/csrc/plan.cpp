@@ -262,6 +262,24 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     P.reuse = net.opt.reuse;
     const bool fp64 = net.opt.precision == JET_PREC_FP64;
     const int64_t es = fp64 ? 16 : 8;
+    // the form a tunable node takes: the autotuner's choice, else the default
+    // (the other one while the tuner times the alternatives)
+    const bool tune_valid = net.tune_path_version == net.path_version && net.tune_slice_version == net.slice_version;
+    auto tuned = [&](int32_t v, int kind, bool deflt) -> bool {
+        if (tune_valid) {
+            auto it = net.tune.find(v);
+            if (it != net.tune.end()) {
+                const int c = kind == 0 ? it->second.group : it->second.apply_tc;
+                if (c >= 0) return c != 0;
+            }
+        }
+        return net.tune_flip ? !deflt : deflt;
+    };
+    auto sig_of = [&](int kind, std::initializer_list<int64_t> xs) {
+        std::string sg = "k" + std::to_string(kind) + ".p" + std::to_string(net.opt.precision);
+        for (int64_t x : xs) sg += "." + std::to_string(x);
+        return sg;
+    };
 
     // ---- fixed labels and their values under an assignment alpha = b * n_sl + s
     std::unordered_map<int64_t, int32_t> open_pos, slice_pos;
@@ -417,6 +435,17 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         if (nk <= 32 && !jet_apply_tc_half((int)nk, (int)nf) &&
             jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX)
             return 3;   // (chunks staged in halves take two groups: up to 256 TMEM columns each)
+        if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
+        return 0;
+    };
+    // the tensor-core form's groups for a shape whatever its size (the tuner's alternative)
+    auto apply_tc_groups_any = [&](int64_t nk, int64_t nf) -> int {
+        if (!tc_mode || fp64 || nk > JET_APPLY_MAXK || nf < 1 || nf > JET_APPLY_TC_MAXF ||
+            (nk > 32 && nf > JET_APPLY_TC_MAXF_MULTI))
+            return 0;
+        if (nk <= 32 && !jet_apply_tc_half((int)nk, (int)nf) &&
+            jet_apply_tc_smem(3, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX)
+            return 3;
         if (jet_apply_tc_smem(2, (int)nk, (int)nf) <= JET_APPLY_TC_SMEM_MAX) return 2;
         return 0;
     };
@@ -1222,7 +1251,18 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         op.flop = flop;
         op.bytes = bytes;
         op.variant = (fp64 ? 1 : 0) | (pow2 ? 4 : 0);
-        if (const int G = apply_tc_groups(nk, nf)) {
+        // the tensor-core form or a CUDA-core one, where both take the shape
+        const int G_def = apply_tc_groups(nk, nf), G_any = apply_tc_groups_any(nk, nf);
+        const bool cuda_ok = (d.nk <= (fp64 ? 16 : JET_APPLY_HOLDK) && d.nk_tmpl * d.nf <= JET_APPLY_MAXB &&
+                              d.nf <= JET_APPLY_MAXF) ||
+                             (!fp64 && d.nk <= JET_APPLY_MAXK && d.nf <= JET_APPLY_STREAMF &&
+                              (d.nf <= 4 || d.nk * ((d.nf + 15) / 16 * 16) <= JET_APPLY_STREAMB));
+        int G = G_def;
+        if (G_any > 0 && cuda_ok) {
+            G = tuned(v, 1, G_def > 0) ? G_any : 0;
+            P.tunables.push_back({v, 1, G > 0 ? 1 : 0, sig_of(1, {nk, nf, d.n_fib, n_inst, (int64_t)pow2})});
+        }
+        if (G) {
             // tensor-core form: one CTA per SM over contiguous ranges of (instance,
             // G tiles of 128 fibers); the status word takes its wait time-outs
             blob.patch_field(so, offsetof(ApplyArgs, status), BASE_STATUS, 0);
@@ -1357,8 +1397,13 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     const double vm = (double)VM.size, vn = (double)VN.size;
                     const double cm = okm ? gm.dup * vn : 1e300, cn = okn ? gn.dup * vm : 1e300;
                     const double budget = 0.25 * ((double)node[idM].n_inst * vm + (double)node[idN].n_inst * vn);
-                    const bool merge = net.opt.gemm_group && (okm || okn) && std::min(cm, cn) <= budget &&
-                                       (okm && cm <= cn ? gm : gn).bM.size() < (size_t)N.n_inst;
+                    const bool can_merge = (okm || okn) && std::min(cm, cn) <= budget &&
+                                           (okm && cm <= cn ? gm : gn).bM.size() < (size_t)N.n_inst;
+                    const bool merge = can_merge && tuned(v, 0, net.opt.gemm_group != 0);
+                    if (can_merge)
+                        P.tunables.push_back({v, 0, merge ? 1 : 0,
+                                              sig_of(0, {nK, dimprod(fM), dimprod(fN), N.n_inst, node[idM].n_inst,
+                                                         node[idN].n_inst, VM.size, VN.size})});
                     if (merge) {
                         G = okm && cm <= cn ? gm : gn;
                     } else {   // one block per instance; every child instance one group

@@ -23,7 +23,7 @@ EXPORTS = ["jet_options_default", "jet_network_create", "jet_network_set_open", 
            "jet_network_destroy", "jet_last_error", "jet_profile", "jet_pair_contract_noalloc",
            "jet_contract_slices", "jet_network_set_free", "jet_path_reconfigure", "jet_plan_slices",
            "jet_network_keep_shared", "jet_network_save_shared", "jet_network_load_shared", "jet_plan_buffers",
-           "jet_plan_ranges", "jet_sum_partials", "jet_selftest_wait"]
+           "jet_plan_ranges", "jet_sum_partials", "jet_selftest_wait", "jet_autotune"]
 
 
 class JetError(RuntimeError):
@@ -111,6 +111,7 @@ def lib():
             "jet_plan_ranges": (I32, [P, I32, P, ctypes.c_size_t, P, P, P, P, P]),
             "jet_sum_partials": (I32, [I32, I64, I64, P, P]),
             "jet_selftest_wait": (I32, [P, I64, P]),
+            "jet_autotune": (I32, [P, I32, P, ctypes.c_char_p, P, P, P, P]),
             "jet_pair_contract_noalloc": (I32, [I32, P, P, P, I32, P, P, P, P, I32, P]),
             "jet_network_destroy": (None, [P]),
             "jet_last_error": (ctypes.c_char_p, []),
@@ -364,6 +365,15 @@ class Network:
         _check(lib().jet_plan_buffers(self._h, recs, n.value, ctypes.byref(n)))
         return [{name: getattr(r, name) for name, _ in BufferRecord._fields_ if name != "pad_"}
                 for r in recs[:n.value]]
+
+    def autotune(self, outputs, cache_file: Optional[str] = None, stream: int = 0) -> Dict[str, float]:
+        """jet_autotune: per-node kernel-form choices timed on the device."""
+        o = self._outputs(outputs)
+        d, t = ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int32()
+        _check(lib().jet_autotune(self._h, o.shape[0], o.ctypes.data, cache_file.encode() if cache_file else None,
+                                  ctypes.c_void_p(stream), ctypes.byref(d), ctypes.byref(t), ctypes.byref(n)))
+        return {"default_ms": d.value, "tuned_ms": t.value, "n_changed": n.value}
 
     def selftest_wait(self, limit_us: int, stream: int = 0):
         """jet_selftest_wait: raises JetError(JET_ETIMEOUT) when the bounded wait
