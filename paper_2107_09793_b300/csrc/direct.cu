@@ -120,18 +120,18 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
     const int64_t inst = blockIdx.z;   // P = 64: an instance block
     if (inst >= a.n_inst) return;
     const int32_t *itab = (const int32_t *)a.itab;
-    const int nbk = P == 64 ? a.blk_na * a.blk_nb : 1;
-    const V *__restrict__ A = (const V *)((const uint64_t *)a.ptrA)[P == 64 ? itab[inst * nbk] : inst];
-    const V *__restrict__ B = (const V *)((const uint64_t *)a.ptrB)[P == 64 ? itab[inst * nbk] : inst];
+    const int nbk = P >= 64 ? a.blk_na * a.blk_nb : 1;
+    const V *__restrict__ A = (const V *)((const uint64_t *)a.ptrA)[P >= 64 ? itab[inst * nbk] : inst];
+    const V *__restrict__ B = (const V *)((const uint64_t *)a.ptrB)[P >= 64 ? itab[inst * nbk] : inst];
     const int64_t out0 = (int64_t)blockIdx.y * JET_SPLITK_G;
-    const int nout = P == 64 ? nbk : (int)((a.n_out - out0) < JET_SPLITK_G ? (a.n_out - out0) : JET_SPLITK_G);
+    const int nout = P >= 64 ? nbk : (int)((a.n_out - out0) < JET_SPLITK_G ? (a.n_out - out0) : JET_SPLITK_G);
     int64_t oa[JET_SPLITK_G], ob[JET_SPLITK_G];
     V acc[JET_SPLITK_G];
 #pragma unroll
     for (int j = 0; j < JET_SPLITK_G; ++j) {
         oa[j] = ob[j] = 0;
         acc[j] = vzero<V>();
-        if (j < (P == 64 ? 1 : nout)) {   // (an instance block has one output per instance)
+        if (j < (P >= 64 ? 1 : nout)) {   // (an instance block has one output per instance)
             int64_t e = out0 + j;
             int64_t r = e / a.n_cols;
             int c = (int)(e - r * a.n_cols);
@@ -158,9 +158,16 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
         }
     };
     const int nklo = a.n_klo, bd = blockDim.x;
-    if (P == 64) {   // dot products of an instance block: blk_na A vectors x blk_nb B vectors
-        constexpr int U = 4, MB = 4;   // at most 4 of each (and 8 products)
+    constexpr bool BLK = P >= 64;          // dot products of instance blocks
+    constexpr int MB = P == 65 ? 2 : 4;    // at most MB A and MB B vectors per block
+    V accB[BLK ? MB : 1][BLK ? MB : 1];
+    if (BLK) {   // dot products of an instance block: blk_na A vectors x blk_nb B vectors
+        constexpr int U = 4;
         const int na = a.blk_na, nb = a.blk_nb;
+#pragma unroll
+        for (int j = 0; j < (BLK ? MB : 1); ++j)
+#pragma unroll
+            for (int l = 0; l < (BLK ? MB : 1); ++l) accB[j][l] = vzero<V>();
         const V *__restrict__ Aj[MB];
         const V *__restrict__ Bl[MB];
 #pragma unroll
@@ -188,8 +195,10 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
                 for (int u = 0; u < U; ++u)
                     if (q0 + u * bd < nklo) {
 #pragma unroll
-                        for (int t = 0; t < JET_SPLITK_G; ++t)
-                            if (t < nbk) acc[t] = cmul_add(acc[t], xa[u][t / nb], xb[u][t % nb]);
+                        for (int j = 0; j < (BLK ? MB : 1); ++j)
+#pragma unroll
+                            for (int l = 0; l < (BLK ? MB : 1); ++l)
+                                if (j < na && l < nb) accB[j][l] = cmul_add(accB[j][l], xa[u][j], xb[u][l]);
                     }
             }
         }
@@ -270,14 +279,29 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (BLK) {   // product (j, l) of the block goes to slot j nb + l
 #pragma unroll
-    for (int j = 0; j < JET_SPLITK_G; ++j) {
-        V s = acc[j];
-        for (int o = 16; o > 0; o >>= 1) {
-            s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-            s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        for (int j = 0; j < (BLK ? MB : 1); ++j)
+#pragma unroll
+            for (int l = 0; l < (BLK ? MB : 1); ++l)
+                if (j < a.blk_na && l < a.blk_nb) {
+                    V s = accB[j][l];
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+                    }
+                    if (lane == 0) red[j * a.blk_nb + l][warp] = s;
+                }
+    } else {
+#pragma unroll
+        for (int j = 0; j < JET_SPLITK_G; ++j) {
+            V s = acc[j];
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            }
+            if (lane == 0) red[j][warp] = s;
         }
-        if (lane == 0) red[j][warp] = s;
     }
     __syncthreads();
     if (threadIdx.x < nout) {
@@ -287,7 +311,7 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
             s.y += red[threadIdx.x][w].y;
         }
         V *part = (V *)a.partials;
-        if (P == 64) part[(int64_t)itab[inst * nbk + threadIdx.x] * a.ksplit + blockIdx.x] = s;   // one output each
+        if (P >= 64) part[(int64_t)itab[inst * nbk + threadIdx.x] * a.ksplit + blockIdx.x] = s;   // one output each
         else part[(inst * a.ksplit + blockIdx.x) * a.n_out + out0 + threadIdx.x] = s;
     }
 }
@@ -498,11 +522,12 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
     bool fp64 = c.variant & 1, splitk = c.variant & 2, pow2 = c.variant & 4;
     size_t smem = c.smem;
     const int na = a.splitk_na;
-    if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20 && na != 32 && na != 64) ||
+    if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20 && na != 32 && na != 64 &&
+                                na != 65) ||
                     (na >= 32 ? a.n_out != 1 : a.n_out % JET_SPLITK_G != 0)))
         return cudaErrorInvalidValue;
-    if (na == 64 && (!a.itab || a.blk_na < 1 || a.blk_nb < 1 || a.blk_na > 4 || a.blk_nb > 4 ||
-                     a.blk_na * a.blk_nb > JET_SPLITK_G || c.gy != 1))
+    if (na >= 64 && (!a.itab || a.blk_na < 1 || a.blk_nb < 1 || a.blk_na > (na == 65 ? 2 : 4) ||
+                     a.blk_nb > (na == 65 ? 2 : 4) || a.blk_na * a.blk_nb > JET_SPLITK_G || c.gy != 1))
         return cudaErrorInvalidValue;
 #define JET_DIRECT_LAUNCH(V, P)                                                                 \
     do {                                                                                        \
@@ -516,6 +541,7 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
             case 20: direct_splitk_kernel<V, P, 20><<<grid, c.block, smem, s>>>(a); break;      \
             case 32: direct_splitk_kernel<V, P, 32><<<grid, c.block, smem, s>>>(a); break;      \
             case 64: direct_splitk_kernel<V, P, 64><<<grid, c.block, smem, s>>>(a); break;      \
+            case 65: direct_splitk_kernel<V, P, 65><<<grid, c.block, smem, s>>>(a); break;      \
             default: direct_splitk_kernel<V, P, 0><<<grid, c.block, smem, s>>>(a); break;       \
             }                                                                                   \
         } else direct_kernel<V, P><<<grid, c.block, smem, s>>>(a);                              \

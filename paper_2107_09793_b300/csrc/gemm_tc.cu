@@ -292,7 +292,11 @@ constexpr int TC_EPI_WARPS = 8;
 // memory (rows padded by one complex value) so that global stores cover whole
 // 128-byte lines, four rows per instruction.
 constexpr int TC_CST_ROW = 17;
-constexpr int TC_CST_BYTES = TC_EPI_WARPS * 32 * TC_CST_ROW * 8;
+// with bulk stores (c_tma) each epilogue warp alternates two dense 32 x 16
+// complex boxes (4 KB each, 128-byte swizzle) instead
+constexpr int TC_CST_BYTES = TC_EPI_WARPS * 32 * TC_CST_ROW * 8 > TC_EPI_WARPS * 2 * 4096
+                                 ? TC_EPI_WARPS * 32 * TC_CST_ROW * 8
+                                 : TC_EPI_WARPS * 2 * 4096;
 constexpr int TC_SMEM_LIMIT = 232448;   // opt-in dynamic shared memory per block
 constexpr int TC_STATIC_SMEM = 4096;    // barriers, scale staging and flags (upper bound)
 template <int MODE>
@@ -545,7 +549,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 return cptr;
             };
-            if (tc_cstage<MODE>() && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
+            if (tc_cstage<MODE>() && a.c_tma && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
+                // bulk tensor stores: the warp's 32 rows x 16 columns staged as one
+                // dense box (16-byte chunk c of row r at chunk c ^ (r % 8): 128-byte
+                // swizzle), stored by lane 0; two boxes alternate, a box rewritten
+                // only once the store that read it two steps before has
+                const uint32_t stb = smem_u32(smem + (size_t)S * STAGE_BYTES) + (uint32_t)(warp - 2) * 8192u;
+                const int row0 = tm * TC_BM + quarter * 32;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const uint32_t box = stb + (uint32_t)(p & 1) * 4096u;
+                    if (lane == 0) bulk_wait_read1();
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        sts_v4(box + (uint32_t)lane * 128u + ((uint32_t)(c ^ (lane & 7)) << 4), racc[p * 16 + 2 * c],
+                               iacc[p * 16 + 2 * c], racc[p * 16 + 2 * c + 1], iacc[p * 16 + 2 * c + 1]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0 && row0 < a.M) tma_store_3d(&a.tmC, box, (int)((col0 + p * 16) * 2), row0, inst);
+                }
+            } else if (tc_cstage<MODE>() && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
                 // whole 64-column half tile in range: stage 16 columns at a time (a
                 // 16-column group lies in one instance); each lane stores 8 rows
                 float2 *st = (float2 *)(smem + (size_t)S * STAGE_BYTES) + (size_t)(warp - 2) * 32 * TC_CST_ROW;
@@ -604,6 +628,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             }
         }
     }
+    if (warp >= 2 && lane == 0 && a.c_tma) bulk_wait_all();   // this lane's bulk stores have completed
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
@@ -765,6 +790,16 @@ int encode_tc_maps(TcGemmArgs &a)
                CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return -3;
+    }
+    if (a.c_tma) {   // outputs as floats: (2 N, M, instances), boxes of 32 floats x 32 rows
+        if ((a.N & 1) || (a.baseC & 15)) return -4;
+        cuuint64_t dims[3] = {(cuuint64_t)(2 * a.N), (cuuint64_t)a.M, (cuuint64_t)a.n_inst};
+        cuuint64_t strides[2] = {(cuuint64_t)(2 * a.N * 4), (cuuint64_t)(a.M * 2 * a.N * 4)};
+        cuuint32_t cbox[3] = {32, 32, 1};
+        if (fn(&a.tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)a.baseC, dims, strides, cbox, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return -5;
     }
     return 0;
 }

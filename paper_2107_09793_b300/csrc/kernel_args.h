@@ -59,8 +59,9 @@ struct DirectArgs {
                                     // summed entry: NA in {1, 2, 4, 8} = NA values of A (fastest)
                                     // x 8 / NA of B; 16 + NB (NB in {2, 4}) = NB of B fastest;
                                     // 32 = a single output (a dot product); 64 = dot
-                                    // products of instance blocks (below)
-    uint64_t itab;                  // splitk_na 64: block b (blockIdx.z) holds node instances
+                                    // products of instance blocks (below; 65: blocks of at
+                                    // most 2 x 2)
+    uint64_t itab;                  // splitk_na 64, 65: block b (blockIdx.z) holds node instances
                                     // itab[(b blk_na + j) blk_nb + l], their A the A of
                                     // instance (j, 0), their B the B of instance (0, l): each
                                     // operand value is loaded once for blk_na x blk_nb outputs

@@ -1048,7 +1048,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 bool ok = (int64_t)ia.size() == n_inst && group_instances(ia, ib, true, G) && G.dup == 0;
                 if (!ok && (int64_t)ia.size() == n_inst) ok = group_instances(ia, ib, false, G) && G.dup == 0;
                 if (ok && G.nA * G.nB >= 2 && G.nA <= 4 && G.nB <= 4 && G.nA * G.nB <= JET_SPLITK_G) {
-                    d.splitk_na = 64;
+                    d.splitk_na = G.nA <= 2 && G.nB <= 2 ? 65 : 64;   // (65: at most 2 x 2, fewer registers)
                     d.blk_na = G.nA;
                     d.blk_nb = G.nB;
                     blk_itab = G.itab;
@@ -1539,6 +1539,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 };
                 g.mi_shift = log2_or(Mv);
                 g.ni_shift = log2_or(Nv);
+                // one product per instance into one contiguous buffer, an even row
+                // length (16-byte strides): C leaves through bulk tensor stores
+                g.c_tma = !grouped && (Nv % 2 == 0) && 2 * Nv <= INT32_MAX && Mv <= INT32_MAX && N.n_inst <= INT32_MAX ? 1 : 0;
                 g.m_pad = m_pad;
                 g.n_pad = n_pad;
                 g.k_pad = k_pad;
@@ -1557,6 +1560,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 blob.patch_field(so, offsetof(TcGemmArgs, zB), BASE_BLOB, (int64_t)o_zb);
                 blob.patch_field(so, offsetof(TcGemmArgs, ptrC), BASE_BLOB, (int64_t)o_c);
                 if (grouped) blob.patch_field(so, offsetof(TcGemmArgs, itab), BASE_BLOB, (int64_t)o_it);
+                if (g.c_tma) blob.patch_field(so, offsetof(TcGemmArgs, baseC), N.base, N.buf_off);
                 blob.patch_field(so, offsetof(TcGemmArgs, status), BASE_STATUS, 0);
                 if (scaled) {
                     blob.patch_field(so, offsetof(TcGemmArgs, scaleA), BASE_ARENA, (int64_t)sclA);

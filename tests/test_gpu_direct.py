@@ -79,36 +79,41 @@ def test_split_k_forms(case, prec, tol):
     net.close()
 
 
-# Dot products of instance blocks: A[x, y, k...] and B[x, z, k...] with x, y, z
-# sliced (x on both operands, y and z joined by Y after the pair).  The pair's
-# 8 instances (x, y, z) form 2 blocks (x = 0, 1) of 2 A instances (y) x 2 B
-# instances (z); each block's 4 dot products read every operand value once.
+# Dot products of instance blocks: A[x, y..., k...] and B[x, z, k...] with x, the
+# y labels and z sliced (x on both operands, the y labels and z joined by Y
+# after the pair).  The pair's instances (x, y..., z) form 2 blocks (x = 0, 1)
+# of 2^len(y) A instances x 2 B instances; each block's dot products read every
+# operand value once (2 x 2 blocks: the two-by-two form; 4 x 2: the general one).
+@pytest.mark.parametrize("ny,form", [(1, 65), (2, 64)])
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-13)])
-def test_split_k_instance_block_dot_products(prec, tol):
+def test_split_k_instance_block_dot_products(prec, tol, ny, form):
     from oracle.einsum import slice_network
-    x, y, z = 200, 201, 202
-    la, lb = [x, y] + K[:8] + K[8:], [x, z] + K[8:] + K[:8]
-    A = _rand(7001, [2] * len(la)).astype(np.complex64)
+    x, z = 200, 202
+    ys = list(range(210, 210 + ny))
+    la, lb = [x] + ys + K[:8] + K[8:], [x, z] + K[8:] + K[:8]
+    A = _rand(7001 + ny, [2] * len(la)).astype(np.complex64)
     B = _rand(7002, [2] * len(lb)).astype(np.complex64)
-    Y = _rand(7003, [2, 2]).astype(np.complex64)
-    labels, data = [la, lb, [y, z]], [A, B, Y]
+    Y = _rand(7003 + ny, [2] * (ny + 1)).astype(np.complex64)
+    labels, data = [la, lb, ys + [z]], [A, B, Y]
+    sliced = [x] + ys + [z]
+    n_sl = 2 ** len(sliced)
     net = jet.Network(labels, data, precision=prec, profile=2)
     try:
         net.set_open([])
         net.path_set([(0, 1), (3, 2)])
-        net.slice([x, y, z])
-        got = net.contract_slices(np.zeros((1, 0), np.int32), list(range(8)))[0]
+        net.slice(sliced)
+        got = net.contract_slices(np.zeros((1, 0), np.int32), list(range(n_sl)))[0]
         recs = [r for r in net.profile() if r["kind"] == "direct" and r["node"] == 3]
     finally:
         net.close()
-    assert len(recs) == 1 and recs[0]["variant"] >> 8 == 64 and recs[0]["grid"][2] == 2, recs
+    assert len(recs) == 1 and recs[0]["variant"] >> 8 == form and recs[0]["grid"][2] == 2, recs
     d64 = [t.astype(np.complex128) for t in data]
     ref = []
-    for s in range(8):
-        vals = [(s >> 2) & 1, (s >> 1) & 1, s & 1]
-        sl, sd = slice_network(labels, d64, [x, y, z], vals)
+    for s_ in range(n_sl):
+        vals = [(s_ >> (len(sliced) - 1 - j)) & 1 for j in range(len(sliced))]
+        sl, sd = slice_network(labels, d64, sliced, vals)
         ref.append(complex(contract_network(sl, sd, [(0, 1), (3, 2)])[1]))
     ref = np.array(ref)
     err = float(np.max(np.abs(got - ref) / np.abs(ref)))
-    print(f"block dot products {prec}: max per-slice rel err {err:.2e}")
+    print(f"block dot products {prec} {form}: max per-slice rel err {err:.2e}")
     assert err <= tol
