@@ -825,6 +825,7 @@ def run_impl(args):
     # where a range's time goes: one more step with every launch timed
     breakdown = {}
     nprof = handle(args.precision, profile=2)
+    nprof.autotune(outs, cache_file=tune_cache, stream=sh)   # the headline's forms, from the cache
     aprof = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
     nprof.contract_async(outs, aprof.data_ptr(), sh)
     torch.cuda.synchronize()

@@ -555,10 +555,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 // swizzle), stored by lane 0; two boxes alternate, a box rewritten
                 // only once the store that read it two steps before has
                 const uint32_t stb = smem_u32(smem + (size_t)S * STAGE_BYTES) + (uint32_t)(warp - 2) * 8192u;
-                const int row0 = tm * TC_BM + quarter * 32;
+                // the warp's 32 rows lie in one instance (grouped blocks: Mi a multiple
+                // of 32), each 16-column group too (Ni a multiple of 16)
+                const int64_t R0 = (int64_t)tm * TC_BM + quarter * 32;
+                int64_t jj = 0, m0 = R0;
+                if (grouped) split_row(R0, jj, m0);
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const uint32_t box = stb + (uint32_t)(p & 1) * 4096u;
+                    int64_t ll = 0, n0 = col0 + p * 16;
+                    if (grouped) split_col(col0 + p * 16, ll, n0);
+                    const int64_t it = grouped ? (int64_t)__ldg(itab + ((int64_t)inst * a.nA + jj) * a.nB + ll) : inst;
                     if (lane == 0) bulk_wait_read1();
                     __syncwarp();
 #pragma unroll
@@ -567,7 +574,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                                iacc[p * 16 + 2 * c], racc[p * 16 + 2 * c + 1], iacc[p * 16 + 2 * c + 1]);
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
-                    if (lane == 0 && row0 < a.M) tma_store_3d(&a.tmC, box, (int)((col0 + p * 16) * 2), row0, inst);
+                    if (lane == 0 && R0 < a.M && it >= 0) tma_store_3d(&a.tmC, box, (int)(n0 * 2), (int)m0, (int)it);
                 }
             } else if (tc_cstage<MODE>() && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
                 // whole 64-column half tile in range: stage 16 columns at a time (a
@@ -791,10 +798,10 @@ int encode_tc_maps(TcGemmArgs &a)
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return -3;
     }
-    if (a.c_tma) {   // outputs as floats: (2 N, M, instances), boxes of 32 floats x 32 rows
-        if ((a.N & 1) || (a.baseC & 15)) return -4;
-        cuuint64_t dims[3] = {(cuuint64_t)(2 * a.N), (cuuint64_t)a.M, (cuuint64_t)a.n_inst};
-        cuuint64_t strides[2] = {(cuuint64_t)(2 * a.N * 4), (cuuint64_t)(a.M * 2 * a.N * 4)};
+    if (a.c_tma) {   // node outputs as floats: (2 Ni, Mi, instances), boxes of 32 floats x 32 rows
+        if ((a.Ni & 1) || (a.baseC & 15) || a.c_inst < 1) return -4;
+        cuuint64_t dims[3] = {(cuuint64_t)(2 * a.Ni), (cuuint64_t)a.Mi, (cuuint64_t)a.c_inst};
+        cuuint64_t strides[2] = {(cuuint64_t)(2 * a.Ni * 4), (cuuint64_t)(a.Mi * 2 * a.Ni * 4)};
         cuuint32_t cbox[3] = {32, 32, 1};
         if (fn(&a.tmC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)a.baseC, dims, strides, cbox, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,

@@ -1541,7 +1541,14 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 g.ni_shift = log2_or(Nv);
                 // one product per instance into one contiguous buffer, an even row
                 // length (16-byte strides): C leaves through bulk tensor stores
-                g.c_tma = !grouped && (Nv % 2 == 0) && 2 * Nv <= INT32_MAX && Mv <= INT32_MAX && N.n_inst <= INT32_MAX ? 1 : 0;
+                // C leaves through bulk tensor stores when a warp's 32 rows and a
+                // 16-column group lie in one instance: every product of a block
+                // (or an instance) is an (Mi x Ni) matrix in the node's buffer
+                g.c_tma = ((!grouped && Nv % 2 == 0) || (grouped && Mv % 32 == 0 && Nv % 16 == 0)) &&
+                                  2 * Nv <= INT32_MAX && Mv <= INT32_MAX && N.n_inst <= INT32_MAX
+                              ? 1
+                              : 0;
+                g.c_inst = N.n_inst;
                 g.m_pad = m_pad;
                 g.n_pad = n_pad;
                 g.k_pad = k_pad;

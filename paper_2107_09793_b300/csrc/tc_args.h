@@ -40,7 +40,7 @@ struct TcGemmArgs {
     CUtensorMap tmA;                 // 3-D map over A planes: (k_pad, m_pad, planes)
     CUtensorMap tmB;                 // 3-D map over B planes: (k_pad, n_pad, planes)
     CUtensorMap tmC;                 // c_tma: 3-D map over the node's outputs as floats:
-                                     // (2 N, M, n_inst), 32 x 32 boxes, 128-byte swizzle
+                                     // (2 Ni, Mi, c_inst), 32 x 32 boxes, 128-byte swizzle
     uint64_t baseC;                  // c_tma: the node's output buffer (instance i at i M N)
     uint64_t planesA, planesB;       // plane bases (device), used to encode the maps
     uint64_t zA, zB;                 // device int32[n_inst]: first plane index of each block's groups
@@ -55,6 +55,7 @@ struct TcGemmArgs {
     int32_t n_inst, mode;            // blocks
     int32_t n_kb, nA;
     int32_t nB, mi_shift;            // log2(Mi) and log2(Ni) when powers of two, else -1
-    int32_t ni_shift, c_tma;         // c_tma: one product per instance, N even: C leaves
-                                     // through tensor-map bulk stores
+    int32_t ni_shift, c_tma;         // c_tma: C leaves through tensor-map bulk stores (Ni even;
+                                     // grouped blocks: Mi a multiple of 32, Ni of 16)
+    int64_t c_inst;                  // c_tma: node instances (the map's third extent)
 };
