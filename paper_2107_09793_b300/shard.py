@@ -70,3 +70,62 @@ def contract_sharded(net, outputs, rank: int, world: int, group=None, stream: in
     else:
         local = np.zeros((o.shape[0], 0), dtype=np.complex128)
     return ordered_sum(gather_partials(local, world, group), ranges)
+
+
+def range_slice_ids(sliced_dims: Sequence[int], fixed_pos: Sequence[int]) -> List[List[int]]:
+    """Slice ids of each range of a partition that fixes the digits of the
+    sliced labels at fixed_pos (positions in the sliced-label order, mixed
+    radix, first label most significant): range k holds every slice whose
+    digits at fixed_pos are the mixed-radix digits of k, in increasing id."""
+    n = len(sliced_dims)
+    w = [1] * n
+    for j in range(n - 2, -1, -1):
+        w[j] = w[j + 1] * sliced_dims[j + 1]
+    total = w[0] * sliced_dims[0] if n else 1
+    n_ranges = 1
+    for j in fixed_pos:
+        n_ranges *= sliced_dims[j]
+    out: List[List[int]] = [[] for _ in range(n_ranges)]
+    for s in range(total):
+        k = 0
+        for j in fixed_pos:
+            k = k * sliced_dims[j] + (s // w[j]) % sliced_dims[j]
+        out[k].append(s)
+    return out
+
+
+def contract_sharded_ranges(net, outputs, rank: int, world: int, max_bytes: int, sliced: Sequence[int],
+                            sliced_dims: Sequence[int], group=None, stream: int = 0) -> np.ndarray:
+    """One amplitude's slices over `world` ranks, by the library's sharing-aware
+    slice ranges (jet_plan_ranges): the workspace cap is halved until there are
+    at least `world` ranges, rank r contracts ranges r, r + world, ... (each one
+    plan, jet_contract_slices), and the partials of every rank, concatenated in
+    increasing slice id, are summed by the library (jet_sum_partials).  Every
+    rank returns the amplitudes, bitwise the same for any rank count that gives
+    the same partition."""
+    o = net._outputs(outputs)
+    cap = int(max_bytes)
+    part = net.plan_ranges(o, cap)
+    while part["n_ranges"] < world and cap > (1 << 20):
+        cap //= 2
+        part = net.plan_ranges(o, cap)
+    pos = [list(sliced).index(x) for x in part["fixed_labels"]]
+    ranges = range_slice_ids(list(sliced_dims), pos)
+    mine_ids, mine_parts = [], []
+    for k in range(rank, len(ranges), world):
+        ids = ranges[k]
+        mine_ids += ids
+        mine_parts.append(net.contract_slices(o, ids, stream=stream))
+    local_ids = np.array(mine_ids, np.int64)
+    local = np.concatenate(mine_parts, axis=1) if mine_parts else np.zeros((o.shape[0], 0), np.complex128)
+    if world > 1:
+        import torch.distributed as dist
+        got: List = [None] * world
+        dist.all_gather_object(got, (local_ids, np.ascontiguousarray(local)), group=group)
+    else:
+        got = [(local_ids, local)]
+    ids_all = np.concatenate([g[0] for g in got])
+    parts_all = np.concatenate([g[1] for g in got], axis=1)
+    order = np.argsort(ids_all, kind="stable")
+    from .jet import sum_partials
+    return sum_partials(parts_all[:, order])

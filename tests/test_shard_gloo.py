@@ -78,3 +78,67 @@ def test_two_gloo_ranks_sum_slices_in_order():
         got = np.array(res[r])
         assert got.tobytes() == single.tobytes()          # same FP64 order, any rank count
     assert abs(single[0] - oracle.amplitude(tn, out)) <= 1e-13
+
+
+def test_range_slice_ids_partition_every_slice_once():
+    from paper_2107_09793_b300.shard import range_slice_ids
+    for dims, pos in [([2] * 6, [1, 4]), ([2, 3, 4], [0, 2]), ([2] * 12, [1, 3]), ([3, 2], [])]:
+        rs = range_slice_ids(dims, pos)
+        flat = sorted(i for r in rs for i in r)
+        assert flat == list(range(int(np.prod(dims))))
+        assert all(r == sorted(r) for r in rs)
+        assert len(rs) == int(np.prod([dims[j] for j in pos])) if pos else len(rs) == 1
+
+
+class _OracleNet:
+    """Stands in for a library handle on the CPU: partials from the FP64 oracle;
+    the partition fixes the first sliced labels, more of them for smaller caps."""
+    def __init__(self, tn, out, sliced):
+        self.tn, self.out, self.sliced = tn, out, sliced
+
+    def _outputs(self, outputs):
+        return np.asarray(outputs, np.int32).reshape(1, -1)
+
+    def plan_ranges(self, outputs, cap):
+        k = 1 if cap >= 1 << 30 else 2
+        return {"fixed_labels": [self.sliced[0], self.sliced[2]][:k], "n_ranges": 2 ** k}
+
+    def contract_slices(self, outputs, ids, stream=0):
+        return oracle.sliced_partials(self.tn, self.out, self.sliced, ids).reshape(1, -1)
+
+
+def _range_rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    from paper_2107_09793_b300.shard import contract_sharded_ranges
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    tn, out, sliced = _case()
+    net = _OracleNet(tn, out, sliced)
+    amp = contract_sharded_ranges(net, [out], rank, world, 1 << 30, sliced, [2] * len(sliced))
+    q.put((rank, np.asarray(amp).tolist()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_share_the_slice_ranges():
+    """Each rank runs every other sharing-aware range; the gathered partials,
+    in increasing slice id, sum (in the library) to the single-process sum."""
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_range_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    tn, out, sliced = _case()
+    n_sl = 2 ** len(sliced)
+    every = oracle.sliced_partials(tn, out, sliced, list(range(n_sl))).reshape(1, -1)
+    single = ordered_sum([every], [(0, n_sl)])
+    for r in (0, 1):
+        assert np.array(res[r]).tobytes() == single.tobytes()
+    assert abs(single[0] - oracle.amplitude(tn, out)) <= 1e-13
