@@ -1184,7 +1184,59 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         };
         ApplyArgs d;
         std::memset(&d, 0, sizeof d);
-        const int64_t nk = dimprod(K), nf = std::max<int64_t>(1, dimprod(fs));
+        const int64_t nk = dimprod(K), nf0 = std::max<int64_t>(1, dimprod(fs));
+        // Instances that apply several small operands to one large operand
+        // instance run as one application of those small operands side by side
+        // (free entry l nf + f is small instance l's entry f): the large operand
+        // is read once for all of them.  Taken when every large instance pairs
+        // with the same number of small ones, their entries and outputs lie at
+        // the same element distances from the first pair's, and the CUDA-core
+        // form held in registers takes the wider operand (each output's sum is
+        // the same sequence of multiply-adds, so the values do not change).
+        int64_t nB = 1;
+        std::vector<int64_t> dB, dC;   // per small slot l: element offset of its entries, of its outputs
+        std::vector<std::pair<int32_t, int64_t>> gl, gs, gc;   // per large instance: the l = 0 pair's refs
+        {
+            const std::vector<int32_t> &il = a_big ? node[v].ia : node[v].ib, &is = a_big ? node[v].ib : node[v].ia;
+            const std::vector<std::pair<int32_t, int64_t>> &pl = a_big ? pa : pb, &ps = a_big ? pb : pa;
+            std::map<int32_t, std::vector<std::pair<int32_t, int32_t>>> by;
+            if ((int64_t)il.size() == n_inst)
+                for (int64_t i = 0; i < n_inst; ++i) by[il[i]].push_back({is[i], (int32_t)i});
+            bool ok = net.opt.gemm_group && !fp64 && n_inst > 1 && !by.empty() && by.size() < (size_t)n_inst;
+            int64_t nb = 0;
+            for (auto &kv : by) {
+                if (!ok) break;
+                auto &lst = kv.second;
+                std::sort(lst.begin(), lst.end());
+                if (nb == 0) nb = (int64_t)lst.size();
+                if ((int64_t)lst.size() != nb) {
+                    ok = false;
+                    break;
+                }
+                std::vector<int64_t> b_off, c_off;
+                for (auto &e : lst) {
+                    const auto &rb = ps[e.second], &rc = pc[e.second], &rb0 = ps[lst[0].second], &rc0 = pc[lst[0].second];
+                    if (rb.first != rb0.first || rc.first != rc0.first) ok = false;
+                    b_off.push_back((rb.second - rb0.second) / es);
+                    c_off.push_back((rc.second - rc0.second) / es);
+                }
+                if (dB.empty()) {
+                    dB = b_off;
+                    dC = c_off;
+                } else if (b_off != dB || c_off != dC) {
+                    ok = false;
+                }
+                gl.push_back(pl[lst[0].second]);
+                gs.push_back(ps[lst[0].second]);
+                gc.push_back(pc[lst[0].second]);
+            }
+            int64_t nkt = 1;
+            while (nkt < nk) nkt *= 2;
+            ok = ok && nb > 1 && apply_tc_groups(nk, nf0) == 0 && nk <= JET_APPLY_HOLDK && nkt * nf0 * nb <= JET_APPLY_MAXB &&
+                 nf0 * nb <= JET_APPLY_MAXF;
+            if (ok) nB = nb;
+        }
+        const int64_t nf = nf0 * nB;
         d.nk = (int32_t)nk;
         d.nf = (int32_t)nf;
         d.nk_tmpl = 1;
@@ -1209,12 +1261,16 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             }
         }
         for (int64_t f = 0; f < nf; ++f) {
-            int64_t r = f;
+            int64_t r = f % nf0;
             for (int j = (int)Fs.size() - 1; j >= 0; --j) {
                 const int64_t dm = net.labels.at(Fs[j]).dim, dg = r % dm;
                 r /= dm;
                 d.cF[f] += dg * stride(Cv, Fs[j]);
                 d.bF[f] += dg * stride(VS, Fs[j]);
+            }
+            if (nB > 1) {   // small slot f / nf0: its entries and outputs
+                d.cF[f] += dC[f / nf0];
+                d.bF[f] += dB[f / nf0];
             }
         }
         // fibers: A's free labels, smallest A stride decoded first
@@ -1233,10 +1289,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             d.shift[j] = bit;
             while (((int64_t)1 << bit) < d.n_fib) ++bit;   // power-of-two dims: log2 of the running product
         }
-        d.n_inst = (int32_t)n_inst;
+        const int64_t n_launch = nB > 1 ? (int64_t)gl.size() : n_inst;   // one unit per large instance
+        d.n_inst = (int32_t)n_launch;
         d.tc_terms = net.opt.precision == JET_PREC_TF32 ? 1 : 3;
-        size_t off_pl = blob.put_ptrs(a_big ? pa : pb), off_ps = blob.put_ptrs(a_big ? pb : pa);
-        size_t off_pc = blob.put_ptrs(pc);
+        size_t off_pl = blob.put_ptrs(nB > 1 ? gl : (a_big ? pa : pb)), off_ps = blob.put_ptrs(nB > 1 ? gs : (a_big ? pb : pa));
+        size_t off_pc = blob.put_ptrs(nB > 1 ? gc : pc);
         size_t so = blob.reserve(sizeof d);
         std::memcpy(blob.bytes.data() + so, &d, sizeof d);
         blob.patch_field(so, offsetof(ApplyArgs, ptrA), BASE_BLOB, (int64_t)off_pl);
@@ -1249,7 +1306,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         op.args_off = so;
         op.args_bytes = sizeof d;
         op.flop = flop;
-        op.bytes = bytes;
+        // grouped: every large instance read once, every small one and every output once
+        op.bytes = nB > 1 ? (double)es * ((double)n_launch * VL.size + (double)n_inst * (VS.size + Cv.size)) : bytes;
         op.variant = (fp64 ? 1 : 0) | (pow2 ? 4 : 0);
         // the tensor-core form or a CUDA-core one, where both take the shape
         const int G_def = apply_tc_groups(nk, nf), G_any = apply_tc_groups_any(nk, nf);
@@ -1258,7 +1316,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                              (!fp64 && d.nk <= JET_APPLY_MAXK && d.nf <= JET_APPLY_STREAMF &&
                               (d.nf <= 4 || d.nk * ((d.nf + 15) / 16 * 16) <= JET_APPLY_STREAMB));
         int G = G_def;
-        if (G_any > 0 && cuda_ok) {
+        if (G_any > 0 && cuda_ok && nB == 1) {
             G = tuned(v, 1, G_def > 0) ? G_any : 0;
             P.tunables.push_back({v, 1, G > 0 ? 1 : 0, sig_of(1, {nk, nf, d.n_fib, n_inst, (int64_t)pow2})});
         }
@@ -1266,7 +1324,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             // tensor-core form: one CTA per SM over contiguous ranges of (instance,
             // G tiles of 128 fibers); the status word takes its wait time-outs
             blob.patch_field(so, offsetof(ApplyArgs, status), BASE_STATUS, 0);
-            const int64_t units = n_inst * (((d.n_fib + 127) / 128 + G - 1) / G);
+            const int64_t units = n_launch * (((d.n_fib + 127) / 128 + G - 1) / G);
             op.variant |= 8;
             op.block = 128 * G;
             op.smem = jet_apply_tc_smem(G, (int)nk, (int)nf);
@@ -1277,7 +1335,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         }
         // 256-thread blocks; complex64 threads take two fibers, complex128 one
         op.block = 256;
-        const int64_t gy = std::min<int64_t>(n_inst, 65535);
+        const int64_t gy = std::min<int64_t>(n_launch, 65535);
         const int64_t per_block = fp64 ? 256 : 512;
         const int64_t blocks = (d.n_fib + per_block - 1) / per_block;
         const int64_t per_sm = 8;

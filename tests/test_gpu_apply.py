@@ -170,3 +170,38 @@ def test_apply_default_routing(case):
     nf = int(np.prod([dims[l] for l in lb if l not in la]))
     tc = nk * nf >= 1024 or (nk <= 32 and 2 * nk * nf >= 1024 and nk * nf >= 10 * (nk + nf))
     assert _check(case, "fp16x3", tc) <= TOL["fp16x3"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16x3"])
+def test_apply_instances_sharing_the_large_operand_run_together(prec):
+    """A large operand without sliced labels and a small one with two sliced
+    labels: the pair's 4 instances apply 4 small operands to one large one and
+    run as one application of an operand 4 times wider (the large one read
+    once).  Each output is the same sum as without the grouping (bit for bit),
+    and every value matches the oracle."""
+    r = list(range(16))
+    k, f, s1, s2 = [100, 101], 102, 103, 104
+    A = _rand(8100, [2] * (len(r) + 2))
+    B = _rand(8101, [2, 2, 2, 2, 2])
+    Y = _rand(8102, [2, 2])
+    labels, data = [r + k, k + [f, s1, s2], [s1, s2]], [A, B, Y]
+    opens = r + [f]
+    got = {}
+    for grp in (True, False):
+        net = jet.Network(labels, data, precision=prec, profile=2, gemm_group=grp)
+        try:
+            net.set_open(opens)
+            net.set_free(opens)
+            net.path_set([(0, 1), (3, 2)])
+            net.slice([s1, s2])
+            got[grp] = net.contract(np.zeros((1, len(opens)), np.int32))[0]
+            app = [x for x in net.profile() if x["kind"] == "apply" and x["node"] == 3]
+        finally:
+            net.close()
+        assert len(app) == 1 and app[0]["n_inst"] == 4
+        assert app[0]["grid"][1] == (1 if grp else 4), app   # one unit per large instance when grouped
+    assert np.array_equal(got[True], got[False])
+    out, ref = contract_network([list(l) for l in labels], [d.astype(np.complex128) for d in data], [(0, 1), (3, 2)])
+    ref = np.transpose(np.asarray(ref), [out.index(l) for l in opens]).ravel()
+    err = float(np.max(np.abs(got[True] - ref)) / np.max(np.abs(ref)))
+    assert err <= 1e-5, err
