@@ -89,16 +89,8 @@ def test_bosonic_environments_vs_statevector_adjoint():
     assert err_env <= 1e-5 and err_amp <= 1e-5
 
 
-def test_angle_gradients_autograd_vs_finite_differences():
-    torch = pytest.importorskip("torch")
-    from paper_2107_09793_b300.autograd import amplitudes
-    circ = param_grid_circuit(2, 3, 4, seed=33)
-    tn = circuit_to_network(circ)
-    outs = random_bitstrings(circ.n, 8, 34)
-    net = jet.from_network(tn, precision="fp32")
-    net.path_greedy(seed=1, n_trials=4)
-    thetas = [torch.tensor(list(g.params), dtype=torch.float64, requires_grad=True) for g in circ.gates]
-
+def _torch_gates(torch, circ, tn, thetas):
+    """The circuit's gate tensors as differentiable functions of their angles."""
     def rzry_t(a, b):
         rz = torch.stack([torch.stack([torch.exp(-0.5j * a), torch.zeros((), dtype=torch.complex128)]),
                           torch.stack([torch.zeros((), dtype=torch.complex128), torch.exp(0.5j * a)])])
@@ -112,25 +104,64 @@ def test_angle_gradients_autograd_vs_finite_differences():
         return torch.stack([torch.stack([o, z, z, z]), torch.stack([z, c, -1j * s, z]),
                             torch.stack([z, -1j * s, c, z]), torch.stack([z, z, z, torch.exp(-1j * ph)])])
 
-    mats = [(rzry_t(*t) if g.kind == "rzry" else fsim_t(*t)).reshape(tn.data[tn.gate_tensor[i]].shape)
+    return [(rzry_t(*t) if g.kind == "rzry" else fsim_t(*t)).reshape(tn.data[tn.gate_tensor[i]].shape)
             for i, (g, t) in enumerate(zip(circ.gates, thetas))]
+
+
+def _fd(circ, outs, gi, pi, h=1e-3):
+    """Central finite difference of sum |amp|^2 in FP64 (the oracle's state vector)."""
+    g = circ.gates[gi]
+    vals = []
+    for sgn in (+1, -1):
+        p = list(g.params)
+        p[pi] += sgn * h
+        ms = [gg.matrix for gg in circ.gates]
+        ms[gi] = gate_with_params(g, p)
+        vals.append(np.sum(np.abs(oracle.sv_amplitudes(circ, outs, gate_mats=ms)) ** 2))
+    return (vals[0] - vals[1]) / (2 * h)
+
+
+def _autograd_angle_grads(torch, circ, tn, outs, trials):
+    from paper_2107_09793_b300.autograd import amplitudes
+    net = jet.from_network(tn, precision="fp32")
+    net.path_greedy_batch(outs, seed=1, n_trials=trials) if len(outs) > 8 else net.path_greedy(seed=1, n_trials=trials)
+    thetas = [torch.tensor(list(g.params), dtype=torch.float64, requires_grad=True) for g in circ.gates]
+    mats = _torch_gates(torch, circ, tn, thetas)
     amps = amplitudes(net, outs, tn.gate_tensor, [m.to(torch.complex64) for m in mats])
     loss = (amps.abs() ** 2).sum()
     loss.backward()
-    grad = np.concatenate([t.grad.numpy() for t in thetas])
-    h = 1e-3
-    fd = []
-    for gi, g in enumerate(circ.gates):
-        for pi in range(len(g.params)):
-            vals = []
-            for sgn in (+1, -1):
-                p = list(g.params)
-                p[pi] += sgn * h
-                ms = [gg.matrix for gg in circ.gates]
-                ms[gi] = gate_with_params(g, p)
-                vals.append(np.sum(np.abs(oracle.sv_amplitudes(circ, outs, gate_mats=ms)) ** 2))
-            fd.append((vals[0] - vals[1]) / (2 * h))
-    fd = np.array(fd)
+    net.close()
+    return [t.grad.numpy() for t in thetas]
+
+
+def test_angle_gradients_autograd_vs_finite_differences():
+    torch = pytest.importorskip("torch")
+    circ = param_grid_circuit(2, 3, 4, seed=33)
+    tn = circuit_to_network(circ)
+    outs = random_bitstrings(circ.n, 8, 34)
+    grads = _autograd_angle_grads(torch, circ, tn, outs, 4)
+    grad = np.concatenate(grads)
+    fd = np.array([_fd(circ, outs, gi, pi) for gi, g in enumerate(circ.gates) for pi in range(len(g.params))])
     err = np.linalg.norm(grad - fd) / np.linalg.norm(fd)
     print(f"angle-gradient rel err vs central FD: {err:.3e}")
     assert err <= 1e-5
+
+
+def test_param20_angle_gradients_vs_finite_differences_on_sampled_angles():
+    """The full-size parameterised workload (20 qubits, 12 cycles, 64 amplitudes,
+    666 angles): every angle's gradient of sum |amp|^2 from the GPU adjoint
+    through torch.autograd; 12 seeded angles checked against central finite
+    differences of the FP64 state vector (h = 1e-3)."""
+    torch = pytest.importorskip("torch")
+    from circuits import SplitMix64
+    w = configs.build("param20")
+    circ, tn, outs = w.circuit, w.network, w.outputs
+    grads = _autograd_angle_grads(torch, circ, tn, outs, 16)
+    flat = [(gi, pi) for gi, g in enumerate(circ.gates) for pi in range(len(g.params))]
+    rng = SplitMix64(2020)
+    pick = sorted({flat[rng.randint(len(flat))] for _ in range(12)})
+    got = np.array([grads[gi][pi] for gi, pi in pick])
+    fd = np.array([_fd(circ, outs, gi, pi) for gi, pi in pick])
+    err = float(np.linalg.norm(got - fd) / np.linalg.norm(fd))
+    print(f"param20: {len(pick)} sampled angle gradients vs central FD: rel err {err:.3e}")
+    assert err <= 2e-5
