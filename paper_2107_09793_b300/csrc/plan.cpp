@@ -885,7 +885,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                            bool a_big, int64_t n_inst, const std::vector<std::pair<int32_t, int64_t>> &pa,
                            const std::vector<std::pair<int32_t, int64_t>> &pb,
                            const std::vector<std::pair<int32_t, int64_t>> &pc, double flop, double bytes,
-                           std::vector<size_t> &scratch, std::vector<size_t> &scratch_bytes) {
+                           std::vector<size_t> &scratch, std::vector<size_t> &scratch_bytes, bool group = true) {
             const View &VX = a_big ? VA : VB;   // operand whose strides order the summed labels
             auto strideA = [&](int64_t l) { int p = find_pos(VA.labels, l); return p < 0 ? 0 : VA.strides[p]; };
             auto strideB = [&](int64_t l) { int p = find_pos(VB.labels, l); return p < 0 ? 0 : VB.strides[p]; };
@@ -1042,7 +1042,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             // loads each operand value once for all of the block's products
             std::vector<int32_t> blk_itab;
             int64_t n_launch_inst = n_inst;
-            if (d.splitk_na == 32 && n_inst > 1) {
+            if (group && d.splitk_na == 32 && n_inst > 1) {
                 GemmGroups G;
                 const std::vector<int32_t> &ia = node[v].ia, &ib = node[v].ib;
                 bool ok = (int64_t)ia.size() == n_inst && group_instances(ia, ib, true, G) && G.dup == 0;
@@ -1172,10 +1172,14 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             }
     };
 
+    // group: instance i pairs node v's child instances ia[i], ib[i] (the forward
+    // contraction of v), so instances that share an operand instance may run as
+    // one block; the adjoint sweep's launches pair other operands and pass false
     auto emit_apply = [&](int32_t v, const View &VA, const View &VB, const View &Cv, const std::vector<int64_t> &K,
                           bool a_big, int64_t n_inst, const std::vector<std::pair<int32_t, int64_t>> &pa,
                           const std::vector<std::pair<int32_t, int64_t>> &pb,
-                          const std::vector<std::pair<int32_t, int64_t>> &pc, double flop, double bytes) {
+                          const std::vector<std::pair<int32_t, int64_t>> &pc, double flop, double bytes,
+                          bool group = true) {
         const View &VL = a_big ? VA : VB, &VS = a_big ? VB : VA;
         const std::vector<int64_t> fs = free_of(VS, K), fl = free_of(VL, K);
         auto stride = [&](const View &V, int64_t l) {
@@ -1202,7 +1206,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             std::map<int32_t, std::vector<std::pair<int32_t, int32_t>>> by;
             if ((int64_t)il.size() == n_inst)
                 for (int64_t i = 0; i < n_inst; ++i) by[il[i]].push_back({is[i], (int32_t)i});
-            bool ok = net.opt.gemm_group && !fp64 && n_inst > 1 && !by.empty() && by.size() < (size_t)n_inst;
+            bool ok = group && net.opt.gemm_group && !fp64 && n_inst > 1 && !by.empty() && by.size() < (size_t)n_inst;
             int64_t nb = 0;
             for (auto &kv : by) {
                 if (!ok) break;
@@ -1316,7 +1320,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                              (!fp64 && d.nk <= JET_APPLY_MAXK && d.nf <= JET_APPLY_STREAMF &&
                               (d.nf <= 4 || d.nk * ((d.nf + 15) / 16 * 16) <= JET_APPLY_STREAMB));
         int G = G_def;
-        if (G_any > 0 && cuda_ok && nB == 1) {
+        if (group && G_any > 0 && cuda_ok && nB == 1) {   // (forward launches only: the tuner's)
             G = tuned(v, 1, G_def > 0) ? G_any : 0;
             P.tunables.push_back({v, 1, G > 0 ? 1 : 0, sig_of(1, {nk, nf, d.n_fib, n_inst, (int64_t)pow2})});
         }
@@ -1891,11 +1895,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                         batch_bytes += bytes;
                     } else if (apply_ok_views(N.view, NO.view, Kb, N.view.size >= NO.view.size, N.n_inst)) {
                         emit_apply(v, N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, N.n_inst, pe, po, pt, flop,
-                                   bytes);
+                                   bytes, false);
                     } else {
                         std::vector<size_t> scr, scrb;
                         emit_direct(v, N.view, NO.view, Tv, Kb, N.view.size >= NO.view.size, N.n_inst, pe, po, pt,
-                                    flop, bytes, scr, scrb);
+                                    flop, bytes, scr, scrb, false);
                         for (size_t q = 0; q < scr.size(); ++q) arena.release(scr[q], scrb[q]);
                     }
                     P.flop_executed += flop;
