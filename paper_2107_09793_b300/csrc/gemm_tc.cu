@@ -102,7 +102,7 @@ __device__ __forceinline__ void split_parts(float x, float (&p)[3])
 }
 
 constexpr int SPLIT_TR = 64, SPLIT_TK = 64;
-constexpr int SPLIT_ROW = SPLIT_TK + 1;                              // padded tile row (float2)
+constexpr int SPLIT_ROW = SPLIT_TK + 2;   // padded tile row (float2; even: 16-byte pairs stay aligned)
 constexpr int SPLIT_SMEM = 2 * SPLIT_TR * SPLIT_ROW * 8               // two tiles
                            + 2 * (SPLIT_TR + SPLIT_TK) * 8;           // their row / column offsets
 
@@ -126,7 +126,6 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
     extern __shared__ __align__(16) uint8_t split_smem[];
     float2 *tiles_s = (float2 *)split_smem;                                        // [2][64][65]
     int64_t *offs = (int64_t *)(split_smem + 2 * SPLIT_TR * SPLIT_ROW * 8);       // [2][64 + 64]
-    __shared__ float mul[SPLIT_TR];   // SCALED: 2^s of each row of this 64-wide chunk
     const int tid = threadIdx.x;
     const int64_t k_tiles = (a.k_pad + SPLIT_TK - 1) / SPLIT_TK;
     const int64_t plane_elems = a.rows_group * a.k_pad;
@@ -206,47 +205,42 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
             const float2 *tile = tiles_s + (size_t)cur * SPLIT_TR * SPLIT_ROW;
             const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
             const int64_t row0 = rt * SPLIT_TR, k0 = kt * SPLIT_TK;
-            if (TcCfg<MODE>::SCALED) {
-                // one power-of-two scale per (row, 64-wide K chunk = this tile's columns):
-                // the chunk's largest |re| or |im| lands in [2^14, 2^15), inside FP16's range
-                static_assert(SPLIT_TR == 64 && SPLIT_TK == 64, "four threads per row of 64");
-                const int r = tid >> 2, sub = tid & 3;
-                float m = 0.f;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float2 v = tile[r * SPLIT_ROW + sub * 16 + q];
-                    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-                }
-                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-                int e = 0;
-                if (m > 0.f) {
-                    frexpf(m, &e);                     // m = f * 2^e, f in [0.5, 1)
-                    e = max(-100, min(100, 15 - e));   // m * 2^e in [2^14, 2^15)
-                }
-                if (sub == 0) {
-                    mul[r] = ldexpf(1.f, e);
-                    const int64_t n_ch = (a.k_pad + 63) >> 6;
-                    if (row0 + r < rows_w)
-                        ((float *)a.scales)[(g * n_ch + kt) * a.rows_group + row_base + row0 + r] = ldexpf(1.f, -e);
-                }
-                __syncthreads();
-            }
+            // a warp takes one row of the tile per step (its lanes two columns each), so
+            // the row's power-of-two scale comes from a warp reduction over the values
+            // the warp holds (FP16x3: one scale per row and 64-wide K chunk, this tile's
+            // columns; the chunk's largest |re| or |im| lands in [2^14, 2^15), inside
+            // FP16's range; padding columns hold zeros)
+            static_assert(SPLIT_TK == 64 && 256 % 32 == 0, "a warp's lanes cover one tile row");
+            const int lane = tid & 31;
 #pragma unroll
             for (int i = 0; i < (SPLIT_TR * SPLIT_TK / 2) / 256; ++i) {
                 const int idx = tid + 256 * i;
-                const int r = idx / (SPLIT_TK / 2), kp = 2 * (idx % (SPLIT_TK / 2));
+                const int r = idx / (SPLIT_TK / 2), kp = 2 * (idx % (SPLIT_TK / 2));   // r warp-uniform, kp = 2 lane
+                if (row0 + r >= rows_w) continue;   // the whole warp
                 const int64_t kcol = k0 + kp;
-                if (kcol >= a.k_pad || row0 + r >= rows_w) continue;
-                const int64_t e = (row0 + r) * a.k_pad + kcol;
-                float2 v0 = tile[r * SPLIT_ROW + kp], v1 = tile[r * SPLIT_ROW + kp + 1];
+                const float4 v = *(const float4 *)(tile + r * SPLIT_ROW + kp);
+                float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
                 if (TcCfg<MODE>::SCALED) {
-                    const float f = mul[r];
+                    float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    int ex = 0;
+                    if (m > 0.f) {
+                        frexpf(m, &ex);                      // m = f * 2^ex, f in [0.5, 1)
+                        ex = max(-100, min(100, 15 - ex));   // m * 2^ex in [2^14, 2^15)
+                    }
+                    const float f = ldexpf(1.f, ex);
+                    if (lane == 0) {
+                        const int64_t n_ch = (a.k_pad + 63) >> 6;
+                        ((float *)a.scales)[(g * n_ch + kt) * a.rows_group + row_base + row0 + r] = ldexpf(1.f, -ex);
+                    }
                     v0.x *= f;
                     v0.y *= f;
                     v1.x *= f;
                     v1.y *= f;
                 }
+                if (kcol >= a.k_pad) continue;
+                const int64_t e = (row0 + r) * a.k_pad + kcol;
                 float re0[3], re1[3], im0[3], im1[3];
                 split_parts<MODE>(v0.x, re0);
                 split_parts<MODE>(v1.x, re1);
