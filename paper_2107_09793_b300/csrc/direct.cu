@@ -175,45 +175,31 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
             Aj[j] = j < na ? (const V *)((const uint64_t *)a.ptrA)[itab[inst * nbk + j * nb]] + oa[0] : A;
             Bl[j] = j < nb ? (const V *)((const uint64_t *)a.ptrB)[itab[inst * nbk + j]] + ob[0] : B;
         }
-        // every thread's inner entries fit one round (U entries a thread): two
-        // outer summed values per round, so twice the loads are in flight
-        // (the 2 x 2 form; the wider one would run out of registers)
-        constexpr int HM = P == 65 ? 2 : 1;
-        const int HU = HM == 2 && nklo <= U * bd ? 2 : 1;
-        for (int64_t h = h0; h < h1; h += HU) {
-            int64_t ha[HM], hb[HM];
-            h_offsets(h, ha[0], hb[0]);
-            const bool two = HU == 2 && h + 1 < h1;
-            if (HM == 2 && HU == 2) h_offsets(two ? h + 1 : h, ha[HM - 1], hb[HM - 1]);   // (block-uniform either way)
+        for (int64_t h = h0; h < h1; ++h) {
+            int64_t ha, hb;
+            h_offsets(h, ha, hb);
             for (int q0 = threadIdx.x; q0 < nklo; q0 += U * bd) {
-                V xa[HM][U][MB], xb[HM][U][MB];
+                V xa[U][MB], xb[U][MB];
 #pragma unroll
-                for (int t = 0; t < HM; ++t) {
-                    const bool live = t == 0 || two;
+                for (int u = 0; u < U; ++u) {
+                    const int q = q0 + u * bd;
+                    const bool ok = q < nklo;
+                    const int64_t ka = ha + (ok ? sKA[q] : 0), kb = hb + (ok ? sKB[q] : 0);
 #pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int q = q0 + u * bd;
-                        const bool ok = live && q < nklo;
-                        const int64_t ka = ha[t] + (ok ? sKA[q] : 0), kb = hb[t] + (ok ? sKB[q] : 0);
-#pragma unroll
-                        for (int j = 0; j < MB; ++j) {
-                            xa[t][u][j] = ok && j < na ? __ldg(Aj[j] + ka) : vzero<V>();
-                            xb[t][u][j] = ok && j < nb ? __ldg(Bl[j] + kb) : vzero<V>();
-                        }
+                    for (int j = 0; j < MB; ++j) {
+                        xa[u][j] = ok && j < na ? __ldg(Aj[j] + ka) : vzero<V>();
+                        xb[u][j] = ok && j < nb ? __ldg(Bl[j] + kb) : vzero<V>();
                     }
                 }
 #pragma unroll
-                for (int t = 0; t < HM; ++t)
+                for (int u = 0; u < U; ++u)
+                    if (q0 + u * bd < nklo) {
 #pragma unroll
-                    for (int u = 0; u < U; ++u)
-                        if ((t == 0 || two) && q0 + u * bd < nklo) {
+                        for (int j = 0; j < (BLK ? MB : 1); ++j)
 #pragma unroll
-                            for (int j = 0; j < (BLK ? MB : 1); ++j)
-#pragma unroll
-                                for (int l = 0; l < (BLK ? MB : 1); ++l)
-                                    if (j < na && l < nb)
-                                        accB[j][l] = cmul_add(accB[j][l], xa[t][u][j], xb[t][u][l]);
-                        }
+                            for (int l = 0; l < (BLK ? MB : 1); ++l)
+                                if (j < na && l < nb) accB[j][l] = cmul_add(accB[j][l], xa[u][j], xb[u][l]);
+                    }
             }
         }
     } else if (P == 32) {   // one output

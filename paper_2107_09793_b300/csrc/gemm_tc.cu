@@ -110,6 +110,10 @@ __device__ __forceinline__ void cp_async8_zfill(uint32_t dst, const void *src, u
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+__device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
 
 // Tiled gather + split: a block walks 64-row x 64-column tiles of the planes.
 // Two tiles are in flight: while one is split and written, the next one's
@@ -161,6 +165,20 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
     auto issue = [&](const float2 *S, int buf) {   // 16 zero-filling 8-byte copies per thread
         const int64_t *rowOff = offs + buf * (SPLIT_TR + SPLIT_TK), *kOff = rowOff + SPLIT_TR;
         float2 *tile = tiles_s + (size_t)buf * SPLIT_TR * SPLIT_ROW;
+        if (a.pair16) {
+            // the fastest summed label has stride 1 (and K is even): entries 2c and
+            // 2c + 1 of a row are adjacent in the source and in the tile, one
+            // 16-byte copy each (8 per thread)
+#pragma unroll
+            for (int i = 0; i < (SPLIT_TR * SPLIT_TK) / 512; ++i) {
+                const int kk = 2 * (tid & (SPLIT_TK / 2 - 1)), r = (tid >> 5) + (256 / (SPLIT_TK / 2)) * i;
+                const int64_t ro = rowOff[r], ko = kOff[kk];
+                const bool in = ro >= 0 && ko >= 0;
+                cp_async16_zfill(smem_u32(tile + r * SPLIT_ROW + kk), in ? (const void *)(S + ro + ko) : (const void *)S,
+                                 in ? 16u : 0u);
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 0; i < (SPLIT_TR * SPLIT_TK) / 256; ++i) {
             int r, kk;

@@ -1527,6 +1527,16 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                             }
                         sa.fast_k = find_pos(kappa, bl) >= 0 ? 1 : 0;
                     }
+                    // 16-byte copies of entry pairs: the fastest summed label has stride 1
+                    // and even dim, every summed dim a power of two (pairs never straddle
+                    // a row's end, and even source offsets keep them 16-byte aligned)
+                    {
+                        bool p16 = sa.fast_k && sa.rank_k > 0 && sa.k_s[0] == 1 && sa.k_dim[0] % 2 == 0;
+                        for (int j = 0; j < sa.rank_k && p16; ++j) p16 = (sa.k_dim[j] & (sa.k_dim[j] - 1)) == 0;
+                        for (int j = 0; j < sa.rank_r && p16; ++j) p16 = sa.r_s[j] % 2 == 0;
+                        for (int j = 1; j < sa.rank_k && p16; ++j) p16 = sa.k_s[j] % 2 == 0;
+                        sa.pair16 = p16 ? 1 : 0;
+                    }
                     // already [rows][K] in this order, dense, K unpadded: a pure format conversion
                     bool conv = nK == k_pad && nK % 4 == 0 && V.labels.size() == f.size() + kappa.size();
                     for (size_t q = 0; conv && q < V.labels.size(); ++q)
@@ -1541,6 +1551,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     std::vector<std::pair<int32_t, int64_t>> ps;
                     for (const auto &gr : groups)
                         for (int32_t j : gr) ps.push_back(base_ref(id, j));
+                    // (16-byte copies also need every instance's base 16-byte aligned; the
+                    // buffers themselves are, so the byte offsets decide)
+                    for (const auto &r : ps)
+                        if (r.second % 16 != 0) sa.pair16 = 0;
                     size_t o_ps = blob.put_ptrs(ps);
                     size_t so = blob.reserve(sizeof sa);
                     std::memcpy(blob.bytes.data() + so, &sa, sizeof sa);
@@ -1565,6 +1579,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                         for (int j = 0; j < sa.rank_k; ++j) pow2 = pow2 && (sa.k_dim[j] & (sa.k_dim[j] - 1)) == 0;
                         if (pow2) op.variant |= 2;
                     }
+                    if (sa.pair16) op.variant |= 16;   // (for the launch records: 16-byte copies)
                     if (conv) {
                         op.variant |= 1;
                         op.grid_x = (int32_t)std::max<int64_t>(

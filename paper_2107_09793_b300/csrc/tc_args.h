@@ -21,7 +21,8 @@ struct TcSplitArgs {
     uint64_t scales;                 // FP16X3: float 2^-s per [group][K chunk][row of the group] (else 0)
     int64_t rows, k, rows_group, k_pad;
     int32_t n_inst, n_planes;
-    int32_t per_group, pad_;
+    int32_t per_group, pair16;       // pair16: the fastest summed label (k_dim[0]) has stride 1,
+                                     // so source entries 2c, 2c + 1 of a row are adjacent
     int32_t rank_r, rank_k;
     int32_t mode, fast_k;           // fast_k: the source's stride-1 label is a summed label
     int64_t r_dim[JET_MAXR], r_s[JET_MAXR];   // row labels, fastest first, source strides
