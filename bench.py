@@ -363,35 +363,86 @@ def run_other_workloads(dev, peaks, peak_src):
 
 def run_reference(args):
     """The reference arm: the FP64 oracle as it stands, on the host's cores,
-    on the headline's workload; a step is one of its 4096 slices (a bounded
-    sample, scaled to amplitudes/s over all of them)."""
+    on the headline's workload.  One slice takes the oracle about half a
+    minute, so a step is the next eighth of a slice's pairwise contractions
+    (the path cut into 8 parts of about equal FLOP; a slice's network is built
+    in its first part): every 8 steps contract one whole slice, and amplitudes/s
+    = the timed steps' share of a slice's FLOP / (4096 x their time).  Exactly
+    --warmup untimed and --steps timed steps run."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     from circuits import configs
+    from oracle.einsum import contract_pairs, slice_network
     w = configs.build("grid53")
     path, sliced, plan_src = grid53_plan(w)
     g, _ = grid53_golden()
     cand = [i for i in (g["slice_ids"] if g else [0]) if not g or i not in set(g["structurally_zero_ids"])]
-    steps = max(1, min(args.steps, 2))
-    warm = min(args.warmup, 1)
-    times, base = [], None
-    for i in range(warm + steps):   # a step: one slice (oracle only, no library)
-        b, _, dt = oracle_grid53_sample(w, path, sliced, cand[i % len(cand)])
-        if i >= warm:
-            times.append(dt)
-        base = b
-    n_sl = 2 ** len(sliced)
+    cores = oracle_cores()
+    tn = w.network.as_complex64()
+    n = len(sliced)
+    n_sl = 2 ** n
+
+    def sliced_net(sid):
+        digits = [(sid >> (n - 1 - j)) & 1 for j in range(n)]
+        return slice_network(tn.labels, tn.data, list(tn.open_labels) + list(sliced), list(w.outputs[0]) + digits)
+
+    # per-pair FLOP along the path (every slice has the same labels): cut into Q parts
+    Q = 8
+    sl0, sd0 = sliced_net(cand[0])
+    dims = {x: d for l, t in zip(sl0, sd0) for x, d in zip(l, np.shape(t))}
+    live, nxt, flop = dict(enumerate([list(l) for l in sl0])), len(sl0), []
+    for a, b in path:
+        la, lb = live.pop(a), live.pop(b)
+        flop.append(8.0 * float(np.prod([dims[x] for x in set(la) | set(lb)])))
+        live[nxt] = [x for x in la if x not in lb] + [x for x in lb if x not in la]
+        nxt += 1
+    del sl0, sd0
+    total = sum(flop)
+    cum, cuts = 0.0, [0]
+    for i, f in enumerate(flop):
+        cum += f
+        if len(cuts) < Q and cum >= total * len(cuts) / Q:
+            cuts.append(i + 1)
+    cuts += [len(path)] * (Q + 1 - len(cuts))
+    share = [sum(flop[cuts[q]:cuts[q + 1]]) / total for q in range(Q)]
+
+    st = {"part": 0, "k": 0, "gen": None, "last": None}
+
+    def step():
+        if st["part"] == 0:
+            sl, sd = sliced_net(cand[st["k"] % len(cand)])
+            st["gen"] = contract_pairs(sl, sd, path)
+        for _ in range(cuts[st["part"] + 1] - cuts[st["part"]]):
+            st["last"] = next(st["gen"])
+        q = st["part"]
+        st["part"] = (q + 1) % Q
+        if st["part"] == 0:
+            st["k"] += 1
+            st["gen"] = None
+        return share[q]
+
+    for _ in range(args.warmup):
+        step()
+    times, done = [], 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        done += step()
+        times.append(time.perf_counter() - t0)
     t = sum(times)
-    value = steps / (n_sl * t)
-    line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": steps,
-            "warmup": warm, "ms_per_step": 1000 * t / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD53, "step": f"one slice of the {n_sl} (bounded sample), along the "
-                                                       f"benchmark's order ({plan_src})"},
+    value = done / (n_sl * t)
+    sample = (f"{args.steps} steps of one eighth of a slice each (slices {cand[:max(1, (args.warmup + args.steps + Q - 1) // Q)]} "
+              f"of the {n_sl}, FP64 pairwise tensordot along the benchmark's order): {done:.3f} slices' FLOP in "
+              f"{t:.1f} s, scaled by {n_sl}")
+    line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * t / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD53,
+                       "step": f"the next eighth (by FLOP) of one slice's pairwise contractions of the {n_sl} "
+                               f"({plan_src})"},
             "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": base["cores"], "kind": "oracle",
-                             "sample": base["sample"]},
+            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -644,17 +695,21 @@ def partial_errors(got, ref, zero_ids, ids):
             "zero_slices_exact": bool(np.all(got[~nz] == 0)), "slices": int(nz.sum())}
 
 
+def oracle_cores():
+    """Threads the oracle's tensordot uses (its BLAS pool), else the usable cores."""
+    try:
+        from threadpoolctl import threadpool_info
+        return int(max((i.get("num_threads", 0) for i in threadpool_info()), default=0) or len(os.sched_getaffinity(0)))
+    except Exception:
+        return len(os.sched_getaffinity(0))
+
+
 def oracle_grid53_sample(w, path, sliced, slice_id):
     """FP64 oracle (pairwise numpy.tensordot) on one slice of the 53-qubit
     amplitude along the benchmark's order; scaled to amplitudes/s over all
     4096 slices."""
-    import oracle
     from oracle.einsum import slice_network, contract_network
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max((i.get("num_threads", 0) for i in threadpool_info()), default=0) or len(os.sched_getaffinity(0))
-    except Exception:
-        cores = len(os.sched_getaffinity(0))
+    cores = oracle_cores()
     tn = w.network.as_complex64()
     n = len(sliced)
     digits = [(slice_id >> (n - 1 - j)) & 1 for j in range(n)]
@@ -899,6 +954,9 @@ def run_impl(args):
     timed = {i: statistics.mean(v) for i, v in kern_ms.items()}
     range_ms = statistics.mean(prof_ms) / ranges["n_ranges"]
     roof = roofline_of(recs, timed, args.precision, peaks, peak_src, range_ms)
+    # every launch of a range above 0.5 ms: [kind, node, ms, GB/s of its algorithmic bytes]
+    heavy = sorted(([r["kind"], r["node"], round(timed[i], 3), round(r["bytes"] / (timed[i] * 1e6), 1)]
+                    for i, r in enumerate(recs) if i in timed and timed[i] > 0.5), key=lambda x: -x[2])
 
     # where a range's time goes: one more step with every launch timed
     breakdown = {}
@@ -1040,7 +1098,7 @@ def run_impl(args):
                               "note": "per stored slice (8 nonzero partials of the 4096, 2 exactly zero): the whole "
                                       "amplitude has no oracle value (4096 FP64 slices of ~45 s each)"},
         "fp32_simt": modes.get("fp32"), "modes": modes, "roofline": roof,
-        "breakdown_per_range": breakdown, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "breakdown_per_range": breakdown, "heavy_launches_per_range": heavy, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         # both loops of the timed region (the steps, then the instrumented steps)
         "gpu_launches": (args.steps + n_prof) * ranges["n_ranges"] * launches_per_range,
         "other_workloads": others,

@@ -131,6 +131,21 @@ def contract_network(labels, data, path: Optional[Sequence[Tuple[int, int]]] = N
     return live_l[k], live_t[k]
 
 
+def contract_pairs(labels, data, path: Sequence[Tuple[int, int]]):
+    """contract_network one pairwise step at a time, for a caller that times
+    parts of a contraction: a generator that performs the next tensordot of
+    the path on each next() and yields (step index, labels, tensor) of that
+    step's result; the last one yielded is the contraction's result."""
+    live_l = dict(enumerate([list(l) for l in labels]))
+    live_t = dict(enumerate([np.asarray(t, dtype=np.complex128) for t in data]))
+    nxt = len(live_l)
+    for i, (a, b) in enumerate(path):
+        out, t = _pair(live_l.pop(a), live_t.pop(a), live_l.pop(b), live_t.pop(b))
+        live_l[nxt], live_t[nxt] = out, t
+        nxt += 1
+        yield i, out, t
+
+
 def amplitude(tn, pattern, sliced: Sequence[int] = (), path=None) -> complex:
     """<x|U|psi0> by pairwise contraction; with sliced labels, as the explicit
     sum of all slice partials (Eq. sliced_sum)."""

@@ -101,6 +101,54 @@ __device__ __forceinline__ void split_parts(float x, float (&p)[3])
     }
 }
 
+// Four adjacent values of one component (re or im) split into the mode's
+// planes, each plane's four parts packed as they are stored: 16-bit formats two
+// per word (w[p][0..1]), TF32 one per word (w[p][0..3]).  Every part is the
+// same rounding of the same remainder as split_parts.
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) { return *(const uint32_t *)&h; }
+__device__ __forceinline__ uint32_t b2_bits(__nv_bfloat162 h) { return *(const uint32_t *)&h; }
+template <int MODE>
+__device__ __forceinline__ void split4(const float (&x)[4], uint32_t (&w)[TcCfg<MODE>::NP / 2][TcCfg<MODE>::EB])
+{
+    if constexpr (MODE == JET_PREC_FP16X3) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const __half2 hi = __floats2half2_rn(x[2 * h], x[2 * h + 1]);
+            const float2 hf = __half22float2(hi);
+            w[0][h] = h2_bits(hi);
+            w[1][h] = h2_bits(__floats2half2_rn(x[2 * h] - hf.x, x[2 * h + 1] - hf.y));
+        }
+    } else if constexpr (MODE == JET_PREC_BF16X3) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[2 * h], x[2 * h + 1]);
+            const float2 hf = __bfloat1622float2(hi);
+            w[0][h] = b2_bits(hi);
+            w[1][h] = b2_bits(__floats2bfloat162_rn(x[2 * h] - hf.x, x[2 * h + 1] - hf.y));
+        }
+    } else if constexpr (MODE == JET_PREC_BF16X6) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(x[2 * h], x[2 * h + 1]);
+            const float2 hf = __bfloat1622float2(hi);
+            const float r0 = x[2 * h] - hf.x, r1 = x[2 * h + 1] - hf.y;
+            const __nv_bfloat162 mid = __floats2bfloat162_rn(r0, r1);
+            const float2 mf = __bfloat1622float2(mid);
+            w[0][h] = b2_bits(hi);
+            w[1][h] = b2_bits(mid);
+            w[2][h] = b2_bits(__floats2bfloat162_rn(r0 - mf.x, r1 - mf.y));
+        }
+    } else {   // TF32, TF32x3: FP32 words
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float p[3];
+            split_parts<MODE>(x[c], p);
+#pragma unroll
+            for (int q = 0; q < TcCfg<MODE>::NP / 2; ++q) w[q][c] = __float_as_uint(p[q]);
+        }
+    }
+}
+
 constexpr int SPLIT_TR = 64, SPLIT_TK = 64;
 constexpr int SPLIT_ROW = SPLIT_TK + 2;   // padded tile row (float2; even: 16-byte pairs stay aligned)
 constexpr int SPLIT_SMEM = 2 * SPLIT_TR * SPLIT_ROW * 8               // two tiles
@@ -223,63 +271,62 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
             const float2 *tile = tiles_s + (size_t)cur * SPLIT_TR * SPLIT_ROW;
             const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
             const int64_t row0 = rt * SPLIT_TR, k0 = kt * SPLIT_TK;
-            // a warp takes one row of the tile per step (its lanes two columns each), so
-            // the row's power-of-two scale comes from a warp reduction over the values
-            // the warp holds (FP16x3: one scale per row and 64-wide K chunk, this tile's
-            // columns; the chunk's largest |re| or |im| lands in [2^14, 2^15), inside
-            // FP16's range; padding columns hold zeros)
-            static_assert(SPLIT_TK == 64 && 256 % 32 == 0, "a warp's lanes cover one tile row");
-            const int lane = tid & 31;
+            // a half-warp takes one row of the tile per step, its lanes four adjacent
+            // columns each (written as one 8- or 16-byte vector per plane), so the
+            // row's power-of-two scale comes from a reduction over 16 lanes (FP16x3:
+            // one scale per row and 64-wide K chunk, this tile's columns; the chunk's
+            // largest |re| or |im| lands in [2^14, 2^15), inside FP16's range;
+            // padding columns and rows hold zeros)
+            static_assert(SPLIT_TK == 64 && SPLIT_ROW % 2 == 0, "16 lanes x 4 columns cover one 16-byte aligned row");
+            const int q16 = tid & 15, rsub = tid >> 4;
+            // a lane reads its two 16-byte halves in the order that puts the 8 lanes
+            // of a quarter-warp on 8 different 16-byte bank groups
+            const int sw = (q16 >> 2) & 1;
+            const int kq = 4 * q16;
+            const bool col_in = k0 + kq < a.k_pad;   // k_pad is a multiple of 16
+            const int64_t pstep = plane_elems * EB;
+            uint8_t *q0 = base + ((row0 + rsub) * a.k_pad + k0 + kq) * EB;
+            float *sc = nullptr;
+            if (TcCfg<MODE>::SCALED)
+                sc = (float *)a.scales + (g * k_tiles + kt) * a.rows_group + row_base + row0 + rsub;
 #pragma unroll
-            for (int i = 0; i < (SPLIT_TR * SPLIT_TK / 2) / 256; ++i) {
-                const int idx = tid + 256 * i;
-                const int r = idx / (SPLIT_TK / 2), kp = 2 * (idx % (SPLIT_TK / 2));   // r warp-uniform, kp = 2 lane
-                if (row0 + r >= rows_w) continue;   // the whole warp
-                const int64_t kcol = k0 + kp;
-                const float4 v = *(const float4 *)(tile + r * SPLIT_ROW + kp);
-                float2 v0 = make_float2(v.x, v.y), v1 = make_float2(v.z, v.w);
+            for (int i = 0; i < SPLIT_TR / 16; ++i) {
+                const int r = rsub + 16 * i;
+                const bool valid = row0 + r < rows_w;
+                const float4 *row4 = (const float4 *)(tile + r * SPLIT_ROW) + 2 * q16;
+                const float4 x0 = row4[sw], x1 = row4[1 - sw];
+                const float4 lo = sw ? x1 : x0, hi = sw ? x0 : x1;
+                float re[4] = {lo.x, lo.z, hi.x, hi.z}, im[4] = {lo.y, lo.w, hi.y, hi.w};
                 if (TcCfg<MODE>::SCALED) {
-                    float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+                    float m = fmaxf(fmaxf(fmaxf(fabsf(re[0]), fabsf(re[1])), fmaxf(fabsf(re[2]), fabsf(re[3]))),
+                                    fmaxf(fmaxf(fabsf(im[0]), fabsf(im[1])), fmaxf(fabsf(im[2]), fabsf(im[3]))));
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    for (int o = 8; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    // m = f 2^e with f in [0.5, 1) and e = (biased exponent) - 126 for
+                    // normal m; scale 2^(15 - e), clamped to [-100, 100] (subnormal m: 100)
                     int ex = 0;
-                    if (m > 0.f) {
-                        frexpf(m, &ex);                      // m = f * 2^ex, f in [0.5, 1)
-                        ex = max(-100, min(100, 15 - ex));   // m * 2^ex in [2^14, 2^15)
+                    if (m > 0.f) ex = max(-100, min(100, 141 - (int)((__float_as_uint(m) >> 23) & 0xffu)));
+                    const float f = __uint_as_float((uint32_t)(127 + ex) << 23);
+                    if (q16 == 0 && valid) sc[16 * i] = __uint_as_float((uint32_t)(127 - ex) << 23);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        re[c] *= f;
+                        im[c] *= f;
                     }
-                    const float f = ldexpf(1.f, ex);
-                    if (lane == 0) {
-                        const int64_t n_ch = (a.k_pad + 63) >> 6;
-                        ((float *)a.scales)[(g * n_ch + kt) * a.rows_group + row_base + row0 + r] = ldexpf(1.f, -ex);
-                    }
-                    v0.x *= f;
-                    v0.y *= f;
-                    v1.x *= f;
-                    v1.y *= f;
                 }
-                if (kcol >= a.k_pad) continue;
-                const int64_t e = (row0 + r) * a.k_pad + kcol;
-                float re0[3], re1[3], im0[3], im1[3];
-                split_parts<MODE>(v0.x, re0);
-                split_parts<MODE>(v1.x, re1);
-                split_parts<MODE>(v0.y, im0);
-                split_parts<MODE>(v1.y, im1);
+                if (!valid || !col_in) continue;
+                uint32_t wr[NPH][EB], wi[NPH][EB];
+                split4<MODE>(re, wr);
+                split4<MODE>(im, wi);
+                uint8_t *q = q0 + (int64_t)(16 * i) * a.k_pad * EB;
 #pragma unroll
                 for (int p = 0; p < NPH; ++p) {
-                    if (EB == 2 && TcCfg<MODE>::FMT == 0) {
-                        __half2 *pr = (__half2 *)((__half *)base + (int64_t)p * plane_elems + e);
-                        __half2 *pi = (__half2 *)((__half *)base + (int64_t)(NPH + p) * plane_elems + e);
-                        *pr = __floats2half2_rn(re0[p], re1[p]);
-                        *pi = __floats2half2_rn(im0[p], im1[p]);
-                    } else if (EB == 2) {
-                        __nv_bfloat162 *pr = (__nv_bfloat162 *)((__nv_bfloat16 *)base + (int64_t)p * plane_elems + e);
-                        __nv_bfloat162 *pi =
-                            (__nv_bfloat162 *)((__nv_bfloat16 *)base + (int64_t)(NPH + p) * plane_elems + e);
-                        *pr = __floats2bfloat162_rn(re0[p], re1[p]);
-                        *pi = __floats2bfloat162_rn(im0[p], im1[p]);
+                    if (EB == 2) {
+                        *(uint2 *)(q + p * pstep) = make_uint2(wr[p][0], wr[p][1]);
+                        *(uint2 *)(q + (NPH + p) * pstep) = make_uint2(wi[p][0], wi[p][1]);
                     } else {
-                        *(float2 *)((float *)base + (int64_t)p * plane_elems + e) = make_float2(re0[p], re1[p]);
-                        *(float2 *)((float *)base + (int64_t)(NPH + p) * plane_elems + e) = make_float2(im0[p], im1[p]);
+                        *(uint4 *)(q + p * pstep) = make_uint4(wr[p][0], wr[p][1], wr[p][2 % EB], wr[p][3 % EB]);
+                        *(uint4 *)(q + (NPH + p) * pstep) = make_uint4(wi[p][0], wi[p][1], wi[p][2 % EB], wi[p][3 % EB]);
                     }
                 }
             }

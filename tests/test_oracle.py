@@ -230,6 +230,20 @@ def test_path_independence_grid12():
         assert abs(v - ref) < 1e-12
 
 
+def test_stepwise_contraction_ends_at_the_state_vector_amplitude():
+    """The stepwise form (one tensordot per next(), used to time parts of a
+    contraction) ends at the state-vector amplitude, one step per pair."""
+    from oracle.einsum import contract_pairs
+    w = configs.build("grid12")
+    x = w.outputs[0]
+    labels, data = oracle.attach_bras(w.network.labels, w.network.data, w.network.open_labels, x, 2)
+    path = greedy_path(labels, {l: 2 for ls in labels for l in ls})
+    steps = list(contract_pairs(labels, data, path))
+    assert [s[0] for s in steps] == list(range(len(path)))
+    assert steps[-1][1] == []
+    assert abs(complex(steps[-1][2]) - oracle.sv_amplitudes(w.circuit, [x])[0]) < 1e-12
+
+
 def _random_path_connected(labels, rng):
     """Random order that only contracts pairs sharing an index (keeps sizes small)."""
     live = {i: set(l) for i, l in enumerate(labels)}
