@@ -107,14 +107,15 @@ __global__ void __launch_bounds__(256) direct_kernel(const __grid_constant__ Dir
 template <typename V, bool POW2, int P>
 __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constant__ DirectArgs a)
 {
-    extern __shared__ int32_t sm[];
-    int32_t *sKA = sm, *sKB = sm + a.n_klo;
+    extern __shared__ __align__(16) int32_t sm[];
+    int32_t *sKA = sm, *sKB = sm + a.n_klo, *sQB = sm + 2 * a.n_klo;
     __shared__ V red[JET_SPLITK_G][8];
     const int32_t *gKA = (const int32_t *)a.kA, *gKB = (const int32_t *)a.kB;
     const int32_t *gColA = (const int32_t *)a.colA, *gColB = (const int32_t *)a.colB;
     for (int i = threadIdx.x; i < a.n_klo; i += blockDim.x) {
         sKA[i] = gKA[i];
         sKB[i] = gKB[i];
+        if (P == 66) sQB[i] = ((const int32_t *)a.qB)[i];
     }
     __syncthreads();
     const int64_t inst = blockIdx.z;   // P = 64: an instance block
@@ -159,9 +160,91 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
     };
     const int nklo = a.n_klo, bd = blockDim.x;
     constexpr bool BLK = P >= 64;          // dot products of instance blocks
-    constexpr int MB = P == 65 ? 2 : 4;    // at most MB A and MB B vectors per block
+    constexpr int MB = P == 64 ? 4 : 2;    // at most MB A and MB B vectors per block
     V accB[BLK ? MB : 1][BLK ? MB : 1];
-    if (BLK) {   // dot products of an instance block: blk_na A vectors x blk_nb B vectors
+    if (BLK && P == 66) {
+        // B's entries of each outer value h pass through shared memory (two
+        // buffers): read in B's own order (kB: B offsets ascending, so a warp's
+        // loads are adjacent), stored at their inner index (qB) with one padding
+        // entry per 32, and read back at the inner index q of A's loads; the
+        // next h's B loads are in flight while this h is summed.  Each product
+        // adds the same terms in the same order as the direct block form.
+        constexpr int U = 4;
+        const int na = a.blk_na, nb = a.blk_nb;
+        const int PAD = nklo + (nklo >> 5);
+        V *Bs = (V *)((uint8_t *)sm + (((size_t)3 * nklo * 4 + 15) & ~(size_t)15));   // [2][MB][PAD]
+#pragma unroll
+        for (int j = 0; j < MB; ++j)
+#pragma unroll
+            for (int l = 0; l < MB; ++l) accB[j][l] = vzero<V>();
+        const V *__restrict__ Aj[MB];
+        const V *__restrict__ Bl[MB];
+#pragma unroll
+        for (int j = 0; j < MB; ++j) {
+            Aj[j] = j < na ? (const V *)((const uint64_t *)a.ptrA)[itab[inst * nbk + j * nb]] + oa[0] : A;
+            Bl[j] = j < nb ? (const V *)((const uint64_t *)a.ptrB)[itab[inst * nbk + j]] + ob[0] : B;
+        }
+        V xb[U][MB];
+        int64_t ha = 0, hb = 0;
+        auto load_b = [&]() {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int jq = threadIdx.x + u * bd;
+                const bool ok = jq < nklo;
+                const int64_t kb = hb + (ok ? sKB[jq] : 0);
+#pragma unroll
+                for (int l = 0; l < MB; ++l) xb[u][l] = ok && l < nb ? __ldg(Bl[l] + kb) : vzero<V>();
+            }
+        };
+        if (h0 < h1) {
+            h_offsets(h0, ha, hb);
+            load_b();
+        }
+        int buf = 0;
+        for (int64_t h = h0; h < h1; ++h) {
+            V *Bb = Bs + (size_t)buf * MB * PAD;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int jq = threadIdx.x + u * bd;
+                if (jq < nklo) {
+                    const int q = sQB[jq], qq = q + (q >> 5);
+#pragma unroll
+                    for (int l = 0; l < MB; ++l) Bb[l * PAD + qq] = xb[u][l];
+                }
+            }
+            const int64_t ha_c = ha;
+            if (h + 1 < h1) {   // block-uniform
+                h_offsets(h + 1, ha, hb);
+                load_b();
+            }
+            __syncthreads();   // this h's B entries are in place; the other buffer's readers are done
+            V xa[U][MB];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = threadIdx.x + u * bd;
+                const bool ok = q < nklo;
+                const int64_t ka = ha_c + (ok ? sKA[q] : 0);
+#pragma unroll
+                for (int j = 0; j < MB; ++j) xa[u][j] = ok && j < na ? __ldg(Aj[j] + ka) : vzero<V>();
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = threadIdx.x + u * bd;
+                if (q < nklo) {
+                    const int qq = q + (q >> 5);
+#pragma unroll
+                    for (int l = 0; l < MB; ++l) {
+                        if (l >= nb) continue;
+                        const V vb = Bb[l * PAD + qq];
+#pragma unroll
+                        for (int j = 0; j < MB; ++j)
+                            if (j < na) accB[j][l] = cmul_add(accB[j][l], xa[u][j], vb);
+                    }
+                }
+            }
+            buf ^= 1;
+        }
+    } else if (BLK) {   // dot products of an instance block: blk_na A vectors x blk_nb B vectors
         constexpr int U = 4;
         const int na = a.blk_na, nb = a.blk_nb;
 #pragma unroll
@@ -523,11 +606,17 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
     size_t smem = c.smem;
     const int na = a.splitk_na;
     if (na != 0 && (!splitk || (na != 1 && na != 2 && na != 4 && na != 8 && na != 18 && na != 20 && na != 32 && na != 64 &&
-                                na != 65) ||
+                                na != 65 && na != 66) ||
                     (na >= 32 ? a.n_out != 1 : a.n_out % JET_SPLITK_G != 0)))
         return cudaErrorInvalidValue;
-    if (na >= 64 && (!a.itab || a.blk_na < 1 || a.blk_nb < 1 || a.blk_na > (na == 65 ? 2 : 4) ||
-                     a.blk_nb > (na == 65 ? 2 : 4) || a.blk_na * a.blk_nb > JET_SPLITK_G || c.gy != 1))
+    if (na >= 64 && (!a.itab || a.blk_na < 1 || a.blk_nb < 1 || a.blk_na > (na == 64 ? 4 : 2) ||
+                     a.blk_nb > (na == 64 ? 4 : 2) || a.blk_na * a.blk_nb > JET_SPLITK_G || c.gy != 1))
+        return cudaErrorInvalidValue;
+    // staged form: complex64 only, its tables and two buffers of 2 B vectors within the default
+    // 48 KB of shared memory, every inner entry one of a thread's U = 4 loads
+    if (na == 66 && (fp64 || !a.qB || a.n_klo > 4 * (int)c.block ||
+                     smem < (((size_t)3 * a.n_klo * 4 + 15) & ~(size_t)15) + (size_t)2 * 2 * (a.n_klo + (a.n_klo >> 5)) * 8 ||
+                     smem > 48 * 1024 - sizeof(float2) * JET_SPLITK_G * 8))
         return cudaErrorInvalidValue;
 #define JET_DIRECT_LAUNCH(V, P)                                                                 \
     do {                                                                                        \
@@ -542,6 +631,7 @@ cudaError_t launch_direct(const DirectArgs &a, const LaunchCfg &c, cudaStream_t 
             case 32: direct_splitk_kernel<V, P, 32><<<grid, c.block, smem, s>>>(a); break;      \
             case 64: direct_splitk_kernel<V, P, 64><<<grid, c.block, smem, s>>>(a); break;      \
             case 65: direct_splitk_kernel<V, P, 65><<<grid, c.block, smem, s>>>(a); break;      \
+            case 66: direct_splitk_kernel<V, P, 66><<<grid, c.block, smem, s>>>(a); break;      \
             default: direct_splitk_kernel<V, P, 0><<<grid, c.block, smem, s>>>(a); break;       \
             }                                                                                   \
         } else direct_kernel<V, P><<<grid, c.block, smem, s>>>(a);                              \

@@ -60,12 +60,15 @@ struct DirectArgs {
                                     // x 8 / NA of B; 16 + NB (NB in {2, 4}) = NB of B fastest;
                                     // 32 = a single output (a dot product); 64 = dot
                                     // products of instance blocks (below; 65: blocks of at
-                                    // most 2 x 2)
+                                    // most 2 x 2; 66: the same with B staged, below)
     uint64_t itab;                  // splitk_na 64, 65: block b (blockIdx.z) holds node instances
                                     // itab[(b blk_na + j) blk_nb + l], their A the A of
                                     // instance (j, 0), their B the B of instance (0, l): each
                                     // operand value is loaded once for blk_na x blk_nb outputs
     int32_t blk_na, blk_nb;
+    uint64_t qB;                    // splitk_na 66 (2 x 2 blocks, B staged in shared memory): kB
+                                    // lists B's inner entries in increasing B offset and
+                                    // device int32[n_klo] qB their inner index q (A's kA order)
     int64_t row_dim[JET_MAXR], row_sA[JET_MAXR], row_sB[JET_MAXR];   // fastest label first
     int64_t khi_dim[JET_MAXR], khi_sA[JET_MAXR], khi_sB[JET_MAXR];   // fastest label first
 };

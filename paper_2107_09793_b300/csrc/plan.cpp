@@ -1089,8 +1089,31 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     }
                 }
             }
+            // 2 x 2 block dot products whose operands order the inner entries
+            // differently (B's entries of 32 consecutive q not adjacent): B is read in
+            // its own order (kB sorted by offset, qB each entry's q) and staged in
+            // shared memory, so that both operands' warp loads cover whole lines
+            std::vector<int32_t> qB;
+            if (d.splitk_na == 65 && !fp64 && nklo >= 64) {
+                bool adjacent = true;
+                for (int64_t q = 1; q < 32 && adjacent; ++q) adjacent = kB[q] == kB[0] + q;
+                if (!adjacent) {
+                    std::vector<int32_t> js(nklo);
+                    for (int64_t j = 0; j < nklo; ++j) js[j] = (int32_t)j;
+                    std::stable_sort(js.begin(), js.end(), [&](int32_t x, int32_t y) { return kB[x] < kB[y]; });
+                    std::vector<int32_t> kB2(nklo);
+                    qB.resize(nklo);
+                    for (int64_t j = 0; j < nklo; ++j) {
+                        kB2[j] = kB[js[j]];
+                        qB[j] = js[j];
+                    }
+                    kB.swap(kB2);
+                    d.splitk_na = 66;
+                }
+            }
             size_t off_colA = blob.put_i32(colA), off_colB = blob.put_i32(colB);
             size_t off_kA = blob.put_i32(kA), off_kB = blob.put_i32(kB);
+            size_t off_qB = qB.empty() ? 0 : blob.put_i32(qB);
             size_t off_pa = blob.put_ptrs(pa), off_pb = blob.put_ptrs(pb), off_pc = blob.put_ptrs(pc);
             size_t off_itab = blk_itab.empty() ? 0 : blob.put_i32(blk_itab);
             if (!blk_itab.empty()) d.n_inst = (int32_t)n_launch_inst;   // the kernel's blocks
@@ -1121,6 +1144,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             blob.patch_field(so, offsetof(DirectArgs, kB), BASE_BLOB, (int64_t)off_kB);
             if (d.ksplit > 1) blob.patch_field(so, offsetof(DirectArgs, partials), BASE_ARENA, (int64_t)part_off);
             if (!blk_itab.empty()) blob.patch_field(so, offsetof(DirectArgs, itab), BASE_BLOB, (int64_t)off_itab);
+            if (!qB.empty()) blob.patch_field(so, offsetof(DirectArgs, qB), BASE_BLOB, (int64_t)off_qB);
             Op op;
             op.kind = OpKind::Direct;
             op.node = v;
@@ -1148,6 +1172,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 op.grid_y = (int32_t)gy;
             }
             op.smem = (int32_t)(8 * ncols + 8 * nklo);
+            if (d.splitk_na == 66)   // tables kA, kB, qB; two buffers of 2 B vectors, one padding entry per 32
+                op.smem = (int32_t)(((3 * nklo * 4 + 15) & ~(int64_t)15) + 2 * 2 * (nklo + (nklo >> 5)) * 8);
             P.ops.push_back(op);
             if (d.ksplit > 1) {
                 SplitKReduceArgs r;

@@ -83,14 +83,17 @@ def test_split_k_forms(case, prec, tol):
 # y labels and z sliced (x on both operands, the y labels and z joined by Y
 # after the pair).  The pair's instances (x, y..., z) form 2 blocks (x = 0, 1)
 # of 2^len(y) A instances x 2 B instances; each block's dot products read every
-# operand value once (2 x 2 blocks: the two-by-two form; 4 x 2: the general one).
-@pytest.mark.parametrize("ny,form", [(1, 65), (2, 64)])
+# operand value once (2 x 2 blocks: the two-by-two form, with B staged in shared
+# memory when the operands order the summed labels differently (FP32); 4 x 2:
+# the general one).
+@pytest.mark.parametrize("ny,crossed", [(1, True), (1, False), (2, True)])
 @pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp64", 1e-13)])
-def test_split_k_instance_block_dot_products(prec, tol, ny, form):
+def test_split_k_instance_block_dot_products(prec, tol, ny, crossed):
     from oracle.einsum import slice_network
+    form = 64 if ny == 2 else 66 if crossed and prec == "fp32" else 65
     x, z = 200, 202
     ys = list(range(210, 210 + ny))
-    la, lb = [x] + ys + K[:8] + K[8:], [x, z] + K[8:] + K[:8]
+    la, lb = [x] + ys + K[:8] + K[8:], [x, z] + (K[8:] + K[:8] if crossed else K[:8] + K[8:])
     A = _rand(7001 + ny, [2] * len(la)).astype(np.complex64)
     B = _rand(7002, [2] * len(lb)).astype(np.complex64)
     Y = _rand(7003 + ny, [2] * (ny + 1)).astype(np.complex64)
