@@ -154,13 +154,16 @@ constexpr int SPLIT_ROW = SPLIT_TK + 2;   // padded tile row (float2; even: 16-b
 constexpr int SPLIT_SMEM = 2 * SPLIT_TR * SPLIT_ROW * 8               // two tiles
                            + 2 * (SPLIT_TR + SPLIT_TK) * 8;           // their row / column offsets
 
+// (no memory clobber: the copies' shared-memory writes are ordered by the
+// wait_group and barrier that follow, which carry it; the offsets they read
+// stay in registers across a tile's copies)
 __device__ __forceinline__ void cp_async8_zfill(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
 }
 __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, uint32_t src_bytes)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
 }
 
 // Tiled gather + split: a block walks 64-row x 64-column tiles of the planes.
@@ -227,20 +230,31 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
             }
             return;
         }
+        if (a.fast_k) {
+#pragma unroll
+            for (int i = 0; i < (SPLIT_TR * SPLIT_TK) / 256; ++i) {
+                const int kk = tid & (SPLIT_TK - 1), r = (tid >> 6) + (256 / SPLIT_TK) * i;
+                const int64_t ro = rowOff[r], ko = kOff[kk];
+                const bool in = ro >= 0 && ko >= 0;
+                cp_async8_zfill(smem_u32(tile + r * SPLIT_ROW + kk), in ? (const void *)(S + ro + ko) : (const void *)S,
+                                in ? 8u : 0u);
+            }
+            return;
+        }
+        // rows along the source's fastest label: a warp takes 16 rows x 2 columns
+        // (two 128-byte runs of a row-contiguous source; with 66-entry tile rows
+        // the 32 lanes' 8-byte writes fall on all 32 banks, two wavefronts)
+        static_assert(SPLIT_TR == 64 && SPLIT_TK == 64 && SPLIT_ROW == 66, "warp: 16 rows x 2 columns");
+        const int lane = tid & 31, w = tid >> 5;
+        const int r = 16 * (w & 3) + (lane & 15), kk0 = 2 * (w >> 2) + (lane >> 4);
+        const int64_t ro = rowOff[r];
+        const float2 *Sr = S + (ro >= 0 ? ro : 0);
+        const uint32_t dst0 = smem_u32(tile + r * SPLIT_ROW + kk0);
 #pragma unroll
         for (int i = 0; i < (SPLIT_TR * SPLIT_TK) / 256; ++i) {
-            int r, kk;
-            if (a.fast_k) {
-                kk = tid & (SPLIT_TK - 1);
-                r = (tid >> 6) + (256 / SPLIT_TK) * i;
-            } else {
-                r = tid & (SPLIT_TR - 1);
-                kk = (tid >> 6) + (256 / SPLIT_TR) * i;
-            }
-            const int64_t ro = rowOff[r], ko = kOff[kk];
+            const int64_t ko = kOff[kk0 + 4 * i];
             const bool in = ro >= 0 && ko >= 0;
-            cp_async8_zfill(smem_u32(tile + r * SPLIT_ROW + kk), in ? (const void *)(S + ro + ko) : (const void *)S,
-                            in ? 8u : 0u);
+            cp_async8_zfill(dst0 + 4 * i * 8, in ? (const void *)(Sr + ko) : (const void *)S, in ? 8u : 0u);
         }
     };
 
