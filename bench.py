@@ -1216,7 +1216,9 @@ def run_grid53_case(args):
     amps = torch.zeros(1, dtype=torch.complex128, device="cuda")
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    net.autotune(w.outputs, stream=stream.cuda_stream)   # the headline's per-node forms
+    # the headline's per-node forms (--tune-cache: the same choices in a second
+    # run, e.g. one under a profiler, whose timings would choose differently)
+    net.autotune(w.outputs, cache_file=args.tune_cache, stream=stream.cuda_stream)
     for _ in range(args.warmup):
         net.contract_async(w.outputs, amps.data_ptr(), stream.cuda_stream)
     torch.cuda.synchronize()
@@ -1259,6 +1261,8 @@ def main():
     ap.add_argument("--impl", default="jet", choices=["jet", "reference"])
     ap.add_argument("--precision", default="fp16x3", choices=["fp32", "tf32", "tf32x3", "bf16x3", "bf16x6", "fp16x3", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--tune-cache", default=None, help="--case grid53: autotune choices file (read if it "
+                                                         "holds every node, else written)")
     ap.add_argument("--skip-fp32", action="store_true", help="skip the other arithmetic modes")
     ap.add_argument("--skip-others", action="store_true", help="skip the other workloads (bosonic lattice, "
                     "parameterised circuit gradient, 53-qubit slices)")

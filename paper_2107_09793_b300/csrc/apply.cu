@@ -15,6 +15,7 @@
 // coalesced whenever the summed labels are not the fastest ones.  The
 // contraction is HBM-bound (8 * nk * nf FLOP per 8 * (nk + nf) bytes).
 #include <type_traits>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -460,6 +461,70 @@ __device__ __forceinline__ void atc_fill_b(const ApplyArgs &a, const float2 *__r
     }
 }
 
+// FP16 form: the power-of-two exponent that brings a chunk's largest magnitude
+// m into [2^14, 2^15) (m = f 2^e, f in [0.5, 1), e = biased exponent - 126 for
+// normal m; clamped to [-100, 100], 0 for m = 0), and 2^x as a float.
+__device__ __forceinline__ int atc_exp16(float m)
+{
+    return m > 0.f ? max(-100, min(100, 141 - (int)((__float_as_uint(m) >> 23) & 0xffu))) : 0;
+}
+__device__ __forceinline__ float atc_pow2(int x) { return __uint_as_float((uint32_t)(127 + x) << 23); }
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *(const uint32_t *)&h; }
+// x = hi + lo up to rounding, both FP16 (x already scaled into FP16's range)
+__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    hi = h2u(h);
+    lo = h2u(__floats2half2_rn(x0 - hf.x, x1 - hf.y));
+}
+
+// FP16 form of atc_fill_b: K block kb holds 16 summed entries (32 halves, 64
+// bytes) of each row; row r (= 2f + c') is scaled by 2^bex[sc nrl + r] in
+// chunk sc of 32 entries (bex: the exponents, binv: their inverses, kept for
+// the epilogue).
+__device__ __forceinline__ void atc_fill_b16(const ApplyArgs &a, const float2 *__restrict__ B, uint32_t sB, int nkb16,
+                                             int nrl, uint32_t bplane, int tid, int nthr, int *bex, float *binv)
+{
+    const int nsc = (a.nk + 31) >> 5;
+    for (int i = tid; i < nsc * nrl; i += nthr) {   // one (chunk, row) per step: its largest magnitude
+        const int sc = i / nrl, row = i - sc * nrl, f = row >> 1;
+        float mx = 0.f;
+        if (f < a.nf)
+            for (int q = 32 * sc; q < min(a.nk, 32 * sc + 32); ++q) {
+                const float2 b = B[a.bF[f] + a.bK[q]];
+                mx = fmaxf(mx, fmaxf(fabsf(b.x), fabsf(b.y)));
+            }
+        const int ex = atc_exp16(mx);
+        bex[i] = ex;
+        binv[i] = atc_pow2(-ex);
+    }
+    __syncthreads();
+    const int per_blk = nrl * 4;   // 16-byte chunks per K block
+    for (int i = tid; i < nkb16 * per_blk; i += nthr) {
+        const int kb = i / per_blk, rem = i - kb * per_blk, row = rem >> 2, j = rem & 3;
+        const int f = row >> 1, q0 = kb * 16 + 4 * j;
+        const float sf = atc_pow2(bex[(q0 >> 5) * nrl + row]);
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = q0 + e;
+            float2 b = make_float2(0.f, 0.f);
+            if (f < a.nf && q < a.nk) b = B[a.bF[f] + a.bK[q]];
+            // imaginary output row: Bi * Ar + Br * Ai; real: Br * Ar - Bi * Ai
+            const float v0 = (row & 1) ? b.y : b.x, v1 = (row & 1) ? b.x : -b.y;
+            split_h2(v0 * sf, v1 * sf, hi[e], lo[e]);
+        }
+        const uint32_t off = (uint32_t)kb * (uint32_t)(nrl * 64) + sw64(row, j);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sB + off), "r"(hi[0]), "r"(hi[1]), "r"(hi[2]),
+                     "r"(hi[3])
+                     : "memory");
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sB + bplane + off), "r"(lo[0]), "r"(lo[1]),
+                     "r"(lo[2]), "r"(lo[3])
+                     : "memory");
+    }
+}
+
 // Bounded mbarrier wait, inlined so that the gathers a thread has in flight
 // stay in flight across it (~2 s, or until another group has given up).
 __device__ __forceinline__ bool mbar_wait_inline(uint32_t bar, uint32_t parity, volatile int *abort_flag)
@@ -482,11 +547,16 @@ __device__ __forceinline__ bool mbar_wait_inline(uint32_t bar, uint32_t parity, 
 // groups): each gathered chunk of 32 is staged in two halves of 16 summed
 // entries accumulated in the same TMEM columns (as many accumulations per
 // promotion as a whole chunk).
-template <int G, bool MULTI, bool POW2, bool HALF>
+// F16: FP16 hi + lo parts (kind::f16, 16 summed reals per MMA) with a
+// power-of-two scale per row and 32-entry chunk of each operand, undone when
+// the chunk is promoted, instead of TF32 hi + lo (8 per MMA): half the MMAs and
+// half the plane bytes for the same three products.
+template <int G, bool MULTI, bool POW2, bool HALF, bool F16>
 __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant__ ApplyArgs a)
 {
     constexpr int KC = HALF ? ATC_KC / 2 : ATC_KC;   // summed entries per staged chunk
-    constexpr uint32_t ABY = HALF ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;   // a group's A planes
+    constexpr int EK = F16 ? 16 : 8;                 // summed entries per 64-byte K block of a plane row
+    constexpr uint32_t ABY = (HALF ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES) / (F16 ? 2 : 1);   // a group's A planes
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[G];
     __shared__ uint32_t tmem_holder;
@@ -494,12 +564,16 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, g = tid >> 7, m = tid & 127, warp = tid >> 5;
     const int nk = a.nk, nf = a.nf, nkb = (nk + 7) >> 3, nch = (MULTI || HALF) ? (nk + KC - 1) / KC : 1;
+    const int nkbx = (nk + EK - 1) / EK;    // K blocks of the small operand's planes
     const int nr = (nf + 7) >> 3;           // 16-column groups of D (8 complex outputs each)
     const int nrl = 16 * nr;                // real columns: the MMA's N
     const uint32_t bplane = (uint32_t)(nkb * nrl * 64);
     const int64_t T = (a.n_fib + ATC_M - 1) / ATC_M, U = (T + G - 1) / G, total = U * a.n_inst;
     const int64_t u0 = total * blockIdx.x / gridDim.x, u1 = total * (blockIdx.x + 1) / gridDim.x;
     const uint32_t sA = smem_u32(smem + g * ABY), sB = smem_u32(smem + G * ABY);
+    // F16: the small operand's exponents and inverse scales per (32-entry chunk, row)
+    int *bex = (int *)(smem + G * ABY + 2 * (size_t)nkb * (16 * ((nf + 7) >> 3)) * 64);
+    float *binv = (float *)(bex + 512);
     const uint32_t bar = smem_u32(&bars[g]);
     const uint64_t *pA = (const uint64_t *)a.ptrA, *pB = (const uint64_t *)a.ptrB, *pC = (const uint64_t *)a.ptrC;
     // TMEM columns per group (the MMA's N: up to 64, 128 or 256), allocated as a power of two
@@ -520,8 +594,10 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder + span * g;
     const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-    // kind::tf32, FP32 D, K-major A and B, M = 128, N = nrl
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nrl >> 3) << 17) | ((uint32_t)(ATC_M >> 4) << 24);
+    // kind::tf32 (operand format 2) or kind::f16 with F16 operands (0), FP32 D,
+    // K-major A and B, M = 128, N = nrl
+    constexpr uint32_t FMT = F16 ? 0u : 2u;
+    const uint32_t idesc = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(nrl >> 3) << 17) | ((uint32_t)(ATC_M >> 4) << 24);
     const int terms = a.tc_terms;
 
     // Unit u is tile group u % U of instance u / U; positions advance by counters.
@@ -597,7 +673,8 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
         }
         if (inst != cur_inst) {   // CTA-uniform: every group's MMAs on the old planes have completed
             __syncthreads();
-            atc_fill_b(a, (const float2 *)pB[inst], sB, nkb, nrl, bplane, tid, 128 * G);
+            if (F16) atc_fill_b16(a, (const float2 *)pB[inst], sB, nkbx, nrl, bplane, tid, 128 * G, bex, binv);
+            else atc_fill_b(a, (const float2 *)pB[inst], sB, nkb, nrl, bplane, tid, 128 * G);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             cur_inst = inst;
@@ -607,12 +684,49 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
         const int64_t r = (tt * G + g) * ATC_M + m;
         const bool rok = r < a.n_fib;
         const int64_t oc = oc_next;
+        float a_inv = 1.f;   // F16: the inverse of this fiber's scale in the current chunk of 32
         for (int c = 0; c < nch; ++c) {
-            const int kv = min(KC, nk - c * KC), kbc = (kv + 7) >> 3;
+            const int kv = min(KC, nk - c * KC), kbc = (kv + EK - 1) / EK;
+            const int sc = HALF ? c >> 1 : c;   // the chunk of 32 entries (scale chunk)
+            float a_f = 1.f;
+            if (F16) {   // the chunk's scale, from all 32 gathered entries (zeros past the end)
+                if (!HALF || !(c & 1)) {
+                    float mx = 0.f;
+#pragma unroll
+                    for (int q = 0; q < ATC_KC; ++q) {
+                        const float2 v = unpack2(X[q]);
+                        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+                    }
+                    const int ex = atc_exp16(mx);
+                    a_inv = atc_pow2(-ex);
+                }
+                a_f = 1.f / a_inv;   // exact: a power of two in range
+            }
             // split the staged entries X[OFF ..] into the hi / lo planes of row m
             // (OFF a compile-time offset: the second half of a chunk)
             auto stage = [&](auto off_tag) {
                 constexpr int OFF = decltype(off_tag)::value;
+                if (F16) {   // 4 entries (8 halves) per 16-byte chunk, 4 chunks per K block
+#pragma unroll
+                    for (int p = 0; p < KC / 4; ++p) {
+                        if ((p >> 2) < kbc) {
+                            uint32_t hi[4], lo[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float2 v = unpack2(X[OFF + 4 * p + e]);
+                                split_h2(v.x * a_f, v.y * a_f, hi[e], lo[e]);
+                            }
+                            const uint32_t off = (uint32_t)(p >> 2) * ATC_KBB + sw64(m, p & 3);
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sA + off), "r"(hi[0]),
+                                         "r"(hi[1]), "r"(hi[2]), "r"(hi[3])
+                                         : "memory");
+                            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sA + ABY / 2 + off),
+                                         "r"(lo[0]), "r"(lo[1]), "r"(lo[2]), "r"(lo[3])
+                                         : "memory");
+                        }
+                    }
+                    return;
+                }
 #pragma unroll
                 for (int p = 0; p < KC / 2; ++p) {
                     if ((p >> 2) < kbc) {
@@ -661,8 +775,8 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                             const int pa = t == 2, pb = t == 1;   // hi.hi, hi.lo, lo.hi
                             const uint64_t ad = sdesc(sA + pa * (ABY / 2) + kb * ATC_KBB + sub * 32);
                             const uint64_t bd =
-                                sdesc(sB + pb * bplane + (uint32_t)(c * (KC / 8) + kb) * (uint32_t)(nrl * 64) + sub * 32);
-                            umma<1>(tmem, ad, bd, idesc, ((HALF ? (c & 1) : 0) | kb | sub | t) ? 1u : 0u);
+                                sdesc(sB + pb * bplane + (uint32_t)(c * (KC / EK) + kb) * (uint32_t)(nrl * 64) + sub * 32);
+                            umma<F16 ? 0 : 1>(tmem, ad, bd, idesc, ((HALF ? (c & 1) : 0) | kb | sub | t) ? 1u : 0u);
                         }
                 umma_commit(bar);
             }
@@ -674,21 +788,21 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                 // planes lie below 256 KB, so an add never carries out of that field).
                 // Products per (K block, 32-byte half): hi.hi, hi.lo, lo.hi.
                 const uint64_t ad0 = sdesc(sA);
-                const uint64_t bd0 = sdesc(sB + (uint32_t)(c * (KC / 8)) * (uint32_t)(nrl * 64));
+                const uint64_t bd0 = sdesc(sB + (uint32_t)(c * (KC / EK)) * (uint32_t)(nrl * 64));
                 const uint64_t b_kb = (uint64_t)(nrl * 4), b_lo = (uint64_t)(bplane >> 4);
                 constexpr uint64_t a_lo = (ABY / 2) >> 4;
                 const uint32_t acc0 = HALF ? (uint32_t)(c & 1) : 0u;   // a second half adds to the first in TMEM
 #pragma unroll
-                for (int kb = 0; kb < KC / 8; ++kb) {
+                for (int kb = 0; kb < KC / EK; ++kb) {
                     if (kb < kbc) {
 #pragma unroll
                         for (int sub = 0; sub < 2; ++sub) {
                             const uint64_t ad = ad0 + (uint64_t)((kb * ATC_KBB + sub * 32) >> 4);
                             const uint64_t bd = bd0 + (uint64_t)kb * b_kb + (uint64_t)(sub * 2);
-                            umma<1>(tmem, ad, bd, idesc, (acc0 | (uint32_t)kb | (uint32_t)sub) ? 1u : 0u);
+                            umma<F16 ? 0 : 1>(tmem, ad, bd, idesc, (acc0 | (uint32_t)kb | (uint32_t)sub) ? 1u : 0u);
                             if (terms > 1) {
-                                umma<1>(tmem, ad, bd + b_lo, idesc, 1u);
-                                umma<1>(tmem, ad + a_lo, bd, idesc, 1u);
+                                umma<F16 ? 0 : 1>(tmem, ad, bd + b_lo, idesc, 1u);
+                                umma<F16 ? 0 : 1>(tmem, ad + a_lo, bd, idesc, 1u);
                             }
                         }
                     }
@@ -711,10 +825,14 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
             // 16-column groups of D
             constexpr int HMAX = MULTI ? JET_APPLY_TC_MAXF_MULTI / 8 : HALF ? JET_APPLY_TC_MAXF / 8 : JET_APPLY_TC_WIDEF / 8;
             auto emit = [&](const int h, const uint32_t (&R)[16]) {
+                // F16: undo the fiber's and the column's scales of this chunk
+                float sbv[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) sbv[j] = F16 ? a_inv * binv[sc * nrl + 16 * h + j] : 1.f;
                 if (MULTI) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float v = __uint_as_float(R[j]);
+                        const float v = F16 ? __uint_as_float(R[j]) * sbv[j] : __uint_as_float(R[j]);
                         acc[(16 * h + j) % (MULTI ? 64 : 1)] = first ? v : acc[(16 * h + j) % (MULTI ? 64 : 1)] + v;
                     }
                 }
@@ -723,9 +841,10 @@ __global__ void __launch_bounds__(128 * G, 1) apply_tc_c64(const __grid_constant
                     for (int j = 0; j < 8; ++j) {
                         const int f = 8 * h + j;
                         if (f < nf) {
-                            const float re = MULTI ? acc[(16 * h + 2 * j) % (MULTI ? 64 : 1)] : __uint_as_float(R[2 * j]);
+                            const float re = MULTI ? acc[(16 * h + 2 * j) % (MULTI ? 64 : 1)]
+                                                   : __uint_as_float(R[2 * j]) * sbv[2 * j];
                             const float im = MULTI ? acc[(16 * h + 2 * j + 1) % (MULTI ? 64 : 1)]
-                                                   : __uint_as_float(R[2 * j + 1]);
+                                                   : __uint_as_float(R[2 * j + 1]) * sbv[2 * j + 1];
                             __stcs(C + oc + a.cF[f], pack2(re, im));
                         }
                     }
@@ -828,7 +947,10 @@ cudaError_t set_apply_tc_smem_limits()
     cudaError_t e = cudaSuccess;
 #define JET_ATCSM(G, MU, P2, W)                                                                                   \
     if (e == cudaSuccess)                                                                                         \
-        e = cudaFuncSetAttribute(apply_tc_c64<G JET_COMMA MU JET_COMMA P2 JET_COMMA W>,                            \
+        e = cudaFuncSetAttribute(apply_tc_c64<G JET_COMMA MU JET_COMMA P2 JET_COMMA W JET_COMMA false>,            \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ATC_SMEM_MAX);                      \
+    if (e == cudaSuccess)                                                                                         \
+        e = cudaFuncSetAttribute(apply_tc_c64<G JET_COMMA MU JET_COMMA P2 JET_COMMA W JET_COMMA true>,             \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ATC_SMEM_MAX)
     JET_ATCSM(2, true, true, false);
     JET_ATCSM(2, true, false, false);
@@ -844,36 +966,44 @@ cudaError_t set_apply_tc_smem_limits()
     return e;
 }
 
+template <bool F16>
+static void launch_apply_tc_form(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s, int G, bool pow2, bool multi,
+                                 bool half, int smem)
+{
+    if (multi && half) {
+        if (pow2) apply_tc_c64<2, true, true, true, F16><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, true, false, true, F16><<<c.gx, 256, smem, s>>>(a);
+    } else if (multi) {
+        if (pow2) apply_tc_c64<2, true, true, false, F16><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, true, false, false, F16><<<c.gx, 256, smem, s>>>(a);
+    } else if (half) {
+        if (pow2) apply_tc_c64<2, false, true, true, F16><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, false, false, true, F16><<<c.gx, 256, smem, s>>>(a);
+    } else if (G == 2) {
+        if (pow2) apply_tc_c64<2, false, true, false, F16><<<c.gx, 256, smem, s>>>(a);
+        else apply_tc_c64<2, false, false, false, F16><<<c.gx, 256, smem, s>>>(a);
+    } else {
+        if (pow2) apply_tc_c64<3, false, true, false, F16><<<c.gx, 384, smem, s>>>(a);
+        else apply_tc_c64<3, false, false, false, F16><<<c.gx, 384, smem, s>>>(a);
+    }
+}
+
 static cudaError_t launch_apply_tc(const ApplyArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
     const int G = c.block / 128;
     if ((G != 2 && G != 3) || c.block != 128 * G || a.nk < 1 || a.nk > JET_APPLY_MAXK || a.nf < 1 ||
-        a.nf > JET_APPLY_TC_MAXF || (a.tc_terms != 1 && a.tc_terms != 3) || a.rank > JET_MAXR || a.n_inst < 1 ||
-        a.n_fib < 1 || !a.status || (c.variant & 1) || c.gx < 1 || c.gy != 1)
+        a.nf > JET_APPLY_TC_MAXF || (a.tc_terms != 1 && a.tc_terms != 3) || (a.tc_f16 && a.tc_terms != 3) ||
+        a.rank > JET_MAXR || a.n_inst < 1 || a.n_fib < 1 || !a.status || (c.variant & 1) || c.gx < 1 || c.gy != 1)
         return cudaErrorInvalidValue;
-    const int smem = jet_apply_tc_smem(G, a.nk, a.nf);
+    const int smem = jet_apply_tc_smem(G, a.nk, a.nf, a.tc_f16);
     if (smem > ATC_SMEM_MAX) return cudaErrorInvalidValue;
     const bool pow2 = c.variant & 4, multi = a.nk > ATC_KC, half = jet_apply_tc_half(a.nk, a.nf);
     // promotion registers: two groups and at most 32 free entries only; halves:
     // two groups (up to 256 TMEM columns each)
     if (multi && (G != 2 || a.nf > JET_APPLY_TC_MAXF_MULTI)) return cudaErrorInvalidValue;
     if (half && G != 2) return cudaErrorInvalidValue;
-    if (multi && half) {
-        if (pow2) apply_tc_c64<2, true, true, true><<<c.gx, 256, smem, s>>>(a);
-        else apply_tc_c64<2, true, false, true><<<c.gx, 256, smem, s>>>(a);
-    } else if (multi) {
-        if (pow2) apply_tc_c64<2, true, true, false><<<c.gx, 256, smem, s>>>(a);
-        else apply_tc_c64<2, true, false, false><<<c.gx, 256, smem, s>>>(a);
-    } else if (half) {
-        if (pow2) apply_tc_c64<2, false, true, true><<<c.gx, 256, smem, s>>>(a);
-        else apply_tc_c64<2, false, false, true><<<c.gx, 256, smem, s>>>(a);
-    } else if (G == 2) {
-        if (pow2) apply_tc_c64<2, false, true, false><<<c.gx, 256, smem, s>>>(a);
-        else apply_tc_c64<2, false, false, false><<<c.gx, 256, smem, s>>>(a);
-    } else {
-        if (pow2) apply_tc_c64<3, false, true, false><<<c.gx, 384, smem, s>>>(a);
-        else apply_tc_c64<3, false, false, false><<<c.gx, 384, smem, s>>>(a);
-    }
+    if (a.tc_f16) launch_apply_tc_form<true>(a, c, s, G, pow2, multi, half, smem);
+    else launch_apply_tc_form<false>(a, c, s, G, pow2, multi, half, smem);
     return cudaGetLastError();
 }
 

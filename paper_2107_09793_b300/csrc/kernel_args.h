@@ -32,11 +32,13 @@ static inline bool jet_apply_tc_half(int nk, int nf)
     const int nkb = (nk + 7) / 8, nr = 2 * ((nf + 7) / 8 * 8);
     return nf > JET_APPLY_TC_WIDEF || 1024 + 2 * JET_APPLY_TC_ABYTES + 2 * nkb * nr * 64 > JET_APPLY_TC_SMEM_MAX;
 }
-static inline int jet_apply_tc_smem(int groups, int nk, int nf)
+// (f16: the FP16 form's A planes take half the bytes; its small operand's
+// exponents and their inverses follow the planes, 512 of each)
+static inline int jet_apply_tc_smem(int groups, int nk, int nf, int f16 = 0)
 {
     const int nkb = (nk + 7) / 8, nr = 2 * ((nf + 7) / 8 * 8);
-    const int abytes = jet_apply_tc_half(nk, nf) ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES;
-    return 1024 + groups * abytes + 2 * nkb * nr * 64;
+    const int abytes = (jet_apply_tc_half(nk, nf) ? JET_APPLY_TC_ABYTES / 2 : JET_APPLY_TC_ABYTES) / (f16 ? 2 : 1);
+    return 1024 + groups * abytes + 2 * nkb * nr * 64 + (f16 ? 512 * 8 : 0);
 }
 
 // Pairwise contraction C = sum_K A * B evaluated directly from strides
@@ -83,7 +85,10 @@ struct ApplyArgs {
     int32_t n_inst, nk, nf, rank;   // nk <= nk_tmpl (entries nk..nk_tmpl-1 are padding)
     int32_t nk_tmpl;                // held form: compile-time summed extent
     int32_t nf_tmpl;                // streamed form (nf_tmpl > 0): free entries per register chunk
-    int32_t tc_terms, pad_;         // tensor-core form: TF32 products per real product (1 or 3)
+    int32_t tc_terms;               // tensor-core form: products per real product (1 or 3)
+    int32_t tc_f16;                 // tensor-core form, 3 terms: FP16 hi + lo parts with a power-of-two
+                                    // scale per row and 32-entry chunk (kind::f16, K = 16 per MMA)
+                                    // instead of TF32 hi + lo (K = 8)
     int64_t kA[JET_APPLY_MAXK], bK[JET_APPLY_MAXK];   // summed entry q: offset in A, in B
     int64_t cF[JET_APPLY_MAXF], bF[JET_APPLY_MAXF];   // B-free entry f: offset in C, in B
     int64_t dim[JET_MAXR], sA[JET_MAXR], sC[JET_MAXR];

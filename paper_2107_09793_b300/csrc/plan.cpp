@@ -1322,6 +1322,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const int64_t n_launch = nB > 1 ? (int64_t)gl.size() : n_inst;   // one unit per large instance
         d.n_inst = (int32_t)n_launch;
         d.tc_terms = net.opt.precision == JET_PREC_TF32 ? 1 : 3;
+        d.tc_f16 = net.opt.precision == JET_PREC_FP16X3 ? 1 : 0;   // (tensor-core form: FP16 hi + lo parts)
         size_t off_pl = blob.put_ptrs(nB > 1 ? gl : (a_big ? pa : pb)), off_ps = blob.put_ptrs(nB > 1 ? gs : (a_big ? pb : pa));
         size_t off_pc = blob.put_ptrs(nB > 1 ? gc : pc);
         size_t so = blob.reserve(sizeof d);
@@ -1357,7 +1358,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             const int64_t units = n_launch * (((d.n_fib + 127) / 128 + G - 1) / G);
             op.variant |= 8;
             op.block = 128 * G;
-            op.smem = jet_apply_tc_smem(G, (int)nk, (int)nf);
+            op.smem = jet_apply_tc_smem(G, (int)nk, (int)nf, d.tc_f16);
             op.grid_x = (int32_t)std::min<int64_t>(148, units);
             op.grid_y = 1;
             P.ops.push_back(op);
