@@ -801,7 +801,7 @@ static void contract_in_ranges(Network &net, int32_t n_amps, const int32_t *outp
         part.resize((size_t)n_amps * n_ids * n_elem);
         copy_d2h(part.data(), net.d_amps, part.size() * sizeof(jet_c128), s);
         if (read_clear_status(net, stream))
-            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (status bits: 1 GEMM, 2 application, 8 chain barrier)");
         mark_kept(net, P, stream);
         for (int32_t b = 0; b < n_amps; ++b)
             for (int64_t j = 0; j < n_ids; ++j)
@@ -855,7 +855,7 @@ int jet_contract(jet_network *net, int32_t n_amps, const int32_t *outputs, jet_c
         copy_d2h(amps_out, net->d_amps, (size_t)n_amps * P.n_elem * sizeof(jet_c128),
                  cuda_stream ? cuda_stream : net->stream);
         if (read_clear_status(*net, cuda_stream))
-            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (status bits: 1 GEMM, 2 application, 8 chain barrier)");
         mark_kept(*net, P, cuda_stream);
     });
 }
@@ -871,7 +871,7 @@ int jet_contract_slices(jet_network *net, int32_t n_amps, const int32_t *outputs
         copy_d2h(partials_out, net->d_amps, (size_t)n_amps * n_ids * P.n_elem * sizeof(jet_c128),
                  cuda_stream ? cuda_stream : net->stream);
         if (read_clear_status(*net, cuda_stream))
-            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+            fail(JET_ETIMEOUT, "a bounded device-side wait ran out (status bits: 1 GEMM, 2 application, 8 chain barrier)");
         mark_kept(*net, P, cuda_stream);
     });
 }
@@ -969,7 +969,7 @@ int jet_contract_grad(jet_network *net, int32_t n_amps, const int32_t *outputs, 
                 amps[2 * b + 1] += part[b].im;
             }
             if (read_clear_status(*net, cuda_stream))
-                fail(JET_ETIMEOUT, "a bounded device-side wait ran out (tensor-core GEMM)");
+                fail(JET_ETIMEOUT, "a bounded device-side wait ran out (status bits: 1 GEMM, 2 application, 8 chain barrier)");
         }
         std::vector<jet_c128> env((size_t)std::max<int64_t>(total, 1));
         copy_d2h(env.data(), net->d_env, (size_t)std::max<int64_t>(total, 1) * sizeof(jet_c128), s);

@@ -12,6 +12,7 @@
 
 #include "kernel_args.h"
 #include "kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace jet {
 
@@ -455,8 +456,109 @@ __global__ void __launch_bounds__(256) small_batch_kernel(const __grid_constant_
     }
 }
 
+// A chain of small levels in one cooperative launch (its blocks co-resident):
+// a level's items are spread over every thread of the grid (task by binary
+// search on its first item), and a grid barrier separates the levels.  One
+// launch instead of one per level, where each would be mostly launch latency.
+// The barrier is an arrival counter that block leaders wait on with a bounded
+// spin (1 s, then status bit 8 and the kernel stops); the last block out sets
+// both counters back to zero for the next launch.
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) small_chain_kernel(const __grid_constant__ SmallBatchArgs a)
+{
+    const SmallTask *T = (const SmallTask *)a.tasks;
+    __shared__ int32_t item0[JET_CHAIN_TASKS];   // the level's first items, searched here
+    __shared__ int stop;
+    uint32_t *arrive = (uint32_t *)a.barrier, *depart = arrive + 1;
+    if (threadIdx.x == 0) stop = 0;
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    int t0 = 0;
+    for (int l = 0; l < a.n_levels; ++l) {
+        const int t1 = a.lv_end[l];
+        __syncthreads();   // the previous level's readers of item0 are done
+        for (int k = threadIdx.x; k < t1 - t0; k += blockDim.x) item0[k] = T[t0 + k].block0;
+        __syncthreads();
+        const SmallTask &tl = T[t1 - 1];
+        const int64_t total = (int64_t)tl.block0 + (int64_t)tl.n_inst * tl.n_out;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += nthr) {
+            int lo = 0, hi = t1 - t0 - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if ((int64_t)item0[mid] <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            const SmallTask &t = T[t0 + lo];
+            const int64_t j = i - t.block0;
+            const int inst = (int)(j / t.n_out), o = (int)(j - (int64_t)inst * t.n_out);
+            const int32_t *__restrict__ kA = (const int32_t *)t.kA, *__restrict__ kB = (const int32_t *)t.kB;
+            const V *__restrict__ A = (const V *)((const uint64_t *)t.ptrA)[inst];
+            const V *__restrict__ B = (const V *)((const uint64_t *)t.ptrB)[inst];
+            V *__restrict__ C = (V *)((const uint64_t *)t.ptrC)[inst];
+            const int32_t xa = ((const int32_t *)t.offA)[o], xb = ((const int32_t *)t.offB)[o];
+            V acc = vzero<V>();
+            for (int q = 0; q < t.n_k; ++q) acc = cmul_add(acc, A[xa + kA[q]], B[xb + kB[q]]);
+            C[o] = acc;
+        }
+        t0 = t1;
+        if (l + 1 < a.n_levels) {   // every block's outputs of this level before any block reads them
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(arrive, 1u);
+                const uint32_t target = (uint32_t)(l + 1) * gridDim.x;
+                const uint64_t tw = globaltimer();
+                while (ld_acquire_u32(arrive) < target) {
+                    if (globaltimer() - tw > 1000000000ull) {
+                        stop = 1;
+                        atomicOr((unsigned int *)a.status, 8u);
+                        break;
+                    }
+                }
+                __threadfence();
+            }
+            __syncthreads();
+            if (stop) break;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // the last block out resets the counters
+        __threadfence();
+        if (atomicAdd(depart, 1u) == gridDim.x - 1) {
+            atomicExch(arrive, 0u);
+            atomicExch(depart, 0u);
+        }
+    }
+}
+
 cudaError_t launch_small_batch(const SmallBatchArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
+    if (c.variant & 2) {   // chain of small levels: one cooperative launch, at most one block per SM
+        if (a.n_levels < 1 || a.n_levels > JET_CHAIN_LEVELS || a.lv_end[a.n_levels - 1] != a.n_tasks || c.gx < 1 ||
+            c.gx > 148 || c.gx != a.n_blocks || !a.barrier || !a.status)
+            return cudaErrorInvalidValue;
+        for (int l = 0; l < a.n_levels; ++l)
+            if (a.lv_end[l] <= (l ? a.lv_end[l - 1] : 0) || a.lv_end[l] - (l ? a.lv_end[l - 1] : 0) > JET_CHAIN_TASKS)
+                return cudaErrorInvalidValue;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)c.gx);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (c.variant & 1) return cudaLaunchKernelEx(&cfg, small_chain_kernel<double2>, a);
+        return cudaLaunchKernelEx(&cfg, small_chain_kernel<float2>, a);
+    }
     if (c.variant & 1) small_batch_kernel<double2><<<c.gx, 256, 0, s>>>(a);
     else small_batch_kernel<float2><<<c.gx, 256, 0, s>>>(a);
     return cudaGetLastError();

@@ -134,10 +134,20 @@ struct SmallTask {
     int32_t block0;                 // first block of this task within the launch
 };
 
-// One launch over many independent small contractions of one tree level.
+// One launch over many independent small contractions of one tree level; or
+// (chain, n_levels > 0) consecutive small levels in one cooperative launch of
+// n_blocks blocks, level l being tasks [lv_end[l - 1], lv_end[l]) run after
+// level l - 1 behind a grid barrier, each task's block0 then holding its first
+// item within its level.
+#define JET_CHAIN_LEVELS 32
+#define JET_CHAIN_TASKS 1024   // tasks per chained level
 struct SmallBatchArgs {
-    uint64_t tasks;                 // device SmallTask[n_tasks], ordered by block0
+    uint64_t tasks;                 // device SmallTask[n_tasks], ordered by block0 (per level)
     int32_t n_tasks, n_blocks;
+    int32_t n_levels, pad_;
+    uint64_t barrier;               // chain: device uint32[2] (arrivals, departures), zero between launches
+    uint64_t status;                // chain: device uint32 error word (bit 8: a grid barrier timed out)
+    int32_t lv_end[JET_CHAIN_LEVELS];
 };
 
 // Adjoint accumulation: for each target instance t, env_t[off(e)] += sum over the

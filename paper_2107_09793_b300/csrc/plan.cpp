@@ -707,7 +707,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         max_inter = std::max(max_inter, N.view.size);
         // small direct contractions are batched per tree level into one launch
         // (their full offset tables are int32: operands below 2^31 elements)
-        N.small = !N.use_gemm && N.view.size <= 4096 && nK <= 2048 &&
+        // (also those of at most 131072 outputs over all instances and 2^20
+        // multiply-adds, which the chained small levels take)
+        N.small = !N.use_gemm && nK <= 2048 &&
+                  (N.view.size <= 4096 || ((double)N.n_inst * (double)N.view.size <= 131072.0 &&
+                                           (double)N.n_inst * (double)N.view.size * (double)nK <= (double)(1 << 20))) &&
                   (double)N.n_inst * (double)N.view.size * (double)nK <= (double)(1 << 24) &&
                   VA.size <= INT32_MAX && VB.size <= INT32_MAX;
         N.depth = 1 + std::max(node[a].depth, node[b].depth);
@@ -778,8 +782,92 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             if (node[c].base == BASE_ARENA)
                 arena.release((size_t)node[c].buf_off, (size_t)node[c].n_inst * node[c].view.size * es);
     };
+    // consecutive tiny levels of the forward sweep run as one chain launch (one
+    // block, a barrier between levels); their children are released when the
+    // chain is issued
+    bool chain_on = true;
+    std::vector<SmallTask> chain;
+    std::vector<Plan::Patch> chain_patches;
+    std::vector<int32_t> chain_nodes, chain_lv_end;
+    double chain_flop = 0, chain_bytes = 0;
+    auto flush_chain = [&]() {
+        if (chain.empty()) return;
+        size_t o_tasks = blob.reserve(sizeof(SmallTask) * chain.size(), 64);
+        for (size_t i = 0; i < chain.size(); ++i)
+            std::memcpy(blob.bytes.data() + o_tasks + i * sizeof(SmallTask), &chain[i], sizeof(SmallTask));
+        for (auto &pt : chain_patches) blob.patches.push_back({o_tasks + pt.at, pt.base, pt.byte_off});
+        // one block per 256 items of the widest level, at most one per SM
+        int64_t widest = 0, lv0 = 0;
+        for (int32_t e : chain_lv_end) {
+            const SmallTask &tl = chain[(size_t)e - 1];
+            widest = std::max<int64_t>(widest, (int64_t)tl.block0 + (int64_t)tl.n_inst * tl.n_out);
+            lv0 = e;
+        }
+        (void)lv0;
+        const int32_t G = (int32_t)std::max<int64_t>(1, std::min<int64_t>(148, (widest + 255) / 256));
+        SmallBatchArgs sb;
+        std::memset(&sb, 0, sizeof sb);
+        sb.n_tasks = (int32_t)chain.size();
+        sb.n_blocks = G;
+        sb.n_levels = (int32_t)chain_lv_end.size();
+        for (size_t l = 0; l < chain_lv_end.size(); ++l) sb.lv_end[l] = chain_lv_end[l];
+        const size_t o_bar = blob.reserve(8, 8);   // the grid barrier's counters (zero)
+        size_t so = blob.reserve(sizeof sb);
+        std::memcpy(blob.bytes.data() + so, &sb, sizeof sb);
+        blob.patch_field(so, offsetof(SmallBatchArgs, tasks), BASE_BLOB, (int64_t)o_tasks);
+        blob.patch_field(so, offsetof(SmallBatchArgs, barrier), BASE_BLOB, (int64_t)o_bar);
+        blob.patch_field(so, offsetof(SmallBatchArgs, status), BASE_STATUS, 0);
+        Op op;
+        op.kind = OpKind::SmallBatch;
+        op.node = chain_nodes.front();
+        op.n_inst = (int64_t)chain.size();
+        op.args_off = so;
+        op.args_bytes = sizeof sb;
+        op.flop = chain_flop;
+        op.bytes = chain_bytes;
+        op.variant = (fp64 ? 1 : 0) | 2;
+        op.grid_x = G;
+        op.block = 256;
+        op.batch_first = (int32_t)P.batch_nodes.size();
+        op.batch_count = (int32_t)chain_nodes.size();
+        P.batch_nodes.insert(P.batch_nodes.end(), chain_nodes.begin(), chain_nodes.end());
+        P.ops.push_back(op);
+        for (int32_t v : chain_nodes) release_children(v);
+        chain.clear();
+        chain_patches.clear();
+        chain_nodes.clear();
+        chain_lv_end.clear();
+        chain_flop = chain_bytes = 0;
+    };
     auto flush_batch = [&]() {
         if (batch.empty()) return;
+        {   // a small level (at most 262144 outputs, about seven per thread of a full
+            // grid, and 8 MFLOP) joins the chain
+            int64_t items = 0;
+            for (auto &t : batch) items += (int64_t)t.n_inst * t.n_out;
+            if (chain_on && items <= 262144 && batch_flop <= 8e6 && (int64_t)batch.size() <= JET_CHAIN_TASKS) {
+                if ((int)chain_lv_end.size() == JET_CHAIN_LEVELS) flush_chain();
+                const size_t base = chain.size() * sizeof(SmallTask);
+                int64_t item0 = 0;
+                for (auto &t : batch) {
+                    SmallTask u = t;
+                    u.block0 = (int32_t)item0;   // first item within the level
+                    item0 += (int64_t)t.n_inst * t.n_out;
+                    chain.push_back(u);
+                }
+                for (auto &pt : batch_patches) chain_patches.push_back({base + pt.at, pt.base, pt.byte_off});
+                chain_lv_end.push_back((int32_t)chain.size());
+                chain_nodes.insert(chain_nodes.end(), batch_nodes.begin(), batch_nodes.end());
+                chain_flop += batch_flop;
+                chain_bytes += batch_bytes;
+                batch.clear();
+                batch_nodes.clear();
+                batch_patches.clear();
+                batch_flop = batch_bytes = 0;
+                return;
+            }
+        }
+        flush_chain();
         int32_t blocks = 0;
         for (auto &t : batch) {
             t.block0 = blocks;
@@ -1386,6 +1474,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         const int64_t nK = dimprod(K), nFa = dimprod(fa), nFb = dimprod(fb);
         const bool use_gemm = N.use_gemm, a_big = N.a_big;
         if (!N.small || (!batch_nodes.empty() && node[batch_nodes.front()].depth != N.depth)) flush_batch();
+        if (!N.small) flush_chain();   // the chain's levels run before this node's launches
 
         // arena buffer for all instances (a kept result: its slot in the pool)
         size_t nbytes = (size_t)N.n_inst * N.view.size * es;
@@ -1803,6 +1892,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         release_children(v);
     }
     flush_batch();
+    flush_chain();
+    chain_on = false;   // (the adjoint sweep's batches run as plain level launches)
 
     // ---- adjoint sweep (environment contraction), reverse launch order.
     // For C = sum_K A B: env(A) = env(C) contracted with B over B's free labels,
