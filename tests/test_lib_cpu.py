@@ -409,6 +409,26 @@ def test_arena_liveness_no_overlap_among_live_buffers(name, prec):
     net.close()
 
 
+def test_small_levels_run_as_chained_launches():
+    """Consecutive small tree levels (Section 3.1: the many tiny contractions of
+    the first levels) are issued as one cooperative launch each run of them,
+    at most one block per SM; grid30's first launch is such a chain."""
+    w = configs.build("grid30")
+    net = jet.from_network(w.network, precision="fp16x3")
+    try:
+        net.path_greedy(seed=1, n_trials=4)
+        net.slice_auto(1 << 24, min_n=2, max_n=24)
+        net.plan(w.outputs)
+        recs = net.profile()
+        chains = [r for r in recs if r["kind"] == "small_batch" and r["variant"] & 2]
+        assert chains and recs[0] in chains
+        assert all(1 <= r["grid"][0] <= 148 and r["block"] == 256 for r in chains)
+        plain = [r for r in recs if r["kind"] in ("small_batch", "direct") and not r["variant"] & 2]
+        assert len(chains) + len(plain) < 12, [(r["kind"], r["node"]) for r in chains + plain]
+    finally:
+        net.close()
+
+
 def test_arena_liveness_catches_a_planted_overlap():
     """The check itself: moving one live buffer onto another is caught."""
     w = configs.build("grid12")
