@@ -476,8 +476,10 @@ int jet_autotune(jet_network *net, int32_t n_amps, const int32_t *outputs, const
  * tensor memory and return; a contraction then fails with JET_ETIMEOUT).  One
  * CTA on the network's device, on cuda_stream, allocates tensor memory, waits
  * with the same bounded-wait helper on an mbarrier that nothing arrives on,
- * gives up after limit_us microseconds, records the time-out, frees the tensor
- * memory and returns; the call reads and clears the status word.  Nothing is
+ * gives up after limit_us microseconds, records the time-out, then waits at
+ * the chained small levels' grid barrier for a block that does not exist and
+ * gives up likewise, frees the tensor memory and returns; the call reads and
+ * clears the status word.  Nothing is
  * left in flight and the handle stays usable.  Returns JET_ETIMEOUT (the
  * expected outcome: the wait ran out and was reported), JET_ECUDA if the wait
  * did not run out or the launch failed, JET_EINVAL (limit_us outside

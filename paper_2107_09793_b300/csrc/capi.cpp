@@ -1209,8 +1209,8 @@ int jet_selftest_wait(jet_network *net, int64_t limit_us, void *cuda_stream)
         if (!net) fail(JET_EINVAL, "net is NULL");
         if (limit_us < 1 || limit_us > 10000000) fail(JET_EINVAL, "limit_us must be in [1, 10^7]");
         const int st = selftest_wait(*net, limit_us, cuda_stream);
-        if (st & 4) fail(JET_ETIMEOUT, "the bounded device-side wait ran out (self-test)");
-        fail(JET_ECUDA, "the self-test's wait completed although nothing arrives on its barrier");
+        if ((st & 12) == 12) fail(JET_ETIMEOUT, "the bounded device-side waits ran out (self-test)");
+        fail(JET_ECUDA, "a self-test wait completed although nothing arrives on its barrier");
     });
 }
 

@@ -463,13 +463,6 @@ __global__ void __launch_bounds__(256) small_batch_kernel(const __grid_constant_
 // The barrier is an arrival counter that block leaders wait on with a bounded
 // spin (1 s, then status bit 8 and the kernel stops); the last block out sets
 // both counters back to zero for the next launch.
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
-{
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 template <typename V>
 __global__ void __launch_bounds__(256) small_chain_kernel(const __grid_constant__ SmallBatchArgs a)
 {
@@ -509,19 +502,9 @@ __global__ void __launch_bounds__(256) small_chain_kernel(const __grid_constant_
         t0 = t1;
         if (l + 1 < a.n_levels) {   // every block's outputs of this level before any block reads them
             __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(arrive, 1u);
-                const uint32_t target = (uint32_t)(l + 1) * gridDim.x;
-                const uint64_t tw = globaltimer();
-                while (ld_acquire_u32(arrive) < target) {
-                    if (globaltimer() - tw > 1000000000ull) {
-                        stop = 1;
-                        atomicOr((unsigned int *)a.status, 8u);
-                        break;
-                    }
-                }
-                __threadfence();
+            if (threadIdx.x == 0 && !grid_arrive_wait(arrive, (uint32_t)(l + 1) * gridDim.x, 1000000000ull)) {
+                stop = 1;
+                atomicOr((unsigned int *)a.status, 8u);
             }
             __syncthreads();
             if (stop) break;

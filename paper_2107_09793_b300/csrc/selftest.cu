@@ -1,9 +1,11 @@
-// Bounded-wait self-test (jet_selftest_wait): the time-out path of the
-// tensor-core kernels exercised without injecting a fault.  One CTA holds
-// tensor memory like those kernels, waits on an mbarrier that nothing arrives
-// on with the same bounded-wait helper and a caller-set limit, records the
-// time-out in the network's status word (bit 4), releases its tensor memory and
-// returns; nothing asynchronous is in flight at any point.
+// Bounded-wait self-test (jet_selftest_wait): the time-out paths of the
+// tensor-core kernels and of the chained small levels exercised without
+// injecting a fault.  One CTA holds tensor memory like those kernels, waits on
+// an mbarrier that nothing arrives on with the same bounded-wait helper and a
+// caller-set limit, records the time-out in the network's status word (bit 4),
+// then waits at the chains' grid barrier for a second block that does not
+// exist (bit 8), releases its tensor memory and returns; nothing asynchronous
+// is in flight at any point.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -12,7 +14,7 @@
 
 namespace jet {
 
-__global__ void __launch_bounds__(64, 1) wait_selftest_kernel(uint32_t *status, uint64_t limit_ns)
+__global__ void __launch_bounds__(64, 1) wait_selftest_kernel(uint32_t *status, uint32_t *arrive, uint64_t limit_ns)
 {
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_holder;
@@ -36,6 +38,9 @@ __global__ void __launch_bounds__(64, 1) wait_selftest_kernel(uint32_t *status, 
             abort_flag = 1;
             atomicOr(status, 4u);
         }
+        *arrive = 0u;   // one block: two arrivals never come
+        if (!grid_arrive_wait(arrive, 2u, limit_ns)) atomicOr(status, 8u);
+        *arrive = 0u;
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -47,7 +52,9 @@ int selftest_wait(Network &net, int64_t limit_us, void *stream)
 {
     ensure_leaves_on_device(net);
     cudaStream_t s = stream ? (cudaStream_t)stream : (cudaStream_t)net.stream;
-    wait_selftest_kernel<<<1, 64, 0, s>>>((uint32_t *)net.d_status, (uint64_t)limit_us * 1000ull);
+    // (the barrier counter: a word of the status buffer past the status word)
+    wait_selftest_kernel<<<1, 64, 0, s>>>((uint32_t *)net.d_status, (uint32_t *)net.d_status + 4,
+                                          (uint64_t)limit_us * 1000ull);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) fail(JET_ECUDA, std::string("self-test launch: ") + cudaGetErrorString(e));
     return read_clear_status(net, stream);

@@ -148,4 +148,25 @@ __device__ __forceinline__ float tf32_rna(float x)
     return __uint_as_float(r);
 }
 
+// Grid barrier, leader thread's part (the rest of its block waits at a
+// __syncthreads around it): count this block's arrival and wait until `target`
+// arrivals, giving up after limit_ns (returns false).  The counter is reset by
+// its owner between uses.
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool grid_arrive_wait(uint32_t *arrive, uint32_t target, uint64_t limit_ns)
+{
+    __threadfence();
+    atomicAdd(arrive, 1u);
+    const uint64_t t0 = globaltimer();
+    while (ld_acquire_u32(arrive) < target)
+        if (globaltimer() - t0 > limit_ns) return false;
+    __threadfence();
+    return true;
+}
+
 }  // namespace jet
