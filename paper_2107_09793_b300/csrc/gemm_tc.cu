@@ -152,7 +152,9 @@ __device__ __forceinline__ void split4(const float (&x)[4], uint32_t (&w)[TcCfg<
 constexpr int SPLIT_TR = 64, SPLIT_TK = 64;
 constexpr int SPLIT_ROW = SPLIT_TK + 2;   // padded tile row (float2; even: 16-byte pairs stay aligned)
 constexpr int SPLIT_SMEM = 2 * SPLIT_TR * SPLIT_ROW * 8               // two tiles
-                           + 2 * (SPLIT_TR + SPLIT_TK) * 8;           // their row / column offsets
+                           + 2 * (SPLIT_TR + SPLIT_TK) * 8            // their row / column offsets
+                           + 3 * SPLIT_TR * 8;                        // plane rows (three tiles: one is
+                                                                      // read while the next-but-one's are decoded)
 
 // (no memory clobber: the copies' shared-memory writes are ordered by the
 // wait_group and barrier that follow, which carry it; the offsets they read
@@ -181,18 +183,22 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
     extern __shared__ __align__(16) uint8_t split_smem[];
     float2 *tiles_s = (float2 *)split_smem;                                        // [2][64][65]
     int64_t *offs = (int64_t *)(split_smem + 2 * SPLIT_TR * SPLIT_ROW * 8);       // [2][64 + 64]
+    int64_t *prows = offs + 2 * (SPLIT_TR + SPLIT_TK);                              // [3][64]
     const int tid = threadIdx.x;
     const int64_t k_tiles = (a.k_pad + SPLIT_TK - 1) / SPLIT_TK;
     const int64_t plane_elems = a.rows_group * a.k_pad;
 
-    auto decode = [&](int64_t t, int buf) {   // threads 0..127: one row or column offset each
+    auto decode = [&](int64_t t, int buf, int pbuf) {   // threads 0..127: one row or column offset each
         static_assert(SPLIT_TR + SPLIT_TK <= 256, "one decoding thread per tile row and column");
         if (tid < SPLIT_TR + SPLIT_TK) {
             const int64_t rt = t / k_tiles, kt = t - rt * k_tiles;
             const bool is_row = tid < SPLIT_TR;
             int64_t x = is_row ? rt * SPLIT_TR + tid : kt * SPLIT_TK + (tid - SPLIT_TR), off = -1;
+            int64_t prow = x;   // (rows: plane row; padding rows and the identity order: x)
             if (x < (is_row ? a.rows : a.k)) {
                 off = 0;
+                const bool perm = is_row && a.row_perm;
+                if (perm) prow = 0;
                 const int rank = is_row ? a.rank_r : a.rank_k;
                 const int64_t *dim = is_row ? a.r_dim : a.k_dim, *str = is_row ? a.r_s : a.k_s;
                 for (int jj = 0; jj < rank; ++jj) {
@@ -207,10 +213,12 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
                         r = x - q * d;
                     }
                     off += r * str[jj];
+                    if (perm) prow += r * a.p_s[jj];
                     x = q;
                 }
             }
             offs[buf * (SPLIT_TR + SPLIT_TK) + tid] = off;
+            if (is_row) prows[pbuf * SPLIT_TR + tid] = prow;
         }
     };
     auto issue = [&](const float2 *S, int buf) {   // 16 zero-filling 8-byte copies per thread
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
         const int64_t n_tiles = ((rows_w + SPLIT_TR - 1) / SPLIT_TR) * k_tiles;
         uint8_t *base = (uint8_t *)a.planes + (g * NP * plane_elems + row_base * a.k_pad) * EB;
         __syncthreads();   // the previous instance's readers of the buffers are done
-        if (blockIdx.x < n_tiles) decode(blockIdx.x, 0);
+        if (blockIdx.x < n_tiles) decode(blockIdx.x, 0, 0);
         __syncthreads();
         if (blockIdx.x < n_tiles) issue(S, 0);
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -276,7 +284,7 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
         for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
             const int cur = k & 1, nxt = cur ^ 1;
             const int64_t t1 = t + gridDim.x;
-            if (t1 < n_tiles) decode(t1, nxt);
+            if (t1 < n_tiles) decode(t1, nxt, (k + 1) % 3);
             __syncthreads();   // next offsets visible; the buffer of tile k-1 is free
             if (t1 < n_tiles) issue(S, nxt);
             asm volatile("cp.async.commit_group;" ::: "memory");
@@ -299,10 +307,9 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
             const int kq = 4 * q16;
             const bool col_in = k0 + kq < a.k_pad;   // k_pad is a multiple of 16
             const int64_t pstep = plane_elems * EB;
-            uint8_t *q0 = base + ((row0 + rsub) * a.k_pad + k0 + kq) * EB;
+            const int64_t *prow = prows + (k % 3) * SPLIT_TR;   // the tile rows' plane rows (relative to row_base)
             float *sc = nullptr;
-            if (TcCfg<MODE>::SCALED)
-                sc = (float *)a.scales + (g * k_tiles + kt) * a.rows_group + row_base + row0 + rsub;
+            if (TcCfg<MODE>::SCALED) sc = (float *)a.scales + (g * k_tiles + kt) * a.rows_group + row_base;
 #pragma unroll
             for (int i = 0; i < SPLIT_TR / 16; ++i) {
                 const int r = rsub + 16 * i;
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
                     int ex = 0;
                     if (m > 0.f) ex = max(-100, min(100, 141 - (int)((__float_as_uint(m) >> 23) & 0xffu)));
                     const float f = __uint_as_float((uint32_t)(127 + ex) << 23);
-                    if (q16 == 0 && valid) sc[16 * i] = __uint_as_float((uint32_t)(127 - ex) << 23);
+                    if (q16 == 0 && valid) sc[prow[r]] = __uint_as_float((uint32_t)(127 - ex) << 23);
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         re[c] *= f;
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
                 uint32_t wr[NPH][EB], wi[NPH][EB];
                 split4<MODE>(re, wr);
                 split4<MODE>(im, wi);
-                uint8_t *q = q0 + (int64_t)(16 * i) * a.k_pad * EB;
+                uint8_t *q = base + (prow[r] * a.k_pad + k0 + kq) * EB;
 #pragma unroll
                 for (int p = 0; p < NPH; ++p) {
                     if (EB == 2) {
@@ -346,6 +353,71 @@ __global__ void __launch_bounds__(256, 3) tc_split_kernel(const __grid_constant_
             }
         }
         asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+}
+
+// ------------------------------------------------------------------ fused split
+// FP16X3 epilogue that writes a row's 16-column group straight into the parent
+// GEMM's operand planes (see TcGemmArgs::fz_*): NK consecutive columns are the
+// NK fastest summed entries of one parent row, and the 2^lgsz lanes of a lane
+// group (consecutive m_k) hold the rest of a 64-entry chunk, so the chunk's
+// scale is a max over the group's lanes; each lane then stores NK halves per
+// plane (contiguous across the group).
+__device__ __forceinline__ uint32_t fz_h2(float x0, float x1, uint32_t &lo)
+{
+    const __half2 h = __floats2half2_rn(x0, x1);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+    lo = *(const uint32_t *)&l;
+    return *(const uint32_t *)&h;
+}
+// (it, ibase, sbase: the group's node instance and its plane and scale bases;
+// rn: the parent-row contributions of the group's 16 / NK n_f values, all
+// looked up at the start of the tile)
+template <int NK>
+__device__ __forceinline__ void fz_store_group(const TcGemmArgs &a, const float *re, const float *im, int64_t it,
+                                               int64_t ibase, int64_t sbase, const int32_t *rn, int32_t rm, int64_t mk,
+                                               int lane)
+{
+    constexpr int LNK = NK == 2 ? 1 : NK == 4 ? 2 : NK == 8 ? 3 : 4;
+    constexpr int GSZ = 64 / NK;   // lanes of one chunk
+    const int64_t k0 = mk << LNK, ch = k0 >> 6;
+    __half *planes = (__half *)a.fz_planes;
+#pragma unroll
+    for (int t = 0; t < 16 / NK; ++t) {
+        const int64_t r = (int64_t)rm + rn[t];
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < NK; ++c) m = fmaxf(m, fmaxf(fabsf(re[t * NK + c]), fabsf(im[t * NK + c])));
+#pragma unroll
+        for (int o = GSZ / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const int ex = m > 0.f ? max(-100, min(100, 141 - (int)((__float_as_uint(m) >> 23) & 0xffu))) : 0;
+        const float f = __uint_as_float((uint32_t)(127 + ex) << 23);
+        if (it < 0) continue;
+        if ((lane & (GSZ - 1)) == 0) ((float *)a.fz_scales)[sbase + ch * a.fz_rows_pad + r] = __uint_as_float((uint32_t)(127 - ex) << 23);
+        uint32_t rh[NK / 2], rl[NK / 2], ih[NK / 2], il[NK / 2];
+#pragma unroll
+        for (int c = 0; c < NK / 2; ++c) {
+            rh[c] = fz_h2(re[t * NK + 2 * c] * f, re[t * NK + 2 * c + 1] * f, rl[c]);
+            ih[c] = fz_h2(im[t * NK + 2 * c] * f, im[t * NK + 2 * c + 1] * f, il[c]);
+        }
+        __half *e = planes + ibase + r * a.fz_kpad + k0;
+        const int64_t pe = a.fz_plane_elems;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t *w = q == 0 ? rh : q == 1 ? rl : q == 2 ? ih : il;
+            __half *d = e + q * pe;
+            if (NK == 2) {
+                *(uint32_t *)d = w[0];
+            } else if (NK == 4) {
+                *(uint2 *)d = make_uint2(w[0], w[1 % (NK / 2)]);
+            } else {
+#pragma unroll
+                for (int v = 0; v < NK / 8; ++v)
+                    *(uint4 *)(d + 8 * v) = make_uint4(w[(4 * v) % (NK / 2)], w[(4 * v + 1) % (NK / 2)],
+                                                       w[(4 * v + 2) % (NK / 2)], w[(4 * v + 3) % (NK / 2)]);
+            }
+        }
     }
 }
 
@@ -522,9 +594,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         const int quarter = warp & 3, half = (warp - 2) >> 2;
         __shared__ float sfn[TC_EPI_WARPS][64];   // SCALED: this warp's 64 column scales of the chunk
         int64_t cg = 0;
+        // fused split: this warp's per-tile lookups (instances, plane and scale
+        // bases of its four 16-column groups, parent-row parts of its n_f values),
+        // staged in its slice of the C staging area while the chunks accumulate
+        int64_t *fz_t64 = (int64_t *)(smem + (size_t)S * STAGE_BYTES + (size_t)(warp - 2) * 8192);
+        int32_t *fz_rn = (int32_t *)(fz_t64 + 12);
         for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
             int inst, tm, tn;
             tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
+            if (Cfg::SCALED && a.fz_planes) {
+                const int64_t c0 = (int64_t)tn * TC_BN + half * 64;
+                __syncwarp();   // the previous tile's readers of the lookups are done
+                if (c0 < a.N) {
+                    const bool grp = a.itab != 0;
+                    int64_t jj = 0;
+                    if (grp) {
+                        const int64_t R0 = (int64_t)tm * TC_BM + quarter * 32;
+                        jj = a.mi_shift >= 0 ? R0 >> a.mi_shift : R0 / a.Mi;
+                    }
+                    auto col_split = [&](int64_t c, int64_t &ll, int64_t &nn) {
+                        if (!grp) {
+                            ll = 0;
+                            nn = c;
+                        } else if (a.ni_shift >= 0) {
+                            ll = c >> a.ni_shift;
+                            nn = c & (a.Ni - 1);
+                        } else {
+                            ll = c / a.Ni;
+                            nn = c - ll * a.Ni;
+                        }
+                    };
+                    if (lane < 4) {
+                        int64_t ll, nn;
+                        col_split(c0 + 16 * lane, ll, nn);
+                        const int64_t it =
+                            grp ? (int64_t)__ldg((const int32_t *)a.itab + ((int64_t)inst * a.nA + jj) * a.nB + ll) : inst;
+                        fz_t64[lane] = it;
+                        fz_t64[4 + lane] = it >= 0 ? __ldg((const long long *)a.fz_ibase + 2 * it) : 0;
+                        fz_t64[8 + lane] = it >= 0 ? __ldg((const long long *)a.fz_ibase + 2 * it + 1) : 0;
+                    }
+                    const int nv = 64 >> a.fz_lnk;   // n_f values of the warp's 64 columns
+                    if (lane < nv) {
+                        int64_t ll, nn;
+                        col_split(c0 + ((int64_t)lane << a.fz_lnk), ll, nn);
+                        fz_rn[lane] = __ldg((const int *)a.fz_pn + (nn >> a.fz_lnk));
+                    }
+                }
+                __syncwarp();
+            }
             float racc[64], iacc[64];
 #pragma unroll
             for (int j = 0; j < 64; ++j) racc[j] = iacc[j] = 0.f;
@@ -622,7 +739,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 return cptr;
             };
-            if (tc_cstage<MODE>() && a.c_tma && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
+            if (Cfg::SCALED && a.fz_planes) {
+                // fused split: the parent's planes (whole tiles of rows, columns in 64s:
+                // a warp's half tile is all in or all out; a warp's 32 rows lie in one
+                // instance, each 16-column group too)
+                if (col0 >= a.N) continue;
+                const int64_t R = (int64_t)tm * TC_BM + quarter * 32 + lane;
+                int64_t jj = 0, mm = R;
+                if (grouped) split_row(R, jj, mm);
+                const int64_t mk = mm & (((int64_t)1 << a.fz_lmk) - 1), mf = mm >> a.fz_lmk;
+                const int32_t rm = __ldg((const int *)a.fz_pm + mf);
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const int64_t it = fz_t64[p], ib = fz_t64[4 + p], sb = fz_t64[8 + p];
+                    const float *re = racc + p * 16, *im = iacc + p * 16;
+                    const int32_t *rn = fz_rn + ((16 * p) >> a.fz_lnk);
+                    switch (a.fz_lnk) {
+                    case 1: fz_store_group<2>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
+                    case 2: fz_store_group<4>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
+                    case 3: fz_store_group<8>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
+                    default: fz_store_group<16>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
+                    }
+                }
+            } else if (tc_cstage<MODE>() && a.c_tma && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
                 // bulk tensor stores: the warp's 32 rows x 16 columns staged as one
                 // dense box (16-byte chunk c of row r at chunk c ^ (r % 8): 128-byte
                 // swizzle), stored by lane 0; two boxes alternate, a box rewritten

@@ -52,6 +52,14 @@ struct NodeInfo {
     bool a_is_m = true;              // GEMM route: child a is the M operand
     std::vector<int64_t> fM, fN;     // GEMM route: output = fM ++ fN, in these orders
     int32_t depth = 0;               // tree level (leaves 0)
+    // FP16X3 fused split (pass 1: candidate; pass 2: fz_ok once its parent's
+    // planes layout is known): this GEMM's epilogue writes its parent GEMM's
+    // operand planes; fz_mk / fz_nk are the parent's summed labels among fM / fN
+    // (the lowest labels of each), fz_kappa the parent's summed-label order
+    bool fuse = false, fz_ok = false;
+    std::vector<int64_t> fz_mk, fz_nk, fz_kappa;
+    size_t alloc_bytes = 0;          // arena bytes of buf_off (0: n_inst view.size elements)
+    size_t fz_scales_off = 0;        // fz_ok: arena offset of the scales (the planes at buf_off)
 };
 
 struct Blob {
@@ -595,11 +603,64 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             N.a_is_m = nFa >= nFb;
             N.fM = N.a_is_m ? N.fa : N.fb;
             N.fN = N.a_is_m ? N.fb : N.fa;
+            const int32_t pp = parent[v];
+            // FP16x3 with a GEMM parent that sums labels of both of this node's
+            // sides: this node's epilogue can write the parent's operand planes
+            // (fused split) when the parent's summed labels from the N side number
+            // 2..16 entries and, with those from the M side, fill whole 64-entry
+            // chunks; they go lowest on each side (fM = [m_f, m_k], fN = [n_f, n_k])
+            if (tc_mode && net.opt.precision == JET_PREC_FP16X3 && !grad && pp >= 0) {
+                const auto &ls = labset[sibling[v]];
+                std::vector<int64_t> Kp, Fp, Fs;
+                for (int64_t l : labset[v]) (find_pos(ls, l) >= 0 ? Kp : Fp).push_back(l);
+                for (int64_t l : ls)
+                    if (find_pos(labset[v], l) < 0) Fs.push_back(l);
+                // (a GEMM parent, or a skinny product the GEMM route also takes; pass 2
+                // checks the parent's route)
+                const int64_t kp = dimprod(Kp), fp_ = dimprod(Fp), fs_ = dimprod(Fs);
+                const bool p_gemm = !Kp.empty() && (gemm_route(kp, fp_, fs_) ||
+                                                    (gemm_ok && kp >= net.opt.gemm_min_k && std::min(fp_, fs_) >= 8 &&
+                                                     std::max(fp_, fs_) >= 4096));
+                bool pow2 = true;
+                for (int64_t l : labset[v]) pow2 = pow2 && (net.labels.at(l).dim & (net.labels.at(l).dim - 1)) == 0;
+                for (int flip = 0; flip < 2 && p_gemm && pow2 && dimprod(Kp) % 64 == 0 && !N.fuse; ++flip) {
+                    const bool am = flip ? !N.a_is_m : N.a_is_m;
+                    const auto &sM = am ? N.fa : N.fb, &sN = am ? N.fb : N.fa;
+                    std::vector<int64_t> mk, nk, mf, nf;
+                    for (int64_t l : sM) (find_pos(Kp, l) >= 0 ? mk : mf).push_back(l);
+                    for (int64_t l : sN) (find_pos(Kp, l) >= 0 ? nk : nf).push_back(l);
+                    const int64_t NKd = dimprod(nk), MKd = dimprod(mk);
+                    // within each group, the label of smallest stride in the child that
+                    // holds it last: this node's own operand splits keep reading along
+                    // the children's fastest labels
+                    auto by_stride = [&](std::vector<int64_t> &ls, int32_t child) {
+                        const View &Vc = node[child].view;
+                        std::stable_sort(ls.begin(), ls.end(), [&](int64_t x, int64_t y) {
+                            return Vc.strides[find_pos(Vc.labels, x)] > Vc.strides[find_pos(Vc.labels, y)];
+                        });
+                    };
+                    const int32_t cM = am ? a : b, cN = am ? b : a;
+                    by_stride(mf, cM);
+                    by_stride(mk, cM);
+                    by_stride(nf, cN);
+                    by_stride(nk, cN);
+                    if (NKd >= 2 && NKd <= 16 && MKd >= 64 / NKd && MKd * NKd == dimprod(Kp) && !mf.empty() &&
+                        !nf.empty()) {
+                        N.a_is_m = am;
+                        N.fM = mf;
+                        N.fM.insert(N.fM.end(), mk.begin(), mk.end());
+                        N.fN = nf;
+                        N.fN.insert(N.fN.end(), nk.begin(), nk.end());
+                        N.fz_mk = mk;
+                        N.fz_nk = nk;
+                        N.fuse = true;
+                    }
+                }
+            }
             // for a tensor-core parent, lay the output out as [parent-free, parent-summed]
             // when the parent's summed labels all come from one side: the parent's
             // operand split is then a plain format conversion
-            const int32_t pp = parent[v];
-            if (tc_mode && pp >= 0) {
+            if (tc_mode && pp >= 0 && !N.fuse) {
                 const auto &ls = labset[sibling[v]];
                 std::vector<int64_t> Kp, Fp, Fs;
                 for (int64_t l : labset[v]) (find_pos(ls, l) >= 0 ? Kp : Fp).push_back(l);
@@ -626,7 +687,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             // for a parent that applies a small operand: its summed labels slowest,
             // when one side holds them all (that side becomes M, their rows first)
             // (tensor-core route: the operand split gathers rows in any order)
-            const std::vector<int64_t> Kc = tc_mode ? consumer_summed(v) : std::vector<int64_t>();
+            const std::vector<int64_t> Kc = tc_mode && !N.fuse ? consumer_summed(v) : std::vector<int64_t>();
             if (!Kc.empty()) {
                 auto holds_all = [&](const std::vector<int64_t> &X) {
                     for (int64_t l : Kc)
@@ -780,7 +841,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         if (grad) return;   // the adjoint sweep reads every forward intermediate
         for (int32_t c : {node[v].a, node[v].b})
             if (node[c].base == BASE_ARENA)
-                arena.release((size_t)node[c].buf_off, (size_t)node[c].n_inst * node[c].view.size * es);
+                arena.release((size_t)node[c].buf_off, node[c].alloc_bytes ? node[c].alloc_bytes
+                                                                            : (size_t)node[c].n_inst * node[c].view.size * es);
     };
     // consecutive tiny levels of the forward sweep run as one chain launch (one
     // block, a barrier between levels); their children are released when the
@@ -1463,6 +1525,39 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         P.ops.push_back(op);
     };
 
+    // GEMM route, tensor cores: the instance blocks of node pv (full products of
+    // M-side and N-side child instance groups when every block has the same shape
+    // and (nearly) no child instance is split twice; else one block per instance).
+    // record: add the choice to the tuner's list (the node's own emission)
+    auto gemm_groups_of = [&](int32_t pv, bool record) {
+        const NodeInfo &Q = node[pv];
+        const int32_t qM = Q.a_is_m ? Q.a : Q.b, qN = Q.a_is_m ? Q.b : Q.a;
+        const std::vector<int32_t> &iM = Q.a_is_m ? Q.ia : Q.ib, &iN = Q.a_is_m ? Q.ib : Q.ia;
+        const View &WM = node[qM].view, &WN = node[qN].view;
+        GemmGroups G, gm, gn;
+        const bool okm = group_instances(iM, iN, true, gm);
+        const bool okn = group_instances(iM, iN, false, gn);
+        const double vm = (double)WM.size, vn = (double)WN.size;
+        const double cm = okm ? gm.dup * vn : 1e300, cn = okn ? gn.dup * vm : 1e300;
+        const double budget = 0.25 * ((double)node[qM].n_inst * vm + (double)node[qN].n_inst * vn);
+        const bool can_merge = (okm || okn) && std::min(cm, cn) <= budget &&
+                               (okm && cm <= cn ? gm : gn).bM.size() < (size_t)Q.n_inst;
+        const bool merge = can_merge && tuned(pv, 0, net.opt.gemm_group != 0);
+        if (can_merge && record)
+            P.tunables.push_back({pv, 0, merge ? 1 : 0,
+                                  sig_of(0, {dimprod(Q.K), dimprod(Q.fM), dimprod(Q.fN), Q.n_inst, node[qM].n_inst,
+                                             node[qN].n_inst, WM.size, WN.size})});
+        if (merge) {
+            G = okm && cm <= cn ? gm : gn;
+        } else {   // one block per instance; every child instance one group
+            for (int64_t j = 0; j < node[qM].n_inst; ++j) G.gM.push_back({(int32_t)j});
+            for (int64_t j = 0; j < node[qN].n_inst; ++j) G.gN.push_back({(int32_t)j});
+            G.bM.assign(iM.begin(), iM.end());
+            G.bN.assign(iN.begin(), iN.end());
+        }
+        return G;
+    };
+
     // ---- pass 2, launch order: arena offsets, pointer tables, launches
     for (int32_t v : order) {
         if (skip[v]) continue;   // a kept result stands for this sub-tree
@@ -1476,15 +1571,101 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         if (!N.small || (!batch_nodes.empty() && node[batch_nodes.front()].depth != N.depth)) flush_batch();
         if (!N.small) flush_chain();   // the chain's levels run before this node's launches
 
+        // fused split: this GEMM's epilogue writes its parent GEMM's FP16 planes
+        // for this node's side (the parent's instance blocks and row order decide
+        // the layout), allocated in place of the complex64 output
+        std::vector<int64_t> fz_ibase;
+        std::vector<int32_t> fz_pm, fz_pn;
+        int64_t fz_plane_elems = 0, fz_kpad = 0, fz_rows_pad = 0;
+        size_t fz_planes_bytes = 0, fz_scales_bytes = 0;
+        N.fz_ok = false;
+        const bool kept_v = std::find(P.kept_fill.begin(), P.kept_fill.end(), v) != P.kept_fill.end();
+        if (N.fuse && use_gemm && tc_mode && !grad && !kept_v && parent[v] >= 0 && !skip[parent[v]]) {
+            const int32_t pv = parent[v], sib = sibling[v];
+            NodeInfo &Q = node[pv];
+            bool ok = Q.use_gemm && !Q.small && std::find(P.kept_fill.begin(), P.kept_fill.end(), pv) == P.kept_fill.end();
+            // one fused operand per parent: the larger one (child a on a tie)
+            const double sz = (double)N.n_inst * N.view.size, szs = (double)node[sib].n_inst * node[sib].view.size;
+            if (ok && node[sib].fuse && (szs > sz || (szs == sz && Q.a == sib))) ok = false;
+            const bool vM = (Q.a_is_m ? Q.a : Q.b) == v;
+            const std::vector<int64_t> &fp = vM ? Q.fM : Q.fN;
+            const size_t nmf = N.fM.size() - N.fz_mk.size(), nnf = N.fN.size() - N.fz_nk.size();
+            std::vector<int64_t> mf(N.fM.begin(), N.fM.begin() + nmf), nf(N.fN.begin(), N.fN.begin() + nnf);
+            if (ok) {   // the parent's rows are this node's m_f and n_f labels, its summed labels m_k and n_k
+                ok = fp.size() == nmf + nnf && Q.K.size() == N.fz_mk.size() + N.fz_nk.size();
+                for (int64_t l : mf) ok = ok && find_pos(fp, l) >= 0;
+                for (int64_t l : nf) ok = ok && find_pos(fp, l) >= 0;
+                for (int64_t l : N.fz_mk) ok = ok && find_pos(Q.K, l) >= 0;
+                for (int64_t l : N.fz_nk) ok = ok && find_pos(Q.K, l) >= 0;
+            }
+            const int64_t kblk = tc_k_block(net.opt.precision), T = tc_tile(), NP = tc_planes(net.opt.precision);
+            const int64_t Kp = dimprod(Q.K);
+            ok = ok && Kp % 64 == 0 && Kp % kblk == 0 && dimprod(N.fz_nk) >= 2 && dimprod(N.fz_nk) <= 16;
+            if (ok) {   // this node's own tiles: whole (rows in 32s per instance, columns in 64s)
+                const GemmGroups Gv = gemm_groups_of(v, false);
+                const int64_t mr = Gv.nA * dimprod(N.fM), nr = Gv.nB * dimprod(N.fN);
+                ok = mr % T == 0 && nr % 64 == 0 && dimprod(N.fM) % 32 == 0 && dimprod(N.fN) % 16 == 0;
+            }
+            if (ok) {
+                const GemmGroups Gp = gemm_groups_of(pv, false);
+                const std::vector<std::vector<int32_t>> &groups = vM ? Gp.gM : Gp.gN;
+                const int64_t per = vM ? Gp.nA : Gp.nB, rows = dimprod(fp);
+                fz_rows_pad = (per * rows + T - 1) / T * T;
+                fz_kpad = Kp;
+                fz_plane_elems = fz_rows_pad * fz_kpad;
+                fz_ibase.assign((size_t)N.n_inst * 2, -1);
+                const int64_t n_ch = fz_kpad / 64;
+                for (size_t g = 0; g < groups.size() && ok; ++g)
+                    for (size_t j = 0; j < groups[g].size() && ok; ++j) {
+                        const int32_t i = groups[g][j];
+                        if (i < 0 || i >= N.n_inst || fz_ibase[2 * (size_t)i] >= 0) {
+                            ok = false;   // each instance in exactly one block group
+                            break;
+                        }
+                        fz_ibase[2 * (size_t)i] = (int64_t)g * NP * fz_plane_elems + (int64_t)j * rows * fz_kpad;
+                        fz_ibase[2 * (size_t)i + 1] = (int64_t)g * n_ch * fz_rows_pad + (int64_t)j * rows;
+                    }
+                for (size_t i = 0; i < (size_t)N.n_inst && ok; ++i) ok = fz_ibase[2 * i] >= 0;
+                if (ok) {
+                    fz_planes_bytes = (size_t)groups.size() * NP * fz_plane_elems * 2;
+                    fz_scales_bytes = (size_t)groups.size() * n_ch * fz_rows_pad * 4;
+                    // parent-row contributions of the m_f and n_f digits (mixed radix,
+                    // last label fastest, in this node's and in the parent's orders)
+                    auto contrib = [&](const std::vector<int64_t> &ls, std::vector<int32_t> &tab) {
+                        const int64_t n = dimprod(ls);
+                        tab.assign((size_t)n, 0);
+                        for (int64_t x = 0; x < n; ++x) {
+                            int64_t r = x, off = 0;
+                            for (int j = (int)ls.size() - 1; j >= 0; --j) {
+                                const int64_t dm = net.labels.at(ls[j]).dim, dg = r % dm;
+                                r /= dm;
+                                int64_t st = 1;
+                                for (size_t q = (size_t)find_pos(fp, ls[j]) + 1; q < fp.size(); ++q) st *= net.labels.at(fp[q]).dim;
+                                off += dg * st;
+                            }
+                            tab[(size_t)x] = (int32_t)off;
+                        }
+                    };
+                    contrib(mf, fz_pm);
+                    contrib(nf, fz_pn);
+                    N.fz_ok = true;
+                    Q.fz_kappa = N.fz_mk;
+                    Q.fz_kappa.insert(Q.fz_kappa.end(), N.fz_nk.begin(), N.fz_nk.end());
+                }
+            }
+        }
+
         // arena buffer for all instances (a kept result: its slot in the pool)
-        size_t nbytes = (size_t)N.n_inst * N.view.size * es;
-        if (std::find(P.kept_fill.begin(), P.kept_fill.end(), v) != P.kept_fill.end()) {
+        size_t nbytes = N.fz_ok ? fz_planes_bytes + fz_scales_bytes : (size_t)N.n_inst * N.view.size * es;
+        N.alloc_bytes = nbytes;
+        if (kept_v) {
             N.base = BASE_KEPT;
             N.buf_off = (int64_t)net.kept.at(v).off;
         } else {
             N.buf_off = (int64_t)arena.alloc(nbytes);
             arena.log.back().node = v;
             N.base = BASE_ARENA;
+            if (N.fz_ok) N.fz_scales_off = (size_t)N.buf_off + fz_planes_bytes;
         }
 
         // per-instance pointer tables
@@ -1546,7 +1727,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             };
             // the larger operand decides the summed-label order (its split is the costly one)
             const bool m_big = VM.size >= VN.size;
-            std::vector<int64_t> kappa = m_big ? split_order(VM, fM, true) : split_order(VN, fN, true);
+            // a fused child writes its planes with the summed labels in its own order
+            const bool fzM = tc_mode && node[idM].fz_ok, fzN = tc_mode && node[idN].fz_ok;
+            std::vector<int64_t> kappa = (fzM || fzN) ? N.fz_kappa
+                                         : m_big      ? split_order(VM, fM, true)
+                                                      : split_order(VN, fN, true);
             if (kappa.empty()) kappa = m_big ? split_order(VM, fM, false) : split_order(VN, fN, false);
             if (kappa.empty()) kappa = m_big ? split_order(VN, fN, true) : split_order(VM, fM, true);
             if (kappa.empty()) kappa = m_big ? split_order(VN, fN, false) : split_order(VM, fM, false);
@@ -1567,30 +1752,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 // instance blocks: group the instances into full products of M-side
                 // and N-side child instances when every block has the same shape and
                 // (nearly) no child instance is split twice; else one block per instance
-                GemmGroups G;
-                {
-                    GemmGroups gm, gn;
-                    const bool okm = group_instances(instM, instN, true, gm);
-                    const bool okn = group_instances(instM, instN, false, gn);
-                    const double vm = (double)VM.size, vn = (double)VN.size;
-                    const double cm = okm ? gm.dup * vn : 1e300, cn = okn ? gn.dup * vm : 1e300;
-                    const double budget = 0.25 * ((double)node[idM].n_inst * vm + (double)node[idN].n_inst * vn);
-                    const bool can_merge = (okm || okn) && std::min(cm, cn) <= budget &&
-                                           (okm && cm <= cn ? gm : gn).bM.size() < (size_t)N.n_inst;
-                    const bool merge = can_merge && tuned(v, 0, net.opt.gemm_group != 0);
-                    if (can_merge)
-                        P.tunables.push_back({v, 0, merge ? 1 : 0,
-                                              sig_of(0, {nK, dimprod(fM), dimprod(fN), N.n_inst, node[idM].n_inst,
-                                                         node[idN].n_inst, VM.size, VN.size})});
-                    if (merge) {
-                        G = okm && cm <= cn ? gm : gn;
-                    } else {   // one block per instance; every child instance one group
-                        for (int64_t j = 0; j < node[idM].n_inst; ++j) G.gM.push_back({(int32_t)j});
-                        for (int64_t j = 0; j < node[idN].n_inst; ++j) G.gN.push_back({(int32_t)j});
-                        G.bM.assign(instM.begin(), instM.end());
-                        G.bN.assign(instN.begin(), instN.end());
-                    }
-                }
+                GemmGroups G = gemm_groups_of(v, true);
                 const bool grouped = !G.itab.empty();
                 const int64_t m_rows = G.nA * Mv, n_rows = G.nB * Nv;
                 const int64_t m_pad = (m_rows + T - 1) / T * T, n_pad = (n_rows + T - 1) / T * T;
@@ -1624,10 +1786,22 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     sa.rank_r = (int32_t)f.size();
                     sa.rank_k = (int32_t)kappa.size();
                     if (sa.rank_r > JET_MAXR || sa.rank_k > JET_MAXR) fail(JET_EINVAL, "operand rank too large");
+                    // tile rows along the source's fastest row labels: the row labels in
+                    // decreasing source stride (the split reads them in that order and
+                    // writes each row to its plane row, p_s the labels' plane strides)
+                    std::vector<int64_t> vf = f;
+                    std::stable_sort(vf.begin(), vf.end(), [&](int64_t x, int64_t y) {
+                        return V.strides[find_pos(V.labels, x)] > V.strides[find_pos(V.labels, y)];
+                    });
+                    sa.row_perm = vf != f ? 1 : 0;
                     for (int j = 0; j < sa.rank_r; ++j) {
-                        int p = find_pos(V.labels, f[f.size() - 1 - j]);
+                        const int64_t l = (sa.row_perm ? vf : f)[f.size() - 1 - j];
+                        int p = find_pos(V.labels, l);
                         sa.r_dim[j] = V.dims[p];
                         sa.r_s[j] = V.strides[p];
+                        int64_t ps = 1;
+                        for (size_t q = (size_t)find_pos(f, l) + 1; q < f.size(); ++q) ps *= net.labels.at(f[q]).dim;
+                        sa.p_s[j] = ps;
                     }
                     for (int j = 0; j < sa.rank_k; ++j) {
                         int p = find_pos(V.labels, kappa[kappa.size() - 1 - j]);
@@ -1706,8 +1880,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     return off;
                 };
                 size_t sclA = 0, sclB = 0;
-                size_t offA = split_child(idM, VM, fM, m_pad, G.gM, sclA);
-                size_t offB = split_child(idN, VN, fN, n_pad, G.gN, sclB);
+                // a fused child's epilogue has already written its side's planes and scales
+                size_t offA = fzM ? (size_t)node[idM].buf_off : split_child(idM, VM, fM, m_pad, G.gM, sclA);
+                size_t offB = fzN ? (size_t)node[idN].buf_off : split_child(idN, VN, fN, n_pad, G.gN, sclB);
+                if (fzM) sclA = node[idM].fz_scales_off;
+                if (fzN) sclB = node[idN].fz_scales_off;
                 const int64_t n_blocks = (int64_t)G.bM.size();
                 std::vector<int32_t> zA, zB;
                 if ((int64_t)(G.gM.size() + G.gN.size()) * NP > INT32_MAX) fail(JET_EINVAL, "too many instances of one GEMM node");
@@ -1742,6 +1919,17 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                               ? 1
                               : 0;
                 g.c_inst = N.n_inst;
+                if (N.fz_ok) {
+                    int lmk = 0, lnk = 0;
+                    while (((int64_t)1 << lmk) < dimprod(N.fz_mk)) ++lmk;
+                    while (((int64_t)1 << lnk) < dimprod(N.fz_nk)) ++lnk;
+                    g.c_tma = 0;
+                    g.fz_plane_elems = fz_plane_elems;
+                    g.fz_kpad = fz_kpad;
+                    g.fz_rows_pad = fz_rows_pad;
+                    g.fz_lmk = lmk;
+                    g.fz_lnk = lnk;
+                }
                 g.m_pad = m_pad;
                 g.n_pad = n_pad;
                 g.k_pad = k_pad;
@@ -1766,6 +1954,16 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     blob.patch_field(so, offsetof(TcGemmArgs, scaleA), BASE_ARENA, (int64_t)sclA);
                     blob.patch_field(so, offsetof(TcGemmArgs, scaleB), BASE_ARENA, (int64_t)sclB);
                 }
+                if (N.fz_ok) {   // fused split: this epilogue writes the parent's planes
+                    size_t o_ib = blob.reserve(fz_ibase.size() * 8, 8);
+                    std::memcpy(blob.bytes.data() + o_ib, fz_ibase.data(), fz_ibase.size() * 8);
+                    const size_t o_pm = blob.put_i32(fz_pm), o_pn = blob.put_i32(fz_pn);
+                    blob.patch_field(so, offsetof(TcGemmArgs, fz_planes), BASE_ARENA, N.buf_off);
+                    blob.patch_field(so, offsetof(TcGemmArgs, fz_scales), BASE_ARENA, (int64_t)N.fz_scales_off);
+                    blob.patch_field(so, offsetof(TcGemmArgs, fz_ibase), BASE_BLOB, (int64_t)o_ib);
+                    blob.patch_field(so, offsetof(TcGemmArgs, fz_pm), BASE_BLOB, (int64_t)o_pm);
+                    blob.patch_field(so, offsetof(TcGemmArgs, fz_pn), BASE_BLOB, (int64_t)o_pn);
+                }
                 Op op;
                 op.kind = OpKind::GemmTc;
                 op.node = v;
@@ -1781,7 +1979,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 op.grid_x = (int32_t)(n_pad / T);
                 op.grid_y = (int32_t)(m_pad / T);
                 op.grid_z = (int32_t)n_blocks;   // persistent launch: the tile count only
-                op.variant = grouped ? 1 : 0;
+                op.variant = (grouped ? 1 : 0) | (N.fz_ok ? 4 : 0);   // 4: writes its parent's planes
                 P.ops.push_back(op);
             } else {
             int formM = form(VM, fM), formN = form(VN, fN);

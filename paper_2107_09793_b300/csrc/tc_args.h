@@ -27,6 +27,11 @@ struct TcSplitArgs {
     int32_t mode, fast_k;           // fast_k: the source's stride-1 label is a summed label
     int64_t r_dim[JET_MAXR], r_s[JET_MAXR];   // row labels, fastest first, source strides
     int64_t k_dim[JET_MAXR], k_s[JET_MAXR];   // summed labels, fastest first, source strides
+    // row_perm: the row labels above are in the order that reads the source best
+    // (tile rows along its fastest labels); a row's plane row is then the sum of
+    // its digits times p_s (the labels' strides in the planes' row order)
+    int64_t p_s[JET_MAXR];
+    int32_t row_perm, pad2_;
 };
 
 // C[m][n] = sum_k A[m][k] B[n][k] over split planes, complex 4M form: the real
@@ -59,4 +64,15 @@ struct TcGemmArgs {
     int32_t ni_shift, c_tma;         // c_tma: C leaves through tensor-map bulk stores (Ni even;
                                      // grouped blocks: Mi a multiple of 32, Ni of 16)
     int64_t c_inst;                  // c_tma: node instances (the map's third extent)
+    // FP16X3 fused split (fz_planes != 0): instead of complex64 C, the epilogue
+    // writes the node's output as its parent GEMM's operand planes and scales.
+    // Node instance i, row m = (m_f, m_k) with m_k the lowest lmk bits, column
+    // n = (n_f, n_k) with n_k the lowest lnk bits: parent row r = fz_pm[m_f] +
+    // fz_pn[n_f], parent summed index k = m_k 2^lnk + n_k; element (r, k) of
+    // plane q at fz_planes + 2 (fz_ibase[2 i] + q fz_plane_elems + r fz_kpad + k)
+    // bytes, its 64-wide chunk scale at fz_scales + 4 (fz_ibase[2 i + 1] +
+    // (k / 64) fz_rows_pad + r) (2^lgsz = 64 / 2^lnk lanes share a chunk)
+    uint64_t fz_planes, fz_scales, fz_ibase, fz_pm, fz_pn;
+    int64_t fz_plane_elems, fz_kpad, fz_rows_pad;
+    int32_t fz_lmk, fz_lnk;
 };
