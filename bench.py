@@ -1019,23 +1019,28 @@ def run_impl(args):
                            "ms_per_step": statistics.mean(msm),
                            "tflops": ranges["flop"] / (statistics.mean(msm) * 1e-3) / 1e12,
                            "amp": [amp_m.real, amp_m.imag], "err_vs_oracle_partials": parity(prec)}
-        # the headline mode with every GEMM instance run as its own product
-        h = handle(args.precision, gemm_group=False)
-        am = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
-        h.contract_async(outs, am.data_ptr(), sh)
-        torch.cuda.synchronize()
-        msm = []
-        for _ in range(2):
-            flush.zero_()
-            ev0.record(stream)
+        # the headline mode with every GEMM instance run as its own product, and
+        # with every GEMM writing complex64 (no fused splits)
+        for tag, kw, note in (("_ungrouped", {"gemm_group": False}, "jet_options.gemm_group = 0: one GEMM per instance"),
+                              ("_unfused", {"fuse_split": False},
+                               "jet_options.fuse_split = 0: every GEMM writes complex64, split by the next GEMM")):
+            h = handle(args.precision, **kw)
+            am = torch.zeros(len(outs), dtype=torch.complex128, device="cuda")
             h.contract_async(outs, am.data_ptr(), sh)
-            ev1.record(stream)
-            ev1.synchronize()
-            msm.append(ev0.elapsed_time(ev1))
-        h.close()
-        modes[args.precision + "_ungrouped"] = {"value": 1000.0 / statistics.mean(msm), "unit": "amplitudes/s",
-                                                "ms_per_step": statistics.mean(msm),
-                                                "note": "jet_options.gemm_group = 0: one GEMM per instance"}
+            torch.cuda.synchronize()
+            msm = []
+            for _ in range(2):
+                flush.zero_()
+                ev0.record(stream)
+                h.contract_async(outs, am.data_ptr(), sh)
+                ev1.record(stream)
+                ev1.synchronize()
+                msm.append(ev0.elapsed_time(ev1))
+            h.close()
+            amp_m = complex(am[0].item())
+            modes[args.precision + tag] = {"value": 1000.0 / statistics.mean(msm), "unit": "amplitudes/s",
+                                           "ms_per_step": statistics.mean(msm), "amp": [amp_m.real, amp_m.imag],
+                                           "note": note}
         if "fp32" in modes:
             a32 = complex(*modes["fp32"]["amp"])
             for prec, m in modes.items():
@@ -1231,6 +1236,42 @@ def run_grid53_case(args):
     return 0
 
 
+def run_fused_case(args):
+    """Two chained GEMMs, the first one's output the second one's larger operand
+    (X[a, k] Y[k, b] -> C1[a, b], then C1 Z summing 4 labels of a and 2 of b),
+    FP16x3, sized for ncu captures (about 0.6 GB): --fuse 1 lets the first GEMM
+    write the second one's planes (fused split), 0 writes complex64 and splits."""
+    import torch
+    from circuits import SplitMix64
+    from paper_2107_09793_b300 import jet
+    torch.cuda.set_device(0)
+    A = list(range(100, 114)); Kl = list(range(200, 208)); B = list(range(300, 308)); C = list(range(400, 407))
+    lx, ly, lz = A + Kl, Kl + B, A[10:] + B[6:] + C
+    rng = np.random.default_rng(SplitMix64(11).next_u64() % (1 << 32))
+    rnd = lambda r: (rng.random([2] * r) - 0.5 + 1j * (rng.random([2] * r) - 0.5)).astype(np.complex64)
+    opens = A[:10] + B[:6] + C
+    net = jet.Network([lx, ly, lz], [rnd(len(lx)), rnd(len(ly)), rnd(len(lz))], precision="fp16x3", profile=1,
+                      fuse_split=bool(args.fuse))
+    net.set_open(opens)
+    net.set_free(opens)
+    net.path_set([(0, 1), (3, 2)])
+    outs = np.zeros((1, len(opens)), np.int32)
+    net.contract(outs)
+    for _ in range(args.warmup):
+        net.contract(outs)
+    kern = {}
+    for _ in range(args.steps):
+        net.contract(outs)
+        for r in net.profile():
+            if r["ms"] >= 0:
+                kern.setdefault(f'{r["kind"]} node {r["node"]} variant {r["variant"]}', []).append(r["ms"])
+    print(json.dumps({"case": "two chained GEMMs (16384 x 256 x 256, then 65536 x 128 x 64), fp16x3",
+                      "fuse_split": int(args.fuse), "ms": {k: statistics.mean(v) for k, v in kern.items()}}),
+          flush=True)
+    net.close()
+    return 0
+
+
 def run_gbs16_case(args):
     """Only the 256-pattern bosonic batch (for a launch list of that workload)."""
     import torch
@@ -1268,7 +1309,8 @@ def main():
                     "parameterised circuit gradient, 53-qubit slices)")
     ap.add_argument("--gemm-shape", default="8192,8192,2048,1", help="--case gemm: M,N,K,IA[,IB]")
     ap.add_argument("--gemm-group", type=int, default=1, help="--case gemm: 1 groups instance pairs into blocks")
-    ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16", "grid53"],
+    ap.add_argument("--fuse", type=int, default=1, help="--case fused: 1 fused split, 0 complex64 + split")
+    ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16", "grid53", "fused"],
                     help="gemm / apply: one kernel family on a case sized for ncu captures; "
                          "gbs16: only the bosonic batch; grid53: only the headline contraction")
     args = ap.parse_args()
@@ -1280,6 +1322,8 @@ def main():
         return run_gbs16_case(args)
     if args.case == "grid53":
         return run_grid53_case(args)
+    if args.case == "fused":
+        return run_fused_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_impl(args)

@@ -108,6 +108,11 @@ typedef struct {
                                  (a shared operand read once per tile row or column, short
                                  sides packed into full tiles); 0: one product per
                                  instance                                                 */
+    int32_t fuse_split;       /* 1 (default): FP16x3, a GEMM whose output is the larger
+                                 operand of the next GEMM writes that GEMM's FP16 operand
+                                 planes and chunk scales from its epilogue (no complex64
+                                 intermediate, no operand split) where the shapes allow
+                                 it; 0: complex64 output, split by the next GEMM          */
 } jet_options;
 
 typedef struct {

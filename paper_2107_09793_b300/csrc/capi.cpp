@@ -165,6 +165,7 @@ void jet_options_default(jet_options *opt)
     opt->profile = 0;
     opt->apply_tc_min_kf = 1024;
     opt->gemm_group = 1;
+    opt->fuse_split = 1;
 }
 
 int jet_network_create(const jet_tensor_desc *tensors, int32_t n, const jet_options *opt, jet_network **out)

@@ -379,13 +379,16 @@ __device__ __forceinline__ void fz_store_group(const TcGemmArgs &a, const float 
                                                int64_t ibase, int64_t sbase, const int32_t *rn, int32_t rm, int64_t mk,
                                                int lane)
 {
-    constexpr int LNK = NK == 2 ? 1 : NK == 4 ? 2 : NK == 8 ? 3 : 4;
+    constexpr int LNK = NK == 4 ? 2 : 3;
     constexpr int GSZ = 64 / NK;   // lanes of one chunk
     const int64_t k0 = mk << LNK, ch = k0 >> 6;
-    __half *planes = (__half *)a.fz_planes;
+    __half *gp = (__half *)a.fz_planes + ibase + k0;                       // plane 0, row 0 of the group's rows
+    float *gs = (float *)a.fz_scales + sbase + ch * a.fz_rows_pad;         // the chunk's scales
+    const uint32_t kpad = (uint32_t)a.fz_kpad;
+    const int64_t pe = a.fz_plane_elems;
 #pragma unroll
     for (int t = 0; t < 16 / NK; ++t) {
-        const int64_t r = (int64_t)rm + rn[t];
+        const uint32_t r = (uint32_t)(rm + rn[t]);
         float m = 0.f;
 #pragma unroll
         for (int c = 0; c < NK; ++c) m = fmaxf(m, fmaxf(fabsf(re[t * NK + c]), fabsf(im[t * NK + c])));
@@ -394,29 +397,24 @@ __device__ __forceinline__ void fz_store_group(const TcGemmArgs &a, const float 
         const int ex = m > 0.f ? max(-100, min(100, 141 - (int)((__float_as_uint(m) >> 23) & 0xffu))) : 0;
         const float f = __uint_as_float((uint32_t)(127 + ex) << 23);
         if (it < 0) continue;
-        if ((lane & (GSZ - 1)) == 0) ((float *)a.fz_scales)[sbase + ch * a.fz_rows_pad + r] = __uint_as_float((uint32_t)(127 - ex) << 23);
+        if ((lane & (GSZ - 1)) == 0) gs[r] = __uint_as_float((uint32_t)(127 - ex) << 23);
         uint32_t rh[NK / 2], rl[NK / 2], ih[NK / 2], il[NK / 2];
 #pragma unroll
         for (int c = 0; c < NK / 2; ++c) {
             rh[c] = fz_h2(re[t * NK + 2 * c] * f, re[t * NK + 2 * c + 1] * f, rl[c]);
             ih[c] = fz_h2(im[t * NK + 2 * c] * f, im[t * NK + 2 * c + 1] * f, il[c]);
         }
-        __half *e = planes + ibase + r * a.fz_kpad + k0;
-        const int64_t pe = a.fz_plane_elems;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t *w = q == 0 ? rh : q == 1 ? rl : q == 2 ? ih : il;
-            __half *d = e + q * pe;
-            if (NK == 2) {
-                *(uint32_t *)d = w[0];
-            } else if (NK == 4) {
-                *(uint2 *)d = make_uint2(w[0], w[1 % (NK / 2)]);
-            } else {
-#pragma unroll
-                for (int v = 0; v < NK / 8; ++v)
-                    *(uint4 *)(d + 8 * v) = make_uint4(w[(4 * v) % (NK / 2)], w[(4 * v + 1) % (NK / 2)],
-                                                       w[(4 * v + 2) % (NK / 2)], w[(4 * v + 3) % (NK / 2)]);
-            }
+        __half *e = gp + (uint64_t)r * kpad;
+        if (NK == 4) {
+            *(uint2 *)e = make_uint2(rh[0], rh[1 % (NK / 2)]);
+            *(uint2 *)(e + pe) = make_uint2(rl[0], rl[1 % (NK / 2)]);
+            *(uint2 *)(e + 2 * pe) = make_uint2(ih[0], ih[1 % (NK / 2)]);
+            *(uint2 *)(e + 3 * pe) = make_uint2(il[0], il[1 % (NK / 2)]);
+        } else {
+            *(uint4 *)e = make_uint4(rh[0], rh[1], rh[2 % (NK / 2)], rh[3 % (NK / 2)]);
+            *(uint4 *)(e + pe) = make_uint4(rl[0], rl[1], rl[2 % (NK / 2)], rl[3 % (NK / 2)]);
+            *(uint4 *)(e + 2 * pe) = make_uint4(ih[0], ih[1], ih[2 % (NK / 2)], ih[3 % (NK / 2)]);
+            *(uint4 *)(e + 3 * pe) = make_uint4(il[0], il[1], il[2 % (NK / 2)], il[3 % (NK / 2)]);
         }
     }
 }
@@ -749,17 +747,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 if (grouped) split_row(R, jj, mm);
                 const int64_t mk = mm & (((int64_t)1 << a.fz_lmk) - 1), mf = mm >> a.fz_lmk;
                 const int32_t rm = __ldg((const int *)a.fz_pm + mf);
+                if (a.fz_lnk == 2) {   // 4 or 8 summed entries from the N side (the planner's two forms)
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const int64_t it = fz_t64[p], ib = fz_t64[4 + p], sb = fz_t64[8 + p];
-                    const float *re = racc + p * 16, *im = iacc + p * 16;
-                    const int32_t *rn = fz_rn + ((16 * p) >> a.fz_lnk);
-                    switch (a.fz_lnk) {
-                    case 1: fz_store_group<2>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
-                    case 2: fz_store_group<4>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
-                    case 3: fz_store_group<8>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
-                    default: fz_store_group<16>(a, re, im, it, ib, sb, rn, rm, mk, lane); break;
-                    }
+                    for (int p = 0; p < 4; ++p)
+                        fz_store_group<4>(a, racc + p * 16, iacc + p * 16, fz_t64[p], fz_t64[4 + p], fz_t64[8 + p],
+                                          fz_rn + 4 * p, rm, mk, lane);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        fz_store_group<8>(a, racc + p * 16, iacc + p * 16, fz_t64[p], fz_t64[4 + p], fz_t64[8 + p],
+                                          fz_rn + 2 * p, rm, mk, lane);
                 }
             } else if (tc_cstage<MODE>() && a.c_tma && (a.Ni & 15) == 0 && col0 + 64 <= a.N) {
                 // bulk tensor stores: the warp's 32 rows x 16 columns staged as one

@@ -607,9 +607,9 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             // FP16x3 with a GEMM parent that sums labels of both of this node's
             // sides: this node's epilogue can write the parent's operand planes
             // (fused split) when the parent's summed labels from the N side number
-            // 2..16 entries and, with those from the M side, fill whole 64-entry
+            // 4 or 8 entries and, with those from the M side, fill whole 64-entry
             // chunks; they go lowest on each side (fM = [m_f, m_k], fN = [n_f, n_k])
-            if (tc_mode && net.opt.precision == JET_PREC_FP16X3 && !grad && pp >= 0) {
+            if (tc_mode && net.opt.precision == JET_PREC_FP16X3 && net.opt.fuse_split && !grad && pp >= 0) {
                 const auto &ls = labset[sibling[v]];
                 std::vector<int64_t> Kp, Fp, Fs;
                 for (int64_t l : labset[v]) (find_pos(ls, l) >= 0 ? Kp : Fp).push_back(l);
@@ -644,7 +644,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     by_stride(mk, cM);
                     by_stride(nf, cN);
                     by_stride(nk, cN);
-                    if (NKd >= 2 && NKd <= 16 && MKd >= 64 / NKd && MKd * NKd == dimprod(Kp) && !mf.empty() &&
+                    if ((NKd == 4 || NKd == 8) && MKd >= 64 / NKd && MKd * NKd == dimprod(Kp) && !mf.empty() &&
                         !nf.empty()) {
                         N.a_is_m = am;
                         N.fM = mf;
@@ -1600,7 +1600,8 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             }
             const int64_t kblk = tc_k_block(net.opt.precision), T = tc_tile(), NP = tc_planes(net.opt.precision);
             const int64_t Kp = dimprod(Q.K);
-            ok = ok && Kp % 64 == 0 && Kp % kblk == 0 && dimprod(N.fz_nk) >= 2 && dimprod(N.fz_nk) <= 16;
+            ok = ok && Kp % 64 == 0 && Kp % kblk == 0 && (dimprod(N.fz_nk) == 4 || dimprod(N.fz_nk) == 8) &&
+                 Kp < ((int64_t)1 << 16);
             if (ok) {   // this node's own tiles: whole (rows in 32s per instance, columns in 64s)
                 const GemmGroups Gv = gemm_groups_of(v, false);
                 const int64_t mr = Gv.nA * dimprod(N.fM), nr = Gv.nB * dimprod(N.fN);

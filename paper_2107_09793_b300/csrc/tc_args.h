@@ -71,7 +71,7 @@ struct TcGemmArgs {
     // fz_pn[n_f], parent summed index k = m_k 2^lnk + n_k; element (r, k) of
     // plane q at fz_planes + 2 (fz_ibase[2 i] + q fz_plane_elems + r fz_kpad + k)
     // bytes, its 64-wide chunk scale at fz_scales + 4 (fz_ibase[2 i + 1] +
-    // (k / 64) fz_rows_pad + r) (2^lgsz = 64 / 2^lnk lanes share a chunk)
+    // (k / 64) fz_rows_pad + r) (64 / 2^lnk lanes share a chunk; lnk is 2 or 3)
     uint64_t fz_planes, fz_scales, fz_ibase, fz_pm, fz_pn;
     int64_t fz_plane_elems, fz_kpad, fz_rows_pad;
     int32_t fz_lmk, fz_lnk;

@@ -35,7 +35,8 @@ class JetError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("reuse", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("gemm_min_k", ctypes.c_int64), ("workspace_limit", ctypes.c_int64),
-                ("profile", ctypes.c_int32), ("apply_tc_min_kf", ctypes.c_int32), ("gemm_group", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("apply_tc_min_kf", ctypes.c_int32), ("gemm_group", ctypes.c_int32),
+                ("fuse_split", ctypes.c_int32)]
 
 
 class OpRecord(ctypes.Structure):
@@ -130,7 +131,7 @@ def _check(rc: int):
 
 
 def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm_min_k=16, profile=0,
-                    apply_tc_min_kf=1024, workspace_limit=0, gemm_group=True) -> Options:
+                    apply_tc_min_kf=1024, workspace_limit=0, gemm_group=True, fuse_split=True) -> Options:
     o = Options()
     lib().jet_options_default(ctypes.byref(o))
     o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
@@ -142,6 +143,7 @@ def default_options(precision="fp32", reuse=True, use_graph=True, device=0, gemm
     o.apply_tc_min_kf = int(apply_tc_min_kf)
     o.workspace_limit = int(workspace_limit)
     o.gemm_group = int(bool(gemm_group))
+    o.fuse_split = int(bool(fuse_split))
     return o
 
 
