@@ -43,11 +43,18 @@ WORKLOAD53 = ("grid53: 53-qubit 9x6 grid minus one corner random circuit, 12 cyc
 # planner settings of the stored grid53 order and slicing (tests/golden/grid53_plan.json)
 GRID53_PLAN = dict(seed=1, n_trials=512, cap=1 << 28, reconfigure_passes=8)
 
-# DRAM bytes (read + write) of the dominant launch, measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on this workload with the kernel
-# as it stands; keyed by (kernel, algorithmic FLOP or bytes of the launch) so that
-# a different plan or precision reports null instead of a stale figure.
-MEASURED_TRAFFIC = {("apply_kernel_c64", 1342308352.0): 1.322e9, ("apply_tc_c64", 1344274432.0): 1.282e9}
+# DRAM bytes (read + write) of the dominant kind's longest launch, measured by
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass, in the launch
+# lists summarised under profiles/) with the kernels as they stand; keyed by
+# (kernel form, node, algorithmic FLOP or bytes of the launch) so that another
+# plan, precision or form reports null instead of a stale figure.
+MEASURED_TRAFFIC = {
+    ("tc_gemm_kernel<fp16x3>", 1883, 8796093022208.0): 69.41e9,   # grid53, writes node 1884's planes
+    ("tc_gemm_kernel<fp16x3>", 1882, 8796093022208.0): 53.90e9,   # grid53, writes node 1883's planes
+    ("tc_gemm_kernel<fp16x3>", 1400, 8796093022208.0): 75.93e9,   # grid53
+    ("apply_tc_c64<fp16x3>", 1017, 1344274432.0): 1.2834e9,        # grid30
+    ("apply_kernel_c64<fp16x3>", 1032, 1342308352.0): 1.3215e9,    # grid30
+}
 
 
 def load_peaks():
@@ -535,7 +542,7 @@ def grid30_line(args, dev, peaks, peak_src):
             peak = peaks["bf16_tflops_sustained"] * (0.5 if args.precision.startswith("tf32") else 1.0)
             kname = f"tc_gemm_kernel<{args.precision}>" if tc else "gemm_simt_kernel"
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["flop"])), "kernel": kname,
+                    "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["node"], recs[big]["flop"])), "kernel": kname,
                     "per_launch_ms": ms, "flop_per_launch": recs[big]["flop"],
                     "issued_tensor_tflops": achieved * issue if tc else None,
                     "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)"
@@ -547,13 +554,13 @@ def grid30_line(args, dev, peaks, peak_src):
             big = max(ids, key=lambda i: timed[i])
             if dom == "apply":   # CUDA-core forms and the tensor-core form (variant bit 8)
                 kname = "apply_kernel_c64 + apply_tc_c64"
-                kbig = "apply_tc_c64" if recs[big]["variant"] & 8 else "apply_kernel_c64"
+                kbig = ("apply_tc_c64" if recs[big]["variant"] & 8 else "apply_kernel_c64") + f"<{args.precision}>"
             else:
                 kname = kbig = f"tc_split_kernel<{args.precision}>"
             achieved = nbytes / (ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "kernel": kname,
-                    "traffic": MEASURED_TRAFFIC.get((kbig, recs[big]["bytes"])),
+                    "traffic": MEASURED_TRAFFIC.get((kbig, recs[big]["node"], recs[big]["bytes"])),
                     "traffic_launch": {"node": recs[big]["node"], "kernel": kbig, "bytes": recs[big]["bytes"],
                                        "ms": timed[big], "gb_s": recs[big]["bytes"] / (timed[big] * 1e-3) / 1e9},
                     "launches_per_step": len(ids), "bytes_per_step": nbytes, "ms_per_step": ms,
@@ -752,20 +759,21 @@ def roofline_of(recs, timed, prec, peaks, peak_src, step_ms):
               "flop_per_range": flop, "bytes_per_range": nbytes,
               "longest_launch": {"node": recs[big]["node"], "ms": timed[big], "flop": recs[big]["flop"],
                                  "bytes": recs[big]["bytes"]},
-              "traffic_note": "dram bytes per launch from the ncu summary under profiles/ (null when not captured "
-                              "for this kernel as it stands)"}
+              "traffic_note": "traffic: dram bytes of the longest launch from the ncu launch list under profiles/ "
+                              "(null when not captured for this kernel as it stands)"}
     if t_tensor > t_hbm:
         achieved = flop / (ms * 1e-3) / 1e12
         peak = tc_peak / issue
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["flop"])),
+                "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["node"], recs[big]["flop"])),
                 "issued_tensor_tflops": achieved * issue, "tensor_peak_for_dtype": tc_peak,
                 "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)" if tf32 else "")
                                + f" / {issue} ({issue} tensor products per real product): the algorithmic ceiling"}
     else:
         achieved = nbytes / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["bytes"])),
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["node"], recs[big]["bytes"])),
                 "peak_source": f"hbm_gbs of {peak_src}"}
     roof.update(common)
     roof["kinds_timed_ms_per_range"] = {k: sum(timed[i] for i in v) for k, v in by_kind.items()}
@@ -1272,6 +1280,16 @@ def run_fused_case(args):
     return 0
 
 
+def run_grid30_case(args):
+    """Only the 30-qubit grid line (about 1.4 GB on the device): for launch lists
+    and captures of its kernels."""
+    import torch
+    torch.cuda.set_device(0)
+    peaks, peak_src = load_peaks()
+    print(json.dumps(grid30_line(args, 0, peaks, peak_src)), flush=True)
+    return 0
+
+
 def run_gbs16_case(args):
     """Only the 256-pattern bosonic batch (for a launch list of that workload)."""
     import torch
@@ -1310,7 +1328,8 @@ def main():
     ap.add_argument("--gemm-shape", default="8192,8192,2048,1", help="--case gemm: M,N,K,IA[,IB]")
     ap.add_argument("--gemm-group", type=int, default=1, help="--case gemm: 1 groups instance pairs into blocks")
     ap.add_argument("--fuse", type=int, default=1, help="--case fused: 1 fused split, 0 complex64 + split")
-    ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16", "grid53", "fused"],
+    ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16", "grid53", "fused",
+                                                            "grid30"],
                     help="gemm / apply: one kernel family on a case sized for ncu captures; "
                          "gbs16: only the bosonic batch; grid53: only the headline contraction")
     args = ap.parse_args()
@@ -1324,6 +1343,8 @@ def main():
         return run_grid53_case(args)
     if args.case == "fused":
         return run_fused_case(args)
+    if args.case == "grid30":
+        return run_grid30_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_impl(args)
