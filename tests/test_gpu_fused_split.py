@@ -43,9 +43,9 @@ def _network(sliced):
     return labels, data, opens, xs + zs
 
 
-def plan_network(sliced, prec="fp16x3"):
+def plan_network(sliced, prec="fp16x3", fuse=True):
     labels, data, opens, sl = _network(sliced)
-    net = jet.Network(labels, data, precision=prec, profile=2)
+    net = jet.Network(labels, data, precision=prec, profile=2, fuse_split=fuse)
     net.set_open(opens)
     net.set_free(opens)
     path = [(0, 1), (4, 2), (5, 3)] if sliced else [(0, 1), (3, 2)]
@@ -93,3 +93,23 @@ def test_fused_split_matches_the_oracle_element_by_element(sliced):
     err = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
     print(f"fused split (sliced={sliced}): max elementwise err {err:.2e}")
     assert err <= 1e-5
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("sliced", [False, True])
+def test_fused_planes_equal_the_split_bit_for_bit(sliced):
+    """The fused epilogue writes the planes and scales the operand split would
+    (same chunk maxima, exponents and roundings), so C2 is bitwise the same
+    with jet_options.fuse_split = 0."""
+    outs = None
+    got = []
+    for fuse in (True, False):
+        net, labels, data, opens, sl, path = plan_network(sliced, fuse=fuse)
+        try:
+            outs = np.zeros((1, len(opens)), np.int32)
+            got.append(np.asarray(net.contract(outs)[0]).copy())
+            fused = any(r["kind"] == "gemm_tc" and r["variant"] & 4 for r in net.profile())
+        finally:
+            net.close()
+        assert fused == fuse
+    assert np.array_equal(got[0], got[1])
