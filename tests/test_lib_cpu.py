@@ -429,6 +429,31 @@ def test_small_levels_run_as_chained_launches():
         net.close()
 
 
+def test_arena_liveness_with_fused_splits_on_the_53_qubit_range_plan():
+    """The benchmark's FP16x3 range plan (GEMMs that write their parent's planes
+    in place of their complex64 output): no two live buffers overlap, and the
+    fused GEMMs' parents split only their other operand."""
+    import json
+    w = configs.build("grid53")
+    plan = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "grid53_plan.json")))
+    net = jet.from_network(w.network, precision="fp16x3")
+    try:
+        net.path_set([tuple(p) for p in plan["path"]])
+        net.slice(plan["sliced_labels"])
+        r = net.plan_ranges(w.outputs, int(216e9))
+        sl = plan["sliced_labels"]
+        T = [sl.index(x) for x in r["fixed_labels"]]
+        n = len(sl)
+        ids = [s_ for s_ in range(2 ** n) if all(((s_ >> (n - 1 - j)) & 1) == 0 for j in T)]
+        net.plan_slices(w.outputs, ids)
+        recs = net.profile()
+        fused = {x["node"] for x in recs if x["kind"] == "gemm_tc" and x["variant"] & 4}
+        assert len(fused) >= 3, recs
+        _check_liveness(net)
+    finally:
+        net.close()
+
+
 def test_arena_liveness_catches_a_planted_overlap():
     """The check itself: moving one live buffer onto another is caught."""
     w = configs.build("grid12")
