@@ -1247,17 +1247,17 @@ def run_grid53_case(args):
 def run_fused_case(args):
     """Two chained GEMMs, the first one's output the second one's larger operand
     (X[a, k] Y[k, b] -> C1[a, b], then C1 Z summing 4 labels of a and 2 of b),
-    FP16x3, sized for ncu captures (about 0.6 GB): --fuse 1 lets the first GEMM
+    FP16x3, sized for ncu captures (about 0.7 GB, beyond L2): --fuse 1 lets the first GEMM
     write the second one's planes (fused split), 0 writes complex64 and splits."""
     import torch
     from circuits import SplitMix64
     from paper_2107_09793_b300 import jet
     torch.cuda.set_device(0)
-    A = list(range(100, 114)); Kl = list(range(200, 208)); B = list(range(300, 308)); C = list(range(400, 407))
-    lx, ly, lz = A + Kl, Kl + B, A[10:] + B[6:] + C
+    A = list(range(100, 116)); Kl = list(range(200, 208)); B = list(range(300, 308)); C = list(range(400, 406))
+    lx, ly, lz = A + Kl, Kl + B, A[12:] + B[6:] + C
     rng = np.random.default_rng(SplitMix64(11).next_u64() % (1 << 32))
     rnd = lambda r: (rng.random([2] * r) - 0.5 + 1j * (rng.random([2] * r) - 0.5)).astype(np.complex64)
-    opens = A[:10] + B[:6] + C
+    opens = A[:12] + B[:6] + C
     net = jet.Network([lx, ly, lz], [rnd(len(lx)), rnd(len(ly)), rnd(len(lz))], precision="fp16x3", profile=1,
                       fuse_split=bool(args.fuse))
     net.set_open(opens)
@@ -1273,7 +1273,7 @@ def run_fused_case(args):
         for r in net.profile():
             if r["ms"] >= 0:
                 kern.setdefault(f'{r["kind"]} node {r["node"]} variant {r["variant"]}', []).append(r["ms"])
-    print(json.dumps({"case": "two chained GEMMs (16384 x 256 x 256, then 65536 x 128 x 64), fp16x3",
+    print(json.dumps({"case": "two chained GEMMs (65536 x 256 x 256, then 262144 x 64 x 64), fp16x3",
                       "fuse_split": int(args.fuse), "ms": {k: statistics.mean(v) for k, v in kern.items()}}),
           flush=True)
     net.close()

@@ -108,11 +108,17 @@ typedef struct {
                                  (a shared operand read once per tile row or column, short
                                  sides packed into full tiles); 0: one product per
                                  instance                                                 */
-    int32_t fuse_split;       /* 1 (default): FP16x3, a GEMM whose output is the larger
-                                 operand of the next GEMM writes that GEMM's FP16 operand
-                                 planes and chunk scales from its epilogue (no complex64
-                                 intermediate, no operand split) where the shapes allow
-                                 it; 0: complex64 output, split by the next GEMM          */
+    int32_t fuse_split;       /* 1 (default): epilogue fusions of the tensor-core GEMMs
+                                 where the shapes allow them: in FP16x3, a GEMM whose
+                                 output is the larger operand of the next GEMM writes that
+                                 GEMM's FP16 operand planes and chunk scales (no complex64
+                                 intermediate, no operand split); a GEMM whose output is
+                                 contracted with its sibling over every label, with its
+                                 summed extent in one accumulator chunk, forms those dot
+                                 products per tile (the parent only adds the tiles' parts;
+                                 taken by default for outputs up to 16 GB, a choice that
+                                 jet_autotune times); 0: complex64 output, contracted by
+                                 the next step                                            */
 } jet_options;
 
 typedef struct {

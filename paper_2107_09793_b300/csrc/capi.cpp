@@ -1165,7 +1165,7 @@ int jet_autotune(jet_network *net, int32_t n_amps, const int32_t *outputs, const
         for (const auto &t : tun0) all_cached = all_cached && cache.count(t.sig);
         auto set_choice = [&](const Plan::Tunable &t, int taken) {
             TuneChoice &c = N.tune[t.node];
-            (t.kind == 0 ? c.group : c.apply_tc) = (int8_t)taken;
+            (t.kind == 0 ? c.group : t.kind == 1 ? c.apply_tc : c.dot) = (int8_t)taken;
             if (taken != t.taken) ++changed;
         };
         if (all_cached) {
@@ -1176,7 +1176,8 @@ int jet_autotune(jet_network *net, int32_t n_amps, const int32_t *outputs, const
             for (const auto &t : tun1) other[{t.node, t.kind}] = t.taken;
             for (const auto &t : tun0) {
                 auto it = other.find({t.node, t.kind});
-                const bool flip = it != other.end() && it->second != t.taken && ms1[t.node] < 0.97 * ms0[t.node];
+                auto both = [&](std::map<int32_t, double> &ms) { return ms[t.node] + (t.node2 >= 0 ? ms[t.node2] : 0.0); };
+                const bool flip = it != other.end() && it->second != t.taken && both(ms1) < 0.97 * both(ms0);
                 set_choice(t, flip ? it->second : t.taken);
                 cache[t.sig] = flip ? it->second : t.taken;
             }

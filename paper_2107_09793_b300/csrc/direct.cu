@@ -400,20 +400,51 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
     }
 }
 
+// FP64 partials of single outputs (a GEMM's dot epilogue: many parts per output):
+// a warp per output, lane l adding parts l, l + 32, ... in order, then the 32
+// lane sums in a fixed butterfly (deterministic), rounded once to V.
 template <typename V>
+__global__ void splitk_reduce_warp_kernel(const __grid_constant__ SplitKReduceArgs a)
+{
+    const int64_t inst = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (inst >= a.n_inst) return;   // warp-uniform
+    const double2 *part = (const double2 *)a.partials + inst * a.ksplit;
+    double sx = 0.0, sy = 0.0;
+    for (int p = lane; p < a.ksplit; p += 32) {
+        const double2 v = part[p];
+        sx += v.x;
+        sy += v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+        V r;
+        r.x = sx;
+        r.y = sy;
+        *(V *)((const uint64_t *)a.ptrC)[inst] = r;
+    }
+}
+
+// (P: the partials' type, V: the output's; FP64 partials are added in FP64 and
+// rounded once)
+template <typename V, typename P = V>
 __global__ void splitk_reduce_kernel(const __grid_constant__ SplitKReduceArgs a)
 {
-    const V *part = (const V *)a.partials;
+    const P *part = (const P *)a.partials;
     const uint64_t *pC = (const uint64_t *)a.ptrC;
     const int64_t total = a.n_out * a.n_inst;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t inst = e / a.n_out, o = e - inst * a.n_out;
-        V s = vzero<V>();
+        P s = vzero<P>();
         // 8 partials loaded at a time, added in increasing part order
         for (int p0 = 0; p0 < a.ksplit; p0 += 8) {
-            V x[8];
+            P x[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = p0 + u < a.ksplit ? part[(inst * a.ksplit + p0 + u) * a.n_out + o] : vzero<V>();
+            for (int u = 0; u < 8; ++u) x[u] = p0 + u < a.ksplit ? part[(inst * a.ksplit + p0 + u) * a.n_out + o] : vzero<P>();
 #pragma unroll
             for (int u = 0; u < 8; ++u)
                 if (p0 + u < a.ksplit) {
@@ -421,7 +452,10 @@ __global__ void splitk_reduce_kernel(const __grid_constant__ SplitKReduceArgs a)
                     s.y += x[u].y;
                 }
         }
-        ((V *)pC[inst])[o] = s;
+        V r;
+        r.x = s.x;
+        r.y = s.y;
+        ((V *)pC[inst])[o] = r;
     }
 }
 
@@ -748,7 +782,14 @@ cudaError_t set_direct_smem_limits()
 
 cudaError_t launch_splitk_reduce(const SplitKReduceArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    if (c.variant & 1) splitk_reduce_kernel<double2><<<c.gx, 256, 0, s>>>(a);
+    if (a.parts64 && a.n_out == 1) {   // a warp per output (grid from the outputs)
+        const unsigned g = (unsigned)(((int64_t)a.n_inst * 32 + 255) / 256);
+        if (c.variant & 1) splitk_reduce_warp_kernel<double2><<<g, 256, 0, s>>>(a);
+        else splitk_reduce_warp_kernel<float2><<<g, 256, 0, s>>>(a);
+    } else if (a.parts64) {
+        if (c.variant & 1) splitk_reduce_kernel<double2, double2><<<c.gx, 256, 0, s>>>(a);
+        else splitk_reduce_kernel<float2, double2><<<c.gx, 256, 0, s>>>(a);
+    } else if (c.variant & 1) splitk_reduce_kernel<double2><<<c.gx, 256, 0, s>>>(a);
     else splitk_reduce_kernel<float2><<<c.gx, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -440,8 +440,26 @@ constexpr int TC_CST_ROW = 17;
 constexpr int TC_CST_BYTES = TC_EPI_WARPS * 32 * TC_CST_ROW * 8 > TC_EPI_WARPS * 2 * 4096
                                  ? TC_EPI_WARPS * 32 * TC_CST_ROW * 8
                                  : TC_EPI_WARPS * 2 * 4096;
+// dot epilogue: each epilogue warp stages A in TC_DOT_BUFS units of 32 rows x 8
+// complex values
+constexpr int TC_DOT_BUFS = 5;
+constexpr int TC_DOT_WARP_BYTES = TC_DOT_BUFS * 2048;
 constexpr int TC_SMEM_LIMIT = 232448;   // opt-in dynamic shared memory per block
 constexpr int TC_STATIC_SMEM = 4096;    // barriers, scale staging and flags (upper bound)
+// K blocks (pipeline stages) per accumulator chunk
+template <int MODE>
+__host__ __device__ constexpr int tc_chunk_kb()
+{
+    return TcCfg<MODE>::CHUNK_K / (TC_ROWB / TcCfg<MODE>::EB) > 0 ? TcCfg<MODE>::CHUNK_K / (TC_ROWB / TcCfg<MODE>::EB)
+                                                                  : 1;
+}
+template <int MODE>
+__host__ __device__ constexpr bool tc_dot_fits()
+{
+    return TcCfg<MODE>::STAGES * 2 * TcCfg<MODE>::NP * TC_PLANE_TILE + 1024 + TC_EPI_WARPS * TC_DOT_WARP_BYTES +
+               TC_STATIC_SMEM <=
+           TC_SMEM_LIMIT;
+}
 template <int MODE>
 __host__ __device__ constexpr bool tc_cstage()
 {
@@ -464,7 +482,91 @@ __device__ __forceinline__ void tile_coords(int64_t t, int tiles_m, int tiles_n,
     tn = idx / gm;
 }
 
-template <int MODE>
+// Dot epilogue: copy A's values of the warp's 32 rows (row offsets xm, one per
+// lane) x the 8 columns of unit q of its 64 (column offsets xn0, xn1: columns
+// lane and 32 + lane) into buf as one group of 16-byte asynchronous copies
+// (through L2 only), each of two values adjacent in A:
+//   dot_lcol 1: columns 2p, 2p + 1 of a row, at r 8 + 2 (p ^ (r / 2 % 4))
+//   dot_lcol 0: rows 2p, 2p + 1 of a column, at c 32 + r
+// (a quarter warp's copies and a row's reads then meet every bank once).
+__device__ __forceinline__ void dot_stage(const TcGemmArgs &a, const float2 *A, int64_t xm, int32_t xn0, int32_t xn1,
+                                          int q, float2 *buf, int lane)
+{
+    const uint32_t b0 = smem_u32(buf);
+    const int32_t xq = q < 4 ? xn0 : xn1;
+    if (a.dot_lcol) {   // a quarter warp covers two rows, a lane a column pair
+        const int p = lane & 3;
+        const int64_t xc = __shfl_sync(0xffffffffu, xq, (q & 3) * 8 + 2 * p);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = 8 * i + (lane >> 2);
+            const int64_t xr = __shfl_sync(0xffffffffu, xm, r);
+            cp_async16_zfill(b0 + (uint32_t)(r * 8 + 2 * (p ^ ((r >> 1) & 3))) * 8u, A + xr + xc, 16);
+        }
+    } else {            // half a warp covers a column's 32 rows, a lane a row pair
+        const int p = lane & 15;
+        const int64_t xr = __shfl_sync(0xffffffffu, xm, 2 * p);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = 2 * i + (lane >> 4);
+            const int64_t xc = __shfl_sync(0xffffffffu, xq, (q & 3) * 8 + c);
+            cp_async16_zfill(b0 + (uint32_t)(c * 32 + 2 * p) * 8u, A + xr + xc, 16);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Dot epilogue: the lane's row of a staged unit (layouts above)
+__device__ __forceinline__ void dot_read(const TcGemmArgs &a, const float2 *buf, int lane, float2 (&av)[8])
+{
+    if (a.dot_lcol) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const float4 v = *(const float4 *)(buf + lane * 8 + 2 * (p ^ ((lane >> 1) & 3)));
+            av[2 * p] = make_float2(v.x, v.y);
+            av[2 * p + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) av[c] = buf[c * 32 + lane];
+    }
+}
+
+// wait until at most n (0 .. 4) of this thread's copy groups are pending
+__device__ __forceinline__ void cp_async_wait_upto(int n)
+{
+    if (n >= 4) asm volatile("cp.async.wait_group 4;" ::: "memory");
+    else if (n == 3) asm volatile("cp.async.wait_group 3;" ::: "memory");
+    else if (n == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// Dot form: the tiles at one position within a node instance come together
+// over the block's instances (j, l), so that instances that pair with one
+// sibling read its tile at about the same time (the later reads from L2):
+// t = ((inst tiles_mi + tmi) tiles_ni + tni) nA nB + j nB + l, Mi and Ni
+// multiples of 128.  key: the instance's itab index; tni: its column tile.
+__device__ __forceinline__ void tile_coords_dot(int64_t t, const TcGemmArgs &a, int &inst, int &tm, int &tn,
+                                                int64_t &key, int64_t &tni)
+{
+    const int64_t nab = (int64_t)a.nA * a.nB, tmi_n = a.Mi >> 7, tni_n = a.Ni >> 7;
+    int64_t r = t / nab;
+    const int64_t jl = t - r * nab, j = jl / a.nB, l = jl - j * a.nB;
+    tni = r % tni_n;
+    r /= tni_n;
+    const int64_t tmi = r % tmi_n;
+    inst = (int)(r / tmi_n);
+    tm = (int)(j * tmi_n + tmi);
+    tn = (int)(l * tni_n + tni);
+    key = (int64_t)inst * nab + jl;
+}
+
+// (DOT: the dot-epilogue form, launched when a.dot_parts is set; a form of its
+// own so that its registers do not weigh on the others.  Its tiles end in the
+// dot block, which leaves the rest of the tile loop unreachable there.)
+#pragma nv_diag_suppress 128
+template <int MODE, bool DOT>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcGemmArgs a)
 {
     using Cfg = TcCfg<MODE>;
@@ -472,11 +574,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     constexpr int STAGE_BYTES = 2 * NP * TC_PLANE_TILE;
     constexpr int KE = TC_ROWB / Cfg::EB;               // K elements per stage
     constexpr int KSUB = TC_ROWB / 32;                   // MMAs of 32 bytes of K per stage
-    constexpr int CHUNK_KB = Cfg::CHUNK_K / KE > 0 ? Cfg::CHUNK_K / KE : 1;   // stages per K chunk
+    constexpr int CHUNK_KB = tc_chunk_kb<MODE>();   // stages per K chunk
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bars[2 * S + 4];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
+    __shared__ int dot_cnt[4];   // dot epilogue: warps done with the tile (a ring of four tiles)
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -497,6 +600,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             mbar_init(tempty0 + 8 * b, TC_EPI_WARPS);
         }
         abort_flag = 0;
+        dot_cnt[0] = dot_cnt[1] = dot_cnt[2] = dot_cnt[3] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -514,7 +618,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             int64_t kg = 0, issued = 0;
             for (int64_t t = blockIdx.x; t < total_tiles && !abort_flag; t += gridDim.x) {
                 int inst, tm, tn;
-                tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
+                if (DOT) {
+                    int64_t key_, tni_;
+                    tile_coords_dot(t, a, inst, tm, tn, key_, tni_);
+                } else {
+                    tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
+                }
                 const int zA = ((const int32_t *)a.zA)[inst], zB = ((const int32_t *)a.zB)[inst];
                 for (int kb = 0; kb < n_kb; ++kb, ++kg) {
                     const int s = (int)(kg % S);
@@ -596,10 +705,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         // bases of its four 16-column groups, parent-row parts of its n_f values),
         // staged in its slice of the C staging area while the chunks accumulate
         int64_t *fz_t64 = (int64_t *)(smem + (size_t)S * STAGE_BYTES + (size_t)(warp - 2) * 8192);
+        // dot epilogue: TC_DOT_BUFS staged 32 x 8 units of A per warp, in place
+        // of the C staging
+        float2 *dstage = (float2 *)(smem + (size_t)S * STAGE_BYTES + (size_t)(warp - 2) * TC_DOT_WARP_BYTES);
         int32_t *fz_rn = (int32_t *)(fz_t64 + 12);
+        // dot form: the next tile's lookups, loaded one tile ahead
+        int32_t n_pr0 = -1, n_pr1 = -1, n_xn0 = 0, n_xn1 = 0;
+        const float2 *n_A0 = nullptr, *n_A1 = nullptr;
+        auto dot_lookup = [&](int64_t tt) {
+            n_pr0 = n_pr1 = -1;
+            if (tt >= total_tiles) return;
+            int ii, tm_, tn_;
+            int64_t key, tni;
+            tile_coords_dot(tt, a, ii, tm_, tn_, key, tni);
+            const int32_t *xn = (const int32_t *)a.dot_xn + (tni << 7) + half * 64;
+            n_xn0 = __ldg(xn + lane);
+            n_xn1 = __ldg(xn + 32 + lane);
+            const int64_t it = a.itab ? __ldg((const int32_t *)a.itab + key) : ii;
+            if (it >= 0) {
+                n_pr0 = __ldg((const int32_t *)a.dot_pair + 2 * it);
+                n_pr1 = __ldg((const int32_t *)a.dot_pair + 2 * it + 1);
+                n_A0 = (const float2 *)__ldg((const unsigned long long *)a.dot_ptrA + 2 * it);
+                n_A1 = (const float2 *)__ldg((const unsigned long long *)a.dot_ptrA + 2 * it + 1);
+            }
+        };
+        if (DOT) dot_lookup(blockIdx.x);
         for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
             int inst, tm, tn;
-            tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
+            if (DOT) {
+                int64_t key_, tni_;
+                tile_coords_dot(t, a, inst, tm, tn, key_, tni_);
+            } else {
+                tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
+            }
             if (Cfg::SCALED && a.fz_planes) {
                 const int64_t c0 = (int64_t)tn * TC_BN + half * 64;
                 __syncwarp();   // the previous tile's readers of the lookups are done
@@ -640,12 +778,166 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 __syncwarp();
             }
+            if (DOT) {
+                // dot epilogue (the whole summed extent in one accumulator chunk):
+                // this tile's part of the parent's dot products, read straight from
+                // the accumulator, which the warp holds until it is done.  The
+                // tile's instance and its parent pairs are looked up one tile
+                // ahead; A's values are staged 8 columns at a time (TC_DOT_BUFS
+                // 2 KB buffers: the copies of the units after this one run while
+                // it is read, the first ones while the accumulator fills).  The
+                // epilogue warps may be up to two tiles apart, so the parts and
+                // counters live in a ring of four tiles
+                __shared__ float2 dred[4][TC_EPI_WARPS][2];
+                int64_t mt0 = (int64_t)tm * TC_BM, nt0 = (int64_t)tn * TC_BN, jj = 0, ll = 0;
+                if (a.itab) {
+                    jj = a.mi_shift >= 0 ? mt0 >> a.mi_shift : mt0 / a.Mi;
+                    mt0 -= jj * a.Mi;
+                    ll = a.ni_shift >= 0 ? nt0 >> a.ni_shift : nt0 / a.Ni;
+                    nt0 -= ll * a.Ni;
+                }
+                const int32_t d_pr0 = n_pr0, d_pr1 = n_pr1, xn0 = n_xn0, xn1 = n_xn1;
+                const float2 *d_A0 = n_A0, *d_A1 = n_A1;
+                dot_lookup(t + gridDim.x);
+                const int U = 8 * ((d_pr0 >= 0) + (d_pr1 >= 0));   // units: slot u / 8, columns 8 (u % 8) ..
+                const int64_t mm = mt0 + quarter * 32 + lane;
+                int64_t xm = 0;
+                for (int b = 0; b < a.dot_mbits; ++b)
+                    if ((mm >> b) & 1) xm += a.dot_sm[b];
+#pragma unroll
+                for (int u = 0; u < TC_DOT_BUFS - 1; ++u)
+                    if (u < U) dot_stage(a, d_A0, xm, xn0, xn1, u, dstage + u * 256, lane);
+                // SCALED: the row's and the warp's 64 column scales of the chunk
+                float fm = 1.f;
+                float *fn = sfn[warp - 2];
+                if (Cfg::SCALED) {
+                    const int64_t instA = ((const int32_t *)a.zA)[inst] / NP, instB = ((const int32_t *)a.zB)[inst] / NP;
+                    fm = __ldg((const float *)a.scaleA + instA * a.m_pad + (int64_t)tm * TC_BM + quarter * 32 + lane);
+                    const float *g = (const float *)a.scaleB + instB * a.n_pad + (int64_t)tn * TC_BN + half * 64;
+                    __syncwarp();
+                    fn[lane] = __ldg(g + lane);
+                    fn[lane + 32] = __ldg(g + lane + 32);
+                    __syncwarp();
+                }
+                const int buf = (int)(cg & 1);
+                if (!mbar_wait_bounded(tfull0 + 8 * buf, (uint32_t)((cg >> 1) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    asm volatile("cp.async.wait_all;" ::: "memory");   // no staged copy outlives the block
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = tmem + buf * 2 * TC_BN + ((uint32_t)(quarter * 32) << 16) + half * 64;
+                float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    if (u < U) {   // warp-uniform (one instance per tile)
+                        constexpr int AH = TC_DOT_BUFS - 1;   // units in flight ahead of this one
+                        if (u + AH < U)
+                            dot_stage(a, u + AH < 8 ? d_A0 : d_A1, xm, xn0, xn1, (u + AH) & 7,
+                                      dstage + ((u + AH) % TC_DOT_BUFS) * 256, lane);
+                        uint32_t R[8], I[8];
+                        JET_TMEM_LD8(base + (u & 7) * 8, R);
+                        JET_TMEM_LD8(base + TC_BN + (u & 7) * 8, I);
+                        cp_async_wait_upto(min(AH, U - 1 - u));   // unit u has landed
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        __syncwarp();
+                        float2 avs[8];
+                        dot_read(a, dstage + (u % TC_DOT_BUFS) * 256, lane, avs);
+                        float sx = 0.f, sy = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float f = Cfg::SCALED ? fm * fn[(u & 7) * 8 + j] : 1.f;
+                            const float cr = __uint_as_float(R[j]) * f, ci = __uint_as_float(I[j]) * f;
+                            const float2 av = avs[j];
+                            sx = fmaf(cr, av.x, fmaf(-ci, av.y, sx));
+                            sy = fmaf(cr, av.y, fmaf(ci, av.x, sy));
+                        }
+                        if (u < 8) {
+                            sx0 += sx;
+                            sy0 += sy;
+                        } else {
+                            sx1 += sx;
+                            sy1 += sy;
+                        }
+                        __syncwarp();   // the buffer is refilled TC_DOT_BUFS - 1 units on
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);   // the accumulator is free
+                ++cg;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx0 += __shfl_xor_sync(0xffffffffu, sx0, o);
+                    sy0 += __shfl_xor_sync(0xffffffffu, sy0, o);
+                    sx1 += __shfl_xor_sync(0xffffffffu, sx1, o);
+                    sy1 += __shfl_xor_sync(0xffffffffu, sy1, o);
+                }
+                const int par = (int)(((t - blockIdx.x) / gridDim.x) & 3);   // this CTA's tile count, mod 4
+                if (lane == 0) {
+                    dred[par][warp - 2][0] = make_float2(sx0, sy0);
+                    dred[par][warp - 2][1] = make_float2(sx1, sy1);
+                }
+                // the last of the eight epilogue warps to finish the tile adds their
+                // parts in warp order (no barrier: a warp that gave up on a wait
+                // never holds the others)
+                int last = 0;
+                if (lane == 0) {
+                    __threadfence_block();
+                    last = atomicAdd(&dot_cnt[par], 1) == TC_EPI_WARPS - 1;
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence_block();
+                    const int32_t pr = lane ? d_pr1 : d_pr0;
+                    if (lane < 2 && pr >= 0) {   // the eight parts added in FP64, the tile's part kept in FP64
+                        const volatile float2 *dr = dred[par][0] + lane;
+                        double ax = dr[0].x, ay = dr[0].y;
+                        for (int w = 1; w < TC_EPI_WARPS; ++w) {
+                            ax += dr[2 * w].x;
+                            ay += dr[2 * w].y;
+                        }
+                        const int64_t tile = (mt0 >> 7) * (a.Ni >> 7) + (nt0 >> 7);
+                        ((double2 *)a.dot_parts)[(int64_t)pr * a.dot_tiles + tile] = make_double2(ax, ay);
+                    }
+                    __syncwarp();
+                    if (lane == 0) dot_cnt[par] = 0;
+                }
+                continue;
+            }
             float racc[64], iacc[64];
 #pragma unroll
             for (int j = 0; j < 64; ++j) racc[j] = iacc[j] = 0.f;
             bool ok = !abort_flag;
+            // SCALED: the operands' power-of-two chunk scales (undone exactly), each
+            // chunk's loaded while the chunk before it accumulates: this row's, and
+            // the warp's 64 column scales (two per lane, read back as broadcasts)
+            float *fn = sfn[warp - 2];
+            const float *sc_a = nullptr, *sc_b = nullptr;
+            float fm_nx = 1.f, fn_nx0 = 1.f, fn_nx1 = 1.f;
+            if (Cfg::SCALED && n_chunks > 0) {
+                const int64_t instA = ((const int32_t *)a.zA)[inst] / NP, instB = ((const int32_t *)a.zB)[inst] / NP;
+                sc_a = (const float *)a.scaleA + instA * n_chunks * a.m_pad + (int64_t)tm * TC_BM + quarter * 32 + lane;
+                sc_b = (const float *)a.scaleB + instB * n_chunks * a.n_pad + (int64_t)tn * TC_BN + half * 64 + lane;
+                fm_nx = __ldg(sc_a);
+                fn_nx0 = __ldg(sc_b);
+                fn_nx1 = __ldg(sc_b + 32);
+            }
             for (int c = 0; c < n_chunks && ok; ++c, ++cg) {
                 const int buf = (int)(cg & 1);
+                float fm = 1.f;
+                if (Cfg::SCALED) {
+                    fm = fm_nx;
+                    __syncwarp();
+                    fn[lane] = fn_nx0;
+                    fn[lane + 32] = fn_nx1;
+                    __syncwarp();
+                    if (c + 1 < n_chunks) {
+                        fm_nx = __ldg(sc_a + (int64_t)(c + 1) * a.m_pad);
+                        fn_nx0 = __ldg(sc_b + (int64_t)(c + 1) * a.n_pad);
+                        fn_nx1 = __ldg(sc_b + (int64_t)(c + 1) * a.n_pad + 32);
+                    }
+                }
                 if (!mbar_wait_bounded(tfull0 + 8 * buf, (uint32_t)((cg >> 1) & 1), &abort_flag)) {
                     abort_flag = 1;
                     ok = false;
@@ -653,21 +945,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t base = tmem + buf * 2 * TC_BN + ((uint32_t)(quarter * 32) << 16) + half * 64;
-                // SCALED: undo the operands' power-of-two chunk scales (exact)
-                float fm = 1.f;
-                float *fn = sfn[warp - 2];
-                if (Cfg::SCALED) {
-                    const int64_t instA = ((const int32_t *)a.zA)[inst] / NP, instB = ((const int32_t *)a.zB)[inst] / NP;
-                    const int64_t row = (int64_t)tm * TC_BM + quarter * 32 + lane;
-                    fm = ((const float *)a.scaleA)[(instA * n_chunks + c) * a.m_pad + row];
-                    // the warp's 64 column scales: two loads per lane, read back as broadcasts
-                    const float *g = (const float *)a.scaleB + (instB * n_chunks + c) * a.n_pad + (int64_t)tn * TC_BN +
-                                     half * 64;
-                    __syncwarp();
-                    fn[lane] = __ldg(g + lane);
-                    fn[lane + 32] = __ldg(g + lane + 32);
-                    __syncwarp();
-                }
                 // 16 columns per TMEM load (8 in the scaled mode, whose scales need registers too)
                 constexpr int LW = Cfg::SCALED ? 8 : 16;
 #pragma unroll
@@ -853,12 +1130,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
     if (threadIdx.x == 0 && abort_flag) atomicOr((unsigned int *)a.status, 1u);
 }
+#pragma nv_diag_default 128
 
 // ------------------------------------------------------------------ host side
 template <int MODE>
-static int tc_smem_bytes()
+static int tc_smem_bytes(bool dot = false)
 {
-    return TcCfg<MODE>::STAGES * 2 * TcCfg<MODE>::NP * TC_PLANE_TILE + 1024 + (tc_cstage<MODE>() ? TC_CST_BYTES : 0);
+    return TcCfg<MODE>::STAGES * 2 * TcCfg<MODE>::NP * TC_PLANE_TILE + 1024 +
+           (dot ? TC_EPI_WARPS * TC_DOT_WARP_BYTES : tc_cstage<MODE>() ? TC_CST_BYTES : 0);
 }
 
 int tc_planes(int mode)
@@ -876,13 +1155,36 @@ int tc_planes(int mode)
 int tc_elem_bytes(int mode) { return (mode == JET_PREC_TF32 || mode == JET_PREC_TF32X3) ? 4 : 2; }
 int tc_k_block(int mode) { return TC_ROWB / tc_elem_bytes(mode); }
 int tc_tile() { return TC_BM; }
+// The dot epilogue stages its sibling values after the pipeline stages (modes
+// whose stages leave room for it) and reads one accumulator chunk: the
+// largest summed extent it takes (0: none)
+template <int MODE>
+static int tc_dot_max_k_of()
+{
+    return tc_dot_fits<MODE>() ? tc_chunk_kb<MODE>() * (TC_ROWB / TcCfg<MODE>::EB) : 0;
+}
+int tc_dot_max_k(int mode)
+{
+    switch (mode) {
+    case JET_PREC_TF32: return tc_dot_max_k_of<JET_PREC_TF32>();
+    case JET_PREC_TF32X3: return tc_dot_max_k_of<JET_PREC_TF32X3>();
+    case JET_PREC_BF16X3: return tc_dot_max_k_of<JET_PREC_BF16X3>();
+    case JET_PREC_BF16X6: return tc_dot_max_k_of<JET_PREC_BF16X6>();
+    case JET_PREC_FP16X3: return tc_dot_max_k_of<JET_PREC_FP16X3>();
+    default: return 0;
+    }
+}
 
 cudaError_t set_tc_smem_limits()
 {
     cudaError_t e = cudaSuccess;
 #define JET_TCSM(M)                                                                                        \
     if (e == cudaSuccess)                                                                                  \
-        e = cudaFuncSetAttribute(tc_gemm_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes<M>())
+        e = cudaFuncSetAttribute(tc_gemm_kernel<M JET_COMMA false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 tc_smem_bytes<M>());                                                       \
+    if (e == cudaSuccess)                                                                                  \
+        e = cudaFuncSetAttribute(tc_gemm_kernel<M JET_COMMA true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 tc_dot_fits<M>() ? tc_smem_bytes<M>(true) : tc_smem_bytes<M>())
     JET_TCSM(JET_PREC_TF32);
     JET_TCSM(JET_PREC_TF32X3);
     JET_TCSM(JET_PREC_BF16X3);
@@ -941,24 +1243,22 @@ cudaError_t launch_tc_gemm(const TcGemmArgs &a, const LaunchCfg &c, cudaStream_t
 {
     const int64_t tiles = (int64_t)c.gx * c.gy * c.gz;   // persistent: one CTA per SM at most
     dim3 grid((unsigned)std::min<int64_t>(tiles, sm_count()), 1, 1);
+#define JET_GEMM(M)                                                                                      \
+    do {                                                                                                 \
+        if (a.dot_parts && (!tc_dot_fits<M>() || a.n_kb > tc_chunk_kb<M>()))                             \
+            return cudaErrorInvalidValue; /* no staging area, or more than one accumulator chunk */      \
+        if (a.dot_parts) tc_gemm_kernel<M, true><<<grid, TC_THREADS, tc_smem_bytes<M>(true), s>>>(a);    \
+        else tc_gemm_kernel<M, false><<<grid, TC_THREADS, tc_smem_bytes<M>(), s>>>(a);                   \
+    } while (0)
     switch (a.mode) {
-    case JET_PREC_TF32:
-        tc_gemm_kernel<JET_PREC_TF32><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_TF32>(), s>>>(a);
-        break;
-    case JET_PREC_TF32X3:
-        tc_gemm_kernel<JET_PREC_TF32X3><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_TF32X3>(), s>>>(a);
-        break;
-    case JET_PREC_BF16X3:
-        tc_gemm_kernel<JET_PREC_BF16X3><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_BF16X3>(), s>>>(a);
-        break;
-    case JET_PREC_BF16X6:
-        tc_gemm_kernel<JET_PREC_BF16X6><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_BF16X6>(), s>>>(a);
-        break;
-    case JET_PREC_FP16X3:
-        tc_gemm_kernel<JET_PREC_FP16X3><<<grid, TC_THREADS, tc_smem_bytes<JET_PREC_FP16X3>(), s>>>(a);
-        break;
+    case JET_PREC_TF32: JET_GEMM(JET_PREC_TF32); break;
+    case JET_PREC_TF32X3: JET_GEMM(JET_PREC_TF32X3); break;
+    case JET_PREC_BF16X3: JET_GEMM(JET_PREC_BF16X3); break;
+    case JET_PREC_BF16X6: JET_GEMM(JET_PREC_BF16X6); break;
+    case JET_PREC_FP16X3: JET_GEMM(JET_PREC_FP16X3); break;
     default: return cudaErrorInvalidValue;
     }
+#undef JET_GEMM
     return cudaGetLastError();
 }
 

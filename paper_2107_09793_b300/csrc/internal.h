@@ -112,7 +112,8 @@ struct Plan {
     // nodes with two feasible forms the autotuner may choose between: (node,
     // kind 0 = GEMM grouping / 1 = application form, the form taken) and a
     // signature of the node's shape that keys the tuner's cache
-    struct Tunable { int32_t node, kind, taken; std::string sig; };
+    // (node2: a second node whose time the choice also moves, or -1)
+    struct Tunable { int32_t node, kind, taken; std::string sig; int32_t node2 = -1; };
     std::vector<Tunable> tunables;
     std::vector<uint8_t> host_args;   // argument blocks (pointers patched at bind time)
     // pointer patch list: (byte offset in host_args, buffer id, element/byte offset)
@@ -177,6 +178,7 @@ struct RangeSet {
 struct TuneChoice {
     int8_t group = -1;      // GEMM route: instance blocks (1) or one product per instance (0)
     int8_t apply_tc = -1;   // small-operand application: tensor-core form (1) or CUDA-core form (0)
+    int8_t dot = -1;        // a GEMM whose parent is a dot product: dot epilogue (1) or its output (0)
 };
 
 struct Network {

@@ -97,10 +97,11 @@ struct ApplyArgs {
 
 // Sum the split-K partials of each output in a fixed order (deterministic).
 struct SplitKReduceArgs {
-    uint64_t partials;              // complex[n_inst][ksplit][n_out]
+    uint64_t partials;              // complex[n_inst][ksplit][n_out] (parts64: complex128)
     uint64_t ptrC;                  // device array of n_inst addresses
     int64_t n_out;
     int32_t n_inst, ksplit;
+    int32_t parts64, pad_;          // 1: FP64 partials summed in FP64 (a GEMM's dot epilogue)
 };
 
 // Gather a strided tensor into a dense one: dst[i] = src[off(i)], where the

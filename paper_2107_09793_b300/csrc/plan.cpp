@@ -60,6 +60,12 @@ struct NodeInfo {
     std::vector<int64_t> fz_mk, fz_nk, fz_kappa;
     size_t alloc_bytes = 0;          // arena bytes of buf_off (0: n_inst view.size elements)
     size_t fz_scales_off = 0;        // fz_ok: arena offset of the scales (the planes at buf_off)
+    // dot epilogue (pass 1: candidate; pass 2: dot_ok): the parent is a full dot
+    // product of this GEMM's output with its sibling; this node's epilogue adds
+    // each tile's part of the parent's products into partials at buf_off
+    // ([parent instance][dot_tiles] complex64), the parent only sums them
+    bool dot = false, dot_ok = false;
+    int32_t dot_tiles = 0;
 };
 
 struct Blob {
@@ -245,6 +251,7 @@ int tc_planes(int mode);
 int tc_elem_bytes(int mode);
 int tc_k_block(int mode);
 int tc_tile();
+int tc_dot_max_k(int mode);
 
 std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *outputs,
                                  const std::vector<int64_t> *slice_ids, const GradRequest *grad)
@@ -277,7 +284,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         if (tune_valid) {
             auto it = net.tune.find(v);
             if (it != net.tune.end()) {
-                const int c = kind == 0 ? it->second.group : it->second.apply_tc;
+                const int c = kind == 0 ? it->second.group : kind == 1 ? it->second.apply_tc : it->second.dot;
                 if (c >= 0) return c != 0;
             }
         }
@@ -657,10 +664,44 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     }
                 }
             }
+            // a parent that contracts this output with its sibling over every label
+            // (a dot product per instance): the epilogue computes the products
+            // itself; each side's labels in decreasing stride in the sibling (when
+            // its view is known), so a warp's reads of the sibling run along it
+            if (tc_mode && net.opt.fuse_split && dimprod(N.K) <= tc_dot_max_k(net.opt.precision) && !grad && pp >= 0 &&
+                !N.fuse) {
+                const int32_t sb = sibling[v];
+                bool full = labset[pp].empty() && labset[sb].size() == labset[v].size();
+                for (int64_t l : labset[v]) full = full && find_pos(labset[sb], l) >= 0;
+                // (a tunable choice: its time is this GEMM's and its parent's.  By
+                // default taken for outputs up to 16 GB: the epilogue's gathers cost
+                // a fixed time per tile, while the plain output and the parent's
+                // dot-product kernel stream at full bandwidth only on large outputs;
+                // measured on B300, 0.5 GB favours the epilogue, 69 GB the plain form)
+                if (full) {
+                    N.dot = tuned(v, 2, (double)N.n_inst * (double)dimprod(labset[v]) * (double)es <= 16e9);
+                    P.tunables.push_back({v, 2, N.dot ? 1 : 0,
+                                          sig_of(2, {dimprod(N.K), dimprod(labset[v]), N.n_inst, node[sb].n_inst,
+                                                     node[pp].n_inst}),
+                                          pp});
+                }
+                if (N.dot) {
+                    if (sb < v) {
+                        const View &Vs = node[sb].view;
+                        auto by_sib = [&](std::vector<int64_t> &ls) {
+                            std::stable_sort(ls.begin(), ls.end(), [&](int64_t x, int64_t y) {
+                                return Vs.strides[find_pos(Vs.labels, x)] > Vs.strides[find_pos(Vs.labels, y)];
+                            });
+                        };
+                        by_sib(N.fM);
+                        by_sib(N.fN);
+                    }
+                }
+            }
             // for a tensor-core parent, lay the output out as [parent-free, parent-summed]
             // when the parent's summed labels all come from one side: the parent's
             // operand split is then a plain format conversion
-            if (tc_mode && pp >= 0 && !N.fuse) {
+            if (tc_mode && pp >= 0 && !N.fuse && !N.dot) {
                 const auto &ls = labset[sibling[v]];
                 std::vector<int64_t> Kp, Fp, Fs;
                 for (int64_t l : labset[v]) (find_pos(ls, l) >= 0 ? Kp : Fp).push_back(l);
@@ -687,7 +728,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             // for a parent that applies a small operand: its summed labels slowest,
             // when one side holds them all (that side becomes M, their rows first)
             // (tensor-core route: the operand split gathers rows in any order)
-            const std::vector<int64_t> Kc = tc_mode && !N.fuse ? consumer_summed(v) : std::vector<int64_t>();
+            const std::vector<int64_t> Kc = tc_mode && !N.fuse && !N.dot ? consumer_summed(v) : std::vector<int64_t>();
             if (!Kc.empty()) {
                 auto holds_all = [&](const std::vector<int64_t> &X) {
                     for (int64_t l : Kc)
@@ -1559,8 +1600,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
     };
 
     // ---- pass 2, launch order: arena offsets, pointer tables, launches
+    std::vector<char> emitted(n_nodes, 0);
+    for (int32_t i = 0; i < n_leaves; ++i) emitted[i] = 1;
     for (int32_t v : order) {
         if (skip[v]) continue;   // a kept result stands for this sub-tree
+        emitted[v] = 1;          // (its launches precede every later node's)
         NodeInfo &N = node[v];
         const int32_t a = N.a, b = N.b;
         const NodeInfo &NA = node[a], &NB = node[b];
@@ -1656,8 +1700,91 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             }
         }
 
+        // dot epilogue: the parent's dot products of this output with its sibling
+        // (already computed: it launched before this node) are formed in this
+        // GEMM's epilogue, per tile, into partials in place of the output
+        std::vector<std::pair<int32_t, int64_t>> dot_a;   // per (instance, slot): the sibling instance
+        std::vector<int32_t> dot_pr, dot_xn;
+        std::vector<int64_t> dot_sm;
+        int32_t dot_lcol = 0;
+        N.dot_ok = false;
+        if (N.dot && use_gemm && tc_mode && dimprod(N.K) <= tc_dot_max_k(net.opt.precision) && !grad && !kept_v && !N.fz_ok &&
+            parent[v] >= 0 && !skip[parent[v]]) {
+            const int32_t pv = parent[v], sb = sibling[v];
+            const NodeInfo &Q = node[pv], &S_ = node[sb];
+            const int64_t Mv = dimprod(N.fM), Nv = dimprod(N.fN);
+            bool ok = emitted[sb] && !Q.use_gemm && Q.view.size == 1 && Mv % 128 == 0 && Nv % 128 == 0 &&
+                      Nv <= INT32_MAX && S_.view.size <= INT32_MAX &&
+                      std::find(P.kept_fill.begin(), P.kept_fill.end(), pv) == P.kept_fill.end();
+            for (int64_t l : N.view.labels) ok = ok && find_pos(S_.view.labels, l) >= 0 &&
+                                                 (net.labels.at(l).dim & (net.labels.at(l).dim - 1)) == 0;
+            ok = ok && S_.view.labels.size() == N.view.labels.size();
+            std::vector<int32_t> nslot(N.n_inst, 0);
+            if (ok) {
+                dot_a.assign((size_t)N.n_inst * 2, base_ref(sb, 0));
+                dot_pr.assign((size_t)N.n_inst * 2, -1);
+                const bool v_is_a = Q.a == v;
+                for (int64_t i = 0; i < Q.n_inst && ok; ++i) {
+                    const int32_t vi = v_is_a ? Q.ia[i] : Q.ib[i], si = v_is_a ? Q.ib[i] : Q.ia[i];
+                    if (vi < 0 || vi >= N.n_inst || nslot[vi] >= 2) {
+                        ok = false;   // at most two parent instances per instance of this node
+                        break;
+                    }
+                    dot_a[2 * (size_t)vi + nslot[vi]] = base_ref(sb, si);
+                    dot_pr[2 * (size_t)vi + nslot[vi]] = (int32_t)i;
+                    ++nslot[vi];
+                }
+            }
+            auto sstride = [&](int64_t l) { return S_.view.strides[find_pos(S_.view.labels, l)]; };
+            if (ok) {   // the sibling's offset of a row: per bit; of a column: by table
+                int bit = 0;
+                for (size_t q = N.fM.size(); q-- > 0 && ok;) {
+                    const int64_t d = net.labels.at(N.fM[q]).dim;
+                    for (int64_t w = 1; w < d; w *= 2) {
+                        if (bit >= JET_MAXR) {
+                            ok = false;
+                            break;
+                        }
+                        dot_sm.push_back(w * sstride(N.fM[q]));
+                        ++bit;
+                    }
+                }
+                dot_xn.assign((size_t)Nv, 0);
+                for (int64_t n = 0; n < Nv && ok; ++n) {
+                    int64_t r = n, off = 0;
+                    for (size_t q = N.fN.size(); q-- > 0;) {
+                        const int64_t d = net.labels.at(N.fN[q]).dim;
+                        off += (r % d) * sstride(N.fN[q]);
+                        r /= d;
+                    }
+                    dot_xn[(size_t)n] = (int32_t)off;
+                }
+            }
+            if (ok) {
+                N.dot_ok = true;
+                N.dot_tiles = (int32_t)((Mv / 128) * (Nv / 128));
+                // the epilogue copies pairs of values adjacent in the sibling: along
+                // the side that holds its stride-1 label (the lowest digit of the
+                // row or column index), all other offsets even, every sibling
+                // instance 16-byte aligned (the buffers are: the offsets decide)
+                if (Nv > 1 && dot_xn[1] == 1) dot_lcol = 1;
+                else if (!dot_sm.empty() && dot_sm[0] == 1) dot_lcol = 0;
+                else N.dot_ok = false;
+                for (size_t q = 0; q < dot_sm.size(); ++q)
+                    if (!(dot_lcol == 0 && q == 0) && dot_sm[q] % 2 != 0) N.dot_ok = false;
+                for (size_t n = 0; n < dot_xn.size(); ++n) {
+                    if ((dot_lcol == 0 || n % 2 == 0) && dot_xn[n] % 2 != 0) N.dot_ok = false;
+                    if (dot_lcol == 1 && n % 2 == 1 && dot_xn[n] != dot_xn[n - 1] + 1) N.dot_ok = false;
+                }
+                for (const auto &r : dot_a)
+                    if (r.second % 16 != 0) N.dot_ok = false;
+                if (!N.dot_ok) N.dot_tiles = 0;
+            }
+        }
+
         // arena buffer for all instances (a kept result: its slot in the pool)
         size_t nbytes = N.fz_ok ? fz_planes_bytes + fz_scales_bytes : (size_t)N.n_inst * N.view.size * es;
+        if (N.dot_ok) nbytes = (size_t)node[parent[v]].n_inst * N.dot_tiles * 16;   // complex128 partials
         N.alloc_bytes = nbytes;
         if (kept_v) {
             N.base = BASE_KEPT;
@@ -1696,8 +1823,34 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         std::vector<size_t> scratch;   // arena scratch freed after this node
         std::vector<size_t> scratch_bytes;
 
+        // ------------------------------------------------ dot products formed by a child's epilogue
+        const int32_t dot_child = node[a].dot_ok ? a : node[b].dot_ok ? b : -1;
+        if (dot_child >= 0) {
+            ++P.n_direct;
+            SplitKReduceArgs r;
+            std::memset(&r, 0, sizeof r);
+            r.n_out = 1;
+            r.n_inst = (int32_t)N.n_inst;
+            r.ksplit = node[dot_child].dot_tiles;   // the child's tiles, added in tile order in FP64
+            r.parts64 = 1;
+            size_t ro = blob.reserve(sizeof r);
+            std::memcpy(blob.bytes.data() + ro, &r, sizeof r);
+            blob.patch_field(ro, offsetof(SplitKReduceArgs, partials), BASE_ARENA, node[dot_child].buf_off);
+            blob.patch_field(ro, offsetof(SplitKReduceArgs, ptrC), BASE_BLOB, (int64_t)blob.put_ptrs(pc));
+            Op rop;
+            rop.kind = OpKind::SplitKReduce;
+            rop.node = v;
+            rop.n_inst = N.n_inst;
+            rop.args_off = ro;
+            rop.args_bytes = sizeof r;
+            rop.flop = 0;
+            rop.bytes = (double)N.n_inst * (double)r.ksplit * 16.0;
+            rop.variant = 0;
+            rop.grid_x = (int32_t)std::min<int64_t>((N.n_inst + 255) / 256, 65535);
+            P.ops.push_back(rop);
+        }
         // ------------------------------------------------ GEMM route (Section 3.1)
-        if (use_gemm) {
+        else if (use_gemm) {
             ++P.n_gemm;
             const bool a_is_m = N.a_is_m;       // the output layout's choice (pass 1)
             const int32_t idM = a_is_m ? a : b, idN = a_is_m ? b : a;
@@ -1920,6 +2073,13 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                               ? 1
                               : 0;
                 g.c_inst = N.n_inst;
+                if (N.dot_ok) {
+                    g.c_tma = 0;
+                    g.dot_mbits = (int32_t)dot_sm.size();
+                    for (size_t q = 0; q < dot_sm.size(); ++q) g.dot_sm[q] = dot_sm[q];
+                    g.dot_tiles = N.dot_tiles;
+                    g.dot_lcol = dot_lcol;
+                }
                 if (N.fz_ok) {
                     int lmk = 0, lnk = 0;
                     while (((int64_t)1 << lmk) < dimprod(N.fz_mk)) ++lmk;
@@ -1955,6 +2115,13 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     blob.patch_field(so, offsetof(TcGemmArgs, scaleA), BASE_ARENA, (int64_t)sclA);
                     blob.patch_field(so, offsetof(TcGemmArgs, scaleB), BASE_ARENA, (int64_t)sclB);
                 }
+                if (N.dot_ok) {   // dot epilogue: this epilogue forms the parent's products
+                    const size_t o_da = blob.put_ptrs(dot_a), o_dp = blob.put_i32(dot_pr), o_dx = blob.put_i32(dot_xn);
+                    blob.patch_field(so, offsetof(TcGemmArgs, dot_parts), BASE_ARENA, N.buf_off);
+                    blob.patch_field(so, offsetof(TcGemmArgs, dot_ptrA), BASE_BLOB, (int64_t)o_da);
+                    blob.patch_field(so, offsetof(TcGemmArgs, dot_pair), BASE_BLOB, (int64_t)o_dp);
+                    blob.patch_field(so, offsetof(TcGemmArgs, dot_xn), BASE_BLOB, (int64_t)o_dx);
+                }
                 if (N.fz_ok) {   // fused split: this epilogue writes the parent's planes
                     size_t o_ib = blob.reserve(fz_ibase.size() * 8, 8);
                     std::memcpy(blob.bytes.data() + o_ib, fz_ibase.data(), fz_ibase.size() * 8);
@@ -1980,7 +2147,12 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 op.grid_x = (int32_t)(n_pad / T);
                 op.grid_y = (int32_t)(m_pad / T);
                 op.grid_z = (int32_t)n_blocks;   // persistent launch: the tile count only
-                op.variant = (grouped ? 1 : 0) | (N.fz_ok ? 4 : 0);   // 4: writes its parent's planes
+                // 4: writes its parent's planes; 8: forms its parent's dot products
+                op.variant = (grouped ? 1 : 0) | (N.fz_ok ? 4 : 0) | (N.dot_ok ? 8 : 0);
+                if (N.dot_ok)   // the operand instances, the sibling's instances once, the partials
+                    op.bytes = (double)es * ((double)node[idM].n_inst * VM.size + (double)node[idN].n_inst * VN.size +
+                                             (double)node[sibling[v]].n_inst * node[sibling[v]].view.size) +
+                               (double)N.alloc_bytes;
                 P.ops.push_back(op);
             } else {
             int formM = form(VM, fM), formN = form(VN, fN);

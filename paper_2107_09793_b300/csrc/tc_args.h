@@ -75,4 +75,21 @@ struct TcGemmArgs {
     uint64_t fz_planes, fz_scales, fz_ibase, fz_pm, fz_pn;
     int64_t fz_plane_elems, fz_kpad, fz_rows_pad;
     int32_t fz_lmk, fz_lnk;
+    // Dot epilogue (dot_parts != 0): the parent contracts this output with a
+    // sibling tensor A over every label (a dot product per parent instance).
+    // Instead of C, every 128 x 128 tile (inside one node instance i: Mi, Ni
+    // multiples of 128) adds C[m][n] A_p[x] over its entries for the parent
+    // instances p that pair i (slots s < 2: A_p at dot_ptrA[2 i + s], p =
+    // dot_pair[2 i + s], -1 for none), x = sum of dot_sm[b] over the set bits b
+    // of m plus dot_xn[n]; the tile's sum goes to dot_parts[p dot_tiles + the
+    // tile's index in the instance] (complex128), summed over tiles in FP64.
+    // A's values of a warp's 32 rows x 8 columns are staged in shared memory by
+    // 16-byte asynchronous copies of two values adjacent in A: two columns of a
+    // row (dot_lcol = 1: A's stride-1 label is a column label) or two rows of a
+    // column (0: a row label); every offset other than the stride-1 label's
+    // digit is even and every A instance's address 16-byte aligned.
+    uint64_t dot_parts, dot_ptrA, dot_pair, dot_xn;
+    int64_t dot_sm[JET_MAXR];
+    int32_t dot_mbits, dot_tiles;
+    int32_t dot_lcol, dot_pad_;
 };
