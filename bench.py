@@ -49,9 +49,10 @@ GRID53_PLAN = dict(seed=1, n_trials=512, cap=1 << 28, reconfigure_passes=8)
 # (kernel form, node, algorithmic FLOP or bytes of the launch) so that another
 # plan, precision or form reports null instead of a stale figure.
 MEASURED_TRAFFIC = {
-    ("tc_gemm_kernel<fp16x3>", 1883, 8796093022208.0): 69.41e9,   # grid53, writes node 1884's planes
-    ("tc_gemm_kernel<fp16x3>", 1882, 8796093022208.0): 53.90e9,   # grid53, writes node 1883's planes
-    ("tc_gemm_kernel<fp16x3>", 1400, 8796093022208.0): 75.93e9,   # grid53
+    ("tc_gemm_kernel<fp16x3>", 1883, 8796093022208.0): 69.32e9,   # grid53, writes node 1884's planes
+    ("tc_gemm_kernel<fp16x3>", 1882, 8796093022208.0): 45.27e9,   # grid53, writes node 1883's planes
+    ("tc_gemm_kernel<fp16x3>", 1400, 8796093022208.0): 73.80e9,   # grid53
+    ("tc_gemm_kernel<fp16x3>", 1921, 1099511627776.0): 73.13e9,   # grid53, output-bound
     ("apply_tc_c64<fp16x3>", 1017, 1344274432.0): 1.2834e9,        # grid30
     ("apply_kernel_c64<fp16x3>", 1032, 1342308352.0): 1.3215e9,    # grid30
 }
