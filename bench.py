@@ -1281,6 +1281,46 @@ def run_fused_case(args):
     return 0
 
 
+def run_dot_case(args):
+    """A GEMM whose parent is a dot product with its sibling, at the shape of the
+    53-qubit root pair scaled down (about 1 GB, beyond L2): X[x, x', a, k] Y[k, b]
+    -> C (65536 x 256 per instance, K = 16, 4 instances), C . D[y, a, b] over a and
+    b (D's fastest labels alternate between a and b), joined by J[x, y, x'];
+    x, x', y sliced (8 slices, each C instance pairs with two D instances).
+    --fuse 1: the GEMM forms the dot products in its epilogue; 0: complex64 C and
+    the parent's dot-product kernel."""
+    import torch
+    from circuits import SplitMix64
+    from paper_2107_09793_b300 import jet
+    torch.cuda.set_device(0)
+    A = list(range(100, 116)); Kl = list(range(200, 204)); B = list(range(300, 308))
+    fast = [B[0], A[-1], A[-2], A[-3], B[1], B[2], A[-4], A[-5], B[3]]   # D's fastest labels first
+    ld = [501] + [l for l in A + B if l not in fast] + fast[::-1]
+    labels = [[500, 502] + A + Kl, Kl + B, ld, [500, 501, 502]]
+    rng = np.random.default_rng(SplitMix64(12).next_u64() % (1 << 32))
+    data = [(rng.random([2] * len(l)) - 0.5 + 1j * (rng.random([2] * len(l)) - 0.5)).astype(np.complex64)
+            for l in labels]
+    net = jet.Network(labels, data, precision="fp16x3", profile=2, fuse_split=bool(args.fuse))
+    net.set_open([])
+    net.path_set([(0, 1), (4, 2), (5, 3)])
+    net.slice([500, 501, 502])
+    rows, ids = np.zeros((1, 0), np.int32), list(range(8))
+    net.contract_slices(rows, ids)
+    for _ in range(args.warmup):
+        net.contract_slices(rows, ids)
+    kern = {}
+    for _ in range(args.steps):
+        net.contract_slices(rows, ids)
+        for r in net.profile():
+            if r["ms"] >= 0:
+                kern.setdefault(f'{r["kind"]} node {r["node"]} variant {r["variant"]}', []).append(r["ms"])
+    print(json.dumps({"case": "GEMM 65536 x 256 x 16 (4 instances) then dot products with D (2 instances), fp16x3",
+                      "fuse_split": int(args.fuse), "ms": {k: statistics.mean(v) for k, v in kern.items()}}),
+          flush=True)
+    net.close()
+    return 0
+
+
 def run_grid30_case(args):
     """Only the 30-qubit grid line (about 1.4 GB on the device): for launch lists
     and captures of its kernels."""
@@ -1328,9 +1368,10 @@ def main():
                     "parameterised circuit gradient, 53-qubit slices)")
     ap.add_argument("--gemm-shape", default="8192,8192,2048,1", help="--case gemm: M,N,K,IA[,IB]")
     ap.add_argument("--gemm-group", type=int, default=1, help="--case gemm: 1 groups instance pairs into blocks")
-    ap.add_argument("--fuse", type=int, default=1, help="--case fused: 1 fused split, 0 complex64 + split")
+    ap.add_argument("--fuse", type=int, default=1, help="--case fused / dot: 1 the epilogue fusion, 0 complex64 "
+                    "output and the next step")
     ap.add_argument("--case", default="workload", choices=["workload", "gemm", "apply", "gbs16", "grid53", "fused",
-                                                            "grid30"],
+                                                            "grid30", "dot"],
                     help="gemm / apply: one kernel family on a case sized for ncu captures; "
                          "gbs16: only the bosonic batch; grid53: only the headline contraction")
     args = ap.parse_args()
@@ -1342,6 +1383,8 @@ def main():
         return run_gbs16_case(args)
     if args.case == "grid53":
         return run_grid53_case(args)
+    if args.case == "dot":
+        return run_dot_case(args)
     if args.case == "fused":
         return run_fused_case(args)
     if args.case == "grid30":

@@ -400,19 +400,21 @@ __global__ void __launch_bounds__(256) direct_splitk_kernel(const __grid_constan
     }
 }
 
-// FP64 partials of single outputs (a GEMM's dot epilogue: many parts per output):
-// a warp per output, lane l adding parts l, l + 32, ... in order, then the 32
-// lane sums in a fixed butterfly (deterministic), rounded once to V.
-template <typename V>
+// Single outputs with many parts (a GEMM's dot epilogue, FP64 parts; a split-K
+// dot product): a warp per output, lane l adding parts l, l + 32, ... in order
+// (in the parts' precision, or FP64 for FP64 parts), then the 32 lane sums in a
+// fixed butterfly (deterministic), rounded once to V.
+template <typename V, typename P>
 __global__ void splitk_reduce_warp_kernel(const __grid_constant__ SplitKReduceArgs a)
 {
+    using R = decltype(P().x);
     const int64_t inst = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (inst >= a.n_inst) return;   // warp-uniform
-    const double2 *part = (const double2 *)a.partials + inst * a.ksplit;
-    double sx = 0.0, sy = 0.0;
+    const P *part = (const P *)a.partials + inst * a.ksplit;
+    R sx = 0, sy = 0;
     for (int p = lane; p < a.ksplit; p += 32) {
-        const double2 v = part[p];
+        const P v = part[p];
         sx += v.x;
         sy += v.y;
     }
@@ -782,10 +784,14 @@ cudaError_t set_direct_smem_limits()
 
 cudaError_t launch_splitk_reduce(const SplitKReduceArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    if (a.parts64 && a.n_out == 1) {   // a warp per output (grid from the outputs)
+    if (a.n_out == 1 && (a.parts64 || a.ksplit >= 64)) {   // a warp per output (grid from the outputs)
         const unsigned g = (unsigned)(((int64_t)a.n_inst * 32 + 255) / 256);
-        if (c.variant & 1) splitk_reduce_warp_kernel<double2><<<g, 256, 0, s>>>(a);
-        else splitk_reduce_warp_kernel<float2><<<g, 256, 0, s>>>(a);
+        if (a.parts64 || (c.variant & 1)) {
+            if (c.variant & 1) splitk_reduce_warp_kernel<double2, double2><<<g, 256, 0, s>>>(a);
+            else splitk_reduce_warp_kernel<float2, double2><<<g, 256, 0, s>>>(a);
+        } else {
+            splitk_reduce_warp_kernel<float2, float2><<<g, 256, 0, s>>>(a);
+        }
     } else if (a.parts64) {
         if (c.variant & 1) splitk_reduce_kernel<double2, double2><<<c.gx, 256, 0, s>>>(a);
         else splitk_reduce_kernel<float2, double2><<<c.gx, 256, 0, s>>>(a);
