@@ -50,12 +50,21 @@ GRID53_PLAN = dict(seed=1, n_trials=512, cap=1 << 28, reconfigure_passes=8)
 # plan, precision or form reports null instead of a stale figure.
 MEASURED_TRAFFIC = {
     ("tc_gemm_kernel<fp16x3>", 1883, 8796093022208.0): 69.32e9,   # grid53, writes node 1884's planes
-    ("tc_gemm_kernel<fp16x3>", 1882, 8796093022208.0): 45.27e9,   # grid53, writes node 1883's planes
-    ("tc_gemm_kernel<fp16x3>", 1400, 8796093022208.0): 73.80e9,   # grid53
-    ("tc_gemm_kernel<fp16x3>", 1921, 1099511627776.0): 73.13e9,   # grid53, output-bound
+    ("tc_gemm_kernel<fp16x3>", 1882, 8796093022208.0): 53.85e9,   # grid53, writes node 1883's planes
+    ("tc_gemm_kernel<fp16x3>", 1400, 8796093022208.0): 76.10e9,   # grid53
+    ("tc_gemm_kernel<fp16x3, dot epilogue>", 1921, 1099511627776.0): 81.85e9,   # grid53, forms the root's products
+    ("tc_gemm_kernel<fp16x3>", 1921, 1099511627776.0): 73.13e9,   # grid53, output-bound (plain form)
     ("apply_tc_c64<fp16x3>", 1017, 1344274432.0): 1.2834e9,        # grid30
     ("apply_kernel_c64<fp16x3>", 1032, 1342308352.0): 1.3215e9,    # grid30
 }
+
+
+def traffic_of(kname, rec, work):
+    """MEASURED_TRAFFIC of one launch record (a GEMM in its dot-epilogue form is
+    a kernel form of its own)."""
+    if kname.startswith("tc_gemm_kernel<") and rec["variant"] & 8:
+        kname = kname[:-1] + ", dot epilogue>"
+    return MEASURED_TRAFFIC.get((kname, rec["node"], rec[work]))
 
 
 def load_peaks():
@@ -543,7 +552,7 @@ def grid30_line(args, dev, peaks, peak_src):
             peak = peaks["bf16_tflops_sustained"] * (0.5 if args.precision.startswith("tf32") else 1.0)
             kname = f"tc_gemm_kernel<{args.precision}>" if tc else "gemm_simt_kernel"
             roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["node"], recs[big]["flop"])), "kernel": kname,
+                    "traffic": traffic_of(kname, recs[big], "flop"), "kernel": kname,
                     "per_launch_ms": ms, "flop_per_launch": recs[big]["flop"],
                     "issued_tensor_tflops": achieved * issue if tc else None,
                     "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)"
@@ -766,7 +775,7 @@ def roofline_of(recs, timed, prec, peaks, peak_src, step_ms):
         achieved = flop / (ms * 1e-3) / 1e12
         peak = tc_peak / issue
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["node"], recs[big]["flop"])),
+                "traffic": traffic_of(kname, recs[big], "flop"),
                 "issued_tensor_tflops": achieved * issue, "tensor_peak_for_dtype": tc_peak,
                 "peak_source": f"bf16_tflops_sustained of {peak_src}" + (" x 1/2 (tf32 nominal ratio)" if tf32 else "")
                                + f" / {issue} ({issue} tensor products per real product): the algorithmic ceiling"}
@@ -774,7 +783,7 @@ def roofline_of(recs, timed, prec, peaks, peak_src, step_ms):
         achieved = nbytes / (ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
-                "traffic": MEASURED_TRAFFIC.get((kname, recs[big]["node"], recs[big]["bytes"])),
+                "traffic": traffic_of(kname, recs[big], "bytes"),
                 "peak_source": f"hbm_gbs of {peak_src}"}
     roof.update(common)
     roof["kinds_timed_ms_per_range"] = {k: sum(timed[i] for i in v) for k, v in by_kind.items()}

@@ -116,9 +116,8 @@ typedef struct {
                                  contracted with its sibling over every label, with its
                                  summed extent in one accumulator chunk, forms those dot
                                  products per tile (the parent only adds the tiles' parts;
-                                 taken by default for outputs up to 16 GB, a choice that
-                                 jet_autotune times); 0: complex64 output, contracted by
-                                 the next step                                            */
+                                 a choice that jet_autotune times); 0: complex64 output,
+                                 contracted by the next step                              */
 } jet_options;
 
 typedef struct {

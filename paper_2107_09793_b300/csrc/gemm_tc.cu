@@ -445,7 +445,7 @@ constexpr int TC_CST_BYTES = TC_EPI_WARPS * 32 * TC_CST_ROW * 8 > TC_EPI_WARPS *
 constexpr int TC_DOT_BUFS = 5;
 constexpr int TC_DOT_WARP_BYTES = TC_DOT_BUFS * 2048;
 constexpr int TC_SMEM_LIMIT = 232448;   // opt-in dynamic shared memory per block
-constexpr int TC_STATIC_SMEM = 4096;    // barriers, scale staging and flags (upper bound)
+constexpr int TC_STATIC_SMEM = 6144;    // barriers, scale staging and flags (upper bound)
 // K blocks (pipeline stages) per accumulator chunk
 template <int MODE>
 __host__ __device__ constexpr int tc_chunk_kb()
@@ -542,30 +542,26 @@ __device__ __forceinline__ void cp_async_wait_upto(int n)
     else asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
-// Dot form: the tiles at one position within a node instance come together
-// over the block's instances (j, l), so that instances that pair with one
-// sibling read its tile at about the same time (the later reads from L2):
-// t = ((inst tiles_mi + tmi) tiles_ni + tni) nA nB + j nB + l, Mi and Ni
-// multiples of 128.  key: the instance's itab index; tni: its column tile.
-__device__ __forceinline__ void tile_coords_dot(int64_t t, const TcGemmArgs &a, int &inst, int &tm, int &tn,
-                                                int64_t &key, int64_t &tni)
+// Dot form: step st is tile position (tmi, tni) of dot block d = st % dot_nblk
+// (blocks fastest, so that blocks sharing sibling instances read them at about
+// the same time, the later ones from L2); its tile k (0, 1) is that of the
+// block's instance c_k (c_0 again when the block has one), entry (j, l) of GEMM
+// block b: rows j Mi + 128 tmi, columns l Ni + 128 tni.
+__device__ __forceinline__ void tile_coords_pair(int64_t st, int k, const TcGemmArgs &a, int &inst, int &tm, int &tn)
 {
-    const int64_t nab = (int64_t)a.nA * a.nB, tmi_n = a.Mi >> 7, tni_n = a.Ni >> 7;
-    int64_t r = t / nab;
-    const int64_t jl = t - r * nab, j = jl / a.nB, l = jl - j * a.nB;
-    tni = r % tni_n;
-    r /= tni_n;
-    const int64_t tmi = r % tmi_n;
-    inst = (int)(r / tmi_n);
-    tm = (int)(j * tmi_n + tmi);
-    tn = (int)(l * tni_n + tni);
-    key = (int64_t)inst * nab + jl;
+    const int64_t tmi_n = a.Mi >> 7, tni_n = a.Ni >> 7, nb = a.dot_nblk;
+    const int64_t d = st % nb, r = st / nb, tni = r % tni_n, tmi = r / tni_n;
+    const int32_t *blk = (const int32_t *)a.dot_pair + 8 * d;
+    int32_t c = __ldg(blk + k);
+    if (c < 0) c = __ldg(blk);
+    const int32_t *cp = (const int32_t *)a.dot_cpos + 3 * (int64_t)c;
+    inst = __ldg(cp);
+    tm = (int)(__ldg(cp + 1) * tmi_n + tmi);
+    tn = (int)(__ldg(cp + 2) * tni_n + tni);
 }
 
 // (DOT: the dot-epilogue form, launched when a.dot_parts is set; a form of its
-// own so that its registers do not weigh on the others.  Its tiles end in the
-// dot block, which leaves the rest of the tile loop unreachable there.)
-#pragma nv_diag_suppress 128
+// own so that its registers do not weigh on the others)
 template <int MODE, bool DOT>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcGemmArgs a)
 {
@@ -589,6 +585,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     const int64_t total_tiles = (int64_t)a.n_inst * tiles_m * tiles_n;
     const int n_kb = a.n_kb;
     const int n_chunks = (n_kb + CHUNK_KB - 1) / CHUNK_KB;
+    // steps of the launch: tiles, or (dot form) tile positions of a dot block,
+    // PER tiles each
+    constexpr int PER = DOT ? 2 : 1;
+    const int64_t n_steps = DOT ? (int64_t)a.dot_nblk * (a.Mi >> 7) * (a.Ni >> 7) : total_tiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -616,14 +616,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     if (warp == 0) {
         if (lane == 0) {
             int64_t kg = 0, issued = 0;
-            for (int64_t t = blockIdx.x; t < total_tiles && !abort_flag; t += gridDim.x) {
+            for (int64_t st = blockIdx.x; st < n_steps && !abort_flag; st += gridDim.x)
+                for (int k = 0; k < PER && !abort_flag; ++k) {
                 int inst, tm, tn;
-                if (DOT) {
-                    int64_t key_, tni_;
-                    tile_coords_dot(t, a, inst, tm, tn, key_, tni_);
-                } else {
-                    tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
-                }
+                if (DOT) tile_coords_pair(st, k, a, inst, tm, tn);
+                else tile_coords(st, tiles_m, tiles_n, inst, tm, tn);
                 const int zA = ((const int32_t *)a.zA)[inst], zB = ((const int32_t *)a.zB)[inst];
                 for (int kb = 0; kb < n_kb; ++kb, ++kg) {
                     const int s = (int)(kg % S);
@@ -654,7 +651,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                                    ((uint32_t)(TC_BM >> 4) << 24);
             const uint32_t idesc_neg = idesc | (1u << 13);
             int64_t kg = 0, cg = 0;
-            for (int64_t t = blockIdx.x; t < total_tiles && !abort_flag; t += gridDim.x) {
+            for (int64_t st = blockIdx.x; st < n_steps && !abort_flag; st += gridDim.x)
+                for (int k = 0; k < PER && !abort_flag; ++k) {
                 for (int c = 0; c < n_chunks && !abort_flag; ++c, ++cg) {
                     const int buf = (int)(cg & 1);
                     if (cg >= 2 && !mbar_wait_bounded(tempty0 + 8 * buf, (uint32_t)(((cg >> 1) - 1) & 1), &abort_flag)) {
@@ -709,35 +707,167 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         // of the C staging
         float2 *dstage = (float2 *)(smem + (size_t)S * STAGE_BYTES + (size_t)(warp - 2) * TC_DOT_WARP_BYTES);
         int32_t *fz_rn = (int32_t *)(fz_t64 + 12);
-        // dot form: the next tile's lookups, loaded one tile ahead
-        int32_t n_pr0 = -1, n_pr1 = -1, n_xn0 = 0, n_xn1 = 0;
-        const float2 *n_A0 = nullptr, *n_A1 = nullptr;
-        auto dot_lookup = [&](int64_t tt) {
-            n_pr0 = n_pr1 = -1;
-            if (tt >= total_tiles) return;
-            int ii, tm_, tn_;
-            int64_t key, tni;
-            tile_coords_dot(tt, a, ii, tm_, tn_, key, tni);
-            const int32_t *xn = (const int32_t *)a.dot_xn + (tni << 7) + half * 64;
-            n_xn0 = __ldg(xn + lane);
-            n_xn1 = __ldg(xn + 32 + lane);
-            const int64_t it = a.itab ? __ldg((const int32_t *)a.itab + key) : ii;
-            if (it >= 0) {
-                n_pr0 = __ldg((const int32_t *)a.dot_pair + 2 * it);
-                n_pr1 = __ldg((const int32_t *)a.dot_pair + 2 * it + 1);
-                n_A0 = (const float2 *)__ldg((const unsigned long long *)a.dot_ptrA + 2 * it);
-                n_A1 = (const float2 *)__ldg((const unsigned long long *)a.dot_ptrA + 2 * it + 1);
+        if (DOT) {
+            // dot epilogue (the whole summed extent in one accumulator chunk): per
+            // step, the parts of up to four products (the block's two tiles times
+            // its two sibling instances), read straight from the two accumulators,
+            // which the warp holds until the step is done.  A's values are staged
+            // 8 columns at a time (TC_DOT_BUFS 2 KB buffers: the copies of the units
+            // after this one run while it is read, the first ones while the
+            // accumulators fill), each unit dotted with both tiles.  The block's
+            // lookups are loaded one step ahead.  The epilogue warps may be up to
+            // two steps apart, so the parts and counters live in a ring of four
+            __shared__ float2 dred[4][TC_EPI_WARPS][4];
+            __shared__ float sfn1[TC_EPI_WARPS][64];   // the second tile's column scales
+            const int64_t tmi_n = a.Mi >> 7, tni_n = a.Ni >> 7, nb = a.dot_nblk;
+            int32_t n_c[2] = {-1, -1}, n_p[4] = {-1, -1, -1, -1};
+            const float2 *n_A[2] = {nullptr, nullptr};
+            auto lookup = [&](int64_t st) {
+                if (st >= n_steps) return;
+                const int64_t d = st % nb;
+                const int4 v0 = __ldg((const int4 *)a.dot_pair + 2 * d), v1 = __ldg((const int4 *)a.dot_pair + 2 * d + 1);
+                n_c[0] = v0.x;
+                n_c[1] = v0.y;
+                n_p[0] = v0.z;
+                n_p[1] = v0.w;
+                n_p[2] = v1.x;
+                n_p[3] = v1.y;
+                n_A[0] = (const float2 *)__ldg((const unsigned long long *)a.dot_ptrA + 2 * d);
+                n_A[1] = (const float2 *)__ldg((const unsigned long long *)a.dot_ptrA + 2 * d + 1);
+            };
+            lookup(blockIdx.x);
+            int64_t i = 0;
+            for (int64_t st = blockIdx.x; st < n_steps; st += gridDim.x, ++i) {
+                const int64_t r = st / nb, tni = r % tni_n, tmi = r / tni_n;
+                const int32_t c0 = n_c[0], c1 = n_c[1] >= 0 ? n_c[1] : n_c[0];
+                const int32_t p00 = n_p[0], p01 = n_p[1], p10 = n_p[2], p11 = n_p[3];
+                const float2 *A0 = n_A[0], *A1 = n_A[1];
+                lookup(st + gridDim.x);
+                // units: sibling m = u / 8, columns 8 (u % 8) ..; sibling 1 only when
+                // a product uses it
+                const int U = (p01 >= 0 || p11 >= 0) ? 16 : 8;
+                const int32_t *xn = (const int32_t *)a.dot_xn + (tni << 7) + half * 64;
+                const int32_t xn0 = __ldg(xn + lane), xn1 = __ldg(xn + 32 + lane);
+                const int64_t mm = (tmi << 7) + quarter * 32 + lane;
+                int64_t xm = 0;
+                for (int b = 0; b < a.dot_mbits; ++b)
+                    if ((mm >> b) & 1) xm += a.dot_sm[b];
+#pragma unroll
+                for (int u = 0; u < TC_DOT_BUFS - 1; ++u) dot_stage(a, A0, xm, xn0, xn1, u, dstage + u * 256, lane);
+                // SCALED: the two tiles' row and column scales
+                float fm0 = 1.f, fm1 = 1.f;
+                if (Cfg::SCALED) {
+                    __syncwarp();
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int32_t *cp = (const int32_t *)a.dot_cpos + 3 * (int64_t)(k ? c1 : c0);
+                        const int b = __ldg(cp);
+                        const int64_t tm = __ldg(cp + 1) * tmi_n + tmi, tn = __ldg(cp + 2) * tni_n + tni;
+                        const int64_t instA = ((const int32_t *)a.zA)[b] / NP, instB = ((const int32_t *)a.zB)[b] / NP;
+                        const float f = __ldg((const float *)a.scaleA + instA * a.m_pad + tm * TC_BM + quarter * 32 + lane);
+                        const float *g = (const float *)a.scaleB + instB * a.n_pad + tn * TC_BN + half * 64;
+                        float *fnk = k ? sfn1[warp - 2] : sfn[warp - 2];
+                        fnk[lane] = __ldg(g + lane);
+                        fnk[lane + 32] = __ldg(g + lane + 32);
+                        if (k) fm1 = f;
+                        else fm0 = f;
+                    }
+                    __syncwarp();
+                }
+                // the step's two tiles: buffers 0 and 1 (cg is even here)
+                if (!mbar_wait_bounded(tfull0, (uint32_t)((cg >> 1) & 1), &abort_flag) ||
+                    !mbar_wait_bounded(tfull0 + 8, (uint32_t)((cg >> 1) & 1), &abort_flag)) {
+                    abort_flag = 1;
+                    asm volatile("cp.async.wait_all;" ::: "memory");   // no staged copy outlives the block
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base0 = tmem + ((uint32_t)(quarter * 32) << 16) + half * 64, base1 = base0 + 2 * TC_BN;
+                float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // (re, im) of (k, m) = (0,0) (0,1) (1,0) (1,1)
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    if (u < U) {   // warp-uniform
+                        constexpr int AH = TC_DOT_BUFS - 1;   // units in flight ahead of this one
+                        if (u + AH < U)
+                            dot_stage(a, u + AH < 8 ? A0 : A1, xm, xn0, xn1, (u + AH) & 7,
+                                      dstage + ((u + AH) % TC_DOT_BUFS) * 256, lane);
+                        uint32_t R0[8], I0[8], R1[8], I1[8];
+                        JET_TMEM_LD8(base0 + (u & 7) * 8, R0);
+                        JET_TMEM_LD8(base0 + TC_BN + (u & 7) * 8, I0);
+                        JET_TMEM_LD8(base1 + (u & 7) * 8, R1);
+                        JET_TMEM_LD8(base1 + TC_BN + (u & 7) * 8, I1);
+                        cp_async_wait_upto(min(AH, U - 1 - u));   // unit u has landed
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        __syncwarp();
+                        float2 avs[8];
+                        dot_read(a, dstage + (u % TC_DOT_BUFS) * 256, lane, avs);
+                        float x0 = 0.f, y0 = 0.f, x1 = 0.f, y1 = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int cj = (u & 7) * 8 + j;
+                            const float f0 = Cfg::SCALED ? fm0 * sfn[warp - 2][cj] : 1.f;
+                            const float f1 = Cfg::SCALED ? fm1 * sfn1[warp - 2][cj] : 1.f;
+                            const float ar = __uint_as_float(R0[j]) * f0, ai = __uint_as_float(I0[j]) * f0;
+                            const float br = __uint_as_float(R1[j]) * f1, bi = __uint_as_float(I1[j]) * f1;
+                            const float2 av = avs[j];
+                            x0 = fmaf(ar, av.x, fmaf(-ai, av.y, x0));
+                            y0 = fmaf(ar, av.y, fmaf(ai, av.x, y0));
+                            x1 = fmaf(br, av.x, fmaf(-bi, av.y, x1));
+                            y1 = fmaf(br, av.y, fmaf(bi, av.x, y1));
+                        }
+                        const int m = u < 8 ? 0 : 1;
+                        s[2 * m] += x0;
+                        s[2 * m + 1] += y0;
+                        s[4 + 2 * m] += x1;
+                        s[4 + 2 * m + 1] += y1;
+                        __syncwarp();   // the buffer is refilled TC_DOT_BUFS - 1 units on
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {   // both accumulators are free
+                    mbar_arrive(tempty0);
+                    mbar_arrive(tempty0 + 8);
+                }
+                cg += 2;
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], o);
+                const int par = (int)(i & 3);   // this CTA's step count, mod 4
+                if (lane == 0) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dred[par][warp - 2][q] = make_float2(s[2 * q], s[2 * q + 1]);
+                }
+                // the last of the eight epilogue warps to finish the step adds their
+                // parts in warp order (no barrier: a warp that gave up on a wait
+                // never holds the others)
+                int last = 0;
+                if (lane == 0) {
+                    __threadfence_block();
+                    last = atomicAdd(&dot_cnt[par], 1) == TC_EPI_WARPS - 1;
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (last) {
+                    __threadfence_block();
+                    const int32_t pr = lane == 0 ? p00 : lane == 1 ? p01 : lane == 2 ? p10 : p11;
+                    if (lane < 4 && pr >= 0) {   // the eight parts added in FP64, the tile's part kept in FP64
+                        const volatile float2 *dr = dred[par][0] + lane;
+                        double ax = dr[0].x, ay = dr[0].y;
+                        for (int w = 1; w < TC_EPI_WARPS; ++w) {
+                            ax += dr[4 * w].x;
+                            ay += dr[4 * w].y;
+                        }
+                        ((double2 *)a.dot_parts)[(int64_t)pr * a.dot_tiles + tmi * tni_n + tni] = make_double2(ax, ay);
+                    }
+                    __syncwarp();
+                    if (lane == 0) dot_cnt[par] = 0;
+                }
             }
-        };
-        if (DOT) dot_lookup(blockIdx.x);
+        } else
         for (int64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
             int inst, tm, tn;
-            if (DOT) {
-                int64_t key_, tni_;
-                tile_coords_dot(t, a, inst, tm, tn, key_, tni_);
-            } else {
-                tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
-            }
+            tile_coords(t, tiles_m, tiles_n, inst, tm, tn);
             if (Cfg::SCALED && a.fz_planes) {
                 const int64_t c0 = (int64_t)tn * TC_BN + half * 64;
                 __syncwarp();   // the previous tile's readers of the lookups are done
@@ -777,133 +907,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
                     }
                 }
                 __syncwarp();
-            }
-            if (DOT) {
-                // dot epilogue (the whole summed extent in one accumulator chunk):
-                // this tile's part of the parent's dot products, read straight from
-                // the accumulator, which the warp holds until it is done.  The
-                // tile's instance and its parent pairs are looked up one tile
-                // ahead; A's values are staged 8 columns at a time (TC_DOT_BUFS
-                // 2 KB buffers: the copies of the units after this one run while
-                // it is read, the first ones while the accumulator fills).  The
-                // epilogue warps may be up to two tiles apart, so the parts and
-                // counters live in a ring of four tiles
-                __shared__ float2 dred[4][TC_EPI_WARPS][2];
-                int64_t mt0 = (int64_t)tm * TC_BM, nt0 = (int64_t)tn * TC_BN, jj = 0, ll = 0;
-                if (a.itab) {
-                    jj = a.mi_shift >= 0 ? mt0 >> a.mi_shift : mt0 / a.Mi;
-                    mt0 -= jj * a.Mi;
-                    ll = a.ni_shift >= 0 ? nt0 >> a.ni_shift : nt0 / a.Ni;
-                    nt0 -= ll * a.Ni;
-                }
-                const int32_t d_pr0 = n_pr0, d_pr1 = n_pr1, xn0 = n_xn0, xn1 = n_xn1;
-                const float2 *d_A0 = n_A0, *d_A1 = n_A1;
-                dot_lookup(t + gridDim.x);
-                const int U = 8 * ((d_pr0 >= 0) + (d_pr1 >= 0));   // units: slot u / 8, columns 8 (u % 8) ..
-                const int64_t mm = mt0 + quarter * 32 + lane;
-                int64_t xm = 0;
-                for (int b = 0; b < a.dot_mbits; ++b)
-                    if ((mm >> b) & 1) xm += a.dot_sm[b];
-#pragma unroll
-                for (int u = 0; u < TC_DOT_BUFS - 1; ++u)
-                    if (u < U) dot_stage(a, d_A0, xm, xn0, xn1, u, dstage + u * 256, lane);
-                // SCALED: the row's and the warp's 64 column scales of the chunk
-                float fm = 1.f;
-                float *fn = sfn[warp - 2];
-                if (Cfg::SCALED) {
-                    const int64_t instA = ((const int32_t *)a.zA)[inst] / NP, instB = ((const int32_t *)a.zB)[inst] / NP;
-                    fm = __ldg((const float *)a.scaleA + instA * a.m_pad + (int64_t)tm * TC_BM + quarter * 32 + lane);
-                    const float *g = (const float *)a.scaleB + instB * a.n_pad + (int64_t)tn * TC_BN + half * 64;
-                    __syncwarp();
-                    fn[lane] = __ldg(g + lane);
-                    fn[lane + 32] = __ldg(g + lane + 32);
-                    __syncwarp();
-                }
-                const int buf = (int)(cg & 1);
-                if (!mbar_wait_bounded(tfull0 + 8 * buf, (uint32_t)((cg >> 1) & 1), &abort_flag)) {
-                    abort_flag = 1;
-                    asm volatile("cp.async.wait_all;" ::: "memory");   // no staged copy outlives the block
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t base = tmem + buf * 2 * TC_BN + ((uint32_t)(quarter * 32) << 16) + half * 64;
-                float sx0 = 0.f, sy0 = 0.f, sx1 = 0.f, sy1 = 0.f;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    if (u < U) {   // warp-uniform (one instance per tile)
-                        constexpr int AH = TC_DOT_BUFS - 1;   // units in flight ahead of this one
-                        if (u + AH < U)
-                            dot_stage(a, u + AH < 8 ? d_A0 : d_A1, xm, xn0, xn1, (u + AH) & 7,
-                                      dstage + ((u + AH) % TC_DOT_BUFS) * 256, lane);
-                        uint32_t R[8], I[8];
-                        JET_TMEM_LD8(base + (u & 7) * 8, R);
-                        JET_TMEM_LD8(base + TC_BN + (u & 7) * 8, I);
-                        cp_async_wait_upto(min(AH, U - 1 - u));   // unit u has landed
-                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        __syncwarp();
-                        float2 avs[8];
-                        dot_read(a, dstage + (u % TC_DOT_BUFS) * 256, lane, avs);
-                        float sx = 0.f, sy = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const float f = Cfg::SCALED ? fm * fn[(u & 7) * 8 + j] : 1.f;
-                            const float cr = __uint_as_float(R[j]) * f, ci = __uint_as_float(I[j]) * f;
-                            const float2 av = avs[j];
-                            sx = fmaf(cr, av.x, fmaf(-ci, av.y, sx));
-                            sy = fmaf(cr, av.y, fmaf(ci, av.x, sy));
-                        }
-                        if (u < 8) {
-                            sx0 += sx;
-                            sy0 += sy;
-                        } else {
-                            sx1 += sx;
-                            sy1 += sy;
-                        }
-                        __syncwarp();   // the buffer is refilled TC_DOT_BUFS - 1 units on
-                    }
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);   // the accumulator is free
-                ++cg;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    sx0 += __shfl_xor_sync(0xffffffffu, sx0, o);
-                    sy0 += __shfl_xor_sync(0xffffffffu, sy0, o);
-                    sx1 += __shfl_xor_sync(0xffffffffu, sx1, o);
-                    sy1 += __shfl_xor_sync(0xffffffffu, sy1, o);
-                }
-                const int par = (int)(((t - blockIdx.x) / gridDim.x) & 3);   // this CTA's tile count, mod 4
-                if (lane == 0) {
-                    dred[par][warp - 2][0] = make_float2(sx0, sy0);
-                    dred[par][warp - 2][1] = make_float2(sx1, sy1);
-                }
-                // the last of the eight epilogue warps to finish the tile adds their
-                // parts in warp order (no barrier: a warp that gave up on a wait
-                // never holds the others)
-                int last = 0;
-                if (lane == 0) {
-                    __threadfence_block();
-                    last = atomicAdd(&dot_cnt[par], 1) == TC_EPI_WARPS - 1;
-                }
-                last = __shfl_sync(0xffffffffu, last, 0);
-                if (last) {
-                    __threadfence_block();
-                    const int32_t pr = lane ? d_pr1 : d_pr0;
-                    if (lane < 2 && pr >= 0) {   // the eight parts added in FP64, the tile's part kept in FP64
-                        const volatile float2 *dr = dred[par][0] + lane;
-                        double ax = dr[0].x, ay = dr[0].y;
-                        for (int w = 1; w < TC_EPI_WARPS; ++w) {
-                            ax += dr[2 * w].x;
-                            ay += dr[2 * w].y;
-                        }
-                        const int64_t tile = (mt0 >> 7) * (a.Ni >> 7) + (nt0 >> 7);
-                        ((double2 *)a.dot_parts)[(int64_t)pr * a.dot_tiles + tile] = make_double2(ax, ay);
-                    }
-                    __syncwarp();
-                    if (lane == 0) dot_cnt[par] = 0;
-                }
-                continue;
             }
             float racc[64], iacc[64];
 #pragma unroll
@@ -1130,7 +1133,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     }
     if (threadIdx.x == 0 && abort_flag) atomicOr((unsigned int *)a.status, 1u);
 }
-#pragma nv_diag_default 128
 
 // ------------------------------------------------------------------ host side
 template <int MODE>

@@ -16,6 +16,7 @@
 // a best-fit allocator simulated in launch order, so the arena size is the
 // peak of live intermediates.
 #include <algorithm>
+#include <map>
 #include <cstring>
 #include <numeric>
 #include <unordered_map>
@@ -673,13 +674,10 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                 const int32_t sb = sibling[v];
                 bool full = labset[pp].empty() && labset[sb].size() == labset[v].size();
                 for (int64_t l : labset[v]) full = full && find_pos(labset[sb], l) >= 0;
-                // (a tunable choice: its time is this GEMM's and its parent's.  By
-                // default taken for outputs up to 16 GB: the epilogue's gathers cost
-                // a fixed time per tile, while the plain output and the parent's
-                // dot-product kernel stream at full bandwidth only on large outputs;
-                // measured on B300, 0.5 GB favours the epilogue, 69 GB the plain form)
+                // (a tunable choice, taken by default: its time is this GEMM's and
+                // its parent's)
                 if (full) {
-                    N.dot = tuned(v, 2, (double)N.n_inst * (double)dimprod(labset[v]) * (double)es <= 16e9);
+                    N.dot = tuned(v, 2, true);
                     P.tunables.push_back({v, 2, N.dot ? 1 : 0,
                                           sig_of(2, {dimprod(N.K), dimprod(labset[v]), N.n_inst, node[sb].n_inst,
                                                      node[pp].n_inst}),
@@ -1703,7 +1701,11 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
         // dot epilogue: the parent's dot products of this output with its sibling
         // (already computed: it launched before this node) are formed in this
         // GEMM's epilogue, per tile, into partials in place of the output
-        std::vector<std::pair<int32_t, int64_t>> dot_a;   // per (instance, slot): the sibling instance
+        // (dot blocks: up to two instances of this node that pair the same sibling
+        // instances, up to two; per block dot_pr holds {c0, c1, p00, p01, p10, p11,
+        // 0, 0}, c1 = -1 for none, p_km the parent instance of (c_k, sibling m) or
+        // -1, and dot_a its two sibling instances)
+        std::vector<std::pair<int32_t, int64_t>> dot_a;
         std::vector<int32_t> dot_pr, dot_xn;
         std::vector<int64_t> dot_sm;
         int32_t dot_lcol = 0;
@@ -1719,21 +1721,40 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
             for (int64_t l : N.view.labels) ok = ok && find_pos(S_.view.labels, l) >= 0 &&
                                                  (net.labels.at(l).dim & (net.labels.at(l).dim - 1)) == 0;
             ok = ok && S_.view.labels.size() == N.view.labels.size();
-            std::vector<int32_t> nslot(N.n_inst, 0);
             if (ok) {
-                dot_a.assign((size_t)N.n_inst * 2, base_ref(sb, 0));
-                dot_pr.assign((size_t)N.n_inst * 2, -1);
+                // each instance's (sibling instance, parent instance) pairs, at most two
+                std::vector<std::vector<std::pair<int32_t, int32_t>>> sl((size_t)N.n_inst);
                 const bool v_is_a = Q.a == v;
                 for (int64_t i = 0; i < Q.n_inst && ok; ++i) {
                     const int32_t vi = v_is_a ? Q.ia[i] : Q.ib[i], si = v_is_a ? Q.ib[i] : Q.ia[i];
-                    if (vi < 0 || vi >= N.n_inst || nslot[vi] >= 2) {
+                    if (vi < 0 || vi >= N.n_inst || sl[(size_t)vi].size() >= 2) {
                         ok = false;   // at most two parent instances per instance of this node
                         break;
                     }
-                    dot_a[2 * (size_t)vi + nslot[vi]] = base_ref(sb, si);
-                    dot_pr[2 * (size_t)vi + nslot[vi]] = (int32_t)i;
-                    ++nslot[vi];
+                    sl[(size_t)vi].push_back({si, (int32_t)i});
                 }
+                // instances with equal sibling sets, two to a block (in instance order)
+                std::map<std::vector<int32_t>, std::vector<int32_t>> by_set;
+                for (int32_t vi = 0; ok && vi < (int32_t)N.n_inst; ++vi) {
+                    auto &x = sl[(size_t)vi];
+                    if (x.empty()) continue;   // no product to form
+                    std::sort(x.begin(), x.end());
+                    std::vector<int32_t> key;
+                    for (const auto &pq : x) key.push_back(pq.first);
+                    by_set[key].push_back(vi);
+                }
+                for (const auto &kv : by_set) {
+                    const auto &key = kv.first;
+                    const auto &cs = kv.second;
+                    for (size_t q = 0; q < cs.size(); q += 2) {
+                        const int32_t c0 = cs[q], c1 = q + 1 < cs.size() ? cs[q + 1] : -1;
+                        auto pr = [&](int32_t c, size_t m) { return c >= 0 && m < key.size() ? sl[(size_t)c][m].second : -1; };
+                        const int32_t row[8] = {c0, c1, pr(c0, 0), pr(c0, 1), pr(c1, 0), pr(c1, 1), 0, 0};
+                        dot_pr.insert(dot_pr.end(), row, row + 8);
+                        for (size_t m = 0; m < 2; ++m) dot_a.push_back(base_ref(sb, key[m < key.size() ? m : 0]));
+                    }
+                }
+                ok = ok && !dot_pr.empty() && dot_pr.size() / 8 <= INT32_MAX;
             }
             auto sstride = [&](int64_t l) { return S_.view.strides[find_pos(S_.view.labels, l)]; };
             if (ok) {   // the sibling's offset of a row: per bit; of a column: by table
@@ -2079,6 +2100,7 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     for (size_t q = 0; q < dot_sm.size(); ++q) g.dot_sm[q] = dot_sm[q];
                     g.dot_tiles = N.dot_tiles;
                     g.dot_lcol = dot_lcol;
+                    g.dot_nblk = (int32_t)(dot_pr.size() / 8);
                 }
                 if (N.fz_ok) {
                     int lmk = 0, lnk = 0;
@@ -2116,7 +2138,31 @@ std::unique_ptr<Plan> build_plan(Network &net, int32_t n_amps, const int32_t *ou
                     blob.patch_field(so, offsetof(TcGemmArgs, scaleB), BASE_ARENA, (int64_t)sclB);
                 }
                 if (N.dot_ok) {   // dot epilogue: this epilogue forms the parent's products
+                    // each instance's place in the launch: its block and its (j, l) there
+                    std::vector<int32_t> cpos((size_t)N.n_inst * 3, -1);
+                    if (grouped) {
+                        for (int64_t b = 0; b < n_blocks; ++b)
+                            for (int32_t j = 0; j < G.nA; ++j)
+                                for (int32_t l = 0; l < G.nB; ++l) {
+                                    const int32_t it = G.itab[((size_t)b * G.nA + j) * G.nB + l];
+                                    if (it < 0) continue;
+                                    cpos[3 * (size_t)it] = (int32_t)b;
+                                    cpos[3 * (size_t)it + 1] = j;
+                                    cpos[3 * (size_t)it + 2] = l;
+                                }
+                    } else {
+                        for (int64_t i = 0; i < N.n_inst; ++i) {
+                            cpos[3 * (size_t)i] = (int32_t)i;
+                            cpos[3 * (size_t)i + 1] = cpos[3 * (size_t)i + 2] = 0;
+                        }
+                    }
+                    for (size_t q = 0; q < dot_pr.size(); q += 8)
+                        for (int k = 0; k < 2; ++k)
+                            if (dot_pr[q + k] >= 0 && cpos[3 * (size_t)dot_pr[q + k]] < 0)
+                                fail(JET_EINVAL, "dot epilogue: an instance outside the GEMM's blocks");
                     const size_t o_da = blob.put_ptrs(dot_a), o_dp = blob.put_i32(dot_pr), o_dx = blob.put_i32(dot_xn);
+                    const size_t o_cp = blob.put_i32(cpos);
+                    blob.patch_field(so, offsetof(TcGemmArgs, dot_cpos), BASE_BLOB, (int64_t)o_cp);
                     blob.patch_field(so, offsetof(TcGemmArgs, dot_parts), BASE_ARENA, N.buf_off);
                     blob.patch_field(so, offsetof(TcGemmArgs, dot_ptrA), BASE_BLOB, (int64_t)o_da);
                     blob.patch_field(so, offsetof(TcGemmArgs, dot_pair), BASE_BLOB, (int64_t)o_dp);

@@ -77,19 +77,24 @@ struct TcGemmArgs {
     int32_t fz_lmk, fz_lnk;
     // Dot epilogue (dot_parts != 0): the parent contracts this output with a
     // sibling tensor A over every label (a dot product per parent instance).
-    // Instead of C, every 128 x 128 tile (inside one node instance i: Mi, Ni
-    // multiples of 128) adds C[m][n] A_p[x] over its entries for the parent
-    // instances p that pair i (slots s < 2: A_p at dot_ptrA[2 i + s], p =
-    // dot_pair[2 i + s], -1 for none), x = sum of dot_sm[b] over the set bits b
-    // of m plus dot_xn[n]; the tile's sum goes to dot_parts[p dot_tiles + the
-    // tile's index in the instance] (complex128), summed over tiles in FP64.
+    // Instead of C, the launch runs dot_nblk blocks of up to two node instances
+    // that pair the same A instances (up to two): dot_pair[8 d ..] = {c0, c1,
+    // p00, p01, p10, p11, 0, 0} (c1 = -1 for none; p_km the parent instance of
+    // c_k with A instance m, or -1), A_m at dot_ptrA[2 d + m]; node instance c
+    // is entry (j, l) of GEMM block b, (b, j, l) = dot_cpos[3 c ..].  A step is
+    // one 128 x 128 tile position (Mi, Ni multiples of 128) of one dot block,
+    // steps ordered block fastest; its two tiles (c0's and c1's, c0's again for
+    // none) accumulate in the two TMEM buffers, and every tile entry (m, n) adds
+    // C_k[m][n] A_m[x] to product p_km, x = the sum of dot_sm[b] over the set
+    // bits b of m plus dot_xn[n]; a tile's sum goes to dot_parts[p dot_tiles +
+    // the tile's index in the instance] (complex128), summed over tiles in FP64.
     // A's values of a warp's 32 rows x 8 columns are staged in shared memory by
     // 16-byte asynchronous copies of two values adjacent in A: two columns of a
     // row (dot_lcol = 1: A's stride-1 label is a column label) or two rows of a
     // column (0: a row label); every offset other than the stride-1 label's
     // digit is even and every A instance's address 16-byte aligned.
-    uint64_t dot_parts, dot_ptrA, dot_pair, dot_xn;
+    uint64_t dot_parts, dot_ptrA, dot_pair, dot_xn, dot_cpos;
     int64_t dot_sm[JET_MAXR];
     int32_t dot_mbits, dot_tiles;
-    int32_t dot_lcol, dot_pad_;
+    int32_t dot_lcol, dot_nblk;
 };
