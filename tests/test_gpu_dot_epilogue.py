@@ -33,18 +33,34 @@ def _rand(rng, shape):
     return (re + 1j * im).reshape(shape).astype(np.complex64)
 
 
-def network(d_along="rows"):
+def network(d_along="rows", form="pairs"):
+    """form: "pairs" (x, x' on X, y on D: 4 C instances, each pairing both D
+    instances, two to a dot block), "single" (no y: 4 C instances, one D
+    instance, U = 8 staged units per step), "unpaired" (no x, x': one C
+    instance pairing both D instances, alone in its block)."""
     rng = SplitMix64(4242)
-    lx, ly = [500, 502] + A_L + K_L, K_L + B_L
+    xs = [] if form == "unpaired" else [500, 502]
+    ys = [] if form == "single" else [501]
+    lx, ly = xs + A_L + K_L, K_L + B_L
     if d_along == "rows":
-        ld = [501] + B_L[::-1] + A_L[4:] + A_L[:4]
+        ld = ys + B_L[::-1] + A_L[4:] + A_L[:4]
     else:
-        ld = [501] + A_L[::-1] + B_L[4:] + B_L[:4]
-    lj = [500, 501, 502]
+        ld = ys + A_L[::-1] + B_L[4:] + B_L[:4]
+    lj = sorted(xs + ys)
     labels = [lx, ly, ld, lj]
     data = [_rand(rng, [2] * len(l)) for l in labels]
     path = [(0, 1), (4, 2), (5, 3)]
-    return labels, data, path, [500, 501, 502]
+    return labels, data, path, lj
+
+
+def _oracle_slices(labels, data, path, sl):
+    d64 = [t.astype(np.complex128) for t in data]
+    n = len(sl)
+    ref = []
+    for s in range(2 ** n):
+        sll, sd = slice_network(labels, d64, sl, [(s >> (n - 1 - j)) & 1 for j in range(n)])
+        ref.append(complex(contract_network(sll, sd, path)[1]))
+    return np.array(ref)
 
 
 @pytest.mark.gpu
@@ -67,14 +83,32 @@ def test_dot_epilogue_matches_the_oracle_per_slice(prec, d_along):
     else:
         assert dot, recs
         assert [r for r in recs if r["kind"] == "splitk_reduce" and r["node"] == 5], recs
-    d64 = [t.astype(np.complex128) for t in data]
-    ref = []
-    for s in range(8):
-        sll, sd = slice_network(labels, d64, sl, [(s >> 2) & 1, (s >> 1) & 1, s & 1])
-        ref.append(complex(contract_network(sll, sd, path)[1]))
-    ref = np.array(ref)
+    ref = _oracle_slices(labels, data, path, sl)
     err = float(np.max(np.abs(np.asarray(got) - ref)) / np.max(np.abs(ref)))
     print(f"dot epilogue {prec}, D along {d_along}: max per-slice err {err:.2e}")
+    assert err <= 1e-5
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("d_along", ["rows", "cols"])
+@pytest.mark.parametrize("form", ["single", "unpaired"])
+def test_dot_epilogue_blocks_with_one_sibling_or_one_instance(form, d_along):
+    """Dot blocks that stage one sibling instance (8 units per step) or hold one
+    node instance (its tile computed twice, the second tile's products unused)."""
+    labels, data, path, sl = network(d_along, form)
+    net = jet.Network(labels, data, precision="fp16x3", profile=2)
+    try:
+        net.set_open([])
+        net.path_set(path)
+        net.slice(sl)
+        got = net.contract_slices(np.zeros((1, 0), np.int32), list(range(2 ** len(sl))))[0]
+        recs = net.profile()
+    finally:
+        net.close()
+    assert [r for r in recs if r["kind"] == "gemm_tc" and r["node"] == 4 and r["variant"] & 8], recs
+    ref = _oracle_slices(labels, data, path, sl)
+    err = float(np.max(np.abs(np.asarray(got) - ref)) / np.max(np.abs(ref)))
+    print(f"dot epilogue, {form} blocks, D along {d_along}: max per-slice err {err:.2e}")
     assert err <= 1e-5
 
 
@@ -99,12 +133,7 @@ def test_autotuner_chooses_between_the_dot_epilogue_and_the_plain_output():
     dot = [r for r in recs if r["kind"] == "gemm_tc" and r["node"] == 4 and r["variant"] & 8]
     plain = [r for r in recs if r["kind"] == "direct" and r["node"] == 5]
     assert bool(dot) != bool(plain), recs
-    d64 = [t_.astype(np.complex128) for t_ in data]
-    ref = []
-    for s in range(8):
-        sll, sd = slice_network(labels, d64, sl, [(s >> 2) & 1, (s >> 1) & 1, s & 1])
-        ref.append(complex(contract_network(sll, sd, path)[1]))
-    ref = np.array(ref)
+    ref = _oracle_slices(labels, data, path, sl)
     err = float(np.max(np.abs(np.asarray(got) - ref)) / np.max(np.abs(ref)))
     print(f"autotuned ({'dot epilogue' if dot else 'plain output'}): {t}, max per-slice err {err:.2e}")
     assert err <= 1e-5
