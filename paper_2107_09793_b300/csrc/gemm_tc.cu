@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     __shared__ __align__(8) uint64_t bars[2 * S + 4];
     __shared__ uint32_t tmem_holder;
     __shared__ int abort_flag;
-    __shared__ int dot_cnt[4];   // dot epilogue: warps done with the tile (a ring of four tiles)
+    __shared__ int dot_cnt[4];   // dot epilogue: warps done with the step (a ring of four steps)
 
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

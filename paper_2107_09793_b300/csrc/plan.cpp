@@ -64,7 +64,7 @@ struct NodeInfo {
     // dot epilogue (pass 1: candidate; pass 2: dot_ok): the parent is a full dot
     // product of this GEMM's output with its sibling; this node's epilogue adds
     // each tile's part of the parent's products into partials at buf_off
-    // ([parent instance][dot_tiles] complex64), the parent only sums them
+    // ([parent instance][dot_tiles] complex128), the parent only sums them
     bool dot = false, dot_ok = false;
     int32_t dot_tiles = 0;
 };
