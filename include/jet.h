@@ -462,9 +462,11 @@ int jet_stats(const jet_network *net, jet_stats_t *out);
 
 /* Autotuner (not in the paper): for the contraction of these outputs, choose
  * per tree node between the kernel forms that both take the node's shape --
- * the GEMM route's instance blocks or one product per instance, and a small
- * operand's tensor-core application or its CUDA-core form -- by timing them on
- * the device.  Two timed runs (each the second of two, CUDA events around every
+ * the GEMM route's instance blocks or one product per instance, a small
+ * operand's tensor-core application or its CUDA-core form, and a GEMM whose
+ * parent is a dot product forming those products in its epilogue or writing
+ * its output (timed together with the parent) -- by timing them on the
+ * device.  Two timed runs (each the second of two, CUDA events around every
  * launch): every tunable node in its default form, then every one in its
  * other form; a node takes the other form where that ran at least 3% faster,
  * and the choices are kept only if a third run of the whole plan is not slower
