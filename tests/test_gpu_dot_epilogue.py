@@ -37,10 +37,11 @@ def network(d_along="rows", form="pairs"):
     """form: "pairs" (x, x' on X, y on D: 4 C instances, each pairing both D
     instances, two to a dot block), "single" (no y: 4 C instances, one D
     instance, U = 8 staged units per step), "unpaired" (no x, x': one C
-    instance pairing both D instances, alone in its block)."""
+    instance pairing both D instances, alone in its block), "four" (y, y' on
+    D: each C instance pairs four D instances, beyond the form's two)."""
     rng = SplitMix64(4242)
     xs = [] if form == "unpaired" else [500, 502]
-    ys = [] if form == "single" else [501]
+    ys = [] if form == "single" else [501, 503] if form == "four" else [501]
     lx, ly = xs + A_L + K_L, K_L + B_L
     if d_along == "rows":
         ld = ys + B_L[::-1] + A_L[4:] + A_L[:4]

@@ -429,22 +429,25 @@ def test_small_levels_run_as_chained_launches():
         net.close()
 
 
-@pytest.mark.parametrize("prec,fuse,dot", [("fp16x3", True, True), ("tf32x3", True, True), ("bf16x6", True, False),
-                                            ("fp16x3", False, False)])
-def test_dot_epilogue_plan_and_arena_liveness(prec, fuse, dot):
+@pytest.mark.parametrize("prec,fuse,form,dot", [("fp16x3", True, "pairs", True), ("tf32x3", True, "pairs", True),
+                                                 ("bf16x6", True, "pairs", False), ("fp16x3", False, "pairs", False),
+                                                 ("fp16x3", True, "single", True), ("fp16x3", True, "unpaired", True),
+                                                 ("fp16x3", True, "four", False)])
+def test_dot_epilogue_plan_and_arena_liveness(prec, fuse, form, dot):
     """A GEMM whose parent is a full dot product with its sibling: the plan takes
     the dot-epilogue form (the GEMM marked, the parent only a reduce of the tile
-    parts) in the modes that have room for its staging and with the epilogue
-    fusions on, the plain output and the parent's dot-product kernel otherwise;
-    the tile parts' buffer obeys the liveness rule."""
+    parts) in the modes that have room for its staging, with the epilogue
+    fusions on and at most two sibling instances per instance; the plain output
+    and the parent's dot-product kernel otherwise; the tile parts' buffer obeys
+    the liveness rule."""
     from test_gpu_dot_epilogue import network
-    labels, data, path, sl = network("cols")
+    labels, data, path, sl = network("cols", form)
     net = jet.Network(labels, data, precision=prec, fuse_split=fuse)
     try:
         net.set_open([])
         net.path_set(path)
         net.slice(sl)
-        net.plan_slices(np.zeros((1, 0), np.int32), list(range(8)))
+        net.plan_slices(np.zeros((1, 0), np.int32), list(range(2 ** len(sl))))
         recs = net.profile()
         gemm = [r for r in recs if r["kind"] == "gemm_tc" and r["node"] == 4]
         parent = {r["kind"] for r in recs if r["node"] == 5}
